@@ -1,0 +1,753 @@
+// CPU FP64 oracle for the discrete contact model's per-pair overlap evaluation.
+//
+// TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+// benchmark's CPU-baseline leg load this library.  It shares no code, header,
+// table or helper with the CUDA library; it is the plain, slow, direct
+// definition that the CUDA path is checked against.
+//
+// Paper: Marquardt, Hafen, Krause, "A novel model for direct numerical
+// simulation of suspension dynamics with arbitrarily shaped convex particles"
+// (arXiv:2401.10878).
+//   * Sec. 2.2: poses refer to the centre of mass X_p (torque reference).
+//   * Sec. 2.3, Eq. (contact_force_normal): F_n = 4/(3 pi) n_c E* sqrt(V_c d)(1 + c ddot_n);
+//     E* = ((1-nu_A^2)/E_A + (1-nu_B^2)/E_B)^-1; Eq. (damping_factor) for c.
+//   * Sec. 3.3.1: contact = sweep over the sample points of the overlap region,
+//     giving overlap volume, contact point, contact normal, indentation depth, force.
+//     A node belongs to a particle by the sign of its signed distance.
+//   * Sec. 3.3.2: across a periodic boundary the contact lives on the side of
+//     the lower-ID particle; the higher-ID particle is shifted there.
+//   * Sec. 5.1: contact enlargement of the particles (inflate parameter).
+//
+// Readings where the paper is silent (each is restated in the design notes):
+//   sample set = lattice nodes k*dx of the intersection of the two particles'
+//   node-range AABBs; sharp indicator H = [phi <= 0]; polytope/cuboid SDF =
+//   max over face planes; smoothed indicator H_w(phi) = S(clamp(1/2 - phi/(w dx),0,1)),
+//   S(t) = 3t^2 - 2t^3; contact normal from G = 1/2 (dV/dX_A - dV/dX_B) in its
+//   band form; indentation depth d = max over overlap nodes of (-phi_A - phi_B);
+//   prefactor 4/(3 pi) as printed; one damping factor c for all contacts.
+//
+// The per-pair evaluation is a template over the scalar type so that the same
+// code, run with forward-mode dual numbers, yields the oracle's own FP64
+// gradient of sum_p (gF_p . F_p + gT_p . T_p) with respect to the poses.
+//
+// Build: g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared [-fopenmp].
+// Contraction must stay off: the AABB node ranges are compared bit for bit.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// ----------------------------------------------------------------------------
+// status codes (same numbering as the public C-ABI, written independently)
+enum { OR_OK = 0, OR_EINVAL = 1, OR_EDOMAIN = 5 };
+enum { SH_SPHERE = 0, SH_CUBOID = 1, SH_POLYTOPE = 2 };
+
+// ----------------------------------------------------------------------------
+// forward-mode dual number with NT tangent directions
+constexpr int NT = 14;
+
+struct Dual {
+  double v;
+  double g[NT];
+  Dual() : v(0.0) { for (double& x : g) x = 0.0; }
+  Dual(double a) : v(a) { for (double& x : g) x = 0.0; }  // NOLINT (implicit by design)
+};
+
+inline Dual operator+(const Dual& a, const Dual& b) {
+  Dual r; r.v = a.v + b.v; for (int i = 0; i < NT; ++i) r.g[i] = a.g[i] + b.g[i]; return r;
+}
+inline Dual operator-(const Dual& a, const Dual& b) {
+  Dual r; r.v = a.v - b.v; for (int i = 0; i < NT; ++i) r.g[i] = a.g[i] - b.g[i]; return r;
+}
+inline Dual operator-(const Dual& a) {
+  Dual r; r.v = -a.v; for (int i = 0; i < NT; ++i) r.g[i] = -a.g[i]; return r;
+}
+inline Dual operator*(const Dual& a, const Dual& b) {
+  Dual r; r.v = a.v * b.v;
+  for (int i = 0; i < NT; ++i) r.g[i] = a.g[i] * b.v + a.v * b.g[i];
+  return r;
+}
+inline Dual operator/(const Dual& a, const Dual& b) {
+  Dual r; r.v = a.v / b.v;
+  for (int i = 0; i < NT; ++i) r.g[i] = (a.g[i] * b.v - a.v * b.g[i]) / (b.v * b.v);
+  return r;
+}
+inline Dual operator+(const Dual& a, double b) { Dual r = a; r.v += b; return r; }
+inline Dual operator+(double a, const Dual& b) { Dual r = b; r.v += a; return r; }
+inline Dual operator-(const Dual& a, double b) { Dual r = a; r.v -= b; return r; }
+inline Dual operator-(double a, const Dual& b) { Dual r = -b; r.v += a; return r; }
+inline Dual operator*(const Dual& a, double b) {
+  Dual r; r.v = a.v * b; for (int i = 0; i < NT; ++i) r.g[i] = a.g[i] * b; return r;
+}
+inline Dual operator*(double a, const Dual& b) { return b * a; }
+inline Dual operator/(const Dual& a, double b) {
+  Dual r; r.v = a.v / b; for (int i = 0; i < NT; ++i) r.g[i] = a.g[i] / b; return r;
+}
+inline Dual operator/(double a, const Dual& b) { return Dual(a) / b; }
+inline Dual sqrt(const Dual& a) {
+  Dual r; r.v = std::sqrt(a.v);
+  for (int i = 0; i < NT; ++i) r.g[i] = (r.v > 0.0) ? a.g[i] / (2.0 * r.v) : 0.0;
+  return r;
+}
+inline Dual fabs(const Dual& a) { return (a.v < 0.0) ? -a : a; }
+
+inline double val(double x) { return x; }
+inline double val(const Dual& x) { return x.v; }
+inline double sqrt_s(double x) { return std::sqrt(x); }
+inline Dual sqrt_s(const Dual& x) { return sqrt(x); }
+inline double fabs_s(double x) { return std::fabs(x); }
+inline Dual fabs_s(const Dual& x) { return fabs(x); }
+
+// ----------------------------------------------------------------------------
+struct Config {
+  int32_t n_cells[3];
+  double dx;
+  int32_t indicator;     // 0 sharp, 1 smoothed
+  double smooth_width;   // w in lattice cells
+  double inflate;        // physical length, subtracted from every SDF (Sec. 5.1)
+  double damping_c;      // c of Eq. (damping_factor), shared by all contacts
+  double band_eps;       // classification band in lattice units (diagnostics only)
+};
+
+struct Shape {
+  int type = SH_SPHERE;
+  double p[3] = {0, 0, 0};         // sphere: radius; cuboid: half extents
+  std::vector<double> planes;      // polytope: (n0, n1, n2, d) per face, n.y <= d
+  std::vector<double> verts;       // vertices of the offset shape used for the AABB
+};
+
+// Rotation matrix of the normalised quaternion (w, x, y, z), Hamilton
+// convention, body -> world, row-major.  The operation order is fixed (and
+// contraction is off) because the AABB node ranges are compared bit for bit.
+template <class S>
+void quat_to_rot(const S q_in[4], S R[9]) {
+  S nrm = sqrt_s(((q_in[0] * q_in[0] + q_in[1] * q_in[1]) + q_in[2] * q_in[2]) + q_in[3] * q_in[3]);
+  S w = q_in[0] / nrm, x = q_in[1] / nrm, y = q_in[2] / nrm, z = q_in[3] / nrm;
+  R[0] = 1.0 - 2.0 * (y * y + z * z);
+  R[1] = 2.0 * (x * y - w * z);
+  R[2] = 2.0 * (x * z + w * y);
+  R[3] = 2.0 * (x * y + w * z);
+  R[4] = 1.0 - 2.0 * (x * x + z * z);
+  R[5] = 2.0 * (y * z - w * x);
+  R[6] = 2.0 * (x * z - w * y);
+  R[7] = 2.0 * (y * z + w * x);
+  R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+// Vertices of the convex polytope {y : n_i . y <= d_i + delta}: every plane
+// triple solved by Cramer's rule, kept when it satisfies all half-spaces.
+std::vector<double> polytope_vertices(const std::vector<double>& pl, double delta) {
+  std::vector<double> out;
+  const int F = static_cast<int>(pl.size() / 4);
+  double dmax = 1.0;
+  for (int i = 0; i < F; ++i) dmax = std::max(dmax, std::fabs(pl[4 * i + 3] + delta));
+  const double tol = 1e-9 * dmax;
+  for (int i = 0; i < F; ++i)
+    for (int j = i + 1; j < F; ++j)
+      for (int k = j + 1; k < F; ++k) {
+        const double* a = &pl[4 * i];
+        const double* b = &pl[4 * j];
+        const double* c = &pl[4 * k];
+        const double bc[3] = {b[1] * c[2] - b[2] * c[1], b[2] * c[0] - b[0] * c[2], b[0] * c[1] - b[1] * c[0]};
+        const double ca[3] = {c[1] * a[2] - c[2] * a[1], c[2] * a[0] - c[0] * a[2], c[0] * a[1] - c[1] * a[0]};
+        const double ab[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+        const double det = a[0] * bc[0] + a[1] * bc[1] + a[2] * bc[2];
+        if (std::fabs(det) < 1e-12) continue;
+        const double da = a[3] + delta, db = b[3] + delta, dc = c[3] + delta;
+        double v[3];
+        for (int t = 0; t < 3; ++t) v[t] = (da * bc[t] + db * ca[t] + dc * ab[t]) / det;
+        bool inside = true;
+        for (int m = 0; m < F && inside; ++m) {
+          const double* e = &pl[4 * m];
+          if (e[0] * v[0] + e[1] * v[1] + e[2] * v[2] - (e[3] + delta) > tol) inside = false;
+        }
+        if (inside) out.insert(out.end(), v, v + 3);
+      }
+  return out;
+}
+
+// A polyhedron {n_i . y <= d_i} with all d_i > 0 is bounded iff no direction u
+// has n_i . u <= 0 for all i.  Extreme rays of the recession cone lie on
+// intersections of two plane boundaries, so testing +-(n_i x n_j) suffices.
+bool polytope_bounded(const std::vector<double>& pl) {
+  const int F = static_cast<int>(pl.size() / 4);
+  if (F < 4) return false;
+  for (int i = 0; i < F; ++i)
+    for (int j = i + 1; j < F; ++j) {
+      const double* a = &pl[4 * i];
+      const double* b = &pl[4 * j];
+      double u[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+      const double nu = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+      if (nu < 1e-12) continue;
+      for (int sgn = -1; sgn <= 1; sgn += 2) {
+        bool ray = true;
+        for (int m = 0; m < F && ray; ++m) {
+          const double* e = &pl[4 * m];
+          if (sgn * (e[0] * u[0] + e[1] * u[1] + e[2] * u[2]) / nu > 1e-12) ray = false;
+        }
+        if (ray) return false;
+      }
+    }
+  return true;
+}
+
+// Signed distance of a shape at world point x (physical units), reduced by
+// `inflate`; also the world gradient of the active branch and, for ties, the
+// gap between the largest and second-largest face value (inf for a sphere).
+template <class S>
+S sdf(const Shape& sh, const S X[3], const S R[9], const double x[3], double inflate, S grad[3],
+      double* gap) {
+  S r[3] = {x[0] - X[0], x[1] - X[1], x[2] - X[2]};
+  if (sh.type == SH_SPHERE) {
+    S nr = sqrt_s(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (val(nr) > 0.0) {
+      for (int k = 0; k < 3; ++k) grad[k] = r[k] / nr;
+    } else {
+      for (int k = 0; k < 3; ++k) grad[k] = S(0.0);
+    }
+    *gap = std::numeric_limits<double>::infinity();
+    return nr - sh.p[0] - inflate;
+  }
+  // body coordinates y = R^T r
+  S y[3];
+  for (int k = 0; k < 3; ++k) y[k] = R[0 * 3 + k] * r[0] + R[1 * 3 + k] * r[1] + R[2 * 3 + k] * r[2];
+  S best(0.0);
+  double gb[3] = {0, 0, 0};
+  double bestv = -std::numeric_limits<double>::infinity();
+  double second = -std::numeric_limits<double>::infinity();
+  if (sh.type == SH_CUBOID) {
+    for (int k = 0; k < 3; ++k) {
+      S a = fabs_s(y[k]) - sh.p[k];
+      if (val(a) > bestv) {
+        second = bestv;
+        bestv = val(a);
+        best = a;
+        gb[0] = gb[1] = gb[2] = 0.0;
+        gb[k] = (val(y[k]) < 0.0) ? -1.0 : 1.0;
+      } else if (val(a) > second) {
+        second = val(a);
+      }
+    }
+  } else {
+    const int F = static_cast<int>(sh.planes.size() / 4);
+    for (int i = 0; i < F; ++i) {
+      const double* e = &sh.planes[4 * i];
+      S a = (e[0] * y[0] + e[1] * y[1] + e[2] * y[2]) - e[3];
+      if (val(a) > bestv) {
+        second = bestv;
+        bestv = val(a);
+        best = a;
+        gb[0] = e[0]; gb[1] = e[1]; gb[2] = e[2];
+      } else if (val(a) > second) {
+        second = val(a);
+      }
+    }
+  }
+  for (int k = 0; k < 3; ++k) grad[k] = R[k * 3 + 0] * gb[0] + R[k * 3 + 1] * gb[1] + R[k * 3 + 2] * gb[2];
+  *gap = bestv - second;
+  return best - inflate;
+}
+
+// Indicator H(phi) and the derivative of the smoothed profile dH_w/dphi.
+// Sharp mode: H = [phi <= 0]; the derivative (used by the normal) is always
+// the smoothed one.  Smoothed mode: H = S(t), t = clamp(1/2 - phi/wdx, 0, 1).
+template <class S>
+void indicator(bool smooth, double wdx, const S& phi, S* H, S* Hp) {
+  S t = 0.5 - phi / wdx;
+  if (val(t) <= 0.0) {
+    *Hp = S(0.0);
+    if (smooth) *H = S(0.0);
+  } else if (val(t) >= 1.0) {
+    *Hp = S(0.0);
+    if (smooth) *H = S(1.0);
+  } else {
+    *Hp = -6.0 * t * (1.0 - t) / wdx;
+    if (smooth) *H = t * t * (3.0 - 2.0 * t);
+  }
+  if (!smooth) *H = S(val(phi) <= 0.0 ? 1.0 : 0.0);
+}
+
+struct PairGeom {
+  int i, j;
+  int shift[3];   // image index s: X_j' = X_j - s * L
+  int lo[3], hi[3];
+};
+
+template <class S>
+struct PairResult {
+  S V, xc[3], n[3], d, F[3], TA[3], TB[3];
+  double G[3];
+  double box_cells, n_band, n_gtie, d_gap, estar;
+};
+
+// Sweep of every lattice node of the pair box (Sec. 3.3.1) and the force law
+// of Eq. (contact_force_normal).  XA, qA, XB (already the image X_j'), qB are
+// the poses; vel (nullable) holds (u, omega) per particle.
+template <class S>
+PairResult<S> eval_pair(const Config& cfg, const Shape& A, const Shape& B, const PairGeom& pg,
+                        const S XA[3], const S qA[4], const S XB[3], const S qB[4], const double* velA,
+                        const double* velB, double estar) {
+  const double dx = cfg.dx;
+  const bool smooth = cfg.indicator == 1;
+  const double wdx = cfg.smooth_width * dx;
+  const double eps = cfg.band_eps * dx;
+  S RA[9], RB[9];
+  quat_to_rot(qA, RA);
+  quat_to_rot(qB, RB);
+
+  S SW(0.0), SM[3] = {S(0.0), S(0.0), S(0.0)}, SG[3] = {S(0.0), S(0.0), S(0.0)};
+  S dbest(0.0);
+  double top1 = -std::numeric_limits<double>::infinity(), top2 = top1;
+  double n_band = 0, n_gtie = 0;
+  const double o[3] = {pg.lo[0] * dx, pg.lo[1] * dx, pg.lo[2] * dx};
+  for (int kz = pg.lo[2]; kz <= pg.hi[2]; ++kz)
+    for (int ky = pg.lo[1]; ky <= pg.hi[1]; ++ky)
+      for (int kx = pg.lo[0]; kx <= pg.hi[0]; ++kx) {
+        const double x[3] = {kx * dx, ky * dx, kz * dx};
+        const double c[3] = {x[0] - o[0], x[1] - o[1], x[2] - o[2]};
+        S gA[3], gB[3];
+        double gapA, gapB;
+        S phA = sdf(A, XA, RA, x, cfg.inflate, gA, &gapA);
+        S phB = sdf(B, XB, RB, x, cfg.inflate, gB, &gapB);
+        S HA, HpA, HB, HpB;
+        indicator(smooth, wdx, phA, &HA, &HpA);
+        indicator(smooth, wdx, phB, &HB, &HpB);
+        S W = HA * HB;
+        SW = SW + W;
+        for (int k = 0; k < 3; ++k) SM[k] = SM[k] + W * c[k];
+        for (int k = 0; k < 3; ++k) SG[k] = SG[k] + (-(HpA * HB)) * gA[k] + (HA * HpB) * gB[k];
+        if (val(W) > 0.0) {
+          S f = -phA - phB;
+          const double fv = val(f);
+          if (fv > top1) {
+            top2 = top1;
+            top1 = fv;
+            dbest = f;
+          } else if (fv > top2) {
+            top2 = fv;
+          }
+        }
+        // diagnostics: cells whose classification or active face is ambiguous
+        // at the eps level (reported, never used in the result)
+        const double pa = val(phA), pb = val(phB);
+        if (!smooth) {
+          const bool loose = pa <= eps && pb <= eps;
+          const bool strict = pa <= -eps && pb <= -eps;
+          if (loose && !strict) n_band += 1;
+        }
+        const bool gA_on = val(HpA) != 0.0 && (smooth ? val(HB) > 0.0 : pb <= eps);
+        const bool gB_on = val(HpB) != 0.0 && (smooth ? val(HA) > 0.0 : pa <= eps);
+        const bool tieA = gapA < eps || (!smooth && std::fabs(pb) <= eps);
+        const bool tieB = gapB < eps || (!smooth && std::fabs(pa) <= eps);
+        if ((gA_on && tieA) || (gB_on && tieB)) n_gtie += 1;
+      }
+
+  PairResult<S> res;
+  const double dx3 = dx * dx * dx;
+  res.box_cells = double(pg.hi[0] - pg.lo[0] + 1) * double(pg.hi[1] - pg.lo[1] + 1) *
+                  double(pg.hi[2] - pg.lo[2] + 1);
+  res.n_band = n_band;
+  res.n_gtie = n_gtie;
+  res.d_gap = (top2 > -std::numeric_limits<double>::infinity()) ? (top1 - top2) / dx
+                                                                : std::numeric_limits<double>::infinity();
+  res.estar = estar;
+  S G[3];
+  for (int k = 0; k < 3; ++k) {
+    G[k] = 0.5 * dx3 * SG[k];
+    res.G[k] = val(G[k]);
+  }
+  S V = dx3 * SW;
+  res.V = V;
+  for (int k = 0; k < 3; ++k) {
+    res.xc[k] = S(0.0); res.n[k] = S(0.0); res.F[k] = S(0.0); res.TA[k] = S(0.0); res.TB[k] = S(0.0);
+  }
+  res.d = S(0.0);
+  if (!(val(V) > 0.0)) {
+    res.V = S(0.0);
+    return res;
+  }
+  for (int k = 0; k < 3; ++k) res.xc[k] = o[k] + (dx3 * SM[k]) / V;
+  S gn = sqrt_s(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
+  if (val(gn) > 1e-12 * dx * dx) {
+    for (int k = 0; k < 3; ++k) res.n[k] = G[k] / gn;
+  } else {
+    S dX[3] = {XB[0] - XA[0], XB[1] - XA[1], XB[2] - XA[2]};
+    S dn = sqrt_s(dX[0] * dX[0] + dX[1] * dX[1] + dX[2] * dX[2]);
+    if (val(dn) > 0.0)
+      for (int k = 0; k < 3; ++k) res.n[k] = dX[k] / dn;
+  }
+  S d = (top1 > 0.0) ? dbest : S(0.0);
+  res.d = d;
+  // relative normal velocity at the contact point (positive when approaching)
+  S damp(1.0);
+  if (velA != nullptr && velB != nullptr && cfg.damping_c != 0.0) {
+    S ra[3] = {res.xc[0] - XA[0], res.xc[1] - XA[1], res.xc[2] - XA[2]};
+    S rb[3] = {res.xc[0] - XB[0], res.xc[1] - XB[1], res.xc[2] - XB[2]};
+    const double* wa = velA + 3;
+    const double* wb = velB + 3;
+    S ua[3] = {velA[0] + (wa[1] * ra[2] - wa[2] * ra[1]), velA[1] + (wa[2] * ra[0] - wa[0] * ra[2]),
+               velA[2] + (wa[0] * ra[1] - wa[1] * ra[0])};
+    S ub[3] = {velB[0] + (wb[1] * rb[2] - wb[2] * rb[1]), velB[1] + (wb[2] * rb[0] - wb[0] * rb[2]),
+               velB[2] + (wb[0] * rb[1] - wb[1] * rb[0])};
+    S ddot = (ua[0] - ub[0]) * res.n[0] + (ua[1] - ub[1]) * res.n[1] + (ua[2] - ub[2]) * res.n[2];
+    damp = 1.0 + cfg.damping_c * ddot;
+    if (val(damp) < 0.0) damp = S(0.0);
+  }
+  S vd = V * d;
+  S fmag(0.0);
+  if (val(vd) > 0.0) fmag = (4.0 / (3.0 * M_PI)) * estar * sqrt_s(vd) * damp;
+  for (int k = 0; k < 3; ++k) res.F[k] = fmag * res.n[k];
+  // F acts on B, -F on A; torques about each particle's centre of mass (Sec. 2.2)
+  S ra[3] = {res.xc[0] - XA[0], res.xc[1] - XA[1], res.xc[2] - XA[2]};
+  S rb[3] = {res.xc[0] - XB[0], res.xc[1] - XB[1], res.xc[2] - XB[2]};
+  S FA[3] = {-res.F[0], -res.F[1], -res.F[2]};
+  res.TA[0] = ra[1] * FA[2] - ra[2] * FA[1];
+  res.TA[1] = ra[2] * FA[0] - ra[0] * FA[2];
+  res.TA[2] = ra[0] * FA[1] - ra[1] * FA[0];
+  res.TB[0] = rb[1] * res.F[2] - rb[2] * res.F[1];
+  res.TB[1] = rb[2] * res.F[0] - rb[0] * res.F[2];
+  res.TB[2] = rb[0] * res.F[1] - rb[1] * res.F[0];
+  return res;
+}
+
+// ----------------------------------------------------------------------------
+struct Problem {
+  Config cfg;
+  int n = 0;
+  std::vector<Shape> shapes;
+  std::vector<double> young, poisson;
+  std::vector<int> lo, hi;   // node ranges [n,3]
+  std::vector<PairGeom> pairs;
+};
+
+int build_problem(Problem& pb, const Config* cfg, int32_t n, const int32_t* shape_type,
+                  const double* shape_param, const int32_t* face_offset, const double* planes,
+                  const double* young, const double* poisson, const double* pos, const double* quat) {
+  pb.cfg = *cfg;
+  pb.n = n;
+  const Config& c = pb.cfg;
+  if (n < 0 || !(c.dx > 0.0) || !std::isfinite(c.dx)) return OR_EINVAL;
+  for (int k = 0; k < 3; ++k)
+    if (c.n_cells[k] < 1) return OR_EINVAL;
+  if (c.indicator != 0 && c.indicator != 1) return OR_EINVAL;
+  if (!(c.smooth_width > 0.0)) return OR_EINVAL;
+  if (!(c.inflate >= 0.0) || !(c.damping_c >= 0.0)) return OR_EINVAL;
+  // offset used for the AABB: inflation plus, in smoothed mode, half the band
+  const double band = (c.indicator == 1) ? (0.5 * c.smooth_width) * c.dx : 0.0;
+  const double delta = c.inflate + band;
+  pb.shapes.resize(n);
+  pb.young.assign(young, young + n);
+  pb.poisson.assign(poisson, poisson + n);
+  double rmax = 0.0;
+  for (int p = 0; p < n; ++p) {
+    Shape& s = pb.shapes[p];
+    s.type = shape_type[p];
+    for (int k = 0; k < 3; ++k) s.p[k] = shape_param[3 * p + k];
+    if (!(young[p] > 0.0) || !(poisson[p] >= 0.0) || !(poisson[p] < 1.0)) return OR_EINVAL;
+    double circ = 0.0;
+    if (s.type == SH_SPHERE) {
+      if (!(s.p[0] > 0.0)) return OR_EINVAL;
+      circ = s.p[0] + delta;
+    } else if (s.type == SH_CUBOID) {
+      for (int k = 0; k < 3; ++k)
+        if (!(s.p[k] > 0.0)) return OR_EINVAL;
+      const double e[3] = {s.p[0] + delta, s.p[1] + delta, s.p[2] + delta};
+      circ = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    } else if (s.type == SH_POLYTOPE) {
+      const int f0 = face_offset[p], f1 = face_offset[p + 1];
+      if (f1 - f0 < 4) return OR_EINVAL;
+      s.planes.assign(planes + 4 * f0, planes + 4 * f1);
+      for (int f = 0; f < f1 - f0; ++f) {
+        double* e = &s.planes[4 * f];
+        const double nn = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+        if (std::fabs(nn - 1.0) > 1e-9) return OR_EINVAL;  // unit normals required
+        if (!(e[3] > 0.0)) return OR_EINVAL;                // origin strictly inside
+      }
+      if (!polytope_bounded(s.planes)) return OR_EINVAL;
+      s.verts = polytope_vertices(s.planes, delta);
+      if (s.verts.size() < 12) return OR_EINVAL;
+      for (size_t v = 0; v < s.verts.size(); v += 3) {
+        const double* w = &s.verts[v];
+        circ = std::max(circ, std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]));
+      }
+    } else {
+      return OR_EINVAL;
+    }
+    rmax = std::max(rmax, circ);
+  }
+  // at most one periodic image of a partner can overlap (Sec. 3.3.2 reading)
+  for (int k = 0; k < 3; ++k)
+    if (n > 0 && !(c.n_cells[k] * c.dx > 4.0 * rmax + 2.0 * c.dx)) return OR_EDOMAIN;
+
+  pb.lo.assign(3 * n, 0);
+  pb.hi.assign(3 * n, 0);
+  for (int p = 0; p < n; ++p) {
+    const double* X = pos + 3 * p;
+    const double* q = quat + 4 * p;
+    for (int k = 0; k < 3; ++k) {
+      const double L = c.n_cells[k] * c.dx;
+      if (!(X[k] >= 0.0) || !(X[k] < L)) return OR_EINVAL;
+    }
+    const double qn = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    if (!(qn > 1e-24) || !std::isfinite(qn)) return OR_EINVAL;
+    double R[9];
+    quat_to_rot(q, R);
+    const Shape& s = pb.shapes[p];
+    double mn[3], mx[3];
+    if (s.type == SH_SPHERE) {
+      const double rad = s.p[0] + delta;
+      for (int k = 0; k < 3; ++k) { mn[k] = X[k] - rad; mx[k] = X[k] + rad; }
+    } else if (s.type == SH_CUBOID) {
+      const double e0 = s.p[0] + delta, e1 = s.p[1] + delta, e2 = s.p[2] + delta;
+      for (int k = 0; k < 3; ++k) {
+        const double ext = std::fabs(R[3 * k + 0]) * e0 + std::fabs(R[3 * k + 1]) * e1 +
+                           std::fabs(R[3 * k + 2]) * e2;
+        mn[k] = X[k] - ext;
+        mx[k] = X[k] + ext;
+      }
+    } else {
+      double wmn[3] = {std::numeric_limits<double>::infinity(), std::numeric_limits<double>::infinity(),
+                       std::numeric_limits<double>::infinity()};
+      double wmx[3] = {-wmn[0], -wmn[1], -wmn[2]};
+      for (size_t v = 0; v < s.verts.size(); v += 3) {
+        const double* w = &s.verts[v];
+        for (int k = 0; k < 3; ++k) {
+          const double t = R[3 * k + 0] * w[0] + R[3 * k + 1] * w[1] + R[3 * k + 2] * w[2];
+          wmn[k] = std::min(wmn[k], t);
+          wmx[k] = std::max(wmx[k], t);
+        }
+      }
+      for (int k = 0; k < 3; ++k) { mn[k] = X[k] + wmn[k]; mx[k] = X[k] + wmx[k]; }
+    }
+    for (int k = 0; k < 3; ++k) {
+      pb.lo[3 * p + k] = static_cast<int>(std::ceil(mn[k] / c.dx));
+      pb.hi[3 * p + k] = static_cast<int>(std::floor(mx[k] / c.dx));
+    }
+  }
+  // O(N^2) candidate test with the image of j nearest to i (Sec. 3.3.2)
+  pb.pairs.clear();
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      PairGeom g;
+      g.i = i;
+      g.j = j;
+      bool hit = true;
+      for (int k = 0; k < 3 && hit; ++k) {
+        const double L = c.n_cells[k] * c.dx;
+        const int s = static_cast<int>(std::nearbyint((pos[3 * j + k] - pos[3 * i + k]) / L));
+        g.shift[k] = s;
+        g.lo[k] = std::max(pb.lo[3 * i + k], pb.lo[3 * j + k] - s * c.n_cells[k]);
+        g.hi[k] = std::min(pb.hi[3 * i + k], pb.hi[3 * j + k] - s * c.n_cells[k]);
+        if (g.lo[k] > g.hi[k]) hit = false;
+      }
+      if (hit) pb.pairs.push_back(g);
+    }
+  return OR_OK;
+}
+
+double effective_modulus(double EA, double nuA, double EB, double nuB) {
+  return 1.0 / ((1.0 - nuA * nuA) / EA + (1.0 - nuB * nuB) / EB);
+}
+
+void image_pos(const Problem& pb, const PairGeom& g, const double* pos, double XB[3]) {
+  for (int k = 0; k < 3; ++k) XB[k] = pos[3 * g.j + k] - g.shift[k] * (pb.cfg.n_cells[k] * pb.cfg.dx);
+}
+
+void set_threads(int32_t n_threads) {
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+  (void)n_threads;
+#endif
+}
+
+}  // namespace
+
+// ============================================================================
+// C interface
+extern "C" {
+
+typedef struct {
+  int32_t n_cells[3];
+  double dx;
+  int32_t indicator;
+  double smooth_width;
+  double inflate;
+  double damping_c;
+  double band_eps;
+} oracle_config;
+
+int32_t oracle_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void oracle_rotation(const double* q, double* R) { quat_to_rot(q, R); }
+
+double oracle_effective_modulus(double EA, double nuA, double EB, double nuB) {
+  return effective_modulus(EA, nuA, EB, nuB);
+}
+
+// Eq. (damping_factor): c from the coefficient of restitution e and the
+// relative speed u0 at first contact.
+double oracle_damping_factor(double e, double u0) {
+  if (!(u0 > 0.0)) return 0.0;
+  return 1.5 * (1.0 - e) * (11.0 - e) / ((1.0 + 9.0 * e) * u0);
+}
+
+// Normal force magnitude of Eq. (contact_force_normal).
+double oracle_normal_force(double estar, double V, double d, double c, double ddot) {
+  double damp = 1.0 + c * ddot;
+  if (damp < 0.0) damp = 0.0;
+  if (!(V * d > 0.0)) return 0.0;
+  return (4.0 / (3.0 * M_PI)) * estar * std::sqrt(V * d) * damp;
+}
+
+int32_t oracle_polytope_vertices(int32_t n_planes, const double* planes, double delta, int32_t max_verts,
+                                 double* verts) {
+  std::vector<double> pl(planes, planes + 4 * n_planes);
+  if (!polytope_bounded(pl)) return -1;
+  std::vector<double> v = polytope_vertices(pl, delta);
+  const int nv = static_cast<int>(v.size() / 3);
+  for (int i = 0; i < std::min(nv, static_cast<int>(max_verts)); ++i)
+    for (int k = 0; k < 3; ++k) verts[3 * i + k] = v[3 * i + k];
+  return nv;
+}
+
+// Particle node ranges (lo, hi) per axis [n,6].  Returns a status code.
+int32_t oracle_aabb(const oracle_config* cfg, int32_t n, const int32_t* shape_type, const double* shape_param,
+                    const int32_t* face_offset, const double* planes, const double* young,
+                    const double* poisson, const double* pos, const double* quat, int32_t* lo_hi) {
+  Problem pb;
+  const int st = build_problem(pb, reinterpret_cast<const Config*>(cfg), n, shape_type, shape_param,
+                               face_offset, planes, young, poisson, pos, quat);
+  if (st != OR_OK) return st;
+  for (int p = 0; p < n; ++p)
+    for (int k = 0; k < 3; ++k) {
+      lo_hi[6 * p + k] = pb.lo[3 * p + k];
+      lo_hi[6 * p + 3 + k] = pb.hi[3 * p + k];
+    }
+  return OR_OK;
+}
+
+// Full contact evaluation.  Returns the number of candidate pairs P (>= 0;
+// only the first max_pairs rows are written when P > max_pairs) or a negative
+// status code.  Per pair: pair_ij [P,2], pair_shift [P,3], pair_box [P,6]
+// (lo, hi), pair_out [P,11] = V, x_c[3], n[3], d, F[3] (force on the
+// higher-ID particle j), pair_aux [P,8] = G[3], box cells, ambiguous cells,
+// ambiguous normal cells, depth gap (lattice units), E*.  force/torque [n,3].
+int64_t oracle_contact_step(const oracle_config* cfg, int32_t n, const int32_t* shape_type,
+                            const double* shape_param, const int32_t* face_offset, const double* planes,
+                            const double* young, const double* poisson, const double* pos,
+                            const double* quat, const double* vel, int64_t max_pairs, int32_t* pair_ij,
+                            int32_t* pair_shift, int32_t* pair_box, double* pair_out, double* pair_aux,
+                            double* force, double* torque, int32_t n_threads) {
+  Problem pb;
+  const int st = build_problem(pb, reinterpret_cast<const Config*>(cfg), n, shape_type, shape_param,
+                               face_offset, planes, young, poisson, pos, quat);
+  if (st != OR_OK) return -st;
+  const int64_t P = static_cast<int64_t>(pb.pairs.size());
+  std::vector<PairResult<double>> res(P);
+  set_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t p = 0; p < P; ++p) {
+    const PairGeom& g = pb.pairs[p];
+    double XB[3];
+    image_pos(pb, g, pos, XB);
+    const double es = effective_modulus(pb.young[g.i], pb.poisson[g.i], pb.young[g.j], pb.poisson[g.j]);
+    res[p] = eval_pair<double>(pb.cfg, pb.shapes[g.i], pb.shapes[g.j], g, pos + 3 * g.i, quat + 4 * g.i, XB,
+                               quat + 4 * g.j, vel ? vel + 6 * g.i : nullptr, vel ? vel + 6 * g.j : nullptr, es);
+  }
+  if (force) std::memset(force, 0, sizeof(double) * 3 * n);
+  if (torque) std::memset(torque, 0, sizeof(double) * 3 * n);
+  for (int64_t p = 0; p < P; ++p) {
+    const PairGeom& g = pb.pairs[p];
+    const PairResult<double>& r = res[p];
+    if (force && torque)
+      for (int k = 0; k < 3; ++k) {
+        force[3 * g.i + k] -= r.F[k];
+        torque[3 * g.i + k] += r.TA[k];
+        force[3 * g.j + k] += r.F[k];
+        torque[3 * g.j + k] += r.TB[k];
+      }
+    if (p >= max_pairs) continue;
+    if (pair_ij) { pair_ij[2 * p] = g.i; pair_ij[2 * p + 1] = g.j; }
+    if (pair_shift)
+      for (int k = 0; k < 3; ++k) pair_shift[3 * p + k] = g.shift[k];
+    if (pair_box)
+      for (int k = 0; k < 3; ++k) { pair_box[6 * p + k] = g.lo[k]; pair_box[6 * p + 3 + k] = g.hi[k]; }
+    if (pair_out) {
+      double* o = pair_out + 11 * p;
+      o[0] = r.V;
+      for (int k = 0; k < 3; ++k) { o[1 + k] = r.xc[k]; o[4 + k] = r.n[k]; o[8 + k] = r.F[k]; }
+      o[7] = r.d;
+    }
+    if (pair_aux) {
+      double* a = pair_aux + 8 * p;
+      a[0] = r.G[0]; a[1] = r.G[1]; a[2] = r.G[2];
+      a[3] = r.box_cells; a[4] = r.n_band; a[5] = r.n_gtie; a[6] = r.d_gap; a[7] = r.estar;
+    }
+  }
+  return P;
+}
+
+// Gradient of L = sum_p (grad_force_p . F_p + grad_torque_p . T_p) with
+// respect to positions [n,3] and raw (unnormalised) quaternions [n,4], by
+// forward-mode dual numbers through the same per-pair code as above.
+int64_t oracle_gradient(const oracle_config* cfg, int32_t n, const int32_t* shape_type, const double* shape_param,
+                        const int32_t* face_offset, const double* planes, const double* young,
+                        const double* poisson, const double* pos, const double* quat, const double* vel,
+                        const double* grad_force, const double* grad_torque, double* grad_pos,
+                        double* grad_quat, int32_t n_threads) {
+  Problem pb;
+  const int st = build_problem(pb, reinterpret_cast<const Config*>(cfg), n, shape_type, shape_param,
+                               face_offset, planes, young, poisson, pos, quat);
+  if (st != OR_OK) return -st;
+  const int64_t P = static_cast<int64_t>(pb.pairs.size());
+  std::vector<double> pg(static_cast<size_t>(P) * NT, 0.0);
+  set_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t p = 0; p < P; ++p) {
+    const PairGeom& g = pb.pairs[p];
+    double XBd[3];
+    image_pos(pb, g, pos, XBd);
+    Dual XA[3], qA[4], XB[3], qB[4];
+    for (int k = 0; k < 3; ++k) { XA[k] = Dual(pos[3 * g.i + k]); XA[k].g[k] = 1.0; }
+    for (int k = 0; k < 4; ++k) { qA[k] = Dual(quat[4 * g.i + k]); qA[k].g[3 + k] = 1.0; }
+    for (int k = 0; k < 3; ++k) { XB[k] = Dual(XBd[k]); XB[k].g[7 + k] = 1.0; }
+    for (int k = 0; k < 4; ++k) { qB[k] = Dual(quat[4 * g.j + k]); qB[k].g[10 + k] = 1.0; }
+    const double es = effective_modulus(pb.young[g.i], pb.poisson[g.i], pb.young[g.j], pb.poisson[g.j]);
+    PairResult<Dual> r = eval_pair<Dual>(pb.cfg, pb.shapes[g.i], pb.shapes[g.j], g, XA, qA, XB, qB,
+                                         vel ? vel + 6 * g.i : nullptr, vel ? vel + 6 * g.j : nullptr, es);
+    Dual L(0.0);
+    for (int k = 0; k < 3; ++k) {
+      L = L + grad_force[3 * g.i + k] * (-r.F[k]) + grad_torque[3 * g.i + k] * r.TA[k];
+      L = L + grad_force[3 * g.j + k] * r.F[k] + grad_torque[3 * g.j + k] * r.TB[k];
+    }
+    for (int t = 0; t < NT; ++t) pg[static_cast<size_t>(p) * NT + t] = L.g[t];
+  }
+  std::memset(grad_pos, 0, sizeof(double) * 3 * n);
+  std::memset(grad_quat, 0, sizeof(double) * 4 * n);
+  for (int64_t p = 0; p < P; ++p) {
+    const PairGeom& g = pb.pairs[p];
+    const double* t = &pg[static_cast<size_t>(p) * NT];
+    for (int k = 0; k < 3; ++k) grad_pos[3 * g.i + k] += t[k];
+    for (int k = 0; k < 4; ++k) grad_quat[4 * g.i + k] += t[3 + k];
+    for (int k = 0; k < 3; ++k) grad_pos[3 * g.j + k] += t[7 + k];
+    for (int k = 0; k < 4; ++k) grad_quat[4 * g.j + k] += t[10 + k];
+  }
+  return P;
+}
+
+}  // extern "C"
