@@ -1,0 +1,421 @@
+#!/usr/bin/env python3
+"""Benchmark of the contact step: cell-evaluations/s and ms per contact_step
+at 1934 particles, with the FP32 roofline fraction of the node-sweep kernel.
+
+Workload (headline): 1934 cuboids of edge 12 at 30 % volume fraction in a
+periodic 223^3 lattice (RSA centres of volume-equivalent spheres, uniform
+random orientations), sharp indicator, FP32 node tests / FP64 reductions,
+swept over seeded steps of small random pose increments (dX ~ N(0, 0.05),
+rotations ~ N(0, 0.01 rad)).  A "step" is one contact_step: pose -> AABB,
+broad phase, work partition, node sweep, pair reduction, force law,
+per-particle sums.  Secondary lines in the same JSON: the 1934-particle mixed
+spheres/cubes/polytopes box, the smoothed-indicator forward + adjoint pass on
+the cuboid box, and the all-FP64 one-pair-per-block form.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: every rank evaluates its own independently seeded
+box (weak scaling, no data-path collective); the barrier and the max over
+ranks of the timed region use torch.distributed.  --impl reference times the
+CPU FP64 oracle (the test-suite's reference implementation) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "contact cell-evaluations/s and ms per contact_step at 1934 particles, % FP32 roofline"
+UNIT = "cell-evals/s"
+FP32_LANES_PER_SM = 128   # FP32 lanes per Blackwell SM
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU baseline budget")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def headline_state(rank: int):
+    from paper_2401_10878_gb300 import workloads as W
+    st = W.settling_cubes_dense(seed=4 + 1000 * rank)
+    st.indicator = 0
+    st.name = "cubes1934_223"
+    return st
+
+
+def workload_config(st, extra=None):
+    cfg = {"workload": "1934 cuboids (edge 12) at 30% volume fraction, periodic 223^3 lattice, dx = 1",
+           "particles": st.n, "lattice": list(st.n_cells), "indicator": "sharp",
+           "precision": "fp32 node tests, fp32 tile partials, fp64 pair/particle reductions",
+           "pose_steps": "seeded increments dX~N(0,0.05), rot~N(0,0.01 rad)",
+           "l2": "flushed (256 MiB write) before every timed step", "parallelism": "weak (one box per GPU)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.path is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, ws, rank):
+    """The CPU FP64 oracle on the host cores, same workload and metric."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2401_10878_gb300 import workloads as W
+    oracle.build()
+    st = headline_state(0)
+    pos, quat = W.pose_sequence(st, max(args.steps + args.warmup, 1))
+    threads = oracle.max_threads()
+    for s in range(args.warmup):
+        oracle.contact_step(st, pos=pos[s], quat=quat[s])
+    cells, secs = 0, 0.0
+    for s in range(args.steps):
+        k = args.warmup + s
+        r = oracle.contact_step(st, pos=pos[k], quat=quat[k])
+        cells += r.cells
+        secs += r.seconds
+    v = cells / secs
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(st),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{args.steps} full contact steps of the workload (all pairs)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def cpu_baseline(st, pos, quat, budget_s):
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    cells, secs, steps = 0, 0.0, 0
+    t_end = time.perf_counter() + budget_s
+    while steps < 3 or (time.perf_counter() < t_end and steps < len(pos)):
+        r = oracle.contact_step(st, pos=pos[steps % len(pos)], quat=quat[steps % len(quat)])
+        cells += r.cells
+        secs += r.seconds
+        steps += 1
+    return {"value": cells / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{steps} full contact steps of the workload ({cells} node evaluations), "
+                      f"OpenMP over pairs", "ms_per_step": 1e3 * secs / steps}
+
+
+def time_forward(model, pos_d, quat_d, steps, warmup, flush):
+    """Per-step device time (events around contact_step on the context stream)."""
+    import torch
+    s = model.stream
+    tot, narrow, cells, ops = 0.0, 0.0, 0, 0
+    per = []
+    for k in range(warmup + steps):
+        idx = k % pos_d.shape[0]
+        with torch.cuda.stream(s):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        model.step_async(pos_d[idx], quat_d[idx])
+        e1.record(s)
+        e1.synchronize()
+        if k >= warmup:
+            ms = e0.elapsed_time(e1)
+            tot += ms
+            per.append(ms)
+            narrow += model.narrow_time_ms()
+            st = model.stats()
+            cells += st["cells"]
+            ops += st["nominal_ops"]
+    model.check()
+    return dict(ms=tot, narrow_ms=narrow, cells=cells, ops=ops, per=per)
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2401_10878_gb300 import workloads as W
+    from paper_2401_10878_gb300.contact import Contact
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    st = headline_state(rank)
+    nseq = min(100, args.steps + args.warmup)
+    pos, quat = W.pose_sequence(st, nseq, seed=11 + rank)
+    pos_d = torch.tensor(pos, device=dev)
+    quat_d = torch.tensor(quat, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    model = Contact.from_state(st)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        res = time_forward(model, pos_d, quat_d, args.steps, args.warmup, flush)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = clk.summary()
+    t_max = res["ms"]
+    total_cells = res["cells"]
+    if ws > 1:
+        t = torch.tensor([res["ms"]], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+        c = torch.tensor([res["cells"]], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(c)
+        total_cells = float(c.item())
+    value = total_cells / (t_max * 1e-3)
+    ms_per_step = t_max / args.steps
+    stats = model.stats()
+
+    # roofline of the node-sweep kernel: nominal FP32 lane-ops / its event time
+    narrow_avg_s = res["narrow_ms"] * 1e-3 / args.steps
+    ops_per_launch = res["ops"] / args.steps
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = sms * FP32_LANES_PER_SM * max_mhz * 1e6 / 1e12          # T lane-ops/s
+    achieved = ops_per_launch / narrow_avg_s / 1e12
+    med = clocks.get("sm_mhz")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32 lane-ops/s",
+                "frac": achieved / peak, "traffic": traffic_from_profile(),
+                "kernel": "k_narrow32 (node sweep)", "ops_per_launch": ops_per_launch,
+                "launch_ms": narrow_avg_s * 1e3,
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz (max SM clock)",
+                "frac_at_median_clock": (achieved / (sms * FP32_LANES_PER_SM * med * 1e6 / 1e12)) if med else None,
+                "cell_evals_per_s_kernel": (res["cells"] / args.steps) / narrow_avg_s}
+
+    # end to end through the public API with host buffers
+    e2e = end_to_end(model, pos, quat, args.steps, args.warmup, dev)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(st, {"pairs_per_step": stats["pairs"],
+                                           "cells_per_step": res["cells"] / args.steps,
+                                           "overlapping_pairs": stats["overlapping"],
+                                           "tiles_per_step": stats["tiles"], "narrow_grid": stats["narrow_grid"]}),
+            "roofline": roofline, "e2e": e2e, "gpu_launches": model.kernels_per_step() * args.steps,
+            "clocks": clocks,
+            "ms_per_step_p10_p90": [float(np.percentile(res["per"], 10)), float(np.percentile(res["per"], 90))]}
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline(st, pos, quat, args.cpu_seconds)
+        if not args.no_extras:
+            line["extras"] = extras(args, dev, flush)
+    model.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def end_to_end(model, pos, quat, steps, warmup, dev):
+    """contact_step through the public API with pinned host inputs/outputs:
+    H2D of the step's poses, the step, D2H of forces and torques, all timed."""
+    import torch
+    s = model.stream
+    hp = torch.tensor(pos).pin_memory()
+    hq = torch.tensor(quat).pin_memory()
+    dp = torch.empty_like(hp[0], device=dev)
+    dq = torch.empty_like(hq[0], device=dev)
+    hf = torch.empty((model.n, 3), dtype=torch.float64).pin_memory()
+    ht = torch.empty((model.n, 3), dtype=torch.float64).pin_memory()
+    tot, cells = 0.0, 0
+    for k in range(warmup + steps):
+        idx = k % hp.shape[0]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            e0.record(s)
+            dp.copy_(hp[idx], non_blocking=True)
+            dq.copy_(hq[idx], non_blocking=True)
+            model.step_async(dp, dq)
+            hf.copy_(model.force, non_blocking=True)
+            ht.copy_(model.torque, non_blocking=True)
+            e1.record(s)
+        e1.synchronize()
+        if k >= warmup:
+            tot += e0.elapsed_time(e1)
+            cells += model.stats()["cells"]
+    model.check()
+    n = model.n
+    return {"value": cells / (tot * 1e-3), "unit": UNIT, "h2d_bytes_per_step": n * 7 * 8,
+            "d2h_bytes_per_step": n * 6 * 8, "ms_per_step": tot / steps}
+
+
+def extras(args, dev, flush):
+    """Secondary workloads, each timed like the headline (no CPU leg)."""
+    import torch
+    from paper_2401_10878_gb300 import workloads as W
+    from paper_2401_10878_gb300.contact import Contact, FP64_PAIR
+
+    out = {}
+    steps = max(5, min(args.steps, 20))
+    # mixed spheres / cubes / polytopes at 30 %
+    st = W.mixed_settling()
+    pos, quat = W.pose_sequence(st, steps + 3)
+    m = Contact.from_state(st)
+    r = time_forward(m, torch.tensor(pos, device=dev), torch.tensor(quat, device=dev), steps, 3, flush)
+    s = m.stats()
+    out["mixed1934_223"] = {"cell_evals_per_s": r["cells"] / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / steps,
+                            "narrow_ms": r["narrow_ms"] / steps, "pairs": s["pairs"],
+                            "cells_per_step": r["cells"] / steps,
+                            "nominal_Tops_per_s": r["ops"] / (r["narrow_ms"] * 1e-3) / 1e12}
+    m.close()
+    # all-FP64 one-pair-per-block form on the headline workload
+    st = headline_state(0)
+    pos, quat = W.pose_sequence(st, steps + 3)
+    m = Contact.from_state(st, precision=FP64_PAIR)
+    r = time_forward(m, torch.tensor(pos, device=dev), torch.tensor(quat, device=dev), steps, 3, flush)
+    out["cubes1934_fp64_form"] = {"cell_evals_per_s": r["cells"] / (r["ms"] * 1e-3),
+                                  "ms_per_step": r["ms"] / steps, "narrow_ms": r["narrow_ms"] / steps}
+    m.close()
+    # smoothed indicator: forward + adjoint
+    st = W.settling_cubes_dense()
+    pos, quat = W.pose_sequence(st, steps + 3)
+    m = Contact.from_state(st)
+    gf, gt = W.loss_weights(st.n)
+    gf, gt = torch.tensor(gf, device=dev), torch.tensor(gt, device=dev)
+    gp = torch.empty((st.n, 3), dtype=torch.float64, device=dev)
+    gq = torch.empty((st.n, 4), dtype=torch.float64, device=dev)
+    pd, qd = torch.tensor(pos, device=dev), torch.tensor(quat, device=dev)
+    fwd, bwd, cells = 0.0, 0.0, 0
+    import ctypes
+    for k in range(steps + 3):
+        with torch.cuda.stream(m.stream):
+            flush.zero_()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(m.stream)
+        m.step_async(pd[k], qd[k])
+        e1.record(m.stream)
+        rc = m.lib.contact_backward(m.ctx, ctypes.c_void_p(gf.data_ptr()), ctypes.c_void_p(gt.data_ptr()),
+                                    ctypes.c_void_p(gp.data_ptr()), ctypes.c_void_p(gq.data_ptr()))
+        assert rc == 0
+        e2.record(m.stream)
+        e2.synchronize()
+        if k >= 3:
+            fwd += e0.elapsed_time(e1)
+            bwd += e1.elapsed_time(e2)
+            cells += m.stats()["cells"]
+    m.check()
+    out["cubes1934_smooth_fwd_bwd"] = {"fwd_ms": fwd / steps, "bwd_ms": bwd / steps,
+                                       "cell_evals_per_s_fwd_bwd": cells / ((fwd + bwd) * 1e-3),
+                                       "cells_per_step": cells / steps}
+    m.close()
+    return out
+
+
+def traffic_from_profile():
+    """DRAM bytes per launch of the node sweep from the committed ncu summary,
+    only while the kernel source is unchanged since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_narrow32_cubes1934.md")
+    src = os.path.join(ROOT, "paper_2401_10878_gb300", "csrc", "k_narrow.cu")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("k_narrow.cu sha256[:16]") != h:
+        return None
+    try:
+        return float(vals["dram bytes per launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

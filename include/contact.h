@@ -1,0 +1,190 @@
+/*
+ * contact.h -- C-ABI of the GB300 discrete-contact library (libcontact.so).
+ *
+ * The library evaluates the discrete contact model of Marquardt, Hafen and
+ * Krause, "A novel model for direct numerical simulation of suspension
+ * dynamics with arbitrarily shaped convex particles" (arXiv:2401.10878), for
+ * spheres, cuboids and convex polytopes in a periodic lattice:
+ *
+ *   broad phase      -> candidate pairs, periodic image of the higher-ID
+ *                       particle moved to the lower-ID side (Sec. 3.3.2)
+ *   overlap sweep    -> every lattice node of each pair's bounding box is tested
+ *                       against both signed distance functions; the nodes are
+ *                       reduced to overlap volume, contact point, contact
+ *                       normal and indentation depth (Sec. 3.3.1)
+ *   force law        -> F = 4/(3 pi) n E* sqrt(V d)(1 + c ddot_n),
+ *                       E* = ((1-nu_A^2)/E_A + (1-nu_B^2)/E_B)^-1 (Sec. 2.3,
+ *                       Eq. contact_force_normal), torques about each centre
+ *                       of mass (Sec. 2.2)
+ *   adjoint          -> gradient of sum_p (gF_p . F_p + gT_p . T_p) with
+ *                       respect to positions and quaternions (smoothed indicator)
+ *
+ * Conventions (all calls):
+ *   - Lattice node k in Z^3 sits at x = k dx; the periodic box is L = n_cells * dx.
+ *   - A pose is a centre of mass X (Sec. 2.2) and a quaternion (w, x, y, z),
+ *     Hamilton convention, body -> world, normalised inside the library.
+ *   - Shapes are given in their body frame with the origin at the centre of
+ *     mass: a sphere by its radius, a cuboid by its half extents, a polytope
+ *     by half-spaces n . y <= d with unit n and d > 0 (bounded).
+ *   - "dev" pointers are device memory of the context's GPU, "host" pointers
+ *     are host memory.  The caller owns every buffer it passes; the context
+ *     owns its scratch, allocated once in contact_init.
+ *   - Calls that take dev pointers enqueue work on the context stream and
+ *     return without synchronising.  contact_step and contact_backward
+ *     allocate nothing.
+ *   - Errors found on the host return at once.  Errors found on the device
+ *     (inputs out of range, capacity overflow) are sticky: they are returned by
+ *     the next call once the device has written them, and by contact_check.
+ */
+#ifndef GB300_CONTACT_H
+#define GB300_CONTACT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct contact_ctx contact_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  CONTACT_OK = 0,
+  CONTACT_EINVAL = 1,    /* invalid argument or input value                   */
+  CONTACT_ENOMEM = 2,    /* device or host allocation failed (contact_init)   */
+  CONTACT_ECUDA = 3,     /* a CUDA runtime call failed                        */
+  CONTACT_ECAPACITY = 4, /* more pairs / neighbours / tiles than configured   */
+  CONTACT_EDOMAIN = 5,   /* periodic box too small for the largest particle   */
+  CONTACT_ETIMEOUT = 6,  /* a bounded device wait ran out                     */
+  CONTACT_ESTATE = 7     /* call out of order (e.g. backward before a step)   */
+} contact_status;
+
+enum { CONTACT_SHAPE_SPHERE = 0, CONTACT_SHAPE_CUBOID = 1, CONTACT_SHAPE_POLYTOPE = 2 };
+enum { CONTACT_INDICATOR_SHARP = 0, CONTACT_INDICATOR_SMOOTH = 1 };
+enum { CONTACT_PRECISION_FP32_TILE = 0, CONTACT_PRECISION_FP64_PAIR = 1 };
+
+/* Width of one row of pair_out. */
+#define CONTACT_PAIR_OUT_COLS 11
+
+typedef struct {
+  int32_t n_particles;
+  int32_t n_cells[3];       /* periodic lattice, L = n_cells * dx                   */
+  double dx;                /* lattice spacing (> 0)                                 */
+  int32_t indicator;        /* CONTACT_INDICATOR_SHARP: H = [phi <= 0];
+                               CONTACT_INDICATOR_SMOOTH: H_w(phi) = S(clamp(1/2 -
+                               phi/(w dx), 0, 1)), S(t) = 3t^2 - 2t^3              */
+  double smooth_width;      /* w in lattice cells (> 0); also the width of the band
+                               used for the contact normal in sharp mode           */
+  double inflate;           /* enlargement subtracted from every signed distance,
+                               physical units (the paper uses dx/5, Sec. 5.1)      */
+  double damping_c;         /* damping factor c of Eq. (contact_force_normal),
+                               applied to every contact when velocities are given;
+                               contact_damping_factor computes it (>= 0)           */
+  int32_t precision;        /* CONTACT_PRECISION_FP32_TILE: FP32 node tests, FP32
+                               tile partials, FP64 per-pair reduction;
+                               CONTACT_PRECISION_FP64_PAIR: everything in FP64,
+                               one thread block per pair                           */
+  int32_t max_pairs;        /* capacity of the pair list (> 0)                       */
+  int32_t max_neighbors;    /* capacity of one particle's candidate list (0: 64)    */
+  int32_t max_tiles;        /* capacity of the node-tile list (0: 64 * max_pairs)   */
+  int32_t use_graph;        /* 1: contact_step captures its launches in a CUDA graph
+                               on first use and replays it while the buffers are
+                               the same (not while the stream is being captured)   */
+} contact_config;
+
+/* Fills *cfg with defaults (sharp indicator, w = 1, no inflation, FP32 tiles,
+ * max_pairs = 16 n, graphs on) for n particles in an n_cells lattice of
+ * spacing dx. */
+void contact_config_default(contact_config* cfg, int32_t n_particles, const int32_t n_cells[3], double dx);
+
+/* Creates a context on the current CUDA device.
+ *   shape_type  [N]      host, CONTACT_SHAPE_*
+ *   shape_param [N,3]    host, sphere: (r, -, -); cuboid: half extents (hx, hy, hz)
+ *   face_offset [N+1]    host, polytope p owns planes[face_offset[p] .. face_offset[p+1])
+ *                        (non-polytopes own none; 4 <= faces <= 32)
+ *   planes      [F,4]    host, (n0, n1, n2, d) body frame, n . y <= d, |n| = 1, d > 0
+ *   young, poisson [N]   host, E > 0 and 0 <= nu < 1 per particle (Sec. 2.3)
+ *   stream               cudaStream_t (NULL: default stream); changeable with
+ *                        contact_set_stream
+ * Returns CONTACT_EINVAL for an invalid shape or configuration,
+ * CONTACT_EDOMAIN when L <= 4 R_max + 2 dx on some axis (R_max = the largest
+ * circumradius after inflation), so that at most one periodic image of a
+ * partner can overlap a particle.  *out is NULL on failure. */
+contact_status contact_init(const contact_config* cfg, const int32_t* shape_type, const double* shape_param,
+                            const int32_t* face_offset, const double* planes, const double* young,
+                            const double* poisson, void* stream, contact_ctx** out);
+
+/* One contact evaluation (Sec. 3.3.1 / 3.3.2 / Eq. contact_force_normal).
+ *   pos   [N,3] dev f64  centres of mass, 0 <= X < L on every axis
+ *   quat  [N,4] dev f64  (w, x, y, z), any non-zero norm
+ *   vel   [N,6] dev f64  (u, omega) per particle, or NULL (then ddot_n = 0)
+ * Outputs (dev, written on the context stream):
+ *   pair_ij  [max_pairs,2] i32   candidate pairs (i < j) sorted by (i, j)
+ *   pair_out [max_pairs,11] f64  per pair: V, x_c[3], n[3], d, F[3]; F is the
+ *                                force on j (-F acts on i), n points from i to
+ *                                j, x_c is in i's frame (not wrapped)
+ *   n_pairs  [1] i32             number of candidate pairs P
+ *   force, torque [N,3] f64      per-particle sums over the pairs, in the order
+ *                                (pairs where the particle is j, by i), then
+ *                                (pairs where it is i, by j)
+ * Pairs whose shapes do not overlap on any node have V = x_c = n = d = F = 0.
+ * Positions outside [0, L), zero quaternions and non-finite values set the
+ * sticky CONTACT_EINVAL; more than max_pairs candidates sets
+ * CONTACT_ECAPACITY (n_pairs then holds the count that was needed). */
+contact_status contact_step(contact_ctx* ctx, const double* pos, const double* quat, const double* vel,
+                            int32_t* pair_ij, double* pair_out, int32_t* n_pairs, double* force,
+                            double* torque);
+
+/* Gradient of L = sum_p (grad_force_p . force_p + grad_torque_p . torque_p)
+ * of the last contact_step with respect to its positions and raw quaternions
+ * (the quaternion gradient is orthogonal to the quaternion).  Needs the
+ * smoothed indicator (CONTACT_ESTATE otherwise) and uses the step's tape, so
+ * the step's pos/quat/vel must still hold the same values.
+ *   grad_force, grad_torque [N,3] dev f64 ; grad_pos [N,3], grad_quat [N,4] dev f64 */
+contact_status contact_backward(contact_ctx* ctx, const double* grad_force, const double* grad_torque,
+                                double* grad_pos, double* grad_quat);
+
+/* Synchronises the context stream and returns the sticky device error (the
+ * error stays set; contact_clear_error resets it). */
+contact_status contact_check(contact_ctx* ctx);
+void contact_clear_error(contact_ctx* ctx);
+
+/* Human-readable description of the last error of the context (never NULL). */
+const char* contact_last_error(contact_ctx* ctx);
+
+/* Makes later calls enqueue on another stream (drops cached graphs). */
+contact_status contact_set_stream(contact_ctx* ctx, void* stream);
+
+/* Synchronises, then fills stats[0..9] (host) with the last step's pair count,
+ * node evaluations (sum of box volumes), node tiles, pairs with V > 0,
+ * kernels launched per step, narrow-phase grid size, bins per axis (x),
+ * whether the last step replayed a graph, the nominal FP32 lane-operations of
+ * the node sweep (sum over pairs of box volume x (ops_i + ops_j), with 7 per
+ * sphere test, 15 per cuboid test and 4F per polytope test), and the tile
+ * capacity. */
+contact_status contact_stats(contact_ctx* ctx, int64_t* stats);
+
+/* Synchronises, then writes the device time in milliseconds of the last
+ * step's narrow-phase kernel (the node sweep), measured with CUDA events that
+ * contact_step records on the context stream around that launch (also when
+ * the step replays a graph).  CONTACT_ESTATE before the first step. */
+contact_status contact_narrow_time(contact_ctx* ctx, float* ms);
+
+/* Per-particle node ranges (lo[3], hi[3]) [N,6] i32 dev of the last step. */
+contact_status contact_particle_boxes(contact_ctx* ctx, int32_t* lo_hi);
+
+/* Eq. (damping_factor): c = 1.5 (1-e)(11-e) / ((1+9e) u0) for u0 > 0, else 0,
+ * from the coefficient of restitution e and the relative speed u0 at first
+ * contact (Carvalho-Martins, as used in Sec. 2.3). */
+double contact_damping_factor(double restitution, double u0);
+
+/* Number of kernel launches one contact_step / contact_backward issues. */
+int32_t contact_kernels_per_step(const contact_ctx* ctx);
+int32_t contact_kernels_per_backward(const contact_ctx* ctx);
+
+void contact_destroy(contact_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_CONTACT_H */

@@ -1,0 +1,278 @@
+"""Python binding of libcontact (ctypes): argument marshalling only.
+
+Every step of the contact path runs in the CUDA library; PyTorch only holds
+device memory and provides the stream.  There is no CPU fallback: without the
+compiled library or a GPU these calls raise.
+
+    model = Contact.from_state(state)                  # contact_init
+    out = model.step(pos, quat)                        # contact_step
+    gpos, gquat = model.backward(gF, gT)               # contact_backward
+    force, torque = contact_forces(model, pos, quat)   # torch.autograd.Function
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ECUDA, ECAPACITY, EDOMAIN, ETIMEOUT, ESTATE = range(8)
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECAPACITY", 5: "EDOMAIN", 6: "ETIMEOUT",
+          7: "ESTATE"}
+SHARP, SMOOTH = 0, 1
+FP32_TILE, FP64_PAIR = 0, 1
+PAIR_OUT_COLS = 11
+
+# every symbol the header declares (checked by the tests)
+EXPORTS = ["contact_config_default", "contact_init", "contact_step", "contact_backward", "contact_check",
+           "contact_clear_error", "contact_last_error", "contact_set_stream", "contact_stats",
+           "contact_particle_boxes", "contact_narrow_time", "contact_damping_factor", "contact_kernels_per_step",
+           "contact_kernels_per_backward", "contact_destroy"]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("n_particles", ctypes.c_int32), ("n_cells", ctypes.c_int32 * 3), ("dx", ctypes.c_double),
+                ("indicator", ctypes.c_int32), ("smooth_width", ctypes.c_double),
+                ("inflate", ctypes.c_double), ("damping_c", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("max_pairs", ctypes.c_int32), ("max_neighbors", ctypes.c_int32),
+                ("max_tiles", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
+class ContactError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"contact library error {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libcontact.so (compiling it first when missing and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ContactError(ECUDA, f"{path} not built (run __graft_entry__.build())")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.contact_config_default.argtypes = [ctypes.POINTER(Config), I32, P, D]
+    lib.contact_config_default.restype = None
+    lib.contact_init.argtypes = [ctypes.POINTER(Config), P, P, P, P, P, P, P, ctypes.POINTER(P)]
+    lib.contact_init.restype = I32
+    lib.contact_step.argtypes = [P] * 9
+    lib.contact_step.restype = I32
+    lib.contact_backward.argtypes = [P] * 5
+    lib.contact_backward.restype = I32
+    lib.contact_check.argtypes = [P]
+    lib.contact_check.restype = I32
+    lib.contact_clear_error.argtypes = [P]
+    lib.contact_clear_error.restype = None
+    lib.contact_last_error.argtypes = [P]
+    lib.contact_last_error.restype = ctypes.c_char_p
+    lib.contact_set_stream.argtypes = [P, P]
+    lib.contact_set_stream.restype = I32
+    lib.contact_stats.argtypes = [P, P]
+    lib.contact_stats.restype = I32
+    lib.contact_narrow_time.argtypes = [P, P]
+    lib.contact_narrow_time.restype = I32
+    lib.contact_particle_boxes.argtypes = [P, P]
+    lib.contact_particle_boxes.restype = I32
+    lib.contact_damping_factor.argtypes = [D, D]
+    lib.contact_damping_factor.restype = D
+    lib.contact_kernels_per_step.argtypes = [P]
+    lib.contact_kernels_per_step.restype = I32
+    lib.contact_kernels_per_backward.argtypes = [P]
+    lib.contact_kernels_per_backward.restype = I32
+    lib.contact_destroy.argtypes = [P]
+    lib.contact_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return ctypes.c_void_p(t.data_ptr())
+    return t.ctypes.data_as(ctypes.c_void_p)
+
+
+def damping_factor(restitution: float, u0: float) -> float:
+    """Eq. (damping_factor) through the library."""
+    return float(load_library().contact_damping_factor(restitution, u0))
+
+
+class Contact:
+    """One contact context (contact_init ... contact_destroy) on a CUDA device."""
+
+    def __init__(self, shape_type, shape_param, face_offset, planes, young, poisson, n_cells, dx,
+                 indicator=SHARP, smooth_width=1.0, inflate=0.0, damping_c=0.0, precision=FP32_TILE,
+                 max_pairs=None, max_neighbors=64, max_tiles=0, use_graph=True, device=None, stream=None):
+        if not torch.cuda.is_available():
+            raise ContactError(ECUDA, "no CUDA device: the contact path has no CPU fallback")
+        self.lib = load_library()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        n = int(len(shape_type))
+        cfg = Config()
+        nc = (ctypes.c_int32 * 3)(*[int(v) for v in n_cells])
+        self.lib.contact_config_default(ctypes.byref(cfg), n, nc, float(dx))
+        cfg.indicator, cfg.smooth_width, cfg.inflate = int(indicator), float(smooth_width), float(inflate)
+        cfg.damping_c, cfg.precision = float(damping_c), int(precision)
+        if max_pairs is not None:
+            cfg.max_pairs = int(max_pairs)
+        cfg.max_neighbors, cfg.max_tiles, cfg.use_graph = int(max_neighbors), int(max_tiles), int(bool(use_graph))
+        self.cfg = cfg
+        self.n = n
+        self.max_pairs = int(cfg.max_pairs)
+        arrs = [np.ascontiguousarray(shape_type, np.int32), np.ascontiguousarray(shape_param, np.float64),
+                np.ascontiguousarray(face_offset, np.int32),
+                np.ascontiguousarray(planes if len(planes) else np.zeros((1, 4)), np.float64),
+                np.ascontiguousarray(young, np.float64), np.ascontiguousarray(poisson, np.float64)]
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+            handle = ctypes.c_void_p()
+            rc = self.lib.contact_init(ctypes.byref(cfg), *[_ptr(a) for a in arrs],
+                                       ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(handle))
+        if rc != OK:
+            raise ContactError(rc, "contact_init rejected the configuration or shapes")
+        self.ctx = handle
+        dev = self.device
+        self.pair_ij = torch.zeros((self.max_pairs, 2), dtype=torch.int32, device=dev)
+        self.pair_out = torch.zeros((self.max_pairs, PAIR_OUT_COLS), dtype=torch.float64, device=dev)
+        self.n_pairs = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.force = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+        self.torque = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+
+    @classmethod
+    def from_state(cls, st, **kw):
+        """Context for a workloads.State (shapes, material, lattice, indicator)."""
+        args = dict(indicator=st.indicator, smooth_width=st.smooth_width, inflate=st.inflate,
+                    damping_c=st.damping_c)
+        args.update(kw)
+        return cls(st.shape_type, st.shape_param, st.face_offset, st.planes, st.young, st.poisson, st.n_cells,
+                   st.dx, **args)
+
+    # ------------------------------------------------------------------ calls
+    def _raise(self, rc, what):
+        msg = self.lib.contact_last_error(self.ctx).decode()
+        raise ContactError(rc, f"{what}: {msg}")
+
+    def step_async(self, pos, quat, vel=None):
+        """Enqueue contact_step on the context stream (outputs in self.*)."""
+        for t in (pos, quat) + ((vel,) if vel is not None else ()):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ContactError(EINVAL, "pos/quat/vel must be contiguous float64 CUDA tensors")
+        if pos.shape != (self.n, 3) or quat.shape != (self.n, 4):
+            raise ContactError(EINVAL, "pos must be [N,3] and quat [N,4]")
+        rc = self.lib.contact_step(self.ctx, _ptr(pos), _ptr(quat), _ptr(vel), _ptr(self.pair_ij),
+                                   _ptr(self.pair_out), _ptr(self.n_pairs), _ptr(self.force), _ptr(self.torque))
+        if rc != OK:
+            self._raise(rc, "contact_step")
+
+    def step(self, pos, quat, vel=None, check=True):
+        """contact_step; waits for the result when check is True."""
+        cur = torch.cuda.current_stream(self.device)
+        self.stream.wait_stream(cur)
+        self.step_async(pos, quat, vel)
+        cur.wait_stream(self.stream)
+        if check:
+            self.check()
+        P = int(self.n_pairs.item())
+        P = min(P, self.max_pairs)
+        return dict(pair_ij=self.pair_ij[:P], pair_out=self.pair_out[:P], force=self.force, torque=self.torque,
+                    n_pairs=P)
+
+    def backward(self, grad_force, grad_torque, check=True):
+        gp = torch.zeros((self.n, 3), dtype=torch.float64, device=self.device)
+        gq = torch.zeros((self.n, 4), dtype=torch.float64, device=self.device)
+        cur = torch.cuda.current_stream(self.device)
+        self.stream.wait_stream(cur)
+        rc = self.lib.contact_backward(self.ctx, _ptr(grad_force.contiguous()), _ptr(grad_torque.contiguous()),
+                                       _ptr(gp), _ptr(gq))
+        if rc != OK:
+            self._raise(rc, "contact_backward")
+        cur.wait_stream(self.stream)
+        if check:
+            self.check()
+        return gp, gq
+
+    def check(self):
+        rc = self.lib.contact_check(self.ctx)
+        if rc != OK:
+            self._raise(rc, "device error")
+
+    def clear_error(self):
+        self.lib.contact_clear_error(self.ctx)
+
+    def stats(self):
+        s = (ctypes.c_int64 * 10)()
+        rc = self.lib.contact_stats(self.ctx, s)
+        if rc != OK:
+            self._raise(rc, "contact_stats")
+        keys = ["pairs", "cells", "tiles", "overlapping", "kernels", "narrow_grid", "bins_x", "replayed",
+                "nominal_ops", "max_tiles"]
+        return dict(zip(keys, [int(v) for v in s]))
+
+    def narrow_time_ms(self) -> float:
+        """Device time of the last step's node-sweep kernel (CUDA events)."""
+        ms = ctypes.c_float()
+        rc = self.lib.contact_narrow_time(self.ctx, ctypes.byref(ms))
+        if rc != OK:
+            self._raise(rc, "contact_narrow_time")
+        return float(ms.value)
+
+    def particle_boxes(self):
+        out = torch.zeros((self.n, 6), dtype=torch.int32, device=self.device)
+        rc = self.lib.contact_particle_boxes(self.ctx, _ptr(out))
+        if rc != OK:
+            self._raise(rc, "contact_particle_boxes")
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return out
+
+    def kernels_per_step(self):
+        return int(self.lib.contact_kernels_per_step(self.ctx))
+
+    def kernels_per_backward(self):
+        return int(self.lib.contact_kernels_per_backward(self.ctx))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.contact_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ContactFunction(torch.autograd.Function):
+    """(pos, quat) -> (force, torque) with the library's adjoint as backward."""
+
+    @staticmethod
+    def forward(ctx, model, pos, quat):
+        out = model.step(pos, quat)
+        ctx.model = model
+        return out["force"].clone(), out["torque"].clone()
+
+    @staticmethod
+    def backward(ctx, gF, gT):
+        gp, gq = ctx.model.backward(gF.to(torch.float64).contiguous(), gT.to(torch.float64).contiguous())
+        return None, gp, gq
+
+
+def contact_forces(model: Contact, pos: torch.Tensor, quat: torch.Tensor):
+    """Per-particle contact force and torque, differentiable w.r.t. pos and quat."""
+    return ContactFunction.apply(model, pos, quat)

@@ -1,0 +1,208 @@
+// Internal layouts and device helpers of libcontact (not part of the C-ABI).
+//
+// Memory layout in HBM (all buffers allocated once by contact_init):
+//   shape tables (read-only): type/kind per particle, FP64 body parameters,
+//     body planes, offset-shape vertices (for the AABB), E and nu;
+//   per-step particle records: FP64 pose copy (the adjoint's tape), FP64
+//     rotation, node ranges, bins, FP32 geometry for the node sweep
+//     (R^T rows, effective sizes, world-frame polytope planes);
+//   pair list: PairRec per candidate pair, tile -> pair map, FP32 tile
+//     partials, FP64 per-pair sums and results.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gbc {
+
+// Sweep kinds: polytopes with up to 20 faces keep their face values in
+// registers (padded to 20); larger ones (up to 32) read planes from shared memory.
+enum Kind : int { KIND_SPHERE = 0, KIND_CUBOID = 1, KIND_POLY = 2, KIND_POLYG = 3 };
+constexpr int kRegFaces = 20;
+
+constexpr int kMaxFaces = 32;         // faces of one polytope
+constexpr int kTileItemsPerLane = 4;  // node lines (segments) per lane per tile
+constexpr int kSegMax = 16;           // longest line segment of one item
+constexpr int kPartialFloats = 12;    // FP32 partial sums per tile
+constexpr int kSumDoubles = 10;       // FP64 sums per pair
+constexpr int kTapeDoubles = 16;      // FP64 per-pair values kept for the adjoint
+constexpr int kFtDoubles = 9;         // per-pair F, T_A, T_B
+
+// Error codes written by kernels (same numbering as contact_status).
+constexpr int kErrInval = 1;
+constexpr int kErrCapacity = 4;
+
+// --------------------------------------------------------------------------
+// Constant per-context parameters, passed to every kernel by value.
+struct Params {
+  int n;                 // particles
+  int ncell[3];          // lattice nodes per axis
+  double dx, inv_dx;
+  double L[3];           // n_cells * dx
+  double delta;          // AABB offset: inflate (+ w dx / 2 in smoothed mode)
+  double inflate;        // physical
+  double wdx;            // smoothing width, physical
+  int smooth;            // 1: smoothed indicator
+  int precision;         // 0: FP32 tiles, 1: FP64 per pair
+  double damping_c;
+  int nbin[3];           // bins per axis
+  double binw[3];        // bin width (physical)
+  int max_pairs, max_nbr, max_tiles;
+  // FP32 copies for the node sweep (lattice units)
+  float inflate_l, inv_w, neg6_over_w;
+};
+
+// Shape tables (read-only after contact_init).
+struct Shapes {
+  const int* type;         // [N] CONTACT_SHAPE_*
+  const double* param;     // [N,3]
+  const int* face_off;     // [N+1]
+  const double* planes;    // [F,4] body frame
+  const int* vert_off;     // [N+1]
+  const double* verts;     // [V,3] vertices of the offset shape (AABB)
+  const double* young;     // [N]
+  const double* poisson;   // [N]
+  const float* size_l;     // [N,3] lattice units incl. inflate: sphere r', cuboid h'
+  const int* nomops;       // [N] nominal FP32 lane-ops of one signed-distance test
+};
+
+// Per-step particle records.
+struct Parts {
+  double* X;       // [N,3] copy of the positions of the step
+  double* qhat;    // [N,4] normalised quaternion
+  double* qnorm;   // [N]
+  double* R;       // [N,9] FP64 rotation, row-major, body -> world
+  int* lohi;       // [N,6]
+  int* bin;        // [N]
+  int* slot;       // [N]
+  float* Rt;       // [N,9] FP32 R^T (row k = body axis k in world)
+  float4* wplane;  // [F] FP32 world normal, offset (lattice units, incl. inflate)
+};
+
+// One candidate pair (i < j).
+struct PairRec {
+  int i, j;
+  int lo[3];       // lower node of the pair box (i's frame)
+  int dim[3];      // nodes per axis
+  int shift[3];    // image index s of j: X_j' = X_j - s L
+  int axis;        // sweep axis
+  int seglen;      // nodes per line segment
+  int nseg;        // segments per line
+  int nitems;      // lines * nseg
+  int tile0;       // first tile of the pair
+  int ntiles;
+  int kinds;       // kind of i | kind of j << 8 (set by the planner)
+  // particle centres relative to lo in lattice units, split into the nearest
+  // integer and an FP32 remainder in [-1/2, 1/2] so that node offsets stay exact
+  int ai[3], bi[3];
+  float af[3], bf[3];
+};
+
+// Work lists shared by the step's kernels.
+struct Lists {
+  int* bin_count;   // [nbins]
+  int* bin_start;   // [nbins + 1]
+  int* bin_items;   // [N]
+  int* up_count;    // [N] partners j > p
+  int* up_list;     // [N, max_nbr]
+  int* dn_count;    // [N] partners i < p
+  int* dn_list;     // [N, max_nbr]
+  int* row_off;     // [N + 1] first pair of particle i
+  PairRec* pairs;   // [max_pairs]
+  int* tile_pair;   // [max_tiles]
+  float* partial;   // [max_tiles, kPartialFloats]
+  double* sums;     // [max_pairs, kSumDoubles] (FP64 path writes here directly)
+  double* tape;     // [max_pairs, kTapeDoubles]
+  double* ft;       // [max_pairs, kFtDoubles]
+  const int* kind;  // [N] sweep kind of each particle (Kind, polytopes by face bucket)
+  int* counters;    // [8]: 0 pairs, 1 tiles, 2 queue, 3 cells(lo), 4 cells(hi), 5 overlapping pairs, 6 adjoint queue
+  unsigned long long* u64;  // [4]: 0 node evaluations, 1 nominal lane-ops of the node sweep
+  int* err;         // [1] sticky device error
+  int* err_host;    // mapped host word mirroring err
+};
+
+// --------------------------------------------------------------------------
+// FP64 helpers with explicit rounding (no contraction): the node ranges must
+// agree bit for bit with an independent CPU evaluation of the same formulas.
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+
+// Rotation of the normalised quaternion (w, x, y, z), body -> world, row-major.
+__device__ inline void rotation_rn(const double q[4], double* qh, double* qn, double R[9]) {
+  const double nrm = __dsqrt_rn(dadd(dadd(dadd(dmul(q[0], q[0]), dmul(q[1], q[1])), dmul(q[2], q[2])),
+                                     dmul(q[3], q[3])));
+  const double w = __ddiv_rn(q[0], nrm), x = __ddiv_rn(q[1], nrm), y = __ddiv_rn(q[2], nrm),
+               z = __ddiv_rn(q[3], nrm);
+  qh[0] = w; qh[1] = x; qh[2] = y; qh[3] = z;
+  *qn = nrm;
+  R[0] = dsub(1.0, dmul(2.0, dadd(dmul(y, y), dmul(z, z))));
+  R[1] = dmul(2.0, dsub(dmul(x, y), dmul(w, z)));
+  R[2] = dmul(2.0, dadd(dmul(x, z), dmul(w, y)));
+  R[3] = dmul(2.0, dadd(dmul(x, y), dmul(w, z)));
+  R[4] = dsub(1.0, dmul(2.0, dadd(dmul(x, x), dmul(z, z))));
+  R[5] = dmul(2.0, dsub(dmul(y, z), dmul(w, x)));
+  R[6] = dmul(2.0, dsub(dmul(x, z), dmul(w, y)));
+  R[7] = dmul(2.0, dadd(dmul(y, z), dmul(w, x)));
+  R[8] = dsub(1.0, dmul(2.0, dadd(dmul(x, x), dmul(y, y))));
+}
+
+// FP64 signed distance (physical units, reduced by inflate) at world point x
+// for a particle at X with rotation R; writes the world gradient of the
+// active branch (first maximal face on ties).
+__device__ inline double sdf64(int type, const double* prm, const double* planes, int nf, const double X[3],
+                               const double R[9], const double x[3], double inflate, double g[3]) {
+  const double r[3] = {x[0] - X[0], x[1] - X[1], x[2] - X[2]};
+  if (type == 0) {
+    const double nr = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    for (int k = 0; k < 3; ++k) g[k] = nr > 0.0 ? r[k] / nr : 0.0;
+    return nr - prm[0] - inflate;
+  }
+  double y[3];
+  for (int k = 0; k < 3; ++k) y[k] = R[k] * r[0] + R[3 + k] * r[1] + R[6 + k] * r[2];
+  double best = -1e300, gb[3] = {0.0, 0.0, 0.0};
+  if (type == 1) {
+    for (int k = 0; k < 3; ++k) {
+      const double a = fabs(y[k]) - prm[k];
+      if (a > best) {
+        best = a;
+        gb[0] = gb[1] = gb[2] = 0.0;
+        gb[k] = y[k] < 0.0 ? -1.0 : 1.0;
+      }
+    }
+  } else {
+    for (int f = 0; f < nf; ++f) {
+      const double* e = planes + 4 * f;
+      const double a = (e[0] * y[0] + e[1] * y[1] + e[2] * y[2]) - e[3];
+      if (a > best) {
+        best = a;
+        gb[0] = e[0]; gb[1] = e[1]; gb[2] = e[2];
+      }
+    }
+  }
+  for (int k = 0; k < 3; ++k) g[k] = R[3 * k] * gb[0] + R[3 * k + 1] * gb[1] + R[3 * k + 2] * gb[2];
+  return best - inflate;
+}
+
+__device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0, code); }
+
+// --------------------------------------------------------------------------
+// Launch wrappers (defined in the kernel translation units).
+void launch_pose(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* pos,
+                 const double* quat, cudaStream_t st);
+void launch_bin_scatter(const Params& P, const Parts& D, const Lists& W, cudaStream_t st);
+void launch_broad(const Params& P, const Parts& D, const Lists& W, cudaStream_t st);
+void launch_plan(const Params& P, const Shapes& S, const Parts& D, const Lists& W, int32_t* pair_ij, int32_t* n_pairs,
+                 cudaStream_t st);
+void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists& W, int grid, cudaStream_t st);
+int narrow_grid(const Params& P);
+void launch_finalize(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel,
+                     double* pair_out, cudaStream_t st);
+void launch_particle_sum(const Params& P, const Parts& D, const Lists& W, double* force, double* torque,
+                         cudaStream_t st);
+size_t adjoint_scratch_doubles(int max_pairs, int max_tiles);
+void launch_adjoint(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel,
+                    const double* gF, const double* gT, double* gpos, double* gquat, double* scratch,
+                    int grid, cudaStream_t st);
+
+}  // namespace gbc

@@ -1,0 +1,520 @@
+// Host side of libcontact: context, shape preparation, validation, buffer
+// allocation, launch sequencing, CUDA-graph replay and error reporting.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/contact.h"
+#include "contact_dev.cuh"
+
+using namespace gbc;
+
+struct contact_ctx {
+  contact_config cfg{};
+  Params P{};
+  Shapes S{};
+  Parts D{};
+  Lists W{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int grid_narrow = 0;
+  int grid_adjoint = 0;
+  std::vector<void*> dev_allocs;
+  int* err_host = nullptr;        // mapped pinned word written by the last kernel of a step
+  double* adj_scratch = nullptr;  // adjoint tile partials, pair seeds and pair gradients
+  std::string last_error = "no error";
+  // graph cache
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[9] = {};
+  bool last_replay = false;
+  cudaEvent_t ev_narrow[2] = {nullptr, nullptr};
+  // tape of the last step (for contact_backward)
+  bool have_step = false;
+  const double* last_vel = nullptr;
+};
+
+namespace {
+
+contact_status fail(contact_ctx* c, contact_status s, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return s;
+}
+
+contact_status cuda_fail(contact_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, CONTACT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <class T>
+cudaError_t dev_alloc(contact_ctx* c, T** p, size_t count) {
+  void* ptr = nullptr;
+  const cudaError_t e = cudaMalloc(&ptr, std::max<size_t>(count, 1) * sizeof(T));
+  if (e == cudaSuccess) {
+    c->dev_allocs.push_back(ptr);
+    *p = static_cast<T*>(ptr);
+  }
+  return e;
+}
+
+template <class T>
+cudaError_t upload(contact_ctx* c, T** p, const std::vector<T>& v) {
+  cudaError_t e = dev_alloc(c, p, v.size());
+  if (e != cudaSuccess || v.empty()) return e;
+  return cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// Vertices of {y : n_i . y <= d_i + delta}: every plane triple solved by
+// Cramer's rule (cross products, determinant, then the weighted sum divided
+// by the determinant), kept when no half-space is violated by more than
+// 1e-9 max(1, |d + delta|).  The AABB node ranges derived from these vertices
+// must match an independent CPU evaluation bit for bit, so the formula and
+// its operation order are fixed; contraction is off for this file.
+std::vector<double> offset_vertices(const double* pl, int F, double delta) {
+  std::vector<double> out;
+  double dmax = 1.0;
+  for (int i = 0; i < F; ++i) dmax = std::max(dmax, std::fabs(pl[4 * i + 3] + delta));
+  const double tol = 1e-9 * dmax;
+  for (int i = 0; i < F; ++i)
+    for (int j = i + 1; j < F; ++j)
+      for (int k = j + 1; k < F; ++k) {
+        const double* a = pl + 4 * i;
+        const double* b = pl + 4 * j;
+        const double* c = pl + 4 * k;
+        const double bc[3] = {b[1] * c[2] - b[2] * c[1], b[2] * c[0] - b[0] * c[2], b[0] * c[1] - b[1] * c[0]};
+        const double ca[3] = {c[1] * a[2] - c[2] * a[1], c[2] * a[0] - c[0] * a[2], c[0] * a[1] - c[1] * a[0]};
+        const double ab[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+        const double det = a[0] * bc[0] + a[1] * bc[1] + a[2] * bc[2];
+        if (std::fabs(det) < 1e-12) continue;
+        const double da = a[3] + delta, db = b[3] + delta, dc = c[3] + delta;
+        double v[3];
+        for (int t = 0; t < 3; ++t) v[t] = (da * bc[t] + db * ca[t] + dc * ab[t]) / det;
+        bool ok = true;
+        for (int m = 0; m < F && ok; ++m) {
+          const double* e = pl + 4 * m;
+          ok = !(e[0] * v[0] + e[1] * v[1] + e[2] * v[2] - (e[3] + delta) > tol);
+        }
+        if (ok) out.insert(out.end(), v, v + 3);
+      }
+  return out;
+}
+
+// Bounded iff no direction u has n_i . u <= 0 for every face; candidate
+// extreme rays of the recession cone are +-(n_i x n_j).
+bool bounded(const double* pl, int F) {
+  for (int i = 0; i < F; ++i)
+    for (int j = i + 1; j < F; ++j) {
+      const double* a = pl + 4 * i;
+      const double* b = pl + 4 * j;
+      const double u[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+      const double nu = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+      if (nu < 1e-12) continue;
+      for (int sg = -1; sg <= 1; sg += 2) {
+        bool ray = true;
+        for (int m = 0; m < F && ray; ++m) {
+          const double* e = pl + 4 * m;
+          ray = !(sg * (e[0] * u[0] + e[1] * u[1] + e[2] * u[2]) / nu > 1e-12);
+        }
+        if (ray) return false;
+      }
+    }
+  return true;
+}
+
+contact_status check_sticky(contact_ctx* c) {
+  const int e = *reinterpret_cast<volatile int*>(c->err_host);
+  if (e != 0) {
+    return fail(c, static_cast<contact_status>(e),
+                e == CONTACT_ECAPACITY ? "device: capacity exceeded (pairs, neighbours or tiles)"
+                                       : "device: invalid pose (position outside [0, L), zero or non-finite quaternion)");
+  }
+  return CONTACT_OK;
+}
+
+void enqueue_step(contact_ctx* c, const double* pos, const double* quat, const double* vel, int32_t* pair_ij,
+                  double* pair_out, int32_t* n_pairs, double* force, double* torque) {
+  const int nbins = c->P.nbin[0] * c->P.nbin[1] * c->P.nbin[2];
+  cudaMemsetAsync(c->W.bin_count, 0, sizeof(int) * nbins, c->stream);
+  launch_pose(c->P, c->S, c->D, c->W, pos, quat, c->stream);
+  launch_bin_scatter(c->P, c->D, c->W, c->stream);
+  launch_broad(c->P, c->D, c->W, c->stream);
+  launch_plan(c->P, c->S, c->D, c->W, pair_ij, n_pairs, c->stream);
+  cudaEventRecord(c->ev_narrow[0], c->stream);
+  launch_narrow(c->P, c->S, c->D, c->W, c->grid_narrow, c->stream);
+  cudaEventRecord(c->ev_narrow[1], c->stream);
+  launch_finalize(c->P, c->S, c->D, c->W, vel, pair_out, c->stream);
+  launch_particle_sum(c->P, c->D, c->W, force, torque, c->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+void contact_config_default(contact_config* cfg, int32_t n_particles, const int32_t n_cells[3], double dx) {
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->n_particles = n_particles;
+  for (int k = 0; k < 3; ++k) cfg->n_cells[k] = n_cells[k];
+  cfg->dx = dx;
+  cfg->indicator = CONTACT_INDICATOR_SHARP;
+  cfg->smooth_width = 1.0;
+  cfg->inflate = 0.0;
+  cfg->damping_c = 0.0;
+  cfg->precision = CONTACT_PRECISION_FP32_TILE;
+  cfg->max_pairs = std::max(64, 16 * n_particles);
+  cfg->max_neighbors = 64;
+  cfg->max_tiles = 0;
+  cfg->use_graph = 1;
+}
+
+double contact_damping_factor(double e, double u0) {
+  if (!(u0 > 0.0)) return 0.0;
+  return 1.5 * (1.0 - e) * (11.0 - e) / ((1.0 + 9.0 * e) * u0);
+}
+
+contact_status contact_init(const contact_config* cfg, const int32_t* shape_type, const double* shape_param,
+                            const int32_t* face_offset, const double* planes, const double* young,
+                            const double* poisson, void* stream, contact_ctx** out) {
+  if (out == nullptr) return CONTACT_EINVAL;
+  *out = nullptr;
+  if (cfg == nullptr || shape_type == nullptr || shape_param == nullptr || face_offset == nullptr ||
+      young == nullptr || poisson == nullptr)
+    return CONTACT_EINVAL;
+  const contact_config& C = *cfg;
+  const int n = C.n_particles;
+  if (n < 1 || !(C.dx > 0.0) || !std::isfinite(C.dx) || C.max_pairs < 1) return CONTACT_EINVAL;
+  for (int k = 0; k < 3; ++k)
+    if (C.n_cells[k] < 1) return CONTACT_EINVAL;
+  if (C.indicator != 0 && C.indicator != 1) return CONTACT_EINVAL;
+  if (C.precision != 0 && C.precision != 1) return CONTACT_EINVAL;
+  if (!(C.smooth_width > 0.0) || !(C.inflate >= 0.0) || !(C.damping_c >= 0.0)) return CONTACT_EINVAL;
+  if (C.max_neighbors < 0 || C.max_neighbors > 512 || C.max_tiles < 0) return CONTACT_EINVAL;
+  const int max_nbr = C.max_neighbors > 0 ? C.max_neighbors : 64;
+  const long long max_tiles_ll = C.max_tiles > 0 ? C.max_tiles : 64LL * C.max_pairs;
+  if (max_tiles_ll > (1LL << 30)) return CONTACT_EINVAL;
+
+  const double band = (C.indicator == 1) ? (0.5 * C.smooth_width) * C.dx : 0.0;
+  const double delta = C.inflate + band;
+  std::vector<int> type(n), kind(n), vert_off(n + 1, 0);
+  std::vector<double> param(3 * static_cast<size_t>(n)), verts;
+  std::vector<float> size_l(3 * static_cast<size_t>(n));
+  // nominal FP32 lane-ops of one signed-distance test (roofline accounting):
+  // sphere 7, cuboid 15, polytope with F faces 4F
+  std::vector<int> nomops(n);
+  const int nfaces = face_offset[n];
+  if (face_offset[0] != 0 || nfaces < 0 || (nfaces > 0 && planes == nullptr)) return CONTACT_EINVAL;
+  double rmax = 0.0;
+  for (int p = 0; p < n; ++p) {
+    type[p] = shape_type[p];
+    for (int k = 0; k < 3; ++k) param[3 * p + k] = shape_param[3 * p + k];
+    if (!(young[p] > 0.0) || !(poisson[p] >= 0.0) || !(poisson[p] < 1.0)) return CONTACT_EINVAL;
+    const int f0 = face_offset[p], f1 = face_offset[p + 1];
+    if (f1 < f0) return CONTACT_EINVAL;
+    double circ = 0.0;
+    if (type[p] == CONTACT_SHAPE_SPHERE) {
+      if (!(param[3 * p] > 0.0) || f1 != f0) return CONTACT_EINVAL;
+      circ = param[3 * p] + delta;
+      kind[p] = KIND_SPHERE;
+      nomops[p] = 7;
+      size_l[3 * p] = static_cast<float>((param[3 * p] + C.inflate) / C.dx);
+    } else if (type[p] == CONTACT_SHAPE_CUBOID) {
+      if (f1 != f0) return CONTACT_EINVAL;
+      double e2 = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        if (!(param[3 * p + k] > 0.0)) return CONTACT_EINVAL;
+        e2 += (param[3 * p + k] + delta) * (param[3 * p + k] + delta);
+        size_l[3 * p + k] = static_cast<float>((param[3 * p + k] + C.inflate) / C.dx);
+      }
+      circ = std::sqrt(e2);
+      kind[p] = KIND_CUBOID;
+      nomops[p] = 15;
+    } else if (type[p] == CONTACT_SHAPE_POLYTOPE) {
+      const int F = f1 - f0;
+      if (F < 4 || F > kMaxFaces) return CONTACT_EINVAL;
+      const double* pl = planes + 4 * f0;
+      for (int f = 0; f < F; ++f) {
+        const double* e = pl + 4 * f;
+        const double nn = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+        if (!(std::fabs(nn - 1.0) <= 1e-9) || !(e[3] > 0.0) || !std::isfinite(e[3])) return CONTACT_EINVAL;
+      }
+      if (!bounded(pl, F)) return CONTACT_EINVAL;
+      std::vector<double> v = offset_vertices(pl, F, delta);
+      if (v.size() < 12) return CONTACT_EINVAL;
+      for (size_t t = 0; t < v.size(); t += 3)
+        circ = std::max(circ, std::sqrt(v[t] * v[t] + v[t + 1] * v[t + 1] + v[t + 2] * v[t + 2]));
+      verts.insert(verts.end(), v.begin(), v.end());
+      kind[p] = F <= kRegFaces ? KIND_POLY : KIND_POLYG;
+      nomops[p] = 4 * F;
+    } else {
+      return CONTACT_EINVAL;
+    }
+    vert_off[p + 1] = static_cast<int>(verts.size() / 3);
+    rmax = std::max(rmax, circ);
+  }
+  double L[3];
+  for (int k = 0; k < 3; ++k) {
+    L[k] = C.n_cells[k] * C.dx;
+    if (!(L[k] > 4.0 * rmax + 2.0 * C.dx)) return CONTACT_EDOMAIN;
+  }
+
+  contact_ctx* c = new contact_ctx();
+  c->cfg = C;
+  c->stream = static_cast<cudaStream_t>(stream);
+  cudaGetDevice(&c->device);
+  Params& P = c->P;
+  P.n = n;
+  for (int k = 0; k < 3; ++k) {
+    P.ncell[k] = C.n_cells[k];
+    P.L[k] = L[k];
+    // bins at least 2 R_max + 2 dx wide: intersecting AABBs sit in adjacent bins
+    int nb = static_cast<int>(std::floor(L[k] / (2.0 * rmax + 2.0 * C.dx)));
+    if (nb < 3) nb = 1;
+    nb = std::min(nb, 256);
+    P.nbin[k] = nb;
+    P.binw[k] = L[k] / nb;
+  }
+  P.dx = C.dx;
+  P.inv_dx = 1.0 / C.dx;
+  P.delta = delta;
+  P.inflate = C.inflate;
+  P.wdx = C.smooth_width * C.dx;
+  P.smooth = C.indicator;
+  P.precision = C.precision;
+  P.damping_c = C.damping_c;
+  P.max_pairs = C.max_pairs;
+  P.max_nbr = max_nbr;
+  P.max_tiles = static_cast<int>(max_tiles_ll);
+  P.inflate_l = static_cast<float>(C.inflate / C.dx);
+  P.inv_w = static_cast<float>(1.0 / C.smooth_width);
+  P.neg6_over_w = static_cast<float>(-6.0 / C.smooth_width);
+
+  cudaError_t e = cudaSuccess;
+  std::vector<double> pl_vec(planes ? planes : nullptr, planes ? planes + 4 * static_cast<size_t>(nfaces) : nullptr);
+  std::vector<int> foff(face_offset, face_offset + n + 1);
+  std::vector<double> yv(young, young + n), pv(poisson, poisson + n);
+  int *d_type, *d_foff, *d_voff, *d_kind;
+  double *d_param, *d_planes, *d_verts, *d_young, *d_pois;
+  float* d_size;
+  int* d_nomops;
+#define GBC_TRY(x)                                              \
+  do {                                                          \
+    e = (x);                                                    \
+    if (e != cudaSuccess) {                                     \
+      contact_destroy(c);                                       \
+      return e == cudaErrorMemoryAllocation ? CONTACT_ENOMEM : CONTACT_ECUDA; \
+    }                                                           \
+  } while (0)
+  GBC_TRY(upload(c, &d_type, type));
+  GBC_TRY(upload(c, &d_kind, kind));
+  GBC_TRY(upload(c, &d_param, param));
+  GBC_TRY(upload(c, &d_foff, foff));
+  GBC_TRY(upload(c, &d_planes, pl_vec));
+  GBC_TRY(upload(c, &d_voff, vert_off));
+  GBC_TRY(upload(c, &d_verts, verts));
+  GBC_TRY(upload(c, &d_young, yv));
+  GBC_TRY(upload(c, &d_pois, pv));
+  GBC_TRY(upload(c, &d_size, size_l));
+  GBC_TRY(upload(c, &d_nomops, nomops));
+  c->S = Shapes{d_type, d_param, d_foff, d_planes, d_voff, d_verts, d_young, d_pois, d_size, d_nomops};
+
+  Parts& D = c->D;
+  GBC_TRY(dev_alloc(c, &D.X, 3 * static_cast<size_t>(n)));
+  GBC_TRY(dev_alloc(c, &D.qhat, 4 * static_cast<size_t>(n)));
+  GBC_TRY(dev_alloc(c, &D.qnorm, static_cast<size_t>(n)));
+  GBC_TRY(dev_alloc(c, &D.R, 9 * static_cast<size_t>(n)));
+  GBC_TRY(dev_alloc(c, &D.lohi, 6 * static_cast<size_t>(n)));
+  GBC_TRY(dev_alloc(c, &D.bin, static_cast<size_t>(n)));
+  GBC_TRY(dev_alloc(c, &D.slot, static_cast<size_t>(n)));
+  GBC_TRY(dev_alloc(c, &D.Rt, 9 * static_cast<size_t>(n)));
+  GBC_TRY(dev_alloc(c, &D.wplane, static_cast<size_t>(std::max(nfaces, 1))));
+
+  Lists& W = c->W;
+  const size_t nbins = static_cast<size_t>(P.nbin[0]) * P.nbin[1] * P.nbin[2];
+  const size_t mp = static_cast<size_t>(C.max_pairs), mt = static_cast<size_t>(P.max_tiles);
+  GBC_TRY(dev_alloc(c, &W.bin_count, nbins));
+  GBC_TRY(dev_alloc(c, &W.bin_start, nbins + 1));
+  GBC_TRY(dev_alloc(c, &W.bin_items, static_cast<size_t>(n)));
+  GBC_TRY(dev_alloc(c, &W.up_count, static_cast<size_t>(n)));
+  GBC_TRY(dev_alloc(c, &W.up_list, static_cast<size_t>(n) * max_nbr));
+  GBC_TRY(dev_alloc(c, &W.dn_count, static_cast<size_t>(n)));
+  GBC_TRY(dev_alloc(c, &W.dn_list, static_cast<size_t>(n) * max_nbr));
+  GBC_TRY(dev_alloc(c, &W.row_off, static_cast<size_t>(n) + 1));
+  GBC_TRY(dev_alloc(c, &W.pairs, mp));
+  GBC_TRY(dev_alloc(c, &W.tile_pair, mt));
+  GBC_TRY(dev_alloc(c, &W.partial, mt * kPartialFloats));
+  GBC_TRY(dev_alloc(c, &W.sums, mp * kSumDoubles));
+  GBC_TRY(dev_alloc(c, &W.tape, mp * kTapeDoubles));
+  GBC_TRY(dev_alloc(c, &W.ft, mp * kFtDoubles));
+  GBC_TRY(dev_alloc(c, &W.counters, 8));
+  GBC_TRY(dev_alloc(c, &W.u64, 4));
+  GBC_TRY(dev_alloc(c, &W.err, 1));
+  GBC_TRY(dev_alloc(c, &c->adj_scratch, adjoint_scratch_doubles(C.max_pairs, P.max_tiles)));
+  W.kind = d_kind;
+  GBC_TRY(cudaMemset(W.counters, 0, 8 * sizeof(int)));
+  GBC_TRY(cudaMemset(W.u64, 0, 4 * sizeof(unsigned long long)));
+  GBC_TRY(cudaMemset(W.err, 0, sizeof(int)));
+  GBC_TRY(cudaMemset(W.up_count, 0, sizeof(int) * n));
+  GBC_TRY(cudaMemset(W.dn_count, 0, sizeof(int) * n));
+  GBC_TRY(cudaEventCreate(&c->ev_narrow[0]));
+  GBC_TRY(cudaEventCreate(&c->ev_narrow[1]));
+  GBC_TRY(cudaHostAlloc(reinterpret_cast<void**>(&c->err_host), sizeof(int), cudaHostAllocMapped));
+  *c->err_host = 0;
+  int* err_dev_view = nullptr;
+  GBC_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&err_dev_view), c->err_host, 0));
+  W.err_host = err_dev_view;
+#undef GBC_TRY
+  c->grid_narrow = narrow_grid(P);
+  c->grid_adjoint = c->grid_narrow;
+  *out = c;
+  return CONTACT_OK;
+}
+
+contact_status contact_set_stream(contact_ctx* c, void* stream) {
+  if (c == nullptr) return CONTACT_EINVAL;
+  c->stream = static_cast<cudaStream_t>(stream);
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  return CONTACT_OK;
+}
+
+contact_status contact_step(contact_ctx* c, const double* pos, const double* quat, const double* vel,
+                            int32_t* pair_ij, double* pair_out, int32_t* n_pairs, double* force,
+                            double* torque) {
+  if (c == nullptr) return CONTACT_EINVAL;
+  if (pos == nullptr || quat == nullptr || pair_ij == nullptr || pair_out == nullptr || n_pairs == nullptr ||
+      force == nullptr || torque == nullptr)
+    return fail(c, CONTACT_EINVAL, "contact_step: null buffer");
+  const contact_status sticky = check_sticky(c);
+  if (sticky != CONTACT_OK) return sticky;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(c->stream, &cap);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamIsCapturing");
+  const void* key[9] = {pos, quat, vel, pair_ij, pair_out, n_pairs, force, torque, c->stream};
+  c->last_replay = false;
+  if (cap == cudaStreamCaptureStatusNone && c->cfg.use_graph && c->stream != nullptr) {
+    if (c->gexec == nullptr || std::memcmp(key, c->gkey, sizeof(key)) != 0) {
+      if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
+      enqueue_step(c, pos, quat, vel, pair_ij, pair_out, n_pairs, force, torque);
+      e = cudaStreamEndCapture(c->stream, &g);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&c->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        c->gexec = nullptr;
+        return cuda_fail(c, e, "cudaGraphInstantiate");
+      }
+      std::memcpy(c->gkey, key, sizeof(key));
+    } else {
+      c->last_replay = true;
+    }
+    e = cudaGraphLaunch(c->gexec, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+  } else {
+    enqueue_step(c, pos, quat, vel, pair_ij, pair_out, n_pairs, force, torque);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+  }
+  c->have_step = true;
+  c->last_vel = vel;
+  return CONTACT_OK;
+}
+
+contact_status contact_check(contact_ctx* c) {
+  if (c == nullptr) return CONTACT_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  int err = 0;
+  e = cudaMemcpy(&err, c->W.err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy");
+  *c->err_host = err;
+  return check_sticky(c);
+}
+
+void contact_clear_error(contact_ctx* c) {
+  if (c == nullptr) return;
+  cudaStreamSynchronize(c->stream);
+  cudaMemset(c->W.err, 0, sizeof(int));
+  *c->err_host = 0;
+  c->last_error = "no error";
+}
+
+const char* contact_last_error(contact_ctx* c) { return c ? c->last_error.c_str() : "null context"; }
+
+contact_status contact_stats(contact_ctx* c, int64_t* stats) {
+  if (c == nullptr || stats == nullptr) return CONTACT_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  int h[8];
+  unsigned long long u[4];
+  e = cudaMemcpy(h, c->W.counters, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(u, c->W.u64, sizeof(u), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy");
+  stats[0] = h[0];
+  stats[1] = static_cast<int64_t>(u[0]);
+  stats[2] = h[1];
+  stats[3] = h[5];
+  stats[4] = contact_kernels_per_step(c);
+  stats[5] = c->grid_narrow;
+  stats[6] = c->P.nbin[0];
+  stats[7] = c->last_replay ? 1 : 0;
+  stats[8] = static_cast<int64_t>(u[1]);
+  stats[9] = c->P.max_tiles;
+  return CONTACT_OK;
+}
+
+contact_status contact_particle_boxes(contact_ctx* c, int32_t* lo_hi) {
+  if (c == nullptr || lo_hi == nullptr) return CONTACT_EINVAL;
+  const cudaError_t e =
+      cudaMemcpyAsync(lo_hi, c->D.lohi, sizeof(int) * 6 * c->P.n, cudaMemcpyDeviceToDevice, c->stream);
+  return e == cudaSuccess ? CONTACT_OK : cuda_fail(c, e, "cudaMemcpyAsync");
+}
+
+contact_status contact_narrow_time(contact_ctx* c, float* ms) {
+  if (c == nullptr || ms == nullptr) return CONTACT_EINVAL;
+  if (!c->have_step) return fail(c, CONTACT_ESTATE, "contact_narrow_time: no step yet");
+  cudaError_t e = cudaEventSynchronize(c->ev_narrow[1]);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
+  e = cudaEventElapsedTime(ms, c->ev_narrow[0], c->ev_narrow[1]);
+  return e == cudaSuccess ? CONTACT_OK : cuda_fail(c, e, "cudaEventElapsedTime");
+}
+
+int32_t contact_kernels_per_step(const contact_ctx*) { return 7; }
+int32_t contact_kernels_per_backward(const contact_ctx*) { return 4; }
+
+contact_status contact_backward(contact_ctx* c, const double* grad_force, const double* grad_torque,
+                                double* grad_pos, double* grad_quat) {
+  if (c == nullptr) return CONTACT_EINVAL;
+  if (grad_force == nullptr || grad_torque == nullptr || grad_pos == nullptr || grad_quat == nullptr)
+    return fail(c, CONTACT_EINVAL, "contact_backward: null buffer");
+  if (!c->have_step) return fail(c, CONTACT_ESTATE, "contact_backward: no contact_step before");
+  if (c->P.smooth != 1) return fail(c, CONTACT_ESTATE, "contact_backward: needs the smoothed indicator");
+  const contact_status sticky = check_sticky(c);
+  if (sticky != CONTACT_OK) return sticky;
+  launch_adjoint(c->P, c->S, c->D, c->W, c->last_vel, grad_force, grad_torque, grad_pos, grad_quat,
+                 c->adj_scratch, c->grid_adjoint, c->stream);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+  return CONTACT_OK;
+}
+
+void contact_destroy(contact_ctx* c) {
+  if (c == nullptr) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  cudaDeviceSynchronize();
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (cudaEvent_t ev : c->ev_narrow)
+    if (ev) cudaEventDestroy(ev);
+  for (void* p : c->dev_allocs) cudaFree(p);
+  if (c->err_host) cudaFreeHost(c->err_host);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,436 @@
+// Adjoint of the contact step (smoothed indicator): gradient of
+//   L = sum_p (gF_p . F_p + gT_p . T_p)
+// with respect to positions and raw quaternions.
+//
+// Forward map per pair (lattice sums over the pair box, lattice units):
+//   S0 = sum W, S1 = sum W c, Sg = sum (mA grad phiA - mB grad phiB),
+//   W = H(phiA) H(phiB), H = S(t), t = clamp(1/2 - phi/w, 0, 1), m = t(1-t) H_other,
+//   V = dx^3 S0, x_c = (lo + S1/S0) dx, G = 1/2 dx^2 (6/w) Sg, n = G/|G|,
+//   d = -phiA(x*) - phiB(x*) at the deepest node x*,
+//   F = 4/(3 pi) E* sqrt(V d)(1 + c ddot_n) n  (Eq. contact_force_normal),
+//   T_A = (x_c - X_A) x (-F), T_B = (x_c - X_B') x F.
+// k_adj_pre: FP64 chain rule from (gF, gT) to seeds dL/dS0, dL/dS1, dL/dSg
+//   and the explicit pose terms (torque arms, damping, fallback normal).
+// k_adj_cells: persistent tile sweep (same tiles as the forward pass); per node
+//   dL/dphi and dL/d(grad phi) pulled back to the 12 pose directions of the
+//   pair (translation and infinitesimal world rotation of each particle):
+//     dphi/dX = -grad phi,  dphi/domega = grad phi x r,
+//     sphere: d(grad phi)/dX = -(I - g g^T)/|r|; faces: d(grad phi) = omega x grad phi.
+// k_adj_post: FP64 sum of tile partials, depth term at x*, lattice -> physical.
+// k_adj_scatter: per particle in the forward order; the rotation gradient tau
+//   becomes dL/dq = (2/|q|) (-v.tau, w tau + tau x v) for q/|q| = (w, v).
+#include <cfloat>
+
+#include "contact_dev.cuh"
+
+namespace gbc {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarps = 8;
+constexpr int kAdjPartial = 12;
+constexpr int kSeedFloats = 8;
+constexpr int kPairGrad = 16;
+
+struct AdjBufs {
+  float* partial;  // [max_tiles, 12]
+  float* seeds;    // [max_pairs, 8]
+  double* pgrad;   // [max_pairs, 16]
+};
+
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double c[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// ---------------------------------------------------------------- pair level
+__global__ void __launch_bounds__(128) k_adj_pre(Params P, Shapes S, Parts D, Lists W, AdjBufs B,
+                                                 const double* __restrict__ vel, const double* __restrict__ gF,
+                                                 const double* __restrict__ gT) {
+  const int np = min(W.counters[0], P.max_pairs);
+  if (blockIdx.x == 0 && threadIdx.x == 0) W.counters[6] = 0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+    const PairRec pr = W.pairs[p];
+    const double* tp = W.tape + static_cast<size_t>(p) * kTapeDoubles;
+    float* sd = B.seeds + static_cast<size_t>(p) * kSeedFloats;
+    double* pg = B.pgrad + static_cast<size_t>(p) * kPairGrad;
+    for (int k = 0; k < kSeedFloats; ++k) sd[k] = 0.f;
+    for (int k = 0; k < kPairGrad; ++k) pg[k] = 0.0;
+    const double S0 = tp[0];
+    const double fmag = tp[12];
+    if (!(S0 > 0.0)) continue;
+    const int i = pr.i, j = pr.j;
+    const double dx = P.dx;
+    double XA[3], XB[3], xc[3], n[3], F[3], rA[3], rB[3], gFi[3], gFj[3], gTi[3], gTj[3];
+    for (int k = 0; k < 3; ++k) {
+      XA[k] = D.X[3 * i + k];
+      XB[k] = D.X[3 * j + k] - pr.shift[k] * P.L[k];
+      xc[k] = tp[1 + k];
+      n[k] = tp[4 + k];
+      F[k] = fmag * n[k];
+      rA[k] = xc[k] - XA[k];
+      rB[k] = xc[k] - XB[k];
+      gFi[k] = gF[3 * i + k]; gFj[k] = gF[3 * j + k];
+      gTi[k] = gT[3 * i + k]; gTj[k] = gT[3 * j + k];
+    }
+    const double V = dx * dx * dx * S0, d = tp[7], gnorm = tp[8], estar = tp[10], damp = tp[11];
+    // dL/dF = Lambda, dL/dx_c, explicit dL/dX_A, dL/dX_B'
+    double c1[3], c2[3], Lam[3], gxc[3], gXA[3], gXB[3], t1[3], t2[3];
+    cross3(gTi, rA, c1);
+    cross3(gTj, rB, c2);
+    for (int k = 0; k < 3; ++k) Lam[k] = gFj[k] - gFi[k] - c1[k] + c2[k];
+    double dT[3] = {gTj[0] - gTi[0], gTj[1] - gTi[1], gTj[2] - gTi[2]};
+    cross3(F, dT, gxc);
+    cross3(F, gTi, t1);
+    cross3(gTj, F, t2);
+    for (int k = 0; k < 3; ++k) { gXA[k] = t1[k]; gXB[k] = t2[k]; }
+    const double Ln = Lam[0] * n[0] + Lam[1] * n[1] + Lam[2] * n[2];
+    double gn[3] = {fmag * Lam[0], fmag * Lam[1], fmag * Lam[2]};
+    double gV = 0.0, gd = 0.0;
+    if (fmag > 0.0) {
+      gV = Ln * fmag / (2.0 * V);
+      gd = Ln * fmag / (2.0 * d);
+      if (vel != nullptr && P.damping_c != 0.0 && damp > 0.0) {
+        const double* va = vel + 6 * i;
+        const double* vb = vel + 6 * j;
+        double wa[3], wb[3], uA[3], uB[3];
+        cross3(va + 3, rA, wa);
+        cross3(vb + 3, rB, wb);
+        for (int k = 0; k < 3; ++k) { uA[k] = va[k] + wa[k]; uB[k] = vb[k] + wb[k]; }
+        const double gdd = Ln * (fmag / damp) * P.damping_c;
+        double na[3], nb[3];
+        cross3(n, va + 3, na);
+        cross3(n, vb + 3, nb);
+        for (int k = 0; k < 3; ++k) {
+          gn[k] += gdd * (uA[k] - uB[k]);
+          gxc[k] += gdd * (na[k] - nb[k]);
+          gXA[k] -= gdd * na[k];
+          gXB[k] += gdd * nb[k];
+        }
+      }
+    }
+    // normal: n = G / |G| with G = kappa Sg, or the centre-line fallback
+    const double kappa = 0.5 * dx * dx * 6.0 / (P.wdx / dx);
+    const double gnn = gn[0] * n[0] + gn[1] * n[1] + gn[2] * n[2];
+    double sg[3] = {0.0, 0.0, 0.0};
+    if (tp[9] == 0.0) {
+      for (int k = 0; k < 3; ++k) sg[k] = kappa * (gn[k] - gnn * n[k]) / gnorm;
+    } else {
+      double dl = 0.0;
+      for (int k = 0; k < 3; ++k) dl += (XB[k] - XA[k]) * (XB[k] - XA[k]);
+      dl = sqrt(dl);
+      if (dl > 0.0)
+        for (int k = 0; k < 3; ++k) {
+          const double g = (gn[k] - gnn * n[k]) / dl;
+          gXB[k] += g;
+          gXA[k] -= g;
+        }
+    }
+    // x_c = (lo + S1/S0) dx ; V = dx^3 S0
+    double s0 = gV * dx * dx * dx;
+    double s1[3];
+    for (int k = 0; k < 3; ++k) {
+      s1[k] = gxc[k] * dx / S0;
+      s0 -= gxc[k] * (xc[k] - pr.lo[k] * dx) / S0;
+    }
+    sd[0] = static_cast<float>(s0);
+    for (int k = 0; k < 3; ++k) {
+      sd[1 + k] = static_cast<float>(s1[k]);
+      sd[4 + k] = static_cast<float>(sg[k]);
+    }
+    for (int k = 0; k < 3; ++k) { pg[k] = gXA[k]; pg[6 + k] = gXB[k]; }
+    pg[12] = gd;
+    (void)estar;
+  }
+}
+
+// ---------------------------------------------------------------- node level
+struct AdjGeom {
+  int type, nf;
+  float c[3];    // centre relative to the box origin (lattice units)
+  float rt[9];   // R^T (row k = body axis k in world)
+  float size[3];
+  const float4* sp;  // world planes (x, y, z, offset) in shared memory
+};
+
+__device__ __forceinline__ void adj_load(const Shapes& S, const Parts& D, int pid, const int* ci, const float* cf,
+                                         float4* sm, AdjGeom& g) {
+  const int lane = threadIdx.x & 31;
+  g.type = S.type[pid];
+  for (int k = 0; k < 3; ++k) {
+    g.c[k] = static_cast<float>(ci[k]) + cf[k];
+    g.size[k] = S.size_l[3 * pid + k];
+  }
+  for (int k = 0; k < 9; ++k) g.rt[k] = D.Rt[9 * pid + k];
+  g.nf = 0;
+  if (g.type == 2) {
+    const int f0 = S.face_off[pid];
+    g.nf = S.face_off[pid + 1] - f0;
+    if (lane < g.nf) sm[lane] = D.wplane[f0 + lane];
+    __syncwarp();
+  }
+  g.sp = sm;
+}
+
+// phi (lattice units, inflate included), unit world gradient, |r| (spheres)
+__device__ __forceinline__ float adj_eval(const AdjGeom& g, const float r[3], float gr[3], float* rn) {
+  if (g.type == 0) {
+    const float q = fmaf(r[0], r[0], fmaf(r[1], r[1], r[2] * r[2]));
+    const float nr = sqrtf(q);
+    const float inv = nr > 0.f ? 1.f / nr : 0.f;
+    for (int k = 0; k < 3; ++k) gr[k] = r[k] * inv;
+    *rn = nr;
+    return nr - g.size[0];
+  }
+  *rn = 0.f;
+  if (g.type == 1) {
+    float y[3], a[3];
+    for (int k = 0; k < 3; ++k) {
+      y[k] = fmaf(g.rt[3 * k], r[0], fmaf(g.rt[3 * k + 1], r[1], g.rt[3 * k + 2] * r[2]));
+      a[k] = fabsf(y[k]) - g.size[k];
+    }
+    int kk = (a[0] >= a[1] && a[0] >= a[2]) ? 0 : (a[1] >= a[2] ? 1 : 2);
+    const float sgn = y[kk] < 0.f ? -1.f : 1.f;
+    for (int k = 0; k < 3; ++k) gr[k] = sgn * g.rt[3 * kk + k];
+    return a[kk];
+  }
+  int kk = 0;
+  float best = -FLT_MAX;
+  for (int f = 0; f < g.nf; ++f) {
+    const float4 e = g.sp[f];
+    const float v = fmaf(e.x, r[0], fmaf(e.y, r[1], fmaf(e.z, r[2], -e.w)));
+    if (v > best) { best = v; kk = f; }
+  }
+  const float4 e = g.sp[kk];
+  gr[0] = e.x; gr[1] = e.y; gr[2] = e.z;
+  return best;
+}
+
+__device__ __forceinline__ void cross3f(const float a[3], const float b[3], float c[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, Parts D, Lists W, AdjBufs B) {
+  __shared__ float4 s_pl[kWarps][2][kMaxFaces];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int ntiles = W.counters[1];
+  const float inv_w = P.inv_w;
+  int t = 0;
+  if (lane == 0) t = atomicAdd(&W.counters[6], 1);
+  t = __shfl_sync(kFull, t, 0);
+  while (t < ntiles) {
+    int tn = 0;
+    if (lane == 0) tn = atomicAdd(&W.counters[6], 1);
+    const int p = W.tile_pair[t];
+    const PairRec pr = W.pairs[p];
+    const float* sd = B.seeds + static_cast<size_t>(p) * kSeedFloats;
+    const float s0 = sd[0], s1[3] = {sd[1], sd[2], sd[3]}, sg[3] = {sd[4], sd[5], sd[6]};
+    float acc[12];
+    for (int k = 0; k < 12; ++k) acc[k] = 0.f;
+    const bool active = (s0 != 0.f) || (s1[0] != 0.f) || (s1[1] != 0.f) || (s1[2] != 0.f) || (sg[0] != 0.f) ||
+                        (sg[1] != 0.f) || (sg[2] != 0.f);
+    if (active) {
+      AdjGeom A, Bg;
+      adj_load(S, D, pr.i, pr.ai, pr.af, s_pl[wid][0], A);
+      adj_load(S, D, pr.j, pr.bi, pr.bf, s_pl[wid][1], Bg);
+      const int ax0 = pr.axis, ax1 = (pr.axis + 1) % 3, ax2 = (pr.axis + 2) % 3;
+      const int du = pr.dim[ax0], dv = pr.dim[ax1];
+      const int it0 = (t - pr.tile0) * 32 * kTileItemsPerLane;
+      for (int s = 0; s < kTileItemsPerLane; ++s) {
+        const int it = it0 + s * 32 + lane;
+        if (it >= pr.nitems) continue;
+        const int line = it / pr.nseg, seg = it - line * pr.nseg;
+        int c[3];
+        c[ax1] = line % dv;
+        c[ax2] = line / dv;
+        const int u0 = seg * pr.seglen, u1 = min(u0 + pr.seglen, du);
+        for (int cu = u0; cu < u1; ++cu) {
+          c[ax0] = cu;
+          float ra[3], rb[3], ga[3], gb[3], na, nb;
+          for (int k = 0; k < 3; ++k) {
+            ra[k] = static_cast<float>(c[k] - pr.ai[k]) - pr.af[k];
+            rb[k] = static_cast<float>(c[k] - pr.bi[k]) - pr.bf[k];
+          }
+          const float fa = adj_eval(A, ra, ga, &na);
+          const float fb = adj_eval(Bg, rb, gb, &nb);
+          const float ta = fminf(fmaxf(fmaf(fa, -inv_w, 0.5f), 0.f), 1.f);
+          const float tb = fminf(fmaxf(fmaf(fb, -inv_w, 0.5f), 0.f), 1.f);
+          const bool ina = ta > 0.f && ta < 1.f, inb = tb > 0.f && tb < 1.f;
+          const float Ha = ta * ta * (3.f - 2.f * ta), Hb = tb * tb * (3.f - 2.f * tb);
+          const float ha = ta * (1.f - ta), hb = tb * (1.f - tb);
+          // derivatives with respect to phi (lattice units); zero outside the band
+          const float dHa = ina ? -6.f * ha * inv_w : 0.f, dHb = inb ? -6.f * hb * inv_w : 0.f;
+          const float dha = ina ? -(1.f - 2.f * ta) * inv_w : 0.f, dhb = inb ? -(1.f - 2.f * tb) * inv_w : 0.f;
+          if (Ha * Hb == 0.f && ha * Hb == 0.f && Ha * hb == 0.f && dHa * Hb == 0.f && Ha * dHb == 0.f) continue;
+          const float sw = fmaf(s1[0], static_cast<float>(c[0]),
+                                fmaf(s1[1], static_cast<float>(c[1]), fmaf(s1[2], static_cast<float>(c[2]), s0)));
+          const float gma = sg[0] * ga[0] + sg[1] * ga[1] + sg[2] * ga[2];
+          const float gmb = sg[0] * gb[0] + sg[1] * gb[1] + sg[2] * gb[2];
+          const float ka = sw * dHa * Hb + dha * Hb * gma - dHa * hb * gmb;
+          const float kb = sw * Ha * dHb + ha * dHb * gma - Ha * dhb * gmb;
+          float xa[3], xb[3];
+          cross3f(ga, ra, xa);
+          cross3f(gb, rb, xb);
+          for (int k = 0; k < 3; ++k) {
+            acc[k] -= ka * ga[k];
+            acc[3 + k] += ka * xa[k];
+            acc[6 + k] -= kb * gb[k];
+            acc[9 + k] += kb * xb[k];
+          }
+          const float wa = ha * Hb, wb = Ha * hb;
+          if (A.type == 0) {
+            if (na > 0.f)
+              for (int k = 0; k < 3; ++k) acc[k] -= wa * (sg[k] - gma * ga[k]) / na;
+          } else {
+            float cr[3];
+            cross3f(ga, sg, cr);
+            for (int k = 0; k < 3; ++k) acc[3 + k] += wa * cr[k];
+          }
+          if (Bg.type == 0) {
+            if (nb > 0.f)
+              for (int k = 0; k < 3; ++k) acc[6 + k] += wb * (sg[k] - gmb * gb[k]) / nb;
+          } else {
+            float cr[3];
+            cross3f(gb, sg, cr);
+            for (int k = 0; k < 3; ++k) acc[9 + k] -= wb * cr[k];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[k] += __shfl_xor_sync(kFull, acc[k], off);
+    if (lane < 12) {
+      float x = acc[0];
+#pragma unroll
+      for (int k = 1; k < 12; ++k) x = (lane == k) ? acc[k] : x;
+      B.partial[static_cast<size_t>(t) * kAdjPartial + lane] = x;
+    }
+    t = __shfl_sync(kFull, tn, 0);
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------- pair post
+__global__ void __launch_bounds__(128) k_adj_post(Params P, Shapes S, Parts D, Lists W, AdjBufs B) {
+  const int np = min(W.counters[0], P.max_pairs);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+    const PairRec pr = W.pairs[p];
+    const double* tp = W.tape + static_cast<size_t>(p) * kTapeDoubles;
+    double* pg = B.pgrad + static_cast<size_t>(p) * kPairGrad;
+    if (!(tp[0] > 0.0)) continue;
+    double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int t = pr.tile0; t < pr.tile0 + pr.ntiles; ++t) {
+      const float* q = B.partial + static_cast<size_t>(t) * kAdjPartial;
+      for (int k = 0; k < 12; ++k) acc[k] += static_cast<double>(q[k]);
+    }
+    const double dx = P.dx;
+    // lattice position -> physical position
+    for (int k = 0; k < 3; ++k) {
+      pg[k] += acc[k] / dx;
+      pg[3 + k] += acc[3 + k];
+      pg[6 + k] += acc[6 + k] / dx;
+      pg[9 + k] += acc[9 + k];
+    }
+    // depth term: d = -phiA(x*) - phiB(x*)
+    const double gd = pg[12];
+    if (gd != 0.0 && tp[7] > 0.0) {
+      const int i = pr.i, j = pr.j;
+      const int idx = min(max(static_cast<int>(tp[13]), 0), pr.dim[0] * pr.dim[1] * pr.dim[2] - 1);
+      const int c[3] = {idx % pr.dim[0], (idx / pr.dim[0]) % pr.dim[1], idx / (pr.dim[0] * pr.dim[1])};
+      const double x[3] = {(pr.lo[0] + c[0]) * dx, (pr.lo[1] + c[1]) * dx, (pr.lo[2] + c[2]) * dx};
+      double XA[3], XB[3], gA[3], gB[3];
+      for (int k = 0; k < 3; ++k) {
+        XA[k] = D.X[3 * i + k];
+        XB[k] = D.X[3 * j + k] - pr.shift[k] * P.L[k];
+      }
+      sdf64(S.type[i], S.param + 3 * i, S.planes + 4 * S.face_off[i], S.face_off[i + 1] - S.face_off[i], XA,
+            D.R + 9 * i, x, P.inflate, gA);
+      sdf64(S.type[j], S.param + 3 * j, S.planes + 4 * S.face_off[j], S.face_off[j + 1] - S.face_off[j], XB,
+            D.R + 9 * j, x, P.inflate, gB);
+      double rA[3], rB[3], cA[3], cB[3];
+      for (int k = 0; k < 3; ++k) { rA[k] = x[k] - XA[k]; rB[k] = x[k] - XB[k]; }
+      cross3(rA, gA, cA);
+      cross3(rB, gB, cB);
+      // d(-phi)/dX = grad phi ; d(-phi)/domega = r x grad phi (physical r: rotation is unitless)
+      for (int k = 0; k < 3; ++k) {
+        pg[k] += gd * gA[k];
+        pg[3 + k] += gd * cA[k];
+        pg[6 + k] += gd * gB[k];
+        pg[9 + k] += gd * cB[k];
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ int pair_index_adj(const Params& P, const Lists& W, int i, int p) {
+  const int* lst = W.up_list + static_cast<size_t>(i) * P.max_nbr;
+  int lo = 0, hi = W.up_count[i];
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (lst[mid] < p) lo = mid + 1; else hi = mid;
+  }
+  return W.row_off[i] + lo;
+}
+
+__global__ void __launch_bounds__(128) k_adj_scatter(Params P, Parts D, Lists W, AdjBufs B,
+                                                     double* __restrict__ gpos, double* __restrict__ gquat) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P.n) return;
+  const int np = min(W.counters[0], P.max_pairs);
+  double gx[3] = {0, 0, 0}, tau[3] = {0, 0, 0};
+  const int nd = W.dn_count[p];
+  for (int r = 0; r < nd; ++r) {
+    const int i = W.dn_list[static_cast<size_t>(p) * P.max_nbr + r];
+    const int q = pair_index_adj(P, W, i, p);
+    if (q >= np) continue;
+    const double* e = B.pgrad + static_cast<size_t>(q) * kPairGrad;
+    for (int k = 0; k < 3; ++k) { gx[k] += e[6 + k]; tau[k] += e[9 + k]; }
+  }
+  const int r0 = W.row_off[p], nu = W.up_count[p];
+  for (int r = 0; r < nu; ++r) {
+    const int q = r0 + r;
+    if (q >= np) break;
+    const double* e = B.pgrad + static_cast<size_t>(q) * kPairGrad;
+    for (int k = 0; k < 3; ++k) { gx[k] += e[k]; tau[k] += e[3 + k]; }
+  }
+  const double w = D.qhat[4 * p], v[3] = {D.qhat[4 * p + 1], D.qhat[4 * p + 2], D.qhat[4 * p + 3]};
+  const double s = 2.0 / D.qnorm[p];
+  double tv[3];
+  cross3(tau, v, tv);
+  for (int k = 0; k < 3; ++k) gpos[3 * p + k] = gx[k];
+  gquat[4 * p] = -s * (v[0] * tau[0] + v[1] * tau[1] + v[2] * tau[2]);
+  for (int k = 0; k < 3; ++k) gquat[4 * p + 1 + k] = s * (w * tau[k] + tv[k]);
+}
+
+}  // namespace
+
+size_t adjoint_scratch_doubles(int max_pairs, int max_tiles) {
+  return static_cast<size_t>(max_tiles) * kAdjPartial / 2 + static_cast<size_t>(max_pairs) * kSeedFloats / 2 +
+         static_cast<size_t>(max_pairs) * kPairGrad + 16;
+}
+
+void launch_adjoint(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel,
+                    const double* gF, const double* gT, double* gpos, double* gquat, double* scratch, int grid,
+                    cudaStream_t st) {
+  AdjBufs B;
+  B.partial = reinterpret_cast<float*>(scratch);
+  B.seeds = B.partial + static_cast<size_t>(P.max_tiles) * kAdjPartial;
+  B.pgrad = reinterpret_cast<double*>(B.seeds + static_cast<size_t>(P.max_pairs) * kSeedFloats + 8);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int need = (P.max_pairs + 127) / 128;
+  const int pgrid = need < 2 * sms ? (need > 0 ? need : 1) : 2 * sms;
+  k_adj_pre<<<pgrid, 128, 0, st>>>(P, S, D, W, B, vel, gF, gT);
+  k_adj_cells<<<grid, kWarps * 32, 0, st>>>(P, S, D, W, B);
+  k_adj_post<<<pgrid, 128, 0, st>>>(P, S, D, W, B);
+  k_adj_scatter<<<(P.n + 127) / 128, 128, 0, st>>>(P, D, W, B, gpos, gquat);
+}
+
+}  // namespace gbc

@@ -1,0 +1,360 @@
+// Pose -> AABB, cell-list broad phase and pair planning of the contact step.
+//
+// Paper (arXiv:2401.10878): Sec. 3.3.1 (a contact is swept over the region
+// where both particles may overlap), Sec. 3.3.2 (periodic boundaries: the
+// higher-ID particle is moved to the side of the lower-ID one), Sec. 4.1
+// (the neighbourhood radius is the largest circumradius).
+#include <cfloat>
+
+#include "contact_dev.cuh"
+
+namespace gbc {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int clamp_node(double v) {
+  // node indices stay far inside int range even for garbage input
+  v = fmin(fmax(v, -1.0e9), 1.0e9);
+  return static_cast<int>(v);
+}
+
+// ---------------------------------------------------------------------------
+// K1: per particle rotation, node ranges, FP32 sweep geometry and bin slot.
+__global__ void k_pose(Params P, Shapes S, Parts D, Lists W, const double* __restrict__ pos,
+                       const double* __restrict__ quat) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P.n) return;
+  double X[3], q[4];
+  bool bad = false;
+  for (int k = 0; k < 3; ++k) {
+    X[k] = pos[3 * p + k];
+    if (!(X[k] >= 0.0) || !(X[k] < P.L[k])) {  // also catches NaN
+      bad = true;
+      X[k] = 0.0;
+    }
+  }
+  for (int k = 0; k < 4; ++k) q[k] = quat[4 * p + k];
+  const double qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+  if (!(qq > 1e-24) || !(qq < 1e300)) {
+    bad = true;
+    q[0] = 1.0; q[1] = q[2] = q[3] = 0.0;
+  }
+  if (bad) set_error(W.err, kErrInval);
+  double qh[4], qn, R[9];
+  rotation_rn(q, qh, &qn, R);
+  for (int k = 0; k < 3; ++k) D.X[3 * p + k] = X[k];
+  for (int k = 0; k < 4; ++k) D.qhat[4 * p + k] = qh[k];
+  D.qnorm[p] = qn;
+  for (int k = 0; k < 9; ++k) D.R[9 * p + k] = R[k];
+
+  // AABB of the offset shape {phi <= delta} (explicit rounding: compared bit for bit)
+  const int type = S.type[p];
+  const double* prm = S.param + 3 * p;
+  double mn[3], mx[3];
+  if (type == 0) {
+    const double rad = dadd(prm[0], P.delta);
+    for (int k = 0; k < 3; ++k) { mn[k] = dsub(X[k], rad); mx[k] = dadd(X[k], rad); }
+  } else if (type == 1) {
+    const double e0 = dadd(prm[0], P.delta), e1 = dadd(prm[1], P.delta), e2 = dadd(prm[2], P.delta);
+    for (int k = 0; k < 3; ++k) {
+      const double ext = dadd(dadd(dmul(fabs(R[3 * k]), e0), dmul(fabs(R[3 * k + 1]), e1)),
+                              dmul(fabs(R[3 * k + 2]), e2));
+      mn[k] = dsub(X[k], ext);
+      mx[k] = dadd(X[k], ext);
+    }
+  } else {
+    double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (int v = S.vert_off[p]; v < S.vert_off[p + 1]; ++v) {
+      const double* w = S.verts + 3 * v;
+      for (int k = 0; k < 3; ++k) {
+        const double t = dadd(dadd(dmul(R[3 * k], w[0]), dmul(R[3 * k + 1], w[1])), dmul(R[3 * k + 2], w[2]));
+        lo[k] = fmin(lo[k], t);
+        hi[k] = fmax(hi[k], t);
+      }
+    }
+    for (int k = 0; k < 3; ++k) { mn[k] = dadd(X[k], lo[k]); mx[k] = dadd(X[k], hi[k]); }
+  }
+  int b[3];
+  for (int k = 0; k < 3; ++k) {
+    D.lohi[6 * p + k] = clamp_node(ceil(__ddiv_rn(mn[k], P.dx)));
+    D.lohi[6 * p + 3 + k] = clamp_node(floor(__ddiv_rn(mx[k], P.dx)));
+    b[k] = min(max(static_cast<int>(X[k] / P.binw[k]), 0), P.nbin[k] - 1);
+  }
+  // FP32 geometry of the node sweep (lattice units)
+  for (int k = 0; k < 3; ++k)
+    for (int j = 0; j < 3; ++j) D.Rt[9 * p + 3 * k + j] = static_cast<float>(R[3 * j + k]);
+  if (type == 2) {
+    for (int f = S.face_off[p]; f < S.face_off[p + 1]; ++f) {
+      const double* e = S.planes + 4 * f;
+      const double m0 = R[0] * e[0] + R[1] * e[1] + R[2] * e[2];
+      const double m1 = R[3] * e[0] + R[4] * e[1] + R[5] * e[2];
+      const double m2 = R[6] * e[0] + R[7] * e[1] + R[8] * e[2];
+      D.wplane[f] = make_float4(static_cast<float>(m0), static_cast<float>(m1), static_cast<float>(m2),
+                                static_cast<float>((e[3] + P.inflate) * P.inv_dx));
+    }
+  }
+  const int bin = b[0] + P.nbin[0] * (b[1] + P.nbin[1] * b[2]);
+  D.bin[p] = bin;
+  D.slot[p] = atomicAdd(&W.bin_count[bin], 1);
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide exclusive scan of n ints in global memory (one CTA of 1024
+// threads, each scanning a contiguous chunk).  Returns the total.
+__device__ long long block_scan_excl(int* data, int n, long long* s_tmp) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int chunk = (n + nt - 1) / nt;
+  const int b = min(n, tid * chunk), e = min(n, b + chunk);
+  long long s = 0;
+  for (int i = b; i < e; ++i) s += data[i];
+  s_tmp[tid] = s;
+  __syncthreads();
+  // Hillis-Steele over the 1024 chunk sums
+  for (int off = 1; off < nt; off <<= 1) {
+    const long long v = (tid >= off) ? s_tmp[tid - off] : 0;
+    __syncthreads();
+    s_tmp[tid] += v;
+    __syncthreads();
+  }
+  const long long total = s_tmp[nt - 1];
+  long long run = s_tmp[tid] - s;
+  for (int i = b; i < e; ++i) {
+    const int v = data[i];
+    data[i] = static_cast<int>(run);
+    run += v;
+  }
+  __syncthreads();
+  return total;
+}
+
+// K2: bin offsets and particle ids grouped by bin (single CTA).
+__global__ void __launch_bounds__(1024) k_bin_scatter(Params P, Parts D, Lists W) {
+  __shared__ long long s_tmp[1024];
+  const int nbins = P.nbin[0] * P.nbin[1] * P.nbin[2];
+  for (int i = threadIdx.x; i < nbins; i += blockDim.x) W.bin_start[i] = W.bin_count[i];
+  __syncthreads();
+  const long long total = block_scan_excl(W.bin_start, nbins, s_tmp);
+  if (threadIdx.x == 0) W.bin_start[nbins] = static_cast<int>(total);
+  __syncthreads();
+  for (int p = threadIdx.x; p < P.n; p += blockDim.x) W.bin_items[W.bin_start[D.bin[p]] + D.slot[p]] = p;
+}
+
+// Node box of pair (p, q) with q's image nearest p; returns false if empty.
+__device__ __forceinline__ bool pair_box(const Params& P, const Parts& D, int p, int q, int s[3], int lo[3],
+                                         int hi[3]) {
+  bool hit = true;
+  for (int k = 0; k < 3; ++k) {
+    s[k] = static_cast<int>(rint(__ddiv_rn(dsub(D.X[3 * q + k], D.X[3 * p + k]), P.L[k])));
+    lo[k] = max(D.lohi[6 * p + k], D.lohi[6 * q + k] - s[k] * P.ncell[k]);
+    hi[k] = min(D.lohi[6 * p + 3 + k], D.lohi[6 * q + 3 + k] - s[k] * P.ncell[k]);
+    hit = hit && lo[k] <= hi[k];
+  }
+  return hit;
+}
+
+// K3: one warp per particle scans the 27 neighbour bins; candidates are
+// compacted with warp ballots into partners above (j > p) and below (j < p),
+// then each list is sorted by rank.
+__global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
+  extern __shared__ int s_buf[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int p = blockIdx.x * (blockDim.x >> 5) + wid;
+  if (p >= P.n) return;
+  const int cap = P.max_nbr;
+  int* up = s_buf + wid * 2 * cap;
+  int* dn = up + cap;
+  const int bin = D.bin[p];
+  const int b[3] = {bin % P.nbin[0], (bin / P.nbin[0]) % P.nbin[1], bin / (P.nbin[0] * P.nbin[1])};
+  int nup = 0, ndn = 0;
+  int cnt[3], first[3];
+  for (int k = 0; k < 3; ++k) {
+    if (P.nbin[k] >= 3) { cnt[k] = 3; first[k] = -1; } else { cnt[k] = P.nbin[k]; first[k] = 0; }
+  }
+  for (int oz = 0; oz < cnt[2]; ++oz)
+    for (int oy = 0; oy < cnt[1]; ++oy)
+      for (int ox = 0; ox < cnt[0]; ++ox) {
+        int c[3] = {ox, oy, oz};
+        for (int k = 0; k < 3; ++k) {
+          c[k] = (P.nbin[k] >= 3) ? b[k] + c[k] + first[k] : c[k];
+          c[k] = (c[k] + P.nbin[k]) % P.nbin[k];
+        }
+        const int q = c[0] + P.nbin[0] * (c[1] + P.nbin[1] * c[2]);
+        const int beg = W.bin_start[q], end = W.bin_start[q + 1];
+        for (int base = beg; base < end; base += 32) {
+          const int idx = base + lane;
+          const int j = (idx < end) ? W.bin_items[idx] : -1;
+          bool hit = false;
+          if (j >= 0 && j != p) {
+            int s[3], lo[3], hi[3];
+            hit = pair_box(P, D, p, j, s, lo, hi);
+          }
+          const unsigned bu = __ballot_sync(kFull, hit && j > p);
+          const unsigned bd = __ballot_sync(kFull, hit && j < p);
+          const unsigned below = (1u << lane) - 1u;
+          if (hit && j > p) {
+            const int at = nup + __popc(bu & below);
+            if (at < cap) up[at] = j;
+          }
+          if (hit && j < p) {
+            const int at = ndn + __popc(bd & below);
+            if (at < cap) dn[at] = j;
+          }
+          nup += __popc(bu);
+          ndn += __popc(bd);
+        }
+      }
+  if (nup > cap || ndn > cap) {
+    if (lane == 0) set_error(W.err, kErrCapacity);
+    nup = min(nup, cap);
+    ndn = min(ndn, cap);
+  }
+  __syncwarp();
+  // rank sort (lists are short and keys unique)
+  for (int e = lane; e < nup; e += 32) {
+    const int v = up[e];
+    int r = 0;
+    for (int t = 0; t < nup; ++t) r += up[t] < v;
+    W.up_list[p * cap + r] = v;
+  }
+  for (int e = lane; e < ndn; e += 32) {
+    const int v = dn[e];
+    int r = 0;
+    for (int t = 0; t < ndn; ++t) r += dn[t] < v;
+    W.dn_list[p * cap + r] = v;
+  }
+  if (lane == 0) {
+    W.up_count[p] = nup;
+    W.dn_count[p] = ndn;
+  }
+}
+
+// K4: pair list in (i, j) order, pair boxes, sweep layout and node tiles
+// (single CTA; O(N + P + tiles)).
+__global__ void __launch_bounds__(1024) k_plan(Params P, Shapes S, Parts D, Lists W, int32_t* __restrict__ pair_ij,
+                                               int32_t* __restrict__ n_pairs_out) {
+  __shared__ long long s_tmp[1024];
+  __shared__ unsigned long long s_cells, s_ops;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int n = P.n;
+  for (int i = tid; i < n; i += nt) W.row_off[i] = W.up_count[i];
+  if (tid == 0) { s_cells = 0; s_ops = 0; }
+  __syncthreads();
+  const long long total_pairs = block_scan_excl(W.row_off, n, s_tmp);
+  if (tid == 0) {
+    W.row_off[n] = static_cast<int>(total_pairs);
+    W.counters[0] = static_cast<int>(total_pairs);
+    *n_pairs_out = static_cast<int>(total_pairs);
+    if (total_pairs > P.max_pairs) set_error(W.err, kErrCapacity);
+  }
+  const int np = static_cast<int>(min(total_pairs, static_cast<long long>(P.max_pairs)));
+  // build the pair records (one thread per particle row)
+  unsigned long long my_cells = 0, my_ops = 0;
+  for (int i = tid; i < n; i += nt) {
+    const int r0 = W.row_off[i], cnt = W.up_count[i];
+    for (int r = 0; r < cnt; ++r) {
+      const int pi = r0 + r;
+      if (pi >= np) break;
+      const int j = W.up_list[i * P.max_nbr + r];
+      PairRec pr;
+      int lo[3], hi[3];
+      pair_box(P, D, i, j, pr.shift, lo, hi);
+      pr.i = i;
+      pr.j = j;
+      int axis = 0;
+      for (int k = 0; k < 3; ++k) {
+        pr.lo[k] = lo[k];
+        pr.dim[k] = hi[k] - lo[k] + 1;
+        if (pr.dim[k] > pr.dim[axis]) axis = k;
+      }
+      pr.axis = axis;
+      const int du = pr.dim[axis];
+      pr.nseg = (du + kSegMax - 1) / kSegMax;
+      pr.seglen = (du + pr.nseg - 1) / pr.nseg;
+      const int lines = pr.dim[(axis + 1) % 3] * pr.dim[(axis + 2) % 3];
+      pr.nitems = lines * pr.nseg;
+      pr.ntiles = (pr.nitems + 32 * kTileItemsPerLane - 1) / (32 * kTileItemsPerLane);
+      pr.tile0 = pr.ntiles;  // scanned below
+      pr.kinds = W.kind[i] | (W.kind[j] << 8);
+      for (int k = 0; k < 3; ++k) {
+        const double a = D.X[3 * i + k] * P.inv_dx - lo[k];
+        const double bb = (D.X[3 * j + k] - pr.shift[k] * P.L[k]) * P.inv_dx - lo[k];
+        pr.ai[k] = static_cast<int>(rint(a));
+        pr.bi[k] = static_cast<int>(rint(bb));
+        pr.af[k] = static_cast<float>(a - pr.ai[k]);
+        pr.bf[k] = static_cast<float>(bb - pr.bi[k]);
+      }
+      const unsigned long long vol = static_cast<unsigned long long>(pr.dim[0]) * pr.dim[1] * pr.dim[2];
+      my_cells += vol;
+      my_ops += vol * static_cast<unsigned long long>(S.nomops[i] + S.nomops[j]);
+      W.pairs[pi] = pr;
+      pair_ij[2 * pi] = i;
+      pair_ij[2 * pi + 1] = j;
+    }
+  }
+  atomicAdd(&s_cells, my_cells);
+  atomicAdd(&s_ops, my_ops);
+  __syncthreads();
+  // tile offsets: scan of ntiles over the pairs (stored in tile0)
+  {
+    const int chunk = (np + nt - 1) / nt;
+    const int b = min(np, tid * chunk), e = min(np, b + chunk);
+    long long s = 0;
+    for (int q = b; q < e; ++q) s += W.pairs[q].ntiles;
+    s_tmp[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+      const long long v = (tid >= off) ? s_tmp[tid - off] : 0;
+      __syncthreads();
+      s_tmp[tid] += v;
+      __syncthreads();
+    }
+    const long long total_tiles = s_tmp[nt - 1];
+    long long run = s_tmp[tid] - s;
+    const bool overflow = total_tiles > P.max_tiles;
+    for (int q = b; q < e; ++q) {
+      W.pairs[q].tile0 = static_cast<int>(run);
+      const int nt_q = W.pairs[q].ntiles;
+      if (!overflow)
+        for (int t = 0; t < nt_q; ++t) W.tile_pair[run + t] = q;
+      run += nt_q;
+    }
+    if (tid == 0) {
+      if (overflow) set_error(W.err, kErrCapacity);
+      W.counters[1] = overflow ? 0 : static_cast<int>(total_tiles);
+      W.counters[2] = 0;
+      W.counters[5] = 0;
+      W.counters[3] = static_cast<int>(s_cells & 0x7fffffffULL);
+      W.counters[4] = static_cast<int>(s_cells >> 31);
+      W.u64[0] = s_cells;
+      W.u64[1] = s_ops;
+    }
+  }
+}
+
+}  // namespace
+
+void launch_pose(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* pos,
+                 const double* quat, cudaStream_t st) {
+  const int nb = (P.n + 127) / 128;
+  if (nb > 0) k_pose<<<nb, 128, 0, st>>>(P, S, D, W, pos, quat);
+}
+
+void launch_bin_scatter(const Params& P, const Parts& D, const Lists& W, cudaStream_t st) {
+  k_bin_scatter<<<1, 1024, 0, st>>>(P, D, W);
+}
+
+void launch_broad(const Params& P, const Parts& D, const Lists& W, cudaStream_t st) {
+  const int warps = 8;
+  const int nb = (P.n + warps - 1) / warps;
+  const size_t smem = static_cast<size_t>(warps) * 2 * P.max_nbr * sizeof(int);
+  if (nb > 0) k_broad<<<nb, warps * 32, smem, st>>>(P, D, W);
+}
+
+void launch_plan(const Params& P, const Shapes& S, const Parts& D, const Lists& W, int32_t* pair_ij, int32_t* n_pairs,
+                 cudaStream_t st) {
+  k_plan<<<1, 1024, 0, st>>>(P, S, D, W, pair_ij, n_pairs);
+}
+
+}  // namespace gbc

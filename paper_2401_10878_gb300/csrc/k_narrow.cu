@@ -1,0 +1,552 @@
+// Narrow phase of the contact step: every lattice node of every candidate
+// pair's box is tested against both particles' signed distance functions and
+// reduced to the overlap volume, its first moments, the band sum behind the
+// contact normal and the deepest node (Sec. 3.3.1 of arXiv:2401.10878: "iterate
+// over the entire overlap region to determine the overlap volume, the contact
+// point, the contact normal, the indentation depth").
+//
+// k_narrow32 (FP32 node tests, FP32 tile partials):
+//   * persistent grid, one warp per tile; warps pull tiles from a device queue
+//     (atomic counter, next tile fetched while the current one runs), so pairs
+//     with very uneven boxes balance across the GPU;
+//   * a pair's box is cut into node lines along its longest axis, lines into
+//     segments of <= 16 nodes; a tile is 32 lanes x 4 segments of one pair;
+//   * along a line only the sweep coordinate changes, so the per-line part of
+//     each face value is computed once and a node costs one FMA per face;
+//   * node coordinates relative to each particle are exact integers minus an
+//     FP32 remainder in [-1/2, 1/2] (no large-offset cancellation);
+//   * polytope faces (<= 20, padded) live in registers, the face table used
+//     for the normal's gradient lookups in shared memory;
+//   * the volume/moment/depth update and the normal-band update run only when
+//     some lane of the warp needs them (warp-uniform branches);
+//   * warp-shuffle reduction per tile; partials go to HBM and are summed per
+//     pair in FP64 by the finalize kernel in tile order (deterministic).
+// k_narrow64: all-FP64 comparison form, one thread block per pair.
+#include <cfloat>
+
+#include "contact_dev.cuh"
+
+namespace gbc {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarps = 8;  // warps per block of the persistent kernel
+
+struct Local {
+  int ax[3];  // local axes: u = sweep axis, v, w
+};
+
+// ---------------------------------------------------------------- evaluators
+// Each evaluator holds one particle's geometry for the current tile, in
+// lattice units, relative to the pair box origin.
+
+struct SphereEval {
+  int iu, iv, iw;
+  float fu, fv, fw, rad;
+  float cnt_u, rv, rw, rho2, ru, q;
+  float gu, gv, gw, gl;
+  __device__ void load(const Shapes& S, const Parts&, int p, const int* ci, const float* cf, const Local& L,
+                       float4*) {
+    iu = ci[L.ax[0]]; iv = ci[L.ax[1]]; iw = ci[L.ax[2]];
+    fu = cf[L.ax[0]]; fv = cf[L.ax[1]]; fw = cf[L.ax[2]];
+    rad = S.size_l[3 * p];
+    gu = gv = gw = 0.f;
+  }
+  __device__ __forceinline__ void begin_line(int cv, int cw, int u0) {
+    rv = static_cast<float>(cv - iv) - fv;
+    rw = static_cast<float>(cw - iw) - fw;
+    rho2 = fmaf(rv, rv, rw * rw);
+    gl = 0.f;
+    cnt_u = static_cast<float>(u0 - iu);
+  }
+  __device__ __forceinline__ float phi() {
+    ru = cnt_u - fu;
+    cnt_u += 1.f;
+    q = fmaf(ru, ru, rho2);
+    return sqrtf(q) - rad;
+  }
+  __device__ __forceinline__ void grad(float m) {
+    const float mi = m * (q > 0.f ? rsqrtf(q) : 0.f);
+    gu = fmaf(mi, ru, gu);
+    gl += mi;
+  }
+  __device__ __forceinline__ void end_line() {
+    gv = fmaf(gl, rv, gv);
+    gw = fmaf(gl, rw, gw);
+  }
+  __device__ void world(float* g, const Local& L) const {
+    g[L.ax[0]] = gu; g[L.ax[1]] = gv; g[L.ax[2]] = gw;
+  }
+};
+
+struct CuboidEval {
+  int iu, iv, iw;
+  float fu, fv, fw;
+  float tu[3], tv[3], tw[3], h[3];
+  float cnt_u, p[3], y[3], a[3];
+  float gb[3];
+  __device__ void load(const Shapes& S, const Parts& D, int pid, const int* ci, const float* cf,
+                       const Local& L, float4*) {
+    iu = ci[L.ax[0]]; iv = ci[L.ax[1]]; iw = ci[L.ax[2]];
+    fu = cf[L.ax[0]]; fv = cf[L.ax[1]]; fw = cf[L.ax[2]];
+    const float* rt = D.Rt + 9 * pid;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      tu[k] = rt[3 * k + L.ax[0]];
+      tv[k] = rt[3 * k + L.ax[1]];
+      tw[k] = rt[3 * k + L.ax[2]];
+      h[k] = S.size_l[3 * pid + k];
+      gb[k] = 0.f;
+    }
+  }
+  __device__ __forceinline__ void begin_line(int cv, int cw, int u0) {
+    const float rv = static_cast<float>(cv - iv) - fv;
+    const float rw = static_cast<float>(cw - iw) - fw;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) p[k] = fmaf(tv[k], rv, tw[k] * rw);
+    cnt_u = static_cast<float>(u0 - iu);
+  }
+  __device__ __forceinline__ float phi() {
+    const float ru = cnt_u - fu;
+    cnt_u += 1.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      y[k] = fmaf(tu[k], ru, p[k]);
+      a[k] = fabsf(y[k]) - h[k];
+    }
+    return fmaxf(a[0], fmaxf(a[1], a[2]));
+  }
+  __device__ __forceinline__ void grad(float m) {
+    // active face: first maximal axis; gradient sign(y_k) e_k (body frame)
+    const bool s0 = a[0] >= a[1] && a[0] >= a[2];
+    const bool s1 = !s0 && a[1] >= a[2];
+    gb[0] += s0 ? copysignf(m, y[0]) : 0.f;
+    gb[1] += s1 ? copysignf(m, y[1]) : 0.f;
+    gb[2] += (!s0 && !s1) ? copysignf(m, y[2]) : 0.f;
+  }
+  __device__ __forceinline__ void end_line() {}
+  __device__ void world(float* g, const Local& L) const {
+    g[L.ax[0]] = tu[0] * gb[0] + tu[1] * gb[1] + tu[2] * gb[2];
+    g[L.ax[1]] = tv[0] * gb[0] + tv[1] * gb[1] + tv[2] * gb[2];
+    g[L.ax[2]] = tw[0] * gb[0] + tw[1] * gb[1] + tw[2] * gb[2];
+  }
+};
+
+// Stage a polytope's world planes in local axes (u, v, w, offset) into shared
+// memory; faces beyond nf are padded so that they never win the maximum.
+__device__ __forceinline__ int stage_planes(const Shapes& S, const Parts& D, int pid, const Local& L,
+                                            float4* sm, int npad) {
+  const int lane = threadIdx.x & 31;
+  const int f0 = S.face_off[pid];
+  const int nf = S.face_off[pid + 1] - f0;
+  if (lane < npad) {
+    float4 e = make_float4(0.f, 0.f, 0.f, 1e30f);
+    if (lane < nf) {
+      const float4 w = D.wplane[f0 + lane];
+      const float c[3] = {w.x, w.y, w.z};
+      e = make_float4(c[L.ax[0]], c[L.ax[1]], c[L.ax[2]], w.w);
+    }
+    sm[lane] = e;
+  }
+  __syncwarp();
+  return nf;
+}
+
+template <int NF>
+struct PolyEval {
+  int iu, iv, iw;
+  float fu, fv, fw;
+  const float4* sp;
+  float mu[NF], p[NF];
+  float cnt_u, ru;
+  float gu, gv, gw;
+  __device__ void load(const Shapes& S, const Parts& D, int pid, const int* ci, const float* cf,
+                       const Local& L, float4* sm) {
+    iu = ci[L.ax[0]]; iv = ci[L.ax[1]]; iw = ci[L.ax[2]];
+    fu = cf[L.ax[0]]; fv = cf[L.ax[1]]; fw = cf[L.ax[2]];
+    stage_planes(S, D, pid, L, sm, NF);
+    sp = sm;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) mu[f] = sm[f].x;
+    gu = gv = gw = 0.f;
+  }
+  __device__ __forceinline__ void begin_line(int cv, int cw, int u0) {
+    const float rv = static_cast<float>(cv - iv) - fv;
+    const float rw = static_cast<float>(cw - iw) - fw;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const float4 e = sp[f];
+      p[f] = fmaf(e.y, rv, fmaf(e.z, rw, -e.w));
+    }
+    cnt_u = static_cast<float>(u0 - iu);
+  }
+  __device__ __forceinline__ float phi() {
+    ru = cnt_u - fu;
+    cnt_u += 1.f;
+    float best = fmaf(mu[0], ru, p[0]);
+#pragma unroll
+    for (int f = 1; f < NF; ++f) best = fmaxf(best, fmaf(mu[f], ru, p[f]));
+    return best;
+  }
+  __device__ __forceinline__ void grad(float m) {
+    int k = 0;
+    float best = fmaf(mu[0], ru, p[0]);
+#pragma unroll
+    for (int f = 1; f < NF; ++f) {
+      const float v = fmaf(mu[f], ru, p[f]);
+      if (v > best) { best = v; k = f; }
+    }
+    const float4 e = sp[k];
+    gu = fmaf(m, e.x, gu);
+    gv = fmaf(m, e.y, gv);
+    gw = fmaf(m, e.z, gw);
+  }
+  __device__ __forceinline__ void end_line() {}
+  __device__ void world(float* g, const Local& L) const {
+    g[L.ax[0]] = gu; g[L.ax[1]] = gv; g[L.ax[2]] = gw;
+  }
+};
+
+// Polytopes with more than kRegFaces faces: planes read from shared memory.
+struct PolyGEval {
+  int iu, iv, iw, nf;
+  float fu, fv, fw;
+  const float4* sp;
+  float cnt_u, ru, rv, rw;
+  float gu, gv, gw;
+  __device__ void load(const Shapes& S, const Parts& D, int pid, const int* ci, const float* cf,
+                       const Local& L, float4* sm) {
+    iu = ci[L.ax[0]]; iv = ci[L.ax[1]]; iw = ci[L.ax[2]];
+    fu = cf[L.ax[0]]; fv = cf[L.ax[1]]; fw = cf[L.ax[2]];
+    nf = stage_planes(S, D, pid, L, sm, kMaxFaces);
+    sp = sm;
+    gu = gv = gw = 0.f;
+  }
+  __device__ __forceinline__ void begin_line(int cv, int cw, int u0) {
+    rv = static_cast<float>(cv - iv) - fv;
+    rw = static_cast<float>(cw - iw) - fw;
+    cnt_u = static_cast<float>(u0 - iu);
+  }
+  __device__ __forceinline__ float value(int f) const {
+    const float4 e = sp[f];
+    return fmaf(e.x, ru, fmaf(e.y, rv, fmaf(e.z, rw, -e.w)));
+  }
+  __device__ __forceinline__ float phi() {
+    ru = cnt_u - fu;
+    cnt_u += 1.f;
+    float best = value(0);
+    for (int f = 1; f < nf; ++f) best = fmaxf(best, value(f));
+    return best;
+  }
+  __device__ __forceinline__ void grad(float m) {
+    int k = 0;
+    float best = value(0);
+    for (int f = 1; f < nf; ++f) {
+      const float v = value(f);
+      if (v > best) { best = v; k = f; }
+    }
+    const float4 e = sp[k];
+    gu = fmaf(m, e.x, gu);
+    gv = fmaf(m, e.y, gv);
+    gw = fmaf(m, e.z, gw);
+  }
+  __device__ __forceinline__ void end_line() {}
+  __device__ void world(float* g, const Local& L) const {
+    g[L.ax[0]] = gu; g[L.ax[1]] = gv; g[L.ax[2]] = gw;
+  }
+};
+
+// ---------------------------------------------------------------- tile sweep
+// out[0] = sum W, out[1..3] = sum W c (box axes), out[4..6] = sum (mA gradA -
+// mB gradB) (world), out[7] = deepest -phiA-phiB over W > 0, out[8] = its
+// node index (x fastest) as int bits.
+template <bool SMOOTH, class EA, class EB>
+__device__ __forceinline__ void sweep_tile(const Params& P, const Shapes& S, const Parts& D, const PairRec& pr,
+                                           int pa, const int* cia, const float* cfa, int pb, const int* cib,
+                                           const float* cfb, int tl, float4* smA, float4* smB, float* out) {
+  const int lane = threadIdx.x & 31;
+  Local L;
+  L.ax[0] = pr.axis;
+  L.ax[1] = (pr.axis + 1) % 3;
+  L.ax[2] = (pr.axis + 2) % 3;
+  EA A;
+  EB B;
+  A.load(S, D, pa, cia, cfa, L, smA);
+  B.load(S, D, pb, cib, cfb, L, smB);
+  const int du = pr.dim[L.ax[0]], dv = pr.dim[L.ax[1]];
+  const int nseg = pr.nseg, seglen = pr.seglen;
+  const float inv_w = P.inv_w;
+  float cnt = 0.f, mu = 0.f, mv = 0.f, mw = 0.f, bestf = -FLT_MAX;
+  int bestidx = 0x7fffffff;
+  const int it0 = tl * 32 * kTileItemsPerLane;
+  for (int s = 0; s < kTileItemsPerLane; ++s) {
+    const int itb = it0 + s * 32;
+    if (itb >= pr.nitems) break;
+    const int it = itb + lane;
+    const bool valid = it < pr.nitems;
+    const int line = it / nseg;
+    const int seg = it - line * nseg;
+    const int cv = line % dv, cw = line / dv;
+    const int u0 = seg * seglen;
+    const int u1 = valid ? min(u0 + seglen, du) : u0;
+    A.begin_line(cv, cw, u0);
+    B.begin_line(cv, cw, u0);
+    float cl = 0.f, ml = 0.f, bfl = -FLT_MAX, cuf = static_cast<float>(u0);
+    int bul = 0;
+    for (int k = 0; k < seglen; ++k) {
+      const bool act = (u0 + k) < u1;
+      const float fa = A.phi();
+      const float fb = B.phi();
+      const float ta = __saturatef(fmaf(fa, -inv_w, 0.5f));
+      const float tb = __saturatef(fmaf(fb, -inv_w, 0.5f));
+      float w, ma, mb;
+      if (SMOOTH) {
+        const float ha = ta * ta * fmaf(-2.f, ta, 3.f);
+        const float hb = tb * tb * fmaf(-2.f, tb, 3.f);
+        w = act ? ha * hb : 0.f;
+        ma = act ? fmaf(-ta, ta, ta) * hb : 0.f;
+        mb = act ? ha * fmaf(-tb, tb, tb) : 0.f;
+      } else {
+        const bool ina = fa <= 0.f, inb = fb <= 0.f;
+        w = (act && ina && inb) ? 1.f : 0.f;
+        ma = (act && inb) ? fmaf(-ta, ta, ta) : 0.f;
+        mb = (act && ina) ? fmaf(-tb, tb, tb) : 0.f;
+      }
+      if (__any_sync(kFull, w > 0.f)) {
+        cl += w;
+        ml = fmaf(w, cuf, ml);
+        const float f = -(fa + fb);
+        if (w > 0.f && f > bfl) {
+          bfl = f;
+          bul = u0 + k;
+        }
+      }
+      if (__any_sync(kFull, (ma != 0.f) || (mb != 0.f))) {
+        A.grad(ma);
+        B.grad(mb);
+      }
+      cuf += 1.f;
+    }
+    A.end_line();
+    B.end_line();
+    cnt += cl;
+    mu += ml;
+    mv = fmaf(cl, static_cast<float>(cv), mv);
+    mw = fmaf(cl, static_cast<float>(cw), mw);
+    if (bfl > -FLT_MAX) {
+      int c[3];
+      c[L.ax[0]] = bul;
+      c[L.ax[1]] = cv;
+      c[L.ax[2]] = cw;
+      const int idx = c[0] + pr.dim[0] * (c[1] + pr.dim[1] * c[2]);
+      if (bfl > bestf || (bfl == bestf && idx < bestidx)) {
+        bestf = bfl;
+        bestidx = idx;
+      }
+    }
+  }
+  float ga[3], gb[3], m[3];
+  A.world(ga, L);
+  B.world(gb, L);
+  m[L.ax[0]] = mu;
+  m[L.ax[1]] = mv;
+  m[L.ax[2]] = mw;
+  out[0] = cnt;
+  out[1] = m[0]; out[2] = m[1]; out[3] = m[2];
+  out[4] = ga[0] - gb[0]; out[5] = ga[1] - gb[1]; out[6] = ga[2] - gb[2];
+  out[7] = bestf;
+  out[8] = __int_as_float(bestidx);
+}
+
+__device__ __forceinline__ void warp_reduce_partials(float* v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) v[k] += __shfl_xor_sync(kFull, v[k], off);
+    const float of = __shfl_xor_sync(kFull, v[7], off);
+    const int oi = __shfl_xor_sync(kFull, __float_as_int(v[8]), off);
+    const int mi = __float_as_int(v[8]);
+    if (of > v[7] || (of == v[7] && oi < mi)) {
+      v[7] = of;
+      v[8] = __int_as_float(oi);
+    }
+  }
+}
+
+template <bool SMOOTH>
+__device__ __forceinline__ void dispatch(const Params& P, const Shapes& S, const Parts& D, const PairRec& pr,
+                                         int tl, float4* smA, float4* smB, float* out) {
+  int ka = pr.kinds & 0xff, kb = pr.kinds >> 8;
+  int pa = pr.i, pb = pr.j;
+  const int *cia = pr.ai, *cib = pr.bi;
+  const float *cfa = pr.af, *cfb = pr.bf;
+  const bool swap = ka > kb;
+  if (swap) {
+    const int t = ka; ka = kb; kb = t;
+    pa = pr.j; pb = pr.i;
+    cia = pr.bi; cib = pr.ai;
+    cfa = pr.bf; cfb = pr.af;
+  }
+#define GBC_CASE(KA, KB, TA, TB)                                                                  \
+  case (KA) * 4 + (KB):                                                                          \
+    sweep_tile<SMOOTH, TA, TB>(P, S, D, pr, pa, cia, cfa, pb, cib, cfb, tl, smA, smB, out);      \
+    break;
+  switch (ka * 4 + kb) {
+    GBC_CASE(0, 0, SphereEval, SphereEval)
+    GBC_CASE(0, 1, SphereEval, CuboidEval)
+    GBC_CASE(0, 2, SphereEval, PolyEval<kRegFaces>)
+    GBC_CASE(0, 3, SphereEval, PolyGEval)
+    GBC_CASE(1, 1, CuboidEval, CuboidEval)
+    GBC_CASE(1, 2, CuboidEval, PolyEval<kRegFaces>)
+    GBC_CASE(1, 3, CuboidEval, PolyGEval)
+    GBC_CASE(2, 2, PolyEval<kRegFaces>, PolyEval<kRegFaces>)
+    GBC_CASE(2, 3, PolyEval<kRegFaces>, PolyGEval)
+    GBC_CASE(3, 3, PolyGEval, PolyGEval)
+    default:
+      break;
+  }
+#undef GBC_CASE
+  if (swap) {
+    out[4] = -out[4]; out[5] = -out[5]; out[6] = -out[6];
+  }
+}
+
+template <bool SMOOTH>
+__global__ void __launch_bounds__(kWarps * 32, 2) k_narrow32(Params P, Shapes S, Parts D, Lists W) {
+  __shared__ float4 s_planes[kWarps][2][kMaxFaces];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int ntiles = W.counters[1];
+  int t = 0;
+  if (lane == 0) t = atomicAdd(&W.counters[2], 1);
+  t = __shfl_sync(kFull, t, 0);
+  while (t < ntiles) {
+    int tn = 0;
+    if (lane == 0) tn = atomicAdd(&W.counters[2], 1);  // next tile, fetched ahead
+    const int p = W.tile_pair[t];
+    const PairRec pr = W.pairs[p];
+    float v[9];
+    dispatch<SMOOTH>(P, S, D, pr, t - pr.tile0, s_planes[wid][0], s_planes[wid][1], v);
+    warp_reduce_partials(v);
+    if (lane < 9) {
+      float x = v[0];
+#pragma unroll
+      for (int k = 1; k < 9; ++k) x = (lane == k) ? v[k] : x;
+      W.partial[static_cast<size_t>(t) * kPartialFloats + lane] = x;
+    }
+    t = __shfl_sync(kFull, tn, 0);
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------- FP64 form
+template <bool SMOOTH>
+__global__ void __launch_bounds__(256) k_narrow64(Params P, Shapes S, Parts D, Lists W) {
+  __shared__ double s_red[8][8];
+  __shared__ double s_bf[8];
+  __shared__ int s_bi[8];
+  const int np = min(W.counters[0], P.max_pairs);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int p = blockIdx.x; p < np; p += gridDim.x) {
+    const PairRec pr = W.pairs[p];
+    const int i = pr.i, j = pr.j;
+    double XA[3], XB[3], RA[9], RB[9];
+    for (int k = 0; k < 3; ++k) {
+      XA[k] = D.X[3 * i + k];
+      XB[k] = D.X[3 * j + k] - pr.shift[k] * P.L[k];
+    }
+    for (int k = 0; k < 9; ++k) { RA[k] = D.R[9 * i + k]; RB[k] = D.R[9 * j + k]; }
+    const int ta = S.type[i], tb = S.type[j];
+    const double* pla = S.planes + 4 * S.face_off[i];
+    const double* plb = S.planes + 4 * S.face_off[j];
+    const int nfa = S.face_off[i + 1] - S.face_off[i], nfb = S.face_off[j + 1] - S.face_off[j];
+    const int vol = pr.dim[0] * pr.dim[1] * pr.dim[2];
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    double bf = -DBL_MAX;
+    int bi = 0x7fffffff;
+    for (int c = threadIdx.x; c < vol; c += blockDim.x) {
+      const int cx = c % pr.dim[0], cy = (c / pr.dim[0]) % pr.dim[1], cz = c / (pr.dim[0] * pr.dim[1]);
+      const double x[3] = {(pr.lo[0] + cx) * P.dx, (pr.lo[1] + cy) * P.dx, (pr.lo[2] + cz) * P.dx};
+      double gA[3], gB[3];
+      const double fa = sdf64(ta, S.param + 3 * i, pla, nfa, XA, RA, x, P.inflate, gA);
+      const double fb = sdf64(tb, S.param + 3 * j, plb, nfb, XB, RB, x, P.inflate, gB);
+      const double tA = fmin(fmax(0.5 - fa / P.wdx, 0.0), 1.0);
+      const double tB = fmin(fmax(0.5 - fb / P.wdx, 0.0), 1.0);
+      double hA, hB;
+      if (SMOOTH) {
+        hA = tA * tA * (3.0 - 2.0 * tA);
+        hB = tB * tB * (3.0 - 2.0 * tB);
+      } else {
+        hA = fa <= 0.0 ? 1.0 : 0.0;
+        hB = fb <= 0.0 ? 1.0 : 0.0;
+      }
+      const double w = hA * hB;
+      const double ma = tA * (1.0 - tA) * hB, mb = hA * tB * (1.0 - tB);
+      acc[0] += w;
+      acc[1] += w * cx; acc[2] += w * cy; acc[3] += w * cz;
+      for (int k = 0; k < 3; ++k) acc[4 + k] += ma * gA[k] - mb * gB[k];
+      if (w > 0.0) {
+        const double f = -(fa + fb) * P.inv_dx;
+        if (f > bf || (f == bf && c < bi)) { bf = f; bi = c; }
+      }
+    }
+    // block reduction
+    for (int off = 16; off > 0; off >>= 1) {
+      for (int k = 0; k < 7; ++k) acc[k] += __shfl_xor_sync(kFull, acc[k], off);
+      const double of = __shfl_xor_sync(kFull, bf, off);
+      const int oi = __shfl_xor_sync(kFull, bi, off);
+      if (of > bf || (of == bf && oi < bi)) { bf = of; bi = oi; }
+    }
+    if (lane == 0) {
+      for (int k = 0; k < 7; ++k) s_red[wid][k] = acc[k];
+      s_bf[wid] = bf;
+      s_bi[wid] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot[7] = {0, 0, 0, 0, 0, 0, 0};
+      double b = -DBL_MAX;
+      int bidx = 0x7fffffff;
+      for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) {
+        for (int k = 0; k < 7; ++k) tot[k] += s_red[w][k];
+        if (s_bf[w] > b || (s_bf[w] == b && s_bi[w] < bidx)) { b = s_bf[w]; bidx = s_bi[w]; }
+      }
+      double* o = W.sums + static_cast<size_t>(p) * kSumDoubles;
+      for (int k = 0; k < 7; ++k) o[k] = tot[k];
+      o[7] = b;
+      o[8] = static_cast<double>(bidx);
+      o[9] = 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+int narrow_grid(const Params& P) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (P.precision == 1) return sms * 4;
+  if (P.smooth)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_narrow32<true>, kWarps * 32, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_narrow32<false>, kWarps * 32, 0);
+  return sms * (per_sm > 0 ? per_sm : 1);
+}
+
+void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists& W, int grid, cudaStream_t st) {
+  if (P.precision == 1) {
+    if (P.smooth)
+      k_narrow64<true><<<grid, 256, 0, st>>>(P, S, D, W);
+    else
+      k_narrow64<false><<<grid, 256, 0, st>>>(P, S, D, W);
+    return;
+  }
+  if (P.smooth)
+    k_narrow32<true><<<grid, kWarps * 32, 0, st>>>(P, S, D, W);
+  else
+    k_narrow32<false><<<grid, kWarps * 32, 0, st>>>(P, S, D, W);
+}
+
+}  // namespace gbc

@@ -1,0 +1,199 @@
+"""CUDA contact step vs the FP64 oracle, element by element (needs a GB300).
+
+Workloads: the 27-particle mixed grid (FP64 on both sides), the 400-cube
+settling box, the 1934-particle mixed-shape box at full size, the 1934-cube
+box in smoothed mode, the resolution sweep; plus edge cases (no pairs, one
+pair, periodic corners, > 20-face polytopes, inflation, damping, capacity and
+input errors, graph replay).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_10878_gb300 import workloads as W
+from tests.helpers import cube_planes, state
+from tests.parity import compare, gpu_step
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def model_for(st, **kw):
+    from paper_2401_10878_gb300.contact import Contact
+    return Contact.from_state(st, **kw)
+
+
+def run_parity(st, precision=0, **kw):
+    m = model_for(st, precision=precision, **kw)
+    g = gpu_step(m, st)
+    r = oracle.contact_step(st)
+    rep = compare(st, g, r, fp64=precision == 1, smooth=st.indicator == 1)
+    boxes = m.particle_boxes().cpu().numpy()
+    assert np.array_equal(boxes, oracle.aabb(st)), "particle node ranges differ"
+    m.close()
+    return rep
+
+
+@pytest.fixture(scope="module")
+def states():
+    return {
+        "c1": W.mixed_grid_27(),
+        "c2": W.settling_cubes(),
+        "c3": W.mixed_settling(),
+        "c4": W.settling_cubes_dense(),
+    }
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_mixed27_grid(states, precision):
+    rep = run_parity(states["c1"], precision)
+    print("mixed27", precision, rep)
+    assert rep.pairs > 40
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cubes400_settling(states, precision):
+    print("cubes400", precision, run_parity(states["c2"], precision))
+
+
+def test_mixed1934_full_size(states):
+    rep = run_parity(states["c3"], 0)
+    print("mixed1934", rep)
+    assert rep.flagged <= 0.01 * rep.pairs
+
+
+def test_mixed1934_fp64_form(states):
+    print("mixed1934 fp64", run_parity(states["c3"], 1))
+
+
+def test_cubes1934_sharp_and_smooth(states):
+    st = states["c4"]
+    sharp = W.State(**{**st.__dict__, "indicator": 0})
+    print("cubes1934 sharp", run_parity(sharp, 0))
+    print("cubes1934 smooth", run_parity(st, 0))
+
+
+@pytest.mark.parametrize("edge", [8, 12, 16, 24])
+def test_resolution_sweep_and_exact_box_volume(edge):
+    st = W.resolution_sweep(edge)
+    print("sweep", edge, run_parity(st, 0))
+    m = model_for(st)
+    g = gpu_step(m, st)
+    # face-aligned pairs (both axis-aligned, faces on half-integer nodes): exact box overlap
+    al = st.info["aligned"]
+    ij = g["pair_ij"]
+    both = al[ij[:, 0]] & al[ij[:, 1]]
+    assert both.sum() > 10
+    h = st.shape_param[0, 0]
+    for p in np.nonzero(both)[0]:
+        i, j = ij[p]
+        d = W.min_image(st.pos[j] - st.pos[i], st.box)
+        ov = np.clip(2 * h - np.abs(d), 0, None)
+        assert g["pair_out"][p, 0] == np.prod(ov)
+    m.close()
+
+
+def test_smoothed_fp64_form(states):
+    st = W.mixed_grid_27()
+    st.indicator = 1
+    print("mixed27 smooth fp64", run_parity(st, 1))
+    print("mixed27 smooth fp32", run_parity(st, 0))
+
+
+# ----------------------------------------------------------------- edge cases
+
+def test_no_pairs_and_single_pair():
+    far = state([0, 1], [[5, 0, 0], [4, 4, 4]], [[10, 10, 10], [40, 40, 40]])
+    m = model_for(far)
+    g = gpu_step(m, far)
+    assert g["n_pairs"] == 0 and np.all(g["force"] == 0) and np.all(g["torque"] == 0)
+    m.close()
+    one = state([0, 1], [[6, 0, 0], [4, 4, 4]], [[20.3, 20.1, 20.7], [29.0, 21.0, 19.5]],
+                quat=[[1, 0, 0, 0], list(W.random_quaternions(np.random.default_rng(1), 1)[0])])
+    print("single", run_parity(one, 0), run_parity(one, 1))
+
+
+def test_periodic_corner_pairs():
+    rng = np.random.default_rng(2)
+    q = W.random_quaternions(rng, 8)
+    pos = []
+    for c in range(4):
+        base = np.array([63.6, 0.4, 63.2]) if c == 0 else rng.random(3) * 64
+        pos += [base, np.mod(base + rng.normal(size=3) * 2 + [8, 0, 0], 64)]
+    st = state([1, 0, 1, 1, 0, 0, 1, 0], [[5, 5, 5], [6, 0, 0]] * 4, pos, q)
+    print("periodic", run_parity(st, 0))
+
+
+def test_many_face_polytopes_and_inflation():
+    rng = np.random.default_rng(3)
+    polys = [W.random_polytope(rng, f, 9.0)[0] for f in (24, 32, 8, 20)]
+    pos = [[20, 20, 20], [35, 21, 19], [20, 36, 21], [34, 36, 20]]
+    q = W.random_quaternions(rng, 4)
+    st = state([2, 2, 2, 2], np.zeros((4, 3)), pos, q, planes=polys, inflate=0.2)
+    print("polytopes", run_parity(st, 0), run_parity(st, 1))
+
+
+def test_velocities_and_damping():
+    st = W.mixed_grid_27()
+    st.damping_c = W.YOUNG and 0.3
+    rng = np.random.default_rng(4)
+    vel = rng.normal(size=(st.n, 6)) * 0.1
+    m = model_for(st)
+    g = gpu_step(m, st, vel=vel)
+    r = oracle.contact_step(st, vel=vel)
+    print("damped", compare(st, g, r, fp64=False, smooth=False))
+    m.close()
+
+
+def test_graph_replay_and_repeat():
+    st = W.mixed_settling(n=300, L=120)
+    m = model_for(st)
+    a = gpu_step(m, st)
+    seq_p, seq_q = W.pose_sequence(st, 3)
+    for s in range(3):
+        g = gpu_step(m, st, seq_p[s], seq_q[s])
+        r = oracle.contact_step(st, pos=seq_p[s], quat=seq_q[s])
+        compare(st.with_poses(seq_p[s], seq_q[s]), g, r, fp64=False, smooth=False)
+    b = gpu_step(m, st)
+    assert np.array_equal(a["pair_out"], b["pair_out"]) and np.array_equal(a["force"], b["force"])
+    m.close()
+
+
+def test_capacity_and_input_errors():
+    from paper_2401_10878_gb300.contact import ContactError, ECAPACITY, EINVAL
+    st = W.mixed_settling(n=300, L=120)
+    m = model_for(st, max_pairs=8)
+    with pytest.raises(ContactError) as e:
+        gpu_step(m, st)
+    assert e.value.code == ECAPACITY
+    assert int(m.n_pairs.item()) == oracle.contact_step(st).n_pairs
+    m.close()
+    m = model_for(st)
+    bad = st.pos.copy()
+    bad[5, 1] = st.box[1] + 3.0
+    with pytest.raises(ContactError) as e:
+        gpu_step(m, st, pos=bad)
+    assert e.value.code == EINVAL
+    m.clear_error()
+    gpu_step(m, st)   # the context is usable again
+    m.close()
+
+
+def test_user_stream_capture():
+    st = W.mixed_grid_27()
+    m = model_for(st, use_graph=False)
+    tp = torch.tensor(st.pos, device="cuda")
+    tq = torch.tensor(st.quat, device="cuda")
+    m.step(tp, tq)
+    ref = m.force.clone()
+    m.force.zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        m.lib.contact_set_stream(m.ctx, __import__("ctypes").c_void_p(s.cuda_stream))
+        with torch.cuda.graph(g, stream=s):
+            m.step_async(tp, tq)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(m.force, ref)
+    m.close()
