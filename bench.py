@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU baseline budget")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
     return ap.parse_args()
 
 
@@ -279,7 +280,7 @@ def run_ours(args, ws, rank, local):
             "roofline": roofline, "e2e": e2e, "gpu_launches": model.kernels_per_step() * args.steps,
             "clocks": clocks,
             "ms_per_step_p10_p90": [float(np.percentile(res["per"], 10)), float(np.percentile(res["per"], 90))]}
-    if rank == 0:
+    if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(st, pos, quat, args.cpu_seconds)
         if not args.no_extras:
             line["extras"] = extras(args, dev, flush)

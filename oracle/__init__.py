@@ -111,7 +111,8 @@ class Result:
     pair_shift: np.ndarray  # [P,3] int32 image index s of j (X_j' = X_j - s L)
     pair_box: np.ndarray    # [P,6] int32 node box lo, hi
     pair_out: np.ndarray    # [P,11] V, x_c[3], n[3], d, F[3] (force on j)
-    pair_aux: np.ndarray    # [P,8] G[3], box cells, ambiguous cells, ambiguous normal cells, depth gap, E*
+    pair_aux: np.ndarray    # [P,11] G[3], box cells, ambiguous cells, ambiguous normal cells, depth gap,
+    #                         E*, sensitivities of V, moments, G to an eps change of every phi
     force: np.ndarray       # [N,3]
     torque: np.ndarray      # [N,3]
     seconds: float = 0.0
@@ -142,7 +143,7 @@ def contact_step(st, pos=None, quat=None, vel=None, n_threads: int = 0, band_eps
         sh = np.zeros((cap, 3), np.int32)
         bx = np.zeros((cap, 6), np.int32)
         out = np.zeros((cap, 11))
-        aux = np.zeros((cap, 8))
+        aux = np.zeros((cap, 11))
         f = np.zeros((n, 3))
         t = np.zeros((n, 3))
         t0 = time.perf_counter()

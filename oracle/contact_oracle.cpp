@@ -286,6 +286,7 @@ struct PairResult {
   S V, xc[3], n[3], d, F[3], TA[3], TB[3];
   double G[3];
   double box_cells, n_band, n_gtie, d_gap, estar;
+  double v_sens, m_sens, g_sens;  // first-order change of V, M, G for a perturbation eps of every phi
 };
 
 // Sweep of every lattice node of the pair box (Sec. 3.3.1) and the force law
@@ -306,7 +307,7 @@ PairResult<S> eval_pair(const Config& cfg, const Shape& A, const Shape& B, const
   S SW(0.0), SM[3] = {S(0.0), S(0.0), S(0.0)}, SG[3] = {S(0.0), S(0.0), S(0.0)};
   S dbest(0.0);
   double top1 = -std::numeric_limits<double>::infinity(), top2 = top1;
-  double n_band = 0, n_gtie = 0;
+  double n_band = 0, n_gtie = 0, v_sens = 0, m_sens = 0, g_sens = 0;
   const double o[3] = {pg.lo[0] * dx, pg.lo[1] * dx, pg.lo[2] * dx};
   for (int kz = pg.lo[2]; kz <= pg.hi[2]; ++kz)
     for (int ky = pg.lo[1]; ky <= pg.hi[1]; ++ky)
@@ -348,6 +349,22 @@ PairResult<S> eval_pair(const Config& cfg, const Shape& A, const Shape& B, const
         const bool tieA = gapA < eps || (!smooth && std::fabs(pb) <= eps);
         const bool tieB = gapB < eps || (!smooth && std::fabs(pa) <= eps);
         if ((gA_on && tieA) || (gB_on && tieB)) n_gtie += 1;
+        // sensitivities (diagnostics): |dW/dphi| eps, |dW/dphi| eps |c|, and the
+        // change of the normal's band terms; smoothed H only (sharp H is a step)
+        const double hpa = std::fabs(val(HpA)), hpb = std::fabs(val(HpB));
+        const double ta = std::min(std::max(0.5 - pa / wdx, 0.0), 1.0);
+        const double tb = std::min(std::max(0.5 - pb / wdx, 0.0), 1.0);
+        const double dhpa = (ta > 0.0 && ta < 1.0) ? 6.0 * std::fabs(1.0 - 2.0 * ta) / (wdx * wdx) : 0.0;
+        const double dhpb = (tb > 0.0 && tb < 1.0) ? 6.0 * std::fabs(1.0 - 2.0 * tb) / (wdx * wdx) : 0.0;
+        const double ha = val(HA), hb = val(HB);
+        if (smooth) {
+          const double dw = hpa * hb + ha * hpb;
+          v_sens += dw * eps;
+          m_sens += dw * eps * std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+          g_sens += (dhpa * hb + 2.0 * hpa * hpb + ha * dhpb) * eps;
+        } else {
+          g_sens += (dhpa * hb + ha * dhpb) * eps;
+        }
       }
 
   PairResult<S> res;
@@ -359,6 +376,9 @@ PairResult<S> eval_pair(const Config& cfg, const Shape& A, const Shape& B, const
   res.d_gap = (top2 > -std::numeric_limits<double>::infinity()) ? (top1 - top2) / dx
                                                                 : std::numeric_limits<double>::infinity();
   res.estar = estar;
+  res.v_sens = dx3 * v_sens;
+  res.m_sens = dx3 * m_sens;
+  res.g_sens = 0.5 * dx3 * g_sens;
   S G[3];
   for (int k = 0; k < 3; ++k) {
     G[k] = 0.5 * dx3 * SG[k];
@@ -645,8 +665,10 @@ int32_t oracle_aabb(const oracle_config* cfg, int32_t n, const int32_t* shape_ty
 // only the first max_pairs rows are written when P > max_pairs) or a negative
 // status code.  Per pair: pair_ij [P,2], pair_shift [P,3], pair_box [P,6]
 // (lo, hi), pair_out [P,11] = V, x_c[3], n[3], d, F[3] (force on the
-// higher-ID particle j), pair_aux [P,8] = G[3], box cells, ambiguous cells,
-// ambiguous normal cells, depth gap (lattice units), E*.  force/torque [n,3].
+// higher-ID particle j), pair_aux [P,11] = G[3], box cells, ambiguous cells,
+// ambiguous normal cells, depth gap (lattice units), E*, and the first-order
+// change of V, of the first moments and of G when every signed distance moves
+// by band_eps (smoothed indicator; G's also in sharp mode).  force/torque [n,3].
 int64_t oracle_contact_step(const oracle_config* cfg, int32_t n, const int32_t* shape_type,
                             const double* shape_param, const int32_t* face_offset, const double* planes,
                             const double* young, const double* poisson, const double* pos,
@@ -694,9 +716,10 @@ int64_t oracle_contact_step(const oracle_config* cfg, int32_t n, const int32_t* 
       o[7] = r.d;
     }
     if (pair_aux) {
-      double* a = pair_aux + 8 * p;
+      double* a = pair_aux + 11 * p;
       a[0] = r.G[0]; a[1] = r.G[1]; a[2] = r.G[2];
       a[3] = r.box_cells; a[4] = r.n_band; a[5] = r.n_gtie; a[6] = r.d_gap; a[7] = r.estar;
+      a[8] = r.v_sens; a[9] = r.m_sens; a[10] = r.g_sens;
     }
   }
   return P;

@@ -44,6 +44,7 @@ struct Params {
   double wdx;            // smoothing width, physical
   int smooth;            // 1: smoothed indicator
   int precision;         // 0: FP32 tiles, 1: FP64 per pair
+  int kind_set;          // 1: only spheres and cuboids (lean node-sweep variant)
   double damping_c;
   int nbin[3];           // bins per axis
   double binw[3];        // bin width (physical)
@@ -107,6 +108,7 @@ struct Lists {
   int* up_list;     // [N, max_nbr]
   int* dn_count;    // [N] partners i < p
   int* dn_list;     // [N, max_nbr]
+  int* dn_pair;     // [N, max_nbr] pair index of (dn_list[p][r], p)
   int* row_off;     // [N + 1] first pair of particle i
   PairRec* pairs;   // [max_pairs]
   int* tile_pair;   // [max_tiles]

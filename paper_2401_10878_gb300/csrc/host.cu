@@ -132,17 +132,20 @@ contact_status check_sticky(contact_ctx* c) {
   return CONTACT_OK;
 }
 
-void enqueue_step(contact_ctx* c, const double* pos, const double* quat, const double* vel, int32_t* pair_ij,
-                  double* pair_out, int32_t* n_pairs, double* force, double* torque) {
+// `capturing`: the stream is being captured (ours or the caller's), so the
+// timing events must become event-record nodes of the graph.
+void enqueue_step(contact_ctx* c, bool capturing, const double* pos, const double* quat, const double* vel,
+                  int32_t* pair_ij, double* pair_out, int32_t* n_pairs, double* force, double* torque) {
+  const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   const int nbins = c->P.nbin[0] * c->P.nbin[1] * c->P.nbin[2];
   cudaMemsetAsync(c->W.bin_count, 0, sizeof(int) * nbins, c->stream);
   launch_pose(c->P, c->S, c->D, c->W, pos, quat, c->stream);
   launch_bin_scatter(c->P, c->D, c->W, c->stream);
   launch_broad(c->P, c->D, c->W, c->stream);
   launch_plan(c->P, c->S, c->D, c->W, pair_ij, n_pairs, c->stream);
-  cudaEventRecord(c->ev_narrow[0], c->stream);
+  cudaEventRecordWithFlags(c->ev_narrow[0], c->stream, ev_flags);
   launch_narrow(c->P, c->S, c->D, c->W, c->grid_narrow, c->stream);
-  cudaEventRecord(c->ev_narrow[1], c->stream);
+  cudaEventRecordWithFlags(c->ev_narrow[1], c->stream, ev_flags);
   launch_finalize(c->P, c->S, c->D, c->W, vel, pair_out, c->stream);
   launch_particle_sum(c->P, c->D, c->W, force, torque, c->stream);
 }
@@ -280,6 +283,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   P.wdx = C.smooth_width * C.dx;
   P.smooth = C.indicator;
   P.precision = C.precision;
+  P.kind_set = std::all_of(kind.begin(), kind.end(), [](int k) { return k == KIND_SPHERE || k == KIND_CUBOID; }) ? 1 : 0;
   P.damping_c = C.damping_c;
   P.max_pairs = C.max_pairs;
   P.max_nbr = max_nbr;
@@ -338,6 +342,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   GBC_TRY(dev_alloc(c, &W.up_list, static_cast<size_t>(n) * max_nbr));
   GBC_TRY(dev_alloc(c, &W.dn_count, static_cast<size_t>(n)));
   GBC_TRY(dev_alloc(c, &W.dn_list, static_cast<size_t>(n) * max_nbr));
+  GBC_TRY(dev_alloc(c, &W.dn_pair, static_cast<size_t>(n) * max_nbr));
   GBC_TRY(dev_alloc(c, &W.row_off, static_cast<size_t>(n) + 1));
   GBC_TRY(dev_alloc(c, &W.pairs, mp));
   GBC_TRY(dev_alloc(c, &W.tile_pair, mt));
@@ -402,7 +407,7 @@ contact_status contact_step(contact_ctx* c, const double* pos, const double* qua
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
-      enqueue_step(c, pos, quat, vel, pair_ij, pair_out, n_pairs, force, torque);
+      enqueue_step(c, true, pos, quat, vel, pair_ij, pair_out, n_pairs, force, torque);
       e = cudaStreamEndCapture(c->stream, &g);
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
       e = cudaGraphInstantiate(&c->gexec, g, 0);
@@ -418,7 +423,8 @@ contact_status contact_step(contact_ctx* c, const double* pos, const double* qua
     e = cudaGraphLaunch(c->gexec, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
   } else {
-    enqueue_step(c, pos, quat, vel, pair_ij, pair_out, n_pairs, force, torque);
+    enqueue_step(c, cap != cudaStreamCaptureStatusNone, pos, quat, vel, pair_ij, pair_out, n_pairs, force,
+                 torque);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
   }
@@ -486,7 +492,7 @@ contact_status contact_narrow_time(contact_ctx* c, float* ms) {
   return e == cudaSuccess ? CONTACT_OK : cuda_fail(c, e, "cudaEventElapsedTime");
 }
 
-int32_t contact_kernels_per_step(const contact_ctx*) { return 7; }
+int32_t contact_kernels_per_step(const contact_ctx*) { return 8; }
 int32_t contact_kernels_per_backward(const contact_ctx*) { return 4; }
 
 contact_status contact_backward(contact_ctx* c, const double* grad_force, const double* grad_torque,

@@ -217,7 +217,7 @@ __device__ __forceinline__ void cross3f(const float a[3], const float b[3], floa
 __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, Parts D, Lists W, AdjBufs B) {
   __shared__ float4 s_pl[kWarps][2][kMaxFaces];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int ntiles = W.counters[1];
+  const int ntiles = min(W.counters[1], P.max_tiles);
   const float inv_w = P.inv_w;
   int t = 0;
   if (lane == 0) t = atomicAdd(&W.counters[6], 1);
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(128) k_adj_post(Params P, Shapes S, Parts D, L
     const PairRec pr = W.pairs[p];
     const double* tp = W.tape + static_cast<size_t>(p) * kTapeDoubles;
     double* pg = B.pgrad + static_cast<size_t>(p) * kPairGrad;
-    if (!(tp[0] > 0.0)) continue;
+    if (!(tp[0] > 0.0) || W.counters[1] > P.max_tiles) continue;
     double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int t = pr.tile0; t < pr.tile0 + pr.ntiles; ++t) {
       const float* q = B.partial + static_cast<size_t>(t) * kAdjPartial;
@@ -368,16 +368,6 @@ __global__ void __launch_bounds__(128) k_adj_post(Params P, Shapes S, Parts D, L
   }
 }
 
-__device__ __forceinline__ int pair_index_adj(const Params& P, const Lists& W, int i, int p) {
-  const int* lst = W.up_list + static_cast<size_t>(i) * P.max_nbr;
-  int lo = 0, hi = W.up_count[i];
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (lst[mid] < p) lo = mid + 1; else hi = mid;
-  }
-  return W.row_off[i] + lo;
-}
-
 __global__ void __launch_bounds__(128) k_adj_scatter(Params P, Parts D, Lists W, AdjBufs B,
                                                      double* __restrict__ gpos, double* __restrict__ gquat) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -386,8 +376,7 @@ __global__ void __launch_bounds__(128) k_adj_scatter(Params P, Parts D, Lists W,
   double gx[3] = {0, 0, 0}, tau[3] = {0, 0, 0};
   const int nd = W.dn_count[p];
   for (int r = 0; r < nd; ++r) {
-    const int i = W.dn_list[static_cast<size_t>(p) * P.max_nbr + r];
-    const int q = pair_index_adj(P, W, i, p);
+    const int q = W.dn_pair[static_cast<size_t>(p) * P.max_nbr + r];
     if (q >= np) continue;
     const double* e = B.pgrad + static_cast<size_t>(q) * kPairGrad;
     for (int k = 0; k < 3; ++k) { gx[k] += e[6 + k]; tau[k] += e[9 + k]; }

@@ -142,11 +142,17 @@ __global__ void __launch_bounds__(1024) k_bin_scatter(Params P, Parts D, Lists W
 }
 
 // Node box of pair (p, q) with q's image nearest p; returns false if empty.
+// The image index s = rint((X_q - X_p) / L) is taken by exact comparisons
+// with L/2 (positions lie in [0, L), so s is -1, 0 or 1; rint's half-way
+// case |X_q - X_p| = L/2 cannot be a candidate because L > 4 R_max).
 __device__ __forceinline__ bool pair_box(const Params& P, const Parts& D, int p, int q, int s[3], int lo[3],
                                          int hi[3]) {
   bool hit = true;
+#pragma unroll
   for (int k = 0; k < 3; ++k) {
-    s[k] = static_cast<int>(rint(__ddiv_rn(dsub(D.X[3 * q + k], D.X[3 * p + k]), P.L[k])));
+    const double d = D.X[3 * q + k] - D.X[3 * p + k];
+    const double h = 0.5 * P.L[k];
+    s[k] = (d > h) ? 1 : ((d < -h) ? -1 : 0);
     lo[k] = max(D.lohi[6 * p + k], D.lohi[6 * q + k] - s[k] * P.ncell[k]);
     hi[k] = min(D.lohi[6 * p + 3 + k], D.lohi[6 * q + 3 + k] - s[k] * P.ncell[k]);
     hit = hit && lo[k] <= hi[k];
@@ -154,9 +160,10 @@ __device__ __forceinline__ bool pair_box(const Params& P, const Parts& D, int p,
   return hit;
 }
 
-// K3: one warp per particle scans the 27 neighbour bins; candidates are
-// compacted with warp ballots into partners above (j > p) and below (j < p),
-// then each list is sorted by rank.
+// K3: one warp per particle.  Lanes 0..26 fetch the ranges of the 27
+// neighbour bins at once; the candidates of all bins are then swept as one
+// flat list, 32 per round, and compacted with warp ballots into partners
+// above (j > p) and below (j < p); each list is sorted by rank.
 __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
   extern __shared__ int s_buf[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -167,44 +174,58 @@ __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
   int* dn = up + cap;
   const int bin = D.bin[p];
   const int b[3] = {bin % P.nbin[0], (bin / P.nbin[0]) % P.nbin[1], bin / (P.nbin[0] * P.nbin[1])};
-  int nup = 0, ndn = 0;
-  int cnt[3], first[3];
-  for (int k = 0; k < 3; ++k) {
-    if (P.nbin[k] >= 3) { cnt[k] = 3; first[k] = -1; } else { cnt[k] = P.nbin[k]; first[k] = 0; }
+  int cnt[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) cnt[k] = P.nbin[k] >= 3 ? 3 : P.nbin[k];
+  const int nnb = cnt[0] * cnt[1] * cnt[2];
+  int beg = 0, num = 0;
+  if (lane < nnb) {
+    int o[3] = {lane % cnt[0], (lane / cnt[0]) % cnt[1], lane / (cnt[0] * cnt[1])};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int c = P.nbin[k] >= 3 ? b[k] + o[k] - 1 : o[k];
+      o[k] = (c + P.nbin[k]) % P.nbin[k];
+    }
+    const int q = o[0] + P.nbin[0] * (o[1] + P.nbin[1] * o[2]);
+    beg = W.bin_start[q];
+    num = W.bin_start[q + 1] - beg;
   }
-  for (int oz = 0; oz < cnt[2]; ++oz)
-    for (int oy = 0; oy < cnt[1]; ++oy)
-      for (int ox = 0; ox < cnt[0]; ++ox) {
-        int c[3] = {ox, oy, oz};
-        for (int k = 0; k < 3; ++k) {
-          c[k] = (P.nbin[k] >= 3) ? b[k] + c[k] + first[k] : c[k];
-          c[k] = (c[k] + P.nbin[k]) % P.nbin[k];
-        }
-        const int q = c[0] + P.nbin[0] * (c[1] + P.nbin[1] * c[2]);
-        const int beg = W.bin_start[q], end = W.bin_start[q + 1];
-        for (int base = beg; base < end; base += 32) {
-          const int idx = base + lane;
-          const int j = (idx < end) ? W.bin_items[idx] : -1;
-          bool hit = false;
-          if (j >= 0 && j != p) {
-            int s[3], lo[3], hi[3];
-            hit = pair_box(P, D, p, j, s, lo, hi);
-          }
-          const unsigned bu = __ballot_sync(kFull, hit && j > p);
-          const unsigned bd = __ballot_sync(kFull, hit && j < p);
-          const unsigned below = (1u << lane) - 1u;
-          if (hit && j > p) {
-            const int at = nup + __popc(bu & below);
-            if (at < cap) up[at] = j;
-          }
-          if (hit && j < p) {
-            const int at = ndn + __popc(bd & below);
-            if (at < cap) dn[at] = j;
-          }
-          nup += __popc(bu);
-          ndn += __popc(bd);
-        }
-      }
+  // exclusive prefix of the bin sizes over the lanes
+  int off = num;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(kFull, off, d);
+    if (lane >= d) off += v;
+  }
+  const int total = __shfl_sync(kFull, off, 31);
+  off -= num;
+  int nup = 0, ndn = 0;
+  const unsigned below = (1u << lane) - 1u;
+  for (int base = 0; base < total; base += 32) {
+    const int e = base + lane;
+    // bin of flat candidate e: the last lane whose offset is <= e
+    int src = 0;
+    for (int t = 1; t < nnb; ++t) src = (e >= __shfl_sync(kFull, off, t)) ? t : src;
+    const int bb = __shfl_sync(kFull, beg, src), bo = __shfl_sync(kFull, off, src);
+    const int j = (e < total) ? W.bin_items[bb + e - bo] : -1;
+    bool hit = false;
+    if (j >= 0 && j != p) {
+      int s[3], lo[3], hi[3];
+      hit = pair_box(P, D, p, j, s, lo, hi);
+    }
+    const unsigned bu = __ballot_sync(kFull, hit && j > p);
+    const unsigned bd = __ballot_sync(kFull, hit && j < p);
+    if (hit && j > p) {
+      const int at = nup + __popc(bu & below);
+      if (at < cap) up[at] = j;
+    }
+    if (hit && j < p) {
+      const int at = ndn + __popc(bd & below);
+      if (at < cap) dn[at] = j;
+    }
+    nup += __popc(bu);
+    ndn += __popc(bd);
+  }
   if (nup > cap || ndn > cap) {
     if (lane == 0) set_error(W.err, kErrCapacity);
     nup = min(nup, cap);
@@ -230,105 +251,113 @@ __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
   }
 }
 
-// K4: pair list in (i, j) order, pair boxes, sweep layout and node tiles
-// (single CTA; O(N + P + tiles)).
-__global__ void __launch_bounds__(1024) k_plan(Params P, Shapes S, Parts D, Lists W, int32_t* __restrict__ pair_ij,
-                                               int32_t* __restrict__ n_pairs_out) {
+// K4a: first pair of every particle row (exclusive scan of the partner
+// counts, one CTA) and reset of the step's counters.
+__global__ void __launch_bounds__(1024) k_rows(Params P, Lists W, int32_t* __restrict__ n_pairs_out) {
   __shared__ long long s_tmp[1024];
-  __shared__ unsigned long long s_cells, s_ops;
-  const int tid = threadIdx.x, nt = blockDim.x;
   const int n = P.n;
-  for (int i = tid; i < n; i += nt) W.row_off[i] = W.up_count[i];
-  if (tid == 0) { s_cells = 0; s_ops = 0; }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) W.row_off[i] = W.up_count[i];
   __syncthreads();
   const long long total_pairs = block_scan_excl(W.row_off, n, s_tmp);
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     W.row_off[n] = static_cast<int>(total_pairs);
     W.counters[0] = static_cast<int>(total_pairs);
+    W.counters[1] = 0;   // tiles allocated
+    W.counters[2] = 0;   // node-sweep queue head
+    W.counters[5] = 0;   // pairs with V > 0
+    W.u64[0] = 0;        // node evaluations
+    W.u64[1] = 0;        // nominal lane-ops
     *n_pairs_out = static_cast<int>(total_pairs);
     if (total_pairs > P.max_pairs) set_error(W.err, kErrCapacity);
   }
-  const int np = static_cast<int>(min(total_pairs, static_cast<long long>(P.max_pairs)));
-  // build the pair records (one thread per particle row)
-  unsigned long long my_cells = 0, my_ops = 0;
-  for (int i = tid; i < n; i += nt) {
-    const int r0 = W.row_off[i], cnt = W.up_count[i];
-    for (int r = 0; r < cnt; ++r) {
-      const int pi = r0 + r;
-      if (pi >= np) break;
-      const int j = W.up_list[i * P.max_nbr + r];
-      PairRec pr;
-      int lo[3], hi[3];
-      pair_box(P, D, i, j, pr.shift, lo, hi);
-      pr.i = i;
-      pr.j = j;
-      int axis = 0;
-      for (int k = 0; k < 3; ++k) {
-        pr.lo[k] = lo[k];
-        pr.dim[k] = hi[k] - lo[k] + 1;
-        if (pr.dim[k] > pr.dim[axis]) axis = k;
-      }
-      pr.axis = axis;
-      const int du = pr.dim[axis];
-      pr.nseg = (du + kSegMax - 1) / kSegMax;
-      pr.seglen = (du + pr.nseg - 1) / pr.nseg;
-      const int lines = pr.dim[(axis + 1) % 3] * pr.dim[(axis + 2) % 3];
-      pr.nitems = lines * pr.nseg;
-      pr.ntiles = (pr.nitems + 32 * kTileItemsPerLane - 1) / (32 * kTileItemsPerLane);
-      pr.tile0 = pr.ntiles;  // scanned below
-      pr.kinds = W.kind[i] | (W.kind[j] << 8);
-      for (int k = 0; k < 3; ++k) {
-        const double a = D.X[3 * i + k] * P.inv_dx - lo[k];
-        const double bb = (D.X[3 * j + k] - pr.shift[k] * P.L[k]) * P.inv_dx - lo[k];
-        pr.ai[k] = static_cast<int>(rint(a));
-        pr.bi[k] = static_cast<int>(rint(bb));
-        pr.af[k] = static_cast<float>(a - pr.ai[k]);
-        pr.bf[k] = static_cast<float>(bb - pr.bi[k]);
-      }
-      const unsigned long long vol = static_cast<unsigned long long>(pr.dim[0]) * pr.dim[1] * pr.dim[2];
-      my_cells += vol;
-      my_ops += vol * static_cast<unsigned long long>(S.nomops[i] + S.nomops[j]);
-      W.pairs[pi] = pr;
-      pair_ij[2 * pi] = i;
-      pair_ij[2 * pi + 1] = j;
+}
+
+// K4b: one thread per (particle row i, partner slot r): the pair record of
+// pair row_off[i] + r, its sweep layout and its node tiles.  Tiles are
+// allocated with one atomic per warp; a pair's tiles are contiguous, and its
+// partial sums do not depend on where they land, so results are deterministic.
+__global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D, Lists W,
+                                                     int32_t* __restrict__ pair_ij) {
+  const int lane = threadIdx.x & 31;
+  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int cap = P.max_nbr;
+  const int i = static_cast<int>(t / cap), r = static_cast<int>(t % cap);
+  const bool active = i < P.n && r < W.up_count[i] && (W.row_off[i] + r) < P.max_pairs;
+  PairRec pr;
+  int pi = 0, ntiles = 0;
+  unsigned long long vol = 0, ops = 0;
+  if (active) {
+    pi = W.row_off[i] + r;
+    const int j = W.up_list[i * cap + r];
+    int lo[3], hi[3];
+    pair_box(P, D, i, j, pr.shift, lo, hi);
+    pr.i = i;
+    pr.j = j;
+    int axis = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      pr.lo[k] = lo[k];
+      pr.dim[k] = hi[k] - lo[k] + 1;
+      if (pr.dim[k] > pr.dim[axis]) axis = k;
     }
+    pr.axis = axis;
+    const int du = pr.dim[axis];
+    pr.nseg = (du + kSegMax - 1) / kSegMax;
+    pr.seglen = (du + pr.nseg - 1) / pr.nseg;
+    const int lines = pr.dim[(axis + 1) % 3] * pr.dim[(axis + 2) % 3];
+    pr.nitems = lines * pr.nseg;
+    ntiles = (pr.nitems + 32 * kTileItemsPerLane - 1) / (32 * kTileItemsPerLane);
+    pr.ntiles = ntiles;
+    pr.kinds = W.kind[i] | (W.kind[j] << 8);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double a = D.X[3 * i + k] * P.inv_dx - lo[k];
+      const double bb = (D.X[3 * j + k] - pr.shift[k] * P.L[k]) * P.inv_dx - lo[k];
+      pr.ai[k] = static_cast<int>(rint(a));
+      pr.bi[k] = static_cast<int>(rint(bb));
+      pr.af[k] = static_cast<float>(a - pr.ai[k]);
+      pr.bf[k] = static_cast<float>(bb - pr.bi[k]);
+    }
+    vol = static_cast<unsigned long long>(pr.dim[0]) * pr.dim[1] * pr.dim[2];
+    ops = vol * static_cast<unsigned long long>(S.nomops[i] + S.nomops[j]);
+    pair_ij[2 * pi] = i;
+    pair_ij[2 * pi + 1] = j;
+    // slot of this pair in j's list of lower partners
+    const int* dl = W.dn_list + static_cast<size_t>(j) * cap;
+    int a0 = 0, a1 = W.dn_count[j];
+    while (a0 < a1) {
+      const int mid = (a0 + a1) >> 1;
+      if (dl[mid] < i) a0 = mid + 1; else a1 = mid;
+    }
+    W.dn_pair[static_cast<size_t>(j) * cap + a0] = pi;
   }
-  atomicAdd(&s_cells, my_cells);
-  atomicAdd(&s_ops, my_ops);
-  __syncthreads();
-  // tile offsets: scan of ntiles over the pairs (stored in tile0)
-  {
-    const int chunk = (np + nt - 1) / nt;
-    const int b = min(np, tid * chunk), e = min(np, b + chunk);
-    long long s = 0;
-    for (int q = b; q < e; ++q) s += W.pairs[q].ntiles;
-    s_tmp[tid] = s;
-    __syncthreads();
-    for (int off = 1; off < nt; off <<= 1) {
-      const long long v = (tid >= off) ? s_tmp[tid - off] : 0;
-      __syncthreads();
-      s_tmp[tid] += v;
-      __syncthreads();
-    }
-    const long long total_tiles = s_tmp[nt - 1];
-    long long run = s_tmp[tid] - s;
-    const bool overflow = total_tiles > P.max_tiles;
-    for (int q = b; q < e; ++q) {
-      W.pairs[q].tile0 = static_cast<int>(run);
-      const int nt_q = W.pairs[q].ntiles;
-      if (!overflow)
-        for (int t = 0; t < nt_q; ++t) W.tile_pair[run + t] = q;
-      run += nt_q;
-    }
-    if (tid == 0) {
-      if (overflow) set_error(W.err, kErrCapacity);
-      W.counters[1] = overflow ? 0 : static_cast<int>(total_tiles);
-      W.counters[2] = 0;
-      W.counters[5] = 0;
-      W.counters[3] = static_cast<int>(s_cells & 0x7fffffffULL);
-      W.counters[4] = static_cast<int>(s_cells >> 31);
-      W.u64[0] = s_cells;
-      W.u64[1] = s_ops;
+  // warp-aggregated tile allocation and counters
+  int incl = ntiles;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += v;
+  }
+  unsigned long long wv = vol, wo = ops;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    wv += __shfl_xor_sync(kFull, wv, d);
+    wo += __shfl_xor_sync(kFull, wo, d);
+  }
+  int base = 0;
+  if (lane == 31 && incl > 0) base = atomicAdd(&W.counters[1], incl);
+  if (lane == 0 && wv > 0) {
+    atomicAdd(&W.u64[0], wv);
+    atomicAdd(&W.u64[1], wo);
+  }
+  base = __shfl_sync(kFull, base, 31);
+  if (active) {
+    pr.tile0 = base + incl - ntiles;
+    W.pairs[pi] = pr;
+    for (int k = 0; k < ntiles; ++k) {
+      const int tt = pr.tile0 + k;
+      if (tt < P.max_tiles) W.tile_pair[tt] = pi;
+      else set_error(W.err, kErrCapacity);
     }
   }
 }
@@ -337,8 +366,8 @@ __global__ void __launch_bounds__(1024) k_plan(Params P, Shapes S, Parts D, List
 
 void launch_pose(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* pos,
                  const double* quat, cudaStream_t st) {
-  const int nb = (P.n + 127) / 128;
-  if (nb > 0) k_pose<<<nb, 128, 0, st>>>(P, S, D, W, pos, quat);
+  const int nb = (P.n + 63) / 64;
+  if (nb > 0) k_pose<<<nb, 64, 0, st>>>(P, S, D, W, pos, quat);
 }
 
 void launch_bin_scatter(const Params& P, const Parts& D, const Lists& W, cudaStream_t st) {
@@ -354,7 +383,10 @@ void launch_broad(const Params& P, const Parts& D, const Lists& W, cudaStream_t 
 
 void launch_plan(const Params& P, const Shapes& S, const Parts& D, const Lists& W, int32_t* pair_ij, int32_t* n_pairs,
                  cudaStream_t st) {
-  k_plan<<<1, 1024, 0, st>>>(P, S, D, W, pair_ij, n_pairs);
+  k_rows<<<1, 1024, 0, st>>>(P, W, n_pairs);
+  const long long threads = static_cast<long long>(P.n) * P.max_nbr;
+  const int nb = static_cast<int>((threads + 127) / 128);
+  k_build_pairs<<<nb > 0 ? nb : 1, 128, 0, st>>>(P, S, D, W, pair_ij);
 }
 
 }  // namespace gbc

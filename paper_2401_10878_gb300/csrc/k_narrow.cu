@@ -374,7 +374,11 @@ __device__ __forceinline__ void warp_reduce_partials(float* v) {
   }
 }
 
-template <bool SMOOTH>
+// Kernel variants: the full set of pair kinds, or spheres and cuboids only
+// (chosen at init when no polytope is present; fewer registers, no spills).
+enum KindSet : int { SET_ALL = 0, SET_SC = 1 };
+
+template <bool SMOOTH, int SET>
 __device__ __forceinline__ void dispatch(const Params& P, const Shapes& S, const Parts& D, const PairRec& pr,
                                          int tl, float4* smA, float4* smB, float* out) {
   int ka = pr.kinds & 0xff, kb = pr.kinds >> 8;
@@ -392,19 +396,29 @@ __device__ __forceinline__ void dispatch(const Params& P, const Shapes& S, const
   case (KA) * 4 + (KB):                                                                          \
     sweep_tile<SMOOTH, TA, TB>(P, S, D, pr, pa, cia, cfa, pb, cib, cfb, tl, smA, smB, out);      \
     break;
-  switch (ka * 4 + kb) {
-    GBC_CASE(0, 0, SphereEval, SphereEval)
-    GBC_CASE(0, 1, SphereEval, CuboidEval)
-    GBC_CASE(0, 2, SphereEval, PolyEval<kRegFaces>)
-    GBC_CASE(0, 3, SphereEval, PolyGEval)
-    GBC_CASE(1, 1, CuboidEval, CuboidEval)
-    GBC_CASE(1, 2, CuboidEval, PolyEval<kRegFaces>)
-    GBC_CASE(1, 3, CuboidEval, PolyGEval)
-    GBC_CASE(2, 2, PolyEval<kRegFaces>, PolyEval<kRegFaces>)
-    GBC_CASE(2, 3, PolyEval<kRegFaces>, PolyGEval)
-    GBC_CASE(3, 3, PolyGEval, PolyGEval)
-    default:
-      break;
+  if constexpr (SET == SET_SC) {
+    switch (ka * 4 + kb) {
+      GBC_CASE(0, 0, SphereEval, SphereEval)
+      GBC_CASE(0, 1, SphereEval, CuboidEval)
+      GBC_CASE(1, 1, CuboidEval, CuboidEval)
+      default:
+        break;
+    }
+  } else {
+    switch (ka * 4 + kb) {
+      GBC_CASE(0, 0, SphereEval, SphereEval)
+      GBC_CASE(0, 1, SphereEval, CuboidEval)
+      GBC_CASE(0, 2, SphereEval, PolyEval<kRegFaces>)
+      GBC_CASE(0, 3, SphereEval, PolyGEval)
+      GBC_CASE(1, 1, CuboidEval, CuboidEval)
+      GBC_CASE(1, 2, CuboidEval, PolyEval<kRegFaces>)
+      GBC_CASE(1, 3, CuboidEval, PolyGEval)
+      GBC_CASE(2, 2, PolyEval<kRegFaces>, PolyEval<kRegFaces>)
+      GBC_CASE(2, 3, PolyEval<kRegFaces>, PolyGEval)
+      GBC_CASE(3, 3, PolyGEval, PolyGEval)
+      default:
+        break;
+    }
   }
 #undef GBC_CASE
   if (swap) {
@@ -412,11 +426,12 @@ __device__ __forceinline__ void dispatch(const Params& P, const Shapes& S, const
   }
 }
 
-template <bool SMOOTH>
-__global__ void __launch_bounds__(kWarps * 32, 2) k_narrow32(Params P, Shapes S, Parts D, Lists W) {
+template <bool SMOOTH, int SET>
+__global__ void __launch_bounds__(kWarps * 32, SET == SET_SC ? 4 : 2) k_narrow32(Params P, Shapes S, Parts D,
+                                                                                 Lists W) {
   __shared__ float4 s_planes[kWarps][2][kMaxFaces];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int ntiles = W.counters[1];
+  const int ntiles = min(W.counters[1], P.max_tiles);
   int t = 0;
   if (lane == 0) t = atomicAdd(&W.counters[2], 1);
   t = __shfl_sync(kFull, t, 0);
@@ -426,7 +441,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_narrow32(Params P, Shapes S,
     const int p = W.tile_pair[t];
     const PairRec pr = W.pairs[p];
     float v[9];
-    dispatch<SMOOTH>(P, S, D, pr, t - pr.tile0, s_planes[wid][0], s_planes[wid][1], v);
+    dispatch<SMOOTH, SET>(P, S, D, pr, t - pr.tile0, s_planes[wid][0], s_planes[wid][1], v);
     warp_reduce_partials(v);
     if (lane < 9) {
       float x = v[0];
@@ -523,16 +538,21 @@ __global__ void __launch_bounds__(256) k_narrow64(Params P, Shapes S, Parts D, L
 
 }  // namespace
 
+template <bool SMOOTH, int SET>
+int blocks_per_sm() {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_narrow32<SMOOTH, SET>, kWarps * 32, 0);
+  return per_sm > 0 ? per_sm : 1;
+}
+
 int narrow_grid(const Params& P) {
-  int dev = 0, sms = 0, per_sm = 0;
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (P.precision == 1) return sms * 4;
-  if (P.smooth)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_narrow32<true>, kWarps * 32, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_narrow32<false>, kWarps * 32, 0);
-  return sms * (per_sm > 0 ? per_sm : 1);
+  const int per_sm = P.smooth ? (P.kind_set ? blocks_per_sm<true, SET_SC>() : blocks_per_sm<true, SET_ALL>())
+                              : (P.kind_set ? blocks_per_sm<false, SET_SC>() : blocks_per_sm<false, SET_ALL>());
+  return sms * per_sm;
 }
 
 void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists& W, int grid, cudaStream_t st) {
@@ -543,10 +563,14 @@ void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists
       k_narrow64<false><<<grid, 256, 0, st>>>(P, S, D, W);
     return;
   }
-  if (P.smooth)
-    k_narrow32<true><<<grid, kWarps * 32, 0, st>>>(P, S, D, W);
-  else
-    k_narrow32<false><<<grid, kWarps * 32, 0, st>>>(P, S, D, W);
+  const int b = kWarps * 32;
+  if (P.smooth) {
+    if (P.kind_set) k_narrow32<true, SET_SC><<<grid, b, 0, st>>>(P, S, D, W);
+    else k_narrow32<true, SET_ALL><<<grid, b, 0, st>>>(P, S, D, W);
+  } else {
+    if (P.kind_set) k_narrow32<false, SET_SC><<<grid, b, 0, st>>>(P, S, D, W);
+    else k_narrow32<false, SET_ALL><<<grid, b, 0, st>>>(P, S, D, W);
+  }
 }
 
 }  // namespace gbc

@@ -22,10 +22,10 @@ __device__ __forceinline__ void cross(const double a[3], const double b[3], doub
 
 // K6: one thread per pair.  FP64 sums of the tile partials in tile order (or
 // the FP64 kernel's sums), then contact point, normal, depth, force, torques.
-__global__ void __launch_bounds__(128) k_finalize(Params P, Shapes S, Parts D, Lists W,
+__global__ void __launch_bounds__(64) k_finalize(Params P, Shapes S, Parts D, Lists W,
                                                   const double* __restrict__ vel, double* __restrict__ pair_out) {
   const int np = min(W.counters[0], P.max_pairs);
-  const bool tiles_ok = P.precision == 1 || W.counters[1] > 0 || np == 0;
+  const bool tiles_ok = P.precision == 1 || W.counters[1] <= P.max_tiles;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
     const PairRec pr = W.pairs[p];
     double s[9] = {0, 0, 0, 0, 0, 0, 0, -DBL_MAX, 0};
@@ -137,43 +137,51 @@ __global__ void __launch_bounds__(128) k_finalize(Params P, Shapes S, Parts D, L
   }
 }
 
-// Index of pair (i, p) with i < p: row of i plus the rank of p in i's sorted partners.
-__device__ __forceinline__ int pair_index(const Params& P, const Lists& W, int i, int p) {
-  const int* lst = W.up_list + static_cast<size_t>(i) * P.max_nbr;
-  int lo = 0, hi = W.up_count[i];
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (lst[mid] < p) lo = mid + 1; else hi = mid;
-  }
-  return W.row_off[i] + lo;
-}
-
-// K7: per particle, pairs where it is j (by i), then pairs where it is i (by j).
+// K7: one warp per particle.  Its contributions are, in this order, the
+// pairs where it is j (by i) and the pairs where it is i (by j); lanes fetch
+// them 32 at a time, lane 0 adds them up in that order (FP64).
 __global__ void __launch_bounds__(128) k_particle_sum(Params P, Parts D, Lists W, double* __restrict__ force,
                                                       double* __restrict__ torque) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p == 0) *W.err_host = *W.err;
+  const int lane = threadIdx.x & 31;
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (p == 0 && lane == 0) *W.err_host = *W.err;
   if (p >= P.n) return;
   const int np = min(W.counters[0], P.max_pairs);
+  const int nd = W.dn_count[p], nu = W.up_count[p], r0 = W.row_off[p];
+  const size_t slot = static_cast<size_t>(p) * P.max_nbr;
   double f[3] = {0, 0, 0}, t[3] = {0, 0, 0};
-  const int nd = W.dn_count[p];
-  for (int r = 0; r < nd; ++r) {
-    const int i = W.dn_list[static_cast<size_t>(p) * P.max_nbr + r];
-    const int q = pair_index(P, W, i, p);
-    if (q >= np) continue;
-    const double* e = W.ft + static_cast<size_t>(q) * kFtDoubles;
-    for (int k = 0; k < 3; ++k) { f[k] += e[k]; t[k] += e[6 + k]; }
+  for (int base = 0; base < nd + nu; base += 32) {
+    const int e = base + lane;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    if (e < nd) {
+      const int q = W.dn_pair[slot + e];
+      if (q < np) {
+        const double* x = W.ft + static_cast<size_t>(q) * kFtDoubles;
+        v[0] = x[0]; v[1] = x[1]; v[2] = x[2];
+        v[3] = x[6]; v[4] = x[7]; v[5] = x[8];
+      }
+    } else if (e < nd + nu) {
+      const int q = r0 + (e - nd);
+      if (q < np) {
+        const double* x = W.ft + static_cast<size_t>(q) * kFtDoubles;
+        v[0] = -x[0]; v[1] = -x[1]; v[2] = -x[2];
+        v[3] = x[3]; v[4] = x[4]; v[5] = x[5];
+      }
+    }
+    const int m = min(32, nd + nu - base);
+    for (int l = 0; l < m; ++l) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        f[k] += __shfl_sync(0xffffffffu, v[k], l);
+        t[k] += __shfl_sync(0xffffffffu, v[3 + k], l);
+      }
+    }
   }
-  const int r0 = W.row_off[p], nu = W.up_count[p];
-  for (int r = 0; r < nu; ++r) {
-    const int q = r0 + r;
-    if (q >= np) break;
-    const double* e = W.ft + static_cast<size_t>(q) * kFtDoubles;
-    for (int k = 0; k < 3; ++k) { f[k] -= e[k]; t[k] += e[3 + k]; }
-  }
-  for (int k = 0; k < 3; ++k) {
-    force[3 * p + k] = f[k];
-    torque[3 * p + k] = t[k];
+  if (lane == 0) {
+    for (int k = 0; k < 3; ++k) {
+      force[3 * p + k] = f[k];
+      torque[3 * p + k] = t[k];
+    }
   }
 }
 
@@ -184,14 +192,14 @@ void launch_finalize(const Params& P, const Shapes& S, const Parts& D, const Lis
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int need = (P.max_pairs + 127) / 128;
-  const int grid = need < 2 * sms ? (need > 0 ? need : 1) : 2 * sms;
-  k_finalize<<<grid, 128, 0, st>>>(P, S, D, W, vel, pair_out);
+  const int need = (P.max_pairs + 63) / 64;
+  const int grid = need < 4 * sms ? (need > 0 ? need : 1) : 4 * sms;
+  k_finalize<<<grid, 64, 0, st>>>(P, S, D, W, vel, pair_out);
 }
 
 void launch_particle_sum(const Params& P, const Parts& D, const Lists& W, double* force, double* torque,
                          cudaStream_t st) {
-  const int nb = (P.n + 127) / 128;
+  const int nb = (P.n + 3) / 4;   // four particles (warps) per block
   k_particle_sum<<<nb > 0 ? nb : 1, 128, 0, st>>>(P, D, W, force, torque);
 }
 

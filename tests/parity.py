@@ -2,12 +2,23 @@
 
 Tolerances (north star, restated): the candidate pair list and the particle
 node ranges are compared bit for bit; volume and first moments within 1e-6
-relative; force and torque within 1e-5 relative (FP32-tile form).  Where
-floating point decides an integer -- a node's inside/outside class, the
-active face behind the normal, the deepest node -- the oracle reports the
-nodes whose decision lies within BAND_EPS = 1e-5 lattice units of flipping.
-Pairs with such nodes are "flagged": their volume must stay within the
-flagged-node count of the oracle's, the rest is reported, not asserted.
+relative; force and torque within 1e-5 relative (FP32-tile form).
+
+FP32 evaluates every signed distance with an absolute error below
+EPS = 1e-5 lattice units (node coordinates are exact integers minus an FP32
+remainder in [-1/2, 1/2]; |r| and face offsets stay below ~25 cells, so the
+three FP32 roundings of a face value stay below ~8e-6).  Consequences:
+  * sharp indicator: a node can change class only if |phi| < EPS.  The oracle
+    reports, per pair, the nodes within EPS of flipping (and of switching the
+    active face or the deepest node).  Pairs with such nodes are "flagged":
+    their volume must stay within the flagged-node count, the remaining
+    outputs are reported, not asserted.  Unflagged pairs: V and the moments are
+    integer sums and must match exactly.
+  * smoothed indicator (and the normal's band sums in both modes): outputs are
+    continuous in phi, so their deviation is bounded by the oracle's
+    first-order sensitivity sum_nodes |d(.)/dphi| EPS (reported per pair),
+    on top of the 1e-6 / 1e-5 relative tolerances.
+The all-FP64 form has no EPS: everything within 1e-9.
 """
 from __future__ import annotations
 
@@ -26,10 +37,10 @@ class Report:
     cells: int
     flagged: int
     flips: int
-    max_rel: dict
+    max_err: dict
 
     def __str__(self):
-        r = ", ".join(f"{k}={v:.2e}" for k, v in self.max_rel.items())
+        r = ", ".join(f"{k}={v:.2e}" for k, v in self.max_err.items())
         return f"pairs={self.pairs} cells={self.cells} flagged={self.flagged} flips={self.flips} {r}"
 
 
@@ -45,78 +56,88 @@ def gpu_step(model, st, pos=None, quat=None, vel=None):
     return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items()}
 
 
-def rel(a, b, scale):
-    return np.abs(a - b) / np.maximum(scale, 1e-300)
+def _check(name, err, tol, out):
+    """Record the largest err/tol ratio and assert err <= tol elementwise."""
+    err = np.asarray(err, float)
+    tol = np.asarray(tol, float)
+    ratio = err / np.maximum(tol, 1e-300)
+    out[name] = float(ratio.max(initial=0.0))
+    assert np.all(err <= tol), f"{name}: err {err.max(initial=0):.3e} beyond tolerance (worst ratio {ratio.max():.2f})"
 
 
 def compare(st, g, r, fp64: bool, smooth: bool) -> Report:
-    """Assert parity of GPU outputs g against the oracle result r."""
+    """Assert parity of GPU outputs g against the oracle result r.  The
+    report's numbers are the worst error / tolerance ratios (<= 1 passes)."""
     assert g["n_pairs"] == r.n_pairs, (g["n_pairs"], r.n_pairs)
     assert np.array_equal(g["pair_ij"], r.pair_ij), "pair list differs"
     go, ro, aux = g["pair_out"], r.pair_out, r.pair_aux
-    dx3 = st.dx ** 3
+    dx, dx3 = st.dx, st.dx ** 3
+    L = float(np.max(st.box))
     gap = aux[:, 6]
-    amb_d = (gap > 0) & (gap < 4 * BAND)
-    flagged = (aux[:, 4] > 0) | (aux[:, 5] > 0) | amb_d
+    flagged = (aux[:, 4] > 0) | (aux[:, 5] > 0) | ((gap > 0) & (gap < 4 * BAND))
     if fp64:
         flagged = np.zeros_like(flagged)
     clean = ~flagged
     out = {}
-    # volume: exact counts in sharp mode, 1e-6 relative otherwise
-    Vs = np.maximum(np.abs(ro[:, 0]), dx3)
-    vt = 1e-9 if fp64 else (0.0 if not smooth else 1e-6)
-    e = rel(go[clean, 0], ro[clean, 0], Vs[clean])
-    out["V"] = float(e.max(initial=0))
-    assert np.all(e <= vt + 1e-12), f"volume beyond tolerance: {e.max()}"
-    flips = np.rint(np.abs(go[flagged, 0] - ro[flagged, 0]) / dx3)
+    V = ro[:, 0]
+    vsens = np.zeros(len(V)) if (fp64 or not smooth) else aux[:, 8]
+    msens = np.zeros(len(V)) if (fp64 or not smooth) else aux[:, 9]
+    gsens = np.zeros(len(V)) if fp64 else aux[:, 10]
+    Gn = np.linalg.norm(aux[:, :3], axis=1)
+    rel = 1e-9 if fp64 else 1e-6
+    relF = 1e-9 if fp64 else 1e-5
+    # volume
+    tolV = rel * np.maximum(V, dx3) + vsens
+    if not smooth and not fp64:
+        tolV = np.zeros_like(V)      # integer node counts: exact
+    _check("V", np.abs(go[clean, 0] - V[clean]), tolV[clean], out)
+    flips = np.rint(np.abs(go[flagged, 0] - V[flagged]) / dx3)
     if not smooth:
         assert np.all(flips <= aux[flagged, 4] + 1e-9), "classification flips outside the band"
-    hit = clean & (ro[:, 0] > 0)
-    # contact point: first moments / volume
-    L = float(np.max(st.box))
-    e = np.abs(go[hit, 1:4] - ro[hit, 1:4]).max(axis=1, initial=0) / L
-    out["x_c"] = float(e.max(initial=0))
-    assert np.all(e <= (1e-12 if (fp64 or not smooth) else 1e-6)), f"contact point: {e.max()}"
-    # normal (unit vector): FP32 band sums
-    e = np.abs(go[hit, 4:7] - ro[hit, 4:7]).max(axis=1, initial=0)
-    out["n"] = float(e.max(initial=0))
-    assert np.all(e <= (1e-9 if fp64 else 1e-5)), f"normal: {e.max()}"
+    hit = clean & (V > 0)
+    # contact point x_c = o + M / V
+    o = r.pair_box[:, :3] * dx
+    arm_o = np.linalg.norm(ro[:, 1:4] - o, axis=1)
+    tolx = np.where(V > 0, (msens + arm_o * vsens) / np.maximum(V, 1e-300), 0) + rel * L
+    if not smooth and not fp64:
+        tolx = np.full(len(V), 1e-12 * L)
+    _check("x_c", np.abs(go[hit, 1:4] - ro[hit, 1:4]).max(axis=1, initial=0), tolx[hit], out)
+    # normal n = G / |G| (FP32 band sums)
+    toln = relF + 2.0 * gsens / np.maximum(Gn, 1e-300)
+    _check("n", np.abs(go[hit, 4:7] - ro[hit, 4:7]).max(axis=1, initial=0), toln[hit], out)
     # depth: FP64 re-evaluation at the deepest node
-    e = np.abs(go[hit, 7] - ro[hit, 7]) / st.dx
-    out["d"] = float(e.max(initial=0))
-    assert np.all(e <= (1e-9 if fp64 else 1e-6)), f"depth: {e.max()}"
-    # force on the pair
-    Fs = np.linalg.norm(ro[hit, 8:11], axis=1)
-    e = np.abs(go[hit, 8:11] - ro[hit, 8:11]).max(axis=1, initial=0) / np.maximum(Fs, 1e-300)
-    e[Fs == 0] = np.abs(go[hit, 8:11][Fs == 0]).max(axis=1, initial=0)
-    out["F_pair"] = float(e.max(initial=0))
-    assert np.all(e <= (1e-9 if fp64 else 1e-5)), f"pair force: {e.max()}"
-    # zero pairs stay exactly zero
-    zero = clean & (ro[:, 0] == 0)
-    assert np.all(go[zero] == 0.0)
-    # per-particle sums: scale = sum of |pair force| (and |torque|) touching the particle
+    told = (1e-9 if fp64 else 1e-6) * dx
+    _check("d", np.abs(go[hit, 7] - ro[hit, 7]), np.full(hit.sum(), told), out)
+    # pair force: |F| ~ sqrt(V d) |n|
+    Fs = np.linalg.norm(ro[:, 8:11], axis=1)
+    d = np.maximum(ro[:, 7], 1e-300)
+    tolFrel = relF + 0.5 * tolV / np.maximum(V, 1e-300) + 0.5 * told / d + toln
+    tolF = tolFrel * Fs
+    tolF[Fs == 0] = 0.0
+    _check("F_pair", np.abs(go[hit, 8:11] - ro[hit, 8:11]).max(axis=1, initial=0), tolF[hit], out)
+    zero = clean & (V == 0)
+    assert np.all(go[zero] == 0.0), "pairs with no overlap must be exactly zero"
+    # per-particle sums: tolerance = sum of the pair tolerances touching it
     touched_flag = np.zeros(st.n, bool)
     touched_flag[r.pair_ij[flagged].ravel()] = True
-    Fabs = np.linalg.norm(ro[:, 8:11], axis=1)
     sF = np.zeros(st.n)
-    np.add.at(sF, r.pair_ij[:, 0], Fabs)
-    np.add.at(sF, r.pair_ij[:, 1], Fabs)
+    tF = np.zeros(st.n)
+    for col in (0, 1):
+        np.add.at(sF, r.pair_ij[:, col], Fs)
+        np.add.at(tF, r.pair_ij[:, col], tolF)
     ok = ~touched_flag & (sF > 0)
-    e = np.abs(g["force"][ok] - r.force[ok]).max(axis=1, initial=0) / sF[ok]
-    out["F"] = float(e.max(initial=0))
-    assert np.all(e <= (1e-9 if fp64 else 1e-5)), f"particle force: {e.max()}"
-    Tabs = np.linalg.norm(r.torque, axis=1)
+    _check("F", np.abs(g["force"][ok] - r.force[ok]).max(axis=1, initial=0), tF[ok] + 1e-12 * sF[ok], out)
     XA = st.pos[r.pair_ij[:, 0]]
-    xc = ro[:, 1:4]
-    arm = np.linalg.norm(xc - XA, axis=1)
+    XB = st.pos[r.pair_ij[:, 1]] - r.pair_shift * st.box
+    armA = np.linalg.norm(ro[:, 1:4] - XA, axis=1)
+    armB = np.linalg.norm(ro[:, 1:4] - XB, axis=1)
+    tT = np.zeros(st.n)
+    np.add.at(tT, r.pair_ij[:, 0], tolF * armA + Fs * tolx)
+    np.add.at(tT, r.pair_ij[:, 1], tolF * armB + Fs * tolx)
     sT = np.zeros(st.n)
-    np.add.at(sT, r.pair_ij[:, 0], Fabs * (arm + st.dx))
-    np.add.at(sT, r.pair_ij[:, 1], Fabs * (arm + st.dx))
-    ok = ok & (sT > 0)
-    e = np.abs(g["torque"][ok] - r.torque[ok]).max(axis=1, initial=0) / sT[ok]
-    out["T"] = float(e.max(initial=0))
-    assert np.all(e <= (1e-9 if fp64 else 1e-5)), f"particle torque: {e.max()}"
-    del Tabs
+    np.add.at(sT, r.pair_ij[:, 0], Fs * armA)
+    np.add.at(sT, r.pair_ij[:, 1], Fs * armB)
+    _check("T", np.abs(g["torque"][ok] - r.torque[ok]).max(axis=1, initial=0), tT[ok] + 1e-12 * sT[ok], out)
     none = ~(sF > 0) & ~touched_flag
     assert np.all(g["force"][none] == 0.0) and np.all(g["torque"][none] == 0.0)
     return Report(r.n_pairs, r.cells, int(flagged.sum()), int(flips.sum()), out)

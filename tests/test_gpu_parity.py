@@ -120,7 +120,8 @@ def test_periodic_corner_pairs():
     for c in range(4):
         base = np.array([63.6, 0.4, 63.2]) if c == 0 else rng.random(3) * 64
         pos += [base, np.mod(base + rng.normal(size=3) * 2 + [8, 0, 0], 64)]
-    st = state([1, 0, 1, 1, 0, 0, 1, 0], [[5, 5, 5], [6, 0, 0]] * 4, pos, q)
+    types = [1, 0, 1, 1, 0, 0, 1, 0]
+    st = state(types, [[5, 5, 5] if t == 1 else [6, 0, 0] for t in types], pos, q)
     print("periodic", run_parity(st, 0))
 
 
