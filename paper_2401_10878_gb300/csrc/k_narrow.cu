@@ -427,7 +427,7 @@ __device__ __forceinline__ void dispatch(const Params& P, const Shapes& S, const
 }
 
 template <bool SMOOTH, int SET>
-__global__ void __launch_bounds__(kWarps * 32, SET == SET_SC ? 4 : 2) k_narrow32(Params P, Shapes S, Parts D,
+__global__ void __launch_bounds__(kWarps * 32, SET == SET_SC ? 3 : 2) k_narrow32(Params P, Shapes S, Parts D,
                                                                                  Lists W) {
   __shared__ float4 s_planes[kWarps][2][kMaxFaces];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
