@@ -50,7 +50,7 @@ struct Params {
   double binw[3];        // bin width (physical)
   int max_pairs, max_nbr, max_tiles;
   // FP32 copies for the node sweep (lattice units)
-  float inflate_l, inv_w, neg6_over_w;
+  float inflate_l, inv_w, neg6_over_w, wdx_l;   // wdx_l: smoothing width in cells
 };
 
 // Shape tables (read-only after contact_init).
@@ -97,7 +97,13 @@ struct PairRec {
   // integer and an FP32 remainder in [-1/2, 1/2] so that node offsets stay exact
   int ai[3], bi[3];
   float af[3], bf[3];
+  // FP32 sweep geometry of both particles: R^T rows and sizes (lattice units)
+  float rta[9], rtb[9];
+  float sza[3], szb[3];
+  int pad[2];
 };
+constexpr int kPairRecWords = sizeof(PairRec) / 4;
+static_assert(sizeof(PairRec) % 16 == 0, "PairRec is staged with 16-byte copies");
 
 // Work lists shared by the step's kernels.
 struct Lists {

@@ -291,6 +291,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   P.inflate_l = static_cast<float>(C.inflate / C.dx);
   P.inv_w = static_cast<float>(1.0 / C.smooth_width);
   P.neg6_over_w = static_cast<float>(-6.0 / C.smooth_width);
+  P.wdx_l = static_cast<float>(C.smooth_width);
 
   cudaError_t e = cudaSuccess;
   std::vector<double> pl_vec(planes ? planes : nullptr, planes ? planes + 4 * static_cast<size_t>(nfaces) : nullptr);

@@ -293,19 +293,39 @@ __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D
     pair_box(P, D, i, j, pr.shift, lo, hi);
     pr.i = i;
     pr.j = j;
-    int axis = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       pr.lo[k] = lo[k];
       pr.dim[k] = hi[k] - lo[k] + 1;
-      if (pr.dim[k] > pr.dim[axis]) axis = k;
     }
-    pr.axis = axis;
-    const int du = pr.dim[axis];
-    pr.nseg = (du + kSegMax - 1) / kSegMax;
-    pr.seglen = (du + pr.nseg - 1) / pr.nseg;
-    const int lines = pr.dim[(axis + 1) % 3] * pr.dim[(axis + 2) % 3];
-    pr.nitems = lines * pr.nseg;
+    // sweep layout: lines along one axis, lines cut into nseg segments; the
+    // choice minimises warp slots x (segment length + 1 for the line set-up)
+    const long long volp = static_cast<long long>(pr.dim[0]) * pr.dim[1] * pr.dim[2];
+    long long best = -1;
+    for (int a = 0; a < 3; ++a) {
+      const int du = pr.dim[a];
+      const long long lines = volp / du;
+      for (int ns = 1; ns <= 8 && ns <= du; ++ns) {
+        const int sl = (du + ns - 1) / ns;
+        if (sl > kSegMax) continue;
+        const long long slots = (lines * ns + 31) / 32;
+        const long long cost = slots * (sl + 1);
+        if (best < 0 || cost < best) {
+          best = cost;
+          pr.axis = a;
+          pr.nseg = ns;
+          pr.seglen = sl;
+        }
+      }
+    }
+    if (best < 0) {   // a box longer than 8 * kSegMax nodes: longest axis, more segments
+      int a = 0;
+      for (int k = 1; k < 3; ++k) a = pr.dim[k] > pr.dim[a] ? k : a;
+      pr.axis = a;
+      pr.nseg = (pr.dim[a] + kSegMax - 1) / kSegMax;
+      pr.seglen = (pr.dim[a] + pr.nseg - 1) / pr.nseg;
+    }
+    pr.nitems = static_cast<int>(volp / pr.dim[pr.axis]) * pr.nseg;
     ntiles = (pr.nitems + 32 * kTileItemsPerLane - 1) / (32 * kTileItemsPerLane);
     pr.ntiles = ntiles;
     pr.kinds = W.kind[i] | (W.kind[j] << 8);
@@ -318,7 +338,18 @@ __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D
       pr.af[k] = static_cast<float>(a - pr.ai[k]);
       pr.bf[k] = static_cast<float>(bb - pr.bi[k]);
     }
-    vol = static_cast<unsigned long long>(pr.dim[0]) * pr.dim[1] * pr.dim[2];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      pr.rta[k] = D.Rt[9 * i + k];
+      pr.rtb[k] = D.Rt[9 * j + k];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      pr.sza[k] = S.size_l[3 * i + k];
+      pr.szb[k] = S.size_l[3 * j + k];
+    }
+    pr.pad[0] = pr.pad[1] = 0;
+    vol = static_cast<unsigned long long>(volp);
     ops = vol * static_cast<unsigned long long>(S.nomops[i] + S.nomops[j]);
     pair_ij[2 * pi] = i;
     pair_ij[2 * pi + 1] = j;

@@ -33,24 +33,57 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarps = 8;  // warps per block of the persistent kernel
 
+// Local sweep axes (u = along the lines, v, w across) and the node-index
+// stride of each (the node index is x-fastest over the pair box).
 struct Local {
-  int ax[3];  // local axes: u = sweep axis, v, w
+  int u, v, w;
+  int su, sv, sw;
 };
+
+__device__ __forceinline__ Local make_local(const PairRec& r) {
+  Local L;
+  L.u = r.axis;
+  L.v = L.u == 2 ? 0 : L.u + 1;
+  L.w = L.v == 2 ? 0 : L.v + 1;
+  const int s1 = r.dim[0], s2 = r.dim[0] * r.dim[1];
+  L.su = L.u == 0 ? 1 : (L.u == 1 ? s1 : s2);
+  L.sv = L.v == 0 ? 1 : (L.v == 1 ? s1 : s2);
+  L.sw = L.w == 0 ? 1 : (L.w == 1 ? s1 : s2);
+  return L;
+}
+
+// (a_u, a_v, a_w) in local axes -> component c of the world vector
+__device__ __forceinline__ float world_comp(int c, const Local& L, float au, float av, float aw) {
+  return c == L.u ? au : (c == L.v ? av : aw);
+}
+
+// floor(a / b) and the remainder for small non-negative ints via an FP32
+// reciprocal, corrected by one step (exact for a < 2^22)
+__device__ __forceinline__ int div_small(int a, int b, float inv_b, int* rem) {
+  int q = static_cast<int>((static_cast<float>(a) + 0.5f) * inv_b);
+  int r = a - q * b;
+  if (r < 0) { --q; r += b; }
+  if (r >= b) { ++q; r -= b; }
+  *rem = r;
+  return q;
+}
 
 // ---------------------------------------------------------------- evaluators
 // Each evaluator holds one particle's geometry for the current tile, in
-// lattice units, relative to the pair box origin.
+// lattice units, relative to the pair box origin; it reads the pair record
+// from shared memory (second = the record's particle j).
 
 struct SphereEval {
   int iu, iv, iw;
   float fu, fv, fw, rad;
   float cnt_u, rv, rw, rho2, ru, q;
   float gu, gv, gw, gl;
-  __device__ void load(const Shapes& S, const Parts&, int p, const int* ci, const float* cf, const Local& L,
-                       float4*) {
-    iu = ci[L.ax[0]]; iv = ci[L.ax[1]]; iw = ci[L.ax[2]];
-    fu = cf[L.ax[0]]; fv = cf[L.ax[1]]; fw = cf[L.ax[2]];
-    rad = S.size_l[3 * p];
+  __device__ void load(const PairRec& r, bool second, const Shapes&, const Parts&, const Local& L, float4*) {
+    const int* ci = second ? r.bi : r.ai;
+    const float* cf = second ? r.bf : r.af;
+    iu = ci[L.u]; iv = ci[L.v]; iw = ci[L.w];
+    fu = cf[L.u]; fv = cf[L.v]; fw = cf[L.w];
+    rad = second ? r.szb[0] : r.sza[0];
     gu = gv = gw = 0.f;
   }
   __device__ __forceinline__ void begin_line(int cv, int cw, int u0) {
@@ -75,9 +108,7 @@ struct SphereEval {
     gv = fmaf(gl, rv, gv);
     gw = fmaf(gl, rw, gw);
   }
-  __device__ void world(float* g, const Local& L) const {
-    g[L.ax[0]] = gu; g[L.ax[1]] = gv; g[L.ax[2]] = gw;
-  }
+  __device__ float world(int c, const Local& L, const PairRec&, bool) const { return world_comp(c, L, gu, gv, gw); }
 };
 
 struct CuboidEval {
@@ -86,17 +117,19 @@ struct CuboidEval {
   float tu[3], tv[3], tw[3], h[3];
   float cnt_u, p[3], y[3], a[3];
   float gb[3];
-  __device__ void load(const Shapes& S, const Parts& D, int pid, const int* ci, const float* cf,
-                       const Local& L, float4*) {
-    iu = ci[L.ax[0]]; iv = ci[L.ax[1]]; iw = ci[L.ax[2]];
-    fu = cf[L.ax[0]]; fv = cf[L.ax[1]]; fw = cf[L.ax[2]];
-    const float* rt = D.Rt + 9 * pid;
+  __device__ void load(const PairRec& r, bool second, const Shapes&, const Parts&, const Local& L, float4*) {
+    const int* ci = second ? r.bi : r.ai;
+    const float* cf = second ? r.bf : r.af;
+    const float* rt = second ? r.rtb : r.rta;
+    const float* sz = second ? r.szb : r.sza;
+    iu = ci[L.u]; iv = ci[L.v]; iw = ci[L.w];
+    fu = cf[L.u]; fv = cf[L.v]; fw = cf[L.w];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      tu[k] = rt[3 * k + L.ax[0]];
-      tv[k] = rt[3 * k + L.ax[1]];
-      tw[k] = rt[3 * k + L.ax[2]];
-      h[k] = S.size_l[3 * pid + k];
+      tu[k] = rt[3 * k + L.u];
+      tv[k] = rt[3 * k + L.v];
+      tw[k] = rt[3 * k + L.w];
+      h[k] = sz[k];
       gb[k] = 0.f;
     }
   }
@@ -126,10 +159,10 @@ struct CuboidEval {
     gb[2] += (!s0 && !s1) ? copysignf(m, y[2]) : 0.f;
   }
   __device__ __forceinline__ void end_line() {}
-  __device__ void world(float* g, const Local& L) const {
-    g[L.ax[0]] = tu[0] * gb[0] + tu[1] * gb[1] + tu[2] * gb[2];
-    g[L.ax[1]] = tv[0] * gb[0] + tv[1] * gb[1] + tv[2] * gb[2];
-    g[L.ax[2]] = tw[0] * gb[0] + tw[1] * gb[1] + tw[2] * gb[2];
+  // world component c of R gb, R^T row k = body axis k in world
+  __device__ float world(int c, const Local&, const PairRec& r, bool second) const {
+    const float* rt = second ? r.rtb : r.rta;
+    return rt[c] * gb[0] + rt[3 + c] * gb[1] + rt[6 + c] * gb[2];
   }
 };
 
@@ -144,8 +177,8 @@ __device__ __forceinline__ int stage_planes(const Shapes& S, const Parts& D, int
     float4 e = make_float4(0.f, 0.f, 0.f, 1e30f);
     if (lane < nf) {
       const float4 w = D.wplane[f0 + lane];
-      const float c[3] = {w.x, w.y, w.z};
-      e = make_float4(c[L.ax[0]], c[L.ax[1]], c[L.ax[2]], w.w);
+      e = make_float4(L.u == 0 ? w.x : (L.u == 1 ? w.y : w.z), L.v == 0 ? w.x : (L.v == 1 ? w.y : w.z),
+                      L.w == 0 ? w.x : (L.w == 1 ? w.y : w.z), w.w);
     }
     sm[lane] = e;
   }
@@ -161,11 +194,13 @@ struct PolyEval {
   float mu[NF], p[NF];
   float cnt_u, ru;
   float gu, gv, gw;
-  __device__ void load(const Shapes& S, const Parts& D, int pid, const int* ci, const float* cf,
-                       const Local& L, float4* sm) {
-    iu = ci[L.ax[0]]; iv = ci[L.ax[1]]; iw = ci[L.ax[2]];
-    fu = cf[L.ax[0]]; fv = cf[L.ax[1]]; fw = cf[L.ax[2]];
-    stage_planes(S, D, pid, L, sm, NF);
+  __device__ void load(const PairRec& r, bool second, const Shapes& S, const Parts& D, const Local& L,
+                       float4* sm) {
+    const int* ci = second ? r.bi : r.ai;
+    const float* cf = second ? r.bf : r.af;
+    iu = ci[L.u]; iv = ci[L.v]; iw = ci[L.w];
+    fu = cf[L.u]; fv = cf[L.v]; fw = cf[L.w];
+    stage_planes(S, D, second ? r.j : r.i, L, sm, NF);
     sp = sm;
 #pragma unroll
     for (int f = 0; f < NF; ++f) mu[f] = sm[f].x;
@@ -203,9 +238,7 @@ struct PolyEval {
     gw = fmaf(m, e.z, gw);
   }
   __device__ __forceinline__ void end_line() {}
-  __device__ void world(float* g, const Local& L) const {
-    g[L.ax[0]] = gu; g[L.ax[1]] = gv; g[L.ax[2]] = gw;
-  }
+  __device__ float world(int c, const Local& L, const PairRec&, bool) const { return world_comp(c, L, gu, gv, gw); }
 };
 
 // Polytopes with more than kRegFaces faces: planes read from shared memory.
@@ -215,11 +248,13 @@ struct PolyGEval {
   const float4* sp;
   float cnt_u, ru, rv, rw;
   float gu, gv, gw;
-  __device__ void load(const Shapes& S, const Parts& D, int pid, const int* ci, const float* cf,
-                       const Local& L, float4* sm) {
-    iu = ci[L.ax[0]]; iv = ci[L.ax[1]]; iw = ci[L.ax[2]];
-    fu = cf[L.ax[0]]; fv = cf[L.ax[1]]; fw = cf[L.ax[2]];
-    nf = stage_planes(S, D, pid, L, sm, kMaxFaces);
+  __device__ void load(const PairRec& r, bool second, const Shapes& S, const Parts& D, const Local& L,
+                       float4* sm) {
+    const int* ci = second ? r.bi : r.ai;
+    const float* cf = second ? r.bf : r.af;
+    iu = ci[L.u]; iv = ci[L.v]; iw = ci[L.w];
+    fu = cf[L.u]; fv = cf[L.v]; fw = cf[L.w];
+    nf = stage_planes(S, D, second ? r.j : r.i, L, sm, kMaxFaces);
     sp = sm;
     gu = gv = gw = 0.f;
   }
@@ -252,68 +287,72 @@ struct PolyGEval {
     gw = fmaf(m, e.z, gw);
   }
   __device__ __forceinline__ void end_line() {}
-  __device__ void world(float* g, const Local& L) const {
-    g[L.ax[0]] = gu; g[L.ax[1]] = gv; g[L.ax[2]] = gw;
-  }
+  __device__ float world(int c, const Local& L, const PairRec&, bool) const { return world_comp(c, L, gu, gv, gw); }
 };
 
 // ---------------------------------------------------------------- tile sweep
 // out[0] = sum W, out[1..3] = sum W c (box axes), out[4..6] = sum (mA gradA -
 // mB gradB) (world), out[7] = deepest -phiA-phiB over W > 0, out[8] = its
-// node index (x fastest) as int bits.
-template <bool SMOOTH, class EA, class EB>
-__device__ __forceinline__ void sweep_tile(const Params& P, const Shapes& S, const Parts& D, const PairRec& pr,
-                                           int pa, const int* cia, const float* cfa, int pb, const int* cib,
-                                           const float* cfb, int tl, float4* smA, float4* smB, float* out) {
+// node index (x fastest) as int bits.  `prefetch` runs once, after the first
+// slot of the tile (it fetches the next tile's record while this one runs).
+template <bool SMOOTH, class EA, class EB, class Pre>
+__device__ __forceinline__ void sweep_tile(const Params& P, const Shapes& S, const Parts& D, const PairRec& r,
+                                           bool swap, int tl, float4* smA, float4* smB, float* out, Pre& prefetch) {
   const int lane = threadIdx.x & 31;
-  Local L;
-  L.ax[0] = pr.axis;
-  L.ax[1] = (pr.axis + 1) % 3;
-  L.ax[2] = (pr.axis + 2) % 3;
+  const Local L = make_local(r);
   EA A;
   EB B;
-  A.load(S, D, pa, cia, cfa, L, smA);
-  B.load(S, D, pb, cib, cfb, L, smB);
-  const int du = pr.dim[L.ax[0]], dv = pr.dim[L.ax[1]];
-  const int nseg = pr.nseg, seglen = pr.seglen;
-  const float inv_w = P.inv_w;
+  A.load(r, swap, S, D, L, smA);
+  B.load(r, !swap, S, D, L, smB);
+  const int du = r.dim[L.u], dv = r.dim[L.v];
+  const int nseg = r.nseg, seglen = r.seglen;
+  const float inv_dv = 1.f / static_cast<float>(dv), inv_nseg = 1.f / static_cast<float>(nseg);
+  const float inv_w = P.inv_w, hw = 0.5f * P.wdx_l;
   float cnt = 0.f, mu = 0.f, mv = 0.f, mw = 0.f, bestf = -FLT_MAX;
   int bestidx = 0x7fffffff;
   const int it0 = tl * 32 * kTileItemsPerLane;
   for (int s = 0; s < kTileItemsPerLane; ++s) {
     const int itb = it0 + s * 32;
-    if (itb >= pr.nitems) break;
+    if (itb >= r.nitems) break;
+    if (s == 1) prefetch();
     const int it = itb + lane;
-    const bool valid = it < pr.nitems;
-    const int line = it / nseg;
-    const int seg = it - line * nseg;
-    const int cv = line % dv, cw = line / dv;
+    const bool valid = it < r.nitems;
+    int seg, cv;
+    const int line = div_small(it, nseg, inv_nseg, &seg);
+    const int cw = div_small(line, dv, inv_dv, &cv);
     const int u0 = seg * seglen;
-    const int u1 = valid ? min(u0 + seglen, du) : u0;
+    const int len = valid ? min(seglen, du - u0) : 0;
     A.begin_line(cv, cw, u0);
     B.begin_line(cv, cw, u0);
     float cl = 0.f, ml = 0.f, bfl = -FLT_MAX, cuf = static_cast<float>(u0);
     int bul = 0;
     for (int k = 0; k < seglen; ++k) {
-      const bool act = (u0 + k) < u1;
+      const bool act = k < len;
       const float fa = A.phi();
       const float fb = B.phi();
-      const float ta = __saturatef(fmaf(fa, -inv_w, 0.5f));
-      const float tb = __saturatef(fmaf(fb, -inv_w, 0.5f));
-      float w, ma, mb;
+      bool any;
       if (SMOOTH) {
-        const float ha = ta * ta * fmaf(-2.f, ta, 3.f);
-        const float hb = tb * tb * fmaf(-2.f, tb, 3.f);
-        w = act ? ha * hb : 0.f;
-        ma = act ? fmaf(-ta, ta, ta) * hb : 0.f;
-        mb = act ? ha * fmaf(-tb, tb, tb) : 0.f;
+        any = act && fa < hw && fb < hw;                       // W > 0 or a band term
       } else {
         const bool ina = fa <= 0.f, inb = fb <= 0.f;
-        w = (act && ina && inb) ? 1.f : 0.f;
-        ma = (act && inb) ? fmaf(-ta, ta, ta) : 0.f;
-        mb = (act && ina) ? fmaf(-tb, tb, tb) : 0.f;
+        any = act && ((ina && inb) || (inb && fabsf(fa) < hw) || (ina && fabsf(fb) < hw));
       }
-      if (__any_sync(kFull, w > 0.f)) {
+      if (__any_sync(kFull, any)) {
+        const float ta = __saturatef(fmaf(fa, -inv_w, 0.5f));
+        const float tb = __saturatef(fmaf(fb, -inv_w, 0.5f));
+        float w, ma, mb;
+        if (SMOOTH) {
+          const float ha = ta * ta * fmaf(-2.f, ta, 3.f);
+          const float hb = tb * tb * fmaf(-2.f, tb, 3.f);
+          w = any ? ha * hb : 0.f;
+          ma = any ? fmaf(-ta, ta, ta) * hb : 0.f;
+          mb = any ? ha * fmaf(-tb, tb, tb) : 0.f;
+        } else {
+          const bool ina = fa <= 0.f, inb = fb <= 0.f;
+          w = (act && ina && inb) ? 1.f : 0.f;
+          ma = (act && inb) ? fmaf(-ta, ta, ta) : 0.f;
+          mb = (act && ina) ? fmaf(-tb, tb, tb) : 0.f;
+        }
         cl += w;
         ml = fmaf(w, cuf, ml);
         const float f = -(fa + fb);
@@ -321,8 +360,6 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Shapes& S, con
           bfl = f;
           bul = u0 + k;
         }
-      }
-      if (__any_sync(kFull, (ma != 0.f) || (mb != 0.f))) {
         A.grad(ma);
         B.grad(mb);
       }
@@ -335,26 +372,20 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Shapes& S, con
     mv = fmaf(cl, static_cast<float>(cv), mv);
     mw = fmaf(cl, static_cast<float>(cw), mw);
     if (bfl > -FLT_MAX) {
-      int c[3];
-      c[L.ax[0]] = bul;
-      c[L.ax[1]] = cv;
-      c[L.ax[2]] = cw;
-      const int idx = c[0] + pr.dim[0] * (c[1] + pr.dim[1] * c[2]);
+      const int idx = bul * L.su + cv * L.sv + cw * L.sw;
       if (bfl > bestf || (bfl == bestf && idx < bestidx)) {
         bestf = bfl;
         bestidx = idx;
       }
     }
   }
-  float ga[3], gb[3], m[3];
-  A.world(ga, L);
-  B.world(gb, L);
-  m[L.ax[0]] = mu;
-  m[L.ax[1]] = mv;
-  m[L.ax[2]] = mw;
+  if (kTileItemsPerLane < 2 || it0 + 32 >= r.nitems) prefetch();   // tiles with a single slot
   out[0] = cnt;
-  out[1] = m[0]; out[2] = m[1]; out[3] = m[2];
-  out[4] = ga[0] - gb[0]; out[5] = ga[1] - gb[1]; out[6] = ga[2] - gb[2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    out[1 + c] = world_comp(c, L, mu, mv, mw);
+    out[4 + c] = A.world(c, L, r, swap) - B.world(c, L, r, !swap);
+  }
   out[7] = bestf;
   out[8] = __int_as_float(bestidx);
 }
@@ -378,23 +409,17 @@ __device__ __forceinline__ void warp_reduce_partials(float* v) {
 // (chosen at init when no polytope is present; fewer registers, no spills).
 enum KindSet : int { SET_ALL = 0, SET_SC = 1 };
 
-template <bool SMOOTH, int SET>
-__device__ __forceinline__ void dispatch(const Params& P, const Shapes& S, const Parts& D, const PairRec& pr,
-                                         int tl, float4* smA, float4* smB, float* out) {
-  int ka = pr.kinds & 0xff, kb = pr.kinds >> 8;
-  int pa = pr.i, pb = pr.j;
-  const int *cia = pr.ai, *cib = pr.bi;
-  const float *cfa = pr.af, *cfb = pr.bf;
-  const bool swap = ka > kb;
+template <bool SMOOTH, int SET, class Pre>
+__device__ __forceinline__ void dispatch(const Params& P, const Shapes& S, const Parts& D, const PairRec& r,
+                                         int tl, float4* smA, float4* smB, float* out, Pre& pre) {
+  int ka = r.kinds & 0xff, kb = r.kinds >> 8;
+  const bool swap = ka > kb;   // evaluate the cheaper kind as A; the normal's sign flips back below
   if (swap) {
     const int t = ka; ka = kb; kb = t;
-    pa = pr.j; pb = pr.i;
-    cia = pr.bi; cib = pr.ai;
-    cfa = pr.bf; cfb = pr.af;
   }
-#define GBC_CASE(KA, KB, TA, TB)                                                                  \
-  case (KA) * 4 + (KB):                                                                          \
-    sweep_tile<SMOOTH, TA, TB>(P, S, D, pr, pa, cia, cfa, pb, cib, cfb, tl, smA, smB, out);      \
+#define GBC_CASE(KA, KB, TA, TB)                                                     \
+  case (KA) * 4 + (KB):                                                             \
+    sweep_tile<SMOOTH, TA, TB>(P, S, D, r, swap, tl, smA, smB, out, pre);           \
     break;
   if constexpr (SET == SET_SC) {
     switch (ka * 4 + kb) {
@@ -402,6 +427,7 @@ __device__ __forceinline__ void dispatch(const Params& P, const Shapes& S, const
       GBC_CASE(0, 1, SphereEval, CuboidEval)
       GBC_CASE(1, 1, CuboidEval, CuboidEval)
       default:
+        pre();
         break;
     }
   } else {
@@ -417,6 +443,7 @@ __device__ __forceinline__ void dispatch(const Params& P, const Shapes& S, const
       GBC_CASE(2, 3, PolyEval<kRegFaces>, PolyGEval)
       GBC_CASE(3, 3, PolyGEval, PolyGEval)
       default:
+        pre();
         break;
     }
   }
@@ -426,22 +453,42 @@ __device__ __forceinline__ void dispatch(const Params& P, const Shapes& S, const
   }
 }
 
+// The warp copies a 224-byte pair record with 14 lanes x 16 bytes.
+__device__ __forceinline__ int4 load_rec_part(const PairRec* src, int lane) {
+  return lane < kPairRecWords / 4 ? reinterpret_cast<const int4*>(src)[lane] : make_int4(0, 0, 0, 0);
+}
+__device__ __forceinline__ void store_rec_part(PairRec* dst, int lane, int4 v) {
+  if (lane < kPairRecWords / 4) reinterpret_cast<int4*>(dst)[lane] = v;
+}
+
 template <bool SMOOTH, int SET>
-__global__ void __launch_bounds__(kWarps * 32, SET == SET_SC ? 3 : 2) k_narrow32(Params P, Shapes S, Parts D,
+__global__ void __launch_bounds__(kWarps * 32, 2) k_narrow32(Params P, Shapes S, Parts D,
                                                                                  Lists W) {
+  __shared__ __align__(16) PairRec s_rec[kWarps][2];
   __shared__ float4 s_planes[kWarps][2][kMaxFaces];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int ntiles = min(W.counters[1], P.max_tiles);
   int t = 0;
   if (lane == 0) t = atomicAdd(&W.counters[2], 1);
   t = __shfl_sync(kFull, t, 0);
+  if (t < ntiles) store_rec_part(&s_rec[wid][0], lane, load_rec_part(W.pairs + W.tile_pair[t], lane));
+  __syncwarp();
+  int buf = 0;
   while (t < ntiles) {
     int tn = 0;
     if (lane == 0) tn = atomicAdd(&W.counters[2], 1);  // next tile, fetched ahead
-    const int p = W.tile_pair[t];
-    const PairRec pr = W.pairs[p];
+    int4 next = make_int4(0, 0, 0, 0);
+    bool fetched = false;
+    auto prefetch = [&]() {
+      if (fetched) return;
+      fetched = true;
+      tn = __shfl_sync(kFull, tn, 0);
+      if (tn < ntiles) next = load_rec_part(W.pairs + W.tile_pair[tn], lane);
+    };
+    const PairRec& r = s_rec[wid][buf];
     float v[9];
-    dispatch<SMOOTH, SET>(P, S, D, pr, t - pr.tile0, s_planes[wid][0], s_planes[wid][1], v);
+    dispatch<SMOOTH, SET>(P, S, D, r, t - r.tile0, s_planes[wid][0], s_planes[wid][1], v, prefetch);
+    prefetch();
     warp_reduce_partials(v);
     if (lane < 9) {
       float x = v[0];
@@ -449,8 +496,11 @@ __global__ void __launch_bounds__(kWarps * 32, SET == SET_SC ? 3 : 2) k_narrow32
       for (int k = 1; k < 9; ++k) x = (lane == k) ? v[k] : x;
       W.partial[static_cast<size_t>(t) * kPartialFloats + lane] = x;
     }
-    t = __shfl_sync(kFull, tn, 0);
     __syncwarp();
+    if (tn < ntiles) store_rec_part(&s_rec[wid][buf ^ 1], lane, next);
+    __syncwarp();
+    buf ^= 1;
+    t = tn;
   }
 }
 
