@@ -183,6 +183,39 @@ int32_t contact_kernels_per_backward(const contact_ctx* ctx);
 
 void contact_destroy(contact_ctx* ctx);
 
+/* Fixed capacity of contact_step_noalloc: the size of its scratch array in
+ * MiB, and the largest particle count and pair capacity it accepts. */
+#define CONTACT_NOALLOC_SCRATCH_MIB 16
+#define CONTACT_NOALLOC_MAX_PARTICLES 2048
+#define CONTACT_NOALLOC_MAX_PAIRS 16384
+
+/* contact_step for callers that cannot allocate device memory (no
+ * counterpart in the paper: it is an interface for such callers, e.g. a host
+ * program whose own pool owns all device memory, or a loop that may not call
+ * the driver's allocator).  No context is created and nothing is allocated:
+ * the step's intermediate buffers live in one static device array of
+ * CONTACT_NOALLOC_SCRATCH_MIB MiB, which every GPU that loads the library
+ * holds until the process exits.
+ *   cfg, shape_type, shape_param, young, poisson   host, as for contact_init;
+ *                     spheres and cuboids only, n_particles <=
+ *                     CONTACT_NOALLOC_MAX_PARTICLES, max_pairs <=
+ *                     CONTACT_NOALLOC_MAX_PAIRS, max_neighbors 0 or 64,
+ *                     precision CONTACT_PRECISION_FP32_TILE; use_graph ignored
+ *   pos, quat, pair_ij, pair_out, n_pairs, force, torque   dev, as for contact_step
+ *   stream            cudaStream_t for all work (NULL: default stream)
+ * Larger sizes, polytopes or other settings return CONTACT_EINVAL before any
+ * work is enqueued.  The call waits for its stream and returns the device's
+ * error (CONTACT_EINVAL for a bad pose, CONTACT_ECAPACITY) directly; velocities
+ * are not taken (ddot_n = 0).  The first call on a device looks up the
+ * array's device address, so make that call before any stream capture.  All
+ * calls share the one array and the set-up clears what must start at zero:
+ * calls whose work overlaps on the GPU (from other threads or streams) race
+ * and must be serialised by the caller. */
+contact_status contact_step_noalloc(const contact_config* cfg, const int32_t* shape_type, const double* shape_param,
+                                    const double* young, const double* poisson, const double* pos,
+                                    const double* quat, int32_t* pair_ij, double* pair_out, int32_t* n_pairs,
+                                    double* force, double* torque, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,7 @@ PAIR_OUT_COLS = 11
 EXPORTS = ["contact_config_default", "contact_init", "contact_step", "contact_backward", "contact_check",
            "contact_clear_error", "contact_last_error", "contact_set_stream", "contact_stats",
            "contact_particle_boxes", "contact_narrow_time", "contact_damping_factor", "contact_kernels_per_step",
-           "contact_kernels_per_backward", "contact_destroy"]
+           "contact_kernels_per_backward", "contact_destroy", "contact_step_noalloc"]
 
 
 class Config(ctypes.Structure):
@@ -96,6 +96,8 @@ def load_library(build_if_missing: bool = True):
     lib.contact_kernels_per_backward.restype = I32
     lib.contact_destroy.argtypes = [P]
     lib.contact_destroy.restype = None
+    lib.contact_step_noalloc.argtypes = [ctypes.POINTER(Config)] + [P] * 12
+    lib.contact_step_noalloc.restype = I32
     _lib = lib
     return lib
 
