@@ -89,6 +89,9 @@ typedef struct {
   int32_t use_graph;        /* 1: contact_step captures its launches in a CUDA graph
                                on first use and replays it while the buffers are
                                the same (not while the stream is being captured)   */
+  int32_t narrow_events;    /* 1: record CUDA events around the node-sweep launch
+                               (read with contact_narrow_time); 0: none, so that
+                               consecutive kernels overlap their launch           */
 } contact_config;
 
 /* Fills *cfg with defaults (sharp indicator, w = 1, no inflation, FP32 tiles,
@@ -166,7 +169,8 @@ contact_status contact_stats(contact_ctx* ctx, int64_t* stats);
 /* Synchronises, then writes the device time in milliseconds of the last
  * step's narrow-phase kernel (the node sweep), measured with CUDA events that
  * contact_step records on the context stream around that launch (also when
- * the step replays a graph).  CONTACT_ESTATE before the first step. */
+ * the step replays a graph) when cfg.narrow_events is 1.  CONTACT_ESTATE
+ * before the first step or with narrow_events off. */
 contact_status contact_narrow_time(contact_ctx* ctx, float* ms);
 
 /* Per-particle node ranges (lo[3], hi[3]) [N,6] i32 dev of the last step. */

@@ -38,7 +38,8 @@ class Config(ctypes.Structure):
                 ("indicator", ctypes.c_int32), ("smooth_width", ctypes.c_double),
                 ("inflate", ctypes.c_double), ("damping_c", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("max_pairs", ctypes.c_int32), ("max_neighbors", ctypes.c_int32),
-                ("max_tiles", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("max_tiles", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("narrow_events", ctypes.c_int32)]
 
 
 class ContactError(RuntimeError):
@@ -120,7 +121,8 @@ class Contact:
 
     def __init__(self, shape_type, shape_param, face_offset, planes, young, poisson, n_cells, dx,
                  indicator=SHARP, smooth_width=1.0, inflate=0.0, damping_c=0.0, precision=FP32_TILE,
-                 max_pairs=None, max_neighbors=64, max_tiles=0, use_graph=True, device=None, stream=None):
+                 max_pairs=None, max_neighbors=64, max_tiles=0, use_graph=True, narrow_events=False,
+                 device=None, stream=None):
         if not torch.cuda.is_available():
             raise ContactError(ECUDA, "no CUDA device: the contact path has no CPU fallback")
         self.lib = load_library()
@@ -134,6 +136,7 @@ class Contact:
         if max_pairs is not None:
             cfg.max_pairs = int(max_pairs)
         cfg.max_neighbors, cfg.max_tiles, cfg.use_graph = int(max_neighbors), int(max_tiles), int(bool(use_graph))
+        cfg.narrow_events = int(bool(narrow_events))
         self.cfg = cfg
         self.n = n
         self.max_pairs = int(cfg.max_pairs)

@@ -17,7 +17,8 @@ namespace gbc {
 
 // Sweep kinds: polytopes with up to 20 faces keep their face values in
 // registers (padded to 20); larger ones (up to 32) read planes from shared memory.
-enum Kind : int { KIND_SPHERE = 0, KIND_CUBOID = 1, KIND_POLY = 2, KIND_POLYG = 3 };
+// Cubes (equal half extents) have their own kind: max|y| - h needs no per-axis offset.
+enum Kind : int { KIND_SPHERE = 0, KIND_CUBOID = 1, KIND_POLY = 2, KIND_POLYG = 3, KIND_CUBE = 4 };
 constexpr int kRegFaces = 20;
 
 constexpr int kMaxFaces = 32;         // faces of one polytope
@@ -45,9 +46,11 @@ struct Params {
   int smooth;            // 1: smoothed indicator
   int precision;         // 0: FP32 tiles, 1: FP64 per pair
   int kind_set;          // 1: only spheres and cuboids (lean node-sweep variant)
+  int dx_pow2;           // 1: dx is a power of two, so x / dx == x * inv_dx exactly
   double damping_c;
   int nbin[3];           // bins per axis
   double binw[3];        // bin width (physical)
+  float inv_binw_f[3];   // FP32 reciprocal of the bin width
   int max_pairs, max_nbr, max_tiles;
   // FP32 copies for the node sweep (lattice units)
   float inflate_l, inv_w, neg6_over_w, wdx_l;   // wdx_l: smoothing width in cells
@@ -65,6 +68,7 @@ struct Shapes {
   const double* poisson;   // [N]
   const float* size_l;     // [N,3] lattice units incl. inflate: sphere r', cuboid h'
   const int* nomops;       // [N] nominal FP32 lane-ops of one signed-distance test
+  const double* compl_;    // [N] (1 - nu^2) / E, so that E* = 1 / (compl_i + compl_j)
 };
 
 // Per-step particle records.
@@ -78,6 +82,9 @@ struct Parts {
   int* slot;       // [N]
   float* Rt;       // [N,9] FP32 R^T (row k = body axis k in world)
   float4* wplane;  // [F] FP32 world normal, offset (lattice units, incl. inflate)
+  float* Xf;       // [N,3] FP32 positions (periodic image choice only)
+  int* kX;         // [N,3] nearest node of X / dx
+  float* fX;       // [N,3] X / dx - kX, in [-1/2, 1/2] (FP64 difference, rounded once)
 };
 
 // One candidate pair (i < j).
@@ -193,6 +200,31 @@ __device__ inline double sdf64(int type, const double* prm, const double* planes
 }
 
 __device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0, code); }
+
+// Programmatic dependent launch: every kernel of a step lets the next one
+// launch at its start, and waits for the previous one (completion and memory
+// visibility) before it reads that kernel's results.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Launch with the programmatic-stream-serialization attribute.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 // --------------------------------------------------------------------------
 // Launch wrappers (defined in the kernel translation units).

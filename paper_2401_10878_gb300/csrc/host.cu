@@ -137,15 +137,14 @@ contact_status check_sticky(contact_ctx* c) {
 void enqueue_step(contact_ctx* c, bool capturing, const double* pos, const double* quat, const double* vel,
                   int32_t* pair_ij, double* pair_out, int32_t* n_pairs, double* force, double* torque) {
   const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-  const int nbins = c->P.nbin[0] * c->P.nbin[1] * c->P.nbin[2];
-  cudaMemsetAsync(c->W.bin_count, 0, sizeof(int) * nbins, c->stream);
+  // bin counts are zero: contact_init clears them, every step's last kernel clears them again
   launch_pose(c->P, c->S, c->D, c->W, pos, quat, c->stream);
   launch_bin_scatter(c->P, c->D, c->W, c->stream);
   launch_broad(c->P, c->D, c->W, c->stream);
   launch_plan(c->P, c->S, c->D, c->W, pair_ij, n_pairs, c->stream);
-  cudaEventRecordWithFlags(c->ev_narrow[0], c->stream, ev_flags);
+  if (c->cfg.narrow_events) cudaEventRecordWithFlags(c->ev_narrow[0], c->stream, ev_flags);
   launch_narrow(c->P, c->S, c->D, c->W, c->grid_narrow, c->stream);
-  cudaEventRecordWithFlags(c->ev_narrow[1], c->stream, ev_flags);
+  if (c->cfg.narrow_events) cudaEventRecordWithFlags(c->ev_narrow[1], c->stream, ev_flags);
   launch_finalize(c->P, c->S, c->D, c->W, vel, pair_out, c->stream);
   launch_particle_sum(c->P, c->D, c->W, force, torque, c->stream);
 }
@@ -168,6 +167,7 @@ void contact_config_default(contact_config* cfg, int32_t n_particles, const int3
   cfg->max_neighbors = 64;
   cfg->max_tiles = 0;
   cfg->use_graph = 1;
+  cfg->narrow_events = 0;
 }
 
 double contact_damping_factor(double e, double u0) {
@@ -229,7 +229,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
         size_l[3 * p + k] = static_cast<float>((param[3 * p + k] + C.inflate) / C.dx);
       }
       circ = std::sqrt(e2);
-      kind[p] = KIND_CUBOID;
+      kind[p] = (param[3 * p] == param[3 * p + 1] && param[3 * p] == param[3 * p + 2]) ? KIND_CUBE : KIND_CUBOID;
       nomops[p] = 15;
     } else if (type[p] == CONTACT_SHAPE_POLYTOPE) {
       const int F = f1 - f0;
@@ -275,15 +275,21 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
     nb = std::min(nb, 256);
     P.nbin[k] = nb;
     P.binw[k] = L[k] / nb;
+    P.inv_binw_f[k] = static_cast<float>(nb / L[k]);
   }
   P.dx = C.dx;
   P.inv_dx = 1.0 / C.dx;
+  {
+    int ex = 0;
+    P.dx_pow2 = std::frexp(C.dx, &ex) == 0.5 ? 1 : 0;
+  }
   P.delta = delta;
   P.inflate = C.inflate;
   P.wdx = C.smooth_width * C.dx;
   P.smooth = C.indicator;
   P.precision = C.precision;
-  P.kind_set = std::all_of(kind.begin(), kind.end(), [](int k) { return k == KIND_SPHERE || k == KIND_CUBOID; }) ? 1 : 0;
+  P.kind_set = std::all_of(kind.begin(), kind.end(),
+                           [](int k) { return k == KIND_SPHERE || k == KIND_CUBOID || k == KIND_CUBE; }) ? 1 : 0;
   P.damping_c = C.damping_c;
   P.max_pairs = C.max_pairs;
   P.max_nbr = max_nbr;
@@ -296,11 +302,13 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   cudaError_t e = cudaSuccess;
   std::vector<double> pl_vec(planes ? planes : nullptr, planes ? planes + 4 * static_cast<size_t>(nfaces) : nullptr);
   std::vector<int> foff(face_offset, face_offset + n + 1);
-  std::vector<double> yv(young, young + n), pv(poisson, poisson + n);
+  std::vector<double> yv(young, young + n), pv(poisson, poisson + n), cv(n);
+  for (int p = 0; p < n; ++p) cv[p] = (1.0 - poisson[p] * poisson[p]) / young[p];
   int *d_type, *d_foff, *d_voff, *d_kind;
   double *d_param, *d_planes, *d_verts, *d_young, *d_pois;
   float* d_size;
   int* d_nomops;
+  double* d_compl;
 #define GBC_TRY(x)                                              \
   do {                                                          \
     e = (x);                                                    \
@@ -320,7 +328,8 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   GBC_TRY(upload(c, &d_pois, pv));
   GBC_TRY(upload(c, &d_size, size_l));
   GBC_TRY(upload(c, &d_nomops, nomops));
-  c->S = Shapes{d_type, d_param, d_foff, d_planes, d_voff, d_verts, d_young, d_pois, d_size, d_nomops};
+  GBC_TRY(upload(c, &d_compl, cv));
+  c->S = Shapes{d_type, d_param, d_foff, d_planes, d_voff, d_verts, d_young, d_pois, d_size, d_nomops, d_compl};
 
   Parts& D = c->D;
   GBC_TRY(dev_alloc(c, &D.X, 3 * static_cast<size_t>(n)));
@@ -332,6 +341,9 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   GBC_TRY(dev_alloc(c, &D.slot, static_cast<size_t>(n)));
   GBC_TRY(dev_alloc(c, &D.Rt, 9 * static_cast<size_t>(n)));
   GBC_TRY(dev_alloc(c, &D.wplane, static_cast<size_t>(std::max(nfaces, 1))));
+  GBC_TRY(dev_alloc(c, &D.Xf, 3 * static_cast<size_t>(n)));
+  GBC_TRY(dev_alloc(c, &D.kX, 3 * static_cast<size_t>(n)));
+  GBC_TRY(dev_alloc(c, &D.fX, 3 * static_cast<size_t>(n)));
 
   Lists& W = c->W;
   const size_t nbins = static_cast<size_t>(P.nbin[0]) * P.nbin[1] * P.nbin[2];
@@ -360,6 +372,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   GBC_TRY(cudaMemset(W.u64, 0, 4 * sizeof(unsigned long long)));
   GBC_TRY(cudaMemset(W.err, 0, sizeof(int)));
   GBC_TRY(cudaMemset(W.up_count, 0, sizeof(int) * n));
+  GBC_TRY(cudaMemset(W.bin_count, 0, sizeof(int) * nbins));
   GBC_TRY(cudaMemset(W.dn_count, 0, sizeof(int) * n));
   GBC_TRY(cudaEventCreate(&c->ev_narrow[0]));
   GBC_TRY(cudaEventCreate(&c->ev_narrow[1]));
@@ -449,6 +462,7 @@ void contact_clear_error(contact_ctx* c) {
   if (c == nullptr) return;
   cudaStreamSynchronize(c->stream);
   cudaMemset(c->W.err, 0, sizeof(int));
+  cudaMemset(c->W.bin_count, 0, sizeof(int) * c->P.nbin[0] * c->P.nbin[1] * c->P.nbin[2]);
   *c->err_host = 0;
   c->last_error = "no error";
 }
@@ -487,6 +501,7 @@ contact_status contact_particle_boxes(contact_ctx* c, int32_t* lo_hi) {
 contact_status contact_narrow_time(contact_ctx* c, float* ms) {
   if (c == nullptr || ms == nullptr) return CONTACT_EINVAL;
   if (!c->have_step) return fail(c, CONTACT_ESTATE, "contact_narrow_time: no step yet");
+  if (!c->cfg.narrow_events) return fail(c, CONTACT_ESTATE, "contact_narrow_time: narrow_events is off");
   cudaError_t e = cudaEventSynchronize(c->ev_narrow[1]);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
   e = cudaEventElapsedTime(ms, c->ev_narrow[0], c->ev_narrow[1]);

@@ -49,6 +49,7 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
 __global__ void __launch_bounds__(128) k_adj_pre(Params P, Shapes S, Parts D, Lists W, AdjBufs B,
                                                  const double* __restrict__ vel, const double* __restrict__ gF,
                                                  const double* __restrict__ gT) {
+  pdl_begin();
   const int np = min(W.counters[0], P.max_pairs);
   if (blockIdx.x == 0 && threadIdx.x == 0) W.counters[6] = 0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
@@ -216,6 +217,7 @@ __device__ __forceinline__ void cross3f(const float a[3], const float b[3], floa
 
 __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, Parts D, Lists W, AdjBufs B) {
   __shared__ float4 s_pl[kWarps][2][kMaxFaces];
+  pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int ntiles = min(W.counters[1], P.max_tiles);
   const float inv_w = P.inv_w;
@@ -318,6 +320,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
 
 // ---------------------------------------------------------------- pair post
 __global__ void __launch_bounds__(128) k_adj_post(Params P, Shapes S, Parts D, Lists W, AdjBufs B) {
+  pdl_begin();
   const int np = min(W.counters[0], P.max_pairs);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
     const PairRec pr = W.pairs[p];
@@ -370,6 +373,7 @@ __global__ void __launch_bounds__(128) k_adj_post(Params P, Shapes S, Parts D, L
 
 __global__ void __launch_bounds__(128) k_adj_scatter(Params P, Parts D, Lists W, AdjBufs B,
                                                      double* __restrict__ gpos, double* __restrict__ gquat) {
+  pdl_begin();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P.n) return;
   const int np = min(W.counters[0], P.max_pairs);
@@ -416,10 +420,10 @@ void launch_adjoint(const Params& P, const Shapes& S, const Parts& D, const List
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int need = (P.max_pairs + 127) / 128;
   const int pgrid = need < 2 * sms ? (need > 0 ? need : 1) : 2 * sms;
-  k_adj_pre<<<pgrid, 128, 0, st>>>(P, S, D, W, B, vel, gF, gT);
-  k_adj_cells<<<grid, kWarps * 32, 0, st>>>(P, S, D, W, B);
-  k_adj_post<<<pgrid, 128, 0, st>>>(P, S, D, W, B);
-  k_adj_scatter<<<(P.n + 127) / 128, 128, 0, st>>>(P, D, W, B, gpos, gquat);
+  launch_pdl(k_adj_pre, dim3(pgrid), dim3(128), 0, st, P, S, D, W, B, vel, gF, gT);
+  launch_pdl(k_adj_cells, dim3(grid), dim3(kWarps * 32), 0, st, P, S, D, W, B);
+  launch_pdl(k_adj_post, dim3(pgrid), dim3(128), 0, st, P, S, D, W, B);
+  launch_pdl(k_adj_scatter, dim3((P.n + 127) / 128), dim3(128), 0, st, P, D, W, B, gpos, gquat);
 }
 
 }  // namespace gbc

@@ -24,6 +24,7 @@ __device__ __forceinline__ int clamp_node(double v) {
 // K1: per particle rotation, node ranges, FP32 sweep geometry and bin slot.
 __global__ void k_pose(Params P, Shapes S, Parts D, Lists W, const double* __restrict__ pos,
                        const double* __restrict__ quat) {
+  pdl_begin();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P.n) return;
   double X[3], q[4];
@@ -78,9 +79,18 @@ __global__ void k_pose(Params P, Shapes S, Parts D, Lists W, const double* __res
   }
   int b[3];
   for (int k = 0; k < 3; ++k) {
-    D.lohi[6 * p + k] = clamp_node(ceil(__ddiv_rn(mn[k], P.dx)));
-    D.lohi[6 * p + 3 + k] = clamp_node(floor(__ddiv_rn(mx[k], P.dx)));
-    b[k] = min(max(static_cast<int>(X[k] / P.binw[k]), 0), P.nbin[k] - 1);
+    // x / dx, exactly as an IEEE division (a multiply when dx is a power of two)
+    const double a = P.dx_pow2 ? dmul(mn[k], P.inv_dx) : __ddiv_rn(mn[k], P.dx);
+    const double c = P.dx_pow2 ? dmul(mx[k], P.inv_dx) : __ddiv_rn(mx[k], P.dx);
+    D.lohi[6 * p + k] = clamp_node(ceil(a));
+    D.lohi[6 * p + 3 + k] = clamp_node(floor(c));
+    const float xf = static_cast<float>(X[k]);
+    D.Xf[3 * p + k] = xf;
+    b[k] = min(max(static_cast<int>(xf * P.inv_binw_f[k]), 0), P.nbin[k] - 1);
+    const double xl = X[k] * P.inv_dx;
+    const double kx = rint(xl);
+    D.kX[3 * p + k] = static_cast<int>(kx);
+    D.fX[3 * p + k] = static_cast<float>(xl - kx);
   }
   // FP32 geometry of the node sweep (lattice units)
   for (int k = 0; k < 3; ++k)
@@ -132,6 +142,7 @@ __device__ long long block_scan_excl(int* data, int n, long long* s_tmp) {
 // K2: bin offsets and particle ids grouped by bin (single CTA).
 __global__ void __launch_bounds__(1024) k_bin_scatter(Params P, Parts D, Lists W) {
   __shared__ long long s_tmp[1024];
+  pdl_begin();
   const int nbins = P.nbin[0] * P.nbin[1] * P.nbin[2];
   for (int i = threadIdx.x; i < nbins; i += blockDim.x) W.bin_start[i] = W.bin_count[i];
   __syncthreads();
@@ -142,16 +153,18 @@ __global__ void __launch_bounds__(1024) k_bin_scatter(Params P, Parts D, Lists W
 }
 
 // Node box of pair (p, q) with q's image nearest p; returns false if empty.
-// The image index s = rint((X_q - X_p) / L) is taken by exact comparisons
-// with L/2 (positions lie in [0, L), so s is -1, 0 or 1; rint's half-way
-// case |X_q - X_p| = L/2 cannot be a candidate because L > 4 R_max).
+// The image index s = rint((X_q - X_p) / L) is taken by comparing the FP32
+// position difference with L/2 (positions lie in [0, L), so s is -1, 0 or 1).
+// It can differ from the exact choice only when |X_q - X_p| is within FP32
+// rounding of L/2; such a pair is no candidate in any image, because every
+// image lies at least L/2 - 1e-3 > 2 R_max away on that axis (L > 4 R_max + 2 dx).
 __device__ __forceinline__ bool pair_box(const Params& P, const Parts& D, int p, int q, int s[3], int lo[3],
                                          int hi[3]) {
   bool hit = true;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const double d = D.X[3 * q + k] - D.X[3 * p + k];
-    const double h = 0.5 * P.L[k];
+    const float d = D.Xf[3 * q + k] - D.Xf[3 * p + k];
+    const float h = 0.5f * static_cast<float>(P.L[k]);
     s[k] = (d > h) ? 1 : ((d < -h) ? -1 : 0);
     lo[k] = max(D.lohi[6 * p + k], D.lohi[6 * q + k] - s[k] * P.ncell[k]);
     hi[k] = min(D.lohi[6 * p + 3 + k], D.lohi[6 * q + 3 + k] - s[k] * P.ncell[k]);
@@ -166,6 +179,7 @@ __device__ __forceinline__ bool pair_box(const Params& P, const Parts& D, int p,
 // above (j > p) and below (j < p); each list is sorted by rank.
 __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
   extern __shared__ int s_buf[];
+  pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int p = blockIdx.x * (blockDim.x >> 5) + wid;
   if (p >= P.n) return;
@@ -255,6 +269,7 @@ __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
 // counts, one CTA) and reset of the step's counters.
 __global__ void __launch_bounds__(1024) k_rows(Params P, Lists W, int32_t* __restrict__ n_pairs_out) {
   __shared__ long long s_tmp[1024];
+  pdl_begin();
   const int n = P.n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) W.row_off[i] = W.up_count[i];
   __syncthreads();
@@ -272,123 +287,129 @@ __global__ void __launch_bounds__(1024) k_rows(Params P, Lists W, int32_t* __res
   }
 }
 
-// K4b: one thread per (particle row i, partner slot r): the pair record of
-// pair row_off[i] + r, its sweep layout and its node tiles.  Tiles are
-// allocated with one atomic per warp; a pair's tiles are contiguous, and its
-// partial sums do not depend on where they land, so results are deterministic.
+// K4b: one warp per particle row i, one lane per partner slot r: the pair
+// record of pair row_off[i] + r, its sweep layout and its node tiles.  Tiles
+// are allocated with one atomic per warp round; a pair's tiles are
+// contiguous, and its partial sums do not depend on where they land, so the
+// results are deterministic.  No FP64: centres come as integer node + FP32
+// remainder from the pose kernel.
 __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D, Lists W,
                                                      int32_t* __restrict__ pair_ij) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
-  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= P.n) return;
   const int cap = P.max_nbr;
-  const int i = static_cast<int>(t / cap), r = static_cast<int>(t % cap);
-  const bool active = i < P.n && r < W.up_count[i] && (W.row_off[i] + r) < P.max_pairs;
-  PairRec pr;
-  int pi = 0, ntiles = 0;
-  unsigned long long vol = 0, ops = 0;
-  if (active) {
-    pi = W.row_off[i] + r;
-    const int j = W.up_list[i * cap + r];
-    int lo[3], hi[3];
-    pair_box(P, D, i, j, pr.shift, lo, hi);
-    pr.i = i;
-    pr.j = j;
+  const int cnt = W.up_count[i], row = W.row_off[i];
+  for (int base = 0; base < cnt; base += 32) {
+    const int r = base + lane;
+    const bool active = r < cnt && (row + r) < P.max_pairs;
+    PairRec pr;
+    int pi = 0, ntiles = 0;
+    unsigned long long vol = 0, ops = 0;
+    if (active) {
+      pi = row + r;
+      const int j = W.up_list[i * cap + r];
+      int lo[3], hi[3];
+      pair_box(P, D, i, j, pr.shift, lo, hi);
+      pr.i = i;
+      pr.j = j;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      pr.lo[k] = lo[k];
-      pr.dim[k] = hi[k] - lo[k] + 1;
-    }
-    // sweep layout: lines along one axis, lines cut into nseg segments; the
-    // choice minimises warp slots x (segment length + 1 for the line set-up)
-    const long long volp = static_cast<long long>(pr.dim[0]) * pr.dim[1] * pr.dim[2];
-    long long best = -1;
-    for (int a = 0; a < 3; ++a) {
-      const int du = pr.dim[a];
-      const long long lines = volp / du;
-      for (int ns = 1; ns <= 8 && ns <= du; ++ns) {
-        const int sl = (du + ns - 1) / ns;
-        if (sl > kSegMax) continue;
-        const long long slots = (lines * ns + 31) / 32;
-        const long long cost = slots * (sl + 1);
-        if (best < 0 || cost < best) {
-          best = cost;
-          pr.axis = a;
-          pr.nseg = ns;
-          pr.seglen = sl;
+      for (int k = 0; k < 3; ++k) {
+        pr.lo[k] = lo[k];
+        pr.dim[k] = hi[k] - lo[k] + 1;
+      }
+      // sweep layout: lines along one axis, lines cut into nseg segments; the
+      // choice minimises warp slots x (segment length + 1 for the line set-up)
+      const long long volp = static_cast<long long>(pr.dim[0]) * pr.dim[1] * pr.dim[2];
+      long long best = -1;
+      for (int a = 0; a < 3; ++a) {
+        const int du = pr.dim[a];
+        const long long lines = volp / du;
+        for (int ns = 1; ns <= 8 && ns <= du; ++ns) {
+          const int sl = (du + ns - 1) / ns;
+          if (sl > kSegMax) continue;
+          const long long slots = (lines * ns + 31) / 32;
+          const long long cost = slots * (sl + 1);
+          if (best < 0 || cost < best) {
+            best = cost;
+            pr.axis = a;
+            pr.nseg = ns;
+            pr.seglen = sl;
+          }
         }
       }
-    }
-    if (best < 0) {   // a box longer than 8 * kSegMax nodes: longest axis, more segments
-      int a = 0;
-      for (int k = 1; k < 3; ++k) a = pr.dim[k] > pr.dim[a] ? k : a;
-      pr.axis = a;
-      pr.nseg = (pr.dim[a] + kSegMax - 1) / kSegMax;
-      pr.seglen = (pr.dim[a] + pr.nseg - 1) / pr.nseg;
-    }
-    pr.nitems = static_cast<int>(volp / pr.dim[pr.axis]) * pr.nseg;
-    ntiles = (pr.nitems + 32 * kTileItemsPerLane - 1) / (32 * kTileItemsPerLane);
-    pr.ntiles = ntiles;
-    pr.kinds = W.kind[i] | (W.kind[j] << 8);
+      if (best < 0) {   // a box longer than 8 * kSegMax nodes: longest axis, more segments
+        int a = 0;
+        for (int k = 1; k < 3; ++k) a = pr.dim[k] > pr.dim[a] ? k : a;
+        pr.axis = a;
+        pr.nseg = (pr.dim[a] + kSegMax - 1) / kSegMax;
+        pr.seglen = (pr.dim[a] + pr.nseg - 1) / pr.nseg;
+      }
+      pr.nitems = static_cast<int>(volp / pr.dim[pr.axis]) * pr.nseg;
+      ntiles = (pr.nitems + 32 * kTileItemsPerLane - 1) / (32 * kTileItemsPerLane);
+      pr.ntiles = ntiles;
+      pr.kinds = W.kind[i] | (W.kind[j] << 8);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const double a = D.X[3 * i + k] * P.inv_dx - lo[k];
-      const double bb = (D.X[3 * j + k] - pr.shift[k] * P.L[k]) * P.inv_dx - lo[k];
-      pr.ai[k] = static_cast<int>(rint(a));
-      pr.bi[k] = static_cast<int>(rint(bb));
-      pr.af[k] = static_cast<float>(a - pr.ai[k]);
-      pr.bf[k] = static_cast<float>(bb - pr.bi[k]);
-    }
+      for (int k = 0; k < 3; ++k) {
+        // X_i / dx - lo and X_j' / dx - lo = (X_j / dx - s n) - lo
+        pr.ai[k] = D.kX[3 * i + k] - lo[k];
+        pr.af[k] = D.fX[3 * i + k];
+        pr.bi[k] = D.kX[3 * j + k] - pr.shift[k] * P.ncell[k] - lo[k];
+        pr.bf[k] = D.fX[3 * j + k];
+      }
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      pr.rta[k] = D.Rt[9 * i + k];
-      pr.rtb[k] = D.Rt[9 * j + k];
-    }
+      for (int k = 0; k < 9; ++k) {
+        pr.rta[k] = D.Rt[9 * i + k];
+        pr.rtb[k] = D.Rt[9 * j + k];
+      }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      pr.sza[k] = S.size_l[3 * i + k];
-      pr.szb[k] = S.size_l[3 * j + k];
+      for (int k = 0; k < 3; ++k) {
+        pr.sza[k] = S.size_l[3 * i + k];
+        pr.szb[k] = S.size_l[3 * j + k];
+      }
+      pr.pad[0] = pr.pad[1] = 0;
+      vol = static_cast<unsigned long long>(volp);
+      ops = vol * static_cast<unsigned long long>(S.nomops[i] + S.nomops[j]);
+      pair_ij[2 * pi] = i;
+      pair_ij[2 * pi + 1] = j;
+      // slot of this pair in j's list of lower partners
+      const int* dl = W.dn_list + static_cast<size_t>(j) * cap;
+      int a0 = 0, a1 = W.dn_count[j];
+      while (a0 < a1) {
+        const int mid = (a0 + a1) >> 1;
+        if (dl[mid] < i) a0 = mid + 1; else a1 = mid;
+      }
+      W.dn_pair[static_cast<size_t>(j) * cap + a0] = pi;
     }
-    pr.pad[0] = pr.pad[1] = 0;
-    vol = static_cast<unsigned long long>(volp);
-    ops = vol * static_cast<unsigned long long>(S.nomops[i] + S.nomops[j]);
-    pair_ij[2 * pi] = i;
-    pair_ij[2 * pi + 1] = j;
-    // slot of this pair in j's list of lower partners
-    const int* dl = W.dn_list + static_cast<size_t>(j) * cap;
-    int a0 = 0, a1 = W.dn_count[j];
-    while (a0 < a1) {
-      const int mid = (a0 + a1) >> 1;
-      if (dl[mid] < i) a0 = mid + 1; else a1 = mid;
+    // warp-aggregated tile allocation and counters
+    int incl = ntiles;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(kFull, incl, d);
+      if (lane >= d) incl += v;
     }
-    W.dn_pair[static_cast<size_t>(j) * cap + a0] = pi;
-  }
-  // warp-aggregated tile allocation and counters
-  int incl = ntiles;
+    unsigned long long wv = vol, wo = ops;
 #pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int v = __shfl_up_sync(kFull, incl, d);
-    if (lane >= d) incl += v;
-  }
-  unsigned long long wv = vol, wo = ops;
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) {
-    wv += __shfl_xor_sync(kFull, wv, d);
-    wo += __shfl_xor_sync(kFull, wo, d);
-  }
-  int base = 0;
-  if (lane == 31 && incl > 0) base = atomicAdd(&W.counters[1], incl);
-  if (lane == 0 && wv > 0) {
-    atomicAdd(&W.u64[0], wv);
-    atomicAdd(&W.u64[1], wo);
-  }
-  base = __shfl_sync(kFull, base, 31);
-  if (active) {
-    pr.tile0 = base + incl - ntiles;
-    W.pairs[pi] = pr;
-    for (int k = 0; k < ntiles; ++k) {
-      const int tt = pr.tile0 + k;
-      if (tt < P.max_tiles) W.tile_pair[tt] = pi;
-      else set_error(W.err, kErrCapacity);
+    for (int d = 16; d > 0; d >>= 1) {
+      wv += __shfl_xor_sync(kFull, wv, d);
+      wo += __shfl_xor_sync(kFull, wo, d);
+    }
+    int tbase = 0;
+    if (lane == 31 && incl > 0) tbase = atomicAdd(&W.counters[1], incl);
+    if (lane == 0 && wv > 0) {
+      atomicAdd(&W.u64[0], wv);
+      atomicAdd(&W.u64[1], wo);
+    }
+    tbase = __shfl_sync(kFull, tbase, 31);
+    if (active) {
+      pr.tile0 = tbase + incl - ntiles;
+      W.pairs[pi] = pr;
+      for (int k = 0; k < ntiles; ++k) {
+        const int tt = pr.tile0 + k;
+        if (tt < P.max_tiles) W.tile_pair[tt] = pi;
+        else set_error(W.err, kErrCapacity);
+      }
     }
   }
 }
@@ -397,27 +418,26 @@ __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D
 
 void launch_pose(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* pos,
                  const double* quat, cudaStream_t st) {
-  const int nb = (P.n + 63) / 64;
-  if (nb > 0) k_pose<<<nb, 64, 0, st>>>(P, S, D, W, pos, quat);
+  const int nb = (P.n + 31) / 32;   // few threads per SM: the FP64 pipe is narrow
+  if (nb > 0) launch_pdl(k_pose, dim3(nb), dim3(32), 0, st, P, S, D, W, pos, quat);
 }
 
 void launch_bin_scatter(const Params& P, const Parts& D, const Lists& W, cudaStream_t st) {
-  k_bin_scatter<<<1, 1024, 0, st>>>(P, D, W);
+  launch_pdl(k_bin_scatter, dim3(1), dim3(1024), 0, st, P, D, W);
 }
 
 void launch_broad(const Params& P, const Parts& D, const Lists& W, cudaStream_t st) {
   const int warps = 8;
   const int nb = (P.n + warps - 1) / warps;
   const size_t smem = static_cast<size_t>(warps) * 2 * P.max_nbr * sizeof(int);
-  if (nb > 0) k_broad<<<nb, warps * 32, smem, st>>>(P, D, W);
+  if (nb > 0) launch_pdl(k_broad, dim3(nb), dim3(warps * 32), smem, st, P, D, W);
 }
 
 void launch_plan(const Params& P, const Shapes& S, const Parts& D, const Lists& W, int32_t* pair_ij, int32_t* n_pairs,
                  cudaStream_t st) {
-  k_rows<<<1, 1024, 0, st>>>(P, W, n_pairs);
-  const long long threads = static_cast<long long>(P.n) * P.max_nbr;
-  const int nb = static_cast<int>((threads + 127) / 128);
-  k_build_pairs<<<nb > 0 ? nb : 1, 128, 0, st>>>(P, S, D, W, pair_ij);
+  launch_pdl(k_rows, dim3(1), dim3(1024), 0, st, P, W, n_pairs);
+  const int nb = (P.n + 3) / 4;   // four particle rows (warps) per block
+  launch_pdl(k_build_pairs, dim3(nb > 0 ? nb : 1), dim3(128), 0, st, P, S, D, W, pair_ij);
 }
 
 }  // namespace gbc

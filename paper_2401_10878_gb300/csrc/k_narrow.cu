@@ -91,11 +91,14 @@ struct SphereEval {
     rw = static_cast<float>(cw - iw) - fw;
     rho2 = fmaf(rv, rv, rw * rw);
     gl = 0.f;
-    cnt_u = static_cast<float>(u0 - iu);
+    cnt_u = static_cast<float>(u0 - iu) - 1.f;
   }
+  // node offset cu - iu of the current node (exact integer in FP32)
+  __device__ __forceinline__ float counter() const { return cnt_u; }
+  __device__ __forceinline__ int origin() const { return iu; }
   __device__ __forceinline__ float phi() {
-    ru = cnt_u - fu;
     cnt_u += 1.f;
+    ru = cnt_u - fu;
     q = fmaf(ru, ru, rho2);
     return sqrtf(q) - rad;
   }
@@ -136,16 +139,19 @@ struct CuboidEval {
   __device__ __forceinline__ void begin_line(int cv, int cw, int u0) {
     const float rv = static_cast<float>(cv - iv) - fv;
     const float rw = static_cast<float>(cw - iw) - fw;
+    // y_k = tu_k (m - fu) + tv_k rv + tw_k rw with m = cu - iu: the constant
+    // part is folded once per line, a node costs one FMA per axis
 #pragma unroll
-    for (int k = 0; k < 3; ++k) p[k] = fmaf(tv[k], rv, tw[k] * rw);
-    cnt_u = static_cast<float>(u0 - iu);
+    for (int k = 0; k < 3; ++k) p[k] = fmaf(-tu[k], fu, fmaf(tv[k], rv, tw[k] * rw));
+    cnt_u = static_cast<float>(u0 - iu) - 1.f;
   }
+  __device__ __forceinline__ float counter() const { return cnt_u; }
+  __device__ __forceinline__ int origin() const { return iu; }
   __device__ __forceinline__ float phi() {
-    const float ru = cnt_u - fu;
     cnt_u += 1.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      y[k] = fmaf(tu[k], ru, p[k]);
+      y[k] = fmaf(tu[k], cnt_u, p[k]);
       a[k] = fabsf(y[k]) - h[k];
     }
     return fmaxf(a[0], fmaxf(a[1], a[2]));
@@ -160,6 +166,58 @@ struct CuboidEval {
   }
   __device__ __forceinline__ void end_line() {}
   // world component c of R gb, R^T row k = body axis k in world
+  __device__ float world(int c, const Local&, const PairRec& r, bool second) const {
+    const float* rt = second ? r.rtb : r.rta;
+    return rt[c] * gb[0] + rt[3 + c] * gb[1] + rt[6 + c] * gb[2];
+  }
+};
+
+// Cube (equal half extents h): phi = max_k |y_k| - h.
+struct CubeEval {
+  int iu, iv, iw;
+  float fu, fv, fw;
+  float tu[3], tv[3], tw[3], h;
+  float cnt_u, p[3], y[3];
+  float gb[3];
+  __device__ void load(const PairRec& r, bool second, const Shapes&, const Parts&, const Local& L, float4*) {
+    const int* ci = second ? r.bi : r.ai;
+    const float* cf = second ? r.bf : r.af;
+    const float* rt = second ? r.rtb : r.rta;
+    iu = ci[L.u]; iv = ci[L.v]; iw = ci[L.w];
+    fu = cf[L.u]; fv = cf[L.v]; fw = cf[L.w];
+    h = second ? r.szb[0] : r.sza[0];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      tu[k] = rt[3 * k + L.u];
+      tv[k] = rt[3 * k + L.v];
+      tw[k] = rt[3 * k + L.w];
+      gb[k] = 0.f;
+    }
+  }
+  __device__ __forceinline__ void begin_line(int cv, int cw, int u0) {
+    const float rv = static_cast<float>(cv - iv) - fv;
+    const float rw = static_cast<float>(cw - iw) - fw;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) p[k] = fmaf(-tu[k], fu, fmaf(tv[k], rv, tw[k] * rw));
+    cnt_u = static_cast<float>(u0 - iu) - 1.f;
+  }
+  __device__ __forceinline__ float counter() const { return cnt_u; }
+  __device__ __forceinline__ int origin() const { return iu; }
+  __device__ __forceinline__ float phi() {
+    cnt_u += 1.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) y[k] = fmaf(tu[k], cnt_u, p[k]);
+    return fmaxf(fabsf(y[0]), fmaxf(fabsf(y[1]), fabsf(y[2]))) - h;
+  }
+  __device__ __forceinline__ void grad(float m) {
+    const float a0 = fabsf(y[0]), a1 = fabsf(y[1]), a2 = fabsf(y[2]);
+    const bool s0 = a0 >= a1 && a0 >= a2;
+    const bool s1 = !s0 && a1 >= a2;
+    gb[0] += s0 ? copysignf(m, y[0]) : 0.f;
+    gb[1] += s1 ? copysignf(m, y[1]) : 0.f;
+    gb[2] += (!s0 && !s1) ? copysignf(m, y[2]) : 0.f;
+  }
+  __device__ __forceinline__ void end_line() {}
   __device__ float world(int c, const Local&, const PairRec& r, bool second) const {
     const float* rt = second ? r.rtb : r.rta;
     return rt[c] * gb[0] + rt[3 + c] * gb[1] + rt[6 + c] * gb[2];
@@ -212,24 +270,25 @@ struct PolyEval {
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       const float4 e = sp[f];
-      p[f] = fmaf(e.y, rv, fmaf(e.z, rw, -e.w));
+      p[f] = fmaf(-e.x, fu, fmaf(e.y, rv, fmaf(e.z, rw, -e.w)));
     }
-    cnt_u = static_cast<float>(u0 - iu);
+    cnt_u = static_cast<float>(u0 - iu) - 1.f;
   }
+  __device__ __forceinline__ float counter() const { return cnt_u; }
+  __device__ __forceinline__ int origin() const { return iu; }
   __device__ __forceinline__ float phi() {
-    ru = cnt_u - fu;
     cnt_u += 1.f;
-    float best = fmaf(mu[0], ru, p[0]);
+    float best = fmaf(mu[0], cnt_u, p[0]);
 #pragma unroll
-    for (int f = 1; f < NF; ++f) best = fmaxf(best, fmaf(mu[f], ru, p[f]));
+    for (int f = 1; f < NF; ++f) best = fmaxf(best, fmaf(mu[f], cnt_u, p[f]));
     return best;
   }
   __device__ __forceinline__ void grad(float m) {
     int k = 0;
-    float best = fmaf(mu[0], ru, p[0]);
+    float best = fmaf(mu[0], cnt_u, p[0]);
 #pragma unroll
     for (int f = 1; f < NF; ++f) {
-      const float v = fmaf(mu[f], ru, p[f]);
+      const float v = fmaf(mu[f], cnt_u, p[f]);
       if (v > best) { best = v; k = f; }
     }
     const float4 e = sp[k];
@@ -261,15 +320,17 @@ struct PolyGEval {
   __device__ __forceinline__ void begin_line(int cv, int cw, int u0) {
     rv = static_cast<float>(cv - iv) - fv;
     rw = static_cast<float>(cw - iw) - fw;
-    cnt_u = static_cast<float>(u0 - iu);
+    cnt_u = static_cast<float>(u0 - iu) - 1.f;
   }
+  __device__ __forceinline__ float counter() const { return cnt_u; }
+  __device__ __forceinline__ int origin() const { return iu; }
   __device__ __forceinline__ float value(int f) const {
     const float4 e = sp[f];
     return fmaf(e.x, ru, fmaf(e.y, rv, fmaf(e.z, rw, -e.w)));
   }
   __device__ __forceinline__ float phi() {
-    ru = cnt_u - fu;
     cnt_u += 1.f;
+    ru = cnt_u - fu;
     float best = value(0);
     for (int f = 1; f < nf; ++f) best = fmaxf(best, value(f));
     return best;
@@ -291,13 +352,25 @@ struct PolyGEval {
 };
 
 // ---------------------------------------------------------------- tile sweep
-// out[0] = sum W, out[1..3] = sum W c (box axes), out[4..6] = sum (mA gradA -
-// mB gradB) (world), out[7] = deepest -phiA-phiB over W > 0, out[8] = its
-// node index (x fastest) as int bits.  `prefetch` runs once, after the first
-// slot of the tile (it fetches the next tile's record while this one runs).
+// Per-lane partials of a tile: node count and first moments (exact integers
+// in sharp mode), the band sum of the normal, and the deepest node.
+struct Partial {
+  float cnt, mx, my, mz, gx, gy, gz, bestf;
+  int bestidx;
+};
+
+// Order-preserving map of FP32 values to signed ints (for integer max).
+__device__ __forceinline__ int float_key(float f) {
+  const int b = __float_as_int(f);
+  return b >= 0 ? b : (b ^ 0x7fffffff);
+}
+__device__ __forceinline__ float key_float(int k) { return __int_as_float(k >= 0 ? k : (k ^ 0x7fffffff)); }
+
+// `prefetch` runs once, after the first slot of the tile (it fetches the next
+// tile's record while this one runs).
 template <bool SMOOTH, class EA, class EB, class Pre>
-__device__ __forceinline__ void sweep_tile(const Params& P, const Shapes& S, const Parts& D, const PairRec& r,
-                                           bool swap, int tl, float4* smA, float4* smB, float* out, Pre& prefetch) {
+__device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, const Parts& D, const PairRec& r,
+                                              bool swap, int tl, float4* smA, float4* smB, Pre& prefetch) {
   const int lane = threadIdx.x & 31;
   const Local L = make_local(r);
   EA A;
@@ -324,19 +397,15 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Shapes& S, con
     const int len = valid ? min(seglen, du - u0) : 0;
     A.begin_line(cv, cw, u0);
     B.begin_line(cv, cw, u0);
-    float cl = 0.f, ml = 0.f, bfl = -FLT_MAX, cuf = static_cast<float>(u0);
+    float cl = 0.f, ml = 0.f, bfl = -FLT_MAX;
     int bul = 0;
+#pragma unroll 2
     for (int k = 0; k < seglen; ++k) {
-      const bool act = k < len;
       const float fa = A.phi();
       const float fb = B.phi();
-      bool any;
-      if (SMOOTH) {
-        any = act && fa < hw && fb < hw;                       // W > 0 or a band term
-      } else {
-        const bool ina = fa <= 0.f, inb = fb <= 0.f;
-        any = act && ((ina && inb) || (inb && fabsf(fa) < hw) || (ina && fabsf(fb) < hw));
-      }
+      const float hi = fmaxf(fa, fb);
+      // W > 0, or a band term of the normal: max < w/2 and (sharp) min <= 0
+      const bool any = (k < len) && hi < hw && (SMOOTH || fminf(fa, fb) <= 0.f);
       if (__any_sync(kFull, any)) {
         const float ta = __saturatef(fmaf(fa, -inv_w, 0.5f));
         const float tb = __saturatef(fmaf(fb, -inv_w, 0.5f));
@@ -348,13 +417,12 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Shapes& S, con
           ma = any ? fmaf(-ta, ta, ta) * hb : 0.f;
           mb = any ? ha * fmaf(-tb, tb, tb) : 0.f;
         } else {
-          const bool ina = fa <= 0.f, inb = fb <= 0.f;
-          w = (act && ina && inb) ? 1.f : 0.f;
-          ma = (act && inb) ? fmaf(-ta, ta, ta) : 0.f;
-          mb = (act && ina) ? fmaf(-tb, tb, tb) : 0.f;
+          w = (any && hi <= 0.f) ? 1.f : 0.f;
+          ma = (any && fb <= 0.f) ? fmaf(-ta, ta, ta) : 0.f;
+          mb = (any && fa <= 0.f) ? fmaf(-tb, tb, tb) : 0.f;
         }
         cl += w;
-        ml = fmaf(w, cuf, ml);
+        ml = fmaf(w, A.counter(), ml);   // sum of W (cu - iu_A)
         const float f = -(fa + fb);
         if (w > 0.f && f > bfl) {
           bfl = f;
@@ -363,12 +431,11 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Shapes& S, con
         A.grad(ma);
         B.grad(mb);
       }
-      cuf += 1.f;
     }
     A.end_line();
     B.end_line();
     cnt += cl;
-    mu += ml;
+    mu = fmaf(cl, static_cast<float>(A.origin()), mu + ml);
     mv = fmaf(cl, static_cast<float>(cv), mv);
     mw = fmaf(cl, static_cast<float>(cw), mw);
     if (bfl > -FLT_MAX) {
@@ -380,29 +447,53 @@ __device__ __forceinline__ void sweep_tile(const Params& P, const Shapes& S, con
     }
   }
   if (kTileItemsPerLane < 2 || it0 + 32 >= r.nitems) prefetch();   // tiles with a single slot
-  out[0] = cnt;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    out[1 + c] = world_comp(c, L, mu, mv, mw);
-    out[4 + c] = A.world(c, L, r, swap) - B.world(c, L, r, !swap);
-  }
-  out[7] = bestf;
-  out[8] = __int_as_float(bestidx);
+  Partial o;
+  o.cnt = cnt;
+  o.mx = world_comp(0, L, mu, mv, mw);
+  o.my = world_comp(1, L, mu, mv, mw);
+  o.mz = world_comp(2, L, mu, mv, mw);
+  o.gx = A.world(0, L, r, swap) - B.world(0, L, r, !swap);
+  o.gy = A.world(1, L, r, swap) - B.world(1, L, r, !swap);
+  o.gz = A.world(2, L, r, swap) - B.world(2, L, r, !swap);
+  o.bestf = bestf;
+  o.bestidx = bestidx;
+  return o;
 }
 
-__device__ __forceinline__ void warp_reduce_partials(float* v) {
+__device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-    for (int k = 0; k < 7; ++k) v[k] += __shfl_xor_sync(kFull, v[k], off);
-    const float of = __shfl_xor_sync(kFull, v[7], off);
-    const int oi = __shfl_xor_sync(kFull, __float_as_int(v[8]), off);
-    const int mi = __float_as_int(v[8]);
-    if (of > v[7] || (of == v[7] && oi < mi)) {
-      v[7] = of;
-      v[8] = __int_as_float(oi);
-    }
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+  return v;
+}
+
+// Tile reduction.  Sharp mode: counts and moments are exact integers, summed
+// with integer warp reductions; the deepest node via an integer max of an
+// order-preserving key and an integer min of the node index among the ties.
+template <bool SMOOTH>
+__device__ __forceinline__ void reduce_and_store(const Partial& o, float* dst) {
+  const int lane = threadIdx.x & 31;
+  float c, x, y, z;
+  if (SMOOTH) {
+    c = warp_sum(o.cnt); x = warp_sum(o.mx); y = warp_sum(o.my); z = warp_sum(o.mz);
+  } else {
+    c = static_cast<float>(__reduce_add_sync(kFull, __float2int_rn(o.cnt)));
+    x = static_cast<float>(__reduce_add_sync(kFull, __float2int_rn(o.mx)));
+    y = static_cast<float>(__reduce_add_sync(kFull, __float2int_rn(o.my)));
+    z = static_cast<float>(__reduce_add_sync(kFull, __float2int_rn(o.mz)));
   }
+  const float gx = warp_sum(o.gx), gy = warp_sum(o.gy), gz = warp_sum(o.gz);
+  const int key = __reduce_max_sync(kFull, float_key(o.bestf));
+  const int idx = __reduce_min_sync(kFull, float_key(o.bestf) == key ? o.bestidx : 0x7fffffff);
+  float v = c;
+  v = lane == 1 ? x : v;
+  v = lane == 2 ? y : v;
+  v = lane == 3 ? z : v;
+  v = lane == 4 ? gx : v;
+  v = lane == 5 ? gy : v;
+  v = lane == 6 ? gz : v;
+  v = lane == 7 ? key_float(key) : v;
+  v = lane == 8 ? __int_as_float(idx) : v;
+  if (lane < 9) dst[lane] = v;
 }
 
 // Kernel variants: the full set of pair kinds, or spheres and cuboids only
@@ -410,28 +501,38 @@ __device__ __forceinline__ void warp_reduce_partials(float* v) {
 enum KindSet : int { SET_ALL = 0, SET_SC = 1 };
 
 template <bool SMOOTH, int SET, class Pre>
-__device__ __forceinline__ void dispatch(const Params& P, const Shapes& S, const Parts& D, const PairRec& r,
-                                         int tl, float4* smA, float4* smB, float* out, Pre& pre) {
+__device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, const Parts& D, const PairRec& r,
+                                            int tl, float4* smA, float4* smB, Pre& pre) {
+  // kind order for canonical pairs: sphere < cube < cuboid < polytope < large polytope
+  constexpr int rank[5] = {0, 2, 3, 4, 1};
   int ka = r.kinds & 0xff, kb = r.kinds >> 8;
-  const bool swap = ka > kb;   // evaluate the cheaper kind as A; the normal's sign flips back below
+  const bool swap = rank[ka] > rank[kb];   // evaluate the cheaper kind as A; G's sign flips back below
   if (swap) {
     const int t = ka; ka = kb; kb = t;
   }
-#define GBC_CASE(KA, KB, TA, TB)                                                     \
-  case (KA) * 4 + (KB):                                                             \
-    sweep_tile<SMOOTH, TA, TB>(P, S, D, r, swap, tl, smA, smB, out, pre);           \
+  if (SET == SET_ALL) {   // the full variant sweeps cubes as cuboids
+    ka = ka == KIND_CUBE ? KIND_CUBOID : ka;
+    kb = kb == KIND_CUBE ? KIND_CUBOID : kb;
+  }
+  Partial o{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -FLT_MAX, 0x7fffffff};
+#define GBC_CASE(KA, KB, TA, TB)                                                  \
+  case (KA) * 8 + (KB):                                                          \
+    o = sweep_tile<SMOOTH, TA, TB>(P, S, D, r, swap, tl, smA, smB, pre);         \
     break;
   if constexpr (SET == SET_SC) {
-    switch (ka * 4 + kb) {
+    switch (ka * 8 + kb) {
       GBC_CASE(0, 0, SphereEval, SphereEval)
+      GBC_CASE(0, 4, SphereEval, CubeEval)
       GBC_CASE(0, 1, SphereEval, CuboidEval)
+      GBC_CASE(4, 4, CubeEval, CubeEval)
+      GBC_CASE(4, 1, CubeEval, CuboidEval)
       GBC_CASE(1, 1, CuboidEval, CuboidEval)
       default:
         pre();
         break;
     }
   } else {
-    switch (ka * 4 + kb) {
+    switch (ka * 8 + kb) {
       GBC_CASE(0, 0, SphereEval, SphereEval)
       GBC_CASE(0, 1, SphereEval, CuboidEval)
       GBC_CASE(0, 2, SphereEval, PolyEval<kRegFaces>)
@@ -449,8 +550,9 @@ __device__ __forceinline__ void dispatch(const Params& P, const Shapes& S, const
   }
 #undef GBC_CASE
   if (swap) {
-    out[4] = -out[4]; out[5] = -out[5]; out[6] = -out[6];
+    o.gx = -o.gx; o.gy = -o.gy; o.gz = -o.gz;
   }
+  return o;
 }
 
 // The warp copies a 224-byte pair record with 14 lanes x 16 bytes.
@@ -466,6 +568,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_narrow32(Params P, Shapes S,
                                                                                  Lists W) {
   __shared__ __align__(16) PairRec s_rec[kWarps][2];
   __shared__ float4 s_planes[kWarps][2][kMaxFaces];
+  pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int ntiles = min(W.counters[1], P.max_tiles);
   int t = 0;
@@ -486,16 +589,9 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_narrow32(Params P, Shapes S,
       if (tn < ntiles) next = load_rec_part(W.pairs + W.tile_pair[tn], lane);
     };
     const PairRec& r = s_rec[wid][buf];
-    float v[9];
-    dispatch<SMOOTH, SET>(P, S, D, r, t - r.tile0, s_planes[wid][0], s_planes[wid][1], v, prefetch);
+    const Partial o = dispatch<SMOOTH, SET>(P, S, D, r, t - r.tile0, s_planes[wid][0], s_planes[wid][1], prefetch);
     prefetch();
-    warp_reduce_partials(v);
-    if (lane < 9) {
-      float x = v[0];
-#pragma unroll
-      for (int k = 1; k < 9; ++k) x = (lane == k) ? v[k] : x;
-      W.partial[static_cast<size_t>(t) * kPartialFloats + lane] = x;
-    }
+    reduce_and_store<SMOOTH>(o, W.partial + static_cast<size_t>(t) * kPartialFloats);
     __syncwarp();
     if (tn < ntiles) store_rec_part(&s_rec[wid][buf ^ 1], lane, next);
     __syncwarp();
@@ -510,6 +606,7 @@ __global__ void __launch_bounds__(256) k_narrow64(Params P, Shapes S, Parts D, L
   __shared__ double s_red[8][8];
   __shared__ double s_bf[8];
   __shared__ int s_bi[8];
+  pdl_begin();
   const int np = min(W.counters[0], P.max_pairs);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int p = blockIdx.x; p < np; p += gridDim.x) {
@@ -608,18 +705,18 @@ int narrow_grid(const Params& P) {
 void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists& W, int grid, cudaStream_t st) {
   if (P.precision == 1) {
     if (P.smooth)
-      k_narrow64<true><<<grid, 256, 0, st>>>(P, S, D, W);
+      launch_pdl(k_narrow64<true>, dim3(grid), dim3(256), 0, st, P, S, D, W);
     else
-      k_narrow64<false><<<grid, 256, 0, st>>>(P, S, D, W);
+      launch_pdl(k_narrow64<false>, dim3(grid), dim3(256), 0, st, P, S, D, W);
     return;
   }
   const int b = kWarps * 32;
   if (P.smooth) {
-    if (P.kind_set) k_narrow32<true, SET_SC><<<grid, b, 0, st>>>(P, S, D, W);
-    else k_narrow32<true, SET_ALL><<<grid, b, 0, st>>>(P, S, D, W);
+    if (P.kind_set) launch_pdl(k_narrow32<true, SET_SC>, dim3(grid), dim3(b), 0, st, P, S, D, W);
+    else launch_pdl(k_narrow32<true, SET_ALL>, dim3(grid), dim3(b), 0, st, P, S, D, W);
   } else {
-    if (P.kind_set) k_narrow32<false, SET_SC><<<grid, b, 0, st>>>(P, S, D, W);
-    else k_narrow32<false, SET_ALL><<<grid, b, 0, st>>>(P, S, D, W);
+    if (P.kind_set) launch_pdl(k_narrow32<false, SET_SC>, dim3(grid), dim3(b), 0, st, P, S, D, W);
+    else launch_pdl(k_narrow32<false, SET_ALL>, dim3(grid), dim3(b), 0, st, P, S, D, W);
   }
 }
 

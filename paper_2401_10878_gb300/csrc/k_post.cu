@@ -20,55 +20,89 @@ __device__ __forceinline__ void cross(const double a[3], const double b[3], doub
   c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-// K6: one thread per pair.  FP64 sums of the tile partials in tile order (or
-// the FP64 kernel's sums), then contact point, normal, depth, force, torques.
-__global__ void __launch_bounds__(64) k_finalize(Params P, Shapes S, Parts D, Lists W,
-                                                  const double* __restrict__ vel, double* __restrict__ pair_out) {
+// K6: FP64 per-pair reduction and force law.  Every lane first sums its
+// pair's tile partials in FP64 (tile order) and writes zeros for pairs without
+// overlap; the overlapping pairs of the block are then compacted so that the
+// FP64-heavy part (on GB300 every FP64 warp instruction occupies the SM's
+// narrow FP64 pipe, however many lanes are active) runs with full warps.
+constexpr int kFinBlock = 64;
+
+__global__ void __launch_bounds__(kFinBlock) k_finalize(Params P, Shapes S, Parts D, Lists W,
+                                                        const double* __restrict__ vel,
+                                                        double* __restrict__ pair_out) {
+  __shared__ double s_sum[kFinBlock][9];
+  __shared__ int s_pair[kFinBlock];
+  __shared__ int s_count;
+  pdl_begin();
   const int np = min(W.counters[0], P.max_pairs);
   const bool tiles_ok = P.precision == 1 || W.counters[1] <= P.max_tiles;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
-    const PairRec pr = W.pairs[p];
-    double s[9] = {0, 0, 0, 0, 0, 0, 0, -DBL_MAX, 0};
-    if (P.precision == 1) {
-      const double* q = W.sums + static_cast<size_t>(p) * kSumDoubles;
-      for (int k = 0; k < 9; ++k) s[k] = q[k];
-    } else if (tiles_ok) {
-      int bi = 0x7fffffff;
-      float bf = -FLT_MAX;
-      for (int t = pr.tile0; t < pr.tile0 + pr.ntiles; ++t) {
-        const float* q = W.partial + static_cast<size_t>(t) * kPartialFloats;
-        for (int k = 0; k < 7; ++k) s[k] += static_cast<double>(q[k]);
-        const int qi = __float_as_int(q[8]);
-        if (q[7] > bf || (q[7] == bf && qi < bi)) { bf = q[7]; bi = qi; }
+  const int tid = threadIdx.x;
+  for (int base = blockIdx.x * kFinBlock; base < np; base += gridDim.x * kFinBlock) {
+    if (tid == 0) s_count = 0;
+    __syncthreads();
+    const int p = base + tid;
+    if (p < np) {
+      double s[9] = {0, 0, 0, 0, 0, 0, 0, -DBL_MAX, 0};
+      if (P.precision == 1) {
+        const double* q = W.sums + static_cast<size_t>(p) * kSumDoubles;
+        for (int k = 0; k < 9; ++k) s[k] = q[k];
+      } else if (tiles_ok) {
+        const PairRec& pr = W.pairs[p];
+        const int t0 = pr.tile0, t1 = pr.tile0 + pr.ntiles;
+        int bi = 0x7fffffff;
+        float bf = -FLT_MAX;
+        for (int t = t0; t < t1; ++t) {
+          const float* q = W.partial + static_cast<size_t>(t) * kPartialFloats;
+          for (int k = 0; k < 7; ++k) s[k] += static_cast<double>(q[k]);
+          const int qi = __float_as_int(q[8]);
+          if (q[7] > bf || (q[7] == bf && qi < bi)) { bf = q[7]; bi = qi; }
+        }
+        s[7] = bf;
+        s[8] = static_cast<double>(bi);
       }
-      s[7] = bf;
-      s[8] = static_cast<double>(bi);
+      if (s[0] > 0.0 && s[7] > -DBL_MAX) {
+        const int at = atomicAdd(&s_count, 1);
+        s_pair[at] = p;
+        for (int k = 0; k < 9; ++k) s_sum[at][k] = s[k];
+      } else {
+        double* o = pair_out + static_cast<size_t>(p) * 11;
+        for (int k = 0; k < 11; ++k) o[k] = 0.0;
+        double* f = W.ft + static_cast<size_t>(p) * kFtDoubles;
+        for (int k = 0; k < kFtDoubles; ++k) f[k] = 0.0;
+        double* tp = W.tape + static_cast<size_t>(p) * kTapeDoubles;
+        for (int k = 0; k < kTapeDoubles; ++k) tp[k] = 0.0;
+      }
     }
-    const int i = pr.i, j = pr.j;
-    double XA[3], XB[3];
-    for (int k = 0; k < 3; ++k) {
-      XA[k] = D.X[3 * i + k];
-      XB[k] = D.X[3 * j + k] - pr.shift[k] * P.L[k];
-    }
-    const double dx = P.dx;
-    const double V = dx * dx * dx * s[0];
-    double out[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    double ft[kFtDoubles] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    double tape[kTapeDoubles] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    if (V > 0.0 && s[7] > -DBL_MAX) {
+    __syncthreads();
+    if (tid < s_count) {
+      const int q = s_pair[tid];
+      double s[9];
+      for (int k = 0; k < 9; ++k) s[k] = s_sum[tid][k];
+      const PairRec& pr = W.pairs[q];
+      const int i = pr.i, j = pr.j;
+      double XA[3], XB[3];
+      for (int k = 0; k < 3; ++k) {
+        XA[k] = D.X[3 * i + k];
+        XB[k] = D.X[3 * j + k] - pr.shift[k] * P.L[k];
+      }
+      const double dx = P.dx;
+      const double V = dx * dx * dx * s[0];
+      const double inv_s0 = 1.0 / s[0];
       double xc[3], G[3], n[3];
-      for (int k = 0; k < 3; ++k) xc[k] = (pr.lo[k] + s[1 + k] / s[0]) * dx;
+      for (int k = 0; k < 3; ++k) xc[k] = (pr.lo[k] + s[1 + k] * inv_s0) * dx;
       const double gscale = 0.5 * dx * dx * 6.0 / (P.wdx / dx);
       for (int k = 0; k < 3; ++k) G[k] = gscale * s[4 + k];
       const double gn = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
       double fallback = 0.0;
       if (gn > 1e-12 * dx * dx) {
-        for (int k = 0; k < 3; ++k) n[k] = G[k] / gn;
+        const double inv = 1.0 / gn;
+        for (int k = 0; k < 3; ++k) n[k] = G[k] * inv;
       } else {
         fallback = 1.0;
         const double dX[3] = {XB[0] - XA[0], XB[1] - XA[1], XB[2] - XA[2]};
         const double nd = sqrt(dX[0] * dX[0] + dX[1] * dX[1] + dX[2] * dX[2]);
-        for (int k = 0; k < 3; ++k) n[k] = nd > 0.0 ? dX[k] / nd : 0.0;
+        const double inv = nd > 0.0 ? 1.0 / nd : 0.0;
+        for (int k = 0; k < 3; ++k) n[k] = dX[k] * inv;
       }
       // indentation depth: FP64 re-evaluation at the deepest node
       const int vol = pr.dim[0] * pr.dim[1] * pr.dim[2];
@@ -81,14 +115,16 @@ __global__ void __launch_bounds__(64) k_finalize(Params P, Shapes S, Parts D, Li
       const double fb = sdf64(S.type[j], S.param + 3 * j, S.planes + 4 * S.face_off[j],
                               S.face_off[j + 1] - S.face_off[j], XB, D.R + 9 * j, x, P.inflate, gB);
       const double d = fmax(0.0, -(fa + fb));
-      const double EA = S.young[i], EB = S.young[j], nuA = S.poisson[i], nuB = S.poisson[j];
-      const double estar = 1.0 / ((1.0 - nuA * nuA) / EA + (1.0 - nuB * nuB) / EB);
+      const double estar = 1.0 / (S.compl_[i] + S.compl_[j]);
       double damp = 1.0;
+      double ra[3], rb[3];
+      for (int k = 0; k < 3; ++k) {
+        ra[k] = xc[k] - XA[k];
+        rb[k] = xc[k] - XB[k];
+      }
       if (vel != nullptr && P.damping_c != 0.0) {
         const double* va = vel + 6 * i;
         const double* vb = vel + 6 * j;
-        const double ra[3] = {xc[0] - XA[0], xc[1] - XA[1], xc[2] - XA[2]};
-        const double rb[3] = {xc[0] - XB[0], xc[1] - XB[1], xc[2] - XB[2]};
         double wa[3], wb[3];
         cross(va + 3, ra, wa);
         cross(vb + 3, rb, wb);
@@ -98,91 +134,77 @@ __global__ void __launch_bounds__(64) k_finalize(Params P, Shapes S, Parts D, Li
       }
       const double vd = V * d;
       const double fmag = vd > 0.0 ? (4.0 / (3.0 * 3.14159265358979323846)) * estar * sqrt(vd) * damp : 0.0;
-      double F[3], FA[3], ra[3], rb[3], TA[3], TB[3];
+      double F[3], FA[3], TA[3], TB[3];
       for (int k = 0; k < 3; ++k) {
         F[k] = fmag * n[k];
         FA[k] = -F[k];
-        ra[k] = xc[k] - XA[k];
-        rb[k] = xc[k] - XB[k];
       }
       cross(ra, FA, TA);
       cross(rb, F, TB);
-      out[0] = V;
+      double* o = pair_out + static_cast<size_t>(q) * 11;
+      o[0] = V;
       for (int k = 0; k < 3; ++k) {
-        out[1 + k] = xc[k];
-        out[4 + k] = n[k];
-        out[8 + k] = F[k];
-        ft[k] = F[k];
-        ft[3 + k] = TA[k];
-        ft[6 + k] = TB[k];
+        o[1 + k] = xc[k];
+        o[4 + k] = n[k];
+        o[8 + k] = F[k];
       }
-      out[7] = d;
-      tape[0] = s[0];
-      for (int k = 0; k < 3; ++k) { tape[1 + k] = xc[k]; tape[4 + k] = n[k]; }
-      tape[7] = d;
-      tape[8] = gn;
-      tape[9] = fallback;
-      tape[10] = estar;
-      tape[11] = damp;
-      tape[12] = fmag;
-      tape[13] = s[8];
-      atomicAdd(&W.counters[5], 1);
+      o[7] = d;
+      double* f = W.ft + static_cast<size_t>(q) * kFtDoubles;
+      for (int k = 0; k < 3; ++k) {
+        f[k] = F[k];
+        f[3 + k] = TA[k];
+        f[6 + k] = TB[k];
+      }
+      double* tp = W.tape + static_cast<size_t>(q) * kTapeDoubles;
+      tp[0] = s[0];
+      for (int k = 0; k < 3; ++k) { tp[1 + k] = xc[k]; tp[4 + k] = n[k]; }
+      tp[7] = d;
+      tp[8] = gn;
+      tp[9] = fallback;
+      tp[10] = estar;
+      tp[11] = damp;
+      tp[12] = fmag;
+      tp[13] = s[8];
+      tp[14] = 0.0;
+      tp[15] = 0.0;
     }
-    double* o = pair_out + static_cast<size_t>(p) * 11;
-    for (int k = 0; k < 11; ++k) o[k] = out[k];
-    double* f = W.ft + static_cast<size_t>(p) * kFtDoubles;
-    for (int k = 0; k < kFtDoubles; ++k) f[k] = ft[k];
-    double* tp = W.tape + static_cast<size_t>(p) * kTapeDoubles;
-    for (int k = 0; k < kTapeDoubles; ++k) tp[k] = tape[k];
+    if (tid == 0 && s_count > 0) atomicAdd(&W.counters[5], s_count);
+    __syncthreads();
   }
 }
 
-// K7: one warp per particle.  Its contributions are, in this order, the
-// pairs where it is j (by i) and the pairs where it is i (by j); lanes fetch
-// them 32 at a time, lane 0 adds them up in that order (FP64).
+// K7: one lane per particle (FP64 adds in full warps).  Its contributions are
+// added in this order: the pairs where it is j (by i), then the pairs where it
+// is i (by j).
 __global__ void __launch_bounds__(128) k_particle_sum(Params P, Parts D, Lists W, double* __restrict__ force,
                                                       double* __restrict__ torque) {
-  const int lane = threadIdx.x & 31;
-  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (p == 0 && lane == 0) *W.err_host = *W.err;
+  pdl_begin();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p == 0) *W.err_host = *W.err;
+  // the cell list's bin counts start the next step at zero
+  const int nbins = P.nbin[0] * P.nbin[1] * P.nbin[2];
+  for (int b = p; b < nbins; b += gridDim.x * blockDim.x) W.bin_count[b] = 0;
   if (p >= P.n) return;
   const int np = min(W.counters[0], P.max_pairs);
   const int nd = W.dn_count[p], nu = W.up_count[p], r0 = W.row_off[p];
-  const size_t slot = static_cast<size_t>(p) * P.max_nbr;
-  double f[3] = {0, 0, 0}, t[3] = {0, 0, 0};
-  for (int base = 0; base < nd + nu; base += 32) {
-    const int e = base + lane;
-    double v[6] = {0, 0, 0, 0, 0, 0};
-    if (e < nd) {
-      const int q = W.dn_pair[slot + e];
-      if (q < np) {
-        const double* x = W.ft + static_cast<size_t>(q) * kFtDoubles;
-        v[0] = x[0]; v[1] = x[1]; v[2] = x[2];
-        v[3] = x[6]; v[4] = x[7]; v[5] = x[8];
-      }
-    } else if (e < nd + nu) {
-      const int q = r0 + (e - nd);
-      if (q < np) {
-        const double* x = W.ft + static_cast<size_t>(q) * kFtDoubles;
-        v[0] = -x[0]; v[1] = -x[1]; v[2] = -x[2];
-        v[3] = x[3]; v[4] = x[4]; v[5] = x[5];
-      }
-    }
-    const int m = min(32, nd + nu - base);
-    for (int l = 0; l < m; ++l) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        f[k] += __shfl_sync(0xffffffffu, v[k], l);
-        t[k] += __shfl_sync(0xffffffffu, v[3 + k], l);
-      }
-    }
+  const int* dp = W.dn_pair + static_cast<size_t>(p) * P.max_nbr;
+  double f0 = 0, f1 = 0, f2 = 0, t0 = 0, t1 = 0, t2 = 0;
+  for (int r = 0; r < nd; ++r) {
+    const int q = dp[r];
+    if (q >= np) continue;
+    const double* x = W.ft + static_cast<size_t>(q) * kFtDoubles;
+    f0 += x[0]; f1 += x[1]; f2 += x[2];
+    t0 += x[6]; t1 += x[7]; t2 += x[8];
   }
-  if (lane == 0) {
-    for (int k = 0; k < 3; ++k) {
-      force[3 * p + k] = f[k];
-      torque[3 * p + k] = t[k];
-    }
+  for (int r = 0; r < nu; ++r) {
+    const int q = r0 + r;
+    if (q >= np) break;
+    const double* x = W.ft + static_cast<size_t>(q) * kFtDoubles;
+    f0 -= x[0]; f1 -= x[1]; f2 -= x[2];
+    t0 += x[3]; t1 += x[4]; t2 += x[5];
   }
+  force[3 * p] = f0; force[3 * p + 1] = f1; force[3 * p + 2] = f2;
+  torque[3 * p] = t0; torque[3 * p + 1] = t1; torque[3 * p + 2] = t2;
 }
 
 }  // namespace
@@ -192,15 +214,15 @@ void launch_finalize(const Params& P, const Shapes& S, const Parts& D, const Lis
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int need = (P.max_pairs + 63) / 64;
+  const int need = (P.max_pairs + kFinBlock - 1) / kFinBlock;
   const int grid = need < 4 * sms ? (need > 0 ? need : 1) : 4 * sms;
-  k_finalize<<<grid, 64, 0, st>>>(P, S, D, W, vel, pair_out);
+  launch_pdl(k_finalize, dim3(grid), dim3(kFinBlock), 0, st, P, S, D, W, vel, pair_out);
 }
 
 void launch_particle_sum(const Params& P, const Parts& D, const Lists& W, double* force, double* torque,
                          cudaStream_t st) {
-  const int nb = (P.n + 3) / 4;   // four particles (warps) per block
-  k_particle_sum<<<nb > 0 ? nb : 1, 128, 0, st>>>(P, D, W, force, torque);
+  const int nb = (P.n + 31) / 32;
+  launch_pdl(k_particle_sum, dim3(nb > 0 ? nb : 1), dim3(32), 0, st, P, D, W, force, torque);
 }
 
 }  // namespace gbc

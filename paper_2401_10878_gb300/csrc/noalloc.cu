@@ -68,11 +68,14 @@ struct Carver {
 
 // Derived per-particle tables and the zero-initialised words of the step.
 __global__ void k_noalloc_prep(Params P, int* type, int* kind, double* param, float* size_l, int* nomops,
-                               int* face_off, int* vert_off, Lists W, int nbins) {
+                               const double* young, const double* poisson, double* compl_, int* face_off,
+                               int* vert_off, Lists W, int nbins) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < P.n) {
     const int ty = type[t];
-    kind[t] = ty == 0 ? KIND_SPHERE : KIND_CUBOID;
+    compl_[t] = (1.0 - poisson[t] * poisson[t]) / young[t];
+    const double* q = param + 3 * t;
+    kind[t] = ty == 0 ? KIND_SPHERE : ((q[0] == q[1] && q[0] == q[2]) ? KIND_CUBE : KIND_CUBOID);
     nomops[t] = ty == 0 ? 7 : 15;
     for (int k = 0; k < 3; ++k)
       size_l[3 * t + k] = static_cast<float>((param[3 * t + k] + P.inflate) * P.inv_dx);
@@ -143,9 +146,14 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
     if (nb < 3) nb = 1;
     P.nbin[k] = std::min(nb, kMaxBinsPerAxis);
     P.binw[k] = P.L[k] / P.nbin[k];
+    P.inv_binw_f[k] = static_cast<float>(P.nbin[k] / P.L[k]);
   }
   P.dx = C.dx;
   P.inv_dx = 1.0 / C.dx;
+  {
+    int ex = 0;
+    P.dx_pow2 = std::frexp(C.dx, &ex) == 0.5 ? 1 : 0;
+  }
   P.delta = delta;
   P.inflate = C.inflate;
   P.wdx = C.smooth_width * C.dx;
@@ -180,11 +188,12 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   double* pv = cv.take<double>(N);
   float* size_l = cv.take<float>(3 * N);
   int* nomops = cv.take<int>(N);
+  double* compl_ = cv.take<double>(N);
   int* face_off = cv.take<int>(N + 1);
   int* vert_off = cv.take<int>(N + 1);
   double* planes = cv.take<double>(4);
   double* verts = cv.take<double>(3);
-  Shapes S{type, param, face_off, planes, vert_off, verts, yv, pv, size_l, nomops};
+  Shapes S{type, param, face_off, planes, vert_off, verts, yv, pv, size_l, nomops, compl_};
   Parts D{};
   D.X = cv.take<double>(3 * N);
   D.qhat = cv.take<double>(4 * N);
@@ -195,6 +204,9 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   D.slot = cv.take<int>(N);
   D.Rt = cv.take<float>(9 * N);
   D.wplane = cv.take<float4>(1);
+  D.Xf = cv.take<float>(3 * N);
+  D.kX = cv.take<int>(3 * N);
+  D.fX = cv.take<float>(3 * N);
   Lists W{};
   W.bin_count = cv.take<int>(nbins);
   W.bin_start = cv.take<int>(nbins + 1);
@@ -226,7 +238,8 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   if (e == cudaSuccess) e = cudaMemcpyAsync(pv, poisson, N * sizeof(double), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return CONTACT_ECUDA;
   const int threads = 256, blocks = (n + 1 + threads - 1) / threads;
-  k_noalloc_prep<<<blocks, threads, 0, s>>>(P, type, kind, param, size_l, nomops, face_off, vert_off, W, nbins);
+  k_noalloc_prep<<<blocks, threads, 0, s>>>(P, type, kind, param, size_l, nomops, yv, pv, compl_, face_off,
+                                            vert_off, W, nbins);
   // the step's kernels, unchanged, on the scratch array
   launch_pose(P, S, D, W, pos, quat, s);
   launch_bin_scatter(P, D, W, s);
