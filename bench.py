@@ -66,6 +66,20 @@ def dist_setup(args):
     return ws, rank, local
 
 
+def combine_ranks(ms: float, cells: float, device):
+    """Whole-job numbers of a weak-scaling run: the slowest rank's timed
+    milliseconds (max) and the node evaluations of all ranks (sum)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(cells)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    c = torch.tensor([float(cells)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
 def headline_state(rank: int):
     from paper_2401_10878_gb300 import workloads as W
     st = W.settling_cubes_dense(seed=4 + 1000 * rank)
@@ -251,15 +265,7 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         torch.distributed.barrier()
     clocks = clk.summary()
-    t_max = res["ms"]
-    total_cells = res["cells"]
-    if ws > 1:
-        t = torch.tensor([res["ms"]], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-        c = torch.tensor([res["cells"]], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(c)
-        total_cells = float(c.item())
+    t_max, total_cells = combine_ranks(res["ms"], res["cells"], dev)
     value = total_cells / (t_max * 1e-3)
     ms_per_step = t_max / args.steps
     stats = model.stats()

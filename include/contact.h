@@ -85,7 +85,7 @@ typedef struct {
                                one thread block per pair                           */
   int32_t max_pairs;        /* capacity of the pair list (> 0)                       */
   int32_t max_neighbors;    /* capacity of one particle's candidate list (0: 64)    */
-  int32_t max_tiles;        /* capacity of the node-tile list (0: 64 * max_pairs)   */
+  int32_t max_tiles;        /* capacity of the node-tile list (0: 8 * max_pairs)    */
   int32_t use_graph;        /* 1: contact_step captures its launches in a CUDA graph
                                on first use and replays it while the buffers are
                                the same (not while the stream is being captured)   */
@@ -189,9 +189,9 @@ void contact_destroy(contact_ctx* ctx);
 
 /* Fixed capacity of contact_step_noalloc: the size of its scratch array in
  * MiB, and the largest particle count and pair capacity it accepts. */
-#define CONTACT_NOALLOC_SCRATCH_MIB 16
+#define CONTACT_NOALLOC_SCRATCH_MIB 32
 #define CONTACT_NOALLOC_MAX_PARTICLES 2048
-#define CONTACT_NOALLOC_MAX_PAIRS 16384
+#define CONTACT_NOALLOC_MAX_PAIRS 8192
 
 /* contact_step for callers that cannot allocate device memory (no
  * counterpart in the paper: it is an interface for such callers, e.g. a host

@@ -27,6 +27,7 @@ constexpr int kSegMax = 16;           // longest line segment of one item
 constexpr int kPartialFloats = 12;    // FP32 partial sums per tile
 constexpr int kSumDoubles = 10;       // FP64 sums per pair
 constexpr int kTapeDoubles = 16;      // FP64 per-pair values kept for the adjoint
+constexpr int kCostBuckets = 4;       // node-sweep queue: tiles grouped by estimated cost, dearest first
 constexpr int kFtDoubles = 9;         // per-pair F, T_A, T_B
 
 // Error codes written by kernels (same numbering as contact_status).
@@ -45,7 +46,7 @@ struct Params {
   double wdx;            // smoothing width, physical
   int smooth;            // 1: smoothed indicator
   int precision;         // 0: FP32 tiles, 1: FP64 per pair
-  int kind_set;          // 1: only spheres and cuboids (lean node-sweep variant)
+  int kind_set;          // node-sweep variant: 0 all kinds, 1 spheres and cuboids, 2 cubes only
   int dx_pow2;           // 1: dx is a power of two, so x / dx == x * inv_dx exactly
   double damping_c;
   int nbin[3];           // bins per axis
@@ -107,7 +108,8 @@ struct PairRec {
   // FP32 sweep geometry of both particles: R^T rows and sizes (lattice units)
   float rta[9], rtb[9];
   float sza[3], szb[3];
-  int pad[2];
+  int tile;        // in a tile record: the tile's index within its pair
+  int pair;        // in a tile record: the pair index
 };
 constexpr int kPairRecWords = sizeof(PairRec) / 4;
 static_assert(sizeof(PairRec) % 16 == 0, "PairRec is staged with 16-byte copies");
@@ -124,13 +126,16 @@ struct Lists {
   int* dn_pair;     // [N, max_nbr] pair index of (dn_list[p][r], p)
   int* row_off;     // [N + 1] first pair of particle i
   PairRec* pairs;   // [max_pairs]
-  int* tile_pair;   // [max_tiles]
+  int* tile_pair;   // [max_tiles] pair of each tile
+  PairRec* tiles;   // [kCostBuckets, max_tiles] one record per tile (the pair's record with tile and
+                    // pair set), in the node sweep's queue order: bucket 0 (dearest) first
   float* partial;   // [max_tiles, kPartialFloats]
   double* sums;     // [max_pairs, kSumDoubles] (FP64 path writes here directly)
   double* tape;     // [max_pairs, kTapeDoubles]
   double* ft;       // [max_pairs, kFtDoubles]
   const int* kind;  // [N] sweep kind of each particle (Kind, polytopes by face bucket)
-  int* counters;    // [8]: 0 pairs, 1 tiles, 2 queue, 3 cells(lo), 4 cells(hi), 5 overlapping pairs, 6 adjoint queue
+  int* counters;    // [16]: 0 pairs, 1 tiles, 2 queue, 3 cells(lo), 4 cells(hi), 5 overlapping pairs,
+                    // 6 adjoint queue, 8.. 8 + kCostBuckets tiles per cost bucket
   unsigned long long* u64;  // [4]: 0 node evaluations, 1 nominal lane-ops of the node sweep
   int* err;         // [1] sticky device error
   int* err_host;    // mapped host word mirroring err

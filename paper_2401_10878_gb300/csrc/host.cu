@@ -193,7 +193,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   if (!(C.smooth_width > 0.0) || !(C.inflate >= 0.0) || !(C.damping_c >= 0.0)) return CONTACT_EINVAL;
   if (C.max_neighbors < 0 || C.max_neighbors > 512 || C.max_tiles < 0) return CONTACT_EINVAL;
   const int max_nbr = C.max_neighbors > 0 ? C.max_neighbors : 64;
-  const long long max_tiles_ll = C.max_tiles > 0 ? C.max_tiles : 64LL * C.max_pairs;
+  const long long max_tiles_ll = C.max_tiles > 0 ? C.max_tiles : 8LL * C.max_pairs;
   if (max_tiles_ll > (1LL << 30)) return CONTACT_EINVAL;
 
   const double band = (C.indicator == 1) ? (0.5 * C.smooth_width) * C.dx : 0.0;
@@ -288,8 +288,9 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   P.wdx = C.smooth_width * C.dx;
   P.smooth = C.indicator;
   P.precision = C.precision;
-  P.kind_set = std::all_of(kind.begin(), kind.end(),
-                           [](int k) { return k == KIND_SPHERE || k == KIND_CUBOID || k == KIND_CUBE; }) ? 1 : 0;
+  P.kind_set = std::all_of(kind.begin(), kind.end(), [](int k) { return k == KIND_CUBE; }) ? 2
+               : std::all_of(kind.begin(), kind.end(),
+                             [](int k) { return k == KIND_SPHERE || k == KIND_CUBOID || k == KIND_CUBE; }) ? 1 : 0;
   P.damping_c = C.damping_c;
   P.max_pairs = C.max_pairs;
   P.max_nbr = max_nbr;
@@ -359,16 +360,17 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   GBC_TRY(dev_alloc(c, &W.row_off, static_cast<size_t>(n) + 1));
   GBC_TRY(dev_alloc(c, &W.pairs, mp));
   GBC_TRY(dev_alloc(c, &W.tile_pair, mt));
+  GBC_TRY(dev_alloc(c, &W.tiles, mt * kCostBuckets));
   GBC_TRY(dev_alloc(c, &W.partial, mt * kPartialFloats));
   GBC_TRY(dev_alloc(c, &W.sums, mp * kSumDoubles));
   GBC_TRY(dev_alloc(c, &W.tape, mp * kTapeDoubles));
   GBC_TRY(dev_alloc(c, &W.ft, mp * kFtDoubles));
-  GBC_TRY(dev_alloc(c, &W.counters, 8));
+  GBC_TRY(dev_alloc(c, &W.counters, 16));
   GBC_TRY(dev_alloc(c, &W.u64, 4));
   GBC_TRY(dev_alloc(c, &W.err, 1));
   GBC_TRY(dev_alloc(c, &c->adj_scratch, adjoint_scratch_doubles(C.max_pairs, P.max_tiles)));
   W.kind = d_kind;
-  GBC_TRY(cudaMemset(W.counters, 0, 8 * sizeof(int)));
+  GBC_TRY(cudaMemset(W.counters, 0, 16 * sizeof(int)));
   GBC_TRY(cudaMemset(W.u64, 0, 4 * sizeof(unsigned long long)));
   GBC_TRY(cudaMemset(W.err, 0, sizeof(int)));
   GBC_TRY(cudaMemset(W.up_count, 0, sizeof(int) * n));
@@ -473,7 +475,7 @@ contact_status contact_stats(contact_ctx* c, int64_t* stats) {
   if (c == nullptr || stats == nullptr) return CONTACT_EINVAL;
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
-  int h[8];
+  int h[16];
   unsigned long long u[4];
   e = cudaMemcpy(h, c->W.counters, sizeof(h), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(u, c->W.u64, sizeof(u), cudaMemcpyDeviceToHost);

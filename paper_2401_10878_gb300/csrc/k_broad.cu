@@ -280,6 +280,7 @@ __global__ void __launch_bounds__(1024) k_rows(Params P, Lists W, int32_t* __res
     W.counters[1] = 0;   // tiles allocated
     W.counters[2] = 0;   // node-sweep queue head
     W.counters[5] = 0;   // pairs with V > 0
+    for (int b = 0; b < kCostBuckets; ++b) W.counters[8 + b] = 0;
     W.u64[0] = 0;        // node evaluations
     W.u64[1] = 0;        // nominal lane-ops
     *n_pairs_out = static_cast<int>(total_pairs);
@@ -320,7 +321,8 @@ __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D
         pr.dim[k] = hi[k] - lo[k] + 1;
       }
       // sweep layout: lines along one axis, lines cut into nseg segments; the
-      // choice minimises warp slots x (segment length + 1 for the line set-up)
+      // choice minimises warp slots x (segment length + 2 node-equivalents
+      // for the line set-up)
       const long long volp = static_cast<long long>(pr.dim[0]) * pr.dim[1] * pr.dim[2];
       long long best = -1;
       for (int a = 0; a < 3; ++a) {
@@ -330,7 +332,7 @@ __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D
           const int sl = (du + ns - 1) / ns;
           if (sl > kSegMax) continue;
           const long long slots = (lines * ns + 31) / 32;
-          const long long cost = slots * (sl + 1);
+          const long long cost = slots * (sl + 2);
           if (best < 0 || cost < best) {
             best = cost;
             pr.axis = a;
@@ -368,7 +370,8 @@ __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D
         pr.sza[k] = S.size_l[3 * i + k];
         pr.szb[k] = S.size_l[3 * j + k];
       }
-      pr.pad[0] = pr.pad[1] = 0;
+      pr.tile = 0;
+      pr.pair = pi;
       vol = static_cast<unsigned long long>(volp);
       ops = vol * static_cast<unsigned long long>(S.nomops[i] + S.nomops[j]);
       pair_ij[2 * pi] = i;
@@ -406,9 +409,33 @@ __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D
       pr.tile0 = tbase + incl - ntiles;
       W.pairs[pi] = pr;
       for (int k = 0; k < ntiles; ++k) {
-        const int tt = pr.tile0 + k;
-        if (tt < P.max_tiles) W.tile_pair[tt] = pi;
+        if (pr.tile0 + k < P.max_tiles) W.tile_pair[pr.tile0 + k] = pi;
         else set_error(W.err, kErrCapacity);
+      }
+    }
+    // queue records, grouped by estimated cost: slots x (segment + 2), scaled
+    // by the pair's nominal ops per node (warp-aggregated atomics per bucket)
+    int maxt = ntiles;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) maxt = max(maxt, __shfl_xor_sync(kFull, maxt, d));
+    const int slots_total = active ? (pr.nitems + 31) / 32 : 0;
+    const int weight = active ? (S.nomops[pr.i] + S.nomops[pr.j]) : 0;
+    for (int k = 0; k < maxt; ++k) {
+      const bool has = active && k < ntiles && pr.tile0 + k < P.max_tiles;
+      int bucket = kCostBuckets;   // none
+      if (has) {
+        const int slots = min(kTileItemsPerLane, slots_total - k * kTileItemsPerLane);
+        const int cost = slots * (pr.seglen + 2) * weight;   // ~ warp instructions
+        bucket = cost >= 2400 ? 0 : (cost >= 1200 ? 1 : (cost >= 600 ? 2 : 3));
+      }
+      const unsigned grp = __match_any_sync(kFull, bucket);
+      const int leader = __ffs(grp) - 1;
+      int pos = 0;
+      if (has && lane == leader) pos = atomicAdd(&W.counters[8 + bucket], __popc(grp));
+      pos = __shfl_sync(kFull, pos, leader) + __popc(grp & ((1u << lane) - 1u));
+      if (has) {
+        pr.tile = k;
+        W.tiles[static_cast<size_t>(bucket) * P.max_tiles + pos] = pr;
       }
     }
   }

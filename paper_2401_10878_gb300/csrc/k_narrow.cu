@@ -172,55 +172,57 @@ struct CuboidEval {
   }
 };
 
-// Cube (equal half extents h): phi = max_k |y_k| - h.
+// Cube (equal half extents h): phi = max_k |y_k| - h.  Only what the node
+// loop needs stays in registers; the cross-axis terms are re-read from the
+// shared-memory pair record at each line start.
 struct CubeEval {
-  int iu, iv, iw;
-  float fu, fv, fw;
-  float tu[3], tv[3], tw[3], h;
-  float cnt_u, p[3], y[3];
-  float gb[3];
+  int iu;
+  float fu, tu0, tu1, tu2, h;
+  float cnt_u, p0, p1, p2, y0, y1, y2;
+  float gb0, gb1, gb2;
   __device__ void load(const PairRec& r, bool second, const Shapes&, const Parts&, const Local& L, float4*) {
     const int* ci = second ? r.bi : r.ai;
     const float* cf = second ? r.bf : r.af;
     const float* rt = second ? r.rtb : r.rta;
-    iu = ci[L.u]; iv = ci[L.v]; iw = ci[L.w];
-    fu = cf[L.u]; fv = cf[L.v]; fw = cf[L.w];
+    iu = ci[L.u];
+    fu = cf[L.u];
     h = second ? r.szb[0] : r.sza[0];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      tu[k] = rt[3 * k + L.u];
-      tv[k] = rt[3 * k + L.v];
-      tw[k] = rt[3 * k + L.w];
-      gb[k] = 0.f;
-    }
+    tu0 = rt[L.u]; tu1 = rt[3 + L.u]; tu2 = rt[6 + L.u];
+    gb0 = gb1 = gb2 = 0.f;
   }
-  __device__ __forceinline__ void begin_line(int cv, int cw, int u0) {
-    const float rv = static_cast<float>(cv - iv) - fv;
-    const float rw = static_cast<float>(cw - iw) - fw;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) p[k] = fmaf(-tu[k], fu, fmaf(tv[k], rv, tw[k] * rw));
+  __device__ __forceinline__ void begin_line_rec(const PairRec& r, bool second, const Local& L, int cv, int cw,
+                                                 int u0) {
+    const int* ci = second ? r.bi : r.ai;
+    const float* cf = second ? r.bf : r.af;
+    const float* rt = second ? r.rtb : r.rta;
+    const float rv = static_cast<float>(cv - ci[L.v]) - cf[L.v];
+    const float rw = static_cast<float>(cw - ci[L.w]) - cf[L.w];
+    p0 = fmaf(-tu0, fu, fmaf(rt[L.v], rv, rt[L.w] * rw));
+    p1 = fmaf(-tu1, fu, fmaf(rt[3 + L.v], rv, rt[3 + L.w] * rw));
+    p2 = fmaf(-tu2, fu, fmaf(rt[6 + L.v], rv, rt[6 + L.w] * rw));
     cnt_u = static_cast<float>(u0 - iu) - 1.f;
   }
   __device__ __forceinline__ float counter() const { return cnt_u; }
   __device__ __forceinline__ int origin() const { return iu; }
   __device__ __forceinline__ float phi() {
     cnt_u += 1.f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) y[k] = fmaf(tu[k], cnt_u, p[k]);
-    return fmaxf(fabsf(y[0]), fmaxf(fabsf(y[1]), fabsf(y[2]))) - h;
+    y0 = fmaf(tu0, cnt_u, p0);
+    y1 = fmaf(tu1, cnt_u, p1);
+    y2 = fmaf(tu2, cnt_u, p2);
+    return fmaxf(fabsf(y0), fmaxf(fabsf(y1), fabsf(y2))) - h;
   }
   __device__ __forceinline__ void grad(float m) {
-    const float a0 = fabsf(y[0]), a1 = fabsf(y[1]), a2 = fabsf(y[2]);
+    const float a0 = fabsf(y0), a1 = fabsf(y1), a2 = fabsf(y2);
     const bool s0 = a0 >= a1 && a0 >= a2;
     const bool s1 = !s0 && a1 >= a2;
-    gb[0] += s0 ? copysignf(m, y[0]) : 0.f;
-    gb[1] += s1 ? copysignf(m, y[1]) : 0.f;
-    gb[2] += (!s0 && !s1) ? copysignf(m, y[2]) : 0.f;
+    gb0 += s0 ? copysignf(m, y0) : 0.f;
+    gb1 += s1 ? copysignf(m, y1) : 0.f;
+    gb2 += (!s0 && !s1) ? copysignf(m, y2) : 0.f;
   }
   __device__ __forceinline__ void end_line() {}
   __device__ float world(int c, const Local&, const PairRec& r, bool second) const {
     const float* rt = second ? r.rtb : r.rta;
-    return rt[c] * gb[0] + rt[3 + c] * gb[1] + rt[6 + c] * gb[2];
+    return rt[c] * gb0 + rt[3 + c] * gb1 + rt[6 + c] * gb2;
   }
 };
 
@@ -351,6 +353,18 @@ struct PolyGEval {
   __device__ float world(int c, const Local& L, const PairRec&, bool) const { return world_comp(c, L, gu, gv, gw); }
 };
 
+// Line start of an evaluator: from the shared-memory record when the
+// evaluator re-reads its cross-axis terms there, else from its registers.
+template <class E>
+__device__ __forceinline__ auto begin_line_of(E& e, const PairRec& r, bool second, const Local& L, int cv, int cw,
+                                              int u0, int) -> decltype(e.begin_line_rec(r, second, L, cv, cw, u0)) {
+  e.begin_line_rec(r, second, L, cv, cw, u0);
+}
+template <class E>
+__device__ __forceinline__ void begin_line_of(E& e, const PairRec&, bool, const Local&, int cv, int cw, int u0, long) {
+  e.begin_line(cv, cw, u0);
+}
+
 // ---------------------------------------------------------------- tile sweep
 // Per-lane partials of a tile: node count and first moments (exact integers
 // in sharp mode), the band sum of the normal, and the deepest node.
@@ -395,8 +409,8 @@ __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, 
     const int cw = div_small(line, dv, inv_dv, &cv);
     const int u0 = seg * seglen;
     const int len = valid ? min(seglen, du - u0) : 0;
-    A.begin_line(cv, cw, u0);
-    B.begin_line(cv, cw, u0);
+    begin_line_of(A, r, swap, L, cv, cw, u0, 0);
+    begin_line_of(B, r, !swap, L, cv, cw, u0, 0);
     float cl = 0.f, ml = 0.f, bfl = -FLT_MAX;
     int bul = 0;
 #pragma unroll 2
@@ -498,7 +512,7 @@ __device__ __forceinline__ void reduce_and_store(const Partial& o, float* dst) {
 
 // Kernel variants: the full set of pair kinds, or spheres and cuboids only
 // (chosen at init when no polytope is present; fewer registers, no spills).
-enum KindSet : int { SET_ALL = 0, SET_SC = 1 };
+enum KindSet : int { SET_ALL = 0, SET_SC = 1, SET_CUBE = 2 };
 
 template <bool SMOOTH, int SET, class Pre>
 __device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, const Parts& D, const PairRec& r,
@@ -519,7 +533,9 @@ __device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, co
   case (KA) * 8 + (KB):                                                          \
     o = sweep_tile<SMOOTH, TA, TB>(P, S, D, r, swap, tl, smA, smB, pre);         \
     break;
-  if constexpr (SET == SET_SC) {
+  if constexpr (SET == SET_CUBE) {
+    o = sweep_tile<SMOOTH, CubeEval, CubeEval>(P, S, D, r, swap, tl, smA, smB, pre);
+  } else if constexpr (SET == SET_SC) {
     switch (ka * 8 + kb) {
       GBC_CASE(0, 0, SphereEval, SphereEval)
       GBC_CASE(0, 4, SphereEval, CubeEval)
@@ -564,34 +580,52 @@ __device__ __forceinline__ void store_rec_part(PairRec* dst, int lane, int4 v) {
 }
 
 template <bool SMOOTH, int SET>
-__global__ void __launch_bounds__(kWarps * 32, 2) k_narrow32(Params P, Shapes S, Parts D,
-                                                                                 Lists W) {
+__global__ void __launch_bounds__(kWarps * 32, SET == SET_CUBE ? 3 : 2) k_narrow32(Params P, Shapes S, Parts D,
+                                                                                  Lists W) {
   __shared__ __align__(16) PairRec s_rec[kWarps][2];
   __shared__ float4 s_planes[kWarps][2][kMaxFaces];
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int ntiles = min(W.counters[1], P.max_tiles);
-  int t = 0;
-  if (lane == 0) t = atomicAdd(&W.counters[2], 1);
-  t = __shfl_sync(kFull, t, 0);
-  if (t < ntiles) store_rec_part(&s_rec[wid][0], lane, load_rec_part(W.pairs + W.tile_pair[t], lane));
+  // queue position -> record: buckets of decreasing cost, one after the other
+  int bend[kCostBuckets];
+  {
+    int acc = 0;
+#pragma unroll
+    for (int b = 0; b < kCostBuckets; ++b) {
+      acc += W.counters[8 + b];
+      bend[b] = acc;
+    }
+  }
+  auto rec_at = [&](int q) -> const PairRec* {
+    int b = 0, start = 0;
+#pragma unroll
+    for (int k = 0; k < kCostBuckets - 1; ++k) {
+      if (q >= bend[k]) { b = k + 1; start = bend[k]; }
+    }
+    return W.tiles + static_cast<size_t>(b) * P.max_tiles + (q - start);
+  };
+  // first tile: the warp's global index; later tiles from the queue
+  const int nwarps = gridDim.x * kWarps;
+  int t = blockIdx.x * kWarps + wid;
+  if (t < ntiles) store_rec_part(&s_rec[wid][0], lane, load_rec_part(rec_at(t), lane));
   __syncwarp();
   int buf = 0;
   while (t < ntiles) {
     int tn = 0;
-    if (lane == 0) tn = atomicAdd(&W.counters[2], 1);  // next tile, fetched ahead
+    if (lane == 0) tn = atomicAdd(&W.counters[2], 1) + nwarps;  // next tile, fetched ahead
     int4 next = make_int4(0, 0, 0, 0);
     bool fetched = false;
     auto prefetch = [&]() {
       if (fetched) return;
       fetched = true;
       tn = __shfl_sync(kFull, tn, 0);
-      if (tn < ntiles) next = load_rec_part(W.pairs + W.tile_pair[tn], lane);
+      if (tn < ntiles) next = load_rec_part(rec_at(tn), lane);
     };
     const PairRec& r = s_rec[wid][buf];
-    const Partial o = dispatch<SMOOTH, SET>(P, S, D, r, t - r.tile0, s_planes[wid][0], s_planes[wid][1], prefetch);
+    const Partial o = dispatch<SMOOTH, SET>(P, S, D, r, r.tile, s_planes[wid][0], s_planes[wid][1], prefetch);
     prefetch();
-    reduce_and_store<SMOOTH>(o, W.partial + static_cast<size_t>(t) * kPartialFloats);
+    reduce_and_store<SMOOTH>(o, W.partial + static_cast<size_t>(r.tile0 + r.tile) * kPartialFloats);
     __syncwarp();
     if (tn < ntiles) store_rec_part(&s_rec[wid][buf ^ 1], lane, next);
     __syncwarp();
@@ -697,8 +731,14 @@ int narrow_grid(const Params& P) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (P.precision == 1) return sms * 4;
-  const int per_sm = P.smooth ? (P.kind_set ? blocks_per_sm<true, SET_SC>() : blocks_per_sm<true, SET_ALL>())
-                              : (P.kind_set ? blocks_per_sm<false, SET_SC>() : blocks_per_sm<false, SET_ALL>());
+  int per_sm = 1;
+  if (P.smooth) {
+    per_sm = P.kind_set == SET_CUBE ? blocks_per_sm<true, SET_CUBE>()
+             : P.kind_set == SET_SC ? blocks_per_sm<true, SET_SC>() : blocks_per_sm<true, SET_ALL>();
+  } else {
+    per_sm = P.kind_set == SET_CUBE ? blocks_per_sm<false, SET_CUBE>()
+             : P.kind_set == SET_SC ? blocks_per_sm<false, SET_SC>() : blocks_per_sm<false, SET_ALL>();
+  }
   return sms * per_sm;
 }
 
@@ -712,10 +752,12 @@ void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists
   }
   const int b = kWarps * 32;
   if (P.smooth) {
-    if (P.kind_set) launch_pdl(k_narrow32<true, SET_SC>, dim3(grid), dim3(b), 0, st, P, S, D, W);
+    if (P.kind_set == SET_CUBE) launch_pdl(k_narrow32<true, SET_CUBE>, dim3(grid), dim3(b), 0, st, P, S, D, W);
+    else if (P.kind_set == SET_SC) launch_pdl(k_narrow32<true, SET_SC>, dim3(grid), dim3(b), 0, st, P, S, D, W);
     else launch_pdl(k_narrow32<true, SET_ALL>, dim3(grid), dim3(b), 0, st, P, S, D, W);
   } else {
-    if (P.kind_set) launch_pdl(k_narrow32<false, SET_SC>, dim3(grid), dim3(b), 0, st, P, S, D, W);
+    if (P.kind_set == SET_CUBE) launch_pdl(k_narrow32<false, SET_CUBE>, dim3(grid), dim3(b), 0, st, P, S, D, W);
+    else if (P.kind_set == SET_SC) launch_pdl(k_narrow32<false, SET_SC>, dim3(grid), dim3(b), 0, st, P, S, D, W);
     else launch_pdl(k_narrow32<false, SET_ALL>, dim3(grid), dim3(b), 0, st, P, S, D, W);
   }
 }

@@ -27,7 +27,7 @@ namespace {
 
 constexpr size_t kScratchBytes = static_cast<size_t>(CONTACT_NOALLOC_SCRATCH_MIB) << 20;
 constexpr int kMaxNbr = 64;
-constexpr int kMaxTilesPerPair = 4;
+constexpr int kMaxTilesPerPair = 2;
 constexpr int kMaxBinsPerAxis = 32;
 
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -85,7 +85,7 @@ __global__ void k_noalloc_prep(Params P, int* type, int* kind, double* param, fl
     vert_off[t] = 0;
   }
   for (int b = t; b < nbins; b += gridDim.x * blockDim.x) W.bin_count[b] = 0;
-  if (t < 8) W.counters[t] = 0;
+  if (t < 16) W.counters[t] = 0;
   if (t < 4) W.u64[t] = 0;
   if (t == 0) {
     *W.err = 0;
@@ -219,12 +219,13 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   W.row_off = cv.take<int>(N + 1);
   W.pairs = cv.take<PairRec>(MP);
   W.tile_pair = cv.take<int>(MT);
+  W.tiles = cv.take<PairRec>(MT * kCostBuckets);
   W.partial = cv.take<float>(MT * kPartialFloats);
   W.sums = cv.take<double>(MP * kSumDoubles);
   W.tape = cv.take<double>(MP * kTapeDoubles);
   W.ft = cv.take<double>(MP * kFtDoubles);
   W.kind = kind;
-  W.counters = cv.take<int>(8);
+  W.counters = cv.take<int>(16);
   W.u64 = cv.take<unsigned long long>(4);
   W.err = cv.take<int>(1);
   W.err_host = cv.take<int>(1);
