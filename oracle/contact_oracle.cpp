@@ -125,21 +125,24 @@ struct Shape {
 };
 
 // Rotation matrix of the normalised quaternion (w, x, y, z), Hamilton
-// convention, body -> world, row-major.  The operation order is fixed (and
-// contraction is off) because the AABB node ranges are compared bit for bit.
+// convention, body -> world, row-major, in homogeneous form: with
+// s = 2 / |q|^2 the products of the raw components give R of q / |q|.  The
+// operation order is fixed (and contraction is off) because the AABB node
+// ranges are compared bit for bit.
 template <class S>
 void quat_to_rot(const S q_in[4], S R[9]) {
-  S nrm = sqrt_s(((q_in[0] * q_in[0] + q_in[1] * q_in[1]) + q_in[2] * q_in[2]) + q_in[3] * q_in[3]);
-  S w = q_in[0] / nrm, x = q_in[1] / nrm, y = q_in[2] / nrm, z = q_in[3] / nrm;
-  R[0] = 1.0 - 2.0 * (y * y + z * z);
-  R[1] = 2.0 * (x * y - w * z);
-  R[2] = 2.0 * (x * z + w * y);
-  R[3] = 2.0 * (x * y + w * z);
-  R[4] = 1.0 - 2.0 * (x * x + z * z);
-  R[5] = 2.0 * (y * z - w * x);
-  R[6] = 2.0 * (x * z - w * y);
-  R[7] = 2.0 * (y * z + w * x);
-  R[8] = 1.0 - 2.0 * (x * x + y * y);
+  const S w = q_in[0], x = q_in[1], y = q_in[2], z = q_in[3];
+  const S nn = ((w * w + x * x) + y * y) + z * z;
+  const S s = 2.0 / nn;
+  R[0] = 1.0 - s * (y * y + z * z);
+  R[1] = s * (x * y - w * z);
+  R[2] = s * (x * z + w * y);
+  R[3] = s * (x * y + w * z);
+  R[4] = 1.0 - s * (x * x + z * z);
+  R[5] = s * (y * z - w * x);
+  R[6] = s * (x * z - w * y);
+  R[7] = s * (y * z + w * x);
+  R[8] = 1.0 - s * (x * x + y * y);
 }
 
 // Vertices of the convex polytope {y : n_i . y <= d_i + delta}: every plane
