@@ -25,7 +25,6 @@ constexpr int kMaxFaces = 32;         // faces of one polytope
 constexpr int kTileItemsPerLane = 4;  // node lines (segments) per lane per tile
 constexpr int kSegMax = 16;           // longest line segment of one item
 constexpr int kPartialFloats = 12;    // FP32 partial sums per tile
-constexpr int kSumDoubles = 10;       // FP64 sums per pair
 constexpr int kTapeDoubles = 16;      // FP64 per-pair values kept for the adjoint
 constexpr int kCostBuckets = 4;       // node-sweep queue: tiles grouped by estimated cost, dearest first
 constexpr int kFtDoubles = 9;         // per-pair F, T_A, T_B
@@ -44,6 +43,9 @@ struct Params {
   double delta;          // AABB offset: inflate (+ w dx / 2 in smoothed mode)
   double inflate;        // physical
   double wdx;            // smoothing width, physical
+  double dx3;            // dx^3 (volume of a node)
+  double gscale;         // 1/2 dx^2 * 6 / w: band sum -> G
+  double g_min2;         // (1e-12 dx^2)^2: |G|^2 below it takes the centre-line normal
   int smooth;            // 1: smoothed indicator
   int precision;         // 0: FP32 tiles, 1: FP64 per pair
   int kind_set;          // node-sweep variant: 0 all kinds, 1 spheres and cuboids, 2 cubes only
@@ -70,13 +72,15 @@ struct Shapes {
   const float* size_l;     // [N,3] lattice units incl. inflate: sphere r', cuboid h'
   const int* nomops;       // [N] nominal FP32 lane-ops of one signed-distance test
   const double* compl_;    // [N] (1 - nu^2) / E, so that E* = 1 / (compl_i + compl_j)
+  const double* ext;       // [N,3] sphere: r + delta; cuboid: h_k + delta (AABB half sizes in the body frame)
+  const float* verts32;    // [V,3] FP32 copy of the offset-shape vertices (prefilter of the extremes)
+  const float* off32;      // [F] (d + inflate) / dx per face, FP32
 };
 
 // Per-step particle records.
 struct Parts {
   double* X;       // [N,3] copy of the positions of the step
-  double* qhat;    // [N,4] normalised quaternion
-  double* qnorm;   // [N]
+  double* qhat;    // [N,4] the step's quaternion as given (normalised by the adjoint)
   double* R;       // [N,9] FP64 rotation, row-major, body -> world
   int* lohi;       // [N,6]
   int* bin;        // [N]
@@ -115,6 +119,20 @@ constexpr int kPairRecWords = sizeof(PairRec) / 4;
 static_assert(sizeof(PairRec) % 16 == 0, "PairRec is staged with 16-byte copies");
 
 // Work lists shared by the step's kernels.
+// One overlapping pair for the force law: its FP64 sums (count, first
+// moments, band terms of G), its deepest node, and the pair record's geometry.
+struct OvlRec {
+  double s[7];     // sum of H, of H x (x, y, z) in box coordinates, of the band terms (x, y, z)
+  int q;           // pair index
+  int idx;         // deepest node (linear index in the pair box)
+  int i, j;        // particles
+  int lo[3];       // pair box origin (nodes)
+  int dim[3];      // pair box nodes per axis
+  int shift[3];    // image index of j
+  int pad[5];
+};
+static_assert(sizeof(OvlRec) == 128, "one overlap record per 128-byte line");
+
 struct Lists {
   int* bin_count;   // [nbins]
   int* bin_start;   // [nbins + 1]
@@ -130,7 +148,8 @@ struct Lists {
   PairRec* tiles;   // [kCostBuckets, max_tiles] one record per tile (the pair's record with tile and
                     // pair set), in the node sweep's queue order: bucket 0 (dearest) first
   float* partial;   // [max_tiles, kPartialFloats]
-  double* sums;     // [max_pairs, kSumDoubles] (FP64 path writes here directly)
+  int* pdone;       // [max_pairs] tiles of the pair swept so far (pairs of several tiles)
+  OvlRec* olist;    // [max_pairs] overlapping pairs, in completion order (count: counters[5])
   double* tape;     // [max_pairs, kTapeDoubles]
   double* ft;       // [max_pairs, kFtDoubles]
   const int* kind;  // [N] sweep kind of each particle (Kind, polytopes by face bucket)
@@ -147,6 +166,25 @@ struct Lists {
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+
+// Row k of the rotation of q / |q| (w, x, y, z), body -> world, in homogeneous
+// form with s = 2 / |q|^2 (2 RN(1/nn) == RN(2/nn): scaling by 2 is exact).
+__device__ inline void rotation_row_rn(const double q[4], double s, int k, double r[3]) {
+  const double w = q[0], x = q[1], y = q[2], z = q[3];
+  if (k == 0) {
+    r[0] = dsub(1.0, dmul(s, dadd(dmul(y, y), dmul(z, z))));
+    r[1] = dmul(s, dsub(dmul(x, y), dmul(w, z)));
+    r[2] = dmul(s, dadd(dmul(x, z), dmul(w, y)));
+  } else if (k == 1) {
+    r[0] = dmul(s, dadd(dmul(x, y), dmul(w, z)));
+    r[1] = dsub(1.0, dmul(s, dadd(dmul(x, x), dmul(z, z))));
+    r[2] = dmul(s, dsub(dmul(y, z), dmul(w, x)));
+  } else {
+    r[0] = dmul(s, dsub(dmul(x, z), dmul(w, y)));
+    r[1] = dmul(s, dadd(dmul(y, z), dmul(w, x)));
+    r[2] = dsub(1.0, dmul(s, dadd(dmul(x, x), dmul(y, y))));
+  }
+}
 
 // Rotation of the normalised quaternion (w, x, y, z), body -> world, row-major.
 __device__ inline void rotation_rn(const double q[4], double* qh, double* qn, double R[9]) {
@@ -206,6 +244,42 @@ __device__ inline double sdf64(int type, const double* prm, const double* planes
 
 __device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0, code); }
 
+// Exact FP32 -> FP64 conversion with integer operations (IEEE 754: sign kept,
+// exponent rebiased by 1023 - 127, fraction widened by 29 bits; subnormals
+// normalised): widening the partials costs no FP64 instruction.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sgn = u & 0x80000000u;
+  int e = static_cast<int>((u >> 23) & 0xffu);
+  unsigned m = u & 0x7fffffu;
+  if (e == 0xff) return static_cast<double>(f);   // inf / NaN: not produced by the sweep
+  if (e == 0) {
+    if (m == 0) return __hiloint2double(static_cast<int>(sgn), 0);
+    const int lz = __clz(m) - 8;                   // moves the leading 1 to the implicit bit
+    m = (m << lz) & 0x7fffffu;
+    e = 1 - lz;
+  }
+  const unsigned hi = sgn | (static_cast<unsigned>(e + 896) << 20) | (m >> 3);
+  return __hiloint2double(static_cast<int>(hi), static_cast<int>(m << 29));
+}
+
+// FP64 reciprocal and reciprocal square root from an FP32 seed and two Newton
+// steps (relative error ~1e-16, not correctly rounded): a few FP64 FMAs
+// instead of a division sequence, which costs ~10x more on this GPU's narrow
+// FP64 pipe.  For positive normal arguments within the FP32 range.
+__device__ __forceinline__ double fast_rcp(double a) {
+  double r = static_cast<double>(__frcp_rn(static_cast<float>(a)));
+  r = r * fma(-a, r, 2.0);
+  r = r * fma(-a, r, 2.0);
+  return r;
+}
+__device__ __forceinline__ double fast_rsqrt(double a) {
+  double y = static_cast<double>(rsqrtf(static_cast<float>(a)));
+  y = y * fma(-0.5 * a, y * y, 1.5);
+  y = y * fma(-0.5 * a, y * y, 1.5);
+  return y;
+}
+
 // Programmatic dependent launch: every kernel of a step lets the next one
 // launch at its start, and waits for the previous one (completion and memory
 // visibility) before it reads that kernel's results.
@@ -239,7 +313,8 @@ void launch_bin_scatter(const Params& P, const Parts& D, const Lists& W, cudaStr
 void launch_broad(const Params& P, const Parts& D, const Lists& W, cudaStream_t st);
 void launch_plan(const Params& P, const Shapes& S, const Parts& D, const Lists& W, int32_t* pair_ij, int32_t* n_pairs,
                  cudaStream_t st);
-void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists& W, int grid, cudaStream_t st);
+void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists& W, double* pair_out, int grid,
+                   cudaStream_t st);
 int narrow_grid(const Params& P);
 void launch_finalize(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel,
                      double* pair_out, cudaStream_t st);

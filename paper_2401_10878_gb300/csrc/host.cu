@@ -143,7 +143,7 @@ void enqueue_step(contact_ctx* c, bool capturing, const double* pos, const doubl
   launch_broad(c->P, c->D, c->W, c->stream);
   launch_plan(c->P, c->S, c->D, c->W, pair_ij, n_pairs, c->stream);
   if (c->cfg.narrow_events) cudaEventRecordWithFlags(c->ev_narrow[0], c->stream, ev_flags);
-  launch_narrow(c->P, c->S, c->D, c->W, c->grid_narrow, c->stream);
+  launch_narrow(c->P, c->S, c->D, c->W, pair_out, c->grid_narrow, c->stream);
   if (c->cfg.narrow_events) cudaEventRecordWithFlags(c->ev_narrow[1], c->stream, ev_flags);
   launch_finalize(c->P, c->S, c->D, c->W, vel, pair_out, c->stream);
   launch_particle_sum(c->P, c->D, c->W, force, torque, c->stream);
@@ -199,7 +199,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   const double band = (C.indicator == 1) ? (0.5 * C.smooth_width) * C.dx : 0.0;
   const double delta = C.inflate + band;
   std::vector<int> type(n), kind(n), vert_off(n + 1, 0);
-  std::vector<double> param(3 * static_cast<size_t>(n)), verts;
+  std::vector<double> param(3 * static_cast<size_t>(n)), verts, ext(3 * static_cast<size_t>(n), 0.0);
   std::vector<float> size_l(3 * static_cast<size_t>(n));
   // nominal FP32 lane-ops of one signed-distance test (roofline accounting):
   // sphere 7, cuboid 15, polytope with F faces 4F
@@ -217,6 +217,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
     if (type[p] == CONTACT_SHAPE_SPHERE) {
       if (!(param[3 * p] > 0.0) || f1 != f0) return CONTACT_EINVAL;
       circ = param[3 * p] + delta;
+      ext[3 * p] = param[3 * p] + delta;
       kind[p] = KIND_SPHERE;
       nomops[p] = 7;
       size_l[3 * p] = static_cast<float>((param[3 * p] + C.inflate) / C.dx);
@@ -226,6 +227,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
       for (int k = 0; k < 3; ++k) {
         if (!(param[3 * p + k] > 0.0)) return CONTACT_EINVAL;
         e2 += (param[3 * p + k] + delta) * (param[3 * p + k] + delta);
+        ext[3 * p + k] = param[3 * p + k] + delta;
         size_l[3 * p + k] = static_cast<float>((param[3 * p + k] + C.inflate) / C.dx);
       }
       circ = std::sqrt(e2);
@@ -286,6 +288,9 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   P.delta = delta;
   P.inflate = C.inflate;
   P.wdx = C.smooth_width * C.dx;
+  P.dx3 = C.dx * C.dx * C.dx;
+  P.gscale = 0.5 * C.dx * C.dx * 6.0 / (P.wdx / C.dx);
+  P.g_min2 = 1e-24 * C.dx * C.dx * C.dx * C.dx;
   P.smooth = C.indicator;
   P.precision = C.precision;
   P.kind_set = std::all_of(kind.begin(), kind.end(), [](int k) { return k == KIND_CUBE; }) ? 2
@@ -330,12 +335,19 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   GBC_TRY(upload(c, &d_size, size_l));
   GBC_TRY(upload(c, &d_nomops, nomops));
   GBC_TRY(upload(c, &d_compl, cv));
-  c->S = Shapes{d_type, d_param, d_foff, d_planes, d_voff, d_verts, d_young, d_pois, d_size, d_nomops, d_compl};
+  std::vector<float> verts32(verts.begin(), verts.end()), off32(static_cast<size_t>(std::max(nfaces, 1)), 0.f);
+  for (int f = 0; f < nfaces; ++f) off32[f] = static_cast<float>((planes[4 * f + 3] + C.inflate) / C.dx);
+  double* d_ext;
+  float *d_verts32, *d_off32;
+  GBC_TRY(upload(c, &d_ext, ext));
+  GBC_TRY(upload(c, &d_verts32, verts32));
+  GBC_TRY(upload(c, &d_off32, off32));
+  c->S = Shapes{d_type, d_param, d_foff, d_planes, d_voff, d_verts, d_young, d_pois, d_size, d_nomops, d_compl,
+                d_ext, d_verts32, d_off32};
 
   Parts& D = c->D;
   GBC_TRY(dev_alloc(c, &D.X, 3 * static_cast<size_t>(n)));
   GBC_TRY(dev_alloc(c, &D.qhat, 4 * static_cast<size_t>(n)));
-  GBC_TRY(dev_alloc(c, &D.qnorm, static_cast<size_t>(n)));
   GBC_TRY(dev_alloc(c, &D.R, 9 * static_cast<size_t>(n)));
   GBC_TRY(dev_alloc(c, &D.lohi, 6 * static_cast<size_t>(n)));
   GBC_TRY(dev_alloc(c, &D.bin, static_cast<size_t>(n)));
@@ -362,7 +374,8 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   GBC_TRY(dev_alloc(c, &W.tile_pair, mt));
   GBC_TRY(dev_alloc(c, &W.tiles, mt * kCostBuckets));
   GBC_TRY(dev_alloc(c, &W.partial, mt * kPartialFloats));
-  GBC_TRY(dev_alloc(c, &W.sums, mp * kSumDoubles));
+  GBC_TRY(dev_alloc(c, &W.pdone, mp));
+  GBC_TRY(dev_alloc(c, &W.olist, mp));
   GBC_TRY(dev_alloc(c, &W.tape, mp * kTapeDoubles));
   GBC_TRY(dev_alloc(c, &W.ft, mp * kFtDoubles));
   GBC_TRY(dev_alloc(c, &W.counters, 16));

@@ -392,8 +392,11 @@ __global__ void __launch_bounds__(128) k_adj_scatter(Params P, Parts D, Lists W,
     const double* e = B.pgrad + static_cast<size_t>(q) * kPairGrad;
     for (int k = 0; k < 3; ++k) { gx[k] += e[k]; tau[k] += e[3 + k]; }
   }
-  const double w = D.qhat[4 * p], v[3] = {D.qhat[4 * p + 1], D.qhat[4 * p + 2], D.qhat[4 * p + 3]};
-  const double s = 2.0 / D.qnorm[p];
+  const double* qr = D.qhat + 4 * p;
+  const double qn = sqrt(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
+  const double iq = 1.0 / qn;
+  const double w = qr[0] * iq, v[3] = {qr[1] * iq, qr[2] * iq, qr[3] * iq};
+  const double s = 2.0 * iq;
   double tv[3];
   cross3(tau, v, tv);
   for (int k = 0; k < 3; ++k) gpos[3 * p + k] = gx[k];

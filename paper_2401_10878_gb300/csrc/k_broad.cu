@@ -21,93 +21,111 @@ __device__ __forceinline__ int clamp_node(double v) {
 }
 
 // ---------------------------------------------------------------------------
-// K1: per particle rotation, node ranges, FP32 sweep geometry and bin slot.
+// K1: one thread per (particle p, axis k): row k of the rotation, the node
+// range along k, the FP32 sweep geometry and, on axis 0, the bin slot.  FP64
+// is kept to what the bit-exact node range needs (every FP64 instruction
+// costs ~64 cycles per warp on this GPU), and spread over three threads.
 __global__ void k_pose(Params P, Shapes S, Parts D, Lists W, const double* __restrict__ pos,
                        const double* __restrict__ quat) {
   pdl_begin();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P.n) return;
-  double X[3], q[4];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * P.n) return;
+  const int p = t / 3, k = t - 3 * p;
+  double q[4];
+  for (int c = 0; c < 4; ++c) q[c] = quat[4 * p + c];
+  // position check by bit patterns: 0 <= X < L (NaN and negatives fail; -0.0 counts as 0)
   bool bad = false;
-  for (int k = 0; k < 3; ++k) {
-    X[k] = pos[3 * p + k];
-    if (!(X[k] >= 0.0) || !(X[k] < P.L[k])) {  // also catches NaN
-      bad = true;
-      X[k] = 0.0;
-    }
+  float xs[3];
+  double Xk = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    const double v = pos[3 * p + c];
+    long long b = __double_as_longlong(v);
+    if (b == static_cast<long long>(0x8000000000000000ULL)) b = 0;
+    const bool ok = b >= 0 && b < __double_as_longlong(P.L[c]);
+    bad = bad || !ok;
+    const double vv = ok ? __longlong_as_double(b) : 0.0;
+    xs[c] = static_cast<float>(vv);
+    if (c == k) Xk = vv;
   }
-  for (int k = 0; k < 4; ++k) q[k] = quat[4 * p + k];
-  const double qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
-  if (!(qq > 1e-24) || !(qq < 1e300)) {
+  const double nn = dadd(dadd(dadd(dmul(q[0], q[0]), dmul(q[1], q[1])), dmul(q[2], q[2])), dmul(q[3], q[3]));
+  if (!(nn > 1e-24) || !(nn < 1e300)) {
     bad = true;
     q[0] = 1.0; q[1] = q[2] = q[3] = 0.0;
   }
-  if (bad) set_error(W.err, kErrInval);
-  double qh[4], qn, R[9];
-  rotation_rn(q, qh, &qn, R);
-  for (int k = 0; k < 3; ++k) D.X[3 * p + k] = X[k];
-  for (int k = 0; k < 4; ++k) D.qhat[4 * p + k] = qh[k];
-  D.qnorm[p] = qn;
-  for (int k = 0; k < 9; ++k) D.R[9 * p + k] = R[k];
-
-  // AABB of the offset shape {phi <= delta} (explicit rounding: compared bit for bit)
+  if (bad && k == 0) set_error(W.err, kErrInval);
+  const double s = bad ? 2.0 : dmul(2.0, __drcp_rn(nn));
+  double r[3];
+  rotation_row_rn(q, s, k, r);
+  D.X[3 * p + k] = Xk;
+  if (k == 0)
+    for (int c = 0; c < 4; ++c) D.qhat[4 * p + c] = q[c];   // raw quaternion of the step (adjoint tape)
+  for (int c = 0; c < 3; ++c) D.R[9 * p + 3 * k + c] = r[c];
+  float r32[3];
+  for (int c = 0; c < 3; ++c) {
+    r32[c] = static_cast<float>(r[c]);
+    D.Rt[9 * p + 3 * c + k] = r32[c];   // R^T row c, column k
+  }
+  // extent along k of the offset shape {phi <= delta} (explicit rounding: compared bit for bit)
   const int type = S.type[p];
-  const double* prm = S.param + 3 * p;
-  double mn[3], mx[3];
+  double mn, mx;
   if (type == 0) {
-    const double rad = dadd(prm[0], P.delta);
-    for (int k = 0; k < 3; ++k) { mn[k] = dsub(X[k], rad); mx[k] = dadd(X[k], rad); }
+    const double rad = S.ext[3 * p];
+    mn = dsub(Xk, rad);
+    mx = dadd(Xk, rad);
   } else if (type == 1) {
-    const double e0 = dadd(prm[0], P.delta), e1 = dadd(prm[1], P.delta), e2 = dadd(prm[2], P.delta);
-    for (int k = 0; k < 3; ++k) {
-      const double ext = dadd(dadd(dmul(fabs(R[3 * k]), e0), dmul(fabs(R[3 * k + 1]), e1)),
-                              dmul(fabs(R[3 * k + 2]), e2));
-      mn[k] = dsub(X[k], ext);
-      mx[k] = dadd(X[k], ext);
-    }
+    const double* e = S.ext + 3 * p;
+    const double ext = dadd(dadd(dmul(fabs(r[0]), e[0]), dmul(fabs(r[1]), e[1])), dmul(fabs(r[2]), e[2]));
+    mn = dsub(Xk, ext);
+    mx = dadd(Xk, ext);
   } else {
-    double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
-    for (int v = S.vert_off[p]; v < S.vert_off[p + 1]; ++v) {
-      const double* w = S.verts + 3 * v;
-      for (int k = 0; k < 3; ++k) {
-        const double t = dadd(dadd(dmul(R[3 * k], w[0]), dmul(R[3 * k + 1], w[1])), dmul(R[3 * k + 2], w[2]));
-        lo[k] = fmin(lo[k], t);
-        hi[k] = fmax(hi[k], t);
-      }
+    // FP32 prefilter of the extreme vertices, FP64 only for those near the extremes
+    const int v0 = S.vert_off[p], v1 = S.vert_off[p + 1];
+    // (the FP32 projection errs by < 4e-7 * (|w0|+|w1|+|w2|); the window is 25x that)
+    float lo32 = FLT_MAX, hi32 = -FLT_MAX, wmax = 0.f;
+    for (int v = v0; v < v1; ++v) {
+      const float* w = S.verts32 + 3 * v;
+      const float tv = fmaf(r32[0], w[0], fmaf(r32[1], w[1], r32[2] * w[2]));
+      lo32 = fminf(lo32, tv);
+      hi32 = fmaxf(hi32, tv);
+      wmax = fmaxf(wmax, fabsf(w[0]) + fabsf(w[1]) + fabsf(w[2]));
     }
-    for (int k = 0; k < 3; ++k) { mn[k] = dadd(X[k], lo[k]); mx[k] = dadd(X[k], hi[k]); }
-  }
-  int b[3];
-  for (int k = 0; k < 3; ++k) {
-    // x / dx, exactly as an IEEE division (a multiply when dx is a power of two)
-    const double a = P.dx_pow2 ? dmul(mn[k], P.inv_dx) : __ddiv_rn(mn[k], P.dx);
-    const double c = P.dx_pow2 ? dmul(mx[k], P.inv_dx) : __ddiv_rn(mx[k], P.dx);
-    D.lohi[6 * p + k] = clamp_node(ceil(a));
-    D.lohi[6 * p + 3 + k] = clamp_node(floor(c));
-    const float xf = static_cast<float>(X[k]);
-    D.Xf[3 * p + k] = xf;
-    b[k] = min(max(static_cast<int>(xf * P.inv_binw_f[k]), 0), P.nbin[k] - 1);
-    const double xl = X[k] * P.inv_dx;
-    const double kx = rint(xl);
-    D.kX[3 * p + k] = static_cast<int>(kx);
-    D.fX[3 * p + k] = static_cast<float>(xl - kx);
-  }
-  // FP32 geometry of the node sweep (lattice units)
-  for (int k = 0; k < 3; ++k)
-    for (int j = 0; j < 3; ++j) D.Rt[9 * p + 3 * k + j] = static_cast<float>(R[3 * j + k]);
-  if (type == 2) {
+    const float tol = 1e-5f * wmax + 1e-30f;
+    double lo = DBL_MAX, hi = -DBL_MAX;
+    for (int v = v0; v < v1; ++v) {
+      const float* w32 = S.verts32 + 3 * v;
+      const float tv = fmaf(r32[0], w32[0], fmaf(r32[1], w32[1], r32[2] * w32[2]));
+      if (tv > lo32 + tol && tv < hi32 - tol) continue;
+      const double* w = S.verts + 3 * v;
+      const double tt = dadd(dadd(dmul(r[0], w[0]), dmul(r[1], w[1])), dmul(r[2], w[2]));
+      lo = fmin(lo, tt);
+      hi = fmax(hi, tt);
+    }
+    mn = dadd(Xk, lo);
+    mx = dadd(Xk, hi);
+    // world normals: component k of R n per face (FP64 product, one rounding to FP32)
+    float* wp = reinterpret_cast<float*>(D.wplane);
     for (int f = S.face_off[p]; f < S.face_off[p + 1]; ++f) {
       const double* e = S.planes + 4 * f;
-      const double m0 = R[0] * e[0] + R[1] * e[1] + R[2] * e[2];
-      const double m1 = R[3] * e[0] + R[4] * e[1] + R[5] * e[2];
-      const double m2 = R[6] * e[0] + R[7] * e[1] + R[8] * e[2];
-      D.wplane[f] = make_float4(static_cast<float>(m0), static_cast<float>(m1), static_cast<float>(m2),
-                                static_cast<float>((e[3] + P.inflate) * P.inv_dx));
+      wp[4 * f + k] = static_cast<float>(fma(r[0], e[0], fma(r[1], e[1], r[2] * e[2])));
+      if (k == 0) wp[4 * f + 3] = S.off32[f];
     }
   }
-  const int bin = b[0] + P.nbin[0] * (b[1] + P.nbin[1] * b[2]);
-  D.bin[p] = bin;
-  D.slot[p] = atomicAdd(&W.bin_count[bin], 1);
+  const double a = P.dx_pow2 ? dmul(mn, P.inv_dx) : __ddiv_rn(mn, P.dx);
+  const double c = P.dx_pow2 ? dmul(mx, P.inv_dx) : __ddiv_rn(mx, P.dx);
+  D.lohi[6 * p + k] = clamp_node(ceil(a));
+  D.lohi[6 * p + 3 + k] = clamp_node(floor(c));
+  D.Xf[3 * p + k] = xs[k];
+  const double xl = Xk * P.inv_dx;
+  const double kx = rint(xl);
+  D.kX[3 * p + k] = static_cast<int>(kx);
+  D.fX[3 * p + k] = static_cast<float>(xl - kx);
+  if (k == 0) {
+    int b[3];
+    for (int cc = 0; cc < 3; ++cc) b[cc] = min(max(static_cast<int>(xs[cc] * P.inv_binw_f[cc]), 0), P.nbin[cc] - 1);
+    const int bin = b[0] + P.nbin[0] * (b[1] + P.nbin[1] * b[2]);
+    D.bin[p] = bin;
+    D.slot[p] = atomicAdd(&W.bin_count[bin], 1);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -322,18 +340,20 @@ __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D
       }
       // sweep layout: lines along one axis, lines cut into nseg segments; the
       // choice minimises warp slots x (segment length + 2 node-equivalents
-      // for the line set-up)
+      // for the line set-up).  Loops unrolled: every division is by a constant.
       const long long volp = static_cast<long long>(pr.dim[0]) * pr.dim[1] * pr.dim[2];
-      long long best = -1;
+      const int lines_of[3] = {pr.dim[1] * pr.dim[2], pr.dim[0] * pr.dim[2], pr.dim[0] * pr.dim[1]};
+      int best = -1;
+#pragma unroll
       for (int a = 0; a < 3; ++a) {
         const int du = pr.dim[a];
-        const long long lines = volp / du;
-        for (int ns = 1; ns <= 8 && ns <= du; ++ns) {
+        const int lines = lines_of[a];
+#pragma unroll
+        for (int ns = 1; ns <= 8; ++ns) {
           const int sl = (du + ns - 1) / ns;
-          if (sl > kSegMax) continue;
-          const long long slots = (lines * ns + 31) / 32;
-          const long long cost = slots * (sl + 2);
-          if (best < 0 || cost < best) {
+          const int slots = (lines * ns + 31) >> 5;
+          const int cost = slots * (sl + 2);
+          if (ns <= du && sl <= kSegMax && (best < 0 || cost < best)) {
             best = cost;
             pr.axis = a;
             pr.nseg = ns;
@@ -348,7 +368,7 @@ __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D
         pr.nseg = (pr.dim[a] + kSegMax - 1) / kSegMax;
         pr.seglen = (pr.dim[a] + pr.nseg - 1) / pr.nseg;
       }
-      pr.nitems = static_cast<int>(volp / pr.dim[pr.axis]) * pr.nseg;
+      pr.nitems = (pr.axis == 0 ? lines_of[0] : (pr.axis == 1 ? lines_of[1] : lines_of[2])) * pr.nseg;
       ntiles = (pr.nitems + 32 * kTileItemsPerLane - 1) / (32 * kTileItemsPerLane);
       pr.ntiles = ntiles;
       pr.kinds = W.kind[i] | (W.kind[j] << 8);
@@ -372,16 +392,19 @@ __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D
       }
       pr.tile = 0;
       pr.pair = pi;
+      W.pdone[pi] = 0;
       vol = static_cast<unsigned long long>(volp);
       ops = vol * static_cast<unsigned long long>(S.nomops[i] + S.nomops[j]);
       pair_ij[2 * pi] = i;
       pair_ij[2 * pi + 1] = j;
-      // slot of this pair in j's list of lower partners
+      // slot of this pair in j's (sorted) list of lower partners: the number
+      // of entries below i, all loads in flight at once
       const int* dl = W.dn_list + static_cast<size_t>(j) * cap;
-      int a0 = 0, a1 = W.dn_count[j];
-      while (a0 < a1) {
-        const int mid = (a0 + a1) >> 1;
-        if (dl[mid] < i) a0 = mid + 1; else a1 = mid;
+      const int dc = W.dn_count[j];
+      int a0 = 0;
+      for (int b = 0; b < dc; b += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a0 += (b + u < dc && dl[b + u] < i) ? 1 : 0;
       }
       W.dn_pair[static_cast<size_t>(j) * cap + a0] = pi;
     }
@@ -445,8 +468,8 @@ __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D
 
 void launch_pose(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* pos,
                  const double* quat, cudaStream_t st) {
-  const int nb = (P.n + 31) / 32;   // few threads per SM: the FP64 pipe is narrow
-  if (nb > 0) launch_pdl(k_pose, dim3(nb), dim3(32), 0, st, P, S, D, W, pos, quat);
+  const int nb = (3 * P.n + 95) / 96;   // 32 particles x 3 axes per block
+  if (nb > 0) launch_pdl(k_pose, dim3(nb), dim3(96), 0, st, P, S, D, W, pos, quat);
 }
 
 void launch_bin_scatter(const Params& P, const Parts& D, const Lists& W, cudaStream_t st) {

@@ -484,7 +484,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 // with integer warp reductions; the deepest node via an integer max of an
 // order-preserving key and an integer min of the node index among the ties.
 template <bool SMOOTH>
-__device__ __forceinline__ void reduce_and_store(const Partial& o, float* dst) {
+__device__ __forceinline__ float reduce_tile(const Partial& o) {
   const int lane = threadIdx.x & 31;
   float c, x, y, z;
   if (SMOOTH) {
@@ -507,7 +507,91 @@ __device__ __forceinline__ void reduce_and_store(const Partial& o, float* dst) {
   v = lane == 6 ? gz : v;
   v = lane == 7 ? key_float(key) : v;
   v = lane == 8 ? __int_as_float(idx) : v;
-  if (lane < 9) dst[lane] = v;
+  return v;   // lane c < 9: component c of the tile partial
+}
+
+// End of a pair (called by the whole warp once all its nodes are summed):
+// lanes c < 7 hold the FP64 sum of component c, every lane the deepest node.
+// A pair without overlap gets its zero outputs here; an overlapping pair is
+// appended to the overlap list for the force law.
+__device__ __forceinline__ void pair_done(const Params& P, const Lists& W, const PairRec& r, double* pair_out,
+                                          double sv, int idx) {
+  const int lane = threadIdx.x & 31;
+  const int q = r.pair;
+  const double s0 = __shfl_sync(kFull, sv, 0);
+  if (__double_as_longlong(s0) > 0) {   // V > 0
+    int pos = 0;
+    if (lane == 0) pos = atomicAdd(&W.counters[5], 1);
+    pos = __shfl_sync(kFull, pos, 0);
+    OvlRec* e = W.olist + pos;
+    if (lane < 7) e->s[lane] = sv;
+    if (lane == 7) e->q = q;
+    if (lane == 8) e->idx = idx;
+    if (lane >= 9 && lane < 20) (&e->i)[lane - 9] = reinterpret_cast<const int*>(&r)[lane - 9];   // i, j, lo, dim, shift
+  } else {
+    if (lane < 11) pair_out[static_cast<size_t>(q) * 11 + lane] = 0.0;
+    if (lane < kFtDoubles) W.ft[static_cast<size_t>(q) * kFtDoubles + lane] = 0.0;
+    if (lane < kTapeDoubles) W.tape[static_cast<size_t>(q) * kTapeDoubles + lane] = 0.0;
+  }
+}
+
+// After a tile: a pair of one tile is finished at once from the warp's
+// registers; otherwise the partial is stored, and the warp that completes the
+// pair's last tile sums all of them in FP64 in a fixed order (4 tile slots x
+// 8 components per lane pattern, slots combined pairwise), whichever warp
+// that is.
+__device__ __forceinline__ void tile_done(const Params& P, const Lists& W, const PairRec& r, double* pair_out,
+                                          float v) {
+  const int lane = threadIdx.x & 31;
+  if (r.ntiles == 1) {
+    const int idx = __shfl_sync(kFull, __float_as_int(v), 8);
+    pair_done(P, W, r, pair_out, lane < 7 ? widen(v) : 0.0, idx);
+    return;
+  }
+  const size_t t0 = static_cast<size_t>(r.tile0);
+  if (lane < 9) W.partial[(t0 + r.tile) * kPartialFloats + lane] = v;
+  __threadfence();
+  int prev = 0;
+  if (lane == 0) prev = atomicAdd(&W.pdone[r.pair], 1);
+  prev = __shfl_sync(kFull, prev, 0);
+  if (prev != r.ntiles - 1) return;
+  __threadfence();
+  const int nt = r.ntiles, slot = lane >> 3, c = lane & 7;
+  double acc = 0.0;
+  float bf = -FLT_MAX;
+  int bi = 0x7fffffff;
+  for (int tb = 0; tb < nt; tb += 32) {   // batches of 32 tiles, all loads in flight at once
+    float x[8];
+    int ix[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = tb + slot + 4 * u;
+      const float* q = W.partial + (t0 + (t < nt ? t : 0)) * kPartialFloats;
+      x[u] = t < nt ? __ldcg(q + c) : 0.0f;
+      ix[u] = (t < nt && c == 7) ? __float_as_int(__ldcg(q + 8)) : 0x7fffffff;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = tb + slot + 4 * u;
+      if (t < nt) {
+        if (c < 7) {
+          const double w = widen(x[u]);
+          acc = t == slot ? w : acc + w;
+        } else if (x[u] > bf || (x[u] == bf && ix[u] < bi)) {
+          bf = x[u];
+          bi = ix[u];
+        }
+      }
+    }
+  }
+  acc += __shfl_xor_sync(kFull, acc, 8);    // (s0 + s1) + (s2 + s3): the same on every lane
+  acc += __shfl_xor_sync(kFull, acc, 16);
+  for (int o = 8; o <= 16; o <<= 1) {
+    const float ob = __shfl_xor_sync(kFull, bf, o);
+    const int oi = __shfl_xor_sync(kFull, bi, o);
+    if (ob > bf || (ob == bf && oi < bi)) { bf = ob; bi = oi; }
+  }
+  pair_done(P, W, r, pair_out, acc, __shfl_sync(kFull, bi, 7));
 }
 
 // Kernel variants: the full set of pair kinds, or spheres and cuboids only
@@ -581,7 +665,7 @@ __device__ __forceinline__ void store_rec_part(PairRec* dst, int lane, int4 v) {
 
 template <bool SMOOTH, int SET>
 __global__ void __launch_bounds__(kWarps * 32, SET == SET_CUBE ? 3 : 2) k_narrow32(Params P, Shapes S, Parts D,
-                                                                                  Lists W) {
+                                                                                  Lists W, double* pair_out) {
   __shared__ __align__(16) PairRec s_rec[kWarps][2];
   __shared__ float4 s_planes[kWarps][2][kMaxFaces];
   pdl_begin();
@@ -625,7 +709,7 @@ __global__ void __launch_bounds__(kWarps * 32, SET == SET_CUBE ? 3 : 2) k_narrow
     const PairRec& r = s_rec[wid][buf];
     const Partial o = dispatch<SMOOTH, SET>(P, S, D, r, r.tile, s_planes[wid][0], s_planes[wid][1], prefetch);
     prefetch();
-    reduce_and_store<SMOOTH>(o, W.partial + static_cast<size_t>(r.tile0 + r.tile) * kPartialFloats);
+    tile_done(P, W, r, pair_out, reduce_tile<SMOOTH>(o));
     __syncwarp();
     if (tn < ntiles) store_rec_part(&s_rec[wid][buf ^ 1], lane, next);
     __syncwarp();
@@ -636,7 +720,7 @@ __global__ void __launch_bounds__(kWarps * 32, SET == SET_CUBE ? 3 : 2) k_narrow
 
 // ---------------------------------------------------------------- FP64 form
 template <bool SMOOTH>
-__global__ void __launch_bounds__(256) k_narrow64(Params P, Shapes S, Parts D, Lists W) {
+__global__ void __launch_bounds__(256) k_narrow64(Params P, Shapes S, Parts D, Lists W, double* pair_out) {
   __shared__ double s_red[8][8];
   __shared__ double s_bf[8];
   __shared__ int s_bi[8];
@@ -699,19 +783,15 @@ __global__ void __launch_bounds__(256) k_narrow64(Params P, Shapes S, Parts D, L
       s_bi[wid] = bi;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double tot[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (wid == 0) {   // lanes c < 7: component c summed over the warps in order
+      double tot = 0.0;
       double b = -DBL_MAX;
       int bidx = 0x7fffffff;
       for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) {
-        for (int k = 0; k < 7; ++k) tot[k] += s_red[w][k];
+        if (lane < 7) tot += s_red[w][lane];
         if (s_bf[w] > b || (s_bf[w] == b && s_bi[w] < bidx)) { b = s_bf[w]; bidx = s_bi[w]; }
       }
-      double* o = W.sums + static_cast<size_t>(p) * kSumDoubles;
-      for (int k = 0; k < 7; ++k) o[k] = tot[k];
-      o[7] = b;
-      o[8] = static_cast<double>(bidx);
-      o[9] = 0.0;
+      pair_done(P, W, W.pairs[p], pair_out, tot, bidx);
     }
     __syncthreads();
   }
@@ -742,23 +822,24 @@ int narrow_grid(const Params& P) {
   return sms * per_sm;
 }
 
-void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists& W, int grid, cudaStream_t st) {
+void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists& W, double* pair_out, int grid,
+                   cudaStream_t st) {
   if (P.precision == 1) {
     if (P.smooth)
-      launch_pdl(k_narrow64<true>, dim3(grid), dim3(256), 0, st, P, S, D, W);
+      launch_pdl(k_narrow64<true>, dim3(grid), dim3(256), 0, st, P, S, D, W, pair_out);
     else
-      launch_pdl(k_narrow64<false>, dim3(grid), dim3(256), 0, st, P, S, D, W);
+      launch_pdl(k_narrow64<false>, dim3(grid), dim3(256), 0, st, P, S, D, W, pair_out);
     return;
   }
   const int b = kWarps * 32;
   if (P.smooth) {
-    if (P.kind_set == SET_CUBE) launch_pdl(k_narrow32<true, SET_CUBE>, dim3(grid), dim3(b), 0, st, P, S, D, W);
-    else if (P.kind_set == SET_SC) launch_pdl(k_narrow32<true, SET_SC>, dim3(grid), dim3(b), 0, st, P, S, D, W);
-    else launch_pdl(k_narrow32<true, SET_ALL>, dim3(grid), dim3(b), 0, st, P, S, D, W);
+    if (P.kind_set == SET_CUBE) launch_pdl(k_narrow32<true, SET_CUBE>, dim3(grid), dim3(b), 0, st, P, S, D, W, pair_out);
+    else if (P.kind_set == SET_SC) launch_pdl(k_narrow32<true, SET_SC>, dim3(grid), dim3(b), 0, st, P, S, D, W, pair_out);
+    else launch_pdl(k_narrow32<true, SET_ALL>, dim3(grid), dim3(b), 0, st, P, S, D, W, pair_out);
   } else {
-    if (P.kind_set == SET_CUBE) launch_pdl(k_narrow32<false, SET_CUBE>, dim3(grid), dim3(b), 0, st, P, S, D, W);
-    else if (P.kind_set == SET_SC) launch_pdl(k_narrow32<false, SET_SC>, dim3(grid), dim3(b), 0, st, P, S, D, W);
-    else launch_pdl(k_narrow32<false, SET_ALL>, dim3(grid), dim3(b), 0, st, P, S, D, W);
+    if (P.kind_set == SET_CUBE) launch_pdl(k_narrow32<false, SET_CUBE>, dim3(grid), dim3(b), 0, st, P, S, D, W, pair_out);
+    else if (P.kind_set == SET_SC) launch_pdl(k_narrow32<false, SET_SC>, dim3(grid), dim3(b), 0, st, P, S, D, W, pair_out);
+    else launch_pdl(k_narrow32<false, SET_ALL>, dim3(grid), dim3(b), 0, st, P, S, D, W, pair_out);
   }
 }
 

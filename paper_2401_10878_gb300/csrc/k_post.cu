@@ -14,197 +14,241 @@ namespace gbc {
 
 namespace {
 
-__device__ __forceinline__ void cross(const double a[3], const double b[3], double c[3]) {
-  c[0] = a[1] * b[2] - a[2] * b[1];
-  c[1] = a[2] * b[0] - a[0] * b[2];
-  c[2] = a[0] * b[1] - a[1] * b[0];
+constexpr unsigned kFull = 0xffffffffu;
+
+// 1/sqrt(a) for a > 0: FP32 seed (the double's leading 24 bits, rsqrt.approx)
+// and two Newton-Raphson steps y <- y + y (1 - a y^2) / 2 in FP64 (each step
+// squares the relative error: 2^-22 -> ~1e-13 -> FP64 rounding).  Arguments
+// outside the FP32 exponent range take the library square root.
+__device__ __forceinline__ double nr_rsqrt(double a) {
+  const unsigned hi = static_cast<unsigned>(__double2hiint(a));
+  const unsigned lo = static_cast<unsigned>(__double2loint(a));
+  const int e = static_cast<int>((hi >> 20) & 0x7ffu) - 896;
+  if (e < 1 || e > 254 || (hi >> 31)) return 1.0 / sqrt(a);
+  const float af = __uint_as_float((static_cast<unsigned>(e) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+  float yf;
+  asm("rsqrt.approx.f32 %0, %1;" : "=f"(yf) : "f"(af));
+  double y = widen(yf);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double h = a * y;
+    const double r = fma(-h, y, 1.0);
+    y = fma(0.5 * y, r, y);
+  }
+  return y;
 }
 
-// K6: FP64 per-pair reduction and force law.  Every lane first sums its
-// pair's tile partials in FP64 (tile order) and writes zeros for pairs without
-// overlap; the overlapping pairs of the block are then compacted so that the
-// FP64-heavy part (on GB300 every FP64 warp instruction occupies the SM's
-// narrow FP64 pipe, however many lanes are active) runs with full warps.
-constexpr int kFinBlock = 64;
+// max of two doubles by their order-preserving integer keys (no FP64 instruction)
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dmax(double a, double b) { return dkey(a) >= dkey(b) ? a : b; }
+
+// Exact int -> FP64 conversion with integer operations (|v| < 2^31).
+__device__ __forceinline__ double int_to_double(int v) {
+  if (v == 0) return 0.0;
+  const unsigned long long sgn = v < 0 ? (1ULL << 63) : 0ULL;
+  const unsigned a = v < 0 ? 0u - static_cast<unsigned>(v) : static_cast<unsigned>(v);
+  const int lz = __clz(a);
+  const unsigned long long frac = (static_cast<unsigned long long>(a) << (lz + 21)) & ((1ULL << 52) - 1ULL);
+  return __longlong_as_double(static_cast<long long>(sgn | (static_cast<unsigned long long>(1054 - lz) << 52) | frac));
+}
+
+// K6: FP64 force law of the overlapping pairs (the node sweep's epilogue has
+// reduced every pair to FP64 sums, written the zero outputs of the pairs
+// without overlap and listed the others).  Four lanes per pair (component
+// k = 0..2 on lanes 0..2, lane 3 for the fourth reciprocal square root),
+// eight pairs per warp, one warp per block: every FP64 warp instruction
+// occupies a sub-partition's FP64 pipe for ~64 cycles however many lanes are
+// active, so the per-pair chain is split over the components and the warps
+// are spread over the sub-partitions.
+constexpr int kFinBlock = 32;
+constexpr int kPairsPerPass = 8;
+
+__device__ __forceinline__ double shape_value(int type, double prm0, double prmk, const double* planes, int nf, int k,
+                                              const double r[3], const double y[3], double yk) {
+  if (type == 0) {   // sphere: |r| - radius (the same on the pair's lanes)
+    const double rr = fma(r[2], r[2], fma(r[1], r[1], r[0] * r[0]));
+    const double nr = __double_as_longlong(rr) > 0 ? rr * nr_rsqrt(rr) : 0.0;
+    return nr - prm0;
+  }
+  if (type == 1) return fabs(yk) - prmk;       // cuboid: this lane's face pair
+  double best = -1e300;                          // polytope: faces k, k + 3, ...
+  for (int f = k; f < nf; f += 3) {
+    const double* e = planes + 4 * f;
+    best = dmax(best, fma(e[2], y[2], fma(e[1], y[1], e[0] * y[0])) - e[3]);
+  }
+  return best;
+}
 
 __global__ void __launch_bounds__(kFinBlock) k_finalize(Params P, Shapes S, Parts D, Lists W,
                                                         const double* __restrict__ vel,
                                                         double* __restrict__ pair_out) {
-  __shared__ double s_sum[kFinBlock][9];
-  __shared__ int s_pair[kFinBlock];
-  __shared__ int s_count;
   pdl_begin();
-  const int np = min(W.counters[0], P.max_pairs);
-  const bool tiles_ok = P.precision == 1 || W.counters[1] <= P.max_tiles;
-  const int tid = threadIdx.x;
-  for (int base = blockIdx.x * kFinBlock; base < np; base += gridDim.x * kFinBlock) {
-    if (tid == 0) s_count = 0;
-    __syncthreads();
-    const int p = base + tid;
-    if (p < np) {
-      double s[9] = {0, 0, 0, 0, 0, 0, 0, -DBL_MAX, 0};
-      if (P.precision == 1) {
-        const double* q = W.sums + static_cast<size_t>(p) * kSumDoubles;
-        for (int k = 0; k < 9; ++k) s[k] = q[k];
-      } else if (tiles_ok) {
-        const PairRec& pr = W.pairs[p];
-        const int t0 = pr.tile0, t1 = pr.tile0 + pr.ntiles;
-        int bi = 0x7fffffff;
-        float bf = -FLT_MAX;
-        for (int t = t0; t < t1; ++t) {
-          const float* q = W.partial + static_cast<size_t>(t) * kPartialFloats;
-          for (int k = 0; k < 7; ++k) s[k] += static_cast<double>(q[k]);
-          const int qi = __float_as_int(q[8]);
-          if (q[7] > bf || (q[7] == bf && qi < bi)) { bf = q[7]; bi = qi; }
-        }
-        s[7] = bf;
-        s[8] = static_cast<double>(bi);
-      }
-      if (s[0] > 0.0 && s[7] > -DBL_MAX) {
-        const int at = atomicAdd(&s_count, 1);
-        s_pair[at] = p;
-        for (int k = 0; k < 9; ++k) s_sum[at][k] = s[k];
-      } else {
-        double* o = pair_out + static_cast<size_t>(p) * 11;
-        for (int k = 0; k < 11; ++k) o[k] = 0.0;
-        double* f = W.ft + static_cast<size_t>(p) * kFtDoubles;
-        for (int k = 0; k < kFtDoubles; ++k) f[k] = 0.0;
-        double* tp = W.tape + static_cast<size_t>(p) * kTapeDoubles;
-        for (int k = 0; k < kTapeDoubles; ++k) tp[k] = 0.0;
-      }
+  const int lane = threadIdx.x;
+  const int m = min(W.counters[5], P.max_pairs);
+  const int slot = lane >> 2, k = lane & 3, kc = k < 3 ? k : 0, b0 = lane & ~3;
+  for (int e0 = blockIdx.x * kPairsPerPass; e0 < m; e0 += gridDim.x * kPairsPerPass) {
+    const bool act = e0 + slot < m;
+    const OvlRec& er = W.olist[act ? e0 + slot : e0];
+    const int q = er.q;
+    const int i = er.i, j = er.j;
+    const int lok = er.lo[kc], d0 = er.dim[0], d1 = er.dim[1], d2 = er.dim[2], sh = er.shift[kc];
+    // one round of global loads: both particles' state and shape data
+    const double XA = D.X[3 * i + kc];
+    const double Xj = D.X[3 * j + kc];
+    const double* RA = D.R + 9 * i;
+    const double* RB = D.R + 9 * j;
+    const double ra0 = RA[kc], ra1 = RA[3 + kc], ra2 = RA[6 + kc];
+    const double rb0 = RB[kc], rb1 = RB[3 + kc], rb2 = RB[6 + kc];
+    const int ta = S.type[i], tb = S.type[j];
+    const double pa0 = S.param[3 * i], pak = S.param[3 * i + kc];
+    const double pb0 = S.param[3 * j], pbk = S.param[3 * j + kc];
+    const int fa0 = S.face_off[i], fa1 = S.face_off[i + 1], fb0 = S.face_off[j], fb1 = S.face_off[j + 1];
+    const double cc = S.compl_[i] + S.compl_[j];
+    const double* sm = er.s;
+    const double Lsel = sh == 0 ? 0.0 : (sh > 0 ? P.L[kc] : -P.L[kc]);
+    const double XB = Xj - Lsel;   // X_j - s L, s in {-1, 0, 1}
+    const double s0 = sm[0];
+    const double V = P.dx3 * s0;
+    const double Gk = P.gscale * sm[4 + kc];
+    const double G0 = __shfl_sync(kFull, Gk, b0), G1 = __shfl_sync(kFull, Gk, b0 + 1),
+               G2 = __shfl_sync(kFull, Gk, b0 + 2);
+    const double gn2 = fma(G2, G2, fma(G1, G1, G0 * G0));
+    const bool gok = __double_as_longlong(gn2) > __double_as_longlong(P.g_min2);
+    // indentation depth: FP64 re-evaluation at the deepest node
+    const int idx = min(max(er.idx, 0), d0 * d1 * d2 - 1);
+    const int ck = kc == 0 ? idx % d0 : (kc == 1 ? (idx / d0) % d1 : idx / (d0 * d1));
+    const double xk = int_to_double(lok + ck) * P.dx;
+    const double rAk = xk - XA, rBk = xk - XB;
+    double rA[3], rB[3], yA[3], yB[3];
+    for (int c = 0; c < 3; ++c) {
+    rA[c] = __shfl_sync(kFull, rAk, b0 + c);
+    rB[c] = __shfl_sync(kFull, rBk, b0 + c);
     }
-    __syncthreads();
-    if (tid < s_count) {
-      const int q = s_pair[tid];
-      double s[9];
-      for (int k = 0; k < 9; ++k) s[k] = s_sum[tid][k];
-      const PairRec& pr = W.pairs[q];
-      const int i = pr.i, j = pr.j;
-      double XA[3], XB[3];
-      for (int k = 0; k < 3; ++k) {
-        XA[k] = D.X[3 * i + k];
-        XB[k] = D.X[3 * j + k] - pr.shift[k] * P.L[k];
-      }
-      const double dx = P.dx;
-      const double V = dx * dx * dx * s[0];
-      const double inv_s0 = 1.0 / s[0];
-      double xc[3], G[3], n[3];
-      for (int k = 0; k < 3; ++k) xc[k] = (pr.lo[k] + s[1 + k] * inv_s0) * dx;
-      const double gscale = 0.5 * dx * dx * 6.0 / (P.wdx / dx);
-      for (int k = 0; k < 3; ++k) G[k] = gscale * s[4 + k];
-      const double gn = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
-      double fallback = 0.0;
-      if (gn > 1e-12 * dx * dx) {
-        const double inv = 1.0 / gn;
-        for (int k = 0; k < 3; ++k) n[k] = G[k] * inv;
-      } else {
-        fallback = 1.0;
-        const double dX[3] = {XB[0] - XA[0], XB[1] - XA[1], XB[2] - XA[2]};
-        const double nd = sqrt(dX[0] * dX[0] + dX[1] * dX[1] + dX[2] * dX[2]);
-        const double inv = nd > 0.0 ? 1.0 / nd : 0.0;
-        for (int k = 0; k < 3; ++k) n[k] = dX[k] * inv;
-      }
-      // indentation depth: FP64 re-evaluation at the deepest node
-      const int vol = pr.dim[0] * pr.dim[1] * pr.dim[2];
-      const int idx = min(max(static_cast<int>(s[8]), 0), vol - 1);
-      const int c[3] = {idx % pr.dim[0], (idx / pr.dim[0]) % pr.dim[1], idx / (pr.dim[0] * pr.dim[1])};
-      const double x[3] = {(pr.lo[0] + c[0]) * dx, (pr.lo[1] + c[1]) * dx, (pr.lo[2] + c[2]) * dx};
-      double gA[3], gB[3];
-      const double fa = sdf64(S.type[i], S.param + 3 * i, S.planes + 4 * S.face_off[i],
-                              S.face_off[i + 1] - S.face_off[i], XA, D.R + 9 * i, x, P.inflate, gA);
-      const double fb = sdf64(S.type[j], S.param + 3 * j, S.planes + 4 * S.face_off[j],
-                              S.face_off[j + 1] - S.face_off[j], XB, D.R + 9 * j, x, P.inflate, gB);
-      const double d = fmax(0.0, -(fa + fb));
-      const double estar = 1.0 / (S.compl_[i] + S.compl_[j]);
-      double damp = 1.0;
-      double ra[3], rb[3];
-      for (int k = 0; k < 3; ++k) {
-        ra[k] = xc[k] - XA[k];
-        rb[k] = xc[k] - XB[k];
-      }
-      if (vel != nullptr && P.damping_c != 0.0) {
-        const double* va = vel + 6 * i;
-        const double* vb = vel + 6 * j;
-        double wa[3], wb[3];
-        cross(va + 3, ra, wa);
-        cross(vb + 3, rb, wb);
-        double ddot = 0.0;
-        for (int k = 0; k < 3; ++k) ddot += ((va[k] + wa[k]) - (vb[k] + wb[k])) * n[k];
-        damp = fmax(0.0, 1.0 + P.damping_c * ddot);
-      }
-      const double vd = V * d;
-      const double fmag = vd > 0.0 ? (4.0 / (3.0 * 3.14159265358979323846)) * estar * sqrt(vd) * damp : 0.0;
-      double F[3], FA[3], TA[3], TB[3];
-      for (int k = 0; k < 3; ++k) {
-        F[k] = fmag * n[k];
-        FA[k] = -F[k];
-      }
-      cross(ra, FA, TA);
-      cross(rb, F, TB);
-      double* o = pair_out + static_cast<size_t>(q) * 11;
-      o[0] = V;
-      for (int k = 0; k < 3; ++k) {
-        o[1 + k] = xc[k];
-        o[4 + k] = n[k];
-        o[8 + k] = F[k];
-      }
-      o[7] = d;
-      double* f = W.ft + static_cast<size_t>(q) * kFtDoubles;
-      for (int k = 0; k < 3; ++k) {
-        f[k] = F[k];
-        f[3 + k] = TA[k];
-        f[6 + k] = TB[k];
-      }
-      double* tp = W.tape + static_cast<size_t>(q) * kTapeDoubles;
-      tp[0] = s[0];
-      for (int k = 0; k < 3; ++k) { tp[1 + k] = xc[k]; tp[4 + k] = n[k]; }
-      tp[7] = d;
-      tp[8] = gn;
-      tp[9] = fallback;
-      tp[10] = estar;
-      tp[11] = damp;
-      tp[12] = fmag;
-      tp[13] = s[8];
-      tp[14] = 0.0;
-      tp[15] = 0.0;
+    const double yAk = fma(ra2, rA[2], fma(ra1, rA[1], ra0 * rA[0]));
+    const double yBk = fma(rb2, rB[2], fma(rb1, rB[1], rb0 * rB[0]));
+    for (int c = 0; c < 3; ++c) {
+    yA[c] = __shfl_sync(kFull, yAk, b0 + c);
+    yB[c] = __shfl_sync(kFull, yBk, b0 + c);
     }
-    if (tid == 0 && s_count > 0) atomicAdd(&W.counters[5], s_count);
-    __syncthreads();
+    double vA = k < 3 ? shape_value(ta, pa0, pak, S.planes + 4 * fa0, fa1 - fa0, kc, rA, yA, yAk) : -1e300;
+    double vB = k < 3 ? shape_value(tb, pb0, pbk, S.planes + 4 * fb0, fb1 - fb0, kc, rB, yB, yBk) : -1e300;
+    vA = dmax(vA, __shfl_xor_sync(kFull, vA, 1));
+    vA = dmax(vA, __shfl_xor_sync(kFull, vA, 2));
+    vB = dmax(vB, __shfl_xor_sync(kFull, vB, 1));
+    vB = dmax(vB, __shfl_xor_sync(kFull, vB, 2));
+    const double fa = vA - P.inflate, fb = vB - P.inflate;
+    const double d = dmax(0.0, -(fa + fb));
+    const double vd = V * d;
+    const bool vok = __double_as_longlong(vd) > 0;
+    // four reciprocal square roots, one per lane: s0, E*'s compliance sum, |G|^2, V d
+    const double arg = k == 0 ? s0 : (k == 1 ? cc : (k == 2 ? (gok ? gn2 : 1.0) : (vok ? vd : 1.0)));
+    const double y = nr_rsqrt(arg);
+    const double y0 = __shfl_sync(kFull, y, b0), y1 = __shfl_sync(kFull, y, b0 + 1),
+               y2 = __shfl_sync(kFull, y, b0 + 2), y3 = __shfl_sync(kFull, y, b0 + 3);
+    const double inv_s0 = y0 * y0;
+    const double estar = y1 * y1;
+    const double xck = fma(sm[1 + kc], inv_s0, int_to_double(lok)) * P.dx;
+    double nk = Gk * y2;
+    double fallback = 0.0;
+    if (__any_sync(kFull, act && !gok)) {   // centre-line fallback normal
+    const double dXk = XB - XA;
+    const double e0v = __shfl_sync(kFull, dXk, b0), e1v = __shfl_sync(kFull, dXk, b0 + 1),
+                 e2v = __shfl_sync(kFull, dXk, b0 + 2);
+    if (!gok) {
+      fallback = 1.0;
+      const double nd2 = fma(e2v, e2v, fma(e1v, e1v, e0v * e0v));
+      nk = __double_as_longlong(nd2) > 0 ? dXk * nr_rsqrt(nd2) : 0.0;
+    }
+    }
+    const double gn = gok ? gn2 * y2 : 0.0;
+    const double rak = xck - XA, rbk = xck - XB;
+    // components k1 = k+1, k2 = k+2 (mod 3) of the lever arms, for the cross products
+    const int k1 = kc == 2 ? 0 : kc + 1, k2 = kc == 0 ? 2 : kc - 1;
+    const double ra1v = __shfl_sync(kFull, rak, b0 + k1), ra2v = __shfl_sync(kFull, rak, b0 + k2);
+    const double rb1v = __shfl_sync(kFull, rbk, b0 + k1), rb2v = __shfl_sync(kFull, rbk, b0 + k2);
+    double damp = 1.0;
+    if (vel != nullptr && P.damping_c != 0.0) {
+    const double* va = vel + 6 * i;
+    const double* vb = vel + 6 * j;
+    // relative normal speed (v_A + w_A x r_A - v_B - w_B x r_B) . n
+    const double wak = fma(va[3 + k1], ra2v, -va[3 + k2] * ra1v);
+    const double wbk = fma(vb[3 + k1], rb2v, -vb[3 + k2] * rb1v);
+    const double uk = ((va[kc] + wak) - (vb[kc] + wbk)) * nk;
+    const double u0 = __shfl_sync(kFull, uk, b0), u1 = __shfl_sync(kFull, uk, b0 + 1),
+                 u2 = __shfl_sync(kFull, uk, b0 + 2);
+    damp = dmax(0.0, fma(P.damping_c, (u0 + u1) + u2, 1.0));
+    }
+    const double fmag = vok ? (4.0 / (3.0 * 3.14159265358979323846)) * estar * (vd * y3) * damp : 0.0;
+    const double Fk = fmag * nk;
+    const double F1 = __shfl_sync(kFull, Fk, b0 + k1), F2 = __shfl_sync(kFull, Fk, b0 + k2);
+    // T_A = r_A x (-F), T_B = r_B x F
+    const double TAk = fma(ra2v, F1, -ra1v * F2);
+    const double TBk = fma(rb1v, F2, -rb2v * F1);
+    if (act) {
+    double* o = pair_out + static_cast<size_t>(q) * 11;
+    double* f = W.ft + static_cast<size_t>(q) * kFtDoubles;
+    double* tp = W.tape + static_cast<size_t>(q) * kTapeDoubles;
+    if (k < 3) {
+      o[1 + k] = xck; o[4 + k] = nk; o[8 + k] = Fk;
+      f[k] = Fk; f[3 + k] = TAk; f[6 + k] = TBk;
+      tp[1 + k] = xck; tp[4 + k] = nk;
+    }
+    if (k == 0) {
+      o[0] = V; o[7] = d;
+      tp[0] = s0; tp[7] = d; tp[8] = gn; tp[9] = fallback;
+    } else if (k == 3) {
+      tp[10] = estar; tp[11] = damp; tp[12] = fmag; tp[13] = int_to_double(idx);
+      tp[14] = 0.0; tp[15] = 0.0;
+    }
+    }
   }
 }
 
-// K7: one lane per particle (FP64 adds in full warps).  Its contributions are
-// added in this order: the pairs where it is j (by i), then the pairs where it
-// is i (by j).
+// K7: per particle and component (eight lanes per particle, six used), FP64
+// adds in a fixed order: the pairs where the particle is j (by i), then the
+// pairs where it is i (by j).  j receives +F and T_B, i receives -F and T_A.
+// The first eight lower-partner pair indices are fetched together with the
+// counts.
 __global__ void __launch_bounds__(128) k_particle_sum(Params P, Parts D, Lists W, double* __restrict__ force,
                                                       double* __restrict__ torque) {
   pdl_begin();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p == 0) *W.err_host = *W.err;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) *W.err_host = *W.err;
   // the cell list's bin counts start the next step at zero
   const int nbins = P.nbin[0] * P.nbin[1] * P.nbin[2];
-  for (int b = p; b < nbins; b += gridDim.x * blockDim.x) W.bin_count[b] = 0;
-  if (p >= P.n) return;
+  for (int b = t; b < nbins; b += gridDim.x * blockDim.x) W.bin_count[b] = 0;
+  const int p = t >> 3, c = t & 7;
+  if (p >= P.n || c >= 6) return;
+  const int* dp = W.dn_pair + static_cast<size_t>(p) * P.max_nbr;
+  int pre[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) pre[u] = u < P.max_nbr ? dp[u] : 0;
   const int np = min(W.counters[0], P.max_pairs);
   const int nd = W.dn_count[p], nu = W.up_count[p], r0 = W.row_off[p];
-  const int* dp = W.dn_pair + static_cast<size_t>(p) * P.max_nbr;
-  double f0 = 0, f1 = 0, f2 = 0, t0 = 0, t1 = 0, t2 = 0;
-  for (int r = 0; r < nd; ++r) {
-    const int q = dp[r];
-    if (q >= np) continue;
-    const double* x = W.ft + static_cast<size_t>(q) * kFtDoubles;
-    f0 += x[0]; f1 += x[1]; f2 += x[2];
-    t0 += x[6]; t1 += x[7]; t2 += x[8];
+  const int offj = c < 3 ? c : c + 3, offi = c;
+  const long long flip_i = c < 3 ? static_cast<long long>(0x8000000000000000ULL) : 0LL;
+  const int total = nd + nu;
+  double acc = 0.0;
+  for (int base = 0; base < total; base += 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u;
+      const bool isj = e < nd;
+      const int q = isj ? (base == 0 ? pre[u] : dp[e]) : (e < total ? r0 + (e - nd) : np);
+      const bool ok = q >= 0 && q < np;
+      const long long b = ok ? __double_as_longlong(W.ft[static_cast<size_t>(q) * kFtDoubles + (isj ? offj : offi)]) : 0LL;
+      v[u] = __longlong_as_double(isj ? b : b ^ flip_i);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (base + u < total) acc += v[u];
   }
-  for (int r = 0; r < nu; ++r) {
-    const int q = r0 + r;
-    if (q >= np) break;
-    const double* x = W.ft + static_cast<size_t>(q) * kFtDoubles;
-    f0 -= x[0]; f1 -= x[1]; f2 -= x[2];
-    t0 += x[3]; t1 += x[4]; t2 += x[5];
-  }
-  force[3 * p] = f0; force[3 * p + 1] = f1; force[3 * p + 2] = f2;
-  torque[3 * p] = t0; torque[3 * p + 1] = t1; torque[3 * p + 2] = t2;
+  if (c < 3) force[3 * p + c] = acc;
+  else torque[3 * p + c - 3] = acc;
 }
 
 }  // namespace
@@ -214,15 +258,15 @@ void launch_finalize(const Params& P, const Shapes& S, const Parts& D, const Lis
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int need = (P.max_pairs + kFinBlock - 1) / kFinBlock;
-  const int grid = need < 4 * sms ? (need > 0 ? need : 1) : 4 * sms;
+  const int need = (P.max_pairs + kPairsPerPass - 1) / kPairsPerPass;
+  const int grid = need < 8 * sms ? (need > 0 ? need : 1) : 8 * sms;
   launch_pdl(k_finalize, dim3(grid), dim3(kFinBlock), 0, st, P, S, D, W, vel, pair_out);
 }
 
 void launch_particle_sum(const Params& P, const Parts& D, const Lists& W, double* force, double* torque,
                          cudaStream_t st) {
-  const int nb = (P.n + 31) / 32;
-  launch_pdl(k_particle_sum, dim3(nb > 0 ? nb : 1), dim3(32), 0, st, P, D, W, force, torque);
+  const int nb = (8 * P.n + 127) / 128;
+  launch_pdl(k_particle_sum, dim3(nb > 0 ? nb : 1), dim3(128), 0, st, P, D, W, force, torque);
 }
 
 }  // namespace gbc

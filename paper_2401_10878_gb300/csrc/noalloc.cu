@@ -68,12 +68,13 @@ struct Carver {
 
 // Derived per-particle tables and the zero-initialised words of the step.
 __global__ void k_noalloc_prep(Params P, int* type, int* kind, double* param, float* size_l, int* nomops,
-                               const double* young, const double* poisson, double* compl_, int* face_off,
-                               int* vert_off, Lists W, int nbins) {
+                               const double* young, const double* poisson, double* compl_, double* ext,
+                               int* face_off, int* vert_off, Lists W, int nbins) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < P.n) {
     const int ty = type[t];
     compl_[t] = (1.0 - poisson[t] * poisson[t]) / young[t];
+    for (int k = 0; k < 3; ++k) ext[3 * t + k] = (ty == 0 && k > 0) ? 0.0 : __dadd_rn(param[3 * t + k], P.delta);
     const double* q = param + 3 * t;
     kind[t] = ty == 0 ? KIND_SPHERE : ((q[0] == q[1] && q[0] == q[2]) ? KIND_CUBE : KIND_CUBOID);
     nomops[t] = ty == 0 ? 7 : 15;
@@ -157,6 +158,9 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   P.delta = delta;
   P.inflate = C.inflate;
   P.wdx = C.smooth_width * C.dx;
+  P.dx3 = C.dx * C.dx * C.dx;
+  P.gscale = 0.5 * C.dx * C.dx * 6.0 / (P.wdx / C.dx);
+  P.g_min2 = 1e-24 * C.dx * C.dx * C.dx * C.dx;
   P.smooth = C.indicator;
   P.precision = CONTACT_PRECISION_FP32_TILE;
   P.kind_set = 1;
@@ -189,15 +193,17 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   float* size_l = cv.take<float>(3 * N);
   int* nomops = cv.take<int>(N);
   double* compl_ = cv.take<double>(N);
+  double* ext = cv.take<double>(3 * N);
+  float* verts32 = cv.take<float>(3);
+  float* off32 = cv.take<float>(1);
   int* face_off = cv.take<int>(N + 1);
   int* vert_off = cv.take<int>(N + 1);
   double* planes = cv.take<double>(4);
   double* verts = cv.take<double>(3);
-  Shapes S{type, param, face_off, planes, vert_off, verts, yv, pv, size_l, nomops, compl_};
+  Shapes S{type, param, face_off, planes, vert_off, verts, yv, pv, size_l, nomops, compl_, ext, verts32, off32};
   Parts D{};
   D.X = cv.take<double>(3 * N);
   D.qhat = cv.take<double>(4 * N);
-  D.qnorm = cv.take<double>(N);
   D.R = cv.take<double>(9 * N);
   D.lohi = cv.take<int>(6 * N);
   D.bin = cv.take<int>(N);
@@ -221,7 +227,8 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   W.tile_pair = cv.take<int>(MT);
   W.tiles = cv.take<PairRec>(MT * kCostBuckets);
   W.partial = cv.take<float>(MT * kPartialFloats);
-  W.sums = cv.take<double>(MP * kSumDoubles);
+  W.pdone = cv.take<int>(MP);
+  W.olist = cv.take<OvlRec>(MP);
   W.tape = cv.take<double>(MP * kTapeDoubles);
   W.ft = cv.take<double>(MP * kFtDoubles);
   W.kind = kind;
@@ -239,14 +246,14 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   if (e == cudaSuccess) e = cudaMemcpyAsync(pv, poisson, N * sizeof(double), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return CONTACT_ECUDA;
   const int threads = 256, blocks = (n + 1 + threads - 1) / threads;
-  k_noalloc_prep<<<blocks, threads, 0, s>>>(P, type, kind, param, size_l, nomops, yv, pv, compl_, face_off,
+  k_noalloc_prep<<<blocks, threads, 0, s>>>(P, type, kind, param, size_l, nomops, yv, pv, compl_, ext, face_off,
                                             vert_off, W, nbins);
   // the step's kernels, unchanged, on the scratch array
   launch_pose(P, S, D, W, pos, quat, s);
   launch_bin_scatter(P, D, W, s);
   launch_broad(P, D, W, s);
   launch_plan(P, S, D, W, pair_ij, n_pairs, s);
-  launch_narrow(P, S, D, W, narrow_grid(P), s);
+  launch_narrow(P, S, D, W, pair_out, narrow_grid(P), s);
   launch_finalize(P, S, D, W, nullptr, pair_out, s);
   launch_particle_sum(P, D, W, force, torque, s);
   if (cudaGetLastError() != cudaSuccess) return CONTACT_ECUDA;
