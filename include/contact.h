@@ -52,7 +52,10 @@ typedef enum {
   CONTACT_EINVAL = 1,    /* invalid argument or input value                   */
   CONTACT_ENOMEM = 2,    /* device or host allocation failed (contact_init)   */
   CONTACT_ECUDA = 3,     /* a CUDA runtime call failed                        */
-  CONTACT_ECAPACITY = 4, /* more pairs / neighbours / tiles than configured   */
+  CONTACT_ECAPACITY = 4, /* more pairs / neighbours / tiles than configured,
+                            or more particle centres in one cell-list bin than
+                            its capacity (twice the bin volume over the
+                            smallest inscribed ball, plus 8)                   */
   CONTACT_EDOMAIN = 5,   /* periodic box too small for the largest particle   */
   CONTACT_ETIMEOUT = 6,  /* a bounded device wait ran out                     */
   CONTACT_ESTATE = 7     /* call out of order (e.g. backward before a step)   */

@@ -52,6 +52,7 @@ struct Params {
   int dx_pow2;           // 1: dx is a power of two, so x / dx == x * inv_dx exactly
   double damping_c;
   int nbin[3];           // bins per axis
+  int bin_cap;           // particles one bin can hold (bin_items row length)
   double binw[3];        // bin width (physical)
   float inv_binw_f[3];   // FP32 reciprocal of the bin width
   int max_pairs, max_nbr, max_tiles;
@@ -84,7 +85,6 @@ struct Parts {
   double* R;       // [N,9] FP64 rotation, row-major, body -> world
   int* lohi;       // [N,6]
   int* bin;        // [N]
-  int* slot;       // [N]
   float* Rt;       // [N,9] FP32 R^T (row k = body axis k in world)
   float4* wplane;  // [F] FP32 world normal, offset (lattice units, incl. inflate)
   float* Xf;       // [N,3] FP32 positions (periodic image choice only)
@@ -135,14 +135,14 @@ static_assert(sizeof(OvlRec) == 128, "one overlap record per 128-byte line");
 
 struct Lists {
   int* bin_count;   // [nbins]
-  int* bin_start;   // [nbins + 1]
-  int* bin_items;   // [N]
+  int* bin_items;   // [nbins, bin_cap] particles of each bin, in arrival order
   int* up_count;    // [N] partners j > p
   int* up_list;     // [N, max_nbr]
   int* dn_count;    // [N] partners i < p
   int* dn_list;     // [N, max_nbr]
   int* dn_pair;     // [N, max_nbr] pair index of (dn_list[p][r], p)
   int* row_off;     // [N + 1] first pair of particle i
+  int* grp_sum;     // [ceil(N / 256)] partners above, summed over groups of 256 particles
   PairRec* pairs;   // [max_pairs]
   int* tile_pair;   // [max_tiles] pair of each tile
   PairRec* tiles;   // [kCostBuckets, max_tiles] one record per tile (the pair's record with tile and
@@ -246,7 +246,7 @@ __device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0
 
 // Exact FP32 -> FP64 conversion with integer operations (IEEE 754: sign kept,
 // exponent rebiased by 1023 - 127, fraction widened by 29 bits; subnormals
-// normalised): widening the partials costs no FP64 instruction.
+// normalised): no FP64 instruction, for kernels whose FP64 pipe is the limit.
 __device__ __forceinline__ double widen(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned sgn = u & 0x80000000u;
@@ -309,10 +309,11 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 // Launch wrappers (defined in the kernel translation units).
 void launch_pose(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* pos,
                  const double* quat, cudaStream_t st);
-void launch_bin_scatter(const Params& P, const Parts& D, const Lists& W, cudaStream_t st);
 void launch_broad(const Params& P, const Parts& D, const Lists& W, cudaStream_t st);
 void launch_plan(const Params& P, const Shapes& S, const Parts& D, const Lists& W, int32_t* pair_ij, int32_t* n_pairs,
                  cudaStream_t st);
+constexpr int kRowGroup = 256;   // particles per group sum of the pair-row offsets
+int bin_capacity(int n, const double binw[3], double rin_min, long long nbins, long long max_entries);
 void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists& W, double* pair_out, int grid,
                    cudaStream_t st);
 int narrow_grid(const Params& P);

@@ -1,6 +1,7 @@
 // Host side of libcontact: context, shape preparation, validation, buffer
 // allocation, launch sequencing, CUDA-graph replay and error reporting.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -46,6 +47,25 @@ contact_status fail(contact_ctx* c, contact_status s, const std::string& msg) {
 contact_status cuda_fail(contact_ctx* c, cudaError_t e, const char* what) {
   return fail(c, CONTACT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
+
+}  // namespace
+
+namespace gbc {
+// Slots per cell-list bin: at most n, else twice the bin volume over the
+// smallest inscribed-ball volume plus 8 (particles overlap only by their
+// contact indentation, so far fewer centres fit in a bin), at least 16, and
+// at most max_entries / nbins.  A fuller bin is reported as ECAPACITY.
+int bin_capacity(int n, const double binw[3], double rin_min, long long nbins, long long max_entries) {
+  const double vmin = 4.0 / 3.0 * 3.14159265358979323846 * rin_min * rin_min * rin_min;
+  const double bound = 2.0 * binw[0] * binw[1] * binw[2] / vmin + 8.0;
+  long long cap = bound < static_cast<double>(n) ? static_cast<long long>(std::ceil(bound)) : n;
+  cap = std::max<long long>(std::min<long long>(cap, n), std::min<long long>(16, n));
+  cap = std::min<long long>(cap, std::max<long long>(1, max_entries / std::max<long long>(1, nbins)));
+  return static_cast<int>(cap);
+}
+}  // namespace gbc
+
+namespace {
 
 template <class T>
 cudaError_t dev_alloc(contact_ctx* c, T** p, size_t count) {
@@ -139,7 +159,6 @@ void enqueue_step(contact_ctx* c, bool capturing, const double* pos, const doubl
   const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   // bin counts are zero: contact_init clears them, every step's last kernel clears them again
   launch_pose(c->P, c->S, c->D, c->W, pos, quat, c->stream);
-  launch_bin_scatter(c->P, c->D, c->W, c->stream);
   launch_broad(c->P, c->D, c->W, c->stream);
   launch_plan(c->P, c->S, c->D, c->W, pair_ij, n_pairs, c->stream);
   if (c->cfg.narrow_events) cudaEventRecordWithFlags(c->ev_narrow[0], c->stream, ev_flags);
@@ -207,6 +226,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   const int nfaces = face_offset[n];
   if (face_offset[0] != 0 || nfaces < 0 || (nfaces > 0 && planes == nullptr)) return CONTACT_EINVAL;
   double rmax = 0.0;
+  double rin_min = DBL_MAX;   // smallest inscribed-ball radius (bounds how many particles one bin holds)
   for (int p = 0; p < n; ++p) {
     type[p] = shape_type[p];
     for (int k = 0; k < 3; ++k) param[3 * p + k] = shape_param[3 * p + k];
@@ -217,6 +237,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
     if (type[p] == CONTACT_SHAPE_SPHERE) {
       if (!(param[3 * p] > 0.0) || f1 != f0) return CONTACT_EINVAL;
       circ = param[3 * p] + delta;
+      rin_min = std::min(rin_min, param[3 * p]);
       ext[3 * p] = param[3 * p] + delta;
       kind[p] = KIND_SPHERE;
       nomops[p] = 7;
@@ -231,6 +252,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
         size_l[3 * p + k] = static_cast<float>((param[3 * p + k] + C.inflate) / C.dx);
       }
       circ = std::sqrt(e2);
+      rin_min = std::min(rin_min, std::min(param[3 * p], std::min(param[3 * p + 1], param[3 * p + 2])));
       kind[p] = (param[3 * p] == param[3 * p + 1] && param[3 * p] == param[3 * p + 2]) ? KIND_CUBE : KIND_CUBOID;
       nomops[p] = 15;
     } else if (type[p] == CONTACT_SHAPE_POLYTOPE) {
@@ -241,6 +263,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
         const double* e = pl + 4 * f;
         const double nn = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
         if (!(std::fabs(nn - 1.0) <= 1e-9) || !(e[3] > 0.0) || !std::isfinite(e[3])) return CONTACT_EINVAL;
+        rin_min = std::min(rin_min, e[3]);   // unit normals, origin inside: the ball of radius min d fits
       }
       if (!bounded(pl, F)) return CONTACT_EINVAL;
       std::vector<double> v = offset_vertices(pl, F, delta);
@@ -279,6 +302,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
     P.binw[k] = L[k] / nb;
     P.inv_binw_f[k] = static_cast<float>(nb / L[k]);
   }
+  P.bin_cap = bin_capacity(n, P.binw, rin_min, static_cast<long long>(P.nbin[0]) * P.nbin[1] * P.nbin[2], 1LL << 26);
   P.dx = C.dx;
   P.inv_dx = 1.0 / C.dx;
   {
@@ -351,7 +375,6 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   GBC_TRY(dev_alloc(c, &D.R, 9 * static_cast<size_t>(n)));
   GBC_TRY(dev_alloc(c, &D.lohi, 6 * static_cast<size_t>(n)));
   GBC_TRY(dev_alloc(c, &D.bin, static_cast<size_t>(n)));
-  GBC_TRY(dev_alloc(c, &D.slot, static_cast<size_t>(n)));
   GBC_TRY(dev_alloc(c, &D.Rt, 9 * static_cast<size_t>(n)));
   GBC_TRY(dev_alloc(c, &D.wplane, static_cast<size_t>(std::max(nfaces, 1))));
   GBC_TRY(dev_alloc(c, &D.Xf, 3 * static_cast<size_t>(n)));
@@ -362,14 +385,14 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   const size_t nbins = static_cast<size_t>(P.nbin[0]) * P.nbin[1] * P.nbin[2];
   const size_t mp = static_cast<size_t>(C.max_pairs), mt = static_cast<size_t>(P.max_tiles);
   GBC_TRY(dev_alloc(c, &W.bin_count, nbins));
-  GBC_TRY(dev_alloc(c, &W.bin_start, nbins + 1));
-  GBC_TRY(dev_alloc(c, &W.bin_items, static_cast<size_t>(n)));
+  GBC_TRY(dev_alloc(c, &W.bin_items, nbins * static_cast<size_t>(P.bin_cap)));
   GBC_TRY(dev_alloc(c, &W.up_count, static_cast<size_t>(n)));
   GBC_TRY(dev_alloc(c, &W.up_list, static_cast<size_t>(n) * max_nbr));
   GBC_TRY(dev_alloc(c, &W.dn_count, static_cast<size_t>(n)));
   GBC_TRY(dev_alloc(c, &W.dn_list, static_cast<size_t>(n) * max_nbr));
   GBC_TRY(dev_alloc(c, &W.dn_pair, static_cast<size_t>(n) * max_nbr));
   GBC_TRY(dev_alloc(c, &W.row_off, static_cast<size_t>(n) + 1));
+  GBC_TRY(dev_alloc(c, &W.grp_sum, static_cast<size_t>((n + kRowGroup - 1) / kRowGroup)));
   GBC_TRY(dev_alloc(c, &W.pairs, mp));
   GBC_TRY(dev_alloc(c, &W.tile_pair, mt));
   GBC_TRY(dev_alloc(c, &W.tiles, mt * kCostBuckets));
@@ -523,7 +546,7 @@ contact_status contact_narrow_time(contact_ctx* c, float* ms) {
   return e == cudaSuccess ? CONTACT_OK : cuda_fail(c, e, "cudaEventElapsedTime");
 }
 
-int32_t contact_kernels_per_step(const contact_ctx*) { return 8; }
+int32_t contact_kernels_per_step(const contact_ctx*) { return 6; }
 int32_t contact_kernels_per_backward(const contact_ctx*) { return 4; }
 
 contact_status contact_backward(contact_ctx* c, const double* grad_force, const double* grad_torque,

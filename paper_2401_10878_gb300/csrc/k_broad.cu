@@ -29,6 +29,17 @@ __global__ void k_pose(Params P, Shapes S, Parts D, Lists W, const double* __res
                        const double* __restrict__ quat) {
   pdl_begin();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  // the step's counters start at zero (the previous step has completed)
+  if (t == 0) {
+    W.counters[0] = 0;   // pairs
+    W.counters[1] = 0;   // tiles allocated
+    W.counters[2] = 0;   // node-sweep queue head
+    W.counters[5] = 0;   // pairs with V > 0
+    for (int b = 0; b < kCostBuckets; ++b) W.counters[8 + b] = 0;
+    W.u64[0] = 0;        // node evaluations
+    W.u64[1] = 0;        // nominal lane-ops
+  }
+  if (t < (P.n + kRowGroup - 1) / kRowGroup) W.grp_sum[t] = 0;
   if (t >= 3 * P.n) return;
   const int p = t / 3, k = t - 3 * p;
   double q[4];
@@ -124,50 +135,10 @@ __global__ void k_pose(Params P, Shapes S, Parts D, Lists W, const double* __res
     for (int cc = 0; cc < 3; ++cc) b[cc] = min(max(static_cast<int>(xs[cc] * P.inv_binw_f[cc]), 0), P.nbin[cc] - 1);
     const int bin = b[0] + P.nbin[0] * (b[1] + P.nbin[1] * b[2]);
     D.bin[p] = bin;
-    D.slot[p] = atomicAdd(&W.bin_count[bin], 1);
+    const int slot = atomicAdd(&W.bin_count[bin], 1);
+    if (slot < P.bin_cap) W.bin_items[static_cast<size_t>(bin) * P.bin_cap + slot] = p;
+    else set_error(W.err, kErrCapacity);
   }
-}
-
-// ---------------------------------------------------------------------------
-// Block-wide exclusive scan of n ints in global memory (one CTA of 1024
-// threads, each scanning a contiguous chunk).  Returns the total.
-__device__ long long block_scan_excl(int* data, int n, long long* s_tmp) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int chunk = (n + nt - 1) / nt;
-  const int b = min(n, tid * chunk), e = min(n, b + chunk);
-  long long s = 0;
-  for (int i = b; i < e; ++i) s += data[i];
-  s_tmp[tid] = s;
-  __syncthreads();
-  // Hillis-Steele over the 1024 chunk sums
-  for (int off = 1; off < nt; off <<= 1) {
-    const long long v = (tid >= off) ? s_tmp[tid - off] : 0;
-    __syncthreads();
-    s_tmp[tid] += v;
-    __syncthreads();
-  }
-  const long long total = s_tmp[nt - 1];
-  long long run = s_tmp[tid] - s;
-  for (int i = b; i < e; ++i) {
-    const int v = data[i];
-    data[i] = static_cast<int>(run);
-    run += v;
-  }
-  __syncthreads();
-  return total;
-}
-
-// K2: bin offsets and particle ids grouped by bin (single CTA).
-__global__ void __launch_bounds__(1024) k_bin_scatter(Params P, Parts D, Lists W) {
-  __shared__ long long s_tmp[1024];
-  pdl_begin();
-  const int nbins = P.nbin[0] * P.nbin[1] * P.nbin[2];
-  for (int i = threadIdx.x; i < nbins; i += blockDim.x) W.bin_start[i] = W.bin_count[i];
-  __syncthreads();
-  const long long total = block_scan_excl(W.bin_start, nbins, s_tmp);
-  if (threadIdx.x == 0) W.bin_start[nbins] = static_cast<int>(total);
-  __syncthreads();
-  for (int p = threadIdx.x; p < P.n; p += blockDim.x) W.bin_items[W.bin_start[D.bin[p]] + D.slot[p]] = p;
 }
 
 // Node box of pair (p, q) with q's image nearest p; returns false if empty.
@@ -191,10 +162,11 @@ __device__ __forceinline__ bool pair_box(const Params& P, const Parts& D, int p,
   return hit;
 }
 
-// K3: one warp per particle.  Lanes 0..26 fetch the ranges of the 27
-// neighbour bins at once; the candidates of all bins are then swept as one
-// flat list, 32 per round, and compacted with warp ballots into partners
-// above (j > p) and below (j < p); each list is sorted by rank.
+// K3: one warp per particle p.  Lane b < 27 owns neighbour bin b of the
+// fixed-capacity cell list; the candidates are read four per lane at a time
+// (their particle data loaded together), tested against p's node range, and
+// compacted with warp ballots into partners above (j > p) and below (j < p);
+// each list is then sorted by rank.
 __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
   extern __shared__ int s_buf[];
   pdl_begin();
@@ -205,12 +177,21 @@ __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
   int* up = s_buf + wid * 2 * cap;
   int* dn = up + cap;
   const int bin = D.bin[p];
+  float xp[3];
+  int plo[3], phi[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    xp[k] = D.Xf[3 * p + k];
+    plo[k] = D.lohi[6 * p + k];
+    phi[k] = D.lohi[6 * p + 3 + k];
+  }
   const int b[3] = {bin % P.nbin[0], (bin / P.nbin[0]) % P.nbin[1], bin / (P.nbin[0] * P.nbin[1])};
   int cnt[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) cnt[k] = P.nbin[k] >= 3 ? 3 : P.nbin[k];
   const int nnb = cnt[0] * cnt[1] * cnt[2];
-  int beg = 0, num = 0;
+  int num = 0;
+  const int* items = W.bin_items;
   if (lane < nnb) {
     int o[3] = {lane % cnt[0], (lane / cnt[0]) % cnt[1], lane / (cnt[0] * cnt[1])};
 #pragma unroll
@@ -219,44 +200,55 @@ __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
       o[k] = (c + P.nbin[k]) % P.nbin[k];
     }
     const int q = o[0] + P.nbin[0] * (o[1] + P.nbin[1] * o[2]);
-    beg = W.bin_start[q];
-    num = W.bin_start[q + 1] - beg;
+    num = min(W.bin_count[q], P.bin_cap);
+    items += static_cast<size_t>(q) * P.bin_cap;
   }
-  // exclusive prefix of the bin sizes over the lanes
-  int off = num;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int v = __shfl_up_sync(kFull, off, d);
-    if (lane >= d) off += v;
-  }
-  const int total = __shfl_sync(kFull, off, 31);
-  off -= num;
+  const int maxn = __reduce_max_sync(kFull, num);
   int nup = 0, ndn = 0;
   const unsigned below = (1u << lane) - 1u;
-  for (int base = 0; base < total; base += 32) {
-    const int e = base + lane;
-    // bin of flat candidate e: the last lane whose offset is <= e
-    int src = 0;
-    for (int t = 1; t < nnb; ++t) src = (e >= __shfl_sync(kFull, off, t)) ? t : src;
-    const int bb = __shfl_sync(kFull, beg, src), bo = __shfl_sync(kFull, off, src);
-    const int j = (e < total) ? W.bin_items[bb + e - bo] : -1;
-    bool hit = false;
-    if (j >= 0 && j != p) {
-      int s[3], lo[3], hi[3];
-      hit = pair_box(P, D, p, j, s, lo, hi);
+  for (int t0 = 0; t0 < maxn; t0 += 4) {
+    int jj[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) jj[u] = t0 + u < num ? items[t0 + u] : -1;
+    float xj[4][3];
+    int jlo[4][3], jhi[4][3];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = jj[u] >= 0 ? jj[u] : p;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        xj[u][k] = D.Xf[3 * j + k];
+        jlo[u][k] = D.lohi[6 * j + k];
+        jhi[u][k] = D.lohi[6 * j + 3 + k];
+      }
     }
-    const unsigned bu = __ballot_sync(kFull, hit && j > p);
-    const unsigned bd = __ballot_sync(kFull, hit && j < p);
-    if (hit && j > p) {
-      const int at = nup + __popc(bu & below);
-      if (at < cap) up[at] = j;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = jj[u];
+      // node ranges intersect, the partner moved by the image shift (as in pair_box)
+      bool hit = j >= 0 && j != p;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float d = xj[u][k] - xp[k];
+        const float h = 0.5f * static_cast<float>(P.L[k]);
+        const int sk = (d > h) ? 1 : ((d < -h) ? -1 : 0);
+        const int lo = max(plo[k], jlo[u][k] - sk * P.ncell[k]);
+        const int hi = min(phi[k], jhi[u][k] - sk * P.ncell[k]);
+        hit = hit && lo <= hi;
+      }
+      const unsigned bu = __ballot_sync(kFull, hit && j > p);
+      const unsigned bd = __ballot_sync(kFull, hit && j < p);
+      if (hit && j > p) {
+        const int at = nup + __popc(bu & below);
+        if (at < cap) up[at] = j;
+      }
+      if (hit && j < p) {
+        const int at = ndn + __popc(bd & below);
+        if (at < cap) dn[at] = j;
+      }
+      nup += __popc(bu);
+      ndn += __popc(bd);
     }
-    if (hit && j < p) {
-      const int at = ndn + __popc(bd & below);
-      if (at < cap) dn[at] = j;
-    }
-    nup += __popc(bu);
-    ndn += __popc(bd);
   }
   if (nup > cap || ndn > cap) {
     if (lane == 0) set_error(W.err, kErrCapacity);
@@ -280,46 +272,54 @@ __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
   if (lane == 0) {
     W.up_count[p] = nup;
     W.dn_count[p] = ndn;
+    if (nup > 0) {
+      atomicAdd(&W.grp_sum[p / kRowGroup], nup);
+      atomicAdd(&W.counters[0], nup);
+    }
   }
 }
 
-// K4a: first pair of every particle row (exclusive scan of the partner
-// counts, one CTA) and reset of the step's counters.
-__global__ void __launch_bounds__(1024) k_rows(Params P, Lists W, int32_t* __restrict__ n_pairs_out) {
-  __shared__ long long s_tmp[1024];
-  pdl_begin();
-  const int n = P.n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) W.row_off[i] = W.up_count[i];
-  __syncthreads();
-  const long long total_pairs = block_scan_excl(W.row_off, n, s_tmp);
-  if (threadIdx.x == 0) {
-    W.row_off[n] = static_cast<int>(total_pairs);
-    W.counters[0] = static_cast<int>(total_pairs);
-    W.counters[1] = 0;   // tiles allocated
-    W.counters[2] = 0;   // node-sweep queue head
-    W.counters[5] = 0;   // pairs with V > 0
-    for (int b = 0; b < kCostBuckets; ++b) W.counters[8 + b] = 0;
-    W.u64[0] = 0;        // node evaluations
-    W.u64[1] = 0;        // nominal lane-ops
-    *n_pairs_out = static_cast<int>(total_pairs);
-    if (total_pairs > P.max_pairs) set_error(W.err, kErrCapacity);
-  }
-}
 
-// K4b: one warp per particle row i, one lane per partner slot r: the pair
+// K4: one warp per particle row i, one lane per partner slot r: the pair
 // record of pair row_off[i] + r, its sweep layout and its node tiles.  Tiles
 // are allocated with one atomic per warp round; a pair's tiles are
 // contiguous, and its partial sums do not depend on where they land, so the
 // results are deterministic.  No FP64: centres come as integer node + FP32
 // remainder from the pose kernel.
 __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D, Lists W,
-                                                     int32_t* __restrict__ pair_ij) {
+                                                     int32_t* __restrict__ pair_ij, int32_t* __restrict__ n_pairs_out) {
   pdl_begin();
   const int lane = threadIdx.x & 31;
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (i >= P.n) return;
   const int cap = P.max_nbr;
-  const int cnt = W.up_count[i], row = W.row_off[i];
+  // first pair of row i: the group sums before i's group plus the counts of
+  // the earlier particles of its group (both sets of loads in flight at once)
+  const int g = i / kRowGroup;
+  int acc = 0;
+  for (int base = 0; base < g; base += 8 * 32) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + 32 * u + lane;
+      acc += e < g ? W.grp_sum[e] : 0;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kRowGroup / 32; ++u) {
+    const int e = g * kRowGroup + 32 * u + lane;
+    acc += e < i ? W.up_count[e] : 0;
+  }
+  const int row = __reduce_add_sync(kFull, acc);
+  const int cnt = W.up_count[i];
+  if (lane == 0) {
+    W.row_off[i] = row;
+    if (i == P.n - 1) {
+      const int total = W.counters[0];
+      W.row_off[P.n] = total;
+      *n_pairs_out = total;
+      if (total > P.max_pairs) set_error(W.err, kErrCapacity);
+    }
+  }
   for (int base = 0; base < cnt; base += 32) {
     const int r = base + lane;
     const bool active = r < cnt && (row + r) < P.max_pairs;
@@ -472,9 +472,6 @@ void launch_pose(const Params& P, const Shapes& S, const Parts& D, const Lists& 
   if (nb > 0) launch_pdl(k_pose, dim3(nb), dim3(96), 0, st, P, S, D, W, pos, quat);
 }
 
-void launch_bin_scatter(const Params& P, const Parts& D, const Lists& W, cudaStream_t st) {
-  launch_pdl(k_bin_scatter, dim3(1), dim3(1024), 0, st, P, D, W);
-}
 
 void launch_broad(const Params& P, const Parts& D, const Lists& W, cudaStream_t st) {
   const int warps = 8;
@@ -485,9 +482,8 @@ void launch_broad(const Params& P, const Parts& D, const Lists& W, cudaStream_t 
 
 void launch_plan(const Params& P, const Shapes& S, const Parts& D, const Lists& W, int32_t* pair_ij, int32_t* n_pairs,
                  cudaStream_t st) {
-  launch_pdl(k_rows, dim3(1), dim3(1024), 0, st, P, W, n_pairs);
   const int nb = (P.n + 3) / 4;   // four particle rows (warps) per block
-  launch_pdl(k_build_pairs, dim3(nb > 0 ? nb : 1), dim3(128), 0, st, P, S, D, W, pair_ij);
+  launch_pdl(k_build_pairs, dim3(nb > 0 ? nb : 1), dim3(128), 0, st, P, S, D, W, pair_ij, n_pairs);
 }
 
 }  // namespace gbc

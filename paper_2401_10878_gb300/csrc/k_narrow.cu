@@ -545,7 +545,8 @@ __device__ __forceinline__ void tile_done(const Params& P, const Lists& W, const
   const int lane = threadIdx.x & 31;
   if (r.ntiles == 1) {
     const int idx = __shfl_sync(kFull, __float_as_int(v), 8);
-    pair_done(P, W, r, pair_out, lane < 7 ? widen(v) : 0.0, idx);
+    // (the hardware conversion: one issue slot on the node sweep's otherwise idle FP64 pipe)
+    pair_done(P, W, r, pair_out, lane < 7 ? static_cast<double>(v) : 0.0, idx);
     return;
   }
   const size_t t0 = static_cast<size_t>(r.tile0);
@@ -575,7 +576,7 @@ __device__ __forceinline__ void tile_done(const Params& P, const Lists& W, const
       const int t = tb + slot + 4 * u;
       if (t < nt) {
         if (c < 7) {
-          const double w = widen(x[u]);
+          const double w = static_cast<double>(x[u]);
           acc = t == slot ? w : acc + w;
         } else if (x[u] > bf || (x[u] == bf && ix[u] < bi)) {
           bf = x[u];

@@ -119,13 +119,14 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
     if (C.n_cells[k] < 1) return CONTACT_EINVAL;
   const double band = (C.indicator == 1) ? (0.5 * C.smooth_width) * C.dx : 0.0;
   const double delta = C.inflate + band;
-  double rmax = 0.0;
+  double rmax = 0.0, rin_min = 1e300;
   for (int p = 0; p < n; ++p) {
     const double* prm = shape_param + 3 * p;
     if (!(young[p] > 0.0) || !(poisson[p] >= 0.0) || !(poisson[p] < 1.0)) return CONTACT_EINVAL;
     if (shape_type[p] == CONTACT_SHAPE_SPHERE) {
       if (!(prm[0] > 0.0)) return CONTACT_EINVAL;
       rmax = std::max(rmax, prm[0] + delta);
+      rin_min = std::min(rin_min, prm[0]);
     } else if (shape_type[p] == CONTACT_SHAPE_CUBOID) {
       double e2 = 0.0;
       for (int k = 0; k < 3; ++k) {
@@ -133,6 +134,7 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
         e2 += (prm[k] + delta) * (prm[k] + delta);
       }
       rmax = std::max(rmax, std::sqrt(e2));
+      rin_min = std::min(rin_min, std::min(prm[0], std::min(prm[1], prm[2])));
     } else {
       return CONTACT_EINVAL;  // polytopes need the context path
     }
@@ -149,6 +151,7 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
     P.binw[k] = P.L[k] / P.nbin[k];
     P.inv_binw_f[k] = static_cast<float>(P.nbin[k] / P.L[k]);
   }
+  P.bin_cap = bin_capacity(n, P.binw, rin_min, static_cast<long long>(P.nbin[0]) * P.nbin[1] * P.nbin[2], 1LL << 20);
   P.dx = C.dx;
   P.inv_dx = 1.0 / C.dx;
   {
@@ -207,7 +210,6 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   D.R = cv.take<double>(9 * N);
   D.lohi = cv.take<int>(6 * N);
   D.bin = cv.take<int>(N);
-  D.slot = cv.take<int>(N);
   D.Rt = cv.take<float>(9 * N);
   D.wplane = cv.take<float4>(1);
   D.Xf = cv.take<float>(3 * N);
@@ -215,14 +217,14 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   D.fX = cv.take<float>(3 * N);
   Lists W{};
   W.bin_count = cv.take<int>(nbins);
-  W.bin_start = cv.take<int>(nbins + 1);
-  W.bin_items = cv.take<int>(N);
+  W.bin_items = cv.take<int>(static_cast<size_t>(nbins) * P.bin_cap);
   W.up_count = cv.take<int>(N);
   W.up_list = cv.take<int>(N * kMaxNbr);
   W.dn_count = cv.take<int>(N);
   W.dn_list = cv.take<int>(N * kMaxNbr);
   W.dn_pair = cv.take<int>(N * kMaxNbr);
   W.row_off = cv.take<int>(N + 1);
+  W.grp_sum = cv.take<int>((N + kRowGroup - 1) / kRowGroup);
   W.pairs = cv.take<PairRec>(MP);
   W.tile_pair = cv.take<int>(MT);
   W.tiles = cv.take<PairRec>(MT * kCostBuckets);
@@ -250,7 +252,6 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
                                             vert_off, W, nbins);
   // the step's kernels, unchanged, on the scratch array
   launch_pose(P, S, D, W, pos, quat, s);
-  launch_bin_scatter(P, D, W, s);
   launch_broad(P, D, W, s);
   launch_plan(P, S, D, W, pair_ij, n_pairs, s);
   launch_narrow(P, S, D, W, pair_out, narrow_grid(P), s);
