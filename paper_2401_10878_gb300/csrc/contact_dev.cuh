@@ -93,7 +93,7 @@ struct Parts {
 };
 
 // One candidate pair (i < j).
-struct PairRec {
+struct __align__(16) PairRec {   // 16-byte aligned: records are copied with 16-byte accesses
   int i, j;
   int lo[3];       // lower node of the pair box (i's frame)
   int dim[3];      // nodes per axis

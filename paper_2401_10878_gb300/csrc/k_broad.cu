@@ -286,12 +286,20 @@ __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
 // contiguous, and its partial sums do not depend on where they land, so the
 // results are deterministic.  No FP64: centres come as integer node + FP32
 // remainder from the pose kernel.
-__global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D, Lists W,
-                                                     int32_t* __restrict__ pair_ij, int32_t* __restrict__ n_pairs_out) {
+constexpr int kBuildWarps = 8;   // particle rows per block of the pair builder
+
+__global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shapes S, Parts D, Lists W,
+                                                                  int32_t* __restrict__ pair_ij,
+                                                                  int32_t* __restrict__ n_pairs_out) {
+  // per warp: tiles, then queue slots per cost bucket (exclusive prefixes after the block scan)
+  __shared__ int s_w[kBuildWarps][1 + kCostBuckets];
+  __shared__ int s_base[1 + kCostBuckets];
+  __shared__ unsigned long long s_u64[kBuildWarps][2];
   pdl_begin();
-  const int lane = threadIdx.x & 31;
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (i >= P.n) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * kBuildWarps + wid;
+  const bool row_ok = i0 < P.n;
+  const int i = row_ok ? i0 : P.n - 1;   // rows past the end take part in the block's barriers only
   const int cap = P.max_nbr;
   // first pair of row i: the group sums before i's group plus the counts of
   // the earlier particles of its group (both sets of loads in flight at once)
@@ -309,9 +317,11 @@ __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D
     const int e = g * kRowGroup + 32 * u + lane;
     acc += e < i ? W.up_count[e] : 0;
   }
+  const int cnt = row_ok ? W.up_count[i] : 0;
+  // the first 32 partners, fetched before the count is known (stale beyond it, unused)
+  const int jpre = lane < cap ? W.up_list[static_cast<size_t>(i) * cap + lane] : 0;
   const int row = __reduce_add_sync(kFull, acc);
-  const int cnt = W.up_count[i];
-  if (lane == 0) {
+  if (lane == 0 && row_ok) {
     W.row_off[i] = row;
     if (i == P.n - 1) {
       const int total = W.counters[0];
@@ -320,7 +330,7 @@ __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D
       if (total > P.max_pairs) set_error(W.err, kErrCapacity);
     }
   }
-  for (int base = 0; base < cnt; base += 32) {
+  for (int base = 0; __syncthreads_or(base < cnt); base += 32) {   // block-uniform rounds of 32 partners
     const int r = base + lane;
     const bool active = r < cnt && (row + r) < P.max_pairs;
     PairRec pr;
@@ -328,7 +338,13 @@ __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D
     unsigned long long vol = 0, ops = 0;
     if (active) {
       pi = row + r;
-      const int j = W.up_list[i * cap + r];
+      const int j = base == 0 ? jpre : W.up_list[static_cast<size_t>(i) * cap + r];
+      // j's lower-partner list, fetched with j's particle data (slot of this pair below)
+      const int* dl = W.dn_list + static_cast<size_t>(j) * cap;
+      const int dc = W.dn_count[j];
+      int dpre[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) dpre[u] = u < cap ? dl[u] : 0;
       int lo[3], hi[3];
       pair_box(P, D, i, j, pr.shift, lo, hi);
       pr.i = i;
@@ -397,18 +413,18 @@ __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D
       ops = vol * static_cast<unsigned long long>(S.nomops[i] + S.nomops[j]);
       pair_ij[2 * pi] = i;
       pair_ij[2 * pi + 1] = j;
-      // slot of this pair in j's (sorted) list of lower partners: the number
-      // of entries below i, all loads in flight at once
-      const int* dl = W.dn_list + static_cast<size_t>(j) * cap;
-      const int dc = W.dn_count[j];
+      // slot of this pair in j's (sorted) list of lower partners: the number of entries below i
       int a0 = 0;
-      for (int b = 0; b < dc; b += 8) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) a0 += (b + u < dc && dl[b + u] < i) ? 1 : 0;
-      }
+      for (int u = 0; u < 8; ++u) a0 += (u < dc && dpre[u] < i) ? 1 : 0;
+      for (int b = 8; b < dc; ++b) a0 += dl[b] < i ? 1 : 0;
       W.dn_pair[static_cast<size_t>(j) * cap + a0] = pi;
     }
-    // warp-aggregated tile allocation and counters
+    // allocations aggregated over the block (one atomic per counter and
+    // block, all in flight together): the pairs' tiles (partials,
+    // counters[1]) and their node-sweep queue slots in a cost bucket
+    // (estimated cost of a full tile: slots x (segment + 2), scaled by the
+    // pair's nominal ops per node; all tiles of a pair in one bucket)
     int incl = ntiles;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -421,13 +437,53 @@ __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D
       wv += __shfl_xor_sync(kFull, wv, d);
       wo += __shfl_xor_sync(kFull, wo, d);
     }
-    int tbase = 0;
-    if (lane == 31 && incl > 0) tbase = atomicAdd(&W.counters[1], incl);
-    if (lane == 0 && wv > 0) {
-      atomicAdd(&W.u64[0], wv);
-      atomicAdd(&W.u64[1], wo);
+    int bucket = kCostBuckets;   // none
+    if (active && ntiles > 0) {
+      const int slots = min(kTileItemsPerLane, (pr.nitems + 31) / 32);
+      const int cost = slots * (pr.seglen + 2) * (S.nomops[pr.i] + S.nomops[pr.j]);   // ~ warp instructions
+      bucket = cost >= 2400 ? 0 : (cost >= 1200 ? 1 : (cost >= 600 ? 2 : 3));
     }
-    tbase = __shfl_sync(kFull, tbase, 31);
+    const int nq = bucket < kCostBuckets ? ntiles : 0;
+    const unsigned grp = __match_any_sync(kFull, bucket);
+    int before = 0;   // exclusive prefix of nq among the warp's lanes of this bucket
+    for (unsigned m = grp; m; m &= m - 1) {   // every lane of the group runs the same iterations
+      const int l = __ffs(m) - 1;
+      const int v = __shfl_sync(grp, nq, l);
+      if (l < lane) before += v;
+    }
+    int wtot[kCostBuckets];
+#pragma unroll
+    for (int b = 0; b < kCostBuckets; ++b) wtot[b] = __reduce_add_sync(kFull, bucket == b ? nq : 0);
+    const int wtiles = __shfl_sync(kFull, incl, 31);
+    if (lane == 0) {
+      s_w[wid][0] = wtiles;
+#pragma unroll
+      for (int b = 0; b < kCostBuckets; ++b) s_w[wid][1 + b] = wtot[b];
+      s_u64[wid][0] = wv;
+      s_u64[wid][1] = wo;
+    }
+    __syncthreads();
+    if (threadIdx.x <= kCostBuckets) {   // counter c: exclusive prefix over the warps, one atomic
+      const int c = threadIdx.x;
+      int run = 0;
+      for (int w = 0; w < kBuildWarps; ++w) {
+        const int v = s_w[w][c];
+        s_w[w][c] = run;
+        run += v;
+      }
+      int* ctr = c == 0 ? &W.counters[1] : &W.counters[8 + c - 1];
+      s_base[c] = run > 0 ? atomicAdd(ctr, run) : 0;
+    } else if (threadIdx.x == kCostBuckets + 1) {
+      unsigned long long a = 0, b = 0;
+      for (int w = 0; w < kBuildWarps; ++w) { a += s_u64[w][0]; b += s_u64[w][1]; }
+      if (a > 0) {
+        atomicAdd(&W.u64[0], a);
+        atomicAdd(&W.u64[1], b);
+      }
+    }
+    __syncthreads();
+    const int tbase = s_base[0] + s_w[wid][0];
+    const int pos = bucket < kCostBuckets ? s_base[1 + bucket] + s_w[wid][1 + bucket] + before : 0;
     if (active) {
       pr.tile0 = tbase + incl - ntiles;
       W.pairs[pi] = pr;
@@ -435,30 +491,12 @@ __global__ void __launch_bounds__(128) k_build_pairs(Params P, Shapes S, Parts D
         if (pr.tile0 + k < P.max_tiles) W.tile_pair[pr.tile0 + k] = pi;
         else set_error(W.err, kErrCapacity);
       }
-    }
-    // queue records, grouped by estimated cost: slots x (segment + 2), scaled
-    // by the pair's nominal ops per node (warp-aggregated atomics per bucket)
-    int maxt = ntiles;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) maxt = max(maxt, __shfl_xor_sync(kFull, maxt, d));
-    const int slots_total = active ? (pr.nitems + 31) / 32 : 0;
-    const int weight = active ? (S.nomops[pr.i] + S.nomops[pr.j]) : 0;
-    for (int k = 0; k < maxt; ++k) {
-      const bool has = active && k < ntiles && pr.tile0 + k < P.max_tiles;
-      int bucket = kCostBuckets;   // none
-      if (has) {
-        const int slots = min(kTileItemsPerLane, slots_total - k * kTileItemsPerLane);
-        const int cost = slots * (pr.seglen + 2) * weight;   // ~ warp instructions
-        bucket = cost >= 2400 ? 0 : (cost >= 1200 ? 1 : (cost >= 600 ? 2 : 3));
-      }
-      const unsigned grp = __match_any_sync(kFull, bucket);
-      const int leader = __ffs(grp) - 1;
-      int pos = 0;
-      if (has && lane == leader) pos = atomicAdd(&W.counters[8 + bucket], __popc(grp));
-      pos = __shfl_sync(kFull, pos, leader) + __popc(grp & ((1u << lane) - 1u));
-      if (has) {
+      // queue records (beyond the tile capacity the step fails with
+      // ECAPACITY and the node sweep does not run)
+      PairRec* dst = W.tiles + static_cast<size_t>(bucket) * P.max_tiles;
+      for (int k = 0; k < nq && pos + k < P.max_tiles; ++k) {
         pr.tile = k;
-        W.tiles[static_cast<size_t>(bucket) * P.max_tiles + pos] = pr;
+        dst[pos + k] = pr;
       }
     }
   }
@@ -482,8 +520,8 @@ void launch_broad(const Params& P, const Parts& D, const Lists& W, cudaStream_t 
 
 void launch_plan(const Params& P, const Shapes& S, const Parts& D, const Lists& W, int32_t* pair_ij, int32_t* n_pairs,
                  cudaStream_t st) {
-  const int nb = (P.n + 3) / 4;   // four particle rows (warps) per block
-  launch_pdl(k_build_pairs, dim3(nb > 0 ? nb : 1), dim3(128), 0, st, P, S, D, W, pair_ij, n_pairs);
+  const int nb = (P.n + kBuildWarps - 1) / kBuildWarps;   // one particle row per warp
+  launch_pdl(k_build_pairs, dim3(nb > 0 ? nb : 1), dim3(kBuildWarps * 32), 0, st, P, S, D, W, pair_ij, n_pairs);
 }
 
 }  // namespace gbc

@@ -671,7 +671,8 @@ __global__ void __launch_bounds__(kWarps * 32, SET == SET_CUBE ? 3 : 2) k_narrow
   __shared__ float4 s_planes[kWarps][2][kMaxFaces];
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int ntiles = min(W.counters[1], P.max_tiles);
+  const int ntiles = W.counters[1];
+  if (ntiles > P.max_tiles) return;   // capacity exceeded: the step reports ECAPACITY
   // queue position -> record: buckets of decreasing cost, one after the other
   int bend[kCostBuckets];
   {

@@ -180,6 +180,28 @@ def test_capacity_and_input_errors():
     m.close()
 
 
+def test_cell_list_bin_capacity():
+    """30 sphere centres inside one cell-list bin whose capacity is 17
+    (twice the bin volume over the inscribed-ball volume, plus 8): the step
+    reports ECAPACITY; after clear_error the context steps a spread-out state."""
+    from paper_2401_10878_gb300.contact import ContactError, ECAPACITY
+    rng = np.random.default_rng(5)
+    k = 30
+    crowded = 6.0 + rng.uniform(-1.0, 1.0, size=(k, 3))
+    st = state([0] * k, [[5.0, 0, 0]] * k, crowded, n=64)
+    m = model_for(st)
+    with pytest.raises(ContactError) as e:
+        gpu_step(m, st)
+    assert e.value.code == ECAPACITY
+    m.clear_error()
+    g = np.stack(np.meshgrid(*[np.arange(4)] * 3, indexing="ij"), -1).reshape(-1, 3)[:k]
+    spread = 8.0 + 14.0 * g + rng.uniform(-0.5, 0.5, size=(k, 3))
+    r = oracle.contact_step(st, pos=spread, quat=st.quat)
+    out = gpu_step(m, st, pos=spread)
+    compare(st.with_poses(spread, st.quat), out, r, fp64=False, smooth=False)
+    m.close()
+
+
 def test_user_stream_capture():
     st = W.mixed_grid_27()
     m = model_for(st, use_graph=False)
