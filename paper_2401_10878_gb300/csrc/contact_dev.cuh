@@ -119,8 +119,9 @@ constexpr int kPairRecWords = sizeof(PairRec) / 4;
 static_assert(sizeof(PairRec) % 16 == 0, "PairRec is staged with 16-byte copies");
 
 // Work lists shared by the step's kernels.
-// One overlapping pair for the force law: its FP64 sums (count, first
-// moments, band terms of G), its deepest node, and the pair record's geometry.
+// One overlapping pair for the force law (staged in shared memory by the warp
+// that completes it): its FP64 sums (count, first moments, band terms of G),
+// its deepest node, and the pair record's geometry.
 struct OvlRec {
   double s[7];     // sum of H, of H x (x, y, z) in box coordinates, of the band terms (x, y, z)
   int q;           // pair index
@@ -149,7 +150,6 @@ struct Lists {
                     // pair set), in the node sweep's queue order: bucket 0 (dearest) first
   float* partial;   // [max_tiles, kPartialFloats]
   int* pdone;       // [max_pairs] tiles of the pair swept so far (pairs of several tiles)
-  OvlRec* olist;    // [max_pairs] overlapping pairs, in completion order (count: counters[5])
   double* tape;     // [max_pairs, kTapeDoubles]
   double* ft;       // [max_pairs, kFtDoubles]
   const int* kind;  // [N] sweep kind of each particle (Kind, polytopes by face bucket)
@@ -314,11 +314,9 @@ void launch_plan(const Params& P, const Shapes& S, const Parts& D, const Lists& 
                  cudaStream_t st);
 constexpr int kRowGroup = 256;   // particles per group sum of the pair-row offsets
 int bin_capacity(int n, const double binw[3], double rin_min, long long nbins, long long max_entries);
-void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists& W, double* pair_out, int grid,
-                   cudaStream_t st);
+void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel,
+                   double* pair_out, int grid, cudaStream_t st);
 int narrow_grid(const Params& P);
-void launch_finalize(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel,
-                     double* pair_out, cudaStream_t st);
 void launch_particle_sum(const Params& P, const Parts& D, const Lists& W, double* force, double* torque,
                          cudaStream_t st);
 size_t adjoint_scratch_doubles(int max_pairs, int max_tiles);

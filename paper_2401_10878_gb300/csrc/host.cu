@@ -162,9 +162,8 @@ void enqueue_step(contact_ctx* c, bool capturing, const double* pos, const doubl
   launch_broad(c->P, c->D, c->W, c->stream);
   launch_plan(c->P, c->S, c->D, c->W, pair_ij, n_pairs, c->stream);
   if (c->cfg.narrow_events) cudaEventRecordWithFlags(c->ev_narrow[0], c->stream, ev_flags);
-  launch_narrow(c->P, c->S, c->D, c->W, pair_out, c->grid_narrow, c->stream);
+  launch_narrow(c->P, c->S, c->D, c->W, vel, pair_out, c->grid_narrow, c->stream);
   if (c->cfg.narrow_events) cudaEventRecordWithFlags(c->ev_narrow[1], c->stream, ev_flags);
-  launch_finalize(c->P, c->S, c->D, c->W, vel, pair_out, c->stream);
   launch_particle_sum(c->P, c->D, c->W, force, torque, c->stream);
 }
 
@@ -398,7 +397,6 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   GBC_TRY(dev_alloc(c, &W.tiles, mt * kCostBuckets));
   GBC_TRY(dev_alloc(c, &W.partial, mt * kPartialFloats));
   GBC_TRY(dev_alloc(c, &W.pdone, mp));
-  GBC_TRY(dev_alloc(c, &W.olist, mp));
   GBC_TRY(dev_alloc(c, &W.tape, mp * kTapeDoubles));
   GBC_TRY(dev_alloc(c, &W.ft, mp * kFtDoubles));
   GBC_TRY(dev_alloc(c, &W.counters, 16));
@@ -546,7 +544,7 @@ contact_status contact_narrow_time(contact_ctx* c, float* ms) {
   return e == cudaSuccess ? CONTACT_OK : cuda_fail(c, e, "cudaEventElapsedTime");
 }
 
-int32_t contact_kernels_per_step(const contact_ctx*) { return 6; }
+int32_t contact_kernels_per_step(const contact_ctx*) { return 5; }
 int32_t contact_kernels_per_backward(const contact_ctx*) { return 4; }
 
 contact_status contact_backward(contact_ctx* c, const double* grad_force, const double* grad_torque,

@@ -1,10 +1,7 @@
-// Per-pair reduction, force law and per-particle sums of the contact step.
+// Per-particle sums of the contact forces and torques (the pairs' force law
+// runs in the node sweep's epilogue, force_law.cuh).
 //
 // Paper (arXiv:2401.10878):
-//   Sec. 3.3.1  overlap volume, contact point, contact normal, indentation depth;
-//   Sec. 2.3    Eq. (contact_force_normal) F = 4/(3 pi) n E* sqrt(V d)(1 + c ddot_n),
-//               E* = ((1-nu_A^2)/E_A + (1-nu_B^2)/E_B)^-1;
-//   Sec. 2.2    torques about the centres of mass;
 //   Sec. 4.3.3  contact forces and torques are delivered to both particles.
 #include <cfloat>
 
@@ -16,198 +13,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// 1/sqrt(a) for a > 0: FP32 seed (the double's leading 24 bits, rsqrt.approx)
-// and two Newton-Raphson steps y <- y + y (1 - a y^2) / 2 in FP64 (each step
-// squares the relative error: 2^-22 -> ~1e-13 -> FP64 rounding).  Arguments
-// outside the FP32 exponent range take the library square root.
-__device__ __forceinline__ double nr_rsqrt(double a) {
-  const unsigned hi = static_cast<unsigned>(__double2hiint(a));
-  const unsigned lo = static_cast<unsigned>(__double2loint(a));
-  const int e = static_cast<int>((hi >> 20) & 0x7ffu) - 896;
-  if (e < 1 || e > 254 || (hi >> 31)) return 1.0 / sqrt(a);
-  const float af = __uint_as_float((static_cast<unsigned>(e) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
-  float yf;
-  asm("rsqrt.approx.f32 %0, %1;" : "=f"(yf) : "f"(af));
-  double y = widen(yf);
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const double h = a * y;
-    const double r = fma(-h, y, 1.0);
-    y = fma(0.5 * y, r, y);
-  }
-  return y;
-}
-
-// max of two doubles by their order-preserving integer keys (no FP64 instruction)
-__device__ __forceinline__ long long dkey(double x) {
-  const long long b = __double_as_longlong(x);
-  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
-}
-__device__ __forceinline__ double dmax(double a, double b) { return dkey(a) >= dkey(b) ? a : b; }
-
-// Exact int -> FP64 conversion with integer operations (|v| < 2^31).
-__device__ __forceinline__ double int_to_double(int v) {
-  if (v == 0) return 0.0;
-  const unsigned long long sgn = v < 0 ? (1ULL << 63) : 0ULL;
-  const unsigned a = v < 0 ? 0u - static_cast<unsigned>(v) : static_cast<unsigned>(v);
-  const int lz = __clz(a);
-  const unsigned long long frac = (static_cast<unsigned long long>(a) << (lz + 21)) & ((1ULL << 52) - 1ULL);
-  return __longlong_as_double(static_cast<long long>(sgn | (static_cast<unsigned long long>(1054 - lz) << 52) | frac));
-}
-
-// K6: FP64 force law of the overlapping pairs (the node sweep's epilogue has
-// reduced every pair to FP64 sums, written the zero outputs of the pairs
-// without overlap and listed the others).  Four lanes per pair (component
-// k = 0..2 on lanes 0..2, lane 3 for the fourth reciprocal square root),
-// eight pairs per warp, one warp per block: every FP64 warp instruction
-// occupies a sub-partition's FP64 pipe for ~64 cycles however many lanes are
-// active, so the per-pair chain is split over the components and the warps
-// are spread over the sub-partitions.
-constexpr int kFinBlock = 32;
-constexpr int kPairsPerPass = 8;
-
-__device__ __forceinline__ double shape_value(int type, double prm0, double prmk, const double* planes, int nf, int k,
-                                              const double r[3], const double y[3], double yk) {
-  if (type == 0) {   // sphere: |r| - radius (the same on the pair's lanes)
-    const double rr = fma(r[2], r[2], fma(r[1], r[1], r[0] * r[0]));
-    const double nr = __double_as_longlong(rr) > 0 ? rr * nr_rsqrt(rr) : 0.0;
-    return nr - prm0;
-  }
-  if (type == 1) return fabs(yk) - prmk;       // cuboid: this lane's face pair
-  double best = -1e300;                          // polytope: faces k, k + 3, ...
-  for (int f = k; f < nf; f += 3) {
-    const double* e = planes + 4 * f;
-    best = dmax(best, fma(e[2], y[2], fma(e[1], y[1], e[0] * y[0])) - e[3]);
-  }
-  return best;
-}
-
-__global__ void __launch_bounds__(kFinBlock) k_finalize(Params P, Shapes S, Parts D, Lists W,
-                                                        const double* __restrict__ vel,
-                                                        double* __restrict__ pair_out) {
-  pdl_begin();
-  const int lane = threadIdx.x;
-  const int m = min(W.counters[5], P.max_pairs);
-  const int slot = lane >> 2, k = lane & 3, kc = k < 3 ? k : 0, b0 = lane & ~3;
-  for (int e0 = blockIdx.x * kPairsPerPass; e0 < m; e0 += gridDim.x * kPairsPerPass) {
-    const bool act = e0 + slot < m;
-    const OvlRec& er = W.olist[act ? e0 + slot : e0];
-    const int q = er.q;
-    const int i = er.i, j = er.j;
-    const int lok = er.lo[kc], d0 = er.dim[0], d1 = er.dim[1], d2 = er.dim[2], sh = er.shift[kc];
-    // one round of global loads: both particles' state and shape data
-    const double XA = D.X[3 * i + kc];
-    const double Xj = D.X[3 * j + kc];
-    const double* RA = D.R + 9 * i;
-    const double* RB = D.R + 9 * j;
-    const double ra0 = RA[kc], ra1 = RA[3 + kc], ra2 = RA[6 + kc];
-    const double rb0 = RB[kc], rb1 = RB[3 + kc], rb2 = RB[6 + kc];
-    const int ta = S.type[i], tb = S.type[j];
-    const double pa0 = S.param[3 * i], pak = S.param[3 * i + kc];
-    const double pb0 = S.param[3 * j], pbk = S.param[3 * j + kc];
-    const int fa0 = S.face_off[i], fa1 = S.face_off[i + 1], fb0 = S.face_off[j], fb1 = S.face_off[j + 1];
-    const double cc = S.compl_[i] + S.compl_[j];
-    const double* sm = er.s;
-    const double Lsel = sh == 0 ? 0.0 : (sh > 0 ? P.L[kc] : -P.L[kc]);
-    const double XB = Xj - Lsel;   // X_j - s L, s in {-1, 0, 1}
-    const double s0 = sm[0];
-    const double V = P.dx3 * s0;
-    const double Gk = P.gscale * sm[4 + kc];
-    const double G0 = __shfl_sync(kFull, Gk, b0), G1 = __shfl_sync(kFull, Gk, b0 + 1),
-               G2 = __shfl_sync(kFull, Gk, b0 + 2);
-    const double gn2 = fma(G2, G2, fma(G1, G1, G0 * G0));
-    const bool gok = __double_as_longlong(gn2) > __double_as_longlong(P.g_min2);
-    // indentation depth: FP64 re-evaluation at the deepest node
-    const int idx = min(max(er.idx, 0), d0 * d1 * d2 - 1);
-    const int ck = kc == 0 ? idx % d0 : (kc == 1 ? (idx / d0) % d1 : idx / (d0 * d1));
-    const double xk = int_to_double(lok + ck) * P.dx;
-    const double rAk = xk - XA, rBk = xk - XB;
-    double rA[3], rB[3], yA[3], yB[3];
-    for (int c = 0; c < 3; ++c) {
-    rA[c] = __shfl_sync(kFull, rAk, b0 + c);
-    rB[c] = __shfl_sync(kFull, rBk, b0 + c);
-    }
-    const double yAk = fma(ra2, rA[2], fma(ra1, rA[1], ra0 * rA[0]));
-    const double yBk = fma(rb2, rB[2], fma(rb1, rB[1], rb0 * rB[0]));
-    for (int c = 0; c < 3; ++c) {
-    yA[c] = __shfl_sync(kFull, yAk, b0 + c);
-    yB[c] = __shfl_sync(kFull, yBk, b0 + c);
-    }
-    double vA = k < 3 ? shape_value(ta, pa0, pak, S.planes + 4 * fa0, fa1 - fa0, kc, rA, yA, yAk) : -1e300;
-    double vB = k < 3 ? shape_value(tb, pb0, pbk, S.planes + 4 * fb0, fb1 - fb0, kc, rB, yB, yBk) : -1e300;
-    vA = dmax(vA, __shfl_xor_sync(kFull, vA, 1));
-    vA = dmax(vA, __shfl_xor_sync(kFull, vA, 2));
-    vB = dmax(vB, __shfl_xor_sync(kFull, vB, 1));
-    vB = dmax(vB, __shfl_xor_sync(kFull, vB, 2));
-    const double fa = vA - P.inflate, fb = vB - P.inflate;
-    const double d = dmax(0.0, -(fa + fb));
-    const double vd = V * d;
-    const bool vok = __double_as_longlong(vd) > 0;
-    // four reciprocal square roots, one per lane: s0, E*'s compliance sum, |G|^2, V d
-    const double arg = k == 0 ? s0 : (k == 1 ? cc : (k == 2 ? (gok ? gn2 : 1.0) : (vok ? vd : 1.0)));
-    const double y = nr_rsqrt(arg);
-    const double y0 = __shfl_sync(kFull, y, b0), y1 = __shfl_sync(kFull, y, b0 + 1),
-               y2 = __shfl_sync(kFull, y, b0 + 2), y3 = __shfl_sync(kFull, y, b0 + 3);
-    const double inv_s0 = y0 * y0;
-    const double estar = y1 * y1;
-    const double xck = fma(sm[1 + kc], inv_s0, int_to_double(lok)) * P.dx;
-    double nk = Gk * y2;
-    double fallback = 0.0;
-    if (__any_sync(kFull, act && !gok)) {   // centre-line fallback normal
-    const double dXk = XB - XA;
-    const double e0v = __shfl_sync(kFull, dXk, b0), e1v = __shfl_sync(kFull, dXk, b0 + 1),
-                 e2v = __shfl_sync(kFull, dXk, b0 + 2);
-    if (!gok) {
-      fallback = 1.0;
-      const double nd2 = fma(e2v, e2v, fma(e1v, e1v, e0v * e0v));
-      nk = __double_as_longlong(nd2) > 0 ? dXk * nr_rsqrt(nd2) : 0.0;
-    }
-    }
-    const double gn = gok ? gn2 * y2 : 0.0;
-    const double rak = xck - XA, rbk = xck - XB;
-    // components k1 = k+1, k2 = k+2 (mod 3) of the lever arms, for the cross products
-    const int k1 = kc == 2 ? 0 : kc + 1, k2 = kc == 0 ? 2 : kc - 1;
-    const double ra1v = __shfl_sync(kFull, rak, b0 + k1), ra2v = __shfl_sync(kFull, rak, b0 + k2);
-    const double rb1v = __shfl_sync(kFull, rbk, b0 + k1), rb2v = __shfl_sync(kFull, rbk, b0 + k2);
-    double damp = 1.0;
-    if (vel != nullptr && P.damping_c != 0.0) {
-    const double* va = vel + 6 * i;
-    const double* vb = vel + 6 * j;
-    // relative normal speed (v_A + w_A x r_A - v_B - w_B x r_B) . n
-    const double wak = fma(va[3 + k1], ra2v, -va[3 + k2] * ra1v);
-    const double wbk = fma(vb[3 + k1], rb2v, -vb[3 + k2] * rb1v);
-    const double uk = ((va[kc] + wak) - (vb[kc] + wbk)) * nk;
-    const double u0 = __shfl_sync(kFull, uk, b0), u1 = __shfl_sync(kFull, uk, b0 + 1),
-                 u2 = __shfl_sync(kFull, uk, b0 + 2);
-    damp = dmax(0.0, fma(P.damping_c, (u0 + u1) + u2, 1.0));
-    }
-    const double fmag = vok ? (4.0 / (3.0 * 3.14159265358979323846)) * estar * (vd * y3) * damp : 0.0;
-    const double Fk = fmag * nk;
-    const double F1 = __shfl_sync(kFull, Fk, b0 + k1), F2 = __shfl_sync(kFull, Fk, b0 + k2);
-    // T_A = r_A x (-F), T_B = r_B x F
-    const double TAk = fma(ra2v, F1, -ra1v * F2);
-    const double TBk = fma(rb1v, F2, -rb2v * F1);
-    if (act) {
-    double* o = pair_out + static_cast<size_t>(q) * 11;
-    double* f = W.ft + static_cast<size_t>(q) * kFtDoubles;
-    double* tp = W.tape + static_cast<size_t>(q) * kTapeDoubles;
-    if (k < 3) {
-      o[1 + k] = xck; o[4 + k] = nk; o[8 + k] = Fk;
-      f[k] = Fk; f[3 + k] = TAk; f[6 + k] = TBk;
-      tp[1 + k] = xck; tp[4 + k] = nk;
-    }
-    if (k == 0) {
-      o[0] = V; o[7] = d;
-      tp[0] = s0; tp[7] = d; tp[8] = gn; tp[9] = fallback;
-    } else if (k == 3) {
-      tp[10] = estar; tp[11] = damp; tp[12] = fmag; tp[13] = int_to_double(idx);
-      tp[14] = 0.0; tp[15] = 0.0;
-    }
-    }
-  }
-}
-
-// K7: per particle and component (eight lanes per particle, six used), FP64
+// K6: per particle and component (eight lanes per particle, six used), FP64
 // adds in a fixed order: the pairs where the particle is j (by i), then the
 // pairs where it is i (by j).  j receives +F and T_B, i receives -F and T_A.
 // The first eight lower-partner pair indices are fetched together with the
@@ -252,16 +58,6 @@ __global__ void __launch_bounds__(128) k_particle_sum(Params P, Parts D, Lists W
 }
 
 }  // namespace
-
-void launch_finalize(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel,
-                     double* pair_out, cudaStream_t st) {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int need = (P.max_pairs + kPairsPerPass - 1) / kPairsPerPass;
-  const int grid = need < 8 * sms ? (need > 0 ? need : 1) : 8 * sms;
-  launch_pdl(k_finalize, dim3(grid), dim3(kFinBlock), 0, st, P, S, D, W, vel, pair_out);
-}
 
 void launch_particle_sum(const Params& P, const Parts& D, const Lists& W, double* force, double* torque,
                          cudaStream_t st) {

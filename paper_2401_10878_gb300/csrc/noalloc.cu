@@ -230,7 +230,6 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   W.tiles = cv.take<PairRec>(MT * kCostBuckets);
   W.partial = cv.take<float>(MT * kPartialFloats);
   W.pdone = cv.take<int>(MP);
-  W.olist = cv.take<OvlRec>(MP);
   W.tape = cv.take<double>(MP * kTapeDoubles);
   W.ft = cv.take<double>(MP * kFtDoubles);
   W.kind = kind;
@@ -254,8 +253,7 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   launch_pose(P, S, D, W, pos, quat, s);
   launch_broad(P, D, W, s);
   launch_plan(P, S, D, W, pair_ij, n_pairs, s);
-  launch_narrow(P, S, D, W, pair_out, narrow_grid(P), s);
-  launch_finalize(P, S, D, W, nullptr, pair_out, s);
+  launch_narrow(P, S, D, W, nullptr, pair_out, narrow_grid(P), s);
   launch_particle_sum(P, D, W, force, torque, s);
   if (cudaGetLastError() != cudaSuccess) return CONTACT_ECUDA;
   // synchronous: the device error word is read back before returning
