@@ -303,8 +303,8 @@ def run_ours(args, ws, rank, local):
             "ms_per_step_p10_p90": [float(np.percentile(res["per"], 10)), float(np.percentile(res["per"], 90))]}
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(st, pos, quat, args.cpu_seconds)
-        if not args.no_extras:
-            line["extras"] = extras(args, dev, flush)
+    if rank == 0 and not args.no_extras:
+        line["extras"] = extras(args, dev, flush)
     model.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -1,20 +1,19 @@
 // FP64 force law of one overlapping pair (Sec. 2.3 Eq. (contact_force_normal),
 // Sec. 2.2 torques, Sec. 3.3.1 contact point, normal and indentation depth),
-// run by the warp that completed the pair's node sweep.
+// run by a node-sweep warp for up to eight overlapping pairs it has completed.
 //
 // Every FP64 warp instruction occupies a sub-partition's FP64 pipe for ~64
-// cycles however many lanes are active, so the pair's chain is split over
-// four lanes: component k = 0..2 on lanes 0..2, lane 3 for the fourth
-// reciprocal square root.  The other lanes run the same instructions on the
-// same pair and store nothing.
+// cycles however many lanes are active, so each pair's chain is split over
+// four lanes (component k = 0..2 on lanes 0..2, lane 3 for the fourth
+// reciprocal square root) and eight pairs share one pass.  Lanes of unused
+// slots run the same instructions on pair 0 and store nothing.
 #pragma once
 
 #include "contact_dev.cuh"
 
 namespace gbc {
 
-// Everything the force law reads or writes, as plain pointers and scalars
-// (passed by value to the out-of-line function).
+// Everything the force law reads or writes, as plain pointers and scalars.
 struct ForceArgs {
   const double* X;
   const double* R;
@@ -82,24 +81,36 @@ __device__ __forceinline__ double shape_value(int type, double prm0, double prmk
     return nr - prm0;
   }
   if (type == 1) return fabs(yk) - prmk;       // cuboid: this lane's face pair
-  double best = -1e300;                          // polytope: faces k, k + 3, ...
-  for (int f = k; f < nf; f += 3) {
-    const double* e = planes + 4 * f;
-    best = dmax(best, fma(e[2], y[2], fma(e[1], y[1], e[0] * y[0])) - e[3]);
+  double best = -1e300;                          // polytope: faces k, k + 3, ... (loads 4 faces at a time)
+  const double2* pl = reinterpret_cast<const double2*>(planes);
+  for (int f0 = k; f0 < nf; f0 += 12) {
+    double2 e01[4], e23[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int f = min(f0 + 3 * u, nf - 1);
+      e01[u] = pl[2 * f];
+      e23[u] = pl[2 * f + 1];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (f0 + 3 * u < nf)
+        best = dmax(best, fma(e23[u].x, y[2], fma(e01[u].y, y[1], e01[u].x * y[0])) - e23[u].y);
   }
   return best;
 }
 
 }  // namespace fl
 
-// The whole warp calls this for the pair described by e (shared memory).
-__device__ __noinline__ void pair_force_law(ForceArgs a, const OvlRec* e) {
+constexpr int kForcePairsPerPass = 8;   // pairs one call handles (four lanes each)
+
+// The whole warp calls this for the n <= 8 pairs e[0..n) (shared memory).
+__device__ __forceinline__ void pair_force_law(ForceArgs a, const OvlRec* e, int n) {
   using namespace fl;
   const int lane = threadIdx.x & 31;
-  const int k = lane & 3, kc = k < 3 ? k : 0, b0 = lane & ~3;
+  const int slot = lane >> 2, k = lane & 3, kc = k < 3 ? k : 0, b0 = lane & ~3;
   {
-    const bool act = lane < 4;
-    const OvlRec& er = *e;
+    const bool act = slot < n;
+    const OvlRec& er = e[act ? slot : 0];
     const int q = er.q;
     const int i = er.i, j = er.j;
     const int lok = er.lo[kc], d0 = er.dim[0], d1 = er.dim[1], d2 = er.dim[2], sh = er.shift[kc];

@@ -506,8 +506,9 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
 
 void launch_pose(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* pos,
                  const double* quat, cudaStream_t st) {
-  const int nb = (3 * P.n + 95) / 96;   // 32 particles x 3 axes per block
-  if (nb > 0) launch_pdl(k_pose, dim3(nb), dim3(96), 0, st, P, S, D, W, pos, quat);
+  // one-warp blocks: the FP64 chains of different warps land on different sub-partitions
+  const int nb = (3 * P.n + 31) / 32;
+  if (nb > 0) launch_pdl(k_pose, dim3(nb), dim3(32), 0, st, P, S, D, W, pos, quat);
 }
 
 

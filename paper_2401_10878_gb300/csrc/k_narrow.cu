@@ -511,32 +511,42 @@ __device__ __forceinline__ float reduce_tile(const Partial& o) {
   return v;   // lane c < 9: component c of the tile partial
 }
 
+// The force law of the warp's staged overlapping pairs (whole warp).
+__device__ __forceinline__ void flush_overlaps(const Params& P, const Shapes& S, const Parts& D, const Lists& W,
+                                               const double* vel, double* pair_out, OvlRec* ov, int& nov) {
+  if (nov == 0) return;
+  __syncwarp();
+  ForceArgs a;
+  a.X = D.X; a.R = D.R;
+  a.type = S.type; a.param = S.param; a.face_off = S.face_off; a.planes = S.planes; a.compl_ = S.compl_;
+  a.vel = vel; a.pair_out = pair_out; a.ft = W.ft; a.tape = W.tape;
+  for (int k = 0; k < 3; ++k) a.L[k] = P.L[k];
+  a.dx = P.dx; a.dx3 = P.dx3; a.gscale = P.gscale; a.g_min2 = P.g_min2; a.inflate = P.inflate;
+  a.damping_c = P.damping_c;
+  pair_force_law(a, ov, nov);
+  __syncwarp();
+  nov = 0;
+}
+
 // End of a pair (called by the whole warp once all its nodes are summed):
 // lanes c < 7 hold the FP64 sum of component c, every lane the deepest node.
-// A pair without overlap gets its zero outputs; for an overlapping pair the
-// warp stages the pair in shared memory and runs the force law.
+// A pair without overlap gets its zero outputs; an overlapping pair is staged
+// in the warp's shared-memory slots (ov, nov of kForcePairsPerPass) and its
+// force law runs when the slots are full or the warp has no more tiles.
 __device__ __forceinline__ void pair_done(const Params& P, const Shapes& S, const Parts& D, const Lists& W,
                                           const PairRec& r, const double* vel, double* pair_out, OvlRec* ov,
-                                          double sv, int idx) {
+                                          int& nov, double sv, int idx) {
   const int lane = threadIdx.x & 31;
   const int q = r.pair;
   const double s0 = __shfl_sync(kFull, sv, 0);
   if (__double_as_longlong(s0) > 0) {   // V > 0
-    if (lane < 7) ov->s[lane] = sv;
-    if (lane == 7) ov->q = q;
-    if (lane == 8) ov->idx = idx;
-    if (lane >= 9 && lane < 20) (&ov->i)[lane - 9] = reinterpret_cast<const int*>(&r)[lane - 9];   // i, j, lo, dim, shift
+    OvlRec* e = ov + nov;
+    if (lane < 7) e->s[lane] = sv;
+    if (lane == 7) e->q = q;
+    if (lane == 8) e->idx = idx;
+    if (lane >= 9 && lane < 20) (&e->i)[lane - 9] = reinterpret_cast<const int*>(&r)[lane - 9];   // i, j, lo, dim, shift
     if (lane == 0) atomicAdd(&W.counters[5], 1);   // overlapping pairs (statistics)
-    __syncwarp();
-    ForceArgs a;
-    a.X = D.X; a.R = D.R;
-    a.type = S.type; a.param = S.param; a.face_off = S.face_off; a.planes = S.planes; a.compl_ = S.compl_;
-    a.vel = vel; a.pair_out = pair_out; a.ft = W.ft; a.tape = W.tape;
-    for (int k = 0; k < 3; ++k) a.L[k] = P.L[k];
-    a.dx = P.dx; a.dx3 = P.dx3; a.gscale = P.gscale; a.g_min2 = P.g_min2; a.inflate = P.inflate;
-    a.damping_c = P.damping_c;
-    pair_force_law(a, ov);
-    __syncwarp();
+    if (++nov == kForcePairsPerPass) flush_overlaps(P, S, D, W, vel, pair_out, ov, nov);
   } else {
     if (lane < 11) pair_out[static_cast<size_t>(q) * 11 + lane] = 0.0;
     if (lane < kFtDoubles) W.ft[static_cast<size_t>(q) * kFtDoubles + lane] = 0.0;
@@ -550,12 +560,13 @@ __device__ __forceinline__ void pair_done(const Params& P, const Shapes& S, cons
 // 8 components per lane pattern, slots combined pairwise), whichever warp
 // that is.
 __device__ __forceinline__ void tile_done(const Params& P, const Shapes& S, const Parts& D, const Lists& W,
-                                          const PairRec& r, const double* vel, double* pair_out, OvlRec* ov, float v) {
+                                          const PairRec& r, const double* vel, double* pair_out, OvlRec* ov, int& nov,
+                                          float v) {
   const int lane = threadIdx.x & 31;
   if (r.ntiles == 1) {
     const int idx = __shfl_sync(kFull, __float_as_int(v), 8);
     // (the hardware conversion: one issue slot on the node sweep's otherwise idle FP64 pipe)
-    pair_done(P, S, D, W, r, vel, pair_out, ov, lane < 7 ? static_cast<double>(v) : 0.0, idx);
+    pair_done(P, S, D, W, r, vel, pair_out, ov, nov, lane < 7 ? static_cast<double>(v) : 0.0, idx);
     return;
   }
   const size_t t0 = static_cast<size_t>(r.tile0);
@@ -601,7 +612,7 @@ __device__ __forceinline__ void tile_done(const Params& P, const Shapes& S, cons
     const int oi = __shfl_xor_sync(kFull, bi, o);
     if (ob > bf || (ob == bf && oi < bi)) { bf = ob; bi = oi; }
   }
-  pair_done(P, S, D, W, r, vel, pair_out, ov, acc, __shfl_sync(kFull, bi, 7));
+  pair_done(P, S, D, W, r, vel, pair_out, ov, nov, acc, __shfl_sync(kFull, bi, 7));
 }
 
 // Kernel variants: the full set of pair kinds, or spheres and cuboids only
@@ -674,11 +685,11 @@ __device__ __forceinline__ void store_rec_part(PairRec* dst, int lane, int4 v) {
 }
 
 template <bool SMOOTH, int SET>
-__global__ void __launch_bounds__(kWarps * 32, SET == SET_CUBE ? 3 : 2) k_narrow32(Params P, Shapes S, Parts D,
+__global__ void __launch_bounds__(kWarps * 32, 2) k_narrow32(Params P, Shapes S, Parts D,
                                                                                   Lists W, const double* vel,
                                                                                   double* pair_out) {
   __shared__ __align__(16) PairRec s_rec[kWarps][2];
-  __shared__ OvlRec s_ovl[kWarps];
+  __shared__ OvlRec s_ovl[kWarps][kForcePairsPerPass];
   __shared__ float4 s_planes[kWarps][2][kMaxFaces];
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -708,6 +719,7 @@ __global__ void __launch_bounds__(kWarps * 32, SET == SET_CUBE ? 3 : 2) k_narrow
   if (t < ntiles) store_rec_part(&s_rec[wid][0], lane, load_rec_part(rec_at(t), lane));
   __syncwarp();
   int buf = 0;
+  int nov = 0;   // overlapping pairs staged in s_ovl[wid]
   while (t < ntiles) {
     int tn = 0;
     if (lane == 0) tn = atomicAdd(&W.counters[2], 1) + nwarps;  // next tile, fetched ahead
@@ -722,13 +734,14 @@ __global__ void __launch_bounds__(kWarps * 32, SET == SET_CUBE ? 3 : 2) k_narrow
     const PairRec& r = s_rec[wid][buf];
     const Partial o = dispatch<SMOOTH, SET>(P, S, D, r, r.tile, s_planes[wid][0], s_planes[wid][1], prefetch);
     prefetch();
-    tile_done(P, S, D, W, r, vel, pair_out, &s_ovl[wid], reduce_tile<SMOOTH>(o));
+    tile_done(P, S, D, W, r, vel, pair_out, s_ovl[wid], nov, reduce_tile<SMOOTH>(o));
     __syncwarp();
     if (tn < ntiles) store_rec_part(&s_rec[wid][buf ^ 1], lane, next);
     __syncwarp();
     buf ^= 1;
     t = tn;
   }
+  flush_overlaps(P, S, D, W, vel, pair_out, s_ovl[wid], nov);
 }
 
 // ---------------------------------------------------------------- FP64 form
@@ -806,7 +819,9 @@ __global__ void __launch_bounds__(256) k_narrow64(Params P, Shapes S, Parts D, L
         if (lane < 7) tot += s_red[w][lane];
         if (s_bf[w] > b || (s_bf[w] == b && s_bi[w] < bidx)) { b = s_bf[w]; bidx = s_bi[w]; }
       }
-      pair_done(P, S, D, W, W.pairs[p], vel, pair_out, &s_ovl, tot, bidx);
+      int nov = 0;
+      pair_done(P, S, D, W, W.pairs[p], vel, pair_out, &s_ovl, nov, tot, bidx);
+      flush_overlaps(P, S, D, W, vel, pair_out, &s_ovl, nov);
     }
     __syncthreads();
   }

@@ -18,7 +18,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // pairs where it is i (by j).  j receives +F and T_B, i receives -F and T_A.
 // The first eight lower-partner pair indices are fetched together with the
 // counts.
-__global__ void __launch_bounds__(128) k_particle_sum(Params P, Parts D, Lists W, double* __restrict__ force,
+__global__ void __launch_bounds__(32) k_particle_sum(Params P, Parts D, Lists W, double* __restrict__ force,
                                                       double* __restrict__ torque) {
   pdl_begin();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -61,8 +61,8 @@ __global__ void __launch_bounds__(128) k_particle_sum(Params P, Parts D, Lists W
 
 void launch_particle_sum(const Params& P, const Parts& D, const Lists& W, double* force, double* torque,
                          cudaStream_t st) {
-  const int nb = (8 * P.n + 127) / 128;
-  launch_pdl(k_particle_sum, dim3(nb > 0 ? nb : 1), dim3(128), 0, st, P, D, W, force, torque);
+  const int nb = (8 * P.n + 31) / 32;   // one-warp blocks (four particles each)
+  launch_pdl(k_particle_sum, dim3(nb > 0 ? nb : 1), dim3(32), 0, st, P, D, W, force, torque);
 }
 
 }  // namespace gbc
