@@ -127,7 +127,8 @@ __device__ __forceinline__ void pair_force_law(ForceArgs a, const OvlRec* e, int
     const int fa0 = a.face_off[i], fa1 = a.face_off[i + 1], fb0 = a.face_off[j], fb1 = a.face_off[j + 1];
     const double cc = a.compl_[i] + a.compl_[j];
     const double* sm = er.s;
-    const double Lsel = sh == 0 ? 0.0 : (sh > 0 ? a.L[kc] : -a.L[kc]);
+    const double Lk = kc == 0 ? a.L[0] : (kc == 1 ? a.L[1] : a.L[2]);
+    const double Lsel = sh == 0 ? 0.0 : (sh > 0 ? Lk : -Lk);
     const double XB = Xj - Lsel;   // X_j - s L, s in {-1, 0, 1}
     const double s0 = sm[0];
     const double V = a.dx3 * s0;
@@ -142,12 +143,14 @@ __device__ __forceinline__ void pair_force_law(ForceArgs a, const OvlRec* e, int
     const double xk = int_to_double(lok + ck) * a.dx;
     const double rAk = xk - XA, rBk = xk - XB;
     double rA[3], rB[3], yA[3], yB[3];
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
       rA[c] = __shfl_sync(kFull, rAk, b0 + c);
       rB[c] = __shfl_sync(kFull, rBk, b0 + c);
     }
     const double yAk = fma(ra2, rA[2], fma(ra1, rA[1], ra0 * rA[0]));
     const double yBk = fma(rb2, rB[2], fma(rb1, rB[1], rb0 * rB[0]));
+#pragma unroll
     for (int c = 0; c < 3; ++c) {
       yA[c] = __shfl_sync(kFull, yAk, b0 + c);
       yB[c] = __shfl_sync(kFull, yBk, b0 + c);
