@@ -22,6 +22,7 @@
 #include <cfloat>
 
 #include "contact_dev.cuh"
+#include "force_law.cuh"
 
 namespace gbc {
 
@@ -46,7 +47,7 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
 }
 
 // ---------------------------------------------------------------- pair level
-__global__ void __launch_bounds__(128) k_adj_pre(Params P, Shapes S, Parts D, Lists W, AdjBufs B,
+__global__ void __launch_bounds__(32) k_adj_pre(Params P, Shapes S, Parts D, Lists W, AdjBufs B,
                                                  const double* __restrict__ vel, const double* __restrict__ gF,
                                                  const double* __restrict__ gT) {
   pdl_begin();
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(128) k_adj_pre(Params P, Shapes S, Parts D, Li
       gFi[k] = gF[3 * i + k]; gFj[k] = gF[3 * j + k];
       gTi[k] = gT[3 * i + k]; gTj[k] = gT[3 * j + k];
     }
-    const double V = dx * dx * dx * S0, d = tp[7], gnorm = tp[8], estar = tp[10], damp = tp[11];
+    const double d = tp[7], gnorm = tp[8], estar = tp[10], damp = tp[11];
     // dL/dF = Lambda, dL/dx_c, explicit dL/dX_A, dL/dX_B'
     double c1[3], c2[3], Lam[3], gxc[3], gXA[3], gXB[3], t1[3], t2[3];
     cross3(gTi, rA, c1);
@@ -90,9 +91,13 @@ __global__ void __launch_bounds__(128) k_adj_pre(Params P, Shapes S, Parts D, Li
     const double Ln = Lam[0] * n[0] + Lam[1] * n[1] + Lam[2] * n[2];
     double gn[3] = {fmag * Lam[0], fmag * Lam[1], fmag * Lam[2]};
     double gV = 0.0, gd = 0.0;
+    // reciprocals by Newton-Raphson from an FP32 seed (no FP64 division sequence)
+    const double inv_S0 = fl::nr_rsqrt(S0) * fl::nr_rsqrt(S0);
     if (fmag > 0.0) {
-      gV = Ln * fmag / (2.0 * V);
-      gd = Ln * fmag / (2.0 * d);
+      const double half_lf = 0.5 * Ln * fmag;
+      gV = half_lf * inv_S0 * (P.inv_dx * P.inv_dx * P.inv_dx);
+      const double yd = fl::nr_rsqrt(d);
+      gd = half_lf * (yd * yd);
       if (vel != nullptr && P.damping_c != 0.0 && damp > 0.0) {
         const double* va = vel + 6 * i;
         const double* vb = vel + 6 * j;
@@ -100,7 +105,7 @@ __global__ void __launch_bounds__(128) k_adj_pre(Params P, Shapes S, Parts D, Li
         cross3(va + 3, rA, wa);
         cross3(vb + 3, rB, wb);
         for (int k = 0; k < 3; ++k) { uA[k] = va[k] + wa[k]; uB[k] = vb[k] + wb[k]; }
-        const double gdd = Ln * (fmag / damp) * P.damping_c;
+        const double gdd = Ln * fmag * P.damping_c / damp;
         double na[3], nb[3];
         cross3(n, va + 3, na);
         cross3(n, vb + 3, nb);
@@ -113,11 +118,13 @@ __global__ void __launch_bounds__(128) k_adj_pre(Params P, Shapes S, Parts D, Li
       }
     }
     // normal: n = G / |G| with G = kappa Sg, or the centre-line fallback
-    const double kappa = 0.5 * dx * dx * 6.0 / (P.wdx / dx);
+    const double kappa = P.gscale;
     const double gnn = gn[0] * n[0] + gn[1] * n[1] + gn[2] * n[2];
     double sg[3] = {0.0, 0.0, 0.0};
     if (tp[9] == 0.0) {
-      for (int k = 0; k < 3; ++k) sg[k] = kappa * (gn[k] - gnn * n[k]) / gnorm;
+      const double yg = fl::nr_rsqrt(gnorm);
+      const double kinv = kappa * (yg * yg);
+      for (int k = 0; k < 3; ++k) sg[k] = kinv * (gn[k] - gnn * n[k]);
     } else {
       double dl = 0.0;
       for (int k = 0; k < 3; ++k) dl += (XB[k] - XA[k]) * (XB[k] - XA[k]);
@@ -133,8 +140,8 @@ __global__ void __launch_bounds__(128) k_adj_pre(Params P, Shapes S, Parts D, Li
     double s0 = gV * dx * dx * dx;
     double s1[3];
     for (int k = 0; k < 3; ++k) {
-      s1[k] = gxc[k] * dx / S0;
-      s0 -= gxc[k] * (xc[k] - pr.lo[k] * dx) / S0;
+      s1[k] = gxc[k] * dx * inv_S0;
+      s0 -= gxc[k] * (xc[k] - pr.lo[k] * dx) * inv_S0;
     }
     sd[0] = static_cast<float>(s0);
     for (int k = 0; k < 3; ++k) {
@@ -192,10 +199,12 @@ __device__ __forceinline__ float adj_eval(const AdjGeom& g, const float r[3], fl
       y[k] = fmaf(g.rt[3 * k], r[0], fmaf(g.rt[3 * k + 1], r[1], g.rt[3 * k + 2] * r[2]));
       a[k] = fabsf(y[k]) - g.size[k];
     }
-    int kk = (a[0] >= a[1] && a[0] >= a[2]) ? 0 : (a[1] >= a[2] ? 1 : 2);
-    const float sgn = y[kk] < 0.f ? -1.f : 1.f;
-    for (int k = 0; k < 3; ++k) gr[k] = sgn * g.rt[3 * kk + k];
-    return a[kk];
+    const int kk = (a[0] >= a[1] && a[0] >= a[2]) ? 0 : (a[1] >= a[2] ? 1 : 2);
+    const float yk = kk == 0 ? y[0] : (kk == 1 ? y[1] : y[2]);
+    const float sgn = yk < 0.f ? -1.f : 1.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gr[k] = sgn * (kk == 0 ? g.rt[k] : (kk == 1 ? g.rt[3 + k] : g.rt[6 + k]));
+    return kk == 0 ? a[0] : (kk == 1 ? a[1] : a[2]);
   }
   int kk = 0;
   float best = -FLT_MAX;
@@ -221,14 +230,40 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int ntiles = min(W.counters[1], P.max_tiles);
   const float inv_w = P.inv_w;
-  int t = 0;
-  if (lane == 0) t = atomicAdd(&W.counters[6], 1);
-  t = __shfl_sync(kFull, t, 0);
-  while (t < ntiles) {
-    int tn = 0;
-    if (lane == 0) tn = atomicAdd(&W.counters[6], 1);
-    const int p = W.tile_pair[t];
-    const PairRec pr = W.pairs[p];
+  // queue position -> tile record of the forward pass: cost buckets, dearest first
+  int bend[kCostBuckets];
+  {
+    int acc0 = 0;
+#pragma unroll
+    for (int b = 0; b < kCostBuckets; ++b) {
+      acc0 += W.counters[8 + b];
+      bend[b] = acc0;
+    }
+  }
+  int qpos = 0;
+  if (lane == 0) qpos = atomicAdd(&W.counters[6], 1);
+  qpos = __shfl_sync(kFull, qpos, 0);
+  while (qpos < ntiles) {
+    int qn = 0;
+    if (lane == 0) qn = atomicAdd(&W.counters[6], 1);
+    int b = 0, start = 0;
+#pragma unroll
+    for (int k = 0; k < kCostBuckets - 1; ++k)
+      if (qpos >= bend[k]) { b = k + 1; start = bend[k]; }
+    // the pair record's fields in registers (no runtime-indexed local copy)
+    const PairRec& prg = W.tiles[static_cast<size_t>(b) * P.max_tiles + (qpos - start)];
+    const int p = prg.pair;
+    const int t = prg.tile0 + prg.tile;   // the tile's index (its partial slot)
+    const int rec_i = prg.i, rec_j = prg.j, axis = prg.axis, nseg = prg.nseg, seglen = prg.seglen;
+    const int nitems = prg.nitems, tile0 = prg.tile0;
+    const int dm0 = prg.dim[0], dm1 = prg.dim[1], dm2 = prg.dim[2];
+    int ai[3], bi[3];
+    float af[3], bf[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      ai[k] = prg.ai[k]; bi[k] = prg.bi[k];
+      af[k] = prg.af[k]; bf[k] = prg.bf[k];
+    }
     const float* sd = B.seeds + static_cast<size_t>(p) * kSeedFloats;
     const float s0 = sd[0], s1[3] = {sd[1], sd[2], sd[3]}, sg[3] = {sd[4], sd[5], sd[6]};
     float acc[12];
@@ -237,25 +272,28 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
                         (sg[1] != 0.f) || (sg[2] != 0.f);
     if (active) {
       AdjGeom A, Bg;
-      adj_load(S, D, pr.i, pr.ai, pr.af, s_pl[wid][0], A);
-      adj_load(S, D, pr.j, pr.bi, pr.bf, s_pl[wid][1], Bg);
-      const int ax0 = pr.axis, ax1 = (pr.axis + 1) % 3, ax2 = (pr.axis + 2) % 3;
-      const int du = pr.dim[ax0], dv = pr.dim[ax1];
-      const int it0 = (t - pr.tile0) * 32 * kTileItemsPerLane;
+      adj_load(S, D, rec_i, ai, af, s_pl[wid][0], A);
+      adj_load(S, D, rec_j, bi, bf, s_pl[wid][1], Bg);
+      const int ax0 = axis;
+      const int du = ax0 == 0 ? dm0 : (ax0 == 1 ? dm1 : dm2);
+      const int dv = ax0 == 0 ? dm1 : (ax0 == 1 ? dm2 : dm0);   // side along (ax0 + 1) mod 3
+      const int it0 = (t - tile0) * 32 * kTileItemsPerLane;
       for (int s = 0; s < kTileItemsPerLane; ++s) {
         const int it = it0 + s * 32 + lane;
-        if (it >= pr.nitems) continue;
-        const int line = it / pr.nseg, seg = it - line * pr.nseg;
-        int c[3];
-        c[ax1] = line % dv;
-        c[ax2] = line / dv;
-        const int u0 = seg * pr.seglen, u1 = min(u0 + pr.seglen, du);
+        if (it >= nitems) continue;
+        const int line = it / nseg, seg = it - line * nseg;
+        const int l1 = line % dv, l2 = line / dv;   // coordinates along axes ax1, ax2
+        const int u0 = seg * seglen, u1 = min(u0 + seglen, du);
         for (int cu = u0; cu < u1; ++cu) {
-          c[ax0] = cu;
+          // node coordinates in box axes x, y, z (selects: no runtime-indexed array)
+          int c[3];
+          c[0] = ax0 == 0 ? cu : (ax0 == 1 ? l2 : l1);
+          c[1] = ax0 == 1 ? cu : (ax0 == 2 ? l2 : l1);
+          c[2] = ax0 == 2 ? cu : (ax0 == 0 ? l2 : l1);
           float ra[3], rb[3], ga[3], gb[3], na, nb;
           for (int k = 0; k < 3; ++k) {
-            ra[k] = static_cast<float>(c[k] - pr.ai[k]) - pr.af[k];
-            rb[k] = static_cast<float>(c[k] - pr.bi[k]) - pr.bf[k];
+            ra[k] = static_cast<float>(c[k] - ai[k]) - af[k];
+            rb[k] = static_cast<float>(c[k] - bi[k]) - bf[k];
           }
           const float fa = adj_eval(A, ra, ga, &na);
           const float fb = adj_eval(Bg, rb, gb, &nb);
@@ -313,44 +351,84 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
       for (int k = 1; k < 12; ++k) x = (lane == k) ? acc[k] : x;
       B.partial[static_cast<size_t>(t) * kAdjPartial + lane] = x;
     }
-    t = __shfl_sync(kFull, tn, 0);
+    qpos = __shfl_sync(kFull, qn, 0);
     __syncwarp();
   }
 }
 
 // ---------------------------------------------------------------- pair post
-__global__ void __launch_bounds__(128) k_adj_post(Params P, Shapes S, Parts D, Lists W, AdjBufs B) {
+// One lane per pair, 32 pairs per one-warp block.  The pair's 12 FP32 tile
+// partials are widened to FP64 (one tile: a conversion only; several tiles:
+// the warp sums them together, 2 tile slots x 16 lanes, all loads of a batch
+// in flight at once), then every lane adds its pair's depth term.
+__global__ void __launch_bounds__(32) k_adj_post(Params P, Shapes S, Parts D, Lists W, AdjBufs B) {
   pdl_begin();
+  const int lane = threadIdx.x;
   const int np = min(W.counters[0], P.max_pairs);
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
-    const PairRec pr = W.pairs[p];
-    const double* tp = W.tape + static_cast<size_t>(p) * kTapeDoubles;
-    double* pg = B.pgrad + static_cast<size_t>(p) * kPairGrad;
-    if (!(tp[0] > 0.0) || W.counters[1] > P.max_tiles) continue;
-    double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int t = pr.tile0; t < pr.tile0 + pr.ntiles; ++t) {
-      const float* q = B.partial + static_cast<size_t>(t) * kAdjPartial;
-      for (int k = 0; k < 12; ++k) acc[k] += static_cast<double>(q[k]);
+  const bool tiles_ok = W.counters[1] <= P.max_tiles;
+  for (int base = blockIdx.x * 32; base < np; base += gridDim.x * 32) {
+    const int p = base + lane;
+    const bool inb = p < np;
+    const PairRec* pr = W.pairs + (inb ? p : 0);
+    const double* tp = W.tape + static_cast<size_t>(inb ? p : 0) * kTapeDoubles;
+    const bool act = inb && tiles_ok && tp[0] > 0.0;
+    const int t0 = pr->tile0, nt = pr->ntiles;
+    double acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = 0.0;
+    if (act && nt == 1) {
+      const float4* q = reinterpret_cast<const float4*>(B.partial + static_cast<size_t>(t0) * kAdjPartial);
+      const float4 a = q[0], b = q[1], c = q[2];
+      acc[0] = widen(a.x); acc[1] = widen(a.y); acc[2] = widen(a.z); acc[3] = widen(a.w);
+      acc[4] = widen(b.x); acc[5] = widen(b.y); acc[6] = widen(b.z); acc[7] = widen(b.w);
+      acc[8] = widen(c.x); acc[9] = widen(c.y); acc[10] = widen(c.z); acc[11] = widen(c.w);
     }
-    const double dx = P.dx;
+    unsigned multi = __ballot_sync(kFull, act && nt > 1);
+    while (multi) {
+      const int src = __ffs(multi) - 1;
+      multi &= multi - 1;
+      const int mt0 = __shfl_sync(kFull, t0, src), mnt = __shfl_sync(kFull, nt, src);
+      const int slot = lane >> 4, c = lane & 15;   // component c < 12 of tiles slot, slot + 2, ...
+      double sum = 0.0;
+      for (int tb = 0; tb < mnt; tb += 16) {
+        float x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int t = tb + slot + 2 * u;
+          x[u] = (t < mnt && c < 12) ? B.partial[static_cast<size_t>(mt0 + t) * kAdjPartial + c] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sum += widen(x[u]);
+      }
+      sum += __shfl_xor_sync(kFull, sum, 16);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const double v = __shfl_sync(kFull, sum, k);
+        if (lane == src) acc[k] = v;
+      }
+    }
+    if (!act) continue;
+    double* pg = B.pgrad + static_cast<size_t>(p) * kPairGrad;
+    const double dx = P.dx, inv_dx = P.inv_dx;
     // lattice position -> physical position
     for (int k = 0; k < 3; ++k) {
-      pg[k] += acc[k] / dx;
+      pg[k] += acc[k] * inv_dx;
       pg[3 + k] += acc[3 + k];
-      pg[6 + k] += acc[6 + k] / dx;
+      pg[6 + k] += acc[6 + k] * inv_dx;
       pg[9 + k] += acc[9 + k];
     }
     // depth term: d = -phiA(x*) - phiB(x*)
     const double gd = pg[12];
     if (gd != 0.0 && tp[7] > 0.0) {
-      const int i = pr.i, j = pr.j;
-      const int idx = min(max(static_cast<int>(tp[13]), 0), pr.dim[0] * pr.dim[1] * pr.dim[2] - 1);
-      const int c[3] = {idx % pr.dim[0], (idx / pr.dim[0]) % pr.dim[1], idx / (pr.dim[0] * pr.dim[1])};
-      const double x[3] = {(pr.lo[0] + c[0]) * dx, (pr.lo[1] + c[1]) * dx, (pr.lo[2] + c[2]) * dx};
+      const int i = pr->i, j = pr->j;
+      const int d0 = pr->dim[0], d1 = pr->dim[1];
+      const int idx = min(max(static_cast<int>(tp[13]), 0), d0 * d1 * pr->dim[2] - 1);
+      const int c[3] = {idx % d0, (idx / d0) % d1, idx / (d0 * d1)};
+      const double x[3] = {(pr->lo[0] + c[0]) * dx, (pr->lo[1] + c[1]) * dx, (pr->lo[2] + c[2]) * dx};
       double XA[3], XB[3], gA[3], gB[3];
       for (int k = 0; k < 3; ++k) {
         XA[k] = D.X[3 * i + k];
-        XB[k] = D.X[3 * j + k] - pr.shift[k] * P.L[k];
+        XB[k] = D.X[3 * j + k] - pr->shift[k] * P.L[k];
       }
       sdf64(S.type[i], S.param + 3 * i, S.planes + 4 * S.face_off[i], S.face_off[i + 1] - S.face_off[i], XA,
             D.R + 9 * i, x, P.inflate, gA);
@@ -371,37 +449,48 @@ __global__ void __launch_bounds__(128) k_adj_post(Params P, Shapes S, Parts D, L
   }
 }
 
-__global__ void __launch_bounds__(128) k_adj_scatter(Params P, Parts D, Lists W, AdjBufs B,
-                                                     double* __restrict__ gpos, double* __restrict__ gquat) {
+// Per particle and component (eight lanes per particle, six used), FP64 adds
+// in the forward order: the pairs where the particle is j (by i), then the
+// pairs where it is i (by j); lane 0 of each group then maps the rotation
+// gradient to the raw quaternion.
+__global__ void __launch_bounds__(32) k_adj_scatter(Params P, Parts D, Lists W, AdjBufs B,
+                                                    double* __restrict__ gpos, double* __restrict__ gquat) {
   pdl_begin();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P.n) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, g0 = lane & ~7;
+  const int p0 = t >> 3, c = t & 7;
+  const bool ok = p0 < P.n;
+  const int p = ok ? p0 : P.n - 1;
   const int np = min(W.counters[0], P.max_pairs);
-  double gx[3] = {0, 0, 0}, tau[3] = {0, 0, 0};
-  const int nd = W.dn_count[p];
-  for (int r = 0; r < nd; ++r) {
-    const int q = W.dn_pair[static_cast<size_t>(p) * P.max_nbr + r];
-    if (q >= np) continue;
-    const double* e = B.pgrad + static_cast<size_t>(q) * kPairGrad;
-    for (int k = 0; k < 3; ++k) { gx[k] += e[6 + k]; tau[k] += e[9 + k]; }
+  double acc = 0.0;
+  if (ok && c < 6) {
+    const int nd = W.dn_count[p];
+    for (int r = 0; r < nd; ++r) {   // p is the pair's j: columns 6..11
+      const int q = W.dn_pair[static_cast<size_t>(p) * P.max_nbr + r];
+      if (q < np) acc += B.pgrad[static_cast<size_t>(q) * kPairGrad + 6 + c];
+    }
+    const int r0 = W.row_off[p], nu = W.up_count[p];
+    for (int r = 0; r < nu; ++r) {   // p is the pair's i: columns 0..5
+      const int q = r0 + r;
+      if (q >= np) break;
+      acc += B.pgrad[static_cast<size_t>(q) * kPairGrad + c];
+    }
   }
-  const int r0 = W.row_off[p], nu = W.up_count[p];
-  for (int r = 0; r < nu; ++r) {
-    const int q = r0 + r;
-    if (q >= np) break;
-    const double* e = B.pgrad + static_cast<size_t>(q) * kPairGrad;
-    for (int k = 0; k < 3; ++k) { gx[k] += e[k]; tau[k] += e[3 + k]; }
+  double tau[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) tau[k] = __shfl_sync(kFull, acc, g0 + 3 + k);
+  if (!ok) return;
+  if (c < 3) gpos[3 * p + c] = acc;
+  if (c == 0) {
+    const double* qr = D.qhat + 4 * p;
+    const double iq = fl::nr_rsqrt(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
+    const double w = qr[0] * iq, v[3] = {qr[1] * iq, qr[2] * iq, qr[3] * iq};
+    const double s2 = 2.0 * iq;
+    double tv[3];
+    cross3(tau, v, tv);
+    gquat[4 * p] = -s2 * (v[0] * tau[0] + v[1] * tau[1] + v[2] * tau[2]);
+    for (int k = 0; k < 3; ++k) gquat[4 * p + 1 + k] = s2 * (w * tau[k] + tv[k]);
   }
-  const double* qr = D.qhat + 4 * p;
-  const double qn = sqrt(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
-  const double iq = 1.0 / qn;
-  const double w = qr[0] * iq, v[3] = {qr[1] * iq, qr[2] * iq, qr[3] * iq};
-  const double s = 2.0 * iq;
-  double tv[3];
-  cross3(tau, v, tv);
-  for (int k = 0; k < 3; ++k) gpos[3 * p + k] = gx[k];
-  gquat[4 * p] = -s * (v[0] * tau[0] + v[1] * tau[1] + v[2] * tau[2]);
-  for (int k = 0; k < 3; ++k) gquat[4 * p + 1 + k] = s * (w * tau[k] + tv[k]);
 }
 
 }  // namespace
@@ -421,12 +510,18 @@ void launch_adjoint(const Params& P, const Shapes& S, const Parts& D, const List
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int need = (P.max_pairs + 127) / 128;
-  const int pgrid = need < 2 * sms ? (need > 0 ? need : 1) : 2 * sms;
-  launch_pdl(k_adj_pre, dim3(pgrid), dim3(128), 0, st, P, S, D, W, B, vel, gF, gT);
-  launch_pdl(k_adj_cells, dim3(grid), dim3(kWarps * 32), 0, st, P, S, D, W, B);
-  launch_pdl(k_adj_post, dim3(pgrid), dim3(128), 0, st, P, S, D, W, B);
-  launch_pdl(k_adj_scatter, dim3((P.n + 127) / 128), dim3(128), 0, st, P, D, W, B, gpos, gquat);
+  const int wneed0 = (P.max_pairs + 31) / 32;
+  const int wgrid0 = wneed0 < 8 * sms ? (wneed0 > 0 ? wneed0 : 1) : 8 * sms;
+  launch_pdl(k_adj_pre, dim3(wgrid0), dim3(32), 0, st, P, S, D, W, B, vel, gF, gT);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_cells, kWarps * 32, 0);
+  const int cgrid = (per_sm > 0 ? per_sm : 1) * sms;   // persistent: every resident slot pulls tiles
+  (void)grid;
+  launch_pdl(k_adj_cells, dim3(cgrid), dim3(kWarps * 32), 0, st, P, S, D, W, B);
+  const int wneed = (P.max_pairs + 31) / 32;
+  const int wgrid = wneed < 8 * sms ? (wneed > 0 ? wneed : 1) : 8 * sms;
+  launch_pdl(k_adj_post, dim3(wgrid), dim3(32), 0, st, P, S, D, W, B);
+  launch_pdl(k_adj_scatter, dim3((8 * P.n + 31) / 32), dim3(32), 0, st, P, D, W, B, gpos, gquat);
 }
 
 }  // namespace gbc
