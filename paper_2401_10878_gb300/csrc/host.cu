@@ -545,7 +545,7 @@ contact_status contact_narrow_time(contact_ctx* c, float* ms) {
 }
 
 int32_t contact_kernels_per_step(const contact_ctx*) { return 5; }
-int32_t contact_kernels_per_backward(const contact_ctx*) { return 4; }
+int32_t contact_kernels_per_backward(const contact_ctx*) { return 3; }
 
 contact_status contact_backward(contact_ctx* c, const double* grad_force, const double* grad_torque,
                                 double* grad_pos, double* grad_quat) {

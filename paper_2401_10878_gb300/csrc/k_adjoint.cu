@@ -16,7 +16,9 @@
 //   pair (translation and infinitesimal world rotation of each particle):
 //     dphi/dX = -grad phi,  dphi/domega = grad phi x r,
 //     sphere: d(grad phi)/dX = -(I - g g^T)/|r|; faces: d(grad phi) = omega x grad phi.
-// k_adj_post: FP64 sum of tile partials, depth term at x*, lattice -> physical.
+//   The warp completing a pair's last tile sums the tile partials in FP64
+//   and stages the pair; eight staged pairs at a time get the post step:
+//   lattice -> physical and the depth term at x* (four lanes per pair).
 // k_adj_scatter: per particle in the forward order; the rotation gradient tau
 //   becomes dL/dq = (2/|q|) (-v.tau, w tau + tau x v) for q/|q| = (w, v).
 #include <cfloat>
@@ -38,7 +40,16 @@ struct AdjBufs {
   float* partial;  // [max_tiles, 12]
   float* seeds;    // [max_pairs, 8]
   double* pgrad;   // [max_pairs, 16]
+  int* done;       // [max_pairs] tiles of the pair swept so far (pairs of several tiles)
 };
+
+// A pair whose cell sums are complete, staged in shared memory for the post step.
+struct AdjStage {
+  double s[12];    // FP64 sums of the 12 pose directions (lattice units)
+  int q;           // pair index
+  int pad;
+};
+constexpr int kAdjStage = 8;   // pairs per post pass (four lanes each)
 
 __device__ __forceinline__ void cross3(const double a[3], const double b[3], double c[3]) {
   c[0] = a[1] * b[2] - a[2] * b[1];
@@ -60,6 +71,7 @@ __global__ void __launch_bounds__(32) k_adj_pre(Params P, Shapes S, Parts D, Lis
     double* pg = B.pgrad + static_cast<size_t>(p) * kPairGrad;
     for (int k = 0; k < kSeedFloats; ++k) sd[k] = 0.f;
     for (int k = 0; k < kPairGrad; ++k) pg[k] = 0.0;
+    B.done[p] = 0;
     const double S0 = tp[0];
     const double fmag = tp[12];
     if (!(S0 > 0.0)) continue;
@@ -218,18 +230,148 @@ __device__ __forceinline__ float adj_eval(const AdjGeom& g, const float r[3], fl
   return best;
 }
 
+// phi alone (the same arithmetic as adj_eval, without the gradient): the band test
+__device__ __forceinline__ float adj_phi(const AdjGeom& g, const float r[3]) {
+  if (g.type == 0) return sqrtf(fmaf(r[0], r[0], fmaf(r[1], r[1], r[2] * r[2]))) - g.size[0];
+  if (g.type == 1) {
+    float best = -FLT_MAX;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float y = fmaf(g.rt[3 * k], r[0], fmaf(g.rt[3 * k + 1], r[1], g.rt[3 * k + 2] * r[2]));
+      best = fmaxf(best, fabsf(y) - g.size[k]);
+    }
+    return best;
+  }
+  float best = -FLT_MAX;
+  for (int f = 0; f < g.nf; ++f) {
+    const float4 e = g.sp[f];
+    best = fmaxf(best, fmaf(e.x, r[0], fmaf(e.y, r[1], fmaf(e.z, r[2], -e.w))));
+  }
+  return best;
+}
+
 __device__ __forceinline__ void cross3f(const float a[3], const float b[3], float c[3]) {
   c[0] = a[1] * b[2] - a[2] * b[1];
   c[1] = a[2] * b[0] - a[0] * b[2];
   c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
+
+// ---------------------------------------------------------------- pair post
+// FP64 post step of up to kAdjStage staged pairs, four lanes per pair
+// (component k = 0..2 on lanes 0..2, lane 3 idle): the cell sums scaled to
+// physical units are added to the pair's pose gradient, then the depth term of
+// d = -phiA(x*) - phiB(x*) at the deepest node: d(-phi)/dX = grad phi and
+// d(-phi)/domega = r x grad phi (world frame; the face of the maximum, first
+// index on ties).
+__device__ __forceinline__ void adj_post_pass(const Params& P, const Shapes& S, const Parts& D, const Lists& W,
+                                              const AdjBufs& B, const AdjStage* e, int n) {
+  const int lane = threadIdx.x & 31;
+  const int slot = lane >> 2, k = lane & 3, kc = k < 3 ? k : 0, b0 = lane & ~3;
+  const int k1 = kc == 2 ? 0 : kc + 1, k2 = kc == 0 ? 2 : kc - 1;
+  const bool act = slot < n;
+  const AdjStage& st = e[act ? slot : 0];
+  const int q = st.q;
+  double* pg = B.pgrad + static_cast<size_t>(q) * kPairGrad;
+  const double* tp = W.tape + static_cast<size_t>(q) * kTapeDoubles;
+  const PairRec& pr = W.pairs[q];
+  const double gd = pg[12];
+  const bool depth = gd != 0.0 && tp[7] > 0.0;
+  const double inv_dx = P.inv_dx;
+  double dA = 0.0, dcA = 0.0, dB = 0.0, dcB = 0.0;   // depth-term increments of component kc
+  if (__any_sync(kFull, act && depth)) {
+    const int i = pr.i, j = pr.j;
+    const int d0 = pr.dim[0], d1 = pr.dim[1], d2 = pr.dim[2];
+    const int idx = min(max(static_cast<int>(tp[13]), 0), d0 * d1 * d2 - 1);
+    const int ck = kc == 0 ? idx % d0 : (kc == 1 ? (idx / d0) % d1 : idx / (d0 * d1));
+    const int lok = kc == 0 ? pr.lo[0] : (kc == 1 ? pr.lo[1] : pr.lo[2]);
+    const int sh = kc == 0 ? pr.shift[0] : (kc == 1 ? pr.shift[1] : pr.shift[2]);
+    const double Lk = kc == 0 ? P.L[0] : (kc == 1 ? P.L[1] : P.L[2]);
+    const double xk = static_cast<double>(lok + ck) * P.dx;
+    const double XA = D.X[3 * i + kc];
+    const double XB = D.X[3 * j + kc] - (sh == 0 ? 0.0 : (sh > 0 ? Lk : -Lk));
+    const double rAk = xk - XA, rBk = xk - XB;
+    double rA[3], rB[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      rA[c] = __shfl_sync(kFull, rAk, b0 + c);
+      rB[c] = __shfl_sync(kFull, rBk, b0 + c);
+    }
+    // world gradient component kc of one particle's phi at x* (r = x* - X, scalars)
+    auto grad_k = [&](int pid, double r0, double r1, double r2) -> double {
+      const double* R = D.R + 9 * pid;
+      const int type = S.type[pid];
+      const double yk = R[kc] * r0 + R[3 + kc] * r1 + R[6 + kc] * r2;   // y = R^T r
+      const double y0 = __shfl_sync(kFull, yk, b0), y1 = __shfl_sync(kFull, yk, b0 + 1),
+                   y2 = __shfl_sync(kFull, yk, b0 + 2);
+      // this lane's candidate: value and index of its faces (cuboid: face pair kc; polytope: kc, kc + 3, ...)
+      double best = -1e300;
+      int bidx = 0x7fffffff;
+      if (type == 1) {
+        best = fabs(yk) - S.param[3 * pid + kc];
+        bidx = kc;
+      } else if (type == 2) {
+        const int f0 = S.face_off[pid], nf = S.face_off[pid + 1] - f0;
+        for (int f = kc; f < nf; f += 3) {
+          const double* pl = S.planes + 4 * (f0 + f);
+          const double a = (pl[0] * y0 + pl[1] * y1 + pl[2] * y2) - pl[3];
+          if (a > best) { best = a; bidx = f; }
+        }
+      }
+      if (k == 3) { best = -1e300; bidx = 0x7fffffff; }
+      // first maximal face over the pair's three lanes
+#pragma unroll
+      for (int o = 1; o <= 2; o <<= 1) {
+        const double ob = __shfl_xor_sync(kFull, best, o);
+        const int oi = __shfl_xor_sync(kFull, bidx, o);
+        if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+      }
+      // sphere r / |r|; cuboid R e_kk sign(y_kk); polytope R n_f
+      if (type == 0) {
+        const double nr = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+        return nr > 0.0 ? (kc == 0 ? r0 : (kc == 1 ? r1 : r2)) / nr : 0.0;
+      }
+      if (type == 1) {
+        const double ykk = bidx == 0 ? y0 : (bidx == 1 ? y1 : y2);
+        return R[3 * kc + bidx] * (ykk < 0.0 ? -1.0 : 1.0);
+      }
+      const double* pl = S.planes + 4 * (S.face_off[pid] + bidx);
+      return R[3 * kc] * pl[0] + R[3 * kc + 1] * pl[1] + R[3 * kc + 2] * pl[2];
+    };
+    const double g[2] = {grad_k(i, rA[0], rA[1], rA[2]), grad_k(j, rB[0], rB[1], rB[2])};
+    // r x grad phi, component kc
+    const double gA1 = __shfl_sync(kFull, g[0], b0 + k1), gA2 = __shfl_sync(kFull, g[0], b0 + k2);
+    const double gB1 = __shfl_sync(kFull, g[1], b0 + k1), gB2 = __shfl_sync(kFull, g[1], b0 + k2);
+    const double rA1 = kc == 0 ? rA[1] : (kc == 1 ? rA[2] : rA[0]), rA2 = kc == 0 ? rA[2] : (kc == 1 ? rA[0] : rA[1]);
+    const double rB1 = kc == 0 ? rB[1] : (kc == 1 ? rB[2] : rB[0]), rB2 = kc == 0 ? rB[2] : (kc == 1 ? rB[0] : rB[1]);
+    dA = gd * g[0];
+    dcA = gd * (rA1 * gA2 - rA2 * gA1);
+    dB = gd * g[1];
+    dcB = gd * (rB1 * gB2 - rB2 * gB1);
+  }
+  if (act && k < 3) {
+    // lattice position -> physical position, then the depth term
+    pg[k] += st.s[k] * inv_dx;
+    pg[3 + k] += st.s[3 + k];
+    pg[6 + k] += st.s[6 + k] * inv_dx;
+    pg[9 + k] += st.s[9 + k];
+    if (depth) {
+      pg[k] += dA;
+      pg[3 + k] += dcA;
+      pg[6 + k] += dB;
+      pg[9 + k] += dcB;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, Parts D, Lists W, AdjBufs B) {
   __shared__ float4 s_pl[kWarps][2][kMaxFaces];
+  __shared__ AdjStage s_st[kWarps][kAdjStage];
+  int nst = 0;   // pairs staged in s_st[wid]
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int ntiles = min(W.counters[1], P.max_tiles);
-  const float inv_w = P.inv_w;
+  const float inv_w = P.inv_w, hw = 0.5f * P.wdx_l;
   // queue position -> tile record of the forward pass: cost buckets, dearest first
   int bend[kCostBuckets];
   {
@@ -269,7 +411,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
     float acc[12];
     for (int k = 0; k < 12; ++k) acc[k] = 0.f;
     const bool active = (s0 != 0.f) || (s1[0] != 0.f) || (s1[1] != 0.f) || (s1[2] != 0.f) || (sg[0] != 0.f) ||
-                        (sg[1] != 0.f) || (sg[2] != 0.f);
+                        (sg[1] != 0.f) || (sg[2] != 0.f) || (B.pgrad[static_cast<size_t>(p) * kPairGrad + 12] != 0.0);
     if (active) {
       AdjGeom A, Bg;
       adj_load(S, D, rec_i, ai, af, s_pl[wid][0], A);
@@ -295,6 +437,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
             ra[k] = static_cast<float>(c[k] - ai[k]) - af[k];
             rb[k] = static_cast<float>(c[k] - bi[k]) - bf[k];
           }
+          // every term below needs both phi inside the upper half of the band
+          if (fmaxf(adj_phi(A, ra), adj_phi(Bg, rb)) >= hw) continue;
           const float fa = adj_eval(A, ra, ga, &na);
           const float fb = adj_eval(Bg, rb, gb, &nb);
           const float ta = fminf(fmaxf(fmaf(fa, -inv_w, 0.5f), 0.f), 1.f);
@@ -345,107 +489,57 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
     for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
       for (int k = 0; k < 12; ++k) acc[k] += __shfl_xor_sync(kFull, acc[k], off);
-    if (lane < 12) {
+    if (active) {
+      // end of the pair: one tile -> its sums directly; several -> the warp
+      // completing the last tile sums all partials in FP64 (fixed order)
+      bool complete = true;
+      double sum = 0.0;   // lane c < 12: component c
       float x = acc[0];
 #pragma unroll
       for (int k = 1; k < 12; ++k) x = (lane == k) ? acc[k] : x;
-      B.partial[static_cast<size_t>(t) * kAdjPartial + lane] = x;
+      const int ntp = prg.ntiles;
+      if (ntp == 1) {
+        sum = widen(x);
+      } else {
+        if (lane < 12) B.partial[static_cast<size_t>(t) * kAdjPartial + lane] = x;
+        __threadfence();
+        int prev = 0;
+        if (lane == 0) prev = atomicAdd(&B.done[p], 1);
+        prev = __shfl_sync(kFull, prev, 0);
+        complete = prev == ntp - 1;
+        if (complete) {
+          __threadfence();
+          const int slot = lane >> 4, c = lane & 15;   // component c < 12 of tiles slot, slot + 2, ...
+          for (int tb = 0; tb < ntp; tb += 16) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int tt = tb + slot + 2 * u;
+              v[u] = (tt < ntp && c < 12) ? __ldcg(B.partial + static_cast<size_t>(tile0 + tt) * kAdjPartial + c) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sum += widen(v[u]);
+          }
+          sum += __shfl_xor_sync(kFull, sum, 16);
+        }
+      }
+      if (complete) {
+        if (lane < 12) s_st[wid][nst].s[lane] = sum;
+        if (lane == 0) s_st[wid][nst].q = p;
+        if (++nst == kAdjStage) {
+          __syncwarp();
+          adj_post_pass(P, S, D, W, B, s_st[wid], nst);
+          __syncwarp();
+          nst = 0;
+        }
+      }
     }
     qpos = __shfl_sync(kFull, qn, 0);
     __syncwarp();
   }
-}
-
-// ---------------------------------------------------------------- pair post
-// One lane per pair, 32 pairs per one-warp block.  The pair's 12 FP32 tile
-// partials are widened to FP64 (one tile: a conversion only; several tiles:
-// the warp sums them together, 2 tile slots x 16 lanes, all loads of a batch
-// in flight at once), then every lane adds its pair's depth term.
-__global__ void __launch_bounds__(32) k_adj_post(Params P, Shapes S, Parts D, Lists W, AdjBufs B) {
-  pdl_begin();
-  const int lane = threadIdx.x;
-  const int np = min(W.counters[0], P.max_pairs);
-  const bool tiles_ok = W.counters[1] <= P.max_tiles;
-  for (int base = blockIdx.x * 32; base < np; base += gridDim.x * 32) {
-    const int p = base + lane;
-    const bool inb = p < np;
-    const PairRec* pr = W.pairs + (inb ? p : 0);
-    const double* tp = W.tape + static_cast<size_t>(inb ? p : 0) * kTapeDoubles;
-    const bool act = inb && tiles_ok && tp[0] > 0.0;
-    const int t0 = pr->tile0, nt = pr->ntiles;
-    double acc[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = 0.0;
-    if (act && nt == 1) {
-      const float4* q = reinterpret_cast<const float4*>(B.partial + static_cast<size_t>(t0) * kAdjPartial);
-      const float4 a = q[0], b = q[1], c = q[2];
-      acc[0] = widen(a.x); acc[1] = widen(a.y); acc[2] = widen(a.z); acc[3] = widen(a.w);
-      acc[4] = widen(b.x); acc[5] = widen(b.y); acc[6] = widen(b.z); acc[7] = widen(b.w);
-      acc[8] = widen(c.x); acc[9] = widen(c.y); acc[10] = widen(c.z); acc[11] = widen(c.w);
-    }
-    unsigned multi = __ballot_sync(kFull, act && nt > 1);
-    while (multi) {
-      const int src = __ffs(multi) - 1;
-      multi &= multi - 1;
-      const int mt0 = __shfl_sync(kFull, t0, src), mnt = __shfl_sync(kFull, nt, src);
-      const int slot = lane >> 4, c = lane & 15;   // component c < 12 of tiles slot, slot + 2, ...
-      double sum = 0.0;
-      for (int tb = 0; tb < mnt; tb += 16) {
-        float x[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int t = tb + slot + 2 * u;
-          x[u] = (t < mnt && c < 12) ? B.partial[static_cast<size_t>(mt0 + t) * kAdjPartial + c] : 0.0f;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) sum += widen(x[u]);
-      }
-      sum += __shfl_xor_sync(kFull, sum, 16);
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        const double v = __shfl_sync(kFull, sum, k);
-        if (lane == src) acc[k] = v;
-      }
-    }
-    if (!act) continue;
-    double* pg = B.pgrad + static_cast<size_t>(p) * kPairGrad;
-    const double dx = P.dx, inv_dx = P.inv_dx;
-    // lattice position -> physical position
-    for (int k = 0; k < 3; ++k) {
-      pg[k] += acc[k] * inv_dx;
-      pg[3 + k] += acc[3 + k];
-      pg[6 + k] += acc[6 + k] * inv_dx;
-      pg[9 + k] += acc[9 + k];
-    }
-    // depth term: d = -phiA(x*) - phiB(x*)
-    const double gd = pg[12];
-    if (gd != 0.0 && tp[7] > 0.0) {
-      const int i = pr->i, j = pr->j;
-      const int d0 = pr->dim[0], d1 = pr->dim[1];
-      const int idx = min(max(static_cast<int>(tp[13]), 0), d0 * d1 * pr->dim[2] - 1);
-      const int c[3] = {idx % d0, (idx / d0) % d1, idx / (d0 * d1)};
-      const double x[3] = {(pr->lo[0] + c[0]) * dx, (pr->lo[1] + c[1]) * dx, (pr->lo[2] + c[2]) * dx};
-      double XA[3], XB[3], gA[3], gB[3];
-      for (int k = 0; k < 3; ++k) {
-        XA[k] = D.X[3 * i + k];
-        XB[k] = D.X[3 * j + k] - pr->shift[k] * P.L[k];
-      }
-      sdf64(S.type[i], S.param + 3 * i, S.planes + 4 * S.face_off[i], S.face_off[i + 1] - S.face_off[i], XA,
-            D.R + 9 * i, x, P.inflate, gA);
-      sdf64(S.type[j], S.param + 3 * j, S.planes + 4 * S.face_off[j], S.face_off[j + 1] - S.face_off[j], XB,
-            D.R + 9 * j, x, P.inflate, gB);
-      double rA[3], rB[3], cA[3], cB[3];
-      for (int k = 0; k < 3; ++k) { rA[k] = x[k] - XA[k]; rB[k] = x[k] - XB[k]; }
-      cross3(rA, gA, cA);
-      cross3(rB, gB, cB);
-      // d(-phi)/dX = grad phi ; d(-phi)/domega = r x grad phi (physical r: rotation is unitless)
-      for (int k = 0; k < 3; ++k) {
-        pg[k] += gd * gA[k];
-        pg[3 + k] += gd * cA[k];
-        pg[6 + k] += gd * gB[k];
-        pg[9 + k] += gd * cB[k];
-      }
-    }
+  if (nst > 0) {
+    __syncwarp();
+    adj_post_pass(P, S, D, W, B, s_st[wid], nst);
   }
 }
 
@@ -497,7 +591,7 @@ __global__ void __launch_bounds__(32) k_adj_scatter(Params P, Parts D, Lists W, 
 
 size_t adjoint_scratch_doubles(int max_pairs, int max_tiles) {
   return static_cast<size_t>(max_tiles) * kAdjPartial / 2 + static_cast<size_t>(max_pairs) * kSeedFloats / 2 +
-         static_cast<size_t>(max_pairs) * kPairGrad + 16;
+         static_cast<size_t>(max_pairs) * kPairGrad + static_cast<size_t>(max_pairs) / 2 + 16;
 }
 
 void launch_adjoint(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel,
@@ -507,6 +601,7 @@ void launch_adjoint(const Params& P, const Shapes& S, const Parts& D, const List
   B.partial = reinterpret_cast<float*>(scratch);
   B.seeds = B.partial + static_cast<size_t>(P.max_tiles) * kAdjPartial;
   B.pgrad = reinterpret_cast<double*>(B.seeds + static_cast<size_t>(P.max_pairs) * kSeedFloats + 8);
+  B.done = reinterpret_cast<int*>(B.pgrad + static_cast<size_t>(P.max_pairs) * kPairGrad);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -518,9 +613,6 @@ void launch_adjoint(const Params& P, const Shapes& S, const Parts& D, const List
   const int cgrid = (per_sm > 0 ? per_sm : 1) * sms;   // persistent: every resident slot pulls tiles
   (void)grid;
   launch_pdl(k_adj_cells, dim3(cgrid), dim3(kWarps * 32), 0, st, P, S, D, W, B);
-  const int wneed = (P.max_pairs + 31) / 32;
-  const int wgrid = wneed < 8 * sms ? (wneed > 0 ? wneed : 1) : 8 * sms;
-  launch_pdl(k_adj_post, dim3(wgrid), dim3(32), 0, st, P, S, D, W, B);
   launch_pdl(k_adj_scatter, dim3((8 * P.n + 31) / 32), dim3(32), 0, st, P, D, W, B, gpos, gquat);
 }
 
