@@ -558,16 +558,22 @@ __global__ void __launch_bounds__(32) k_adj_scatter(Params P, Parts D, Lists W, 
   const int np = min(W.counters[0], P.max_pairs);
   double acc = 0.0;
   if (ok && c < 6) {
-    const int nd = W.dn_count[p];
-    for (int r = 0; r < nd; ++r) {   // p is the pair's j: columns 6..11
-      const int q = W.dn_pair[static_cast<size_t>(p) * P.max_nbr + r];
-      if (q < np) acc += B.pgrad[static_cast<size_t>(q) * kPairGrad + 6 + c];
-    }
-    const int r0 = W.row_off[p], nu = W.up_count[p];
-    for (int r = 0; r < nu; ++r) {   // p is the pair's i: columns 0..5
-      const int q = r0 + r;
-      if (q >= np) break;
-      acc += B.pgrad[static_cast<size_t>(q) * kPairGrad + c];
+    // contributions in order (j side, then i side), eight loads in flight at a time
+    const int* dp = W.dn_pair + static_cast<size_t>(p) * P.max_nbr;
+    const int nd = W.dn_count[p], r0 = W.row_off[p], nu = W.up_count[p];
+    const int total = nd + nu;
+    for (int base = 0; base < total; base += 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = base + u;
+        const bool isj = e < nd;   // p is the pair's j: columns 6..11; else its i: columns 0..5
+        const int q = isj ? dp[e] : (e < total ? r0 + (e - nd) : np);
+        v[u] = (q >= 0 && q < np) ? B.pgrad[static_cast<size_t>(q) * kPairGrad + (isj ? 6 + c : c)] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (base + u < total) acc += v[u];
     }
   }
   double tau[3];
