@@ -163,7 +163,9 @@ contact_status contact_set_stream(contact_ctx* ctx, void* stream);
 /* Synchronises, then fills stats[0..9] (host) with the last step's pair count,
  * node evaluations (sum of box volumes), node tiles, pairs with V > 0,
  * kernels launched per step, narrow-phase grid size, bins per axis (x),
- * whether the last step replayed a graph, the nominal FP32 lane-operations of
+ * whether the last step replayed a graph (0: instantiated it, or no graph;
+ * 1: replayed; 2: replayed after updating it in place for new buffers on the
+ * same stream), the nominal FP32 lane-operations of
  * the node sweep (sum over pairs of box volume x (ops_i + ops_j), with 7 per
  * sphere test, 15 per cuboid test and 4F per polytope test), and the tile
  * capacity. */

@@ -30,7 +30,7 @@ struct contact_ctx {
   // graph cache
   cudaGraphExec_t gexec = nullptr;
   const void* gkey[9] = {};
-  bool last_replay = false;
+  int last_replay = 0;   // 0 instantiated (or no graph), 1 replayed, 2 replayed after an in-place update
   cudaEvent_t ev_narrow[2] = {nullptr, nullptr};
   // tape of the last step (for contact_backward)
   bool have_step = false;
@@ -447,28 +447,42 @@ contact_status contact_step(contact_ctx* c, const double* pos, const double* qua
   cudaError_t e = cudaStreamIsCapturing(c->stream, &cap);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamIsCapturing");
   const void* key[9] = {pos, quat, vel, pair_ij, pair_out, n_pairs, force, torque, c->stream};
-  c->last_replay = false;
+  c->last_replay = 0;
   if (cap == cudaStreamCaptureStatusNone && c->cfg.use_graph && c->stream != nullptr) {
     if (c->gexec == nullptr || std::memcmp(key, c->gkey, sizeof(key)) != 0) {
-      if (c->gexec) {
-        cudaGraphExecDestroy(c->gexec);
-        c->gexec = nullptr;
-      }
+      // capture the step; new buffers on the same stream only change kernel
+      // arguments, so the executable graph is updated in place (no
+      // re-instantiation); otherwise it is instantiated anew
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
       enqueue_step(c, true, pos, quat, vel, pair_ij, pair_out, n_pairs, force, torque);
       e = cudaStreamEndCapture(c->stream, &g);
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
-      e = cudaGraphInstantiate(&c->gexec, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) {
-        c->gexec = nullptr;
-        return cuda_fail(c, e, "cudaGraphInstantiate");
+      bool updated = false;
+      if (c->gexec != nullptr && c->gkey[8] == c->stream) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(c->gexec, g, &info) == cudaSuccess;
+        if (!updated) cudaGetLastError();   // clear the update failure; instantiate below
       }
+      if (!updated) {
+        if (c->gexec) {
+          cudaGraphExecDestroy(c->gexec);
+          c->gexec = nullptr;
+        }
+        e = cudaGraphInstantiate(&c->gexec, g, 0);
+        if (e != cudaSuccess) {
+          cudaGraphDestroy(g);
+          c->gexec = nullptr;
+          return cuda_fail(c, e, "cudaGraphInstantiate");
+        }
+      } else {
+        c->last_replay = 2;
+      }
+      cudaGraphDestroy(g);
       std::memcpy(c->gkey, key, sizeof(key));
     } else {
-      c->last_replay = true;
+      c->last_replay = 1;
     }
     e = cudaGraphLaunch(c->gexec, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
@@ -521,7 +535,7 @@ contact_status contact_stats(contact_ctx* c, int64_t* stats) {
   stats[4] = contact_kernels_per_step(c);
   stats[5] = c->grid_narrow;
   stats[6] = c->P.nbin[0];
-  stats[7] = c->last_replay ? 1 : 0;
+  stats[7] = c->last_replay;
   stats[8] = static_cast<int64_t>(u[1]);
   stats[9] = c->P.max_tiles;
   return CONTACT_OK;

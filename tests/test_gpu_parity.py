@@ -202,6 +202,27 @@ def test_cell_list_bin_capacity():
     m.close()
 
 
+def test_graph_update_for_new_buffers():
+    """New input buffers on the same stream update the captured graph in place
+    (stats 'replayed' = 2) instead of instantiating it again; the results stay
+    those of a fresh context, and the same buffers replay it (= 1)."""
+    st = W.mixed_grid_27()
+    m = model_for(st)
+    tp = torch.tensor(st.pos, device="cuda")
+    tq = torch.tensor(st.quat, device="cuda")
+    m.step(tp, tq)
+    assert m.stats()["replayed"] == 0
+    ref_f, ref_p = m.force.clone(), m.pair_out.clone()
+    tp2, tq2 = tp.clone(), tq.clone()
+    m.step(tp2, tq2)
+    assert m.stats()["replayed"] == 2
+    assert torch.equal(m.force, ref_f) and torch.equal(m.pair_out, ref_p)
+    m.step(tp2, tq2)
+    assert m.stats()["replayed"] == 1
+    assert torch.equal(m.force, ref_f)
+    m.close()
+
+
 def test_user_stream_capture():
     st = W.mixed_grid_27()
     m = model_for(st, use_graph=False)
