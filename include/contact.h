@@ -140,6 +140,22 @@ contact_status contact_step(contact_ctx* ctx, const double* pos, const double* q
                             int32_t* pair_ij, double* pair_out, int32_t* n_pairs, double* force,
                             double* torque);
 
+/* contact_step with HOST buffers, end to end: copies pos [N,3], quat [N,4]
+ * and vel [N,6] (or NULL) from host memory into context-owned device buffers,
+ * runs the step, copies force and torque [N,3] and the pair count back to host
+ * memory (n_pairs, force, torque must not be NULL), and returns when the
+ * copies are complete.  When pair_ij / pair_out are not NULL the first
+ * min(P, max_pairs) rows of the pair outputs are copied to them as well (as
+ * laid out by contact_step).  Page-locked host buffers are copied inside one
+ * captured graph together with the step; pageable ones with ordinary copies
+ * around it.  The device buffers are allocated at the first call and owned by
+ * the context.  Errors: those of contact_step, reported by this call (it
+ * synchronises the context stream); CONTACT_ENOMEM if the buffers cannot be
+ * allocated.  A later contact_backward differentiates this step. */
+contact_status contact_step_host(contact_ctx* ctx, const double* pos, const double* quat, const double* vel,
+                                 int32_t* n_pairs, double* force, double* torque, int32_t* pair_ij,
+                                 double* pair_out);
+
 /* Gradient of L = sum_p (grad_force_p . force_p + grad_torque_p . torque_p)
  * of the last contact_step with respect to its positions and raw quaternions
  * (the quaternion gradient is orthogonal to the quaternion).  Needs the

@@ -30,7 +30,7 @@ PAIR_OUT_COLS = 11
 EXPORTS = ["contact_config_default", "contact_init", "contact_step", "contact_backward", "contact_check",
            "contact_clear_error", "contact_last_error", "contact_set_stream", "contact_stats",
            "contact_particle_boxes", "contact_narrow_time", "contact_damping_factor", "contact_kernels_per_step",
-           "contact_kernels_per_backward", "contact_destroy", "contact_step_noalloc"]
+           "contact_kernels_per_backward", "contact_destroy", "contact_step_noalloc", "contact_step_host"]
 
 
 class Config(ctypes.Structure):
@@ -99,6 +99,8 @@ def load_library(build_if_missing: bool = True):
     lib.contact_destroy.restype = None
     lib.contact_step_noalloc.argtypes = [ctypes.POINTER(Config)] + [P] * 12
     lib.contact_step_noalloc.restype = I32
+    lib.contact_step_host.argtypes = [P] * 9
+    lib.contact_step_host.restype = I32
     _lib = lib
     return lib
 
@@ -172,6 +174,42 @@ class Contact:
     def _raise(self, rc, what):
         msg = self.lib.contact_last_error(self.ctx).decode()
         raise ContactError(rc, f"{what}: {msg}")
+
+    def step_host(self, pos, quat, vel=None, force=None, torque=None, pairs=False):
+        """contact_step_host: host (CPU) float64 arrays in, host forces and
+        torques out; returns when the copies are complete.  Page-locked torch
+        CPU tensors (pin_memory) are copied inside one captured graph with the
+        step.  With pairs=True the pair ids and outputs are copied too."""
+        def host(t, shape):
+            t = torch.as_tensor(t, dtype=torch.float64)
+            if t.is_cuda or tuple(t.shape) != shape or not t.is_contiguous():
+                raise ContactError(EINVAL, f"step_host: expected a contiguous CPU float64 array of shape {shape}")
+            return t
+        pos = host(pos, (self.n, 3))
+        quat = host(quat, (self.n, 4))
+        vel = host(vel, (self.n, 6)) if vel is not None else None
+        force = torch.empty((self.n, 3), dtype=torch.float64) if force is None else host(force, (self.n, 3))
+        torque = torch.empty((self.n, 3), dtype=torch.float64) if torque is None else host(torque, (self.n, 3))
+        pin = force.is_pinned()
+        if getattr(self, "_host_np", {}).get(pin) is None:   # reused across calls (a pinned allocation is slow)
+            self._host_np = dict(getattr(self, "_host_np", {}))
+            self._host_np[pin] = torch.zeros(1, dtype=torch.int32, pin_memory=pin)
+        n_pairs = self._host_np[pin]
+        pij = torch.empty((self.max_pairs, 2), dtype=torch.int32) if pairs else None
+        pout = torch.empty((self.max_pairs, 11), dtype=torch.float64) if pairs else None
+        rc = self.lib.contact_step_host(self.ctx, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(quat.data_ptr()),
+                                        ctypes.c_void_p(vel.data_ptr() if vel is not None else 0),
+                                        ctypes.c_void_p(n_pairs.data_ptr()), ctypes.c_void_p(force.data_ptr()),
+                                        ctypes.c_void_p(torque.data_ptr()),
+                                        ctypes.c_void_p(pij.data_ptr() if pairs else 0),
+                                        ctypes.c_void_p(pout.data_ptr() if pairs else 0))
+        if rc != OK:
+            self._raise(rc, "contact_step_host")
+        out = dict(force=force, torque=torque, n_pairs=int(n_pairs.item()))
+        if pairs:
+            P = min(out["n_pairs"], self.max_pairs)
+            out.update(pair_ij=pij[:P], pair_out=pout[:P])
+        return out
 
     def step_async(self, pos, quat, vel=None):
         """Enqueue contact_step on the context stream (outputs in self.*)."""

@@ -32,6 +32,12 @@ struct contact_ctx {
   const void* gkey[9] = {};
   int last_replay = 0;   // 0 instantiated (or no graph), 1 replayed, 2 replayed after an in-place update
   cudaEvent_t ev_narrow[2] = {nullptr, nullptr};
+  // contact_step_host: device staging buffers and their own graph cache
+  double *hs_pos = nullptr, *hs_quat = nullptr, *hs_vel = nullptr, *hs_force = nullptr, *hs_torque = nullptr;
+  double* hs_pair_out = nullptr;
+  int32_t *hs_pair_ij = nullptr, *hs_npairs = nullptr;
+  cudaGraphExec_t hexec = nullptr;
+  const void* hkey[7] = {};
   // tape of the last step (for contact_backward)
   bool have_step = false;
   const double* last_vel = nullptr;
@@ -577,9 +583,107 @@ contact_status contact_backward(contact_ctx* c, const double* grad_force, const 
   return CONTACT_OK;
 }
 
+contact_status contact_step_host(contact_ctx* c, const double* pos, const double* quat, const double* vel,
+                                 int32_t* n_pairs, double* force, double* torque, int32_t* pair_ij,
+                                 double* pair_out) {
+  if (c == nullptr) return CONTACT_EINVAL;
+  if (pos == nullptr || quat == nullptr || n_pairs == nullptr || force == nullptr || torque == nullptr)
+    return fail(c, CONTACT_EINVAL, "contact_step_host: null buffer");
+  const contact_status sticky = check_sticky(c);
+  if (sticky != CONTACT_OK) return sticky;
+  const size_t n = static_cast<size_t>(c->P.n), mp = static_cast<size_t>(c->P.max_pairs);
+  cudaError_t e = cudaSuccess;
+  if (c->hs_pos == nullptr) {   // first call: the device side of the host buffers
+    if ((e = dev_alloc(c, &c->hs_pos, 3 * n)) != cudaSuccess || (e = dev_alloc(c, &c->hs_quat, 4 * n)) != cudaSuccess ||
+        (e = dev_alloc(c, &c->hs_vel, 6 * n)) != cudaSuccess || (e = dev_alloc(c, &c->hs_force, 3 * n)) != cudaSuccess ||
+        (e = dev_alloc(c, &c->hs_torque, 3 * n)) != cudaSuccess ||
+        (e = dev_alloc(c, &c->hs_pair_ij, 2 * mp)) != cudaSuccess ||
+        (e = dev_alloc(c, &c->hs_pair_out, 11 * mp)) != cudaSuccess ||
+        (e = dev_alloc(c, &c->hs_npairs, 1)) != cudaSuccess) {
+      c->hs_pos = nullptr;
+      return e == cudaErrorMemoryAllocation ? fail(c, CONTACT_ENOMEM, "contact_step_host: device buffers")
+                                            : cuda_fail(c, e, "cudaMalloc");
+    }
+  }
+  // page-locked host memory (all of it): copies inside the captured graph
+  auto pinned = [](const void* p) {
+    if (p == nullptr) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+  };
+  const bool all_pinned = pinned(pos) && pinned(quat) && pinned(vel) && pinned(n_pairs) && pinned(force) &&
+                          pinned(torque);
+  double* dvel = vel != nullptr ? c->hs_vel : nullptr;
+  auto enqueue_all = [&](bool capturing) {
+    cudaMemcpyAsync(c->hs_pos, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->hs_quat, quat, 4 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (vel != nullptr) cudaMemcpyAsync(c->hs_vel, vel, 6 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    enqueue_step(c, capturing, c->hs_pos, c->hs_quat, dvel, c->hs_pair_ij, c->hs_pair_out, c->hs_npairs,
+                 c->hs_force, c->hs_torque);
+    cudaMemcpyAsync(force, c->hs_force, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(torque, c->hs_torque, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(n_pairs, c->hs_npairs, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+  };
+  if (all_pinned && c->cfg.use_graph && c->stream != nullptr) {
+    const void* key[7] = {pos, quat, vel, n_pairs, force, torque, c->stream};
+    if (c->hexec == nullptr || std::memcmp(key, c->hkey, sizeof(key)) != 0) {
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
+      enqueue_all(true);
+      e = cudaStreamEndCapture(c->stream, &g);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+      bool updated = false;
+      if (c->hexec != nullptr && c->hkey[6] == c->stream) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(c->hexec, g, &info) == cudaSuccess;
+        if (!updated) cudaGetLastError();
+      }
+      if (!updated) {
+        if (c->hexec) cudaGraphExecDestroy(c->hexec);
+        c->hexec = nullptr;
+        e = cudaGraphInstantiate(&c->hexec, g, 0);
+        if (e != cudaSuccess) {
+          cudaGraphDestroy(g);
+          c->hexec = nullptr;
+          return cuda_fail(c, e, "cudaGraphInstantiate");
+        }
+      }
+      cudaGraphDestroy(g);
+      std::memcpy(c->hkey, key, sizeof(key));
+    }
+    e = cudaGraphLaunch(c->hexec, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+  } else {
+    enqueue_all(false);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "contact_step_host");
+  }
+  c->have_step = true;
+  c->last_vel = dvel;
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  const contact_status st = check_sticky(c);
+  if (st != CONTACT_OK) return st;
+  if (pair_ij != nullptr || pair_out != nullptr) {
+    const size_t P = static_cast<size_t>(std::min<int32_t>(std::max<int32_t>(*n_pairs, 0), c->P.max_pairs));
+    if (P > 0 && pair_ij != nullptr)
+      e = cudaMemcpy(pair_ij, c->hs_pair_ij, 2 * P * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && P > 0 && pair_out != nullptr)
+      e = cudaMemcpy(pair_out, c->hs_pair_out, 11 * P * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy");
+  }
+  return CONTACT_OK;
+}
+
 void contact_destroy(contact_ctx* c) {
   if (c == nullptr) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->hexec) cudaGraphExecDestroy(c->hexec);
   cudaDeviceSynchronize();
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   for (cudaEvent_t ev : c->ev_narrow)

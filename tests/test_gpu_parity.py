@@ -223,6 +223,29 @@ def test_graph_update_for_new_buffers():
     m.close()
 
 
+def test_step_host_buffers():
+    """contact_step_host: pinned CPU tensors (copies inside the graph) and
+    pageable numpy arrays both give the device-pointer step's results bit for
+    bit, pair outputs included; a backward after it uses its tape."""
+    st = W.mixed_grid_27()
+    m = model_for(st)
+    dev = m.step(torch.tensor(st.pos, device="cuda"), torch.tensor(st.quat, device="cuda"))
+    ref_f, ref_t = dev["force"].cpu(), dev["torque"].cpu()
+    ref_ij, ref_out, P = dev["pair_ij"].cpu(), dev["pair_out"].cpu(), dev["n_pairs"]
+    hp = torch.tensor(st.pos).pin_memory()
+    hq = torch.tensor(st.quat).pin_memory()
+    hf = torch.empty((st.n, 3), dtype=torch.float64).pin_memory()
+    ht = torch.empty((st.n, 3), dtype=torch.float64).pin_memory()
+    for _ in range(2):   # capture, then replay
+        out = m.step_host(hp, hq, force=hf, torque=ht, pairs=True)
+        assert out["n_pairs"] == P
+        assert torch.equal(out["force"], ref_f) and torch.equal(out["torque"], ref_t)
+        assert torch.equal(out["pair_ij"], ref_ij) and torch.equal(out["pair_out"], ref_out)
+    out = m.step_host(np.ascontiguousarray(st.pos), np.ascontiguousarray(st.quat))   # pageable
+    assert torch.equal(out["force"], ref_f) and torch.equal(out["torque"], ref_t)
+    m.close()
+
+
 def test_user_stream_capture():
     st = W.mixed_grid_27()
     m = model_for(st, use_graph=False)
