@@ -195,9 +195,18 @@ def cpu_baseline(st, pos, quat, budget_s):
         cells += r.cells
         secs += r.seconds
         steps += 1
+    # one thread, a shorter sample (about a quarter of the budget)
+    c1, s1, n1 = 0, 0.0, 0
+    t_end = time.perf_counter() + budget_s / 4
+    while n1 < 1 or (time.perf_counter() < t_end and n1 < len(pos)):
+        r = oracle.contact_step(st, pos=pos[n1 % len(pos)], quat=quat[n1 % len(quat)], n_threads=1)
+        c1 += r.cells
+        s1 += r.seconds
+        n1 += 1
     return {"value": cells / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{steps} full contact steps of the workload ({cells} node evaluations), "
-                      f"OpenMP over pairs", "ms_per_step": 1e3 * secs / steps}
+                      f"OpenMP over pairs", "ms_per_step": 1e3 * secs / steps,
+            "one_thread": {"value": c1 / s1, "ms_per_step": 1e3 * s1 / n1, "steps": n1}}
 
 
 def time_forward(model, pos_d, quat_d, steps, warmup, flush, narrow=False):
@@ -300,11 +309,12 @@ def run_ours(args, ws, rank, local):
                                            "tiles_per_step": stats["tiles"], "narrow_grid": stats["narrow_grid"]}),
             "roofline": roofline, "e2e": e2e, "gpu_launches": model.kernels_per_step() * args.steps,
             "clocks": clocks,
+            "ms_per_step_median": float(np.median(res["per"])),
             "ms_per_step_p10_p90": [float(np.percentile(res["per"], 10)), float(np.percentile(res["per"], 90))]}
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(st, pos, quat, args.cpu_seconds)
     if rank == 0 and not args.no_extras:
-        line["extras"] = extras(args, dev, flush)
+        line["extras"] = extras(args, dev, flush, peak)
     model.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -341,7 +351,27 @@ def end_to_end(model, pos, quat, steps, warmup, dev):
             "timing": "wall clock around contact_step_host (pinned host buffers, copies inside the call)"}
 
 
-def extras(args, dev, flush):
+def box_volume_percentiles(m, st, pos):
+    """Pair-box volumes (nodes) of the last step, from the GPU's node ranges and
+    pair list: the same box as the library's (partner image by the FP32
+    position difference against L/2)."""
+    import torch
+    m.step(torch.tensor(pos, device=m.device), torch.tensor(st.quat, device=m.device))
+    P = int(m.n_pairs.item())
+    ij = m.pair_ij[:P].cpu().numpy()
+    lohi = m.particle_boxes().cpu().numpy().astype(np.int64)
+    X = np.asarray(pos, dtype=np.float64).astype(np.float32)
+    d = X[ij[:, 1]] - X[ij[:, 0]]
+    h = (0.5 * np.asarray(st.n_cells, dtype=np.float64) * st.dx).astype(np.float32)
+    sft = (d > h).astype(np.int64) - (d < -h).astype(np.int64)
+    n = np.asarray(st.n_cells, dtype=np.int64)
+    lo = np.maximum(lohi[ij[:, 0], :3], lohi[ij[:, 1], :3] - sft * n)
+    hi = np.minimum(lohi[ij[:, 0], 3:], lohi[ij[:, 1], 3:] - sft * n)
+    vol = np.prod(np.maximum(hi - lo + 1, 0), axis=1)
+    return [float(v) for v in np.percentile(vol, [10, 50, 90, 99])] if P else []
+
+
+def extras(args, dev, flush, peak):
     """Secondary workloads, each timed like the headline (no CPU leg)."""
     import torch
     from paper_2401_10878_gb300 import workloads as W
@@ -359,6 +389,7 @@ def extras(args, dev, flush):
                             "narrow_ms": r["narrow_ms"] / steps, "pairs": s["pairs"],
                             "cells_per_step": r["cells"] / steps,
                             "nominal_Tops_per_s": r["ops"] / (r["narrow_ms"] * 1e-3) / 1e12}
+    out["mixed1934_223"]["box_volume_percentiles_10_50_90_99"] = box_volume_percentiles(m, st, st.pos)
     m.close()
     # all-FP64 one-pair-per-block form on the headline workload
     st = headline_state(0)
@@ -368,6 +399,24 @@ def extras(args, dev, flush):
     out["cubes1934_fp64_form"] = {"cell_evals_per_s": r["cells"] / (r["ms"] * 1e-3),
                                   "ms_per_step": r["ms"] / steps, "narrow_ms": r["narrow_ms"] / steps}
     m.close()
+    # 400 cubes at 10 %, and the resolution sweep (500 cubes at 20 %, edge 8..24), both forms
+    def both_forms(st, nsteps):
+        pos, quat = W.pose_sequence(st, nsteps + 3)
+        pd, qd = torch.tensor(pos, device=dev), torch.tensor(quat, device=dev)
+        res = {"L": int(st.n_cells[0])}
+        for name, prec in (("fp32_tile", 0), ("fp64_form", FP64_PAIR)):
+            m = Contact.from_state(st, precision=prec, narrow_events=True)
+            r = time_forward(m, pd, qd, nsteps, 3, flush, narrow=True)
+            s_ = m.stats()
+            res[name] = {"cell_evals_per_s": r["cells"] / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / nsteps,
+                         "narrow_ms": r["narrow_ms"] / nsteps}
+            if prec == 0:
+                res.update(pairs=s_["pairs"], cells_per_step=r["cells"] / nsteps)
+                res[name]["node_sweep_frac_of_fp32_peak"] = (r["ops"] / (r["narrow_ms"] * 1e-3)) / (peak * 1e12)
+            m.close()
+        return res
+    out["cubes400_190"] = both_forms(W.settling_cubes(), steps)
+    out["resolution_sweep"] = {f"edge{e}": both_forms(W.resolution_sweep(e), min(steps, 20)) for e in (8, 12, 16, 24)}
     # smoothed indicator: forward + adjoint
     st = W.settling_cubes_dense()
     pos, quat = W.pose_sequence(st, steps + 3)
