@@ -92,33 +92,87 @@ __global__ void k_pose(Params P, Shapes S, Parts D, Lists W, const double* __res
     // FP32 prefilter of the extreme vertices, FP64 only for those near the extremes
     const int v0 = S.vert_off[p], v1 = S.vert_off[p + 1];
     // (the FP32 projection errs by < 4e-7 * (|w0|+|w1|+|w2|); the window is 25x that)
+    // (vertices eight at a time: each batch's loads are in flight together)
     float lo32 = FLT_MAX, hi32 = -FLT_MAX, wmax = 0.f;
-    for (int v = v0; v < v1; ++v) {
-      const float* w = S.verts32 + 3 * v;
-      const float tv = fmaf(r32[0], w[0], fmaf(r32[1], w[1], r32[2] * w[2]));
-      lo32 = fminf(lo32, tv);
-      hi32 = fmaxf(hi32, tv);
-      wmax = fmaxf(wmax, fabsf(w[0]) + fabsf(w[1]) + fabsf(w[2]));
+    for (int vb = v0; vb < v1; vb += 8) {
+      float x[8][3];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float* w = S.verts32 + 3 * (vb + u < v1 ? vb + u : v0);
+        x[u][0] = w[0]; x[u][1] = w[1]; x[u][2] = w[2];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (vb + u < v1) {
+          const float tv = fmaf(r32[0], x[u][0], fmaf(r32[1], x[u][1], r32[2] * x[u][2]));
+          lo32 = fminf(lo32, tv);
+          hi32 = fmaxf(hi32, tv);
+          wmax = fmaxf(wmax, fabsf(x[u][0]) + fabsf(x[u][1]) + fabsf(x[u][2]));
+        }
+      }
     }
     const float tol = 1e-5f * wmax + 1e-30f;
-    double lo = DBL_MAX, hi = -DBL_MAX;
-    for (int v = v0; v < v1; ++v) {
-      const float* w32 = S.verts32 + 3 * v;
-      const float tv = fmaf(r32[0], w32[0], fmaf(r32[1], w32[1], r32[2] * w32[2]));
-      if (tv > lo32 + tol && tv < hi32 - tol) continue;
+    // vertices within tol of the FP32 extremes (at most two per side kept;
+    // more than two on a side -> every vertex in FP64 below)
+    int lc[2] = {v0, v0}, hc[2] = {v0, v0}, nlo = 0, nhi = 0;
+    for (int vb = v0; vb < v1; vb += 8) {
+      float x[8][3];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float* w = S.verts32 + 3 * (vb + u < v1 ? vb + u : v0);
+        x[u][0] = w[0]; x[u][1] = w[1]; x[u][2] = w[2];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (vb + u < v1) {
+          const float tv = fmaf(r32[0], x[u][0], fmaf(r32[1], x[u][1], r32[2] * x[u][2]));
+          if (tv <= lo32 + tol) {
+            if (nlo < 2) lc[nlo == 0 ? 0 : 1] = vb + u;
+            ++nlo;
+          }
+          if (tv >= hi32 - tol) {
+            if (nhi < 2) hc[nhi == 0 ? 0 : 1] = vb + u;
+            ++nhi;
+          }
+        }
+      }
+    }
+    // exact FP64 projections of the candidates (explicit rounding: compared bit for bit)
+    auto proj = [&](int v) {
       const double* w = S.verts + 3 * v;
-      const double tt = dadd(dadd(dmul(r[0], w[0]), dmul(r[1], w[1])), dmul(r[2], w[2]));
-      lo = fmin(lo, tt);
-      hi = fmax(hi, tt);
+      return dadd(dadd(dmul(r[0], w[0]), dmul(r[1], w[1])), dmul(r[2], w[2]));
+    };
+    double lo = proj(lc[0]), hi = proj(hc[0]);
+    if (nlo > 1) lo = fmin(lo, proj(lc[1]));
+    if (nhi > 1) hi = fmax(hi, proj(hc[1]));
+    if (nlo > 2 || nhi > 2) {   // rare: many vertices at the extremes
+      for (int v = v0; v < v1; ++v) {
+        const double tt = proj(v);
+        lo = fmin(lo, tt);
+        hi = fmax(hi, tt);
+      }
     }
     mn = dadd(Xk, lo);
     mx = dadd(Xk, hi);
     // world normals: component k of R n per face (FP64 product, one rounding to FP32)
     float* wp = reinterpret_cast<float*>(D.wplane);
-    for (int f = S.face_off[p]; f < S.face_off[p + 1]; ++f) {
-      const double* e = S.planes + 4 * f;
-      wp[4 * f + k] = static_cast<float>(fma(r[0], e[0], fma(r[1], e[1], r[2] * e[2])));
-      if (k == 0) wp[4 * f + 3] = S.off32[f];
+    const int f0 = S.face_off[p], f1 = S.face_off[p + 1];
+    for (int fb = f0; fb < f1; fb += 4) {   // four faces at a time
+      double2 e01[4], e2x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double2* e = reinterpret_cast<const double2*>(S.planes + 4 * (fb + u < f1 ? fb + u : f0));
+        e01[u] = e[0];
+        e2x[u] = e[1];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int f = fb + u;
+        if (f < f1) {
+          wp[4 * f + k] = static_cast<float>(fma(r[0], e01[u].x, fma(r[1], e01[u].y, r[2] * e2x[u].x)));
+          if (k == 0) wp[4 * f + 3] = S.off32[f];
+        }
+      }
     }
   }
   const double a = P.dx_pow2 ? dmul(mn, P.inv_dx) : __ddiv_rn(mn, P.dx);
