@@ -181,15 +181,17 @@ class Contact:
         CPU tensors (pin_memory) are copied inside one captured graph with the
         step.  With pairs=True the pair ids and outputs are copied too."""
         def host(t, shape):
-            t = torch.as_tensor(t, dtype=torch.float64)
-            if t.is_cuda or tuple(t.shape) != shape or not t.is_contiguous():
+            if not isinstance(t, torch.Tensor) or t.dtype != torch.float64:
+                t = torch.as_tensor(t, dtype=torch.float64)
+            if t.is_cuda or t.shape != shape or not t.is_contiguous():
                 raise ContactError(EINVAL, f"step_host: expected a contiguous CPU float64 array of shape {shape}")
             return t
-        pos = host(pos, (self.n, 3))
-        quat = host(quat, (self.n, 4))
-        vel = host(vel, (self.n, 6)) if vel is not None else None
-        force = torch.empty((self.n, 3), dtype=torch.float64) if force is None else host(force, (self.n, 3))
-        torque = torch.empty((self.n, 3), dtype=torch.float64) if torque is None else host(torque, (self.n, 3))
+        s3, s4, s6 = torch.Size((self.n, 3)), torch.Size((self.n, 4)), torch.Size((self.n, 6))
+        pos = host(pos, s3)
+        quat = host(quat, s4)
+        vel = host(vel, s6) if vel is not None else None
+        force = torch.empty(s3, dtype=torch.float64) if force is None else host(force, s3)
+        torque = torch.empty(s3, dtype=torch.float64) if torque is None else host(torque, s3)
         pin = force.is_pinned()
         if getattr(self, "_host_np", {}).get(pin) is None:   # reused across calls (a pinned allocation is slow)
             self._host_np = dict(getattr(self, "_host_np", {}))
