@@ -42,6 +42,11 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+class _Law(ctypes.Structure):
+    _fields_ = [("restitution", ctypes.c_double), ("mu_s", ctypes.c_double), ("mu_k", ctypes.c_double),
+                ("u_k", ctypes.c_double), ("history", ctypes.c_int32), ("friction", ctypes.c_int32)]
+
+
 class _Cfg(ctypes.Structure):
     _fields_ = [("n_cells", ctypes.c_int32 * 3), ("dx", ctypes.c_double), ("indicator", ctypes.c_int32),
                 ("smooth_width", ctypes.c_double), ("inflate", ctypes.c_double),
@@ -57,6 +62,9 @@ def _load():
         lib.oracle_contact_step.restype = ctypes.c_int64
         lib.oracle_contact_step.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 9 + \
             [ctypes.c_int64] + [P] * 7 + [ctypes.c_int32]
+        lib.oracle_contact_step_ext.restype = ctypes.c_int64
+        lib.oracle_contact_step_ext.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Law), ctypes.c_int32] + \
+            [P] * 9 + [ctypes.c_int64] + [P] * 5 + [ctypes.c_int64, P, P, ctypes.c_int64, P, P, P, ctypes.c_int32]
         lib.oracle_gradient.restype = ctypes.c_int64
         lib.oracle_gradient.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 13 + [ctypes.c_int32]
         lib.oracle_aabb.restype = ctypes.c_int32
@@ -155,6 +163,71 @@ def contact_step(st, pos=None, quat=None, vel=None, n_threads: int = 0, band_eps
             raise OracleError(-P)
         if P <= cap:
             return Result(ij[:P], sh[:P], bx[:P], out[:P], aux[:P], f, t, dt, threads)
+        cap = int(P)
+
+
+@dataclasses.dataclass
+class ContactLaw:
+    """The contact law's extensions: contact history (each contact keeps the
+    damping factor of Eq. (damping_factor) computed from its approach speed at
+    its first step, with coefficient of restitution `restitution`) and the
+    friction of Eq. (contact_force_tangential) with mu_s, mu_k and u_k."""
+    restitution: float = 1.0
+    mu_s: float = 0.0
+    mu_k: float = 0.0
+    u_k: float = 1.0
+    history: bool = False
+    friction: bool = False
+
+
+@dataclasses.dataclass
+class ExtResult:
+    pair_ij: np.ndarray
+    pair_out: np.ndarray
+    pair_c: np.ndarray
+    force: np.ndarray
+    torque: np.ndarray
+    hist_ij: np.ndarray     # this step's contacts (V > 0), sorted by (i, j)
+    hist_c: np.ndarray
+
+    @property
+    def n_pairs(self):
+        return len(self.pair_ij)
+
+
+def contact_step_ext(st, law: ContactLaw, pos=None, quat=None, vel=None, hist=None, n_threads: int = 0) -> ExtResult:
+    """The contact step with friction and the contact history; hist is the
+    previous step's (hist_ij, hist_c) or None (no ongoing contact)."""
+    lib = _load()
+    pos = _c(st.pos if pos is None else pos, np.float64)
+    quat = _c(st.quat if quat is None else quat, np.float64)
+    vel = None if vel is None else _c(vel, np.float64)
+    arrs = _shape_arrays(st)
+    cfg = _cfg(st, BAND_EPS)
+    lw = _Law(law.restitution, law.mu_s, law.mu_k, law.u_k, int(law.history), int(law.friction))
+    hij = np.zeros((0, 2), np.int32) if hist is None else _c(hist[0], np.int32)
+    hc = np.zeros(0) if hist is None else _c(hist[1], np.float64)
+    n = st.n
+    cap = max(16, 16 * n)
+    threads = n_threads if n_threads > 0 else lib.oracle_max_threads()
+    while True:
+        ij = np.zeros((cap, 2), np.int32)
+        out = np.zeros((cap, 11))
+        pc = np.zeros(cap)
+        f = np.zeros((n, 3))
+        t = np.zeros((n, 3))
+        hij_o = np.zeros((cap, 2), np.int32)
+        hc_o = np.zeros(cap)
+        nh = ctypes.c_int64(0)
+        P = lib.oracle_contact_step_ext(ctypes.byref(cfg), ctypes.byref(lw), n, *[_ptr(a) for a in arrs],
+                                        _ptr(pos), _ptr(quat), _ptr(vel), cap, _ptr(ij), _ptr(out), _ptr(pc),
+                                        _ptr(f), _ptr(t), len(hc), _ptr(hij), _ptr(hc), cap, _ptr(hij_o),
+                                        _ptr(hc_o), ctypes.byref(nh), threads)
+        if P < 0:
+            raise OracleError(-P)
+        if P <= cap:
+            H = nh.value
+            return ExtResult(ij[:P], out[:P], pc[:P], f, t, hij_o[:H], hc_o[:H])
         cap = int(P)
 
 

@@ -290,6 +290,26 @@ struct PairResult {
   double G[3];
   double box_cells, n_band, n_gtie, d_gap, estar;
   double v_sens, m_sens, g_sens;  // first-order change of V, M, G for a perturbation eps of every phi
+  double c_used;                  // damping factor the force law used
+};
+
+// Eq. (damping_factor): c from the coefficient of restitution e and the
+// relative speed u0 at the initial contact (0 for u0 <= 0).
+inline double damping_factor(double e, double u0) {
+  if (!(u0 > 0.0)) return 0.0;
+  return 1.5 * (1.0 - e) * (11.0 - e) / ((1.0 + 9.0 * e) * u0);
+}
+
+// The contact law of one pair: its damping factor c (of an ongoing contact,
+// or the shared one), or, for a contact that begins at this step with the
+// contact history on, c from this step's approach speed u0 = ddot_n
+// (Eq. damping_factor); and the friction law of Eq. (contact_force_tangential).
+struct ContactLaw {
+  double c = 0.0;
+  bool new_contact = false;
+  double restitution = 1.0;
+  bool friction = false;
+  double mu_s = 0.0, mu_k = 0.0, u_k = 1.0;
 };
 
 // Sweep of every lattice node of the pair box (Sec. 3.3.1) and the force law
@@ -298,7 +318,7 @@ struct PairResult {
 template <class S>
 PairResult<S> eval_pair(const Config& cfg, const Shape& A, const Shape& B, const PairGeom& pg,
                         const S XA[3], const S qA[4], const S XB[3], const S qB[4], const double* velA,
-                        const double* velB, double estar) {
+                        const double* velB, double estar, const ContactLaw& law) {
   const double dx = cfg.dx;
   const bool smooth = cfg.indicator == 1;
   const double wdx = cfg.smooth_width * dx;
@@ -409,9 +429,12 @@ PairResult<S> eval_pair(const Config& cfg, const Shape& A, const Shape& B, const
   }
   S d = (top1 > 0.0) ? dbest : S(0.0);
   res.d = d;
-  // relative normal velocity at the contact point (positive when approaching)
-  S damp(1.0);
-  if (velA != nullptr && velB != nullptr && cfg.damping_c != 0.0) {
+  // velocity of A relative to B at the contact point; its normal part ddot_n
+  // is positive when approaching (n points from A to B)
+  const bool have_vel = velA != nullptr && velB != nullptr;
+  S uab[3] = {S(0.0), S(0.0), S(0.0)};
+  S ddot(0.0);
+  if (have_vel) {
     S ra[3] = {res.xc[0] - XA[0], res.xc[1] - XA[1], res.xc[2] - XA[2]};
     S rb[3] = {res.xc[0] - XB[0], res.xc[1] - XB[1], res.xc[2] - XB[2]};
     const double* wa = velA + 3;
@@ -420,14 +443,36 @@ PairResult<S> eval_pair(const Config& cfg, const Shape& A, const Shape& B, const
                velA[2] + (wa[0] * ra[1] - wa[1] * ra[0])};
     S ub[3] = {velB[0] + (wb[1] * rb[2] - wb[2] * rb[1]), velB[1] + (wb[2] * rb[0] - wb[0] * rb[2]),
                velB[2] + (wb[0] * rb[1] - wb[1] * rb[0])};
-    S ddot = (ua[0] - ub[0]) * res.n[0] + (ua[1] - ub[1]) * res.n[1] + (ua[2] - ub[2]) * res.n[2];
-    damp = 1.0 + cfg.damping_c * ddot;
+    for (int k = 0; k < 3; ++k) uab[k] = ua[k] - ub[k];
+    ddot = uab[0] * res.n[0] + uab[1] * res.n[1] + uab[2] * res.n[2];
+  }
+  // damping factor: the contact's own, or from u0 = ddot_n at the start of the contact
+  const double c = law.new_contact ? damping_factor(law.restitution, have_vel ? val(ddot) : 0.0) : law.c;
+  res.c_used = c;
+  S damp(1.0);
+  if (have_vel && c != 0.0) {
+    damp = 1.0 + c * ddot;
     if (val(damp) < 0.0) damp = S(0.0);
   }
   S vd = V * d;
   S fmag(0.0);
   if (val(vd) > 0.0) fmag = (4.0 / (3.0 * M_PI)) * estar * sqrt_s(vd) * damp;
   for (int k = 0; k < 3; ++k) res.F[k] = fmag * res.n[k];
+  // friction, Eq. (contact_force_tangential): the force on A opposes A's
+  // tangential velocity relative to B, so B receives +coef |F_n| t
+  if (law.friction && have_vel && val(fmag) > 0.0) {
+    S ut[3];
+    for (int k = 0; k < 3; ++k) ut[k] = uab[k] - ddot * res.n[k];
+    const S utn = sqrt_s(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
+    if (val(utn) > 0.0) {
+      const S a = utn / law.u_k;
+      const double ratio = law.mu_k / law.mu_s;
+      const double mus_star = law.mu_s * (1.0 - 0.09 * ratio * ratio * ratio * ratio);
+      const S a2 = a * a;
+      const S coef = (2.0 * mus_star - law.mu_k) * a2 / (a2 * a2 + 1.0) + law.mu_k - law.mu_k / (a2 + 1.0);
+      for (int k = 0; k < 3; ++k) res.F[k] = res.F[k] + coef * fmag * ut[k] / utn;
+    }
+  }
   // F acts on B, -F on A; torques about each particle's centre of mass (Sec. 2.2)
   S ra[3] = {res.xc[0] - XA[0], res.xc[1] - XA[1], res.xc[2] - XA[2]};
   S rb[3] = {res.xc[0] - XB[0], res.xc[1] - XB[1], res.xc[2] - XB[2]};
@@ -691,8 +736,10 @@ int64_t oracle_contact_step(const oracle_config* cfg, int32_t n, const int32_t* 
     double XB[3];
     image_pos(pb, g, pos, XB);
     const double es = effective_modulus(pb.young[g.i], pb.poisson[g.i], pb.young[g.j], pb.poisson[g.j]);
+    ContactLaw law;
+    law.c = pb.cfg.damping_c;
     res[p] = eval_pair<double>(pb.cfg, pb.shapes[g.i], pb.shapes[g.j], g, pos + 3 * g.i, quat + 4 * g.i, XB,
-                               quat + 4 * g.j, vel ? vel + 6 * g.i : nullptr, vel ? vel + 6 * g.j : nullptr, es);
+                               quat + 4 * g.j, vel ? vel + 6 * g.i : nullptr, vel ? vel + 6 * g.j : nullptr, es, law);
   }
   if (force) std::memset(force, 0, sizeof(double) * 3 * n);
   if (torque) std::memset(torque, 0, sizeof(double) * 3 * n);
@@ -728,6 +775,103 @@ int64_t oracle_contact_step(const oracle_config* cfg, int32_t n, const int32_t* 
   return P;
 }
 
+typedef struct {
+  double restitution;   // e of Eq. (damping_factor) (contact history)
+  double mu_s, mu_k;    // coefficients of static and kinetic friction
+  double u_k;           // transition speed of Eq. (contact_force_tangential)
+  int32_t history;      // 1: every contact keeps the c of its first step
+  int32_t friction;     // 1: tangential force of Eq. (contact_force_tangential)
+} oracle_contact_law;
+
+// The contact step with the contact law's extensions: friction, and the
+// contact history of Sec. 4.3.3 (a contact keeps the damping factor computed
+// from its approach speed at the first step with V > 0; it ends with the
+// first step without overlap).  hist_ij [n_hist,2] / hist_c [n_hist] are the
+// contacts of the previous step sorted by (i, j); the contacts of this step
+// (pairs with V > 0, in pair order) go to hist_ij_out / hist_c_out (up to
+// max_hist rows; *n_hist_out receives their count).  pair_c [P] (nullable)
+// receives the damping factor each pair used.  Other arguments and the
+// return value as oracle_contact_step.
+int64_t oracle_contact_step_ext(const oracle_config* cfg, const oracle_contact_law* law_in, int32_t n,
+                                const int32_t* shape_type, const double* shape_param, const int32_t* face_offset,
+                                const double* planes, const double* young, const double* poisson,
+                                const double* pos, const double* quat, const double* vel, int64_t max_pairs,
+                                int32_t* pair_ij, double* pair_out, double* pair_c, double* force, double* torque,
+                                int64_t n_hist, const int32_t* hist_ij, const double* hist_c, int64_t max_hist,
+                                int32_t* hist_ij_out, double* hist_c_out, int64_t* n_hist_out, int32_t n_threads) {
+  Problem pb;
+  const int st = build_problem(pb, reinterpret_cast<const Config*>(cfg), n, shape_type, shape_param,
+                               face_offset, planes, young, poisson, pos, quat);
+  if (st != OR_OK) return -st;
+  if (law_in->friction && (!(law_in->mu_s > 0.0) || !(law_in->mu_k >= 0.0) || !(law_in->u_k > 0.0)))
+    return -OR_EINVAL;
+  const int64_t P = static_cast<int64_t>(pb.pairs.size());
+  std::vector<PairResult<double>> res(P);
+  set_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t p = 0; p < P; ++p) {
+    const PairGeom& g = pb.pairs[p];
+    double XB[3];
+    image_pos(pb, g, pos, XB);
+    const double es = effective_modulus(pb.young[g.i], pb.poisson[g.i], pb.young[g.j], pb.poisson[g.j]);
+    ContactLaw law;
+    law.c = pb.cfg.damping_c;
+    law.restitution = law_in->restitution;
+    law.friction = law_in->friction != 0;
+    law.mu_s = law_in->mu_s;
+    law.mu_k = law_in->mu_k;
+    law.u_k = law_in->u_k;
+    if (law_in->history) {   // an ongoing contact keeps its c; a new one takes c from u0
+      int64_t a = 0, b = n_hist;
+      while (a < b) {
+        const int64_t m = (a + b) / 2;
+        const bool less = hist_ij[2 * m] < g.i || (hist_ij[2 * m] == g.i && hist_ij[2 * m + 1] < g.j);
+        if (less) a = m + 1; else b = m;
+      }
+      if (a < n_hist && hist_ij[2 * a] == g.i && hist_ij[2 * a + 1] == g.j) {
+        law.c = hist_c[a];
+      } else {
+        law.new_contact = true;
+      }
+    }
+    res[p] = eval_pair<double>(pb.cfg, pb.shapes[g.i], pb.shapes[g.j], g, pos + 3 * g.i, quat + 4 * g.i, XB,
+                               quat + 4 * g.j, vel ? vel + 6 * g.i : nullptr, vel ? vel + 6 * g.j : nullptr, es, law);
+  }
+  if (force) std::memset(force, 0, sizeof(double) * 3 * n);
+  if (torque) std::memset(torque, 0, sizeof(double) * 3 * n);
+  int64_t nh = 0;
+  for (int64_t p = 0; p < P; ++p) {
+    const PairGeom& g = pb.pairs[p];
+    const PairResult<double>& r = res[p];
+    if (force && torque)
+      for (int k = 0; k < 3; ++k) {
+        force[3 * g.i + k] -= r.F[k];
+        torque[3 * g.i + k] += r.TA[k];
+        force[3 * g.j + k] += r.F[k];
+        torque[3 * g.j + k] += r.TB[k];
+      }
+    if (r.V > 0.0) {
+      if (nh < max_hist) {
+        hist_ij_out[2 * nh] = g.i;
+        hist_ij_out[2 * nh + 1] = g.j;
+        hist_c_out[nh] = r.c_used;
+      }
+      ++nh;
+    }
+    if (p >= max_pairs) continue;
+    if (pair_ij) { pair_ij[2 * p] = g.i; pair_ij[2 * p + 1] = g.j; }
+    if (pair_out) {
+      double* o = pair_out + 11 * p;
+      o[0] = r.V;
+      for (int k = 0; k < 3; ++k) { o[1 + k] = r.xc[k]; o[4 + k] = r.n[k]; o[8 + k] = r.F[k]; }
+      o[7] = r.d;
+    }
+    if (pair_c) pair_c[p] = r.V > 0.0 ? r.c_used : 0.0;
+  }
+  *n_hist_out = nh;
+  return P;
+}
+
 // Gradient of L = sum_p (grad_force_p . F_p + grad_torque_p . T_p) with
 // respect to positions [n,3] and raw (unnormalised) quaternions [n,4], by
 // forward-mode dual numbers through the same per-pair code as above.
@@ -754,8 +898,10 @@ int64_t oracle_gradient(const oracle_config* cfg, int32_t n, const int32_t* shap
     for (int k = 0; k < 3; ++k) { XB[k] = Dual(XBd[k]); XB[k].g[7 + k] = 1.0; }
     for (int k = 0; k < 4; ++k) { qB[k] = Dual(quat[4 * g.j + k]); qB[k].g[10 + k] = 1.0; }
     const double es = effective_modulus(pb.young[g.i], pb.poisson[g.i], pb.young[g.j], pb.poisson[g.j]);
+    ContactLaw law;
+    law.c = pb.cfg.damping_c;
     PairResult<Dual> r = eval_pair<Dual>(pb.cfg, pb.shapes[g.i], pb.shapes[g.j], g, XA, qA, XB, qB,
-                                         vel ? vel + 6 * g.i : nullptr, vel ? vel + 6 * g.j : nullptr, es);
+                                         vel ? vel + 6 * g.i : nullptr, vel ? vel + 6 * g.j : nullptr, es, law);
     Dual L(0.0);
     for (int k = 0; k < 3; ++k) {
       L = L + grad_force[3 * g.i + k] * (-r.F[k]) + grad_torque[3 * g.i + k] * r.TA[k];
