@@ -65,6 +65,9 @@ def _load():
         lib.oracle_contact_step_ext.restype = ctypes.c_int64
         lib.oracle_contact_step_ext.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Law), ctypes.c_int32] + \
             [P] * 9 + [ctypes.c_int64] + [P] * 5 + [ctypes.c_int64, P, P, ctypes.c_int64, P, P, P, ctypes.c_int32]
+        lib.oracle_gradient_ext.restype = ctypes.c_int64
+        lib.oracle_gradient_ext.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Law), ctypes.c_int32] + \
+            [P] * 9 + [ctypes.c_int64] + [P] * 6 + [ctypes.c_int32]
         lib.oracle_gradient.restype = ctypes.c_int64
         lib.oracle_gradient.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 13 + [ctypes.c_int32]
         lib.oracle_aabb.restype = ctypes.c_int32
@@ -244,6 +247,30 @@ def gradient(st, grad_force, grad_torque, pos=None, quat=None, vel=None, n_threa
     P = lib.oracle_gradient(ctypes.byref(_cfg(st)), st.n, *[_ptr(a) for a in arrs], _ptr(pos), _ptr(quat),
                             _ptr(vel), _ptr(_c(grad_force, np.float64)), _ptr(_c(grad_torque, np.float64)),
                             _ptr(gp), _ptr(gq), threads)
+    if P < 0:
+        raise OracleError(-P)
+    return gp, gq
+
+
+def gradient_ext(st, law: ContactLaw, grad_force, grad_torque, pos=None, quat=None, vel=None, table=None,
+                 n_threads: int = 0):
+    """Oracle gradient with friction and, with the history on, each contact's
+    damping factor from table = (ij [H,2] sorted, c [H]) held fixed."""
+    lib = _load()
+    pos = _c(st.pos if pos is None else pos, np.float64)
+    quat = _c(st.quat if quat is None else quat, np.float64)
+    vel = None if vel is None else _c(vel, np.float64)
+    arrs = _shape_arrays(st)
+    lw = _Law(law.restitution, law.mu_s, law.mu_k, law.u_k, int(law.history), int(law.friction))
+    hij = np.zeros((0, 2), np.int32) if table is None else _c(table[0], np.int32)
+    hc = np.zeros(0) if table is None else _c(table[1], np.float64)
+    gp = np.zeros((st.n, 3))
+    gq = np.zeros((st.n, 4))
+    threads = n_threads if n_threads > 0 else lib.oracle_max_threads()
+    P = lib.oracle_gradient_ext(ctypes.byref(_cfg(st)), ctypes.byref(lw), st.n, *[_ptr(a) for a in arrs], _ptr(pos),
+                                _ptr(quat), _ptr(vel), len(hc), _ptr(hij), _ptr(hc),
+                                _ptr(_c(grad_force, np.float64)), _ptr(_c(grad_torque, np.float64)), _ptr(gp),
+                                _ptr(gq), threads)
     if P < 0:
         raise OracleError(-P)
     return gp, gq

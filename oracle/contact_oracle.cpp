@@ -783,6 +783,17 @@ typedef struct {
   int32_t friction;     // 1: tangential force of Eq. (contact_force_tangential)
 } oracle_contact_law;
 
+// Row of contact (i, j) in a history table sorted by (i, j), or -1.
+static int64_t hist_find(int64_t n_hist, const int32_t* hist_ij, int i, int j) {
+  int64_t a = 0, b = n_hist;
+  while (a < b) {
+    const int64_t m = (a + b) / 2;
+    const bool less = hist_ij[2 * m] < i || (hist_ij[2 * m] == i && hist_ij[2 * m + 1] < j);
+    if (less) a = m + 1; else b = m;
+  }
+  return (a < n_hist && hist_ij[2 * a] == i && hist_ij[2 * a + 1] == j) ? a : -1;
+}
+
 // The contact step with the contact law's extensions: friction, and the
 // contact history of Sec. 4.3.3 (a contact keeps the damping factor computed
 // from its approach speed at the first step with V > 0; it ends with the
@@ -822,14 +833,9 @@ int64_t oracle_contact_step_ext(const oracle_config* cfg, const oracle_contact_l
     law.mu_k = law_in->mu_k;
     law.u_k = law_in->u_k;
     if (law_in->history) {   // an ongoing contact keeps its c; a new one takes c from u0
-      int64_t a = 0, b = n_hist;
-      while (a < b) {
-        const int64_t m = (a + b) / 2;
-        const bool less = hist_ij[2 * m] < g.i || (hist_ij[2 * m] == g.i && hist_ij[2 * m + 1] < g.j);
-        if (less) a = m + 1; else b = m;
-      }
-      if (a < n_hist && hist_ij[2 * a] == g.i && hist_ij[2 * a + 1] == g.j) {
-        law.c = hist_c[a];
+      const int64_t row = hist_find(n_hist, hist_ij, g.i, g.j);
+      if (row >= 0) {
+        law.c = hist_c[row];
       } else {
         law.new_contact = true;
       }
@@ -872,14 +878,20 @@ int64_t oracle_contact_step_ext(const oracle_config* cfg, const oracle_contact_l
   return P;
 }
 
+}  // extern "C"
+
 // Gradient of L = sum_p (grad_force_p . F_p + grad_torque_p . T_p) with
 // respect to positions [n,3] and raw (unnormalised) quaternions [n,4], by
-// forward-mode dual numbers through the same per-pair code as above.
-int64_t oracle_gradient(const oracle_config* cfg, int32_t n, const int32_t* shape_type, const double* shape_param,
-                        const int32_t* face_offset, const double* planes, const double* young,
-                        const double* poisson, const double* pos, const double* quat, const double* vel,
-                        const double* grad_force, const double* grad_torque, double* grad_pos,
-                        double* grad_quat, int32_t n_threads) {
+// forward-mode dual numbers through the same per-pair code as above.  With a
+// contact law (nullable), each contact's damping factor c is looked up in the
+// table (hist_ij, hist_c) and held fixed: c is a constant of the contact
+// (Eq. damping_factor, Sec. 4.3.3); pairs missing from it take c = 0.
+static int64_t gradient_impl(const oracle_config* cfg, const oracle_contact_law* law_in, int32_t n,
+                             const int32_t* shape_type, const double* shape_param, const int32_t* face_offset,
+                             const double* planes, const double* young, const double* poisson,
+                             const double* pos, const double* quat, const double* vel, int64_t n_hist,
+                             const int32_t* hist_ij, const double* hist_c, const double* grad_force,
+                             const double* grad_torque, double* grad_pos, double* grad_quat, int32_t n_threads) {
   Problem pb;
   const int st = build_problem(pb, reinterpret_cast<const Config*>(cfg), n, shape_type, shape_param,
                                face_offset, planes, young, poisson, pos, quat);
@@ -900,6 +912,16 @@ int64_t oracle_gradient(const oracle_config* cfg, int32_t n, const int32_t* shap
     const double es = effective_modulus(pb.young[g.i], pb.poisson[g.i], pb.young[g.j], pb.poisson[g.j]);
     ContactLaw law;
     law.c = pb.cfg.damping_c;
+    if (law_in != nullptr) {
+      law.friction = law_in->friction != 0;
+      law.mu_s = law_in->mu_s;
+      law.mu_k = law_in->mu_k;
+      law.u_k = law_in->u_k;
+      if (law_in->history) {
+        const int64_t row = hist_find(n_hist, hist_ij, g.i, g.j);
+        law.c = row >= 0 ? hist_c[row] : 0.0;
+      }
+    }
     PairResult<Dual> r = eval_pair<Dual>(pb.cfg, pb.shapes[g.i], pb.shapes[g.j], g, XA, qA, XB, qB,
                                          vel ? vel + 6 * g.i : nullptr, vel ? vel + 6 * g.j : nullptr, es, law);
     Dual L(0.0);
@@ -920,6 +942,32 @@ int64_t oracle_gradient(const oracle_config* cfg, int32_t n, const int32_t* shap
     for (int k = 0; k < 4; ++k) grad_quat[4 * g.j + k] += t[10 + k];
   }
   return P;
+}
+
+extern "C" {
+
+int64_t oracle_gradient(const oracle_config* cfg, int32_t n, const int32_t* shape_type, const double* shape_param,
+                        const int32_t* face_offset, const double* planes, const double* young,
+                        const double* poisson, const double* pos, const double* quat, const double* vel,
+                        const double* grad_force, const double* grad_torque, double* grad_pos,
+                        double* grad_quat, int32_t n_threads) {
+  return gradient_impl(cfg, nullptr, n, shape_type, shape_param, face_offset, planes, young, poisson, pos, quat,
+                       vel, 0, nullptr, nullptr, grad_force, grad_torque, grad_pos, grad_quat, n_threads);
+}
+
+// The gradient with the contact law's extensions: friction, and the damping
+// factor of each contact from the table (hist_ij [n_hist,2] sorted by (i, j),
+// hist_c [n_hist]: the c every contact of the step used), held fixed.
+int64_t oracle_gradient_ext(const oracle_config* cfg, const oracle_contact_law* law, int32_t n,
+                            const int32_t* shape_type, const double* shape_param, const int32_t* face_offset,
+                            const double* planes, const double* young, const double* poisson, const double* pos,
+                            const double* quat, const double* vel, int64_t n_hist, const int32_t* hist_ij,
+                            const double* hist_c, const double* grad_force, const double* grad_torque,
+                            double* grad_pos, double* grad_quat, int32_t n_threads) {
+  if (law == nullptr) return -OR_EINVAL;
+  if (law->friction && (!(law->mu_s > 0.0) || !(law->mu_k >= 0.0) || !(law->u_k > 0.0))) return -OR_EINVAL;
+  return gradient_impl(cfg, law, n, shape_type, shape_param, face_offset, planes, young, poisson, pos, quat, vel,
+                       n_hist, hist_ij, hist_c, grad_force, grad_torque, grad_pos, grad_quat, n_threads);
 }
 
 }  // extern "C"

@@ -159,3 +159,59 @@ def test_history_contact_starting_apart_keeps_no_damping():
     assert ratio0 == 1.0 and h[1][0] == 0.0
     ratio1, h = _ratio(law, vel(uA=(0.4, 0, 0)), hist=h)
     assert ratio1 == 1.0 and h[1][0] == 0.0
+
+
+def test_gradient_ext_without_extensions_is_the_base_gradient():
+    from paper_2401_10878_gb300 import workloads as W
+    st = W.mixed_grid_27()
+    st.indicator, st.smooth_width = 1, 1.0
+    gf, gt = W.loss_weights(st.n)
+    a = oracle.gradient(st, gf, gt)
+    b = oracle.gradient_ext(st, oracle.ContactLaw(), gf, gt)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_gradient_ext_friction_and_fixed_c_match_central_differences():
+    """Friction and each contact's c held fixed (every contact found in the
+    table): the forward-mode gradient equals central differences of the
+    oracle's forward map with that table as the previous step's contacts."""
+    from paper_2401_10878_gb300 import workloads as W
+    st = W.mixed_grid_27()
+    st.indicator, st.smooth_width = 1, 1.0
+    rng = np.random.default_rng(21)
+    v = np.concatenate([rng.normal(size=(st.n, 3)) * 0.05, rng.normal(size=(st.n, 3)) * 0.01], axis=1)
+    law = oracle.ContactLaw(restitution=0.5, history=True, friction=True, mu_s=0.5, mu_k=0.3, u_k=0.05)
+    r0 = oracle.contact_step_ext(st, law, vel=v)
+    table = (r0.hist_ij, r0.hist_c)
+    assert len(table[1]) > 20 and np.count_nonzero(table[1]) > 5
+    gf, gt = W.loss_weights(st.n)
+    gp, gq = oracle.gradient_ext(st, law, gf, gt, vel=v, table=table)
+
+    def loss(pos, quat):
+        r = oracle.contact_step_ext(st, law, pos=pos, quat=quat, vel=v, hist=table)
+        return float(np.sum(gf * r.force) + np.sum(gt * r.torque))
+
+    h = 1e-4
+    fp = np.zeros_like(gp)
+    fq = np.zeros_like(gq)
+    for p in range(st.n):
+        for k in range(3):
+            a, b = st.pos.copy(), st.pos.copy()
+            a[p, k] += h
+            b[p, k] -= h
+            fp[p, k] = (loss(a, st.quat) - loss(b, st.quat)) / (2 * h)
+        for k in range(4):
+            a, b = st.quat.copy(), st.quat.copy()
+            a[p, k] += h
+            b[p, k] -= h
+            fq[p, k] = (loss(st.pos, a) - loss(st.pos, b)) / (2 * h)
+    g = np.concatenate([gp.ravel(), gq.ravel()])
+    f = np.concatenate([fp.ravel(), fq.ravel()])
+    scale = np.abs(g).max()
+    assert scale > 0
+    err = np.abs(g - f) / scale
+    assert np.mean(err < 1e-4) >= 0.98, np.sort(err)[-10:]
+    assert np.median(err) < 1e-6
+    # friction changes the gradient (the test is not blind to it)
+    g0 = oracle.gradient_ext(st, oracle.ContactLaw(restitution=0.5, history=True), gf, gt, vel=v, table=table)
+    assert np.abs(g0[0] - gp).max() > 1e-3 * scale
