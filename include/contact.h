@@ -95,9 +95,27 @@ typedef struct {
   int32_t narrow_events;    /* 1: record CUDA events around the node-sweep launch
                                (read with contact_narrow_time); 0: none, so that
                                consecutive kernels overlap their launch           */
+  int32_t history;          /* 1: contact history (Sec. 4.3.3): a contact (a pair
+                               with V > 0) keeps the damping factor of Eq.
+                               (damping_factor) computed with `restitution` from
+                               its approach speed ddot_n at its first step (u0 <= 0
+                               gives 0) until the first step without overlap;
+                               damping_c is then unused.  Needs velocities.        */
+  int32_t friction;         /* 1: tangential force of Eq. (contact_force_tangential)
+                               added to F: B receives +f(a) |F_n| t, A the
+                               opposite, t the direction of A's velocity relative to
+                               B at x_c minus its normal part, a = |u_t| / u_k,
+                               f(a) = (2 mu_s* - mu_k) a^2/(a^4+1) + mu_k -
+                               mu_k/(a^2+1), mu_s* = mu_s (1 - 0.09 (mu_k/mu_s)^4).
+                               Needs velocities.                                  */
+  double restitution;       /* coefficient of restitution e in [0, 1] (history)   */
+  double mu_s, mu_k;        /* friction coefficients (mu_s > 0, mu_k >= 0)        */
+  double u_k;               /* transition speed of the friction law (> 0), in the
+                               caller's velocity units (the paper: 0.001 m/s)     */
 } contact_config;
 
 /* Fills *cfg with defaults (sharp indicator, w = 1, no inflation, FP32 tiles,
+ * no contact history (restitution 1), no friction (mu_s = mu_k = 0, u_k = 1),
  * max_pairs = 16 n, graphs on) for n particles in an n_cells lattice of
  * spacing dx. */
 void contact_config_default(contact_config* cfg, int32_t n_particles, const int32_t n_cells[3], double dx);
@@ -160,7 +178,10 @@ contact_status contact_step_host(contact_ctx* ctx, const double* pos, const doub
  * of the last contact_step with respect to its positions and raw quaternions
  * (the quaternion gradient is orthogonal to the quaternion).  Needs the
  * smoothed indicator (CONTACT_ESTATE otherwise) and uses the step's tape, so
- * the step's pos/quat/vel must still hold the same values.
+ * the step's pos/quat/vel must still hold the same values (the buffers are
+ * read again).  Covers damping and friction; each contact's damping factor c
+ * (the shared one, or with the contact history the contact's own) is held
+ * fixed, a constant of the contact.
  *   grad_force, grad_torque [N,3] dev f64 ; grad_pos [N,3], grad_quat [N,4] dev f64 */
 contact_status contact_backward(contact_ctx* ctx, const double* grad_force, const double* grad_torque,
                                 double* grad_pos, double* grad_quat);
@@ -196,6 +217,22 @@ contact_status contact_narrow_time(contact_ctx* ctx, float* ms);
 
 /* Per-particle node ranges (lo[3], hi[3]) [N,6] i32 dev of the last step. */
 contact_status contact_particle_boxes(contact_ctx* ctx, int32_t* lo_hi);
+
+/* Contact history (cfg.history = 1; Sec. 4.3.3): the contacts of the last
+ * completed step (pairs (i, j), i < j, with V > 0) and the damping factor c
+ * each keeps; the next step reads them.  All three return CONTACT_ESTATE
+ * with the history off.
+ * contact_history_get synchronises, then writes the first min(*n, max_rows)
+ * contacts, sorted by (i, j), to ij [max_rows,2] i32 host and c [max_rows]
+ * f64 host; *n receives the number of contacts (which may exceed max_rows).
+ * contact_history_set replaces them with the n_rows given (host arrays, as
+ * a checkpoint to resume from): CONTACT_EINVAL for a row with i >= j, an
+ * index outside [0, N), a repeated (i, j), or more than max_neighbors rows
+ * of one i.  contact_history_reset forgets every contact (asynchronous, on
+ * the context stream). */
+contact_status contact_history_get(contact_ctx* ctx, int64_t max_rows, int32_t* ij, double* c, int64_t* n);
+contact_status contact_history_set(contact_ctx* ctx, int64_t n_rows, const int32_t* ij, const double* c);
+contact_status contact_history_reset(contact_ctx* ctx);
 
 /* Eq. (damping_factor): c = 1.5 (1-e)(11-e) / ((1+9e) u0) for u0 > 0, else 0,
  * from the coefficient of restitution e and the relative speed u0 at first

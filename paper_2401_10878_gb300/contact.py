@@ -30,7 +30,8 @@ PAIR_OUT_COLS = 11
 EXPORTS = ["contact_config_default", "contact_init", "contact_step", "contact_backward", "contact_check",
            "contact_clear_error", "contact_last_error", "contact_set_stream", "contact_stats",
            "contact_particle_boxes", "contact_narrow_time", "contact_damping_factor", "contact_kernels_per_step",
-           "contact_kernels_per_backward", "contact_destroy", "contact_step_noalloc", "contact_step_host"]
+           "contact_kernels_per_backward", "contact_destroy", "contact_step_noalloc", "contact_step_host",
+           "contact_history_get", "contact_history_set", "contact_history_reset"]
 
 
 class Config(ctypes.Structure):
@@ -39,7 +40,9 @@ class Config(ctypes.Structure):
                 ("inflate", ctypes.c_double), ("damping_c", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("max_pairs", ctypes.c_int32), ("max_neighbors", ctypes.c_int32),
                 ("max_tiles", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("narrow_events", ctypes.c_int32)]
+                ("narrow_events", ctypes.c_int32), ("history", ctypes.c_int32), ("friction", ctypes.c_int32),
+                ("restitution", ctypes.c_double), ("mu_s", ctypes.c_double), ("mu_k", ctypes.c_double),
+                ("u_k", ctypes.c_double)]
 
 
 class ContactError(RuntimeError):
@@ -101,6 +104,12 @@ def load_library(build_if_missing: bool = True):
     lib.contact_step_noalloc.restype = I32
     lib.contact_step_host.argtypes = [P] * 9
     lib.contact_step_host.restype = I32
+    lib.contact_history_get.argtypes = [P, ctypes.c_int64, P, P, P]
+    lib.contact_history_get.restype = I32
+    lib.contact_history_set.argtypes = [P, ctypes.c_int64, P, P]
+    lib.contact_history_set.restype = I32
+    lib.contact_history_reset.argtypes = [P]
+    lib.contact_history_reset.restype = I32
     _lib = lib
     return lib
 
@@ -124,6 +133,7 @@ class Contact:
     def __init__(self, shape_type, shape_param, face_offset, planes, young, poisson, n_cells, dx,
                  indicator=SHARP, smooth_width=1.0, inflate=0.0, damping_c=0.0, precision=FP32_TILE,
                  max_pairs=None, max_neighbors=64, max_tiles=0, use_graph=True, narrow_events=False,
+                 history=False, restitution=1.0, friction=False, mu_s=0.0, mu_k=0.0, u_k=1.0,
                  device=None, stream=None):
         if not torch.cuda.is_available():
             raise ContactError(ECUDA, "no CUDA device: the contact path has no CPU fallback")
@@ -135,6 +145,8 @@ class Contact:
         self.lib.contact_config_default(ctypes.byref(cfg), n, nc, float(dx))
         cfg.indicator, cfg.smooth_width, cfg.inflate = int(indicator), float(smooth_width), float(inflate)
         cfg.damping_c, cfg.precision = float(damping_c), int(precision)
+        cfg.history, cfg.restitution = int(bool(history)), float(restitution)
+        cfg.friction, cfg.mu_s, cfg.mu_k, cfg.u_k = int(bool(friction)), float(mu_s), float(mu_k), float(u_k)
         if max_pairs is not None:
             cfg.max_pairs = int(max_pairs)
         cfg.max_neighbors, cfg.max_tiles, cfg.use_graph = int(max_neighbors), int(max_tiles), int(bool(use_graph))
@@ -284,6 +296,35 @@ class Contact:
             self._raise(rc, "contact_particle_boxes")
         torch.cuda.current_stream(self.device).wait_stream(self.stream)
         return out
+
+    def history(self):
+        """Contact history after the last step: (ij [H,2] int32, c [H] float64)
+        host arrays sorted by (i, j)."""
+        n = ctypes.c_int64()
+        rc = self.lib.contact_history_get(self.ctx, 0, None, None, ctypes.byref(n))
+        if rc != OK:
+            self._raise(rc, "contact_history_get")
+        ij = np.zeros((n.value, 2), dtype=np.int32)
+        c = np.zeros(n.value, dtype=np.float64)
+        rc = self.lib.contact_history_get(self.ctx, n.value, ij.ctypes.data, c.ctypes.data, ctypes.byref(n))
+        if rc != OK:
+            self._raise(rc, "contact_history_get")
+        return ij, c
+
+    def set_history(self, ij, c):
+        """Replace the contact history (e.g. from a checkpoint)."""
+        ij = np.ascontiguousarray(ij, dtype=np.int32).reshape(-1, 2)
+        c = np.ascontiguousarray(c, dtype=np.float64).reshape(-1)
+        if len(c) != len(ij):
+            raise ContactError(EINVAL, "ij and c differ in length")
+        rc = self.lib.contact_history_set(self.ctx, len(c), ij.ctypes.data, c.ctypes.data)
+        if rc != OK:
+            self._raise(rc, "contact_history_set")
+
+    def reset_history(self):
+        rc = self.lib.contact_history_reset(self.ctx)
+        if rc != OK:
+            self._raise(rc, "contact_history_reset")
 
     def kernels_per_step(self):
         return int(self.lib.contact_kernels_per_step(self.ctx))

@@ -27,6 +27,7 @@ constexpr int kSegMax = 16;           // longest line segment of one item
 constexpr int kPartialFloats = 12;    // FP32 partial sums per tile
 constexpr int kTapeDoubles = 16;      // FP64 per-pair values kept for the adjoint
 constexpr int kCostBuckets = 4;       // node-sweep queue: tiles grouped by estimated cost, dearest first
+constexpr int kStepCounter = 12;      // counters[] slot of the completed-step count
 constexpr int kFtDoubles = 9;         // per-pair F, T_A, T_B
 
 // Error codes written by kernels (same numbering as contact_status).
@@ -51,6 +52,9 @@ struct Params {
   int kind_set;          // node-sweep variant: 0 all kinds, 1 spheres and cuboids, 2 cubes only
   int dx_pow2;           // 1: dx is a power of two, so x / dx == x * inv_dx exactly
   double damping_c;
+  int history, friction;  // contact history; tangential force
+  double damp_K;         // history: c = damp_K / u0 at a contact's first step (u0 > 0)
+  double mu_s_star, mu_k, inv_u_k;   // friction law
   int nbin[3];           // bins per axis
   int bin_cap;           // particles one bin can hold (bin_items row length)
   double binw[3];        // bin width (physical)
@@ -144,6 +148,9 @@ struct Lists {
   int* dn_pair;     // [N, max_nbr] pair index of (dn_list[p][r], p)
   int* row_off;     // [N + 1] first pair of particle i
   int* grp_sum;     // [ceil(N / 256)] partners above, summed over groups of 256 particles
+  int* hist_j;      // [2, N, max_nbr] contact history: partner j > i of each ongoing contact of i
+  double* hist_c;   // [2, N, max_nbr] its damping factor
+  int* hist_n;      // [2, N] contacts per particle; buffer (steps & 1) is read, the other written
   PairRec* pairs;   // [max_pairs]
   int* tile_pair;   // [max_tiles] pair of each tile
   PairRec* tiles;   // [kCostBuckets, max_tiles] one record per tile (the pair's record with tile and
@@ -154,7 +161,8 @@ struct Lists {
   double* ft;       // [max_pairs, kFtDoubles]
   const int* kind;  // [N] sweep kind of each particle (Kind, polytopes by face bucket)
   int* counters;    // [16]: 0 pairs, 1 tiles, 2 queue, 3 cells(lo), 4 cells(hi), 5 overlapping pairs,
-                    // 6 adjoint queue, 8.. 8 + kCostBuckets tiles per cost bucket
+                    // 6 adjoint queue, 8.. 8 + kCostBuckets tiles per cost bucket,
+                    // kStepCounter steps completed (its parity selects the contact-history buffer)
   unsigned long long* u64;  // [4]: 0 node evaluations, 1 nominal lane-ops of the node sweep
   int* err;         // [1] sticky device error
   int* err_host;    // mapped host word mirroring err

@@ -28,6 +28,17 @@ struct ForceArgs {
   double* tape;
   double L[3];
   double dx, dx3, gscale, g_min2, inflate, damping_c;
+  // contact history (Sec. 4.3.3): last step's contacts of each particle i
+  // (partner j, damping factor c) are read from *_rd, this step's go to *_wr
+  int history, friction, hist_cap;
+  const int* hn_rd;
+  const int* hj_rd;
+  const double* hc_rd;
+  int* hn_wr;
+  int* hj_wr;
+  double* hc_wr;
+  double damp_K;                    // c = damp_K / u0 for a contact's first step
+  double mu_s_star, mu_k, inv_u_k;  // friction law of Eq. (contact_force_tangential)
 };
 
 namespace fl {
@@ -191,20 +202,85 @@ __device__ __forceinline__ void pair_force_law(ForceArgs a, const OvlRec* e, int
     const int k1 = kc == 2 ? 0 : kc + 1, k2 = kc == 0 ? 2 : kc - 1;
     const double ra1v = __shfl_sync(kFull, rak, b0 + k1), ra2v = __shfl_sync(kFull, rak, b0 + k2);
     const double rb1v = __shfl_sync(kFull, rbk, b0 + k1), rb2v = __shfl_sync(kFull, rbk, b0 + k2);
-    double damp = 1.0;
-    if (a.vel != nullptr && a.damping_c != 0.0) {
+    // velocity of A relative to B at x_c, u_AB = (v_A + w_A x r_A) - (v_B + w_B x r_B),
+    // and its normal part ddot_n (> 0 when approaching)
+    double uabk = 0.0, ddot = 0.0;
+    if (a.vel != nullptr && (a.damping_c != 0.0 || a.history || a.friction)) {
       const double* va = a.vel + 6 * i;
       const double* vb = a.vel + 6 * j;
-      // relative normal speed (v_A + w_A x r_A - v_B - w_B x r_B) . n
       const double wak = fma(va[3 + k1], ra2v, -va[3 + k2] * ra1v);
       const double wbk = fma(vb[3 + k1], rb2v, -vb[3 + k2] * rb1v);
-      const double uk = ((va[kc] + wak) - (vb[kc] + wbk)) * nk;
+      uabk = (va[kc] + wak) - (vb[kc] + wbk);
+      const double uk = uabk * nk;
       const double u0 = __shfl_sync(kFull, uk, b0), u1 = __shfl_sync(kFull, uk, b0 + 1),
                      u2 = __shfl_sync(kFull, uk, b0 + 2);
-      damp = dmax(0.0, fma(a.damping_c, (u0 + u1) + u2, 1.0));
+      ddot = (u0 + u1) + u2;
     }
+    // tangential part u_t = u_AB - ddot_n n, for the friction law
+    double utk = 0.0, utn2 = 0.0;
+    if (a.friction && a.vel != nullptr) {
+      utk = fma(-ddot, nk, uabk);
+      const double t2 = utk * utk;
+      const double t0 = __shfl_sync(kFull, t2, b0), t1 = __shfl_sync(kFull, t2, b0 + 1),
+                     t2b = __shfl_sync(kFull, t2, b0 + 2);
+      utn2 = (t0 + t1) + t2b;
+    }
+    // two more reciprocal square roots: of ddot_n (lane 0, a new contact's
+    // c = damp_K / ddot_n) and of |u_t|^2 (lane 1)
+    double inv_ddot = 0.0, inv_utn = 0.0;
+    const bool dpos = __double_as_longlong(ddot) > 0, upos = __double_as_longlong(utn2) > 0;
+    if (a.history || a.friction) {
+      const double y5 = nr_rsqrt(k == 0 ? (dpos ? ddot : 1.0) : (upos ? utn2 : 1.0));
+      const double ya = __shfl_sync(kFull, y5, b0), yb = __shfl_sync(kFull, y5, b0 + 1);
+      inv_ddot = dpos ? ya * ya : 0.0;
+      inv_utn = upos ? yb : 0.0;
+    }
+    double cdamp = a.damping_c;   // c of Eq. (damping_factor) for this pair
+    if (a.history) {
+      // an ongoing contact (i, j) keeps its c; a new one takes c from u0 = ddot_n
+      // (0 without velocities or for u0 <= 0).  Lane k of the pair checks the
+      // entries k, k + 4, ... of i's list; the first 8 are loaded before the count.
+      const size_t base = static_cast<size_t>(i) * a.hist_cap;
+      const int cnt = min(a.hn_rd[i], a.hist_cap);
+      int hit = -1;
+      double ch = 0.0;
+      {
+        const int m0 = k, m1 = k + 4;
+        const int j0 = m0 < a.hist_cap ? a.hj_rd[base + m0] : -1;
+        const int j1 = m1 < a.hist_cap ? a.hj_rd[base + m1] : -1;
+        const double c0 = m0 < a.hist_cap ? a.hc_rd[base + m0] : 0.0;
+        const double c1 = m1 < a.hist_cap ? a.hc_rd[base + m1] : 0.0;
+        if (m0 < cnt && j0 == j) { hit = m0; ch = c0; }
+        if (m1 < cnt && j1 == j) { hit = m1; ch = c1; }
+      }
+      const int cmax = __reduce_max_sync(kFull, act ? cnt : 0);
+      for (int m0 = 8; m0 < cmax; m0 += 4) {
+        const int m = m0 + k;
+        if (m < cnt && a.hj_rd[base + m] == j) { hit = m; ch = a.hc_rd[base + m]; }
+      }
+      // the pair's lane with the hit (if any) supplies c
+      int src = hit >= 0 ? lane : -1;
+      src = max(src, __shfl_xor_sync(kFull, src, 1));
+      src = max(src, __shfl_xor_sync(kFull, src, 2));
+      ch = __shfl_sync(kFull, ch, src >= 0 ? src : b0);
+      cdamp = src >= 0 ? ch : a.damp_K * inv_ddot;
+    }
+    double damp = 1.0;
+    if (a.vel != nullptr && cdamp != 0.0) damp = dmax(0.0, fma(cdamp, ddot, 1.0));
     const double fmag = vok ? (4.0 / (3.0 * 3.14159265358979323846)) * estar * (vd * y3) * damp : 0.0;
-    const double Fk = fmag * nk;
+    double Fk = fmag * nk;
+    if (a.friction && __double_as_longlong(fmag) > 0 && upos) {
+      // Eq. (contact_force_tangential): B receives +f(a) |F_n| t, a = |u_t| / u_k,
+      // f = (2 mu_s* - mu_k) a^2 / (a^4 + 1) + mu_k a^2 / (a^2 + 1)
+      const double sa = utn2 * inv_utn * a.inv_u_k;
+      const double a2 = sa * sa;
+      double coef = a.mu_k;
+      if (a2 < 1e30) {
+        const double den1 = fma(a2, a2, 1.0), den2 = a2 + 1.0;
+        coef = a2 * fma(2.0 * a.mu_s_star - a.mu_k, den2, a.mu_k * den1) / (den1 * den2);
+      }
+      Fk = fma(coef * fmag, utk * inv_utn, Fk);
+    }
     const double F1 = __shfl_sync(kFull, Fk, b0 + k1), F2 = __shfl_sync(kFull, Fk, b0 + k2);
     // T_A = r_A x (-F), T_B = r_B x F
     const double TAk = fma(ra2v, F1, -ra1v * F2);
@@ -223,7 +299,14 @@ __device__ __forceinline__ void pair_force_law(ForceArgs a, const OvlRec* e, int
         tp[0] = s0; tp[7] = d; tp[8] = gn; tp[9] = fallback;
       } else if (k == 3) {
         tp[10] = estar; tp[11] = damp; tp[12] = fmag; tp[13] = int_to_double(idx);
-        tp[14] = 0.0; tp[15] = 0.0;
+        tp[14] = cdamp; tp[15] = 0.0;
+      }
+      if (a.history && k == 0) {   // this step's contact list of i
+        const int slot = atomicAdd(a.hn_wr + i, 1);
+        if (slot < a.hist_cap) {
+          a.hj_wr[static_cast<size_t>(i) * a.hist_cap + slot] = j;
+          a.hc_wr[static_cast<size_t>(i) * a.hist_cap + slot] = cdamp;
+        }
       }
     }
   }

@@ -192,6 +192,12 @@ void contact_config_default(contact_config* cfg, int32_t n_particles, const int3
   cfg->max_tiles = 0;
   cfg->use_graph = 1;
   cfg->narrow_events = 0;
+  cfg->history = 0;
+  cfg->friction = 0;
+  cfg->restitution = 1.0;
+  cfg->mu_s = 0.0;
+  cfg->mu_k = 0.0;
+  cfg->u_k = 1.0;
 }
 
 double contact_damping_factor(double e, double u0) {
@@ -216,6 +222,12 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   if (C.precision != 0 && C.precision != 1) return CONTACT_EINVAL;
   if (!(C.smooth_width > 0.0) || !(C.inflate >= 0.0) || !(C.damping_c >= 0.0)) return CONTACT_EINVAL;
   if (C.max_neighbors < 0 || C.max_neighbors > 512 || C.max_tiles < 0) return CONTACT_EINVAL;
+  if (C.history != 0 && C.history != 1) return CONTACT_EINVAL;
+  if (C.history && !(C.restitution >= 0.0 && C.restitution <= 1.0)) return CONTACT_EINVAL;
+  if (C.friction != 0 && C.friction != 1) return CONTACT_EINVAL;
+  if (C.friction && (!(C.mu_s > 0.0) || !(C.mu_k >= 0.0) || !(C.u_k > 0.0) || !std::isfinite(C.mu_s) ||
+                     !std::isfinite(C.mu_k) || !std::isfinite(C.u_k)))
+    return CONTACT_EINVAL;
   const int max_nbr = C.max_neighbors > 0 ? C.max_neighbors : 64;
   const long long max_tiles_ll = C.max_tiles > 0 ? C.max_tiles : 8LL * C.max_pairs;
   if (max_tiles_ll > (1LL << 30)) return CONTACT_EINVAL;
@@ -326,6 +338,13 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
                : std::all_of(kind.begin(), kind.end(),
                              [](int k) { return k == KIND_SPHERE || k == KIND_CUBOID || k == KIND_CUBE; }) ? 1 : 0;
   P.damping_c = C.damping_c;
+  P.history = C.history;
+  P.friction = C.friction;
+  // Eq. (damping_factor) as c = K / u0 with K = 1.5 (1 - e)(11 - e) / (1 + 9 e)
+  P.damp_K = C.history ? 1.5 * (1.0 - C.restitution) * (11.0 - C.restitution) / (1.0 + 9.0 * C.restitution) : 0.0;
+  P.mu_k = C.mu_k;
+  P.mu_s_star = C.friction ? C.mu_s * (1.0 - 0.09 * std::pow(C.mu_k / C.mu_s, 4)) : 0.0;
+  P.inv_u_k = C.friction ? 1.0 / C.u_k : 0.0;
   P.max_pairs = C.max_pairs;
   P.max_nbr = max_nbr;
   P.max_tiles = static_cast<int>(max_tiles_ll);
@@ -398,6 +417,12 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   GBC_TRY(dev_alloc(c, &W.dn_pair, static_cast<size_t>(n) * max_nbr));
   GBC_TRY(dev_alloc(c, &W.row_off, static_cast<size_t>(n) + 1));
   GBC_TRY(dev_alloc(c, &W.grp_sum, static_cast<size_t>((n + kRowGroup - 1) / kRowGroup)));
+  // contact history: two buffers (read the previous step's, write this step's)
+  if (C.history) {
+    GBC_TRY(dev_alloc(c, &W.hist_j, 2 * static_cast<size_t>(n) * max_nbr));
+    GBC_TRY(dev_alloc(c, &W.hist_c, 2 * static_cast<size_t>(n) * max_nbr));
+    GBC_TRY(dev_alloc(c, &W.hist_n, 2 * static_cast<size_t>(n)));
+  }
   GBC_TRY(dev_alloc(c, &W.pairs, mp));
   GBC_TRY(dev_alloc(c, &W.tile_pair, mt));
   GBC_TRY(dev_alloc(c, &W.tiles, mt * kCostBuckets));
@@ -416,6 +441,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   GBC_TRY(cudaMemset(W.up_count, 0, sizeof(int) * n));
   GBC_TRY(cudaMemset(W.bin_count, 0, sizeof(int) * nbins));
   GBC_TRY(cudaMemset(W.dn_count, 0, sizeof(int) * n));
+  if (C.history) GBC_TRY(cudaMemset(W.hist_n, 0, sizeof(int) * 2 * n));
   GBC_TRY(cudaEventCreate(&c->ev_narrow[0]));
   GBC_TRY(cudaEventCreate(&c->ev_narrow[1]));
   GBC_TRY(cudaHostAlloc(reinterpret_cast<void**>(&c->err_host), sizeof(int), cudaHostAllocMapped));
@@ -562,6 +588,82 @@ contact_status contact_narrow_time(contact_ctx* c, float* ms) {
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
   e = cudaEventElapsedTime(ms, c->ev_narrow[0], c->ev_narrow[1]);
   return e == cudaSuccess ? CONTACT_OK : cuda_fail(c, e, "cudaEventElapsedTime");
+}
+
+namespace {
+// The contact-history buffer the next step reads (after the stream's work).
+contact_status history_buffer(contact_ctx* c, int* buf) {
+  if (!c->P.history) return fail(c, CONTACT_ESTATE, "contact history is off");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  int steps = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpy(&steps, c->W.counters + kStepCounter, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "contact history");
+  *buf = steps & 1;
+  return CONTACT_OK;
+}
+}  // namespace
+
+contact_status contact_history_get(contact_ctx* c, int64_t max_rows, int32_t* ij, double* cv, int64_t* n) {
+  if (c == nullptr || n == nullptr || max_rows < 0 || (max_rows > 0 && (ij == nullptr || cv == nullptr)))
+    return CONTACT_EINVAL;
+  int b = 0;
+  const contact_status hs = history_buffer(c, &b);
+  if (hs != CONTACT_OK) return hs;
+  const size_t np = static_cast<size_t>(c->P.n), cap = static_cast<size_t>(c->P.max_nbr);
+  std::vector<int> cnt(np), hj(np * cap);
+  std::vector<double> hc(np * cap);
+  cudaError_t e = cudaMemcpy(cnt.data(), c->W.hist_n + b * np, sizeof(int) * np, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(hj.data(), c->W.hist_j + b * np * cap, sizeof(int) * np * cap, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(hc.data(), c->W.hist_c + b * np * cap, sizeof(double) * np * cap, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "contact_history_get");
+  std::vector<std::pair<std::pair<int, int>, double>> rows;
+  for (size_t i = 0; i < np; ++i)
+    for (int m = 0; m < std::min(cnt[i], c->P.max_nbr); ++m)
+      rows.push_back({{static_cast<int>(i), hj[i * cap + m]}, hc[i * cap + m]});
+  std::sort(rows.begin(), rows.end());
+  *n = static_cast<int64_t>(rows.size());
+  for (int64_t r = 0; r < std::min<int64_t>(max_rows, *n); ++r) {
+    ij[2 * r] = rows[r].first.first;
+    ij[2 * r + 1] = rows[r].first.second;
+    cv[r] = rows[r].second;
+  }
+  return CONTACT_OK;
+}
+
+contact_status contact_history_set(contact_ctx* c, int64_t n_rows, const int32_t* ij, const double* cv) {
+  if (c == nullptr || n_rows < 0 || (n_rows > 0 && (ij == nullptr || cv == nullptr))) return CONTACT_EINVAL;
+  int b = 0;
+  const contact_status hs = history_buffer(c, &b);
+  if (hs != CONTACT_OK) return hs;
+  const size_t np = static_cast<size_t>(c->P.n), cap = static_cast<size_t>(c->P.max_nbr);
+  std::vector<int> cnt(np, 0), hj(np * cap, -1);
+  std::vector<double> hc(np * cap, 0.0);
+  for (int64_t r = 0; r < n_rows; ++r) {
+    const int i = ij[2 * r], j = ij[2 * r + 1];
+    if (i < 0 || j <= i || j >= c->P.n) return fail(c, CONTACT_EINVAL, "contact_history_set: bad (i, j)");
+    if (cnt[i] >= c->P.max_nbr) return fail(c, CONTACT_EINVAL, "contact_history_set: more rows of i than max_neighbors");
+    for (int m = 0; m < cnt[i]; ++m)
+      if (hj[i * cap + m] == j) return fail(c, CONTACT_EINVAL, "contact_history_set: repeated (i, j)");
+    hj[i * cap + cnt[i]] = j;
+    hc[i * cap + cnt[i]] = cv[r];
+    ++cnt[i];
+  }
+  cudaError_t e = cudaMemcpy(c->W.hist_n + b * np, cnt.data(), sizeof(int) * np, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->W.hist_j + b * np * cap, hj.data(), sizeof(int) * np * cap, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->W.hist_c + b * np * cap, hc.data(), sizeof(double) * np * cap, cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? CONTACT_OK : cuda_fail(c, e, "contact_history_set");
+}
+
+contact_status contact_history_reset(contact_ctx* c) {
+  if (c == nullptr) return CONTACT_EINVAL;
+  if (!c->P.history) return fail(c, CONTACT_ESTATE, "contact history is off");
+  const cudaError_t e = cudaMemsetAsync(c->W.hist_n, 0, sizeof(int) * 2 * c->P.n, c->stream);
+  return e == cudaSuccess ? CONTACT_OK : cuda_fail(c, e, "cudaMemsetAsync");
 }
 
 int32_t contact_kernels_per_step(const contact_ctx*) { return 5; }

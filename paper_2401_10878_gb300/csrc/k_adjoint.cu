@@ -90,6 +90,44 @@ __global__ void __launch_bounds__(32) k_adj_pre(Params P, Shapes S, Parts D, Lis
       gTi[k] = gT[3 * i + k]; gTj[k] = gT[3 * j + k];
     }
     const double d = tp[7], gnorm = tp[8], estar = tp[10], damp = tp[11];
+    // c of Eq. (damping_factor) as the forward used it (the shared one, or the
+    // contact's own with contact history, held fixed like every per-contact constant)
+    const double cdamp = tp[14];
+    // relative velocity u_AB = (v_A + w_A x r_A) - (v_B + w_B x r_B) at x_c, ddot_n = u_AB . n
+    double uab[3] = {0.0, 0.0, 0.0}, ddot = 0.0;
+    const double* va = vel != nullptr ? vel + 6 * i : nullptr;
+    const double* vb = vel != nullptr ? vel + 6 * j : nullptr;
+    if (vel != nullptr && fmag > 0.0 && (cdamp != 0.0 || P.friction)) {
+      double wa[3], wb[3];
+      cross3(va + 3, rA, wa);
+      cross3(vb + 3, rB, wb);
+      for (int k = 0; k < 3; ++k) uab[k] = (va[k] + wa[k]) - (vb[k] + wb[k]);
+      ddot = uab[0] * n[0] + uab[1] * n[1] + uab[2] * n[2];
+    }
+    // friction, Eq. (contact_force_tangential): F = fmag (n + f(a) t), t = u_t / |u_t|,
+    // u_t = u_AB - ddot_n n, a = |u_t| / u_k
+    bool fric = false;
+    double tdir[3] = {0.0, 0.0, 0.0}, coef = 0.0, dcoef = 0.0, utn = 0.0;
+    if (P.friction && vel != nullptr && fmag > 0.0) {
+      double ut[3];
+      for (int k = 0; k < 3; ++k) ut[k] = uab[k] - ddot * n[k];
+      const double utn2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
+      if (utn2 > 0.0) {
+        fric = true;
+        utn = sqrt(utn2);
+        for (int k = 0; k < 3; ++k) tdir[k] = ut[k] / utn;
+        const double a = utn * P.inv_u_k, a2 = a * a;
+        const double A = 2.0 * P.mu_s_star - P.mu_k;
+        coef = P.mu_k;
+        if (a2 < 1e30) {
+          const double den1 = a2 * a2 + 1.0, den2 = a2 + 1.0;
+          coef = a2 * (A * den2 + P.mu_k * den1) / (den1 * den2);
+          // f'(a) = 2a [A (1 - a^4) / (a^4 + 1)^2 + mu_k / (a^2 + 1)^2]
+          dcoef = 2.0 * a * (A * (1.0 - a2 * a2) / (den1 * den1) + P.mu_k / (den2 * den2));
+        }
+        for (int k = 0; k < 3; ++k) F[k] += fmag * coef * tdir[k];
+      }
+    }
     // dL/dF = Lambda, dL/dx_c, explicit dL/dX_A, dL/dX_B'
     double c1[3], c2[3], Lam[3], gxc[3], gXA[3], gXB[3], t1[3], t2[3];
     cross3(gTi, rA, c1);
@@ -101,32 +139,46 @@ __global__ void __launch_bounds__(32) k_adj_pre(Params P, Shapes S, Parts D, Lis
     cross3(gTj, F, t2);
     for (int k = 0; k < 3; ++k) { gXA[k] = t1[k]; gXB[k] = t2[k]; }
     const double Ln = Lam[0] * n[0] + Lam[1] * n[1] + Lam[2] * n[2];
+    const double Lt = Lam[0] * tdir[0] + Lam[1] * tdir[1] + Lam[2] * tdir[2];
+    const double Lm = Ln + coef * Lt;   // dL/dfmag
     double gn[3] = {fmag * Lam[0], fmag * Lam[1], fmag * Lam[2]};
+    double guab[3] = {0.0, 0.0, 0.0};   // dL/du_AB
+    if (fric) {
+      // through t (projected on its normal plane) and through f(a)
+      double gut[3];
+      const double s_dir = fmag * coef / utn, s_mag = fmag * Lt * dcoef * P.inv_u_k;
+      for (int k = 0; k < 3; ++k) gut[k] = s_dir * (Lam[k] - Lt * tdir[k]) + s_mag * tdir[k];
+      const double gun = gut[0] * n[0] + gut[1] * n[1] + gut[2] * n[2];
+      for (int k = 0; k < 3; ++k) {
+        guab[k] += gut[k] - gun * n[k];
+        gn[k] -= uab[k] * gun + ddot * gut[k];
+      }
+    }
     double gV = 0.0, gd = 0.0;
     // reciprocals by Newton-Raphson from an FP32 seed (no FP64 division sequence)
     const double inv_S0 = fl::nr_rsqrt(S0) * fl::nr_rsqrt(S0);
     if (fmag > 0.0) {
-      const double half_lf = 0.5 * Ln * fmag;
+      const double half_lf = 0.5 * Lm * fmag;
       gV = half_lf * inv_S0 * (P.inv_dx * P.inv_dx * P.inv_dx);
       const double yd = fl::nr_rsqrt(d);
       gd = half_lf * (yd * yd);
-      if (vel != nullptr && P.damping_c != 0.0 && damp > 0.0) {
-        const double* va = vel + 6 * i;
-        const double* vb = vel + 6 * j;
-        double wa[3], wb[3], uA[3], uB[3];
-        cross3(va + 3, rA, wa);
-        cross3(vb + 3, rB, wb);
-        for (int k = 0; k < 3; ++k) { uA[k] = va[k] + wa[k]; uB[k] = vb[k] + wb[k]; }
-        const double gdd = Ln * fmag * P.damping_c / damp;
-        double na[3], nb[3];
-        cross3(n, va + 3, na);
-        cross3(n, vb + 3, nb);
+      if (vel != nullptr && cdamp != 0.0 && damp > 0.0) {
+        const double gdd = Lm * fmag * cdamp / damp;   // dL/d(ddot_n)
         for (int k = 0; k < 3; ++k) {
-          gn[k] += gdd * (uA[k] - uB[k]);
-          gxc[k] += gdd * (na[k] - nb[k]);
-          gXA[k] -= gdd * na[k];
-          gXB[k] += gdd * nb[k];
+          gn[k] += gdd * uab[k];
+          guab[k] += gdd * n[k];
         }
+      }
+    }
+    if (vel != nullptr && (fric || cdamp != 0.0)) {
+      // u_AB depends on x_c, X_A and X_B' through the angular velocities
+      double ga[3], gb[3];
+      cross3(guab, va + 3, ga);
+      cross3(guab, vb + 3, gb);
+      for (int k = 0; k < 3; ++k) {
+        gxc[k] += ga[k] - gb[k];
+        gXA[k] -= ga[k];
+        gXB[k] += gb[k];
       }
     }
     // normal: n = G / |G| with G = kappa Sg, or the centre-line fallback

@@ -40,6 +40,8 @@ __global__ void k_pose(Params P, Shapes S, Parts D, Lists W, const double* __res
     W.u64[1] = 0;        // nominal lane-ops
   }
   if (t < (P.n + kRowGroup - 1) / kRowGroup) W.grp_sum[t] = 0;
+  // contact history: this step's lists (the buffer not read) start empty
+  if (P.history && t < P.n) W.hist_n[static_cast<size_t>(((W.counters[kStepCounter] & 1) ^ 1)) * P.n + t] = 0;
   if (t >= 3 * P.n) return;
   const int p = t / 3, k = t - 3 * p;
   double q[4];

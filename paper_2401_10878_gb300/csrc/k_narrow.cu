@@ -523,6 +523,17 @@ __device__ __forceinline__ void flush_overlaps(const Params& P, const Shapes& S,
   for (int k = 0; k < 3; ++k) a.L[k] = P.L[k];
   a.dx = P.dx; a.dx3 = P.dx3; a.gscale = P.gscale; a.g_min2 = P.g_min2; a.inflate = P.inflate;
   a.damping_c = P.damping_c;
+  a.history = P.history; a.friction = P.friction; a.hist_cap = P.max_nbr;
+  a.damp_K = P.damp_K; a.mu_s_star = P.mu_s_star; a.mu_k = P.mu_k; a.inv_u_k = P.inv_u_k;
+  if (P.history) {   // buffer (steps & 1) holds the previous step's contacts
+    const int rd = W.counters[kStepCounter] & 1;
+    const size_t nn = static_cast<size_t>(P.n);
+    a.hn_rd = W.hist_n + rd * nn; a.hn_wr = W.hist_n + (rd ^ 1) * nn;
+    a.hj_rd = W.hist_j + rd * nn * P.max_nbr; a.hj_wr = W.hist_j + (rd ^ 1) * nn * P.max_nbr;
+    a.hc_rd = W.hist_c + rd * nn * P.max_nbr; a.hc_wr = W.hist_c + (rd ^ 1) * nn * P.max_nbr;
+  } else {
+    a.hn_rd = a.hj_rd = nullptr; a.hc_rd = nullptr; a.hn_wr = a.hj_wr = nullptr; a.hc_wr = nullptr;
+  }
   pair_force_law(a, ov, nov);
   __syncwarp();
   nov = 0;

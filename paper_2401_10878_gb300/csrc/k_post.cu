@@ -22,7 +22,10 @@ __global__ void __launch_bounds__(32) k_particle_sum(Params P, Parts D, Lists W,
                                                       double* __restrict__ torque) {
   pdl_begin();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t == 0) *W.err_host = *W.err;
+  if (t == 0) {
+    *W.err_host = *W.err;
+    ++W.counters[kStepCounter];   // the contact history written this step is read by the next
+  }
   // the cell list's bin counts start the next step at zero
   const int nbins = P.nbin[0] * P.nbin[1] * P.nbin[2];
   for (int b = t; b < nbins; b += gridDim.x * blockDim.x) W.bin_count[b] = 0;
