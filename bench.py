@@ -209,7 +209,7 @@ def cpu_baseline(st, pos, quat, budget_s):
             "one_thread": {"value": c1 / s1, "ms_per_step": 1e3 * s1 / n1, "steps": n1}}
 
 
-def time_forward(model, pos_d, quat_d, steps, warmup, flush, narrow=False):
+def time_forward(model, pos_d, quat_d, steps, warmup, flush, narrow=False, vel_d=None):
     """Per-step device time (events around contact_step on the context stream),
     L2 flushed before every step.  With narrow=True the model records the
     library's events around the node-sweep launch and their times are summed."""
@@ -224,7 +224,7 @@ def time_forward(model, pos_d, quat_d, steps, warmup, flush, narrow=False):
         with torch.cuda.stream(s):
             flush.zero_()
         e0.record(s)
-        model.step_async(pos_d[idx], quat_d[idx])
+        model.step_async(pos_d[idx], quat_d[idx], None if vel_d is None else vel_d[idx])
         e1.record(s)
         e1.synchronize()
         if idx not in per_pose:
@@ -399,6 +399,27 @@ def extras(args, dev, flush, peak):
     out["cubes1934_fp64_form"] = {"cell_evals_per_s": r["cells"] / (r["ms"] * 1e-3),
                                   "ms_per_step": r["ms"] / steps, "narrow_ms": r["narrow_ms"] / steps}
     m.close()
+    # the headline workload with velocities: shared damping, then contact history + friction
+    # (timed like the other extras, with the library's events around the node sweep; the
+    # first entry, without velocities, is the same timing of the headline step)
+    st = headline_state(0)
+    pos, quat = W.pose_sequence(st, steps + 3)
+    rng = np.random.default_rng(17)
+    vel = np.concatenate([rng.normal(size=(steps + 3, st.n, 3)) * 0.05,
+                          rng.normal(size=(steps + 3, st.n, 3)) * 0.01], axis=2)
+    pd, qd, vd = (torch.tensor(x, device=dev) for x in (pos, quat, vel))
+    law = {}
+    for name, kw in (("no_velocities", dict()), ("shared_damping", dict(damping_c=0.3)),
+                     ("history_friction", dict(history=True, restitution=0.5, friction=True, mu_s=0.5, mu_k=0.3,
+                                               u_k=0.02))):
+        m = Contact.from_state(st, narrow_events=True, **kw)
+        r = time_forward(m, pd, qd, steps, 3, flush, narrow=True, vel_d=vd if kw else None)
+        law[name] = {"cell_evals_per_s": r["cells"] / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / steps,
+                     "narrow_ms": r["narrow_ms"] / steps, "overlapping_pairs": m.stats()["overlapping"]}
+        if kw.get("history"):
+            law[name]["contacts_in_history"] = int(len(m.history()[1]))
+        m.close()
+    out["cubes1934_velocities"] = law
     # 400 cubes at 10 %, and the resolution sweep (500 cubes at 20 %, edge 8..24), both forms
     def both_forms(st, nsteps):
         pos, quat = W.pose_sequence(st, nsteps + 3)
@@ -452,21 +473,29 @@ def extras(args, dev, flush, peak):
     return out
 
 
+def node_sweep_source_hash():
+    """Hash of the sources the node-sweep kernel is compiled from."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("k_narrow.cu", "force_law.cuh", "contact_dev.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2401_10878_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profile():
     """DRAM bytes per launch of the node sweep from the committed ncu summary,
     only while the kernel source is unchanged since the capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "k_narrow32_cubes1934.md")
-    src = os.path.join(ROOT, "paper_2401_10878_gb300", "csrc", "k_narrow.cu")
     if not os.path.exists(path):
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = node_sweep_source_hash()
     vals = {}
     for line in open(path):
         if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
+            k, v = line.strip()[2:].rsplit(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("k_narrow.cu sha256[:16]") != h:
+    if vals.get("node sweep sources sha256[:16]") != h:
         return None
     try:
         return float(vals["dram bytes per launch"])

@@ -344,6 +344,30 @@ __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
 // remainder from the pose kernel.
 constexpr int kBuildWarps = 8;   // particle rows per block of the pair builder
 
+// Store a pair record (with its tile index) as fourteen 16-byte stores from
+// registers, field by field (an aggregate copy would stage it in local memory).
+__device__ __forceinline__ void store_pair_rec(PairRec* dst, const PairRec& r, int tile) {
+  int4* d = reinterpret_cast<int4*>(dst);
+  const auto f = [](float x) { return __float_as_int(x); };
+  d[0] = make_int4(r.i, r.j, r.lo[0], r.lo[1]);
+  d[1] = make_int4(r.lo[2], r.dim[0], r.dim[1], r.dim[2]);
+  d[2] = make_int4(r.shift[0], r.shift[1], r.shift[2], r.axis);
+  d[3] = make_int4(r.seglen, r.nseg, r.nitems, r.tile0);
+  d[4] = make_int4(r.ntiles, r.kinds, r.ai[0], r.ai[1]);
+  d[5] = make_int4(r.ai[2], r.bi[0], r.bi[1], r.bi[2]);
+  d[6] = make_int4(f(r.af[0]), f(r.af[1]), f(r.af[2]), f(r.bf[0]));
+  d[7] = make_int4(f(r.bf[1]), f(r.bf[2]), f(r.rta[0]), f(r.rta[1]));
+  d[8] = make_int4(f(r.rta[2]), f(r.rta[3]), f(r.rta[4]), f(r.rta[5]));
+  d[9] = make_int4(f(r.rta[6]), f(r.rta[7]), f(r.rta[8]), f(r.rtb[0]));
+  d[10] = make_int4(f(r.rtb[1]), f(r.rtb[2]), f(r.rtb[3]), f(r.rtb[4]));
+  d[11] = make_int4(f(r.rtb[5]), f(r.rtb[6]), f(r.rtb[7]), f(r.rtb[8]));
+  d[12] = make_int4(f(r.sza[0]), f(r.sza[1]), f(r.sza[2]), f(r.szb[0]));
+  d[13] = make_int4(f(r.szb[1]), f(r.szb[2]), tile, r.pair);
+}
+static_assert(offsetof(PairRec, rta) == 30 * 4 && offsetof(PairRec, szb) == 51 * 4 &&
+                  offsetof(PairRec, pair) == 55 * 4 && sizeof(PairRec) == 14 * 16,
+              "store_pair_rec follows the PairRec layout");
+
 __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shapes S, Parts D, Lists W,
                                                                   int32_t* __restrict__ pair_ij,
                                                                   int32_t* __restrict__ n_pairs_out) {
@@ -402,7 +426,10 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
 #pragma unroll
       for (int u = 0; u < 8; ++u) dpre[u] = u < cap ? dl[u] : 0;
       int lo[3], hi[3];
-      pair_box(P, D, i, j, pr.shift, lo, hi);
+      int shift[3];
+      pair_box(P, D, i, j, shift, lo, hi);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) pr.shift[k] = shift[k];
       pr.i = i;
       pr.j = j;
 #pragma unroll
@@ -434,11 +461,12 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
         }
       }
       if (best < 0) {   // a box longer than 8 * kSegMax nodes: longest axis, more segments
-        int a = 0;
-        for (int k = 1; k < 3; ++k) a = pr.dim[k] > pr.dim[a] ? k : a;
+        // (selects, not a runtime index into pr.dim: that would put pr in local memory)
+        const int a = pr.dim[1] > pr.dim[0] ? (pr.dim[2] > pr.dim[1] ? 2 : 1) : (pr.dim[2] > pr.dim[0] ? 2 : 0);
+        const int da = a == 0 ? pr.dim[0] : (a == 1 ? pr.dim[1] : pr.dim[2]);
         pr.axis = a;
-        pr.nseg = (pr.dim[a] + kSegMax - 1) / kSegMax;
-        pr.seglen = (pr.dim[a] + pr.nseg - 1) / pr.nseg;
+        pr.nseg = (da + kSegMax - 1) / kSegMax;
+        pr.seglen = (da + pr.nseg - 1) / pr.nseg;
       }
       pr.nitems = (pr.axis == 0 ? lines_of[0] : (pr.axis == 1 ? lines_of[1] : lines_of[2])) * pr.nseg;
       ntiles = (pr.nitems + 32 * kTileItemsPerLane - 1) / (32 * kTileItemsPerLane);
@@ -542,7 +570,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
     const int pos = bucket < kCostBuckets ? s_base[1 + bucket] + s_w[wid][1 + bucket] + before : 0;
     if (active) {
       pr.tile0 = tbase + incl - ntiles;
-      W.pairs[pi] = pr;
+      store_pair_rec(W.pairs + pi, pr, 0);
       for (int k = 0; k < ntiles; ++k) {
         if (pr.tile0 + k < P.max_tiles) W.tile_pair[pr.tile0 + k] = pi;
         else set_error(W.err, kErrCapacity);
@@ -550,10 +578,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
       // queue records (beyond the tile capacity the step fails with
       // ECAPACITY and the node sweep does not run)
       PairRec* dst = W.tiles + static_cast<size_t>(bucket) * P.max_tiles;
-      for (int k = 0; k < nq && pos + k < P.max_tiles; ++k) {
-        pr.tile = k;
-        dst[pos + k] = pr;
-      }
+      for (int k = 0; k < nq && pos + k < P.max_tiles; ++k) store_pair_rec(dst + pos + k, pr, k);
     }
   }
 }
