@@ -50,7 +50,9 @@ class _Law(ctypes.Structure):
 class _Cfg(ctypes.Structure):
     _fields_ = [("n_cells", ctypes.c_int32 * 3), ("dx", ctypes.c_double), ("indicator", ctypes.c_int32),
                 ("smooth_width", ctypes.c_double), ("inflate", ctypes.c_double),
-                ("damping_c", ctypes.c_double), ("band_eps", ctypes.c_double)]
+                ("damping_c", ctypes.c_double), ("band_eps", ctypes.c_double),
+                ("n_walls", ctypes.c_int32), ("walls", ctypes.c_void_p), ("wall_young", ctypes.c_void_p),
+                ("wall_poisson", ctypes.c_void_p)]
 
 
 def _load():
@@ -101,6 +103,13 @@ def _cfg(st, band_eps=BAND_EPS):
         c.n_cells[k] = int(st.n_cells[k])
     c.dx, c.indicator, c.smooth_width = float(st.dx), int(st.indicator), float(st.smooth_width)
     c.inflate, c.damping_c, c.band_eps = float(st.inflate), float(st.damping_c), float(band_eps)
+    walls = getattr(st, "walls", None)
+    if walls is not None and len(walls):
+        arrs = (_c(np.asarray(walls).reshape(-1, 4), np.float64), _c(st.wall_young, np.float64),
+                _c(st.wall_poisson, np.float64))
+        c.n_walls = len(arrs[0])
+        c.walls, c.wall_young, c.wall_poisson = (a.ctypes.data for a in arrs)
+        c._keep = arrs   # the arrays live as long as the struct
     return c
 
 

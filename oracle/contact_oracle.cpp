@@ -17,6 +17,9 @@
 //   * Sec. 3.3.2: across a periodic boundary the contact lives on the side of
 //     the lower-ID particle; the higher-ID particle is shifted there.
 //   * Sec. 5.1: contact enlargement of the particles (inflate parameter).
+//   * Sec. 4.3: particle-wall contacts; walls do not move.  A wall is the
+//     half-space m . x <= h (unit m pointing out of the wall), not periodic;
+//     its contacts are pairs (i, N + w) evaluated like particle pairs.
 //
 // Readings where the paper is silent (each is restated in the design notes):
 //   sample set = lattice nodes k*dx of the intersection of the two particles'
@@ -48,7 +51,7 @@ namespace {
 // ----------------------------------------------------------------------------
 // status codes (same numbering as the public C-ABI, written independently)
 enum { OR_OK = 0, OR_EINVAL = 1, OR_EDOMAIN = 5 };
-enum { SH_SPHERE = 0, SH_CUBOID = 1, SH_POLYTOPE = 2 };
+enum { SH_SPHERE = 0, SH_CUBOID = 1, SH_POLYTOPE = 2, SH_WALL = 3 };
 
 // ----------------------------------------------------------------------------
 // forward-mode dual number with NT tangent directions
@@ -115,12 +118,16 @@ struct Config {
   double inflate;        // physical length, subtracted from every SDF (Sec. 5.1)
   double damping_c;      // c of Eq. (damping_factor), shared by all contacts
   double band_eps;       // classification band in lattice units (diagnostics only)
+  int32_t n_walls;       // fixed walls: half-spaces m . x <= h, (m, h) per row of `walls`
+  const double* walls;   // [n_walls, 4]
+  const double* wall_young;
+  const double* wall_poisson;
 };
 
 struct Shape {
   int type = SH_SPHERE;
   double p[3] = {0, 0, 0};         // sphere: radius; cuboid: half extents
-  std::vector<double> planes;      // polytope: (n0, n1, n2, d) per face, n.y <= d
+  std::vector<double> planes;      // polytope: (n0, n1, n2, d) per face, n.y <= d; wall: (m, h), world frame
   std::vector<double> verts;       // vertices of the offset shape used for the AABB
 };
 
@@ -208,6 +215,12 @@ bool polytope_bounded(const std::vector<double>& pl) {
 template <class S>
 S sdf(const Shape& sh, const S X[3], const S R[9], const double x[3], double inflate, S grad[3],
       double* gap) {
+  if (sh.type == SH_WALL) {   // fixed half-space m . x <= h (world frame)
+    const double* e = sh.planes.data();
+    for (int k = 0; k < 3; ++k) grad[k] = S(e[k]);
+    *gap = std::numeric_limits<double>::infinity();
+    return S(((e[0] * x[0] + e[1] * x[1]) + e[2] * x[2]) - e[3] - inflate);
+  }
   S r[3] = {x[0] - X[0], x[1] - X[1], x[2] - X[2]};
   if (sh.type == SH_SPHERE) {
     S nr = sqrt_s(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
@@ -421,6 +434,8 @@ PairResult<S> eval_pair(const Config& cfg, const Shape& A, const Shape& B, const
   S gn = sqrt_s(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
   if (val(gn) > 1e-12 * dx * dx) {
     for (int k = 0; k < 3; ++k) res.n[k] = G[k] / gn;
+  } else if (B.type == SH_WALL) {   // into the wall: -m
+    for (int k = 0; k < 3; ++k) res.n[k] = S(-B.planes[k]);
   } else {
     S dX[3] = {XB[0] - XA[0], XB[1] - XA[1], XB[2] - XA[2]};
     S dn = sqrt_s(dX[0] * dX[0] + dX[1] * dX[1] + dX[2] * dX[2]);
@@ -489,12 +504,40 @@ PairResult<S> eval_pair(const Config& cfg, const Shape& A, const Shape& B, const
 // ----------------------------------------------------------------------------
 struct Problem {
   Config cfg;
-  int n = 0;
+  int n = 0;        // particles; shapes/young/poisson hold them, then the walls
   std::vector<Shape> shapes;
   std::vector<double> young, poisson;
   std::vector<int> lo, hi;   // node ranges [n,3]
   std::vector<PairGeom> pairs;
 };
+
+// Node box of particle range [lo, hi] against the wall m . x <= h widened by
+// delta: empty (false) when even the range's lowest corner in m has
+// m . x > h + delta; else the range clipped, per axis with m_k != 0, to the
+// nodes that some node of the range with that coordinate keeps inside.
+bool wall_box(const Config& c, const double* e, double delta, const int* lo_in, const int* hi_in, int lo[3],
+              int hi[3]) {
+  const double H = e[3] + delta;
+  double t[3];
+  for (int k = 0; k < 3; ++k) {
+    const int ck = e[k] > 0.0 ? lo_in[k] : hi_in[k];
+    t[k] = e[k] * (ck * c.dx);
+    lo[k] = lo_in[k];
+    hi[k] = hi_in[k];
+  }
+  if (!(((t[0] + t[1]) + t[2]) <= H)) return false;
+  for (int k = 0; k < 3; ++k) {
+    if (e[k] == 0.0) continue;
+    const double rest = k == 0 ? t[1] + t[2] : (k == 1 ? t[0] + t[2] : t[0] + t[1]);
+    const double b = ((H - rest) / e[k]) / c.dx;
+    if (e[k] > 0.0) {
+      if (b < hi[k]) hi[k] = static_cast<int>(std::floor(b));
+    } else {
+      if (b > lo[k]) lo[k] = static_cast<int>(std::ceil(b));
+    }
+  }
+  return true;
+}
 
 int build_problem(Problem& pb, const Config* cfg, int32_t n, const int32_t* shape_type,
                   const double* shape_param, const int32_t* face_offset, const double* planes,
@@ -551,6 +594,21 @@ int build_problem(Problem& pb, const Config* cfg, int32_t n, const int32_t* shap
     }
     rmax = std::max(rmax, circ);
   }
+  // walls: shapes N + w, unit normals, materials
+  if (c.n_walls < 0 || (c.n_walls > 0 && (c.walls == nullptr || c.wall_young == nullptr || c.wall_poisson == nullptr)))
+    return OR_EINVAL;
+  for (int w = 0; w < c.n_walls; ++w) {
+    const double* e = c.walls + 4 * w;
+    const double nn = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    if (std::fabs(nn - 1.0) > 1e-9 || !std::isfinite(e[3])) return OR_EINVAL;
+    if (!(c.wall_young[w] > 0.0) || !(c.wall_poisson[w] >= 0.0) || !(c.wall_poisson[w] < 1.0)) return OR_EINVAL;
+    Shape s;
+    s.type = SH_WALL;
+    s.planes.assign(e, e + 4);
+    pb.shapes.push_back(s);
+    pb.young.push_back(c.wall_young[w]);
+    pb.poisson.push_back(c.wall_poisson[w]);
+  }
   // at most one periodic image of a partner can overlap (Sec. 3.3.2 reading)
   for (int k = 0; k < 3; ++k)
     if (n > 0 && !(c.n_cells[k] * c.dx > 4.0 * rmax + 2.0 * c.dx)) return OR_EDOMAIN;
@@ -602,7 +660,7 @@ int build_problem(Problem& pb, const Config* cfg, int32_t n, const int32_t* shap
   }
   // O(N^2) candidate test with the image of j nearest to i (Sec. 3.3.2)
   pb.pairs.clear();
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
     for (int j = i + 1; j < n; ++j) {
       PairGeom g;
       g.i = i;
@@ -618,6 +676,18 @@ int build_problem(Problem& pb, const Config* cfg, int32_t n, const int32_t* shap
       }
       if (hit) pb.pairs.push_back(g);
     }
+    // particle-wall candidates: nodes of i's range with m . x <= h + delta
+    // (the wall's band-widened half-space); the box is i's range clipped to it
+    for (int w = 0; w < c.n_walls; ++w) {
+      PairGeom g;
+      if (wall_box(c, c.walls + 4 * w, delta, &pb.lo[3 * i], &pb.hi[3 * i], g.lo, g.hi)) {
+        g.i = i;
+        g.j = n + w;
+        g.shift[0] = g.shift[1] = g.shift[2] = 0;
+        pb.pairs.push_back(g);
+      }
+    }
+  }
   return OR_OK;
 }
 
@@ -625,8 +695,20 @@ double effective_modulus(double EA, double nuA, double EB, double nuB) {
   return 1.0 / ((1.0 - nuA * nuA) / EA + (1.0 - nuB * nuB) / EB);
 }
 
+// Pose of the pair's partner j: its image position, or for a wall the
+// origin with the identity rotation; its velocity (a wall is at rest).
 void image_pos(const Problem& pb, const PairGeom& g, const double* pos, double XB[3]) {
-  for (int k = 0; k < 3; ++k) XB[k] = pos[3 * g.j + k] - g.shift[k] * (pb.cfg.n_cells[k] * pb.cfg.dx);
+  for (int k = 0; k < 3; ++k)
+    XB[k] = g.j < pb.n ? pos[3 * g.j + k] - g.shift[k] * (pb.cfg.n_cells[k] * pb.cfg.dx) : 0.0;
+}
+const double kIdentityQuat[4] = {1.0, 0.0, 0.0, 0.0};
+const double kRest[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+const double* partner_quat(const Problem& pb, const PairGeom& g, const double* quat) {
+  return g.j < pb.n ? quat + 4 * g.j : kIdentityQuat;
+}
+const double* partner_vel(const Problem& pb, const PairGeom& g, const double* vel) {
+  if (vel == nullptr) return nullptr;
+  return g.j < pb.n ? vel + 6 * g.j : kRest;
 }
 
 void set_threads(int32_t n_threads) {
@@ -651,6 +733,10 @@ typedef struct {
   double inflate;
   double damping_c;
   double band_eps;
+  int32_t n_walls;
+  const double* walls;
+  const double* wall_young;
+  const double* wall_poisson;
 } oracle_config;
 
 int32_t oracle_max_threads(void) {
@@ -739,7 +825,7 @@ int64_t oracle_contact_step(const oracle_config* cfg, int32_t n, const int32_t* 
     ContactLaw law;
     law.c = pb.cfg.damping_c;
     res[p] = eval_pair<double>(pb.cfg, pb.shapes[g.i], pb.shapes[g.j], g, pos + 3 * g.i, quat + 4 * g.i, XB,
-                               quat + 4 * g.j, vel ? vel + 6 * g.i : nullptr, vel ? vel + 6 * g.j : nullptr, es, law);
+                               partner_quat(pb, g, quat), vel ? vel + 6 * g.i : nullptr, partner_vel(pb, g, vel), es, law);
   }
   if (force) std::memset(force, 0, sizeof(double) * 3 * n);
   if (torque) std::memset(torque, 0, sizeof(double) * 3 * n);
@@ -750,8 +836,10 @@ int64_t oracle_contact_step(const oracle_config* cfg, int32_t n, const int32_t* 
       for (int k = 0; k < 3; ++k) {
         force[3 * g.i + k] -= r.F[k];
         torque[3 * g.i + k] += r.TA[k];
-        force[3 * g.j + k] += r.F[k];
-        torque[3 * g.j + k] += r.TB[k];
+        if (g.j < n) {   // a wall takes no sum
+          force[3 * g.j + k] += r.F[k];
+          torque[3 * g.j + k] += r.TB[k];
+        }
       }
     if (p >= max_pairs) continue;
     if (pair_ij) { pair_ij[2 * p] = g.i; pair_ij[2 * p + 1] = g.j; }
@@ -841,7 +929,7 @@ int64_t oracle_contact_step_ext(const oracle_config* cfg, const oracle_contact_l
       }
     }
     res[p] = eval_pair<double>(pb.cfg, pb.shapes[g.i], pb.shapes[g.j], g, pos + 3 * g.i, quat + 4 * g.i, XB,
-                               quat + 4 * g.j, vel ? vel + 6 * g.i : nullptr, vel ? vel + 6 * g.j : nullptr, es, law);
+                               partner_quat(pb, g, quat), vel ? vel + 6 * g.i : nullptr, partner_vel(pb, g, vel), es, law);
   }
   if (force) std::memset(force, 0, sizeof(double) * 3 * n);
   if (torque) std::memset(torque, 0, sizeof(double) * 3 * n);
@@ -853,8 +941,10 @@ int64_t oracle_contact_step_ext(const oracle_config* cfg, const oracle_contact_l
       for (int k = 0; k < 3; ++k) {
         force[3 * g.i + k] -= r.F[k];
         torque[3 * g.i + k] += r.TA[k];
-        force[3 * g.j + k] += r.F[k];
-        torque[3 * g.j + k] += r.TB[k];
+        if (g.j < n) {   // a wall takes no sum
+          force[3 * g.j + k] += r.F[k];
+          torque[3 * g.j + k] += r.TB[k];
+        }
       }
     if (r.V > 0.0) {
       if (nh < max_hist) {
@@ -908,7 +998,8 @@ static int64_t gradient_impl(const oracle_config* cfg, const oracle_contact_law*
     for (int k = 0; k < 3; ++k) { XA[k] = Dual(pos[3 * g.i + k]); XA[k].g[k] = 1.0; }
     for (int k = 0; k < 4; ++k) { qA[k] = Dual(quat[4 * g.i + k]); qA[k].g[3 + k] = 1.0; }
     for (int k = 0; k < 3; ++k) { XB[k] = Dual(XBd[k]); XB[k].g[7 + k] = 1.0; }
-    for (int k = 0; k < 4; ++k) { qB[k] = Dual(quat[4 * g.j + k]); qB[k].g[10 + k] = 1.0; }
+    const double* qj = partner_quat(pb, g, quat);
+    for (int k = 0; k < 4; ++k) { qB[k] = Dual(qj[k]); qB[k].g[10 + k] = 1.0; }
     const double es = effective_modulus(pb.young[g.i], pb.poisson[g.i], pb.young[g.j], pb.poisson[g.j]);
     ContactLaw law;
     law.c = pb.cfg.damping_c;
@@ -923,11 +1014,11 @@ static int64_t gradient_impl(const oracle_config* cfg, const oracle_contact_law*
       }
     }
     PairResult<Dual> r = eval_pair<Dual>(pb.cfg, pb.shapes[g.i], pb.shapes[g.j], g, XA, qA, XB, qB,
-                                         vel ? vel + 6 * g.i : nullptr, vel ? vel + 6 * g.j : nullptr, es, law);
+                                         vel ? vel + 6 * g.i : nullptr, partner_vel(pb, g, vel), es, law);
     Dual L(0.0);
     for (int k = 0; k < 3; ++k) {
       L = L + grad_force[3 * g.i + k] * (-r.F[k]) + grad_torque[3 * g.i + k] * r.TA[k];
-      L = L + grad_force[3 * g.j + k] * r.F[k] + grad_torque[3 * g.j + k] * r.TB[k];
+      if (g.j < n) L = L + grad_force[3 * g.j + k] * r.F[k] + grad_torque[3 * g.j + k] * r.TB[k];
     }
     for (int t = 0; t < NT; ++t) pg[static_cast<size_t>(p) * NT + t] = L.g[t];
   }
@@ -938,6 +1029,7 @@ static int64_t gradient_impl(const oracle_config* cfg, const oracle_contact_law*
     const double* t = &pg[static_cast<size_t>(p) * NT];
     for (int k = 0; k < 3; ++k) grad_pos[3 * g.i + k] += t[k];
     for (int k = 0; k < 4; ++k) grad_quat[4 * g.i + k] += t[3 + k];
+    if (g.j >= n) continue;   // walls do not move
     for (int k = 0; k < 3; ++k) grad_pos[3 * g.j + k] += t[7 + k];
     for (int k = 0; k < 4; ++k) grad_quat[4 * g.j + k] += t[10 + k];
   }

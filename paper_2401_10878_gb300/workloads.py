@@ -49,6 +49,10 @@ class State:
     inflate: float = 0.0
     damping_c: float = 0.0
     info: dict = dataclasses.field(default_factory=dict)
+    # fixed walls (Sec. 4.3): half-spaces m . x <= h, one (m, h) row each, not periodic
+    walls: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 4)))
+    wall_young: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
+    wall_poisson: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
 
     @property
     def n(self) -> int:
