@@ -112,7 +112,21 @@ typedef struct {
   double mu_s, mu_k;        /* friction coefficients (mu_s > 0, mu_k >= 0)        */
   double u_k;               /* transition speed of the friction law (> 0), in the
                                caller's velocity units (the paper: 0.001 m/s)     */
+  int32_t n_walls;          /* fixed walls (Sec. 4.3), 0..CONTACT_MAX_WALLS: wall w
+                               is the half-space m . x <= h, not periodic (it is
+                               tested in the frame where the particle's centre lies
+                               in [0, L)); its contacts are pairs (i, N + w) and
+                               are evaluated like particle pairs, the wall at rest
+                               with the identity pose at the origin.  Forces and
+                               torques are reported for the particles only.       */
+  int32_t reserved;
+  const double* walls;      /* [n_walls,4] host, (m, h) with unit m pointing out of
+                               the wall; read by contact_init only                */
+  const double* wall_young; /* [n_walls] host, E of each wall (> 0)               */
+  const double* wall_poisson; /* [n_walls] host, nu of each wall (0 <= nu < 1)    */
 } contact_config;
+
+enum { CONTACT_MAX_WALLS = 64 };
 
 /* Fills *cfg with defaults (sharp indicator, w = 1, no inflation, FP32 tiles,
  * no contact history (restitution 1), no friction (mu_s = mu_k = 0, u_k = 1),
@@ -142,7 +156,8 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
  *   quat  [N,4] dev f64  (w, x, y, z), any non-zero norm
  *   vel   [N,6] dev f64  (u, omega) per particle, or NULL (then ddot_n = 0)
  * Outputs (dev, written on the context stream):
- *   pair_ij  [max_pairs,2] i32   candidate pairs (i < j) sorted by (i, j)
+ *   pair_ij  [max_pairs,2] i32   candidate pairs (i < j) sorted by (i, j); j >= N
+ *                                is wall j - N
  *   pair_out [max_pairs,11] f64  per pair: V, x_c[3], n[3], d, F[3]; F is the
  *                                force on j (-F acts on i), n points from i to
  *                                j, x_c is in i's frame (not wrapped)

@@ -514,7 +514,9 @@ struct Problem {
 // Node box of particle range [lo, hi] against the wall m . x <= h widened by
 // delta: empty (false) when even the range's lowest corner in m has
 // m . x > h + delta; else the range clipped, per axis with m_k != 0, to the
-// nodes that some node of the range with that coordinate keeps inside.
+// nodes that some node of the range with that coordinate keeps inside (and
+// false if rounding leaves no node).  Plain FP64 operations in this order,
+// no contraction: the box is compared bit for bit.
 bool wall_box(const Config& c, const double* e, double delta, const int* lo_in, const int* hi_in, int lo[3],
               int hi[3]) {
   const double H = e[3] + delta;
@@ -536,7 +538,7 @@ bool wall_box(const Config& c, const double* e, double delta, const int* lo_in, 
       if (b > lo[k]) lo[k] = static_cast<int>(std::ceil(b));
     }
   }
-  return true;
+  return lo[0] <= hi[0] && lo[1] <= hi[1] && lo[2] <= hi[2];   // rounding may leave no node
 }
 
 int build_problem(Problem& pb, const Config* cfg, int32_t n, const int32_t* shape_type,

@@ -42,7 +42,8 @@ class Config(ctypes.Structure):
                 ("max_tiles", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("narrow_events", ctypes.c_int32), ("history", ctypes.c_int32), ("friction", ctypes.c_int32),
                 ("restitution", ctypes.c_double), ("mu_s", ctypes.c_double), ("mu_k", ctypes.c_double),
-                ("u_k", ctypes.c_double)]
+                ("u_k", ctypes.c_double), ("n_walls", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("walls", ctypes.c_void_p), ("wall_young", ctypes.c_void_p), ("wall_poisson", ctypes.c_void_p)]
 
 
 class ContactError(RuntimeError):
@@ -134,7 +135,7 @@ class Contact:
                  indicator=SHARP, smooth_width=1.0, inflate=0.0, damping_c=0.0, precision=FP32_TILE,
                  max_pairs=None, max_neighbors=64, max_tiles=0, use_graph=True, narrow_events=False,
                  history=False, restitution=1.0, friction=False, mu_s=0.0, mu_k=0.0, u_k=1.0,
-                 device=None, stream=None):
+                 walls=None, wall_young=None, wall_poisson=None, device=None, stream=None):
         if not torch.cuda.is_available():
             raise ContactError(ECUDA, "no CUDA device: the contact path has no CPU fallback")
         self.lib = load_library()
@@ -147,6 +148,17 @@ class Contact:
         cfg.damping_c, cfg.precision = float(damping_c), int(precision)
         cfg.history, cfg.restitution = int(bool(history)), float(restitution)
         cfg.friction, cfg.mu_s, cfg.mu_k, cfg.u_k = int(bool(friction)), float(mu_s), float(mu_k), float(u_k)
+        wall_arrs = ()
+        if walls is not None and len(walls):
+            # fixed walls (m, h): read by contact_init only, alive until it returns
+            wall_arrs = (np.ascontiguousarray(walls, dtype=np.float64).reshape(-1, 4),
+                         np.ascontiguousarray(wall_young, dtype=np.float64).reshape(-1),
+                         np.ascontiguousarray(wall_poisson, dtype=np.float64).reshape(-1))
+            if not (len(wall_arrs[1]) == len(wall_arrs[2]) == len(wall_arrs[0])):
+                raise ContactError(EINVAL, "walls, wall_young and wall_poisson differ in length")
+            cfg.n_walls = len(wall_arrs[0])
+            cfg.walls, cfg.wall_young, cfg.wall_poisson = (a.ctypes.data for a in wall_arrs)
+        self.n_walls = int(cfg.n_walls)
         if max_pairs is not None:
             cfg.max_pairs = int(max_pairs)
         cfg.max_neighbors, cfg.max_tiles, cfg.use_graph = int(max_neighbors), int(max_tiles), int(bool(use_graph))
@@ -177,7 +189,8 @@ class Contact:
     def from_state(cls, st, **kw):
         """Context for a workloads.State (shapes, material, lattice, indicator)."""
         args = dict(indicator=st.indicator, smooth_width=st.smooth_width, inflate=st.inflate,
-                    damping_c=st.damping_c)
+                    damping_c=st.damping_c, walls=getattr(st, "walls", None),
+                    wall_young=getattr(st, "wall_young", None), wall_poisson=getattr(st, "wall_poisson", None))
         args.update(kw)
         return cls(st.shape_type, st.shape_param, st.face_offset, st.planes, st.young, st.poisson, st.n_cells,
                    st.dx, **args)

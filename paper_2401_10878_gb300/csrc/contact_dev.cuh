@@ -18,7 +18,7 @@ namespace gbc {
 // Sweep kinds: polytopes with up to 20 faces keep their face values in
 // registers (padded to 20); larger ones (up to 32) read planes from shared memory.
 // Cubes (equal half extents) have their own kind: max|y| - h needs no per-axis offset.
-enum Kind : int { KIND_SPHERE = 0, KIND_CUBOID = 1, KIND_POLY = 2, KIND_POLYG = 3, KIND_CUBE = 4 };
+enum Kind : int { KIND_SPHERE = 0, KIND_CUBOID = 1, KIND_POLY = 2, KIND_POLYG = 3, KIND_CUBE = 4, KIND_WALL = 5 };
 constexpr int kRegFaces = 20;
 
 constexpr int kMaxFaces = 32;         // faces of one polytope
@@ -52,6 +52,8 @@ struct Params {
   int kind_set;          // node-sweep variant: 0 all kinds, 1 spheres and cuboids, 2 cubes only
   int dx_pow2;           // 1: dx is a power of two, so x / dx == x * inv_dx exactly
   double damping_c;
+  int nwall;             // fixed walls: partner indices n .. n + nwall - 1
+  const double* wall;    // [nwall,4] (m, h): the half-space m . x <= h
   int history, friction;  // contact history; tangential force
   double damp_K;         // history: c = damp_K / u0 at a contact's first step (u0 > 0)
   double mu_s_star, mu_k, inv_u_k;   // friction law
@@ -64,7 +66,8 @@ struct Params {
   float inflate_l, inv_w, neg6_over_w, wdx_l;   // wdx_l: smoothing width in cells
 };
 
-// Shape tables (read-only after contact_init).
+// Shape tables (read-only after contact_init); rows N .. N + nwall - 1 are
+// the walls, one-plane polytopes (the plane in the world frame).
 struct Shapes {
   const int* type;         // [N] CONTACT_SHAPE_*
   const double* param;     // [N,3]
@@ -82,7 +85,8 @@ struct Shapes {
   const float* off32;      // [F] (d + inflate) / dx per face, FP32
 };
 
-// Per-step particle records.
+// Per-step particle records; rows N .. N + nwall - 1 are the walls (set once:
+// X = 0, R = I, Rt row 0 = the wall normal m, kX = fX = 0).
 struct Parts {
   double* X;       // [N,3] copy of the positions of the step
   double* qhat;    // [N,4] the step's quaternion as given (normalised by the adjoint)
@@ -94,6 +98,7 @@ struct Parts {
   float* Xf;       // [N,3] FP32 positions (periodic image choice only)
   int* kX;         // [N,3] nearest node of X / dx
   float* fX;       // [N,3] X / dx - kX, in [-1/2, 1/2] (FP64 difference, rounded once)
+  const double* rest6;   // [6] zeros: the velocity of a wall
 };
 
 // One candidate pair (i < j).
@@ -121,6 +126,38 @@ struct __align__(16) PairRec {   // 16-byte aligned: records are copied with 16-
 };
 constexpr int kPairRecWords = sizeof(PairRec) / 4;
 static_assert(sizeof(PairRec) % 16 == 0, "PairRec is staged with 16-byte copies");
+
+// Node box of particle node range [lo_in, hi_in] against the wall m . x <= h
+// widened by delta (e = (m, h)): false when even the range's lowest corner in
+// m lies beyond h + delta, or when the clip leaves no node; else the range
+// clipped, per axis with m_k != 0, to the nodes that some node of the range
+// with that coordinate keeps inside.  Rounded FP64 operations in a fixed
+// order (no contraction), so that the box is reproducible bit for bit.
+__device__ __forceinline__ bool wall_box(const double* e, double delta, double dx, const int* lo_in,
+                                         const int* hi_in, int lo[3], int hi[3]) {
+  const double H = __dadd_rn(e[3], delta);
+  double t[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int ck = e[k] > 0.0 ? lo_in[k] : hi_in[k];
+    t[k] = __dmul_rn(e[k], __dmul_rn(static_cast<double>(ck), dx));
+    lo[k] = lo_in[k];
+    hi[k] = hi_in[k];
+  }
+  if (!(__dadd_rn(__dadd_rn(t[0], t[1]), t[2]) <= H)) return false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (e[k] == 0.0) continue;
+    const double rest = k == 0 ? __dadd_rn(t[1], t[2]) : (k == 1 ? __dadd_rn(t[0], t[2]) : __dadd_rn(t[0], t[1]));
+    const double b = __ddiv_rn(__ddiv_rn(__dsub_rn(H, rest), e[k]), dx);
+    if (e[k] > 0.0) {
+      if (b < hi[k]) hi[k] = static_cast<int>(floor(b));
+    } else {
+      if (b > lo[k]) lo[k] = static_cast<int>(ceil(b));
+    }
+  }
+  return lo[0] <= hi[0] && lo[1] <= hi[1] && lo[2] <= hi[2];
+}
 
 // Work lists shared by the step's kernels.
 // One overlapping pair for the force law (staged in shared memory by the warp

@@ -28,6 +28,8 @@ struct ForceArgs {
   double* tape;
   double L[3];
   double dx, dx3, gscale, g_min2, inflate, damping_c;
+  int n;                 // particles: a partner j >= n is wall j - n (at rest, fallback normal -m)
+  const double* rest6;   // [6] zeros, the velocity of a wall
   // contact history (Sec. 4.3.3): last step's contacts of each particle i
   // (partner j, damping factor c) are read from *_rd, this step's go to *_wr
   int history, friction, hist_cap;
@@ -186,7 +188,7 @@ __device__ __forceinline__ void pair_force_law(ForceArgs a, const OvlRec* e, int
     const double xck = fma(sm[1 + kc], inv_s0, int_to_double(lok)) * a.dx;
     double nk = Gk * y2;
     double fallback = 0.0;
-    if (__any_sync(kFull, act && !gok)) {   // centre-line fallback normal
+    if (__any_sync(kFull, act && !gok)) {   // centre-line fallback normal (a wall: -m)
       const double dXk = XB - XA;
       const double e0v = __shfl_sync(kFull, dXk, b0), e1v = __shfl_sync(kFull, dXk, b0 + 1),
                      e2v = __shfl_sync(kFull, dXk, b0 + 2);
@@ -194,6 +196,7 @@ __device__ __forceinline__ void pair_force_law(ForceArgs a, const OvlRec* e, int
         fallback = 1.0;
         const double nd2 = fma(e2v, e2v, fma(e1v, e1v, e0v * e0v));
         nk = __double_as_longlong(nd2) > 0 ? dXk * nr_rsqrt(nd2) : 0.0;
+        if (j >= a.n) nk = -a.planes[4 * fb0 + kc];
       }
     }
     const double gn = gok ? gn2 * y2 : 0.0;
@@ -207,7 +210,7 @@ __device__ __forceinline__ void pair_force_law(ForceArgs a, const OvlRec* e, int
     double uabk = 0.0, ddot = 0.0;
     if (a.vel != nullptr && (a.damping_c != 0.0 || a.history || a.friction)) {
       const double* va = a.vel + 6 * i;
-      const double* vb = a.vel + 6 * j;
+      const double* vb = j < a.n ? a.vel + 6 * j : a.rest6;
       const double wak = fma(va[3 + k1], ra2v, -va[3 + k2] * ra1v);
       const double wbk = fma(vb[3 + k1], rb2v, -vb[3 + k2] * rb1v);
       uabk = (va[kc] + wak) - (vb[kc] + wbk);

@@ -198,6 +198,11 @@ void contact_config_default(contact_config* cfg, int32_t n_particles, const int3
   cfg->mu_s = 0.0;
   cfg->mu_k = 0.0;
   cfg->u_k = 1.0;
+  cfg->n_walls = 0;
+  cfg->reserved = 0;
+  cfg->walls = nullptr;
+  cfg->wall_young = nullptr;
+  cfg->wall_poisson = nullptr;
 }
 
 double contact_damping_factor(double e, double u0) {
@@ -228,6 +233,16 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   if (C.friction && (!(C.mu_s > 0.0) || !(C.mu_k >= 0.0) || !(C.u_k > 0.0) || !std::isfinite(C.mu_s) ||
                      !std::isfinite(C.mu_k) || !std::isfinite(C.u_k)))
     return CONTACT_EINVAL;
+  const int nw = C.n_walls;
+  if (nw < 0 || nw > CONTACT_MAX_WALLS) return CONTACT_EINVAL;
+  if (nw > 0 && (C.walls == nullptr || C.wall_young == nullptr || C.wall_poisson == nullptr)) return CONTACT_EINVAL;
+  for (int w = 0; w < nw; ++w) {
+    const double* e = C.walls + 4 * w;
+    const double nn = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    if (!(std::fabs(nn - 1.0) <= 1e-9) || !std::isfinite(e[3])) return CONTACT_EINVAL;
+    if (!(C.wall_young[w] > 0.0) || !(C.wall_poisson[w] >= 0.0) || !(C.wall_poisson[w] < 1.0))
+      return CONTACT_EINVAL;
+  }
   const int max_nbr = C.max_neighbors > 0 ? C.max_neighbors : 64;
   const long long max_tiles_ll = C.max_tiles > 0 ? C.max_tiles : 8LL * C.max_pairs;
   if (max_tiles_ll > (1LL << 30)) return CONTACT_EINVAL;
@@ -296,6 +311,18 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
     vert_off[p + 1] = static_cast<int>(verts.size() / 3);
     rmax = std::max(rmax, circ);
   }
+  // walls: rows n .. n + nw - 1 of the shape tables, one world-frame plane each
+  for (int w = 0; w < nw; ++w) {
+    type.push_back(CONTACT_SHAPE_POLYTOPE);
+    kind.push_back(KIND_WALL);
+    for (int k = 0; k < 3; ++k) {
+      param.push_back(0.0);
+      ext.push_back(0.0);
+      size_l.push_back(0.f);
+    }
+    nomops.push_back(4);   // one plane
+    vert_off.push_back(vert_off.back());
+  }
   double L[3];
   for (int k = 0; k < 3; ++k) {
     L[k] = C.n_cells[k] * C.dx;
@@ -334,9 +361,12 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   P.g_min2 = 1e-24 * C.dx * C.dx * C.dx * C.dx;
   P.smooth = C.indicator;
   P.precision = C.precision;
-  P.kind_set = std::all_of(kind.begin(), kind.end(), [](int k) { return k == KIND_CUBE; }) ? 2
-               : std::all_of(kind.begin(), kind.end(),
+  // node-sweep variant from the particle kinds; walls need a variant with the wall evaluator
+  P.kind_set = std::all_of(kind.begin(), kind.begin() + n, [](int k) { return k == KIND_CUBE; }) ? 2
+               : std::all_of(kind.begin(), kind.begin() + n,
                              [](int k) { return k == KIND_SPHERE || k == KIND_CUBOID || k == KIND_CUBE; }) ? 1 : 0;
+  if (nw > 0 && P.kind_set == 2) P.kind_set = 1;
+  P.nwall = nw;
   P.damping_c = C.damping_c;
   P.history = C.history;
   P.friction = C.friction;
@@ -358,6 +388,16 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   std::vector<int> foff(face_offset, face_offset + n + 1);
   std::vector<double> yv(young, young + n), pv(poisson, poisson + n), cv(n);
   for (int p = 0; p < n; ++p) cv[p] = (1.0 - poisson[p] * poisson[p]) / young[p];
+  std::vector<double> wall_tab(C.walls ? C.walls : nullptr, C.walls ? C.walls + 4 * static_cast<size_t>(nw) : nullptr);
+  for (int w = 0; w < nw; ++w) {
+    pl_vec.insert(pl_vec.end(), C.walls + 4 * w, C.walls + 4 * w + 4);
+    foff.push_back(foff.back() + 1);
+    yv.push_back(C.wall_young[w]);
+    pv.push_back(C.wall_poisson[w]);
+    cv.push_back((1.0 - C.wall_poisson[w] * C.wall_poisson[w]) / C.wall_young[w]);
+  }
+  const int nrows = n + nw;             // particle rows, then wall rows
+  const int nplanes = nfaces + nw;      // particle faces, then one plane per wall
   int *d_type, *d_foff, *d_voff, *d_kind;
   double *d_param, *d_planes, *d_verts, *d_young, *d_pois;
   float* d_size;
@@ -383,8 +423,8 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   GBC_TRY(upload(c, &d_size, size_l));
   GBC_TRY(upload(c, &d_nomops, nomops));
   GBC_TRY(upload(c, &d_compl, cv));
-  std::vector<float> verts32(verts.begin(), verts.end()), off32(static_cast<size_t>(std::max(nfaces, 1)), 0.f);
-  for (int f = 0; f < nfaces; ++f) off32[f] = static_cast<float>((planes[4 * f + 3] + C.inflate) / C.dx);
+  std::vector<float> verts32(verts.begin(), verts.end()), off32(static_cast<size_t>(std::max(nplanes, 1)), 0.f);
+  for (int f = 0; f < nplanes; ++f) off32[f] = static_cast<float>((pl_vec[4 * f + 3] + C.inflate) / C.dx);
   double* d_ext;
   float *d_verts32, *d_off32;
   GBC_TRY(upload(c, &d_ext, ext));
@@ -394,16 +434,47 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
                 d_ext, d_verts32, d_off32};
 
   Parts& D = c->D;
-  GBC_TRY(dev_alloc(c, &D.X, 3 * static_cast<size_t>(n)));
+  GBC_TRY(dev_alloc(c, &D.X, 3 * static_cast<size_t>(nrows)));
   GBC_TRY(dev_alloc(c, &D.qhat, 4 * static_cast<size_t>(n)));
-  GBC_TRY(dev_alloc(c, &D.R, 9 * static_cast<size_t>(n)));
-  GBC_TRY(dev_alloc(c, &D.lohi, 6 * static_cast<size_t>(n)));
+  GBC_TRY(dev_alloc(c, &D.R, 9 * static_cast<size_t>(nrows)));
+  GBC_TRY(dev_alloc(c, &D.lohi, 6 * static_cast<size_t>(nrows)));
   GBC_TRY(dev_alloc(c, &D.bin, static_cast<size_t>(n)));
-  GBC_TRY(dev_alloc(c, &D.Rt, 9 * static_cast<size_t>(n)));
-  GBC_TRY(dev_alloc(c, &D.wplane, static_cast<size_t>(std::max(nfaces, 1))));
-  GBC_TRY(dev_alloc(c, &D.Xf, 3 * static_cast<size_t>(n)));
-  GBC_TRY(dev_alloc(c, &D.kX, 3 * static_cast<size_t>(n)));
-  GBC_TRY(dev_alloc(c, &D.fX, 3 * static_cast<size_t>(n)));
+  GBC_TRY(dev_alloc(c, &D.Rt, 9 * static_cast<size_t>(nrows)));
+  GBC_TRY(dev_alloc(c, &D.wplane, static_cast<size_t>(std::max(nplanes, 1))));
+  GBC_TRY(dev_alloc(c, &D.Xf, 3 * static_cast<size_t>(nrows)));
+  GBC_TRY(dev_alloc(c, &D.kX, 3 * static_cast<size_t>(nrows)));
+  GBC_TRY(dev_alloc(c, &D.fX, 3 * static_cast<size_t>(nrows)));
+  {
+    double* rest = nullptr;
+    GBC_TRY(dev_alloc(c, &rest, 8));
+    GBC_TRY(cudaMemset(rest, 0, 8 * sizeof(double)));
+    D.rest6 = rest;
+  }
+  if (nw > 0) {   // wall rows: at the origin, identity rotation, Rt row 0 = m, world plane
+    std::vector<double> X0(3 * static_cast<size_t>(nw), 0.0), R0(9 * static_cast<size_t>(nw), 0.0);
+    std::vector<float> Rt0(9 * static_cast<size_t>(nw), 0.f), f0(3 * static_cast<size_t>(nw), 0.f);
+    std::vector<int> k0(3 * static_cast<size_t>(nw), 0), lohi0(6 * static_cast<size_t>(nw), 0);
+    std::vector<float4> wp(nw);
+    for (int w = 0; w < nw; ++w) {
+      R0[9 * w] = R0[9 * w + 4] = R0[9 * w + 8] = 1.0;
+      for (int k = 0; k < 3; ++k) Rt0[9 * w + k] = static_cast<float>(C.walls[4 * w + k]);
+      wp[w] = make_float4(static_cast<float>(C.walls[4 * w]), static_cast<float>(C.walls[4 * w + 1]),
+                          static_cast<float>(C.walls[4 * w + 2]), off32[nfaces + w]);
+    }
+    const size_t o3 = 3 * static_cast<size_t>(n), o9 = 9 * static_cast<size_t>(n);
+    GBC_TRY(cudaMemcpy(D.X + o3, X0.data(), sizeof(double) * X0.size(), cudaMemcpyHostToDevice));
+    GBC_TRY(cudaMemcpy(D.R + o9, R0.data(), sizeof(double) * R0.size(), cudaMemcpyHostToDevice));
+    GBC_TRY(cudaMemcpy(D.Rt + o9, Rt0.data(), sizeof(float) * Rt0.size(), cudaMemcpyHostToDevice));
+    GBC_TRY(cudaMemcpy(D.Xf + o3, f0.data(), sizeof(float) * f0.size(), cudaMemcpyHostToDevice));
+    GBC_TRY(cudaMemcpy(D.fX + o3, f0.data(), sizeof(float) * f0.size(), cudaMemcpyHostToDevice));
+    GBC_TRY(cudaMemcpy(D.kX + o3, k0.data(), sizeof(int) * k0.size(), cudaMemcpyHostToDevice));
+    GBC_TRY(cudaMemcpy(D.lohi + 6 * static_cast<size_t>(n), lohi0.data(), sizeof(int) * lohi0.size(),
+                       cudaMemcpyHostToDevice));
+    GBC_TRY(cudaMemcpy(D.wplane + nfaces, wp.data(), sizeof(float4) * wp.size(), cudaMemcpyHostToDevice));
+    double* d_wall = nullptr;
+    GBC_TRY(upload(c, &d_wall, wall_tab));
+    P.wall = d_wall;
+  }
 
   Lists& W = c->W;
   const size_t nbins = static_cast<size_t>(P.nbin[0]) * P.nbin[1] * P.nbin[2];

@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(32) k_adj_pre(Params P, Shapes S, Parts D, Lis
       F[k] = fmag * n[k];
       rA[k] = xc[k] - XA[k];
       rB[k] = xc[k] - XB[k];
-      gFi[k] = gF[3 * i + k]; gFj[k] = gF[3 * j + k];
-      gTi[k] = gT[3 * i + k]; gTj[k] = gT[3 * j + k];
+      gFi[k] = gF[3 * i + k]; gFj[k] = j < P.n ? gF[3 * j + k] : 0.0;   // a wall has no output
+      gTi[k] = gT[3 * i + k]; gTj[k] = j < P.n ? gT[3 * j + k] : 0.0;
     }
     const double d = tp[7], gnorm = tp[8], estar = tp[10], damp = tp[11];
     // c of Eq. (damping_factor) as the forward used it (the shared one, or the
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(32) k_adj_pre(Params P, Shapes S, Parts D, Lis
     // relative velocity u_AB = (v_A + w_A x r_A) - (v_B + w_B x r_B) at x_c, ddot_n = u_AB . n
     double uab[3] = {0.0, 0.0, 0.0}, ddot = 0.0;
     const double* va = vel != nullptr ? vel + 6 * i : nullptr;
-    const double* vb = vel != nullptr ? vel + 6 * j : nullptr;
+    const double* vb = vel != nullptr ? (j < P.n ? vel + 6 * j : D.rest6) : nullptr;
     if (vel != nullptr && fmag > 0.0 && (cdamp != 0.0 || P.friction)) {
       double wa[3], wb[3];
       cross3(va + 3, rA, wa);
@@ -227,9 +227,22 @@ struct AdjGeom {
   const float4* sp;  // world planes (x, y, z, offset) in shared memory
 };
 
+// A wall (pid >= n) is type 3: phi = m . c + p0 at box-relative node c, with
+// m from Rt row 0 and p0 from the pair record's size slot (wall_p0).
 __device__ __forceinline__ void adj_load(const Shapes& S, const Parts& D, int pid, const int* ci, const float* cf,
-                                         float4* sm, AdjGeom& g) {
+                                         float4* sm, AdjGeom& g, int n, float wall_p0) {
   const int lane = threadIdx.x & 31;
+  if (pid >= n) {
+    g.type = 3;
+    for (int k = 0; k < 3; ++k) {
+      g.c[k] = 0.f;
+      g.size[k] = wall_p0;
+    }
+    for (int k = 0; k < 9; ++k) g.rt[k] = D.Rt[9 * pid + k];
+    g.nf = 0;
+    g.sp = sm;
+    return;
+  }
   g.type = S.type[pid];
   for (int k = 0; k < 3; ++k) {
     g.c[k] = static_cast<float>(ci[k]) + cf[k];
@@ -257,6 +270,10 @@ __device__ __forceinline__ float adj_eval(const AdjGeom& g, const float r[3], fl
     return nr - g.size[0];
   }
   *rn = 0.f;
+  if (g.type == 3) {   // wall
+    for (int k = 0; k < 3; ++k) gr[k] = g.rt[k];
+    return fmaf(g.rt[0], r[0], fmaf(g.rt[1], r[1], fmaf(g.rt[2], r[2], g.size[0])));
+  }
   if (g.type == 1) {
     float y[3], a[3];
     for (int k = 0; k < 3; ++k) {
@@ -285,6 +302,7 @@ __device__ __forceinline__ float adj_eval(const AdjGeom& g, const float r[3], fl
 // phi alone (the same arithmetic as adj_eval, without the gradient): the band test
 __device__ __forceinline__ float adj_phi(const AdjGeom& g, const float r[3]) {
   if (g.type == 0) return sqrtf(fmaf(r[0], r[0], fmaf(r[1], r[1], r[2] * r[2]))) - g.size[0];
+  if (g.type == 3) return fmaf(g.rt[0], r[0], fmaf(g.rt[1], r[1], fmaf(g.rt[2], r[2], g.size[0])));
   if (g.type == 1) {
     float best = -FLT_MAX;
 #pragma unroll
@@ -450,6 +468,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
     const int t = prg.tile0 + prg.tile;   // the tile's index (its partial slot)
     const int rec_i = prg.i, rec_j = prg.j, axis = prg.axis, nseg = prg.nseg, seglen = prg.seglen;
     const int nitems = prg.nitems, tile0 = prg.tile0;
+    const float wall_p0 = prg.szb[0];   // used when j is a wall
     const int dm0 = prg.dim[0], dm1 = prg.dim[1], dm2 = prg.dim[2];
     int ai[3], bi[3];
     float af[3], bf[3];
@@ -466,8 +485,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
                         (sg[1] != 0.f) || (sg[2] != 0.f) || (B.pgrad[static_cast<size_t>(p) * kPairGrad + 12] != 0.0);
     if (active) {
       AdjGeom A, Bg;
-      adj_load(S, D, rec_i, ai, af, s_pl[wid][0], A);
-      adj_load(S, D, rec_j, bi, bf, s_pl[wid][1], Bg);
+      adj_load(S, D, rec_i, ai, af, s_pl[wid][0], A, P.n, 0.f);
+      adj_load(S, D, rec_j, bi, bf, s_pl[wid][1], Bg, P.n, wall_p0);
       const int ax0 = axis;
       const int du = ax0 == 0 ? dm0 : (ax0 == 1 ? dm1 : dm2);
       const int dv = ax0 == 0 ? dm1 : (ax0 == 1 ? dm2 : dm0);   // side along (ax0 + 1) mod 3

@@ -306,6 +306,35 @@ __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
       ndn += __popc(bd);
     }
   }
+  // walls (partners n + w, after every particle): lane w tests wall w with an
+  // FP32 prefilter, then exactly in FP64 (the node box must be non-empty)
+  for (int w0 = 0; w0 < P.nwall; w0 += 32) {
+    const int w = w0 + lane;
+    bool hit = false;
+    if (w < P.nwall) {
+      const double* e = P.wall + 4 * w;
+      const float m0 = static_cast<float>(e[0]), m1 = static_cast<float>(e[1]), m2 = static_cast<float>(e[2]);
+      const float dxf = static_cast<float>(P.dx);
+      const float t0 = m0 * static_cast<float>(m0 > 0.f ? plo[0] : phi[0]);
+      const float t1 = m1 * static_cast<float>(m1 > 0.f ? plo[1] : phi[1]);
+      const float t2 = m2 * static_cast<float>(m2 > 0.f ? plo[2] : phi[2]);
+      const float lowest = (t0 + t1 + t2) * dxf;
+      const float H = static_cast<float>(e[3] + P.delta);
+      // the FP32 error of `lowest` is below 1e-6 of its terms' magnitudes:
+      // walls beyond 1e-4 of them skip the exact FP64 test
+      const float mag = (fabsf(t0) + fabsf(t1) + fabsf(t2)) * dxf + fabsf(H) + dxf;
+      if (lowest <= H + 1e-4f * mag) {
+        int lo[3], hi[3];
+        hit = wall_box(e, P.delta, P.dx, plo, phi, lo, hi);
+      }
+    }
+    const unsigned bw = __ballot_sync(kFull, hit);
+    if (hit) {
+      const int at = nup + __popc(bw & below);
+      if (at < cap) up[at] = P.n + w;
+    }
+    nup += __popc(bw);
+  }
   if (nup > cap || ndn > cap) {
     if (lane == 0) set_error(W.err, kErrCapacity);
     nup = min(nup, cap);
@@ -419,15 +448,27 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
     if (active) {
       pi = row + r;
       const int j = base == 0 ? jpre : W.up_list[static_cast<size_t>(i) * cap + r];
-      // j's lower-partner list, fetched with j's particle data (slot of this pair below)
-      const int* dl = W.dn_list + static_cast<size_t>(j) * cap;
-      const int dc = W.dn_count[j];
+      // j's lower-partner list, fetched with j's particle data (slot of this pair below);
+      // a wall (j >= n) has none
+      const bool wall = j >= P.n;
+      const int* dl = W.dn_list + static_cast<size_t>(wall ? 0 : j) * cap;
+      const int dc = wall ? 0 : W.dn_count[j];
       int dpre[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) dpre[u] = u < cap ? dl[u] : 0;
       int lo[3], hi[3];
-      int shift[3];
-      pair_box(P, D, i, j, shift, lo, hi);
+      int shift[3] = {0, 0, 0};
+      if (wall) {
+        int plo[3], phi[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          plo[k] = D.lohi[6 * i + k];
+          phi[k] = D.lohi[6 * i + 3 + k];
+        }
+        wall_box(P.wall + 4 * (j - P.n), P.delta, P.dx, plo, phi, lo, hi);   // non-empty (tested by the broad phase)
+      } else {
+        pair_box(P, D, i, j, shift, lo, hi);
+      }
 #pragma unroll
       for (int k = 0; k < 3; ++k) pr.shift[k] = shift[k];
       pr.i = i;
@@ -490,6 +531,17 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
         pr.sza[k] = S.size_l[3 * i + k];
         pr.szb[k] = S.size_l[3 * j + k];
       }
+      if (wall) {   // the wall's value at the box origin, m . lo - (h + inflate) / dx (lattice
+                    // units), and its origin at the box origin (node offsets are box-relative)
+        const double* e = P.wall + 4 * (j - P.n);
+        const double p0 = ((e[0] * lo[0] + e[1] * lo[1]) + e[2] * lo[2]) - (e[3] + P.inflate) * P.inv_dx;
+        pr.szb[0] = static_cast<float>(p0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          pr.bi[k] = 0;
+          pr.bf[k] = 0.f;
+        }
+      }
       pr.tile = 0;
       pr.pair = pi;
       W.pdone[pi] = 0;
@@ -502,7 +554,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
 #pragma unroll
       for (int u = 0; u < 8; ++u) a0 += (u < dc && dpre[u] < i) ? 1 : 0;
       for (int b = 8; b < dc; ++b) a0 += dl[b] < i ? 1 : 0;
-      W.dn_pair[static_cast<size_t>(j) * cap + a0] = pi;
+      if (!wall) W.dn_pair[static_cast<size_t>(j) * cap + a0] = pi;
     }
     // allocations aggregated over the block (one atomic per counter and
     // block, all in flight together): the pairs' tiles (partials,

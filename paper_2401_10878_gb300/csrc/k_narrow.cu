@@ -354,6 +354,37 @@ struct PolyGEval {
   __device__ float world(int c, const Local& L, const PairRec&, bool) const { return world_comp(c, L, gu, gv, gw); }
 };
 
+// Fixed wall m . x <= h: phi = m . c + p0 at box-relative node c (lattice
+// units; p0 = the value at the box origin, inflate included, computed in
+// FP64 by the pair builder and kept in the record's size slot; the record's
+// centre of a wall is the box origin).  Box-relative values stay small, so
+// FP32 keeps them to ~1e-6.
+struct WallEval {
+  float mu_, mv_, mw_, p0;
+  float base, cnt_u, g;
+  __device__ void load(const PairRec& r, bool second, const Shapes&, const Parts&, const Local& L, float4*) {
+    const float* rt = second ? r.rtb : r.rta;   // row 0: the wall normal m (world)
+    mu_ = rt[L.u]; mv_ = rt[L.v]; mw_ = rt[L.w];
+    p0 = second ? r.szb[0] : r.sza[0];
+    g = 0.f;
+  }
+  __device__ __forceinline__ void begin_line(int cv, int cw, int u0) {
+    base = fmaf(mv_, static_cast<float>(cv), fmaf(mw_, static_cast<float>(cw), p0));
+    cnt_u = static_cast<float>(u0) - 1.f;
+  }
+  __device__ __forceinline__ float counter() const { return cnt_u; }
+  __device__ __forceinline__ int origin() const { return 0; }
+  __device__ __forceinline__ float phi() {
+    cnt_u += 1.f;
+    return fmaf(mu_, cnt_u, base);
+  }
+  __device__ __forceinline__ void grad(float m) { g += m; }
+  __device__ __forceinline__ void end_line() {}
+  __device__ float world(int c, const Local&, const PairRec& r, bool second) const {
+    return (second ? r.rtb : r.rta)[c] * g;
+  }
+};
+
 // Line start of an evaluator: from the shared-memory record when the
 // evaluator re-reads its cross-axis terms there, else from its registers.
 template <class E>
@@ -524,6 +555,7 @@ __device__ __forceinline__ void flush_overlaps(const Params& P, const Shapes& S,
   a.dx = P.dx; a.dx3 = P.dx3; a.gscale = P.gscale; a.g_min2 = P.g_min2; a.inflate = P.inflate;
   a.damping_c = P.damping_c;
   a.history = P.history; a.friction = P.friction; a.hist_cap = P.max_nbr;
+  a.n = P.n; a.rest6 = D.rest6;
   a.damp_K = P.damp_K; a.mu_s_star = P.mu_s_star; a.mu_k = P.mu_k; a.inv_u_k = P.inv_u_k;
   if (P.history) {   // buffer (steps & 1) holds the previous step's contacts
     const int rd = W.counters[kStepCounter] & 1;
@@ -633,8 +665,8 @@ enum KindSet : int { SET_ALL = 0, SET_SC = 1, SET_CUBE = 2 };
 template <bool SMOOTH, int SET, class Pre>
 __device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, const Parts& D, const PairRec& r,
                                             int tl, float4* smA, float4* smB, Pre& pre) {
-  // kind order for canonical pairs: sphere < cube < cuboid < polytope < large polytope
-  constexpr int rank[5] = {0, 2, 3, 4, 1};
+  // kind order for canonical pairs: wall < sphere < cube < cuboid < polytope < large polytope
+  constexpr int rank[6] = {1, 3, 4, 5, 2, 0};
   int ka = r.kinds & 0xff, kb = r.kinds >> 8;
   const bool swap = rank[ka] > rank[kb];   // evaluate the cheaper kind as A; G's sign flips back below
   if (swap) {
@@ -659,6 +691,9 @@ __device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, co
       GBC_CASE(4, 4, CubeEval, CubeEval)
       GBC_CASE(4, 1, CubeEval, CuboidEval)
       GBC_CASE(1, 1, CuboidEval, CuboidEval)
+      GBC_CASE(5, 0, WallEval, SphereEval)
+      GBC_CASE(5, 4, WallEval, CubeEval)
+      GBC_CASE(5, 1, WallEval, CuboidEval)
       default:
         pre();
         break;
@@ -675,6 +710,10 @@ __device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, co
       GBC_CASE(2, 2, PolyEval<kRegFaces>, PolyEval<kRegFaces>)
       GBC_CASE(2, 3, PolyEval<kRegFaces>, PolyGEval)
       GBC_CASE(3, 3, PolyGEval, PolyGEval)
+      GBC_CASE(5, 0, WallEval, SphereEval)
+      GBC_CASE(5, 1, WallEval, CuboidEval)
+      GBC_CASE(5, 2, WallEval, PolyEval<kRegFaces>)
+      GBC_CASE(5, 3, WallEval, PolyGEval)
       default:
         pre();
         break;

@@ -404,6 +404,25 @@ def resolution_sweep(edge: int, seed: int = 5, n: int = 500, phi: float = 0.20,
     return st
 
 
+def with_walls(state: State, walls, young=None, poisson=None) -> State:
+    """The state with fixed walls (rows (m, h): the half-space m . x <= h, unit m
+    out of the wall), of the particles' material unless given."""
+    st = dataclasses.replace(state)
+    st.walls = np.asarray(walls, float).reshape(-1, 4).copy()
+    st.walls[:, :3] /= np.linalg.norm(st.walls[:, :3], axis=1, keepdims=True)
+    w = len(st.walls)
+    st.wall_young = np.full(w, float(state.young[0] if young is None else young))
+    st.wall_poisson = np.full(w, float(state.poisson[0] if poisson is None else poisson))
+    return st
+
+
+def floor_and_ceiling(state: State, gap: float = 2.0) -> State:
+    """A floor below the lowest centre and a ceiling above the highest, each
+    `gap` from it, so the particles near them press into the walls."""
+    z = state.pos[:, 2]
+    return with_walls(state, [[0.0, 0.0, 1.0, z.min() - gap], [0.0, 0.0, -1.0, -(z.max() + gap)]])
+
+
 def pose_sequence(state: State, steps: int, seed: int = 11, sigma_x: float = 0.05,
                   sigma_rot: float = 0.01):
     """`steps` poses after small random increments: dX ~ N(0, sigma_x) per

@@ -64,9 +64,12 @@ class LawTracker:
         F = o[:, 8:11]
         Fn = np.linalg.norm(F, axis=1)
         fmag0 = np.linalg.norm(r_undamped.pair_out[:, 8:11], axis=1)   # undamped, no friction
-        XA = pos[ij[:, 0]]
-        XB = pos[ij[:, 1]] - r_base.pair_shift * st.box
-        vA, vB = vel[ij[:, 0]], vel[ij[:, 1]]
+        nw = len(getattr(st, "walls", ()))   # partners j >= n are walls: at the origin, at rest
+        pos_w = np.concatenate([pos, np.zeros((nw, 3))])
+        vel_w = np.concatenate([vel, np.zeros((nw, 6))])
+        XA = pos_w[ij[:, 0]]
+        XB = pos_w[ij[:, 1]] - r_base.pair_shift * st.box
+        vA, vB = vel_w[ij[:, 0]], vel_w[ij[:, 1]]
         uab = (vA[:, :3] + np.cross(vA[:, 3:], xc - XA)) - (vB[:, :3] + np.cross(vB[:, 3:], xc - XB))
         wrel = np.linalg.norm(vA[:, 3:] - vB[:, 3:], axis=1)
         ddot = np.einsum("pk,pk->p", uab, n)

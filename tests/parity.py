@@ -131,25 +131,30 @@ def compare(st, g, r, fp64: bool, smooth: bool, forces=None, tol_force=None) -> 
     zero = clean & (V == 0)
     assert np.all(go[zero] == 0.0), "pairs with no overlap must be exactly zero"
     # per-particle sums: tolerance = sum of the pair tolerances touching it
-    touched_flag = np.zeros(st.n, bool)
+    # rows n .. n + walls - 1 stand for the walls (partner indices j >= n; no sums)
+    nrow = st.n + len(getattr(st, "walls", ()))
+    touched_flag = np.zeros(nrow, bool)
     touched_flag[r.pair_ij[flagged | skipF].ravel()] = True
-    sF = np.zeros(st.n)
-    tF = np.zeros(st.n)
+    sF = np.zeros(nrow)
+    tF = np.zeros(nrow)
     for col in (0, 1):
         np.add.at(sF, r.pair_ij[:, col], Fs)
         np.add.at(tF, r.pair_ij[:, col], tolF)
+    touched_flag, sF, tF = touched_flag[:st.n], sF[:st.n], tF[:st.n]
     ok = ~touched_flag & ((sF > 0) | (tF > 0))
     _check("F", np.abs(g["force"][ok] - r_force[ok]).max(axis=1, initial=0), tF[ok] + 1e-12 * sF[ok], out)
-    XA = st.pos[r.pair_ij[:, 0]]
-    XB = st.pos[r.pair_ij[:, 1]] - r.pair_shift * st.box
+    pos_w = np.concatenate([st.pos, np.zeros((nrow - st.n, 3))])   # a wall sits at the origin
+    XA = pos_w[r.pair_ij[:, 0]]
+    XB = pos_w[r.pair_ij[:, 1]] - r.pair_shift * st.box
     armA = np.linalg.norm(ro[:, 1:4] - XA, axis=1)
     armB = np.linalg.norm(ro[:, 1:4] - XB, axis=1)
-    tT = np.zeros(st.n)
+    tT = np.zeros(nrow)
     np.add.at(tT, r.pair_ij[:, 0], tolF * armA + Fs * tolx)
     np.add.at(tT, r.pair_ij[:, 1], tolF * armB + Fs * tolx)
-    sT = np.zeros(st.n)
+    sT = np.zeros(nrow)
     np.add.at(sT, r.pair_ij[:, 0], Fs * armA)
     np.add.at(sT, r.pair_ij[:, 1], Fs * armB)
+    tT, sT = tT[:st.n], sT[:st.n]
     _check("T", np.abs(g["torque"][ok] - r_torque[ok]).max(axis=1, initial=0), tT[ok] + 1e-12 * sT[ok], out)
     none = ~ok & ~touched_flag
     assert np.all(g["force"][none] == 0.0) and np.all(g["torque"][none] == 0.0)
