@@ -420,6 +420,17 @@ def extras(args, dev, flush, peak):
             law[name]["contacts_in_history"] = int(len(m.history()[1]))
         m.close()
     out["cubes1934_velocities"] = law
+    # the headline workload between a floor and a ceiling (fixed walls, 2 of them)
+    st_w = W.floor_and_ceiling(headline_state(0))
+    m = Contact.from_state(st_w, narrow_events=True)
+    r = time_forward(m, pd, qd, steps, 3, flush, narrow=True)
+    s_ = m.stats()
+    ij = m.pair_ij[:s_["pairs"]].cpu().numpy()
+    out["cubes1934_floor_ceiling"] = {"cell_evals_per_s": r["cells"] / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / steps,
+                                      "narrow_ms": r["narrow_ms"] / steps, "pairs": s_["pairs"],
+                                      "wall_pairs": int((ij[:, 1] >= st_w.n).sum()),
+                                      "cells_per_step": r["cells"] / steps}
+    m.close()
     # 400 cubes at 10 %, and the resolution sweep (500 cubes at 20 %, edge 8..24), both forms
     def both_forms(st, nsteps):
         pos, quat = W.pose_sequence(st, nsteps + 3)
