@@ -52,7 +52,8 @@ class _Cfg(ctypes.Structure):
                 ("smooth_width", ctypes.c_double), ("inflate", ctypes.c_double),
                 ("damping_c", ctypes.c_double), ("band_eps", ctypes.c_double),
                 ("n_walls", ctypes.c_int32), ("walls", ctypes.c_void_p), ("wall_young", ctypes.c_void_p),
-                ("wall_poisson", ctypes.c_void_p)]
+                ("wall_poisson", ctypes.c_void_p), ("box_mode", ctypes.c_int32),
+                ("contact_resolution", ctypes.c_int32)]
 
 
 def _load():
@@ -70,6 +71,9 @@ def _load():
         lib.oracle_gradient_ext.restype = ctypes.c_int64
         lib.oracle_gradient_ext.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Law), ctypes.c_int32] + \
             [P] * 9 + [ctypes.c_int64] + [P] * 6 + [ctypes.c_int32]
+        lib.oracle_box_pipeline.restype = ctypes.c_int64
+        lib.oracle_box_pipeline.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 8 + \
+            [ctypes.c_int64] + [P] * 3
         lib.oracle_gradient.restype = ctypes.c_int64
         lib.oracle_gradient.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 13 + [ctypes.c_int32]
         lib.oracle_aabb.restype = ctypes.c_int32
@@ -103,6 +107,8 @@ def _cfg(st, band_eps=BAND_EPS):
         c.n_cells[k] = int(st.n_cells[k])
     c.dx, c.indicator, c.smooth_width = float(st.dx), int(st.indicator), float(st.smooth_width)
     c.inflate, c.damping_c, c.band_eps = float(st.inflate), float(st.damping_c), float(band_eps)
+    c.box_mode = int(getattr(st, "box_mode", 0))
+    c.contact_resolution = int(getattr(st, "contact_resolution", 8))
     walls = getattr(st, "walls", None)
     if walls is not None and len(walls):
         arrs = (_c(np.asarray(walls).reshape(-1, 4), np.float64), _c(st.wall_young, np.float64),
@@ -283,6 +289,26 @@ def gradient_ext(st, law: ContactLaw, grad_force, grad_torque, pos=None, quat=No
     if P < 0:
         raise OracleError(-P)
     return gp, gq
+
+
+def box_pipeline(st, pos=None, quat=None):
+    """The box pipeline's rough boxes [P,6] (node indices), corrected boxes
+    [P,6] (physical) and flags [P,2] per candidate pair (st.box_mode = 1)."""
+    lib = _load()
+    pos = _c(st.pos if pos is None else pos, np.float64)
+    quat = _c(st.quat if quat is None else quat, np.float64)
+    cap = max(16, 16 * st.n)
+    while True:
+        rough = np.zeros((cap, 6), np.int32)
+        box = np.zeros((cap, 6))
+        flags = np.zeros((cap, 2))
+        P = lib.oracle_box_pipeline(ctypes.byref(_cfg(st)), st.n, *[_ptr(a) for a in _shape_arrays(st)], _ptr(pos),
+                                    _ptr(quat), cap, _ptr(rough), _ptr(box), _ptr(flags))
+        if P < 0:
+            raise OracleError(-P)
+        if P <= cap:
+            return rough[:P], box[:P], flags[:P]
+        cap = int(P)
 
 
 def aabb(st, pos=None, quat=None):

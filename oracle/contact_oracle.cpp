@@ -122,6 +122,8 @@ struct Config {
   const double* walls;   // [n_walls, 4]
   const double* wall_young;
   const double* wall_poisson;
+  int32_t box_mode;      // 0: every lattice node of the pair box; 1: the paper's box pipeline
+  int32_t contact_resolution;   // N_c of the box pipeline (points per direction)
 };
 
 struct Shape {
@@ -304,6 +306,11 @@ struct PairResult {
   double box_cells, n_band, n_gtie, d_gap, estar;
   double v_sens, m_sens, g_sens;  // first-order change of V, M, G for a perturbation eps of every phi
   double c_used;                  // damping factor the force law used
+  // box pipeline: rough box (node indices), corrected box (physical), and
+  // the nodes / faces whose outcome is within eps of changing
+  int rough[6];
+  double box[6];
+  double n_rough_band, n_face_tie;
 };
 
 // Eq. (damping_factor): c from the coefficient of restitution e and the
@@ -325,6 +332,164 @@ struct ContactLaw {
   double mu_s = 0.0, mu_k = 0.0, u_k = 1.0;
 };
 
+// Parameter interval [t0, t1] of the line p + t e inside a shape reduced by
+// `inflate` (empty: t0 > t1): a sphere by its quadratic, a cuboid / polytope /
+// wall by clipping against each face plane (world frame).
+void line_interval(const Shape& sh, const double X[3], const double R[9], const double p[3], const double e[3],
+                   double inflate, double* t0, double* t1) {
+  const double inf = std::numeric_limits<double>::infinity();
+  *t0 = -inf;
+  *t1 = inf;
+  if (sh.type == SH_SPHERE) {
+    const double r = sh.p[0] + inflate;
+    const double q[3] = {p[0] - X[0], p[1] - X[1], p[2] - X[2]};
+    const double b = q[0] * e[0] + q[1] * e[1] + q[2] * e[2];   // |e| = 1
+    const double c = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] - r * r;
+    const double disc = b * b - c;
+    if (disc < 0.0) {
+      *t0 = inf;
+      *t1 = -inf;
+      return;
+    }
+    const double sq = std::sqrt(disc);
+    *t0 = -b - sq;
+    *t1 = -b + sq;
+    return;
+  }
+  // faces (n_w, offset) with n_w . x <= offset along the line: a + t b <= 0
+  auto clip = [&](const double nw[3], double off) {
+    const double a = (nw[0] * p[0] + nw[1] * p[1] + nw[2] * p[2]) - off;
+    const double b = nw[0] * e[0] + nw[1] * e[1] + nw[2] * e[2];
+    if (b > 0.0) {
+      *t1 = std::min(*t1, -a / b);
+    } else if (b < 0.0) {
+      *t0 = std::max(*t0, -a / b);
+    } else if (a > 0.0) {
+      *t0 = inf;
+      *t1 = -inf;
+    }
+  };
+  if (sh.type == SH_WALL) {
+    clip(sh.planes.data(), sh.planes[3] + inflate);
+    return;
+  }
+  if (sh.type == SH_CUBOID) {
+    for (int k = 0; k < 3; ++k)
+      for (int sgn = -1; sgn <= 1; sgn += 2) {
+        const double nw[3] = {sgn * R[0 * 3 + k], sgn * R[1 * 3 + k], sgn * R[2 * 3 + k]};   // +-R e_k
+        clip(nw, (nw[0] * X[0] + nw[1] * X[1] + nw[2] * X[2]) + sh.p[k] + inflate);
+      }
+    return;
+  }
+  const int F = static_cast<int>(sh.planes.size() / 4);
+  for (int f = 0; f < F; ++f) {
+    const double* b = &sh.planes[4 * f];
+    const double nw[3] = {R[0] * b[0] + R[1] * b[1] + R[2] * b[2], R[3] * b[0] + R[4] * b[1] + R[5] * b[2],
+                          R[6] * b[0] + R[7] * b[1] + R[8] * b[2]};
+    clip(nw, (nw[0] * X[0] + nw[1] * X[1] + nw[2] * X[2]) + b[3] + inflate);
+  }
+}
+
+// The paper's box pipeline (Sec. 3.3.1), restated:
+//  1. rough detection: the lattice nodes where both signed distances are
+//     below half the cell diagonal, sqrt(0.75) dx (all inside the pair box,
+//     whose node ranges are widened by that much); their node-index bounds are
+//     the rough box (none: no contact);
+//  2. correction: the rough box widened by sqrt(0.75) dx (every point inside
+//     both shapes lies within that distance of such a node) is B0; on each of
+//     its six faces an N_c x N_c grid of points (cell centres of the face)
+//     casts lines along the inward normal; each line's entry into the overlap
+//     (both shapes, the line clipped exactly) is its distance to the contact,
+//     and the face moves inward by the smallest such distance (a face whose
+//     lines all miss stays; an axis left empty keeps B0's extent);
+//  3. the N_c^3 cell centres of the corrected box are the sample points.
+// Fills the sample box (lo, spacing) or returns false when no node is rough-in.
+template <class S>
+bool box_pipeline(const Config& cfg, const Shape& A, const Shape& B, const PairGeom& pg, const double XA[3],
+                  const double RA[9], const double XB[3], const double RB[9], PairResult<S>& res, double lo[3],
+                  double step[3]) {
+  const double dx = cfg.dx;
+  const int Nc = cfg.contact_resolution;
+  const double srough = std::sqrt(0.75) * dx;
+  const double eps = cfg.band_eps * dx;
+  int mn[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, mx[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+  double n_rough_band = 0;
+  // (the node ranges of the box pipeline are widened by sqrt(0.75) dx, so
+  // the pair box holds every node where both distances are below it)
+  for (int kz = pg.lo[2]; kz <= pg.hi[2]; ++kz)
+    for (int ky = pg.lo[1]; ky <= pg.hi[1]; ++ky)
+      for (int kx = pg.lo[0]; kx <= pg.hi[0]; ++kx) {
+        const double x[3] = {kx * dx, ky * dx, kz * dx};
+        double gA[3], gB[3], gapA, gapB;
+        const double pa = sdf(A, XA, RA, x, cfg.inflate, gA, &gapA);
+        const double pb = sdf(B, XB, RB, x, cfg.inflate, gB, &gapB);
+        if (pa < srough && pb < srough) {
+          const int k[3] = {kx, ky, kz};
+          for (int a = 0; a < 3; ++a) {
+            mn[a] = std::min(mn[a], k[a]);
+            mx[a] = std::max(mx[a], k[a]);
+          }
+        }
+        const bool loose = pa < srough + eps && pb < srough + eps;
+        const bool strict = pa < srough - eps && pb < srough - eps;
+        if (loose && !strict) n_rough_band += 1;
+      }
+  res.n_rough_band = n_rough_band;
+  if (mn[0] > mx[0]) return false;
+  double b0lo[3], b0hi[3];
+  for (int a = 0; a < 3; ++a) {
+    res.rough[a] = mn[a];
+    res.rough[3 + a] = mx[a];
+    b0lo[a] = mn[a] * dx - srough;
+    b0hi[a] = mx[a] * dx + srough;
+  }
+  // correction: face (axis k, lower / upper), lines along the inward normal
+  double shift[3][2];
+  double n_face_tie = 0;
+  for (int k = 0; k < 3; ++k)
+    for (int side = 0; side < 2; ++side) {
+      const int u = k == 0 ? 1 : 0, v = k == 2 ? 1 : 2;
+      const double len = b0hi[k] - b0lo[k];
+      double best = std::numeric_limits<double>::infinity(), second = best;
+      for (int a = 0; a < Nc; ++a)
+        for (int b = 0; b < Nc; ++b) {
+          double p[3], e[3] = {0.0, 0.0, 0.0};
+          p[u] = b0lo[u] + (a + 0.5) * (b0hi[u] - b0lo[u]) / Nc;
+          p[v] = b0lo[v] + (b + 0.5) * (b0hi[v] - b0lo[v]) / Nc;
+          p[k] = side == 0 ? b0lo[k] : b0hi[k];
+          e[k] = side == 0 ? 1.0 : -1.0;
+          double a0, a1, c0, c1;
+          line_interval(A, XA, RA, p, e, cfg.inflate, &a0, &a1);
+          line_interval(B, XB, RB, p, e, cfg.inflate, &c0, &c1);
+          const double tin = std::max(std::max(a0, c0), 0.0);
+          const double tout = std::min(std::min(a1, c1), len);
+          if (tin <= tout) {
+            if (tin < best) {
+              second = best;
+              best = tin;
+            } else if (tin < second) {
+              second = tin;
+            }
+          }
+        }
+      shift[k][side] = std::isfinite(best) ? best : 0.0;
+      if (std::isfinite(second) && second - best < 1e-4 * dx && second != best) n_face_tie += 1;
+    }
+  res.n_face_tie = n_face_tie;
+  for (int k = 0; k < 3; ++k) {
+    double l = b0lo[k] + shift[k][0], h = b0hi[k] - shift[k][1];
+    if (!(l <= h)) {
+      l = b0lo[k];
+      h = b0hi[k];
+    }
+    lo[k] = l;
+    step[k] = (h - l) / Nc;
+    res.box[k] = l;
+    res.box[3 + k] = h;
+  }
+  return true;
+}
+
 // Sweep of every lattice node of the pair box (Sec. 3.3.1) and the force law
 // of Eq. (contact_force_normal).  XA, qA, XB (already the image X_j'), qB are
 // the poses; vel (nullable) holds (u, omega) per particle.
@@ -345,10 +510,32 @@ PairResult<S> eval_pair(const Config& cfg, const Shape& A, const Shape& B, const
   double top1 = -std::numeric_limits<double>::infinity(), top2 = top1;
   double n_band = 0, n_gtie = 0, v_sens = 0, m_sens = 0, g_sens = 0;
   const double o[3] = {pg.lo[0] * dx, pg.lo[1] * dx, pg.lo[2] * dx};
-  for (int kz = pg.lo[2]; kz <= pg.hi[2]; ++kz)
-    for (int ky = pg.lo[1]; ky <= pg.hi[1]; ++ky)
-      for (int kx = pg.lo[0]; kx <= pg.hi[0]; ++kx) {
-        const double x[3] = {kx * dx, ky * dx, kz * dx};
+  // sample set: every node of the pair box, or the box pipeline's N_c^3 points
+  const bool boxed = cfg.box_mode == 1;
+  int cnt[3] = {pg.hi[0] - pg.lo[0] + 1, pg.hi[1] - pg.lo[1] + 1, pg.hi[2] - pg.lo[2] + 1};
+  double s_lo[3] = {o[0], o[1], o[2]}, s_step[3] = {dx, dx, dx};
+  PairResult<S> res;
+  for (int k = 0; k < 6; ++k) { res.rough[k] = 0; res.box[k] = 0.0; }
+  res.n_rough_band = res.n_face_tie = 0.0;
+  if (boxed) {
+    double XAd[3], XBd[3], RAd[9], RBd[9];
+    for (int k = 0; k < 3; ++k) { XAd[k] = val(XA[k]); XBd[k] = val(XB[k]); }
+    for (int k = 0; k < 9; ++k) { RAd[k] = val(RA[k]); RBd[k] = val(RB[k]); }
+    if (box_pipeline(cfg, A, B, pg, XAd, RAd, XBd, RBd, res, s_lo, s_step)) {
+      for (int k = 0; k < 3; ++k) {
+        cnt[k] = cfg.contact_resolution;
+        s_lo[k] += 0.5 * s_step[k];   // cell centres
+      }
+    } else {
+      cnt[0] = cnt[1] = cnt[2] = 0;
+    }
+  }
+  for (int iz = 0; iz < cnt[2]; ++iz)
+    for (int iy = 0; iy < cnt[1]; ++iy)
+      for (int ix = 0; ix < cnt[0]; ++ix) {
+        const double x[3] = {boxed ? s_lo[0] + ix * s_step[0] : (pg.lo[0] + ix) * dx,
+                             boxed ? s_lo[1] + iy * s_step[1] : (pg.lo[1] + iy) * dx,
+                             boxed ? s_lo[2] + iz * s_step[2] : (pg.lo[2] + iz) * dx};
         const double c[3] = {x[0] - o[0], x[1] - o[1], x[2] - o[2]};
         S gA[3], gB[3];
         double gapA, gapB;
@@ -403,10 +590,9 @@ PairResult<S> eval_pair(const Config& cfg, const Shape& A, const Shape& B, const
         }
       }
 
-  PairResult<S> res;
-  const double dx3 = dx * dx * dx;
-  res.box_cells = double(pg.hi[0] - pg.lo[0] + 1) * double(pg.hi[1] - pg.lo[1] + 1) *
-                  double(pg.hi[2] - pg.lo[2] + 1);
+  // volume of one sample: dx^3 on the lattice, the sample cell in the box pipeline
+  const double dx3 = boxed ? s_step[0] * s_step[1] * s_step[2] : dx * dx * dx;
+  res.box_cells = double(cnt[0]) * double(cnt[1]) * double(cnt[2]);
   res.n_band = n_band;
   res.n_gtie = n_gtie;
   res.d_gap = (top2 > -std::numeric_limits<double>::infinity()) ? (top1 - top2) / dx
@@ -551,10 +737,15 @@ int build_problem(Problem& pb, const Config* cfg, int32_t n, const int32_t* shap
   for (int k = 0; k < 3; ++k)
     if (c.n_cells[k] < 1) return OR_EINVAL;
   if (c.indicator != 0 && c.indicator != 1) return OR_EINVAL;
+  if (c.box_mode != 0 && c.box_mode != 1) return OR_EINVAL;
+  if (c.box_mode == 1 && (c.contact_resolution < 1 || c.contact_resolution > 64)) return OR_EINVAL;
   if (!(c.smooth_width > 0.0)) return OR_EINVAL;
   if (!(c.inflate >= 0.0) || !(c.damping_c >= 0.0)) return OR_EINVAL;
   // offset used for the AABB: inflation plus, in smoothed mode, half the band
-  const double band = (c.indicator == 1) ? (0.5 * c.smooth_width) * c.dx : 0.0;
+  // offset of the node ranges: inflation plus, in smoothed mode, half the band;
+  // the box pipeline widens them to its rough-detection threshold sqrt(0.75) dx
+  double band = (c.indicator == 1) ? (0.5 * c.smooth_width) * c.dx : 0.0;
+  if (c.box_mode == 1) band = std::max(band, std::sqrt(0.75) * c.dx);
   const double delta = c.inflate + band;
   pb.shapes.resize(n);
   pb.young.assign(young, young + n);
@@ -739,6 +930,8 @@ typedef struct {
   const double* walls;
   const double* wall_young;
   const double* wall_poisson;
+  int32_t box_mode;
+  int32_t contact_resolution;
 } oracle_config;
 
 int32_t oracle_max_threads(void) {
@@ -988,6 +1181,7 @@ static int64_t gradient_impl(const oracle_config* cfg, const oracle_contact_law*
   const int st = build_problem(pb, reinterpret_cast<const Config*>(cfg), n, shape_type, shape_param,
                                face_offset, planes, young, poisson, pos, quat);
   if (st != OR_OK) return -st;
+  if (pb.cfg.box_mode != 0) return -OR_EINVAL;   // the box pipeline's samples move with the box: no gradient
   const int64_t P = static_cast<int64_t>(pb.pairs.size());
   std::vector<double> pg(static_cast<size_t>(P) * NT, 0.0);
   set_threads(n_threads);
@@ -1062,6 +1256,42 @@ int64_t oracle_gradient_ext(const oracle_config* cfg, const oracle_contact_law* 
   if (law->friction && (!(law->mu_s > 0.0) || !(law->mu_k >= 0.0) || !(law->u_k > 0.0))) return -OR_EINVAL;
   return gradient_impl(cfg, law, n, shape_type, shape_param, face_offset, planes, young, poisson, pos, quat, vel,
                        n_hist, hist_ij, hist_c, grad_force, grad_torque, grad_pos, grad_quat, n_threads);
+}
+
+// The box pipeline's boxes per candidate pair (cfg.box_mode must be 1):
+// rough [P,6] node-index bounds (0 when no node is rough-in), box [P,6] the
+// corrected box (physical), flags [P,2] = rough-detection nodes within
+// band_eps of the threshold, faces whose two smallest line distances lie
+// within 1e-4 dx.  Returns P or a negative status.
+int64_t oracle_box_pipeline(const oracle_config* cfg, int32_t n, const int32_t* shape_type,
+                            const double* shape_param, const int32_t* face_offset, const double* planes,
+                            const double* young, const double* poisson, const double* pos, const double* quat,
+                            int64_t max_pairs, int32_t* rough, double* box, double* flags) {
+  Problem pb;
+  const int st = build_problem(pb, reinterpret_cast<const Config*>(cfg), n, shape_type, shape_param,
+                               face_offset, planes, young, poisson, pos, quat);
+  if (st != OR_OK) return -st;
+  if (pb.cfg.box_mode != 1) return -OR_EINVAL;
+  const int64_t P = static_cast<int64_t>(pb.pairs.size());
+  for (int64_t p = 0; p < std::min(P, max_pairs); ++p) {
+    const PairGeom& g = pb.pairs[p];
+    double XB[3], RA[9], RB[9];
+    image_pos(pb, g, pos, XB);
+    quat_to_rot(quat + 4 * g.i, RA);
+    quat_to_rot(partner_quat(pb, g, quat), RB);
+    PairResult<double> r;
+    for (int k = 0; k < 6; ++k) { r.rough[k] = 0; r.box[k] = 0.0; }
+    double lo[3], step[3];
+    r.n_face_tie = 0.0;
+    box_pipeline(pb.cfg, pb.shapes[g.i], pb.shapes[g.j], g, pos + 3 * g.i, RA, XB, RB, r, lo, step);
+    for (int k = 0; k < 6; ++k) {
+      rough[6 * p + k] = r.rough[k];
+      box[6 * p + k] = r.box[k];
+    }
+    flags[2 * p] = r.n_rough_band;
+    flags[2 * p + 1] = r.n_face_tie;
+  }
+  return P;
 }
 
 }  // extern "C"

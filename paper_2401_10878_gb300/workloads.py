@@ -53,6 +53,10 @@ class State:
     walls: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 4)))
     wall_young: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
     wall_poisson: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(0))
+    # sample set: 0 every lattice node of the pair box; 1 the paper's box pipeline
+    # (rough detection, box correction, contact_resolution^3 points; Sec. 3.3.1)
+    box_mode: int = 0
+    contact_resolution: int = 8
 
     @property
     def n(self) -> int:
