@@ -124,6 +124,17 @@ typedef struct {
                                the wall; read by contact_init only                */
   const double* wall_young; /* [n_walls] host, E of each wall (> 0)               */
   const double* wall_poisson; /* [n_walls] host, nu of each wall (0 <= nu < 1)    */
+  int32_t box_mode;         /* 0: the sample set is every lattice node of the pair
+                               box (default); 1: the paper's box pipeline (Sec.
+                               3.3.1): rough detection at the nodes where both
+                               signed distances are below sqrt(0.75) dx (node
+                               ranges widened by that much), the box widened by
+                               it and each face moved inward to the nearest entry
+                               of contact_resolution^2 axis-parallel lines into the
+                               overlap, then contact_resolution^3 cell-centre
+                               samples; shared damping c only (no history, no
+                               friction), no contact_backward                     */
+  int32_t contact_resolution; /* N_c of box_mode 1, 1..64 (the paper uses 8)      */
 } contact_config;
 
 enum { CONTACT_MAX_WALLS = 64 };

@@ -43,7 +43,8 @@ class Config(ctypes.Structure):
                 ("narrow_events", ctypes.c_int32), ("history", ctypes.c_int32), ("friction", ctypes.c_int32),
                 ("restitution", ctypes.c_double), ("mu_s", ctypes.c_double), ("mu_k", ctypes.c_double),
                 ("u_k", ctypes.c_double), ("n_walls", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("walls", ctypes.c_void_p), ("wall_young", ctypes.c_void_p), ("wall_poisson", ctypes.c_void_p)]
+                ("walls", ctypes.c_void_p), ("wall_young", ctypes.c_void_p), ("wall_poisson", ctypes.c_void_p),
+                ("box_mode", ctypes.c_int32), ("contact_resolution", ctypes.c_int32)]
 
 
 class ContactError(RuntimeError):
@@ -135,7 +136,8 @@ class Contact:
                  indicator=SHARP, smooth_width=1.0, inflate=0.0, damping_c=0.0, precision=FP32_TILE,
                  max_pairs=None, max_neighbors=64, max_tiles=0, use_graph=True, narrow_events=False,
                  history=False, restitution=1.0, friction=False, mu_s=0.0, mu_k=0.0, u_k=1.0,
-                 walls=None, wall_young=None, wall_poisson=None, device=None, stream=None):
+                 walls=None, wall_young=None, wall_poisson=None, box_mode=0, contact_resolution=8,
+                 device=None, stream=None):
         if not torch.cuda.is_available():
             raise ContactError(ECUDA, "no CUDA device: the contact path has no CPU fallback")
         self.lib = load_library()
@@ -159,6 +161,7 @@ class Contact:
             cfg.n_walls = len(wall_arrs[0])
             cfg.walls, cfg.wall_young, cfg.wall_poisson = (a.ctypes.data for a in wall_arrs)
         self.n_walls = int(cfg.n_walls)
+        cfg.box_mode, cfg.contact_resolution = int(box_mode), int(contact_resolution)
         if max_pairs is not None:
             cfg.max_pairs = int(max_pairs)
         cfg.max_neighbors, cfg.max_tiles, cfg.use_graph = int(max_neighbors), int(max_tiles), int(bool(use_graph))
@@ -190,7 +193,8 @@ class Contact:
         """Context for a workloads.State (shapes, material, lattice, indicator)."""
         args = dict(indicator=st.indicator, smooth_width=st.smooth_width, inflate=st.inflate,
                     damping_c=st.damping_c, walls=getattr(st, "walls", None),
-                    wall_young=getattr(st, "wall_young", None), wall_poisson=getattr(st, "wall_poisson", None))
+                    wall_young=getattr(st, "wall_young", None), wall_poisson=getattr(st, "wall_poisson", None),
+                    box_mode=getattr(st, "box_mode", 0), contact_resolution=getattr(st, "contact_resolution", 8))
         args.update(kw)
         return cls(st.shape_type, st.shape_param, st.face_offset, st.planes, st.young, st.poisson, st.n_cells,
                    st.dx, **args)

@@ -52,6 +52,7 @@ struct Params {
   int kind_set;          // node-sweep variant: 0 all kinds, 1 spheres and cuboids, 2 cubes only
   int dx_pow2;           // 1: dx is a power of two, so x / dx == x * inv_dx exactly
   double damping_c;
+  int box_mode, box_res; // 1: the paper's box pipeline with box_res (N_c) points per direction
   int nwall;             // fixed walls: partner indices n .. n + nwall - 1
   const double* wall;    // [nwall,4] (m, h): the half-space m . x <= h
   int history, friction;  // contact history; tangential force
@@ -362,6 +363,8 @@ int bin_capacity(int n, const double binw[3], double rin_min, long long nbins, l
 void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel,
                    double* pair_out, int grid, cudaStream_t st);
 int narrow_grid(const Params& P);
+void launch_box(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel, double* pair_out,
+                int grid, cudaStream_t st);
 void launch_particle_sum(const Params& P, const Parts& D, const Lists& W, double* force, double* torque,
                          cudaStream_t st);
 size_t adjoint_scratch_doubles(int max_pairs, int max_tiles);

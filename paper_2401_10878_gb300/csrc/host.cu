@@ -203,6 +203,8 @@ void contact_config_default(contact_config* cfg, int32_t n_particles, const int3
   cfg->walls = nullptr;
   cfg->wall_young = nullptr;
   cfg->wall_poisson = nullptr;
+  cfg->box_mode = 0;
+  cfg->contact_resolution = 8;
 }
 
 double contact_damping_factor(double e, double u0) {
@@ -233,6 +235,9 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   if (C.friction && (!(C.mu_s > 0.0) || !(C.mu_k >= 0.0) || !(C.u_k > 0.0) || !std::isfinite(C.mu_s) ||
                      !std::isfinite(C.mu_k) || !std::isfinite(C.u_k)))
     return CONTACT_EINVAL;
+  if (C.box_mode != 0 && C.box_mode != 1) return CONTACT_EINVAL;
+  if (C.box_mode == 1 && (C.contact_resolution < 1 || C.contact_resolution > 64 || C.history || C.friction))
+    return CONTACT_EINVAL;
   const int nw = C.n_walls;
   if (nw < 0 || nw > CONTACT_MAX_WALLS) return CONTACT_EINVAL;
   if (nw > 0 && (C.walls == nullptr || C.wall_young == nullptr || C.wall_poisson == nullptr)) return CONTACT_EINVAL;
@@ -247,7 +252,10 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   const long long max_tiles_ll = C.max_tiles > 0 ? C.max_tiles : 8LL * C.max_pairs;
   if (max_tiles_ll > (1LL << 30)) return CONTACT_EINVAL;
 
-  const double band = (C.indicator == 1) ? (0.5 * C.smooth_width) * C.dx : 0.0;
+  // offset of the node ranges: inflation plus, in smoothed mode, half the band;
+  // the box pipeline widens them to its rough-detection threshold sqrt(0.75) dx
+  double band = (C.indicator == 1) ? (0.5 * C.smooth_width) * C.dx : 0.0;
+  if (C.box_mode == 1) band = std::max(band, std::sqrt(0.75) * C.dx);
   const double delta = C.inflate + band;
   std::vector<int> type(n), kind(n), vert_off(n + 1, 0);
   std::vector<double> param(3 * static_cast<size_t>(n)), verts, ext(3 * static_cast<size_t>(n), 0.0);
@@ -367,6 +375,8 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
                              [](int k) { return k == KIND_SPHERE || k == KIND_CUBOID || k == KIND_CUBE; }) ? 1 : 0;
   if (nw > 0 && P.kind_set == 2) P.kind_set = 1;
   P.nwall = nw;
+  P.box_mode = C.box_mode;
+  P.box_res = C.box_mode == 1 ? C.contact_resolution : 0;
   P.damping_c = C.damping_c;
   P.history = C.history;
   P.friction = C.friction;
@@ -747,6 +757,8 @@ contact_status contact_backward(contact_ctx* c, const double* grad_force, const 
     return fail(c, CONTACT_EINVAL, "contact_backward: null buffer");
   if (!c->have_step) return fail(c, CONTACT_ESTATE, "contact_backward: no contact_step before");
   if (c->P.smooth != 1) return fail(c, CONTACT_ESTATE, "contact_backward: needs the smoothed indicator");
+  if (c->P.box_mode != 0)
+    return fail(c, CONTACT_ESTATE, "contact_backward: the box pipeline's samples move with the box (no adjoint)");
   const contact_status sticky = check_sticky(c);
   if (sticky != CONTACT_OK) return sticky;
   launch_adjoint(c->P, c->S, c->D, c->W, c->last_vel, grad_force, grad_torque, grad_pos, grad_quat,

@@ -1,0 +1,475 @@
+// The paper's own box pipeline (Sec. 3.3.1 of arXiv:2401.10878): rough
+// contact detection on the lattice, correction of the bounding box, and the
+// final sweep of N_c points per direction over the corrected box.
+//
+//   1. rough detection: the lattice nodes where both signed distances are
+//      below half the cell diagonal, sqrt(0.75) dx; their node-index bounds
+//      form the rough box (none: no contact).  The node ranges of this mode
+//      are widened by that threshold, so the pair box holds all such nodes.
+//   2. correction: the rough box widened by sqrt(0.75) dx (every point inside
+//      both shapes lies within that distance of such a node) is B0; on each of
+//      its six faces an N_c x N_c grid of points (the face's cell centres)
+//      casts lines along the inward normal; a line's entry into the overlap
+//      (the line clipped exactly against both shapes) is its distance to the
+//      contact, and the face moves inward by the smallest one (a face whose
+//      lines all miss stays; an axis left empty keeps B0's extent).
+//   3. the N_c^3 cell centres of the corrected box are the sample points of
+//      the overlap volume, contact point, normal and depth (the lattice
+//      path's estimators, each sample weighing its cell's volume), then the
+//      force law of Eq. (contact_force_normal).
+//
+// One warp per pair, pairs pulled from a queue.  The node tests, the line
+// clipping and the sample sweep run in FP32 relative to the particle centres
+// (offsets formed in FP64); each face's nearest line is re-clipped in FP64,
+// so the corrected box carries no FP32 error; the pair sums, the depth at the
+// deepest sample and the force law are FP64.
+#include <cfloat>
+#include <climits>
+
+#include "contact_dev.cuh"
+
+namespace gbc {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBoxWarps = 8;
+
+// One shape of the pair in FP32, lattice units: centre relative to the pair
+// box origin, R^T rows, sizes (inflate included), world planes (polytope),
+// plane value at the box origin (wall).
+struct ShapeF {
+  int kind;
+  float c[3];
+  float rt[9];
+  float sz[3];
+  const float4* pl;
+  int nf;
+};
+
+__device__ __forceinline__ void load_shape(const PairRec& r, bool second, const Shapes& S, const Parts& D, int pid,
+                                           float4* sm, ShapeF& s) {
+  const int lane = threadIdx.x & 31;
+  s.kind = second ? (r.kinds >> 8) : (r.kinds & 0xff);
+  const int* ci = second ? r.bi : r.ai;
+  const float* cf = second ? r.bf : r.af;
+  const float* rt = second ? r.rtb : r.rta;
+  const float* sz = second ? r.szb : r.sza;
+  for (int k = 0; k < 3; ++k) {
+    s.c[k] = static_cast<float>(ci[k]) + cf[k];
+    s.sz[k] = sz[k];
+  }
+  for (int k = 0; k < 9; ++k) s.rt[k] = rt[k];
+  s.nf = 0;
+  s.pl = sm;
+  if (s.kind == KIND_POLY || s.kind == KIND_POLYG) {
+    const int f0 = S.face_off[pid];
+    s.nf = S.face_off[pid + 1] - f0;
+    if (lane < s.nf) sm[lane] = D.wplane[f0 + lane];
+    __syncwarp();
+  }
+}
+
+// Signed distance (lattice units) at q = point - centre, and the world
+// gradient of the active branch (first maximal face).
+__device__ __forceinline__ float phi_f(const ShapeF& s, const float q[3], float g[3]) {
+  if (s.kind == KIND_SPHERE) {
+    const float n2 = fmaf(q[0], q[0], fmaf(q[1], q[1], q[2] * q[2]));
+    const float nr = sqrtf(n2);
+    const float inv = nr > 0.f ? 1.f / nr : 0.f;
+    for (int k = 0; k < 3; ++k) g[k] = q[k] * inv;
+    return nr - s.sz[0];
+  }
+  if (s.kind == KIND_WALL) {   // q = box-relative point; sz[0] = value at the box origin
+    for (int k = 0; k < 3; ++k) g[k] = s.rt[k];
+    return fmaf(s.rt[0], q[0], fmaf(s.rt[1], q[1], fmaf(s.rt[2], q[2], s.sz[0])));
+  }
+  if (s.kind == KIND_CUBOID || s.kind == KIND_CUBE) {
+    float best = -FLT_MAX;
+    int kk = 0;
+    float sg = 1.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float y = fmaf(s.rt[3 * k], q[0], fmaf(s.rt[3 * k + 1], q[1], s.rt[3 * k + 2] * q[2]));
+      const float a = fabsf(y) - s.sz[k];
+      if (a > best) { best = a; kk = k; sg = y < 0.f ? -1.f : 1.f; }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[k] = sg * (kk == 0 ? s.rt[k] : (kk == 1 ? s.rt[3 + k] : s.rt[6 + k]));
+    return best;
+  }
+  float best = -FLT_MAX;
+  int kk = 0;
+  for (int f = 0; f < s.nf; ++f) {
+    const float4 e = s.pl[f];
+    const float v = fmaf(e.x, q[0], fmaf(e.y, q[1], fmaf(e.z, q[2], -e.w)));
+    if (v > best) { best = v; kk = f; }
+  }
+  const float4 e = s.pl[kk];
+  g[0] = e.x; g[1] = e.y; g[2] = e.z;
+  return best;
+}
+
+// Interval [t0, t1] of the line q + t e (q = start - centre, e = +-axis k)
+// inside the shape, FP32 (empty: t0 > t1).
+__device__ __forceinline__ void clip_f(const ShapeF& s, const float q[3], int k, float sgn, float* t0, float* t1) {
+  *t0 = -FLT_MAX;
+  *t1 = FLT_MAX;
+  auto plane = [&](float n0, float n1, float n2, float off) {
+    const float a = fmaf(n0, q[0], fmaf(n1, q[1], fmaf(n2, q[2], -off)));
+    const float b = sgn * (k == 0 ? n0 : (k == 1 ? n1 : n2));
+    if (b > 0.f) *t1 = fminf(*t1, -a / b);
+    else if (b < 0.f) *t0 = fmaxf(*t0, -a / b);
+    else if (a > 0.f) { *t0 = FLT_MAX; *t1 = -FLT_MAX; }
+  };
+  if (s.kind == KIND_SPHERE) {
+    const float b = sgn * q[k];
+    const float c = fmaf(q[0], q[0], fmaf(q[1], q[1], q[2] * q[2])) - s.sz[0] * s.sz[0];
+    const float disc = b * b - c;
+    if (disc < 0.f) { *t0 = FLT_MAX; *t1 = -FLT_MAX; return; }
+    const float sq = sqrtf(disc);
+    *t0 = -b - sq;
+    *t1 = -b + sq;
+    return;
+  }
+  if (s.kind == KIND_WALL) {
+    plane(s.rt[0], s.rt[1], s.rt[2], -s.sz[0]);
+    return;
+  }
+  if (s.kind == KIND_CUBOID || s.kind == KIND_CUBE) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      plane(s.rt[3 * a], s.rt[3 * a + 1], s.rt[3 * a + 2], s.sz[a]);
+      plane(-s.rt[3 * a], -s.rt[3 * a + 1], -s.rt[3 * a + 2], s.sz[a]);
+    }
+    return;
+  }
+  for (int f = 0; f < s.nf; ++f) {
+    const float4 e = s.pl[f];
+    plane(e.x, e.y, e.z, e.w);
+  }
+}
+
+// FP64 interval of the line p + t e (physical units) inside particle / wall
+// `pid`, the same clipping as the FP32 form; used for each face's nearest line.
+__device__ void clip_d(const Params& P, const Shapes& S, const Parts& D, int pid, const double X[3], const double p[3],
+                       int k, double sgn, double* t0, double* t1) {
+  *t0 = -DBL_MAX;
+  *t1 = DBL_MAX;
+  const int type = S.type[pid];
+  const double* R = D.R + 9 * static_cast<size_t>(pid);
+  auto plane = [&](double n0, double n1, double n2, double off) {
+    const double a = ((n0 * p[0] + n1 * p[1]) + n2 * p[2]) - off;
+    const double b = sgn * (k == 0 ? n0 : (k == 1 ? n1 : n2));
+    if (b > 0.0) *t1 = fmin(*t1, -a / b);
+    else if (b < 0.0) *t0 = fmax(*t0, -a / b);
+    else if (a > 0.0) { *t0 = DBL_MAX; *t1 = -DBL_MAX; }
+  };
+  if (type == 0) {   // sphere
+    const double r = S.param[3 * pid] + P.inflate;
+    const double q[3] = {p[0] - X[0], p[1] - X[1], p[2] - X[2]};
+    const double b = sgn * q[k];
+    const double c = (q[0] * q[0] + q[1] * q[1] + q[2] * q[2]) - r * r;
+    const double disc = b * b - c;
+    if (disc < 0.0) { *t0 = DBL_MAX; *t1 = -DBL_MAX; return; }
+    const double sq = sqrt(disc);
+    *t0 = -b - sq;
+    *t1 = -b + sq;
+    return;
+  }
+  if (type == 1) {   // cuboid
+    for (int a = 0; a < 3; ++a)
+      for (int sg = -1; sg <= 1; sg += 2) {
+        const double n0 = sg * R[a], n1 = sg * R[3 + a], n2 = sg * R[6 + a];   // +-R e_a
+        plane(n0, n1, n2, ((n0 * X[0] + n1 * X[1]) + n2 * X[2]) + S.param[3 * pid + a] + P.inflate);
+      }
+    return;
+  }
+  const int f0 = S.face_off[pid], nf = S.face_off[pid + 1] - f0;   // polytope, or a wall's single plane
+  for (int f = 0; f < nf; ++f) {
+    const double* b = S.planes + 4 * (f0 + f);
+    const double n0 = (R[0] * b[0] + R[1] * b[1]) + R[2] * b[2];
+    const double n1 = (R[3] * b[0] + R[4] * b[1]) + R[5] * b[2];
+    const double n2 = (R[6] * b[0] + R[7] * b[1]) + R[8] * b[2];
+    plane(n0, n1, n2, ((n0 * X[0] + n1 * X[1]) + n2 * X[2]) + b[3] + P.inflate);
+  }
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void zero_pair(const Lists& W, double* pair_out, int q) {
+  const int lane = threadIdx.x & 31;
+  if (lane < 11) pair_out[static_cast<size_t>(q) * 11 + lane] = 0.0;
+  if (lane < kFtDoubles) W.ft[static_cast<size_t>(q) * kFtDoubles + lane] = 0.0;
+  if (lane < kTapeDoubles) W.tape[static_cast<size_t>(q) * kTapeDoubles + lane] = 0.0;
+}
+
+__global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S, Parts D, Lists W,
+                                                              const double* __restrict__ vel,
+                                                              double* __restrict__ pair_out) {
+  __shared__ float4 s_pl[kBoxWarps][2][kMaxFaces];
+  pdl_begin();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int np = min(W.counters[0], P.max_pairs);
+  const int Nc = P.box_res;
+  const float srough = 0.8660254037844386f;   // sqrt(0.75): half the cell diagonal, lattice units
+  for (;;) {
+    int q = 0;
+    if (lane == 0) q = atomicAdd(&W.counters[2], 1);
+    q = __shfl_sync(kFull, q, 0);
+    if (q >= np) break;
+    const PairRec& r = W.pairs[q];
+    const int i = r.i, j = r.j;
+    const int d0 = r.dim[0], d1 = r.dim[1], d2 = r.dim[2];
+    ShapeF A, B;
+    load_shape(r, false, S, D, i, s_pl[wid][0], A);
+    load_shape(r, true, S, D, j, s_pl[wid][1], B);
+    // 1. rough detection over the pair box's nodes (box-relative node c)
+    int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
+    const int vol = d0 * d1 * d2;
+    for (int n0 = 0; n0 < vol; n0 += 32) {
+      const int n = n0 + lane;
+      if (n < vol) {
+        const int c[3] = {n % d0, (n / d0) % d1, n / (d0 * d1)};
+        float qa[3], qb[3], g[3];
+        for (int k = 0; k < 3; ++k) {
+          qa[k] = static_cast<float>(c[k] - r.ai[k]) - r.af[k];
+          qb[k] = B.kind == KIND_WALL ? static_cast<float>(c[k]) : static_cast<float>(c[k] - r.bi[k]) - r.bf[k];
+        }
+        if (phi_f(A, qa, g) < srough && phi_f(B, qb, g) < srough)
+          for (int k = 0; k < 3; ++k) {
+            mn[k] = min(mn[k], c[k]);
+            mx[k] = max(mx[k], c[k]);
+          }
+      }
+    }
+    for (int k = 0; k < 3; ++k) {
+      mn[k] = __reduce_min_sync(kFull, mn[k]);
+      mx[k] = __reduce_max_sync(kFull, mx[k]);
+    }
+    if (mn[0] > mx[0]) {
+      zero_pair(W, pair_out, q);
+      continue;
+    }
+    // 2. B0 (physical, as the rough box's nodes +- sqrt(0.75) dx), then the lines
+    const double s64 = sqrt(0.75) * P.dx;
+    double b0lo[3], b0hi[3];
+    for (int k = 0; k < 3; ++k) {
+      b0lo[k] = (r.lo[k] + mn[k]) * P.dx - s64;
+      b0hi[k] = (r.lo[k] + mx[k]) * P.dx + s64;
+    }
+    double XA[3], XB[3];
+    for (int k = 0; k < 3; ++k) {
+      XA[k] = D.X[3 * i + k];
+      XB[k] = D.X[3 * j + k] - r.shift[k] * P.L[k];
+    }
+    double shift_face[6];
+    const int nl = Nc * Nc;
+    for (int f = 0; f < 6; ++f) {
+      const int k = f >> 1, side = f & 1;
+      const int u = k == 0 ? 1 : 0, v = k == 2 ? 1 : 2;
+      const double len = b0hi[k] - b0lo[k];
+      const float sgn = side == 0 ? 1.f : -1.f;
+      float best = FLT_MAX;
+      int bestl = 0x7fffffff;
+      for (int l0 = 0; l0 < nl; l0 += 32) {
+        const int l = l0 + lane;
+        if (l < nl) {
+          const int a = l / Nc, b = l - a * Nc;
+          double p[3];
+          p[u] = b0lo[u] + (a + 0.5) * (b0hi[u] - b0lo[u]) / Nc;
+          p[v] = b0lo[v] + (b + 0.5) * (b0hi[v] - b0lo[v]) / Nc;
+          p[k] = side == 0 ? b0lo[k] : b0hi[k];
+          // FP32 offsets from each centre (lattice units), formed in FP64
+          float qa[3], qb[3];
+          for (int c = 0; c < 3; ++c) {
+            qa[c] = static_cast<float>((p[c] - XA[c]) * P.inv_dx);
+            qb[c] = B.kind == KIND_WALL ? static_cast<float>(p[c] * P.inv_dx - r.lo[c])
+                                        : static_cast<float>((p[c] - XB[c]) * P.inv_dx);
+          }
+          float a0, a1, c0, c1;
+          clip_f(A, qa, k, sgn, &a0, &a1);
+          clip_f(B, qb, k, sgn, &c0, &c1);
+          const float tin = fmaxf(fmaxf(a0, c0), 0.f);
+          const float tout = fminf(fminf(a1, c1), static_cast<float>(len * P.inv_dx));
+          if (tin <= tout && tin < best) { best = tin; bestl = l; }
+        }
+      }
+      // the face's nearest line (first index on ties), re-clipped in FP64
+      unsigned key = best < FLT_MAX ? __float_as_uint(best) : 0xffffffffu;   // best >= 0: bits order as floats
+      const unsigned kmin = __reduce_min_sync(kFull, key);
+      const int lmin = __reduce_min_sync(kFull, key == kmin ? bestl : 0x7fffffff);
+      double sh = 0.0;
+      if (kmin != 0xffffffffu) {
+        const int a = lmin / Nc, b = lmin - a * Nc;
+        double p[3];
+        p[u] = b0lo[u] + (a + 0.5) * (b0hi[u] - b0lo[u]) / Nc;
+        p[v] = b0lo[v] + (b + 0.5) * (b0hi[v] - b0lo[v]) / Nc;
+        p[k] = side == 0 ? b0lo[k] : b0hi[k];
+        double a0, a1, c0, c1;
+        clip_d(P, S, D, i, XA, p, k, side == 0 ? 1.0 : -1.0, &a0, &a1);
+        clip_d(P, S, D, j, XB, p, k, side == 0 ? 1.0 : -1.0, &c0, &c1);
+        const double tin = fmax(fmax(a0, c0), 0.0);
+        const double tout = fmin(fmin(a1, c1), len);
+        sh = tin <= tout ? tin : static_cast<double>(__uint_as_float(kmin)) * P.dx;
+      }
+      shift_face[f] = sh;
+    }
+    double lo1[3], step[3];
+    for (int k = 0; k < 3; ++k) {
+      double l = b0lo[k] + shift_face[2 * k], h = b0hi[k] - shift_face[2 * k + 1];
+      if (!(l <= h)) {
+        l = b0lo[k];
+        h = b0hi[k];
+      }
+      lo1[k] = l;
+      step[k] = (h - l) / Nc;
+    }
+    // 3. the N_c^3 sample points: offsets from each centre (and the box origin) in FP64, rounded once
+    float oA[3], oB[3], st[3];
+    for (int k = 0; k < 3; ++k) {
+      const double c0 = lo1[k] + 0.5 * step[k];
+      oA[k] = static_cast<float>((c0 - XA[k]) * P.inv_dx);
+      oB[k] = B.kind == KIND_WALL ? static_cast<float>(c0 * P.inv_dx - r.lo[k])
+                                  : static_cast<float>((c0 - XB[k]) * P.inv_dx);
+      st[k] = static_cast<float>(step[k] * P.inv_dx);
+    }
+    const float inv_w = P.inv_w, hw = 0.5f * P.wdx_l;
+    float cnt = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, bestf = -FLT_MAX;
+    int bestidx = 0x7fffffff;
+    const int ns = Nc * Nc * Nc;
+    for (int s0 = 0; s0 < ns; s0 += 32) {
+      const int sidx = s0 + lane;
+      if (sidx >= ns) continue;
+      const int ix = sidx % Nc, iy = (sidx / Nc) % Nc, iz = sidx / (Nc * Nc);
+      const float t[3] = {static_cast<float>(ix), static_cast<float>(iy), static_cast<float>(iz)};
+      float qa[3], qb[3], ga[3], gb[3];
+      for (int k = 0; k < 3; ++k) {
+        qa[k] = fmaf(t[k], st[k], oA[k]);
+        qb[k] = fmaf(t[k], st[k], oB[k]);
+      }
+      const float fa = phi_f(A, qa, ga), fb = phi_f(B, qb, gb);
+      if (fmaxf(fa, fb) >= hw) continue;   // no weight and no band term
+      const float ta = __saturatef(fmaf(fa, -inv_w, 0.5f)), tb = __saturatef(fmaf(fb, -inv_w, 0.5f));
+      float w, ma, mb;
+      if (P.smooth) {
+        const float ha = ta * ta * fmaf(-2.f, ta, 3.f), hb = tb * tb * fmaf(-2.f, tb, 3.f);
+        w = ha * hb;
+        ma = fmaf(-ta, ta, ta) * hb;
+        mb = ha * fmaf(-tb, tb, tb);
+      } else {
+        w = (fa <= 0.f && fb <= 0.f) ? 1.f : 0.f;
+        ma = fb <= 0.f ? fmaf(-ta, ta, ta) : 0.f;
+        mb = fa <= 0.f ? fmaf(-tb, tb, tb) : 0.f;
+      }
+      cnt += w;   // moments of the sample indices (exact integers in sharp mode)
+      m0 = fmaf(w, t[0], m0);
+      m1 = fmaf(w, t[1], m1);
+      m2 = fmaf(w, t[2], m2);
+      g0 += ma * ga[0] - mb * gb[0];
+      g1 += ma * ga[1] - mb * gb[1];
+      g2 += ma * ga[2] - mb * gb[2];
+      const float f = -(fa + fb);
+      if (w > 0.f && (f > bestf || (f == bestf && sidx < bestidx))) { bestf = f; bestidx = sidx; }
+    }
+    cnt = warp_sum_f(cnt);
+    m0 = warp_sum_f(m0); m1 = warp_sum_f(m1); m2 = warp_sum_f(m2);
+    g0 = warp_sum_f(g0); g1 = warp_sum_f(g1); g2 = warp_sum_f(g2);
+    {
+      const int bk = __float_as_int(bestf);   // order-preserving key (-FLT_MAX: no sample, the lowest)
+      const int key = bk >= 0 ? bk : (bk ^ 0x7fffffff);
+      const int kmax = __reduce_max_sync(kFull, key);
+      bestidx = __reduce_min_sync(kFull, key == kmax ? bestidx : 0x7fffffff);
+    }
+    if (!(cnt > 0.f)) {
+      zero_pair(W, pair_out, q);
+      continue;
+    }
+    // 4. FP64 pair results and the force law (lane 0)
+    if (lane == 0) {
+      const double dV = step[0] * step[1] * step[2];
+      const double V = dV * cnt;
+      double xc[3], G[3], nv[3];
+      const double Mx[3] = {m0, m1, m2}, Gs[3] = {g0, g1, g2};
+      const double gscale = 0.5 * dV * 6.0 / P.wdx;
+      for (int k = 0; k < 3; ++k) {
+        xc[k] = lo1[k] + (Mx[k] / cnt + 0.5) * step[k];
+        G[k] = gscale * Gs[k];
+      }
+      const double gn = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
+      if (gn > 1e-12 * P.dx * P.dx) {
+        for (int k = 0; k < 3; ++k) nv[k] = G[k] / gn;
+      } else if (j >= P.n) {
+        const double* e = S.planes + 4 * S.face_off[j];
+        for (int k = 0; k < 3; ++k) nv[k] = -e[k];
+      } else {
+        const double dd[3] = {XB[0] - XA[0], XB[1] - XA[1], XB[2] - XA[2]};
+        const double dn = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+        for (int k = 0; k < 3; ++k) nv[k] = dn > 0.0 ? dd[k] / dn : 0.0;
+      }
+      // depth at the deepest sample, FP64
+      const int bi = min(max(bestidx, 0), ns - 1);
+      const int bx = bi % Nc, by = (bi / Nc) % Nc, bz = bi / (Nc * Nc);
+      const double xs[3] = {lo1[0] + (bx + 0.5) * step[0], lo1[1] + (by + 0.5) * step[1],
+                            lo1[2] + (bz + 0.5) * step[2]};
+      double gA[3], gB[3];
+      const int fa0 = S.face_off[i], fb0 = S.face_off[j];
+      const double pa = sdf64(S.type[i], S.param + 3 * i, S.planes + 4 * fa0, S.face_off[i + 1] - fa0, XA,
+                              D.R + 9 * i, xs, P.inflate, gA);
+      const double pb = sdf64(S.type[j], S.param + 3 * j, S.planes + 4 * fb0, S.face_off[j + 1] - fb0, XB,
+                              D.R + 9 * j, xs, P.inflate, gB);
+      const double d = fmax(0.0, -(pa + pb));
+      const double estar = 1.0 / (S.compl_[i] + S.compl_[j]);
+      double damp = 1.0;
+      double ra[3], rb[3];
+      for (int k = 0; k < 3; ++k) {
+        ra[k] = xc[k] - XA[k];
+        rb[k] = xc[k] - XB[k];
+      }
+      if (vel != nullptr && P.damping_c != 0.0) {
+        const double* va = vel + 6 * i;
+        const double* vb = j < P.n ? vel + 6 * j : D.rest6;
+        const double ua[3] = {va[0] + (va[4] * ra[2] - va[5] * ra[1]), va[1] + (va[5] * ra[0] - va[3] * ra[2]),
+                              va[2] + (va[3] * ra[1] - va[4] * ra[0])};
+        const double ub[3] = {vb[0] + (vb[4] * rb[2] - vb[5] * rb[1]), vb[1] + (vb[5] * rb[0] - vb[3] * rb[2]),
+                              vb[2] + (vb[3] * rb[1] - vb[4] * rb[0])};
+        const double ddot = (ua[0] - ub[0]) * nv[0] + (ua[1] - ub[1]) * nv[1] + (ua[2] - ub[2]) * nv[2];
+        damp = fmax(0.0, 1.0 + P.damping_c * ddot);
+      }
+      const double vd = V * d;
+      const double fmag = vd > 0.0 ? (4.0 / (3.0 * 3.14159265358979323846)) * estar * sqrt(vd) * damp : 0.0;
+      double F[3], TA[3], TB[3];
+      for (int k = 0; k < 3; ++k) F[k] = fmag * nv[k];
+      TA[0] = -(ra[1] * F[2] - ra[2] * F[1]);
+      TA[1] = -(ra[2] * F[0] - ra[0] * F[2]);
+      TA[2] = -(ra[0] * F[1] - ra[1] * F[0]);
+      TB[0] = rb[1] * F[2] - rb[2] * F[1];
+      TB[1] = rb[2] * F[0] - rb[0] * F[2];
+      TB[2] = rb[0] * F[1] - rb[1] * F[0];
+      double* o = pair_out + static_cast<size_t>(q) * 11;
+      double* ft = W.ft + static_cast<size_t>(q) * kFtDoubles;
+      o[0] = V;
+      for (int k = 0; k < 3; ++k) {
+        o[1 + k] = xc[k]; o[4 + k] = nv[k]; o[8 + k] = F[k];
+        ft[k] = F[k]; ft[3 + k] = TA[k]; ft[6 + k] = TB[k];
+      }
+      o[7] = d;
+      double* tp = W.tape + static_cast<size_t>(q) * kTapeDoubles;
+      for (int k = 0; k < kTapeDoubles; ++k) tp[k] = 0.0;
+      atomicAdd(&W.counters[5], 1);
+    }
+  }
+}
+
+}  // namespace
+
+void launch_box(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel, double* pair_out,
+                int grid, cudaStream_t st) {
+  launch_pdl(k_box_pairs, dim3(grid), dim3(kBoxWarps * 32), 0, st, P, S, D, W, vel, pair_out);
+}
+
+}  // namespace gbc

@@ -904,6 +904,10 @@ int narrow_grid(const Params& P) {
 
 void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel,
                    double* pair_out, int grid, cudaStream_t st) {
+  if (P.box_mode == 1) {   // the paper's box pipeline instead of every node of the pair box
+    launch_box(P, S, D, W, vel, pair_out, grid, st);
+    return;
+  }
   if (P.precision == 1) {
     if (P.smooth)
       launch_pdl(k_narrow64<true>, dim3(grid), dim3(256), 0, st, P, S, D, W, vel, pair_out);

@@ -113,7 +113,7 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   if (C.max_neighbors != 0 && C.max_neighbors != kMaxNbr) return CONTACT_EINVAL;
   if (C.max_tiles != 0 && C.max_tiles > kMaxTilesPerPair * CONTACT_NOALLOC_MAX_PAIRS) return CONTACT_EINVAL;
   if (C.precision != CONTACT_PRECISION_FP32_TILE) return CONTACT_EINVAL;
-  if (C.history != 0 || C.friction != 0 || C.n_walls != 0)
+  if (C.history != 0 || C.friction != 0 || C.n_walls != 0 || C.box_mode != 0)
     return CONTACT_EINVAL;   // contact history, friction, walls: the context path
   if (!(C.dx > 0.0) || !std::isfinite(C.dx) || (C.indicator != 0 && C.indicator != 1)) return CONTACT_EINVAL;
   if (!(C.smooth_width > 0.0) || !(C.inflate >= 0.0) || !(C.damping_c >= 0.0)) return CONTACT_EINVAL;

@@ -65,14 +65,20 @@ def _check(name, err, tol, out):
     assert np.all(err <= tol), f"{name}: err {err.max(initial=0):.3e} beyond tolerance (worst ratio {ratio.max():.2f})"
 
 
-def compare(st, g, r, fp64: bool, smooth: bool, forces=None, tol_force=None) -> Report:
+def compare(st, g, r, fp64: bool, smooth: bool, forces=None, tol_force=None, box=None) -> Report:
     """Assert parity of GPU outputs g against the oracle result r.  The
     report's numbers are the worst error / tolerance ratios (<= 1 passes).
 
     forces = (pair F [P,3], force [N,3], torque [N,3]) replaces r's forces
     (the oracle's contact-law extensions); tol_force(toln, tolx, tolV, told)
     then returns the per-pair force tolerance and the pairs whose forces are
-    reported, not asserted (their particles' sums too, like flagged pairs)."""
+    reported, not asserted (their particles' sums too, like flagged pairs).
+
+    box = (dV [P], flag [P], ext [P]) for the box pipeline: the volume of one
+    sample (counts are exact, the sample volume to FP64 rounding of the box
+    corners, relative 1e-12 L / ext for the box's smallest extent ext), the
+    pairs whose rough box or face correction the oracle reports within eps of
+    changing."""
     assert g["n_pairs"] == r.n_pairs, (g["n_pairs"], r.n_pairs)
     assert np.array_equal(g["pair_ij"], r.pair_ij), "pair list differs"
     go, ro, aux = g["pair_out"], r.pair_out.copy(), r.pair_aux
@@ -86,6 +92,10 @@ def compare(st, g, r, fp64: bool, smooth: bool, forces=None, tol_force=None) -> 
     flagged = (aux[:, 4] > 0) | (aux[:, 5] > 0) | ((gap > 0) & (gap < 4 * BAND))
     if fp64:
         flagged = np.zeros_like(flagged)
+    unit = np.full(len(flagged), dx3)   # volume of one sample
+    if box is not None:
+        unit = np.where(box[0] > 0, box[0], dx3)
+        flagged = flagged | box[1]
     clean = ~flagged
     out = {}
     V = ro[:, 0]
@@ -98,9 +108,9 @@ def compare(st, g, r, fp64: bool, smooth: bool, forces=None, tol_force=None) -> 
     # volume
     tolV = rel * np.maximum(V, dx3) + vsens
     if not smooth and not fp64:
-        tolV = np.zeros_like(V)      # integer node counts: exact
+        tolV = np.zeros_like(V) if box is None else 1e-12 * V * (1 + L / np.maximum(box[2], 1e-300))
     _check("V", np.abs(go[clean, 0] - V[clean]), tolV[clean], out)
-    flips = np.rint(np.abs(go[flagged, 0] - V[flagged]) / dx3)
+    flips = np.rint(np.abs(go[flagged, 0] - V[flagged]) / unit[flagged])
     if not smooth:
         assert np.all(flips <= aux[flagged, 4] + 1e-9), "classification flips outside the band"
     hit = clean & (V > 0)

@@ -41,5 +41,5 @@ def test_config_struct_layout():
     from paper_2401_10878_gb300.contact import Config
     # int32 + int32[3] (16), double dx (24), int32 + pad (32), 3 doubles (56),
     # 6 int32 (80): 80 bytes
-    assert ctypes.sizeof(Config) == 152
+    assert ctypes.sizeof(Config) == 160
     assert Config.dx.offset == 16 and Config.smooth_width.offset == 32 and Config.precision.offset == 56
