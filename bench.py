@@ -22,6 +22,7 @@ CPU FP64 oracle (the test-suite's reference implementation) on the host cores.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import signal
@@ -420,6 +421,20 @@ def extras(args, dev, flush, peak):
             law[name]["contacts_in_history"] = int(len(m.history()[1]))
         m.close()
     out["cubes1934_velocities"] = law
+    # the paper's box pipeline on the headline workload (rough detection, box
+    # correction, N_c^3 samples), N_c = 8 as in the paper's runs, and 16
+    boxm = {}
+    for nc in (8, 16):
+        st_b = dataclasses.replace(headline_state(0))
+        st_b.box_mode, st_b.contact_resolution = 1, nc
+        m = Contact.from_state(st_b, narrow_events=True)
+        r = time_forward(m, pd, qd, steps, 3, flush, narrow=True)
+        s_ = m.stats()
+        boxm[f"nc{nc}"] = {"ms_per_step": r["ms"] / steps, "box_kernel_ms": r["narrow_ms"] / steps,
+                           "pairs": s_["pairs"], "pairs_with_overlap": s_["overlapping"],
+                           "samples_per_step": s_["pairs"] * nc ** 3}
+        m.close()
+    out["cubes1934_box_pipeline"] = boxm
     # the headline workload between a floor and a ceiling (fixed walls, 2 of them)
     st_w = W.floor_and_ceiling(headline_state(0))
     m = Contact.from_state(st_w, narrow_events=True)

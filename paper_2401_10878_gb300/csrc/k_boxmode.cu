@@ -267,58 +267,75 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
       XA[k] = D.X[3 * i + k];
       XB[k] = D.X[3 * j + k] - r.shift[k] * P.L[k];
     }
-    double shift_face[6];
+    // per face: the FP32 nearest line (line starts as FP32 offsets from each
+    // centre: the face corner formed in FP64, plus the line's position on the
+    // face), then lane f re-clips face f's nearest line in FP64
     const int nl = Nc * Nc;
+    unsigned my_key = 0xffffffffu;
+    int my_line = 0;
     for (int f = 0; f < 6; ++f) {
       const int k = f >> 1, side = f & 1;
       const int u = k == 0 ? 1 : 0, v = k == 2 ? 1 : 2;
-      const double len = b0hi[k] - b0lo[k];
       const float sgn = side == 0 ? 1.f : -1.f;
+      const double corner[3] = {k == 0 ? (side == 0 ? b0lo[0] : b0hi[0]) : b0lo[0],
+                                k == 1 ? (side == 0 ? b0lo[1] : b0hi[1]) : b0lo[1],
+                                k == 2 ? (side == 0 ? b0lo[2] : b0hi[2]) : b0lo[2]};
+      float ca[3], cb[3];
+      for (int c = 0; c < 3; ++c) {
+        ca[c] = static_cast<float>((corner[c] - XA[c]) * P.inv_dx);
+        cb[c] = B.kind == KIND_WALL ? static_cast<float>(corner[c] * P.inv_dx - r.lo[c])
+                                    : static_cast<float>((corner[c] - XB[c]) * P.inv_dx);
+      }
+      const float du = static_cast<float>((b0hi[u] - b0lo[u]) * P.inv_dx / Nc);
+      const float dv = static_cast<float>((b0hi[v] - b0lo[v]) * P.inv_dx / Nc);
+      const float lenl = static_cast<float>((b0hi[k] - b0lo[k]) * P.inv_dx);
       float best = FLT_MAX;
       int bestl = 0x7fffffff;
       for (int l0 = 0; l0 < nl; l0 += 32) {
         const int l = l0 + lane;
         if (l < nl) {
           const int a = l / Nc, b = l - a * Nc;
-          double p[3];
-          p[u] = b0lo[u] + (a + 0.5) * (b0hi[u] - b0lo[u]) / Nc;
-          p[v] = b0lo[v] + (b + 0.5) * (b0hi[v] - b0lo[v]) / Nc;
-          p[k] = side == 0 ? b0lo[k] : b0hi[k];
-          // FP32 offsets from each centre (lattice units), formed in FP64
-          float qa[3], qb[3];
-          for (int c = 0; c < 3; ++c) {
-            qa[c] = static_cast<float>((p[c] - XA[c]) * P.inv_dx);
-            qb[c] = B.kind == KIND_WALL ? static_cast<float>(p[c] * P.inv_dx - r.lo[c])
-                                        : static_cast<float>((p[c] - XB[c]) * P.inv_dx);
-          }
+          const float ou = (static_cast<float>(a) + 0.5f) * du, ov = (static_cast<float>(b) + 0.5f) * dv;
+          float qa[3] = {ca[0], ca[1], ca[2]}, qb[3] = {cb[0], cb[1], cb[2]};
+          qa[u] += ou; qb[u] += ou;
+          qa[v] += ov; qb[v] += ov;
           float a0, a1, c0, c1;
           clip_f(A, qa, k, sgn, &a0, &a1);
           clip_f(B, qb, k, sgn, &c0, &c1);
           const float tin = fmaxf(fmaxf(a0, c0), 0.f);
-          const float tout = fminf(fminf(a1, c1), static_cast<float>(len * P.inv_dx));
+          const float tout = fminf(fminf(a1, c1), lenl);
           if (tin <= tout && tin < best) { best = tin; bestl = l; }
         }
       }
-      // the face's nearest line (first index on ties), re-clipped in FP64
-      unsigned key = best < FLT_MAX ? __float_as_uint(best) : 0xffffffffu;   // best >= 0: bits order as floats
+      // the face's nearest line (first index on ties): t >= 0, so the bits order as the values
+      const unsigned key = best < FLT_MAX ? __float_as_uint(best) : 0xffffffffu;
       const unsigned kmin = __reduce_min_sync(kFull, key);
       const int lmin = __reduce_min_sync(kFull, key == kmin ? bestl : 0x7fffffff);
-      double sh = 0.0;
-      if (kmin != 0xffffffffu) {
-        const int a = lmin / Nc, b = lmin - a * Nc;
-        double p[3];
-        p[u] = b0lo[u] + (a + 0.5) * (b0hi[u] - b0lo[u]) / Nc;
-        p[v] = b0lo[v] + (b + 0.5) * (b0hi[v] - b0lo[v]) / Nc;
-        p[k] = side == 0 ? b0lo[k] : b0hi[k];
-        double a0, a1, c0, c1;
-        clip_d(P, S, D, i, XA, p, k, side == 0 ? 1.0 : -1.0, &a0, &a1);
-        clip_d(P, S, D, j, XB, p, k, side == 0 ? 1.0 : -1.0, &c0, &c1);
-        const double tin = fmax(fmax(a0, c0), 0.0);
-        const double tout = fmin(fmin(a1, c1), len);
-        sh = tin <= tout ? tin : static_cast<double>(__uint_as_float(kmin)) * P.dx;
+      if (lane == f) {
+        my_key = kmin;
+        my_line = lmin;
       }
-      shift_face[f] = sh;
     }
+    double my_shift = 0.0;
+    if (lane < 6 && my_key != 0xffffffffu) {
+      const int f = lane, k = f >> 1, side = f & 1;
+      const int u = k == 0 ? 1 : 0, v = k == 2 ? 1 : 2;
+      const int a = my_line / Nc, b = my_line - a * Nc;
+      double p[3];
+      p[u] = b0lo[u] + (a + 0.5) * (b0hi[u] - b0lo[u]) / Nc;
+      p[v] = b0lo[v] + (b + 0.5) * (b0hi[v] - b0lo[v]) / Nc;
+      p[k] = side == 0 ? b0lo[k] : b0hi[k];
+      double a0, a1, c0, c1;
+      clip_d(P, S, D, i, XA, p, k, side == 0 ? 1.0 : -1.0, &a0, &a1);
+      clip_d(P, S, D, j, XB, p, k, side == 0 ? 1.0 : -1.0, &c0, &c1);
+      const double len = b0hi[k] - b0lo[k];
+      const double tin = fmax(fmax(a0, c0), 0.0);
+      const double tout = fmin(fmin(a1, c1), len);
+      my_shift = tin <= tout ? tin : static_cast<double>(__uint_as_float(my_key)) * P.dx;
+    }
+    double shift_face[6];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) shift_face[f] = __shfl_sync(kFull, my_shift, f);
     double lo1[3], step[3];
     for (int k = 0; k < 3; ++k) {
       double l = b0lo[k] + shift_face[2 * k], h = b0hi[k] - shift_face[2 * k + 1];
