@@ -123,7 +123,7 @@ __device__ __forceinline__ void clip_f(const ShapeF& s, const float q[3], int k,
     else if (a > 0.f) { *t0 = FLT_MAX; *t1 = -FLT_MAX; }
   };
   if (s.kind == KIND_SPHERE) {
-    const float b = sgn * q[k];
+    const float b = sgn * (k == 0 ? q[0] : (k == 1 ? q[1] : q[2]));
     const float c = fmaf(q[0], q[0], fmaf(q[1], q[1], q[2] * q[2])) - s.sz[0] * s.sz[0];
     const float disc = b * b - c;
     if (disc < 0.f) { *t0 = FLT_MAX; *t1 = -FLT_MAX; return; }
@@ -151,25 +151,18 @@ __device__ __forceinline__ void clip_f(const ShapeF& s, const float q[3], int k,
 }
 
 // FP64 interval of the line p + t e (physical units) inside particle / wall
-// `pid`, the same clipping as the FP32 form; used for each face's nearest line.
+// `pid`, the same clipping as the FP32 form; used for each face's nearest
+// line.  The bounds -a/b of the face planes are compared as fractions (b
+// carries the sign), so only the two winning ones are divided.
 __device__ void clip_d(const Params& P, const Shapes& S, const Parts& D, int pid, const double X[3], const double p[3],
                        int k, double sgn, double* t0, double* t1) {
-  *t0 = -DBL_MAX;
-  *t1 = DBL_MAX;
   const int type = S.type[pid];
   const double* R = D.R + 9 * static_cast<size_t>(pid);
-  auto plane = [&](double n0, double n1, double n2, double off) {
-    const double a = ((n0 * p[0] + n1 * p[1]) + n2 * p[2]) - off;
-    const double b = sgn * (k == 0 ? n0 : (k == 1 ? n1 : n2));
-    if (b > 0.0) *t1 = fmin(*t1, -a / b);
-    else if (b < 0.0) *t0 = fmax(*t0, -a / b);
-    else if (a > 0.0) { *t0 = DBL_MAX; *t1 = -DBL_MAX; }
-  };
   if (type == 0) {   // sphere
     const double r = S.param[3 * pid] + P.inflate;
-    const double q[3] = {p[0] - X[0], p[1] - X[1], p[2] - X[2]};
-    const double b = sgn * q[k];
-    const double c = (q[0] * q[0] + q[1] * q[1] + q[2] * q[2]) - r * r;
+    const double q0 = p[0] - X[0], q1 = p[1] - X[1], q2 = p[2] - X[2];
+    const double b = sgn * (k == 0 ? q0 : (k == 1 ? q1 : q2));
+    const double c = (q0 * q0 + q1 * q1 + q2 * q2) - r * r;
     const double disc = b * b - c;
     if (disc < 0.0) { *t0 = DBL_MAX; *t1 = -DBL_MAX; return; }
     const double sq = sqrt(disc);
@@ -177,22 +170,39 @@ __device__ void clip_d(const Params& P, const Shapes& S, const Parts& D, int pid
     *t1 = -b + sq;
     return;
   }
+  // lower bound -a0/b0 (b0 < 0), upper bound -a1/b1 (b1 > 0); none yet: b = 0
+  double a0 = 0.0, b0 = 0.0, a1 = 0.0, b1 = 0.0;
+  bool empty = false;
+  auto plane = [&](double n0, double n1, double n2, double off) {
+    const double a = ((n0 * p[0] + n1 * p[1]) + n2 * p[2]) - off;
+    const double b = sgn * (k == 0 ? n0 : (k == 1 ? n1 : n2));
+    if (b > 0.0) {   // t <= -a/b: keep the smaller, -a/b < -a1/b1  <=>  a b1 > a1 b
+      if (b1 == 0.0 || a * b1 > a1 * b) { a1 = a; b1 = b; }
+    } else if (b < 0.0) {   // t >= -a/b: keep the larger, -a/b > -a0/b0  <=>  a b0 < a0 b (b b0 > 0)
+      if (b0 == 0.0 || a * b0 < a0 * b) { a0 = a; b0 = b; }
+    } else if (a > 0.0) {
+      empty = true;
+    }
+  };
   if (type == 1) {   // cuboid
     for (int a = 0; a < 3; ++a)
       for (int sg = -1; sg <= 1; sg += 2) {
         const double n0 = sg * R[a], n1 = sg * R[3 + a], n2 = sg * R[6 + a];   // +-R e_a
         plane(n0, n1, n2, ((n0 * X[0] + n1 * X[1]) + n2 * X[2]) + S.param[3 * pid + a] + P.inflate);
       }
-    return;
+  } else {   // polytope, or a wall's single plane
+    const int f0 = S.face_off[pid], nf = S.face_off[pid + 1] - f0;
+    for (int f = 0; f < nf; ++f) {
+      const double* b = S.planes + 4 * (f0 + f);
+      const double n0 = (R[0] * b[0] + R[1] * b[1]) + R[2] * b[2];
+      const double n1 = (R[3] * b[0] + R[4] * b[1]) + R[5] * b[2];
+      const double n2 = (R[6] * b[0] + R[7] * b[1]) + R[8] * b[2];
+      plane(n0, n1, n2, ((n0 * X[0] + n1 * X[1]) + n2 * X[2]) + b[3] + P.inflate);
+    }
   }
-  const int f0 = S.face_off[pid], nf = S.face_off[pid + 1] - f0;   // polytope, or a wall's single plane
-  for (int f = 0; f < nf; ++f) {
-    const double* b = S.planes + 4 * (f0 + f);
-    const double n0 = (R[0] * b[0] + R[1] * b[1]) + R[2] * b[2];
-    const double n1 = (R[3] * b[0] + R[4] * b[1]) + R[5] * b[2];
-    const double n2 = (R[6] * b[0] + R[7] * b[1]) + R[8] * b[2];
-    plane(n0, n1, n2, ((n0 * X[0] + n1 * X[1]) + n2 * X[2]) + b[3] + P.inflate);
-  }
+  if (empty) { *t0 = DBL_MAX; *t1 = -DBL_MAX; return; }
+  *t0 = b0 != 0.0 ? -a0 / b0 : -DBL_MAX;
+  *t1 = b1 != 0.0 ? -a1 / b1 : DBL_MAX;
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -271,8 +281,10 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
     // centre: the face corner formed in FP64, plus the line's position on the
     // face), then lane f re-clips face f's nearest line in FP64
     const int nl = Nc * Nc;
+    const double inv_nc = 1.0 / Nc;
     unsigned my_key = 0xffffffffu;
     int my_line = 0;
+    auto sel = [](const double* a, int c) { return c == 0 ? a[0] : (c == 1 ? a[1] : a[2]); };
     for (int f = 0; f < 6; ++f) {
       const int k = f >> 1, side = f & 1;
       const int u = k == 0 ? 1 : 0, v = k == 2 ? 1 : 2;
@@ -286,9 +298,9 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
         cb[c] = B.kind == KIND_WALL ? static_cast<float>(corner[c] * P.inv_dx - r.lo[c])
                                     : static_cast<float>((corner[c] - XB[c]) * P.inv_dx);
       }
-      const float du = static_cast<float>((b0hi[u] - b0lo[u]) * P.inv_dx / Nc);
-      const float dv = static_cast<float>((b0hi[v] - b0lo[v]) * P.inv_dx / Nc);
-      const float lenl = static_cast<float>((b0hi[k] - b0lo[k]) * P.inv_dx);
+      const float du = static_cast<float>((sel(b0hi, u) - sel(b0lo, u)) * (P.inv_dx * inv_nc));
+      const float dv = static_cast<float>((sel(b0hi, v) - sel(b0lo, v)) * (P.inv_dx * inv_nc));
+      const float lenl = static_cast<float>((sel(b0hi, k) - sel(b0lo, k)) * P.inv_dx);
       float best = FLT_MAX;
       int bestl = 0x7fffffff;
       for (int l0 = 0; l0 < nl; l0 += 32) {
@@ -296,9 +308,10 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
         if (l < nl) {
           const int a = l / Nc, b = l - a * Nc;
           const float ou = (static_cast<float>(a) + 0.5f) * du, ov = (static_cast<float>(b) + 0.5f) * dv;
-          float qa[3] = {ca[0], ca[1], ca[2]}, qb[3] = {cb[0], cb[1], cb[2]};
-          qa[u] += ou; qb[u] += ou;
-          qa[v] += ov; qb[v] += ov;
+          // (selects, not a runtime index: the arrays stay in registers)
+          const float o0 = u == 0 ? ou : (v == 0 ? ov : 0.f), o1 = u == 1 ? ou : (v == 1 ? ov : 0.f);
+          const float o2 = u == 2 ? ou : (v == 2 ? ov : 0.f);
+          const float qa[3] = {ca[0] + o0, ca[1] + o1, ca[2] + o2}, qb[3] = {cb[0] + o0, cb[1] + o1, cb[2] + o2};
           float a0, a1, c0, c1;
           clip_f(A, qa, k, sgn, &a0, &a1);
           clip_f(B, qb, k, sgn, &c0, &c1);
@@ -322,13 +335,15 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
       const int u = k == 0 ? 1 : 0, v = k == 2 ? 1 : 2;
       const int a = my_line / Nc, b = my_line - a * Nc;
       double p[3];
-      p[u] = b0lo[u] + (a + 0.5) * (b0hi[u] - b0lo[u]) / Nc;
-      p[v] = b0lo[v] + (b + 0.5) * (b0hi[v] - b0lo[v]) / Nc;
-      p[k] = side == 0 ? b0lo[k] : b0hi[k];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double ic = c == u ? a + 0.5 : b + 0.5;
+        p[c] = c == k ? (side == 0 ? b0lo[c] : b0hi[c]) : b0lo[c] + ic * (b0hi[c] - b0lo[c]) * inv_nc;
+      }
       double a0, a1, c0, c1;
       clip_d(P, S, D, i, XA, p, k, side == 0 ? 1.0 : -1.0, &a0, &a1);
       clip_d(P, S, D, j, XB, p, k, side == 0 ? 1.0 : -1.0, &c0, &c1);
-      const double len = b0hi[k] - b0lo[k];
+      const double len = sel(b0hi, k) - sel(b0lo, k);
       const double tin = fmax(fmax(a0, c0), 0.0);
       const double tout = fmin(fmin(a1, c1), len);
       my_shift = tin <= tout ? tin : static_cast<double>(__uint_as_float(my_key)) * P.dx;
@@ -344,7 +359,7 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
         h = b0hi[k];
       }
       lo1[k] = l;
-      step[k] = (h - l) / Nc;
+      step[k] = (h - l) * inv_nc;
     }
     // 3. the N_c^3 sample points: offsets from each centre (and the box origin) in FP64, rounded once
     float oA[3], oB[3], st[3];
@@ -413,13 +428,15 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
       double xc[3], G[3], nv[3];
       const double Mx[3] = {m0, m1, m2}, Gs[3] = {g0, g1, g2};
       const double gscale = 0.5 * dV * 6.0 / P.wdx;
+      const double inv_cnt = 1.0 / static_cast<double>(cnt);
       for (int k = 0; k < 3; ++k) {
-        xc[k] = lo1[k] + (Mx[k] / cnt + 0.5) * step[k];
+        xc[k] = lo1[k] + (Mx[k] * inv_cnt + 0.5) * step[k];
         G[k] = gscale * Gs[k];
       }
       const double gn = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
       if (gn > 1e-12 * P.dx * P.dx) {
-        for (int k = 0; k < 3; ++k) nv[k] = G[k] / gn;
+        const double ig = 1.0 / gn;
+        for (int k = 0; k < 3; ++k) nv[k] = G[k] * ig;
       } else if (j >= P.n) {
         const double* e = S.planes + 4 * S.face_off[j];
         for (int k = 0; k < 3; ++k) nv[k] = -e[k];
