@@ -53,6 +53,7 @@ struct Params {
   int dx_pow2;           // 1: dx is a power of two, so x / dx == x * inv_dx exactly
   double damping_c;
   int box_mode, box_res; // 1: the paper's box pipeline with box_res (N_c) points per direction
+  int npoly;             // polytope particles (one pose warp each)
   int nwall;             // fixed walls: partner indices n .. n + nwall - 1
   const double* wall;    // [nwall,4] (m, h): the half-space m . x <= h
   int history, friction;  // contact history; tangential force
@@ -84,6 +85,7 @@ struct Shapes {
   const double* ext;       // [N,3] sphere: r + delta; cuboid: h_k + delta (AABB half sizes in the body frame)
   const float* verts32;    // [V,3] FP32 copy of the offset-shape vertices (prefilter of the extremes)
   const float* off32;      // [F] (d + inflate) / dx per face, FP32
+  const int* poly_ids;     // [npoly] the polytope particles (the pose kernel's polytope warps)
 };
 
 // Per-step particle records; rows N .. N + nwall - 1 are the walls (set once:

@@ -440,8 +440,15 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   GBC_TRY(upload(c, &d_ext, ext));
   GBC_TRY(upload(c, &d_verts32, verts32));
   GBC_TRY(upload(c, &d_off32, off32));
+  std::vector<int> poly_ids;
+  for (int p = 0; p < n; ++p)
+    if (type[p] == CONTACT_SHAPE_POLYTOPE) poly_ids.push_back(p);
+  if (poly_ids.empty()) poly_ids.push_back(0);   // (a non-empty allocation; npoly stays 0)
+  P.npoly = static_cast<int>(std::count(type.begin(), type.begin() + n, static_cast<int>(CONTACT_SHAPE_POLYTOPE)));
+  int* d_poly;
+  GBC_TRY(upload(c, &d_poly, poly_ids));
   c->S = Shapes{d_type, d_param, d_foff, d_planes, d_voff, d_verts, d_young, d_pois, d_size, d_nomops, d_compl,
-                d_ext, d_verts32, d_off32};
+                d_ext, d_verts32, d_off32, d_poly};
 
   Parts& D = c->D;
   GBC_TRY(dev_alloc(c, &D.X, 3 * static_cast<size_t>(nrows)));

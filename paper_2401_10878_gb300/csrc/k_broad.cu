@@ -25,9 +25,180 @@ __device__ __forceinline__ int clamp_node(double v) {
 // range along k, the FP32 sweep geometry and, on axis 0, the bin slot.  FP64
 // is kept to what the bit-exact node range needs (every FP64 instruction
 // costs ~64 cycles per warp on this GPU), and spread over three threads.
+// Polytope p by one warp: the node range along each axis (the extreme
+// projections of the offset-shape vertices: an FP32 prefilter over the
+// vertices on all lanes, FP64 for the at most two candidates per side, all
+// vertices in FP64 when more lie within the prefilter's window) and the
+// FP32 world planes (faces on lanes).  The FP64 arithmetic is the per-axis
+// thread's, operation for operation, so the node range is the same bit for bit.
+__device__ void pose_polytope(const Params& P, const Shapes& S, const Parts& D, int p, const double* __restrict__ pos,
+                              const double* __restrict__ quat) {
+  const int lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  double q[4];
+  for (int c = 0; c < 4; ++c) q[c] = quat[4 * p + c];
+  bool bad = false;
+  double Xv[3];
+  for (int c = 0; c < 3; ++c) {
+    const double v = pos[3 * p + c];
+    long long b = __double_as_longlong(v);
+    if (b == static_cast<long long>(0x8000000000000000ULL)) b = 0;
+    const bool ok = b >= 0 && b < __double_as_longlong(P.L[c]);
+    bad = bad || !ok;
+    Xv[c] = ok ? __longlong_as_double(b) : 0.0;
+  }
+  const double nn = dadd(dadd(dadd(dmul(q[0], q[0]), dmul(q[1], q[1])), dmul(q[2], q[2])), dmul(q[3], q[3]));
+  if (!(nn > 1e-24) || !(nn < 1e300)) {
+    bad = true;
+    q[0] = 1.0; q[1] = q[2] = q[3] = 0.0;
+  }
+  const double s = bad ? 2.0 : dmul(2.0, __drcp_rn(nn));
+  // rotation rows: lane k < 3 computes row k, then every lane holds all nine
+  double rk[3] = {0.0, 0.0, 0.0};
+  if (lane < 3) rotation_row_rn(q, s, lane, rk);
+  double R[3][3];
+  float R32[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      R[k][c] = __shfl_sync(full, rk[c], k);
+      R32[k][c] = static_cast<float>(R[k][c]);
+    }
+  const int v0 = S.vert_off[p], v1 = S.vert_off[p + 1];
+  // FP32 prefilter: extremes per axis and the largest |w|_1
+  float lo32[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi32[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX}, wmax = 0.f;
+  for (int vb = v0; vb < v1; vb += 32) {
+    const int v = vb + lane;
+    if (v < v1) {
+      const float* w = S.verts32 + 3 * v;
+      const float x0 = w[0], x1 = w[1], x2 = w[2];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float tv = fmaf(R32[k][0], x0, fmaf(R32[k][1], x1, R32[k][2] * x2));
+        lo32[k] = fminf(lo32[k], tv);
+        hi32[k] = fmaxf(hi32[k], tv);
+      }
+      wmax = fmaxf(wmax, fabsf(x0) + fabsf(x1) + fabsf(x2));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      lo32[k] = fminf(lo32[k], __shfl_xor_sync(full, lo32[k], o));
+      hi32[k] = fmaxf(hi32[k], __shfl_xor_sync(full, hi32[k], o));
+    }
+    wmax = fmaxf(wmax, __shfl_xor_sync(full, wmax, o));
+  }
+  const float tol = 1e-5f * wmax + 1e-30f;
+  // candidates within tol of the FP32 extremes, the first two in vertex order
+  int lc[3][2], hc[3][2], nlo[3] = {0, 0, 0}, nhi[3] = {0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) lc[k][0] = lc[k][1] = hc[k][0] = hc[k][1] = v0;
+  for (int vb = v0; vb < v1; vb += 32) {
+    const int v = vb + lane;
+    float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+    if (v < v1) {
+      const float* w = S.verts32 + 3 * v;
+      x0 = w[0]; x1 = w[1]; x2 = w[2];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float tv = fmaf(R32[k][0], x0, fmaf(R32[k][1], x1, R32[k][2] * x2));
+      unsigned bl = __ballot_sync(full, v < v1 && tv <= lo32[k] + tol);
+      unsigned bh = __ballot_sync(full, v < v1 && tv >= hi32[k] - tol);
+      while (bl) {
+        const int l = __ffs(bl) - 1;
+        if (nlo[k] == 0) lc[k][0] = vb + l;
+        else if (nlo[k] == 1) lc[k][1] = vb + l;
+        ++nlo[k];
+        bl &= bl - 1;
+      }
+      while (bh) {
+        const int l = __ffs(bh) - 1;
+        if (nhi[k] == 0) hc[k][0] = vb + l;
+        else if (nhi[k] == 1) hc[k][1] = vb + l;
+        ++nhi[k];
+        bh &= bh - 1;
+      }
+    }
+  }
+  // exact FP64 projections of the candidates: lane k < 3 takes axis k
+  auto proj3 = [&](double r0, double r1, double r2, int v) {
+    const double* w = S.verts + 3 * v;
+    return dadd(dadd(dmul(r0, w[0]), dmul(r1, w[1])), dmul(r2, w[2]));
+  };
+  double lo = 0.0, hi = 0.0;
+  if (lane < 3) {
+    const int k = lane;
+    const int a0 = k == 0 ? lc[0][0] : (k == 1 ? lc[1][0] : lc[2][0]);
+    const int a1 = k == 0 ? lc[0][1] : (k == 1 ? lc[1][1] : lc[2][1]);
+    const int b0 = k == 0 ? hc[0][0] : (k == 1 ? hc[1][0] : hc[2][0]);
+    const int b1 = k == 0 ? hc[0][1] : (k == 1 ? hc[1][1] : hc[2][1]);
+    const int nl = k == 0 ? nlo[0] : (k == 1 ? nlo[1] : nlo[2]);
+    const int nh = k == 0 ? nhi[0] : (k == 1 ? nhi[1] : nhi[2]);
+    const double r0 = k == 0 ? R[0][0] : (k == 1 ? R[1][0] : R[2][0]);
+    const double r1 = k == 0 ? R[0][1] : (k == 1 ? R[1][1] : R[2][1]);
+    const double r2 = k == 0 ? R[0][2] : (k == 1 ? R[1][2] : R[2][2]);
+    lo = proj3(r0, r1, r2, a0);
+    hi = proj3(r0, r1, r2, b0);
+    if (nl > 1) lo = fmin(lo, proj3(r0, r1, r2, a1));
+    if (nh > 1) hi = fmax(hi, proj3(r0, r1, r2, b1));
+  }
+  // rare: more than two vertices at an extreme -> every vertex in FP64 (lanes over vertices)
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (nlo[k] > 2 || nhi[k] > 2) {
+      double l = DBL_MAX, h = -DBL_MAX;
+      for (int v = v0 + lane; v < v1; v += 32) {
+        const double tt = proj3(R[k][0], R[k][1], R[k][2], v);
+        l = fmin(l, tt);
+        h = fmax(h, tt);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        l = fmin(l, __shfl_xor_sync(full, l, o));
+        h = fmax(h, __shfl_xor_sync(full, h, o));
+      }
+      if (lane == k) {
+        lo = fmin(lo, l);
+        hi = fmax(hi, h);
+      }
+    }
+  }
+  if (lane < 3) {
+    const int k = lane;
+    const double Xk = k == 0 ? Xv[0] : (k == 1 ? Xv[1] : Xv[2]);
+    const double mn = dadd(Xk, lo), mx = dadd(Xk, hi);
+    const double a = P.dx_pow2 ? dmul(mn, P.inv_dx) : __ddiv_rn(mn, P.dx);
+    const double c = P.dx_pow2 ? dmul(mx, P.inv_dx) : __ddiv_rn(mx, P.dx);
+    D.lohi[6 * p + k] = clamp_node(ceil(a));
+    D.lohi[6 * p + 3 + k] = clamp_node(floor(c));
+  }
+  // world planes: face f on lane f (FP64 product per component, one rounding to FP32)
+  const int f0 = S.face_off[p], f1 = S.face_off[p + 1];
+  for (int f = f0 + lane; f < f1; f += 32) {
+    const double2* e = reinterpret_cast<const double2*>(S.planes + 4 * f);
+    const double2 e01 = e[0], e2x = e[1];
+    float4 o;
+    o.x = static_cast<float>(fma(R[0][0], e01.x, fma(R[0][1], e01.y, R[0][2] * e2x.x)));
+    o.y = static_cast<float>(fma(R[1][0], e01.x, fma(R[1][1], e01.y, R[1][2] * e2x.x)));
+    o.z = static_cast<float>(fma(R[2][0], e01.x, fma(R[2][1], e01.y, R[2][2] * e2x.x)));
+    o.w = S.off32[f];
+    D.wplane[f] = o;
+  }
+}
+
 __global__ void k_pose(Params P, Shapes S, Parts D, Lists W, const double* __restrict__ pos,
                        const double* __restrict__ quat) {
   pdl_begin();
+  // blocks past the per-axis threads: one polytope each
+  const int nb_main = (3 * P.n + 31) / 32;
+  if (static_cast<int>(blockIdx.x) >= nb_main) {
+    pose_polytope(P, S, D, S.poly_ids[blockIdx.x - nb_main], pos, quat);
+    return;
+  }
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   // the step's counters start at zero (the previous step has completed)
   if (t == 0) {
@@ -91,96 +262,14 @@ __global__ void k_pose(Params P, Shapes S, Parts D, Lists W, const double* __res
     mn = dsub(Xk, ext);
     mx = dadd(Xk, ext);
   } else {
-    // FP32 prefilter of the extreme vertices, FP64 only for those near the extremes
-    const int v0 = S.vert_off[p], v1 = S.vert_off[p + 1];
-    // (the FP32 projection errs by < 4e-7 * (|w0|+|w1|+|w2|); the window is 25x that)
-    // (vertices eight at a time: each batch's loads are in flight together)
-    float lo32 = FLT_MAX, hi32 = -FLT_MAX, wmax = 0.f;
-    for (int vb = v0; vb < v1; vb += 8) {
-      float x[8][3];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float* w = S.verts32 + 3 * (vb + u < v1 ? vb + u : v0);
-        x[u][0] = w[0]; x[u][1] = w[1]; x[u][2] = w[2];
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        if (vb + u < v1) {
-          const float tv = fmaf(r32[0], x[u][0], fmaf(r32[1], x[u][1], r32[2] * x[u][2]));
-          lo32 = fminf(lo32, tv);
-          hi32 = fmaxf(hi32, tv);
-          wmax = fmaxf(wmax, fabsf(x[u][0]) + fabsf(x[u][1]) + fabsf(x[u][2]));
-        }
-      }
-    }
-    const float tol = 1e-5f * wmax + 1e-30f;
-    // vertices within tol of the FP32 extremes (at most two per side kept;
-    // more than two on a side -> every vertex in FP64 below)
-    int lc[2] = {v0, v0}, hc[2] = {v0, v0}, nlo = 0, nhi = 0;
-    for (int vb = v0; vb < v1; vb += 8) {
-      float x[8][3];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float* w = S.verts32 + 3 * (vb + u < v1 ? vb + u : v0);
-        x[u][0] = w[0]; x[u][1] = w[1]; x[u][2] = w[2];
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        if (vb + u < v1) {
-          const float tv = fmaf(r32[0], x[u][0], fmaf(r32[1], x[u][1], r32[2] * x[u][2]));
-          if (tv <= lo32 + tol) {
-            if (nlo < 2) lc[nlo == 0 ? 0 : 1] = vb + u;
-            ++nlo;
-          }
-          if (tv >= hi32 - tol) {
-            if (nhi < 2) hc[nhi == 0 ? 0 : 1] = vb + u;
-            ++nhi;
-          }
-        }
-      }
-    }
-    // exact FP64 projections of the candidates (explicit rounding: compared bit for bit)
-    auto proj = [&](int v) {
-      const double* w = S.verts + 3 * v;
-      return dadd(dadd(dmul(r[0], w[0]), dmul(r[1], w[1])), dmul(r[2], w[2]));
-    };
-    double lo = proj(lc[0]), hi = proj(hc[0]);
-    if (nlo > 1) lo = fmin(lo, proj(lc[1]));
-    if (nhi > 1) hi = fmax(hi, proj(hc[1]));
-    if (nlo > 2 || nhi > 2) {   // rare: many vertices at the extremes
-      for (int v = v0; v < v1; ++v) {
-        const double tt = proj(v);
-        lo = fmin(lo, tt);
-        hi = fmax(hi, tt);
-      }
-    }
-    mn = dadd(Xk, lo);
-    mx = dadd(Xk, hi);
-    // world normals: component k of R n per face (FP64 product, one rounding to FP32)
-    float* wp = reinterpret_cast<float*>(D.wplane);
-    const int f0 = S.face_off[p], f1 = S.face_off[p + 1];
-    for (int fb = f0; fb < f1; fb += 4) {   // four faces at a time
-      double2 e01[4], e2x[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const double2* e = reinterpret_cast<const double2*>(S.planes + 4 * (fb + u < f1 ? fb + u : f0));
-        e01[u] = e[0];
-        e2x[u] = e[1];
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int f = fb + u;
-        if (f < f1) {
-          wp[4 * f + k] = static_cast<float>(fma(r[0], e01[u].x, fma(r[1], e01[u].y, r[2] * e2x[u].x)));
-          if (k == 0) wp[4 * f + 3] = S.off32[f];
-        }
-      }
-    }
+    mn = mx = 0.0;   // polytope: node range and world planes by the polytope warps below
   }
   const double a = P.dx_pow2 ? dmul(mn, P.inv_dx) : __ddiv_rn(mn, P.dx);
   const double c = P.dx_pow2 ? dmul(mx, P.inv_dx) : __ddiv_rn(mx, P.dx);
-  D.lohi[6 * p + k] = clamp_node(ceil(a));
-  D.lohi[6 * p + 3 + k] = clamp_node(floor(c));
+  if (type != 2) {
+    D.lohi[6 * p + k] = clamp_node(ceil(a));
+    D.lohi[6 * p + 3 + k] = clamp_node(floor(c));
+  }
   D.Xf[3 * p + k] = xs[k];
   const double xl = Xk * P.inv_dx;
   const double kx = rint(xl);
@@ -640,7 +729,8 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
 void launch_pose(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* pos,
                  const double* quat, cudaStream_t st) {
   // one-warp blocks: the FP64 chains of different warps land on different sub-partitions
-  const int nb = (3 * P.n + 31) / 32;
+  // (plus one block per polytope for its vertices and faces)
+  const int nb = (3 * P.n + 31) / 32 + P.npoly;
   if (nb > 0) launch_pdl(k_pose, dim3(nb), dim3(32), 0, st, P, S, D, W, pos, quat);
 }
 
