@@ -252,9 +252,9 @@ contact_status contact_particle_boxes(contact_ctx* ctx, int32_t* lo_hi);
  * contacts, sorted by (i, j), to ij [max_rows,2] i32 host and c [max_rows]
  * f64 host; *n receives the number of contacts (which may exceed max_rows).
  * contact_history_set replaces them with the n_rows given (host arrays, as
- * a checkpoint to resume from): CONTACT_EINVAL for a row with i >= j, an
- * index outside [0, N), a repeated (i, j), or more than max_neighbors rows
- * of one i.  contact_history_reset forgets every contact (asynchronous, on
+ * a checkpoint to resume from): CONTACT_EINVAL for a row with i >= j, i
+ * outside [0, N), j outside [0, N + n_walls) (j >= N: a wall), a repeated
+ * (i, j), or more than max_neighbors rows of one i.  contact_history_reset forgets every contact (asynchronous, on
  * the context stream). */
 contact_status contact_history_get(contact_ctx* ctx, int64_t max_rows, int32_t* ij, double* c, int64_t* n);
 contact_status contact_history_set(contact_ctx* ctx, int64_t n_rows, const int32_t* ij, const double* c);

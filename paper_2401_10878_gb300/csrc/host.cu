@@ -731,7 +731,8 @@ contact_status contact_history_set(contact_ctx* c, int64_t n_rows, const int32_t
   std::vector<double> hc(np * cap, 0.0);
   for (int64_t r = 0; r < n_rows; ++r) {
     const int i = ij[2 * r], j = ij[2 * r + 1];
-    if (i < 0 || j <= i || j >= c->P.n) return fail(c, CONTACT_EINVAL, "contact_history_set: bad (i, j)");
+    if (i < 0 || i >= c->P.n || j <= i || j >= c->P.n + c->P.nwall)   // j >= N: a wall
+      return fail(c, CONTACT_EINVAL, "contact_history_set: bad (i, j)");
     if (cnt[i] >= c->P.max_nbr) return fail(c, CONTACT_EINVAL, "contact_history_set: more rows of i than max_neighbors");
     for (int m = 0; m < cnt[i]; ++m)
       if (hj[i * cap + m] == j) return fail(c, CONTACT_EINVAL, "contact_history_set: repeated (i, j)");

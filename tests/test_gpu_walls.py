@@ -115,8 +115,15 @@ def test_walls_with_history_and_friction():
         forces, tol = tr.step(sts, pos[s], vel, rb, rx, rb)
         print("walls + law", s, compare(sts, g, rb, fp64=False, smooth=False, forces=forces, tol_force=tol))
         hist = (rx.hist_ij, rx.hist_c)
-        gij, _ = m.history()
+        gij, gc = m.history()
         assert (gij[:, 1] >= st.n).sum() > 10   # wall contacts kept in the history
+    # a checkpoint with wall contacts restores into a fresh context
+    m2 = model_for(st, precision=0, history=True, restitution=law.restitution, friction=True, mu_s=law.mu_s,
+                   mu_k=law.mu_k, u_k=law.u_k)
+    m2.set_history(gij, gc)
+    hij, hc = m2.history()
+    assert np.array_equal(hij, gij) and np.array_equal(hc, gc)
+    m2.close()
     m.close()
 
 
