@@ -265,7 +265,8 @@ contact_status contact_history_reset(contact_ctx* ctx);
  * contact (Carvalho-Martins, as used in Sec. 2.3). */
 double contact_damping_factor(double restitution, double u0);
 
-/* Number of kernel launches one contact_step / contact_backward issues. */
+/* Number of kernel launches one contact_step / contact_backward issues (a
+ * step has one more when polytopes are present). */
 int32_t contact_kernels_per_step(const contact_ctx* ctx);
 int32_t contact_kernels_per_backward(const contact_ctx* ctx);
 

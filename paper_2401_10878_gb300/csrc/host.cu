@@ -755,7 +755,7 @@ contact_status contact_history_reset(contact_ctx* c) {
   return e == cudaSuccess ? CONTACT_OK : cuda_fail(c, e, "cudaMemsetAsync");
 }
 
-int32_t contact_kernels_per_step(const contact_ctx*) { return 5; }
+int32_t contact_kernels_per_step(const contact_ctx* c) { return c != nullptr && c->P.npoly > 0 ? 6 : 5; }
 int32_t contact_kernels_per_backward(const contact_ctx*) { return 3; }
 
 contact_status contact_backward(contact_ctx* c, const double* grad_force, const double* grad_torque,

@@ -190,15 +190,16 @@ __device__ void pose_polytope(const Params& P, const Shapes& S, const Parts& D, 
   }
 }
 
+// K1b: one warp per polytope (node range and world planes), its own kernel so
+// that the per-axis kernel's code stays as lean as it is without polytopes.
+__global__ void k_pose_poly(Params P, Shapes S, Parts D, const double* __restrict__ pos, const double* __restrict__ quat) {
+  pdl_begin();
+  pose_polytope(P, S, D, S.poly_ids[blockIdx.x], pos, quat);
+}
+
 __global__ void k_pose(Params P, Shapes S, Parts D, Lists W, const double* __restrict__ pos,
                        const double* __restrict__ quat) {
   pdl_begin();
-  // blocks past the per-axis threads: one polytope each
-  const int nb_main = (3 * P.n + 31) / 32;
-  if (static_cast<int>(blockIdx.x) >= nb_main) {
-    pose_polytope(P, S, D, S.poly_ids[blockIdx.x - nb_main], pos, quat);
-    return;
-  }
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   // the step's counters start at zero (the previous step has completed)
   if (t == 0) {
@@ -729,9 +730,10 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
 void launch_pose(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* pos,
                  const double* quat, cudaStream_t st) {
   // one-warp blocks: the FP64 chains of different warps land on different sub-partitions
-  // (plus one block per polytope for its vertices and faces)
-  const int nb = (3 * P.n + 31) / 32 + P.npoly;
+  // (then one block per polytope for its vertices and faces)
+  const int nb = (3 * P.n + 31) / 32;
   if (nb > 0) launch_pdl(k_pose, dim3(nb), dim3(32), 0, st, P, S, D, W, pos, quat);
+  if (P.npoly > 0) launch_pdl(k_pose_poly, dim3(P.npoly), dim3(32), 0, st, P, S, D, pos, quat);
 }
 
 
