@@ -163,9 +163,9 @@ __device__ __forceinline__ bool wall_box(const double* e, double delta, double d
 }
 
 // Work lists shared by the step's kernels.
-// One overlapping pair for the force law (staged in shared memory by the warp
-// that completes it): its FP64 sums (count, first moments, band terms of G),
-// its deepest node, and the pair record's geometry.
+// One overlapping pair for the force law (appended to the step's overlap list
+// by the warp that completes it): its FP64 sums (count, first moments, band
+// terms of G), its deepest node, and the pair record's geometry.
 struct OvlRec {
   double s[7];     // sum of H, of H x (x, y, z) in box coordinates, of the band terms (x, y, z)
   int q;           // pair index
@@ -192,6 +192,7 @@ struct Lists {
   double* hist_c;   // [2, N, max_nbr] its damping factor
   int* hist_n;      // [2, N] contacts per particle; buffer (steps & 1) is read, the other written
   PairRec* pairs;   // [max_pairs]
+  OvlRec* olist;    // [max_pairs] the step's overlapping pairs (counters[5] of them): the force law's work list
   int* tile_pair;   // [max_tiles] pair of each tile
   PairRec* tiles;   // [kCostBuckets, max_tiles] one record per tile (the pair's record with tile and
                     // pair set), in the node sweep's queue order: bucket 0 (dearest) first
@@ -367,6 +368,8 @@ void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists
 int narrow_grid(const Params& P);
 void launch_box(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel, double* pair_out,
                 int grid, cudaStream_t st);
+void launch_force(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel, double* pair_out,
+                  cudaStream_t st);
 void launch_particle_sum(const Params& P, const Parts& D, const Lists& W, double* force, double* torque,
                          cudaStream_t st);
 size_t adjoint_scratch_doubles(int max_pairs, int max_tiles);

@@ -170,6 +170,7 @@ void enqueue_step(contact_ctx* c, bool capturing, const double* pos, const doubl
   if (c->cfg.narrow_events) cudaEventRecordWithFlags(c->ev_narrow[0], c->stream, ev_flags);
   launch_narrow(c->P, c->S, c->D, c->W, vel, pair_out, c->grid_narrow, c->stream);
   if (c->cfg.narrow_events) cudaEventRecordWithFlags(c->ev_narrow[1], c->stream, ev_flags);
+  if (c->P.box_mode == 0) launch_force(c->P, c->S, c->D, c->W, vel, pair_out, c->stream);
   launch_particle_sum(c->P, c->D, c->W, force, torque, c->stream);
 }
 
@@ -512,6 +513,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
     GBC_TRY(dev_alloc(c, &W.hist_n, 2 * static_cast<size_t>(n)));
   }
   GBC_TRY(dev_alloc(c, &W.pairs, mp));
+  GBC_TRY(dev_alloc(c, &W.olist, mp));
   GBC_TRY(dev_alloc(c, &W.tile_pair, mt));
   GBC_TRY(dev_alloc(c, &W.tiles, mt * kCostBuckets));
   GBC_TRY(dev_alloc(c, &W.partial, mt * kPartialFloats));
@@ -755,7 +757,10 @@ contact_status contact_history_reset(contact_ctx* c) {
   return e == cudaSuccess ? CONTACT_OK : cuda_fail(c, e, "cudaMemsetAsync");
 }
 
-int32_t contact_kernels_per_step(const contact_ctx* c) { return c != nullptr && c->P.npoly > 0 ? 6 : 5; }
+int32_t contact_kernels_per_step(const contact_ctx* c) {
+  if (c == nullptr) return 0;
+  return 5 + (c->P.npoly > 0 ? 1 : 0) + (c->P.box_mode == 0 ? 1 : 0);   // + polytope pose, + force law
+}
 int32_t contact_kernels_per_backward(const contact_ctx*) { return 3; }
 
 contact_status contact_backward(contact_ctx* c, const double* grad_force, const double* grad_torque,

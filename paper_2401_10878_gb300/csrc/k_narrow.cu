@@ -542,9 +542,9 @@ __device__ __forceinline__ float reduce_tile(const Partial& o) {
   return v;   // lane c < 9: component c of the tile partial
 }
 
-// The force law of the warp's staged overlapping pairs (whole warp).
+// The force law of the n <= 8 overlapping pairs staged in ov (whole warp).
 __device__ __forceinline__ void flush_overlaps(const Params& P, const Shapes& S, const Parts& D, const Lists& W,
-                                               const double* vel, double* pair_out, OvlRec* ov, int& nov) {
+                                               const double* vel, double* pair_out, OvlRec* ov, int nov) {
   if (nov == 0) return;
   __syncwarp();
   ForceArgs a;
@@ -568,28 +568,29 @@ __device__ __forceinline__ void flush_overlaps(const Params& P, const Shapes& S,
   }
   pair_force_law(a, ov, nov);
   __syncwarp();
-  nov = 0;
 }
 
 // End of a pair (called by the whole warp once all its nodes are summed):
 // lanes c < 7 hold the FP64 sum of component c, every lane the deepest node.
-// A pair without overlap gets its zero outputs; an overlapping pair is staged
-// in the warp's shared-memory slots (ov, nov of kForcePairsPerPass) and its
-// force law runs when the slots are full or the warp has no more tiles.
-__device__ __forceinline__ void pair_done(const Params& P, const Shapes& S, const Parts& D, const Lists& W,
-                                          const PairRec& r, const double* vel, double* pair_out, OvlRec* ov,
-                                          int& nov, double sv, int idx) {
+// A pair without overlap gets its zero outputs; an overlapping pair is
+// appended to the step's overlap list, whose force law the next kernel runs
+// eight pairs per warp pass.
+__device__ __forceinline__ void pair_done(const Params& P, const Lists& W, const PairRec& r, double* pair_out,
+                                          double sv, int idx) {
   const int lane = threadIdx.x & 31;
   const int q = r.pair;
   const double s0 = __shfl_sync(kFull, sv, 0);
   if (__double_as_longlong(s0) > 0) {   // V > 0
-    OvlRec* e = ov + nov;
-    if (lane < 7) e->s[lane] = sv;
-    if (lane == 7) e->q = q;
-    if (lane == 8) e->idx = idx;
-    if (lane >= 9 && lane < 20) (&e->i)[lane - 9] = reinterpret_cast<const int*>(&r)[lane - 9];   // i, j, lo, dim, shift
-    if (lane == 0) atomicAdd(&W.counters[5], 1);   // overlapping pairs (statistics)
-    if (++nov == kForcePairsPerPass) flush_overlaps(P, S, D, W, vel, pair_out, ov, nov);
+    int slot = 0;
+    if (lane == 0) slot = atomicAdd(&W.counters[5], 1);
+    slot = __shfl_sync(kFull, slot, 0);
+    if (slot < P.max_pairs) {
+      OvlRec* e = W.olist + slot;
+      if (lane < 7) e->s[lane] = sv;
+      if (lane == 7) e->q = q;
+      if (lane == 8) e->idx = idx;
+      if (lane >= 9 && lane < 20) (&e->i)[lane - 9] = reinterpret_cast<const int*>(&r)[lane - 9];   // i, j, lo, dim, shift
+    }
   } else {
     if (lane < 11) pair_out[static_cast<size_t>(q) * 11 + lane] = 0.0;
     if (lane < kFtDoubles) W.ft[static_cast<size_t>(q) * kFtDoubles + lane] = 0.0;
@@ -602,14 +603,13 @@ __device__ __forceinline__ void pair_done(const Params& P, const Shapes& S, cons
 // pair's last tile sums all of them in FP64 in a fixed order (4 tile slots x
 // 8 components per lane pattern, slots combined pairwise), whichever warp
 // that is.
-__device__ __forceinline__ void tile_done(const Params& P, const Shapes& S, const Parts& D, const Lists& W,
-                                          const PairRec& r, const double* vel, double* pair_out, OvlRec* ov, int& nov,
+__device__ __forceinline__ void tile_done(const Params& P, const Lists& W, const PairRec& r, double* pair_out,
                                           float v) {
   const int lane = threadIdx.x & 31;
   if (r.ntiles == 1) {
     const int idx = __shfl_sync(kFull, __float_as_int(v), 8);
     // (the hardware conversion: one issue slot on the node sweep's otherwise idle FP64 pipe)
-    pair_done(P, S, D, W, r, vel, pair_out, ov, nov, lane < 7 ? static_cast<double>(v) : 0.0, idx);
+    pair_done(P, W, r, pair_out, lane < 7 ? static_cast<double>(v) : 0.0, idx);
     return;
   }
   const size_t t0 = static_cast<size_t>(r.tile0);
@@ -655,7 +655,7 @@ __device__ __forceinline__ void tile_done(const Params& P, const Shapes& S, cons
     const int oi = __shfl_xor_sync(kFull, bi, o);
     if (ob > bf || (ob == bf && oi < bi)) { bf = ob; bi = oi; }
   }
-  pair_done(P, S, D, W, r, vel, pair_out, ov, nov, acc, __shfl_sync(kFull, bi, 7));
+  pair_done(P, W, r, pair_out, acc, __shfl_sync(kFull, bi, 7));
 }
 
 // Kernel variants: the full set of pair kinds, or spheres and cuboids only
@@ -739,7 +739,6 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_narrow32(Params P, Shapes S,
                                                                                   Lists W, const double* vel,
                                                                                   double* pair_out) {
   __shared__ __align__(16) PairRec s_rec[kWarps][2];
-  __shared__ OvlRec s_ovl[kWarps][kForcePairsPerPass];
   __shared__ float4 s_planes[kWarps][2][kMaxFaces];
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -769,7 +768,6 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_narrow32(Params P, Shapes S,
   if (t < ntiles) store_rec_part(&s_rec[wid][0], lane, load_rec_part(rec_at(t), lane));
   __syncwarp();
   int buf = 0;
-  int nov = 0;   // overlapping pairs staged in s_ovl[wid]
   while (t < ntiles) {
     int tn = 0;
     if (lane == 0) tn = atomicAdd(&W.counters[2], 1) + nwarps;  // next tile, fetched ahead
@@ -784,21 +782,46 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_narrow32(Params P, Shapes S,
     const PairRec& r = s_rec[wid][buf];
     const Partial o = dispatch<SMOOTH, SET>(P, S, D, r, r.tile, s_planes[wid][0], s_planes[wid][1], prefetch);
     prefetch();
-    tile_done(P, S, D, W, r, vel, pair_out, s_ovl[wid], nov, reduce_tile<SMOOTH>(o));
+    tile_done(P, W, r, pair_out, reduce_tile<SMOOTH>(o));
     __syncwarp();
     if (tn < ntiles) store_rec_part(&s_rec[wid][buf ^ 1], lane, next);
     __syncwarp();
     buf ^= 1;
     t = tn;
   }
-  flush_overlaps(P, S, D, W, vel, pair_out, s_ovl[wid], nov);
+  (void)vel;   // the velocities enter with the force law (next kernel)
+}
+
+// The force law of the step's overlapping pairs (the overlap list), eight per
+// warp pass (four lanes each).  Batch b goes to block b mod grid, so the FP64
+// passes spread over the SMs instead of meeting at the sweep's tail.
+__global__ void __launch_bounds__(kWarps * 32) k_force(Params P, Shapes S, Parts D, Lists W, const double* vel,
+                                                       double* pair_out) {
+  __shared__ __align__(16) OvlRec s_ovl[kWarps][kForcePairsPerPass];
+  pdl_begin();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nov = min(W.counters[5], P.max_pairs);
+  const int nb = (nov + kForcePairsPerPass - 1) / kForcePairsPerPass;
+  for (int b = wid * gridDim.x + blockIdx.x; b < nb; b += gridDim.x * kWarps) {
+    const int first = b * kForcePairsPerPass, n = min(kForcePairsPerPass, nov - first);
+    // stage the batch: 8 records x 128 bytes, two 16-byte pieces per lane
+    const int4* src = reinterpret_cast<const int4*>(W.olist + first);
+    int4* dst = reinterpret_cast<int4*>(s_ovl[wid]);
+    constexpr int kPieces = static_cast<int>(sizeof(OvlRec) / 16);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = lane + 32 * u;
+      if (e < n * kPieces) dst[e] = src[e];
+    }
+    __syncwarp();
+    flush_overlaps(P, S, D, W, vel, pair_out, s_ovl[wid], n);
+  }
 }
 
 // ---------------------------------------------------------------- FP64 form
 template <bool SMOOTH>
 __global__ void __launch_bounds__(256) k_narrow64(Params P, Shapes S, Parts D, Lists W, const double* vel,
                                                   double* pair_out) {
-  __shared__ OvlRec s_ovl;
   __shared__ double s_red[8][8];
   __shared__ double s_bf[8];
   __shared__ int s_bi[8];
@@ -869,9 +892,7 @@ __global__ void __launch_bounds__(256) k_narrow64(Params P, Shapes S, Parts D, L
         if (lane < 7) tot += s_red[w][lane];
         if (s_bf[w] > b || (s_bf[w] == b && s_bi[w] < bidx)) { b = s_bf[w]; bidx = s_bi[w]; }
       }
-      int nov = 0;
-      pair_done(P, S, D, W, W.pairs[p], vel, pair_out, &s_ovl, nov, tot, bidx);
-      flush_overlaps(P, S, D, W, vel, pair_out, &s_ovl, nov);
+      pair_done(P, W, W.pairs[p], pair_out, tot, bidx);
     }
     __syncthreads();
   }
@@ -900,6 +921,14 @@ int narrow_grid(const Params& P) {
              : P.kind_set == SET_SC ? blocks_per_sm<false, SET_SC>() : blocks_per_sm<false, SET_ALL>();
   }
   return sms * per_sm;
+}
+
+void launch_force(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel, double* pair_out,
+                  cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  launch_pdl(k_force, dim3(sms > 0 ? 2 * sms : 2), dim3(kWarps * 32), 0, st, P, S, D, W, vel, pair_out);
 }
 
 void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel,

@@ -228,6 +228,7 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   W.row_off = cv.take<int>(N + 1);
   W.grp_sum = cv.take<int>((N + kRowGroup - 1) / kRowGroup);
   W.pairs = cv.take<PairRec>(MP);
+  W.olist = cv.take<OvlRec>(MP);
   W.tile_pair = cv.take<int>(MT);
   W.tiles = cv.take<PairRec>(MT * kCostBuckets);
   W.partial = cv.take<float>(MT * kPartialFloats);
@@ -256,6 +257,7 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   launch_broad(P, D, W, s);
   launch_plan(P, S, D, W, pair_ij, n_pairs, s);
   launch_narrow(P, S, D, W, nullptr, pair_out, narrow_grid(P), s);
+  launch_force(P, S, D, W, nullptr, pair_out, s);
   launch_particle_sum(P, D, W, force, torque, s);
   if (cudaGetLastError() != cudaSuccess) return CONTACT_ECUDA;
   // synchronous: the device error word is read back before returning
