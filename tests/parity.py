@@ -1,6 +1,6 @@
 """Shared comparison of the CUDA contact step with the FP64 oracle.
 
-Tolerances (north star, restated): the candidate pair list and the particle
+Tolerances: the candidate pair list and the particle
 node ranges are compared bit for bit; volume and first moments within 1e-6
 relative; force and torque within 1e-5 relative (FP32-tile form).
 
