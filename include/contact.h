@@ -260,6 +260,16 @@ contact_status contact_history_get(contact_ctx* ctx, int64_t max_rows, int32_t* 
 contact_status contact_history_set(contact_ctx* ctx, int64_t n_rows, const int32_t* ij, const double* c);
 contact_status contact_history_reset(contact_ctx* ctx);
 
+/* Volume centroid (host) of the polytope {y : n_f . y <= d_f} given by
+ * n_faces >= 4 rows (n, d) with unit n and d > 0 (origin inside), bounded.
+ * Poses refer to the centre of mass (Sec. 2.2): contact_init refuses a
+ * polytope whose centroid lies more than 1e-6 x (its smallest d) from its
+ * body origin (CONTACT_EINVAL); shifting every d_f by -n_f . centroid moves
+ * the origin there (the position then names the centroid).
+ *   planes [n_faces,4] host; centroid [3] host out.  CONTACT_EINVAL on
+ *   invalid planes. */
+contact_status contact_polytope_centroid(const double* planes, int32_t n_faces, double* centroid);
+
 /* Eq. (damping_factor): c = 1.5 (1-e)(11-e) / ((1+9e) u0) for u0 > 0, else 0,
  * from the coefficient of restitution e and the relative speed u0 at first
  * contact (Carvalho-Martins, as used in Sec. 2.3). */

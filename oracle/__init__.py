@@ -74,6 +74,8 @@ def _load():
         lib.oracle_box_pipeline.restype = ctypes.c_int64
         lib.oracle_box_pipeline.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 8 + \
             [ctypes.c_int64] + [P] * 3
+        lib.oracle_polytope_centroid.restype = ctypes.c_int32
+        lib.oracle_polytope_centroid.argtypes = [P, ctypes.c_int32, P]
         lib.oracle_gradient.restype = ctypes.c_int64
         lib.oracle_gradient.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 13 + [ctypes.c_int32]
         lib.oracle_aabb.restype = ctypes.c_int32
@@ -309,6 +311,17 @@ def box_pipeline(st, pos=None, quat=None):
         if P <= cap:
             return rough[:P], box[:P], flags[:P]
         cap = int(P)
+
+
+def polytope_centroid(planes):
+    """Volume centroid of the polytope n . y <= d (rows (n, d), origin inside)."""
+    lib = _load()
+    pl = _c(np.asarray(planes, float).reshape(-1, 4), np.float64)
+    c = np.zeros(3)
+    rc = lib.oracle_polytope_centroid(_ptr(pl), len(pl), _ptr(c))
+    if rc != 0:
+        raise OracleError(rc)
+    return c
 
 
 def aabb(st, pos=None, quat=None):

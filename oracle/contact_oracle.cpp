@@ -189,6 +189,60 @@ std::vector<double> polytope_vertices(const std::vector<double>& pl, double delt
 // A polyhedron {n_i . y <= d_i} with all d_i > 0 is bounded iff no direction u
 // has n_i . u <= 0 for all i.  Extreme rays of the recession cone lie on
 // intersections of two plane boundaries, so testing +-(n_i x n_j) suffices.
+// Volume and centroid of the polytope {y : n_f . y <= d_f} with the origin
+// inside, as pyramids from the origin over its faces: a face of area A at
+// distance d has volume d A / 3 and its centroid 3/4 of the way from the
+// origin to the face's area centroid (triangles of the face polygon, its
+// vertices ordered around their mean).
+bool polytope_centroid(const std::vector<double>& pl, double c[3]) {
+  const std::vector<double> v = polytope_vertices(pl, 0.0);
+  const int F = static_cast<int>(pl.size() / 4), nv = static_cast<int>(v.size() / 3);
+  double V = 0.0, mom[3] = {0.0, 0.0, 0.0};
+  for (int f = 0; f < F; ++f) {
+    const double* e = &pl[4 * f];
+    std::vector<const double*> pts;
+    for (int i = 0; i < nv; ++i) {
+      const double* w = &v[3 * i];
+      if (std::fabs(e[0] * w[0] + e[1] * w[1] + e[2] * w[2] - e[3]) <= 1e-9 * std::max(1.0, std::fabs(e[3])))
+        pts.push_back(w);
+    }
+    if (pts.size() < 3) continue;
+    double ctr[3] = {0.0, 0.0, 0.0};
+    for (const double* w : pts)
+      for (int k = 0; k < 3; ++k) ctr[k] += w[k];
+    for (int k = 0; k < 3; ++k) ctr[k] /= static_cast<double>(pts.size());
+    // order around ctr by the angle in the face plane (reference direction: the first point)
+    const double ref[3] = {pts[0][0] - ctr[0], pts[0][1] - ctr[1], pts[0][2] - ctr[2]};
+    std::vector<std::pair<double, const double*>> order;
+    for (const double* w : pts) {
+      const double r[3] = {w[0] - ctr[0], w[1] - ctr[1], w[2] - ctr[2]};
+      const double cx[3] = {ref[1] * r[2] - ref[2] * r[1], ref[2] * r[0] - ref[0] * r[2], ref[0] * r[1] - ref[1] * r[0]};
+      const double sn = cx[0] * e[0] + cx[1] * e[1] + cx[2] * e[2];
+      const double cs = ref[0] * r[0] + ref[1] * r[1] + ref[2] * r[2];
+      order.push_back({std::atan2(sn, cs), w});
+    }
+    std::sort(order.begin(), order.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    double area = 0.0, ac[3] = {0.0, 0.0, 0.0};
+    for (size_t t = 0; t < order.size(); ++t) {
+      const double* p = order[t].second;
+      const double* q = order[(t + 1) % order.size()].second;
+      const double u[3] = {p[0] - ctr[0], p[1] - ctr[1], p[2] - ctr[2]};
+      const double w[3] = {q[0] - ctr[0], q[1] - ctr[1], q[2] - ctr[2]};
+      const double cx[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+      const double a = 0.5 * std::sqrt(cx[0] * cx[0] + cx[1] * cx[1] + cx[2] * cx[2]);
+      area += a;
+      for (int k = 0; k < 3; ++k) ac[k] += a * (ctr[k] + p[k] + q[k]) / 3.0;
+    }
+    if (!(area > 0.0)) continue;
+    const double vf = e[3] * area / 3.0;
+    V += vf;
+    for (int k = 0; k < 3; ++k) mom[k] += vf * 0.75 * (ac[k] / area);
+  }
+  if (!(V > 0.0)) return false;
+  for (int k = 0; k < 3; ++k) c[k] = mom[k] / V;
+  return true;
+}
+
 bool polytope_bounded(const std::vector<double>& pl) {
   const int F = static_cast<int>(pl.size() / 4);
   if (F < 4) return false;
@@ -776,6 +830,11 @@ int build_problem(Problem& pb, const Config* cfg, int32_t n, const int32_t* shap
         if (!(e[3] > 0.0)) return OR_EINVAL;                // origin strictly inside
       }
       if (!polytope_bounded(s.planes)) return OR_EINVAL;
+      // poses refer to the centre of mass (Sec. 2.2): the body origin must be the centroid
+      double cm[3], dmin = std::numeric_limits<double>::infinity();
+      if (!polytope_centroid(s.planes, cm)) return OR_EINVAL;
+      for (int f = 0; f < f1 - f0; ++f) dmin = std::min(dmin, s.planes[4 * f + 3]);
+      if (std::sqrt(cm[0] * cm[0] + cm[1] * cm[1] + cm[2] * cm[2]) > 1e-6 * dmin) return OR_EINVAL;
       s.verts = polytope_vertices(s.planes, delta);
       if (s.verts.size() < 12) return OR_EINVAL;
       for (size_t v = 0; v < s.verts.size(); v += 3) {
@@ -933,6 +992,14 @@ typedef struct {
   int32_t box_mode;
   int32_t contact_resolution;
 } oracle_config;
+
+// Volume centroid of a polytope given by n_faces rows (n, d) (origin inside).
+// Returns 0, or 1 for a polytope the centroid cannot be formed for.
+int32_t oracle_polytope_centroid(const double* planes, int32_t n_faces, double* centroid) {
+  std::vector<double> pl(planes, planes + 4 * static_cast<size_t>(n_faces));
+  if (n_faces < 4 || !polytope_bounded(pl)) return OR_EINVAL;
+  return polytope_centroid(pl, centroid) ? OR_OK : OR_EINVAL;
+}
 
 int32_t oracle_max_threads(void) {
 #ifdef _OPENMP

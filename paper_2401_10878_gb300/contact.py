@@ -31,7 +31,7 @@ EXPORTS = ["contact_config_default", "contact_init", "contact_step", "contact_ba
            "contact_clear_error", "contact_last_error", "contact_set_stream", "contact_stats",
            "contact_particle_boxes", "contact_narrow_time", "contact_damping_factor", "contact_kernels_per_step",
            "contact_kernels_per_backward", "contact_destroy", "contact_step_noalloc", "contact_step_host",
-           "contact_history_get", "contact_history_set", "contact_history_reset"]
+           "contact_history_get", "contact_history_set", "contact_history_reset", "contact_polytope_centroid"]
 
 
 class Config(ctypes.Structure):
@@ -106,6 +106,8 @@ def load_library(build_if_missing: bool = True):
     lib.contact_step_noalloc.restype = I32
     lib.contact_step_host.argtypes = [P] * 9
     lib.contact_step_host.restype = I32
+    lib.contact_polytope_centroid.argtypes = [P, I32, P]
+    lib.contact_polytope_centroid.restype = I32
     lib.contact_history_get.argtypes = [P, ctypes.c_int64, P, P, P]
     lib.contact_history_get.restype = I32
     lib.contact_history_set.argtypes = [P, ctypes.c_int64, P, P]
@@ -359,6 +361,19 @@ class Contact:
             self.close()
         except Exception:
             pass
+
+
+def polytope_centroid(planes) -> np.ndarray:
+    """Volume centroid of the polytope n . y <= d (rows (n, d), unit n, d > 0).
+    Poses refer to the centre of mass: a polytope whose centroid is off its
+    body origin is refused by contact_init; subtract n . centroid from every d."""
+    lib = load_library()
+    pl = np.ascontiguousarray(planes, dtype=np.float64).reshape(-1, 4)
+    c = np.zeros(3)
+    rc = lib.contact_polytope_centroid(pl.ctypes.data, len(pl), c.ctypes.data)
+    if rc != OK:
+        raise ContactError(rc, "contact_polytope_centroid: invalid planes")
+    return c
 
 
 class ContactFunction(torch.autograd.Function):

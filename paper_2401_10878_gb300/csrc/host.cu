@@ -126,6 +126,62 @@ std::vector<double> offset_vertices(const double* pl, int F, double delta) {
   return out;
 }
 
+// smallest face offset: the radius of a ball about the origin inside the polytope
+double rin_poly(const double* pl, int F) {
+  double r = DBL_MAX;
+  for (int f = 0; f < F; ++f) r = std::min(r, pl[4 * f + 3]);
+  return r;
+}
+constexpr double kCentroidTol = 1e-6;   // |centroid| allowed, relative to rin_poly
+
+// Volume centroid of the polytope {y : n_f . y <= d_f} (origin inside): each
+// face's vertices ordered by angle around their mean, fanned from it into
+// triangles, and each triangle closed to a tetrahedron with the origin.
+// Returns false when a face has fewer than three vertices.
+bool polytope_centroid(const double* pl, int F, double c[3]) {
+  const std::vector<double> v = offset_vertices(pl, F, 0.0);
+  const int nv = static_cast<int>(v.size() / 3);
+  double dmax = 1.0;
+  for (int f = 0; f < F; ++f) dmax = std::max(dmax, std::fabs(pl[4 * f + 3]));
+  const double tol = 1e-9 * dmax;
+  double vol = 0.0, acc[3] = {0.0, 0.0, 0.0};
+  for (int f = 0; f < F; ++f) {
+    const double* e = pl + 4 * f;
+    std::vector<int> on;
+    for (int i = 0; i < nv; ++i) {
+      const double* w = &v[3 * i];
+      if (std::fabs(e[0] * w[0] + e[1] * w[1] + e[2] * w[2] - e[3]) <= tol) on.push_back(i);
+    }
+    if (on.size() < 3) continue;   // a redundant plane touching at an edge or vertex
+    double m[3] = {0.0, 0.0, 0.0};
+    for (int i : on)
+      for (int k = 0; k < 3; ++k) m[k] += v[3 * i + k] / on.size();
+    // in-plane basis (a, b) of the face
+    double a[3] = {v[3 * on[0]] - m[0], v[3 * on[0] + 1] - m[1], v[3 * on[0] + 2] - m[2]};
+    const double na = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    if (!(na > 0.0)) continue;
+    for (double& x : a) x /= na;
+    const double b[3] = {e[1] * a[2] - e[2] * a[1], e[2] * a[0] - e[0] * a[2], e[0] * a[1] - e[1] * a[0]};
+    std::vector<std::pair<double, int>> ang;
+    for (int i : on) {
+      const double r[3] = {v[3 * i] - m[0], v[3 * i + 1] - m[1], v[3 * i + 2] - m[2]};
+      ang.push_back({std::atan2(r[0] * b[0] + r[1] * b[1] + r[2] * b[2], r[0] * a[0] + r[1] * a[1] + r[2] * a[2]), i});
+    }
+    std::sort(ang.begin(), ang.end());
+    for (size_t t = 0; t < ang.size(); ++t) {
+      const double* p1 = &v[3 * ang[t].second];
+      const double* p2 = &v[3 * ang[(t + 1) % ang.size()].second];
+      const double cr[3] = {p1[1] * p2[2] - p1[2] * p2[1], p1[2] * p2[0] - p1[0] * p2[2], p1[0] * p2[1] - p1[1] * p2[0]};
+      const double tv = std::fabs(m[0] * cr[0] + m[1] * cr[1] + m[2] * cr[2]) / 6.0;   // tetrahedron (0, m, p1, p2)
+      vol += tv;
+      for (int k = 0; k < 3; ++k) acc[k] += tv * (m[k] + p1[k] + p2[k]) / 4.0;
+    }
+  }
+  if (!(vol > 0.0)) return false;
+  for (int k = 0; k < 3; ++k) c[k] = acc[k] / vol;
+  return true;
+}
+
 // Bounded iff no direction u has n_i . u <= 0 for every face; candidate
 // extreme rays of the recession cone are +-(n_i x n_j).
 bool bounded(const double* pl, int F) {
@@ -206,6 +262,17 @@ void contact_config_default(contact_config* cfg, int32_t n_particles, const int3
   cfg->wall_poisson = nullptr;
   cfg->box_mode = 0;
   cfg->contact_resolution = 8;
+}
+
+contact_status contact_polytope_centroid(const double* planes, int32_t n_faces, double* centroid) {
+  if (planes == nullptr || centroid == nullptr || n_faces < 4) return CONTACT_EINVAL;
+  for (int f = 0; f < n_faces; ++f) {
+    const double* e = planes + 4 * f;
+    const double nn = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    if (!(std::fabs(nn - 1.0) <= 1e-9) || !(e[3] > 0.0) || !std::isfinite(e[3])) return CONTACT_EINVAL;
+  }
+  if (!bounded(planes, n_faces)) return CONTACT_EINVAL;
+  return polytope_centroid(planes, n_faces, centroid) ? CONTACT_OK : CONTACT_EINVAL;
 }
 
 double contact_damping_factor(double e, double u0) {
@@ -307,6 +374,10 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
         rin_min = std::min(rin_min, e[3]);   // unit normals, origin inside: the ball of radius min d fits
       }
       if (!bounded(pl, F)) return CONTACT_EINVAL;
+      // the body origin must be the centre of mass (the torque reference, Sec. 2.2)
+      double cm[3];
+      if (!polytope_centroid(pl, F, cm)) return CONTACT_EINVAL;
+      if (std::sqrt(cm[0] * cm[0] + cm[1] * cm[1] + cm[2] * cm[2]) > kCentroidTol * rin_poly(pl, F)) return CONTACT_EINVAL;
       std::vector<double> v = offset_vertices(pl, F, delta);
       if (v.size() < 12) return CONTACT_EINVAL;
       for (size_t t = 0; t < v.size(); t += 3)
