@@ -262,13 +262,20 @@ contact_status contact_history_reset(contact_ctx* ctx);
 
 /* Volume centroid (host) of the polytope {y : n_f . y <= d_f} given by
  * n_faces >= 4 rows (n, d) with unit n and d > 0 (origin inside), bounded.
- * Poses refer to the centre of mass (Sec. 2.2): contact_init refuses a
- * polytope whose centroid lies more than 1e-6 x (its smallest d) from its
- * body origin (CONTACT_EINVAL); shifting every d_f by -n_f . centroid moves
- * the origin there (the position then names the centroid).
  *   planes [n_faces,4] host; centroid [3] host out.  CONTACT_EINVAL on
  *   invalid planes. */
 contact_status contact_polytope_centroid(const double* planes, int32_t n_faces, double* centroid);
+
+/* Poses refer to the centre of mass (Sec. 2.2: the torque reference).
+ * contact_init moves the body origin of every polytope whose volume centroid
+ * c lies more than 1e-6 x (its smallest d) from it to c, by d_f -= n_f . c in
+ * its own copy of the planes; positions passed to contact_step then name the
+ * centroid (a caller holding the origin's position X_o passes X_o + R c).
+ * Polytopes given about their centroid are used unchanged, bit for bit.
+ * contact_polytope_shift writes c per particle, shift [N,3] f64 host (zero
+ * for spheres, cuboids and unmoved polytopes).  CONTACT_EINVAL for a null
+ * argument. */
+contact_status contact_polytope_shift(const contact_ctx* ctx, double* shift);
 
 /* Eq. (damping_factor): c = 1.5 (1-e)(11-e) / ((1+9e) u0) for u0 > 0, else 0,
  * from the coefficient of restitution e and the relative speed u0 at first

@@ -78,6 +78,8 @@ def _load():
         lib.oracle_polytope_centroid.argtypes = [P, ctypes.c_int32, P]
         lib.oracle_gradient.restype = ctypes.c_int64
         lib.oracle_gradient.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 13 + [ctypes.c_int32]
+        lib.oracle_polytope_shift.restype = ctypes.c_int32
+        lib.oracle_polytope_shift.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 9
         lib.oracle_aabb.restype = ctypes.c_int32
         lib.oracle_aabb.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 9
         lib.oracle_rotation.restype = None
@@ -322,6 +324,19 @@ def polytope_centroid(planes):
     if rc != 0:
         raise OracleError(rc)
     return c
+
+
+def polytope_shift(st):
+    """Per particle [N,3]: the offset by which a polytope's body origin is
+    moved to its volume centroid (zero where it already is, within 1e-6 x the
+    smallest face offset); positions then name the centroid."""
+    lib = _load()
+    out = np.zeros((st.n, 3))
+    rc = lib.oracle_polytope_shift(ctypes.byref(_cfg(st)), st.n, *[_ptr(a) for a in _shape_arrays(st)],
+                                   _ptr(_c(st.pos, np.float64)), _ptr(_c(st.quat, np.float64)), _ptr(out))
+    if rc != 0:
+        raise OracleError(rc)
+    return out
 
 
 def aabb(st, pos=None, quat=None):

@@ -748,6 +748,7 @@ struct Problem {
   std::vector<Shape> shapes;
   std::vector<double> young, poisson;
   std::vector<int> lo, hi;   // node ranges [n,3]
+  std::vector<double> shift; // [n,3]: body origin moved to the centroid by this (polytopes)
   std::vector<PairGeom> pairs;
 };
 
@@ -802,6 +803,7 @@ int build_problem(Problem& pb, const Config* cfg, int32_t n, const int32_t* shap
   if (c.box_mode == 1) band = std::max(band, std::sqrt(0.75) * c.dx);
   const double delta = c.inflate + band;
   pb.shapes.resize(n);
+  pb.shift.assign(3 * static_cast<size_t>(std::max(n, 0)), 0.0);
   pb.young.assign(young, young + n);
   pb.poisson.assign(poisson, poisson + n);
   double rmax = 0.0;
@@ -830,11 +832,19 @@ int build_problem(Problem& pb, const Config* cfg, int32_t n, const int32_t* shap
         if (!(e[3] > 0.0)) return OR_EINVAL;                // origin strictly inside
       }
       if (!polytope_bounded(s.planes)) return OR_EINVAL;
-      // poses refer to the centre of mass (Sec. 2.2): the body origin must be the centroid
+      // poses refer to the centre of mass (Sec. 2.2): a body origin further than
+      // 1e-6 x (smallest d) from the volume centroid is moved there, d_f -= n_f . c
       double cm[3], dmin = std::numeric_limits<double>::infinity();
       if (!polytope_centroid(s.planes, cm)) return OR_EINVAL;
       for (int f = 0; f < f1 - f0; ++f) dmin = std::min(dmin, s.planes[4 * f + 3]);
-      if (std::sqrt(cm[0] * cm[0] + cm[1] * cm[1] + cm[2] * cm[2]) > 1e-6 * dmin) return OR_EINVAL;
+      if (std::sqrt(cm[0] * cm[0] + cm[1] * cm[1] + cm[2] * cm[2]) > 1e-6 * dmin) {
+        for (int f = 0; f < f1 - f0; ++f) {
+          double* e = &s.planes[4 * f];
+          e[3] -= e[0] * cm[0] + e[1] * cm[1] + e[2] * cm[2];
+          if (!(e[3] > 0.0)) return OR_EINVAL;
+        }
+        for (int k = 0; k < 3; ++k) pb.shift[3 * p + k] = cm[k];
+      }
       s.verts = polytope_vertices(s.planes, delta);
       if (s.verts.size() < 12) return OR_EINVAL;
       for (size_t v = 0; v < s.verts.size(); v += 3) {
@@ -1054,6 +1064,21 @@ int32_t oracle_aabb(const oracle_config* cfg, int32_t n, const int32_t* shape_ty
       lo_hi[6 * p + k] = pb.lo[3 * p + k];
       lo_hi[6 * p + 3 + k] = pb.hi[3 * p + k];
     }
+  return OR_OK;
+}
+
+// Per particle [n,3]: the centroid offset by which a polytope's body origin
+// was moved (zero for spheres, cuboids and polytopes given about their
+// centroid).  Returns a status code.
+int32_t oracle_polytope_shift(const oracle_config* cfg, int32_t n, const int32_t* shape_type,
+                              const double* shape_param, const int32_t* face_offset, const double* planes,
+                              const double* young, const double* poisson, const double* pos,
+                              const double* quat, double* shift) {
+  Problem pb;
+  const int st = build_problem(pb, reinterpret_cast<const Config*>(cfg), n, shape_type, shape_param,
+                               face_offset, planes, young, poisson, pos, quat);
+  if (st != OR_OK) return st;
+  std::copy(pb.shift.begin(), pb.shift.end(), shift);
   return OR_OK;
 }
 

@@ -31,7 +31,8 @@ EXPORTS = ["contact_config_default", "contact_init", "contact_step", "contact_ba
            "contact_clear_error", "contact_last_error", "contact_set_stream", "contact_stats",
            "contact_particle_boxes", "contact_narrow_time", "contact_damping_factor", "contact_kernels_per_step",
            "contact_kernels_per_backward", "contact_destroy", "contact_step_noalloc", "contact_step_host",
-           "contact_history_get", "contact_history_set", "contact_history_reset", "contact_polytope_centroid"]
+           "contact_history_get", "contact_history_set", "contact_history_reset", "contact_polytope_centroid",
+           "contact_polytope_shift"]
 
 
 class Config(ctypes.Structure):
@@ -108,6 +109,8 @@ def load_library(build_if_missing: bool = True):
     lib.contact_step_host.restype = I32
     lib.contact_polytope_centroid.argtypes = [P, I32, P]
     lib.contact_polytope_centroid.restype = I32
+    lib.contact_polytope_shift.argtypes = [P, P]
+    lib.contact_polytope_shift.restype = I32
     lib.contact_history_get.argtypes = [P, ctypes.c_int64, P, P, P]
     lib.contact_history_get.restype = I32
     lib.contact_history_set.argtypes = [P, ctypes.c_int64, P, P]
@@ -314,6 +317,16 @@ class Contact:
         if rc != OK:
             self._raise(rc, "contact_particle_boxes")
         torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return out
+
+    def polytope_shift(self):
+        """[N,3] float64 host: the offset by which each polytope's body origin
+        was moved to its volume centroid (zero where it already was);
+        positions name the centroid."""
+        out = np.zeros((self.n, 3))
+        rc = self.lib.contact_polytope_shift(self.ctx, out.ctypes.data)
+        if rc != OK:
+            self._raise(rc, "contact_polytope_shift")
         return out
 
     def history(self):

@@ -30,6 +30,7 @@ struct contact_ctx {
   // graph cache
   cudaGraphExec_t gexec = nullptr;
   const void* gkey[9] = {};
+  std::vector<double> shift;   // [N,3]: polytope body origins moved to the centroid by this
   int last_replay = 0;   // 0 instantiated (or no graph), 1 replayed, 2 replayed after an in-place update
   cudaEvent_t ev_narrow[2] = {nullptr, nullptr};
   // contact_step_host: device staging buffers and their own graph cache
@@ -280,6 +281,12 @@ double contact_damping_factor(double e, double u0) {
   return 1.5 * (1.0 - e) * (11.0 - e) / ((1.0 + 9.0 * e) * u0);
 }
 
+contact_status contact_polytope_shift(const contact_ctx* ctx, double* shift) {
+  if (ctx == nullptr || shift == nullptr) return CONTACT_EINVAL;
+  std::copy(ctx->shift.begin(), ctx->shift.end(), shift);
+  return CONTACT_OK;
+}
+
 contact_status contact_init(const contact_config* cfg, const int32_t* shape_type, const double* shape_param,
                             const int32_t* face_offset, const double* planes, const double* young,
                             const double* poisson, void* stream, contact_ctx** out) {
@@ -333,6 +340,9 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   std::vector<int> nomops(n);
   const int nfaces = face_offset[n];
   if (face_offset[0] != 0 || nfaces < 0 || (nfaces > 0 && planes == nullptr)) return CONTACT_EINVAL;
+  // the library's own copy of the planes: polytopes off their centroid are shifted in it
+  std::vector<double> pl_in(planes ? planes : nullptr, planes ? planes + 4 * static_cast<size_t>(nfaces) : nullptr);
+  std::vector<double> shift(3 * static_cast<size_t>(n), 0.0);
   double rmax = 0.0;
   double rin_min = DBL_MAX;   // smallest inscribed-ball radius (bounds how many particles one bin holds)
   for (int p = 0; p < n; ++p) {
@@ -366,18 +376,26 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
     } else if (type[p] == CONTACT_SHAPE_POLYTOPE) {
       const int F = f1 - f0;
       if (F < 4 || F > kMaxFaces) return CONTACT_EINVAL;
-      const double* pl = planes + 4 * f0;
+      double* pl = pl_in.data() + 4 * f0;
       for (int f = 0; f < F; ++f) {
         const double* e = pl + 4 * f;
         const double nn = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
         if (!(std::fabs(nn - 1.0) <= 1e-9) || !(e[3] > 0.0) || !std::isfinite(e[3])) return CONTACT_EINVAL;
-        rin_min = std::min(rin_min, e[3]);   // unit normals, origin inside: the ball of radius min d fits
       }
       if (!bounded(pl, F)) return CONTACT_EINVAL;
-      // the body origin must be the centre of mass (the torque reference, Sec. 2.2)
+      // poses refer to the centre of mass (the torque reference, Sec. 2.2): an
+      // origin off the volume centroid is moved there, d_f -= n_f . c
       double cm[3];
       if (!polytope_centroid(pl, F, cm)) return CONTACT_EINVAL;
-      if (std::sqrt(cm[0] * cm[0] + cm[1] * cm[1] + cm[2] * cm[2]) > kCentroidTol * rin_poly(pl, F)) return CONTACT_EINVAL;
+      if (std::sqrt(cm[0] * cm[0] + cm[1] * cm[1] + cm[2] * cm[2]) > kCentroidTol * rin_poly(pl, F)) {
+        for (int f = 0; f < F; ++f) {
+          double* e = pl + 4 * f;
+          e[3] -= e[0] * cm[0] + e[1] * cm[1] + e[2] * cm[2];
+          if (!(e[3] > 0.0)) return CONTACT_EINVAL;
+        }
+        for (int k = 0; k < 3; ++k) shift[3 * p + k] = cm[k];
+      }
+      rin_min = std::min(rin_min, rin_poly(pl, F));   // unit normals, origin inside: the ball of radius min d fits
       std::vector<double> v = offset_vertices(pl, F, delta);
       if (v.size() < 12) return CONTACT_EINVAL;
       for (size_t t = 0; t < v.size(); t += 3)
@@ -411,6 +429,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
 
   contact_ctx* c = new contact_ctx();
   c->cfg = C;
+  c->shift = std::move(shift);
   c->stream = static_cast<cudaStream_t>(stream);
   cudaGetDevice(&c->device);
   Params& P = c->P;
@@ -466,7 +485,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   P.wdx_l = static_cast<float>(C.smooth_width);
 
   cudaError_t e = cudaSuccess;
-  std::vector<double> pl_vec(planes ? planes : nullptr, planes ? planes + 4 * static_cast<size_t>(nfaces) : nullptr);
+  std::vector<double> pl_vec(std::move(pl_in));
   std::vector<int> foff(face_offset, face_offset + n + 1);
   std::vector<double> yv(young, young + n), pv(poisson, poisson + n), cv(n);
   for (int p = 0; p < n; ++p) cv[p] = (1.0 - poisson[p] * poisson[p]) / young[p];

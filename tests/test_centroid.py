@@ -1,9 +1,8 @@
 """The centre-of-mass convention (Sec. 2.2: poses refer to the centre of
 mass): polytope volume centroids, by the oracle (face pyramids) against
-closed forms, by the library (tetrahedra) against the oracle, and the
-refusal of a polytope whose body origin is not its centroid (CPU only; the
-library's check runs before any device work)."""
-import ctypes
+closed forms and by the library (tetrahedra) against the oracle; a polytope
+whose body origin is off its centroid is moved there, by both sides (the
+last test needs a GB300)."""
 
 import numpy as np
 import pytest
@@ -65,23 +64,55 @@ def test_library_centroid_matches_oracle():
     assert np.abs(c).max() < 1e-14
 
 
-def test_off_centre_polytope_refused():
-    from paper_2401_10878_gb300 import contact as C
-    lib = C.load_library()
-    pl = box_planes(np.array([-1.0, -2.0, -0.5]), np.array([3.0, 2.0, 1.5]))   # centroid (1, 0, 0.5)
-    st = state([2], [[0, 0, 0]], [[30.0, 30.0, 30.0]], planes=[pl])
-    with pytest.raises(oracle.OracleError):
-        oracle.contact_step(st)
-    cfg = C.Config()
-    n_cells = (ctypes.c_int32 * 3)(*st.n_cells)
-    lib.contact_config_default(ctypes.byref(cfg), st.n, n_cells, st.dx)
-    arrs = [np.ascontiguousarray(a) for a in (st.shape_type, st.shape_param, st.face_offset, st.planes, st.young,
-                                              st.poisson)]
-    ctx = ctypes.c_void_p()
-    rc = lib.contact_init(ctypes.byref(cfg), *[a.ctypes.data for a in arrs], None, ctypes.byref(ctx))
-    assert rc == C.EINVAL and not ctx.value
-    # re-centred planes are accepted by the oracle
-    c = oracle.polytope_centroid(pl)
+def test_off_centre_polytope_moved_to_its_centroid():
+    """An off-centre box is moved to its centroid (1, 0, 0.5): the step equals
+    that of the box given about its centroid at the same position, and the
+    shift is reported; centred polytopes are not moved."""
+    pl = box_planes(np.array([-1.0, -2.0, -0.5]), np.array([3.0, 2.0, 1.5]))
+    pos = [[20.3, 20.1, 20.2], [25.0, 21.4, 20.9]]
+    cube = cube_planes(3.0)
+    st = state([2, 2], np.zeros((2, 3)), pos, planes=[pl, cube])
+    assert np.array_equal(oracle.polytope_shift(st), [[1.0, 0.0, 0.5], [0.0, 0.0, 0.0]])
     pl2 = pl.copy()
-    pl2[:, 3] -= pl[:, :3] @ c
-    oracle.contact_step(state([2], [[0, 0, 0]], [[30.0, 30.0, 30.0]], planes=[pl2]))
+    pl2[:, 3] -= pl[:, :3] @ np.array([1.0, 0.0, 0.5])   # axis normals: exact
+    r1 = oracle.contact_step(st)
+    r2 = oracle.contact_step(state([2, 2], np.zeros((2, 3)), pos, planes=[pl2, cube]))
+    assert r1.n_pairs == 1 and r1.pair_out[0, 0] > 0
+    assert np.array_equal(r1.pair_out, r2.pair_out) and np.array_equal(r1.force, r2.force)
+    rng = np.random.default_rng(5)
+    centred = state([2, 2], np.zeros((2, 3)), pos, planes=[W.random_polytope(rng, f, 5.0)[0] for f in (12, 20)])
+    assert not oracle.polytope_shift(centred).any()
+
+
+def off_centre_polytopes():
+    rng = np.random.default_rng(11)
+    polys = []
+    for f in (14, 20, 16, 24):
+        pl = W.random_polytope(rng, f, 8.0)[0]
+        u = rng.normal(size=3)
+        pl[:, 3] += pl[:, :3] @ (u / np.linalg.norm(u) * 0.4 * pl[:, 3].min())   # the origin moved off the centroid
+        polys.append(pl)
+    pos = [[20, 20, 20], [29, 21, 19], [20, 29, 21], [29, 29, 20]]
+    return state([2, 2, 2, 2], np.zeros((4, 3)), pos, W.random_quaternions(rng, 4), planes=polys)
+
+
+def test_off_centre_state_needs_a_shift():
+    st = off_centre_polytopes()
+    sh = oracle.polytope_shift(st)
+    assert (np.linalg.norm(sh, axis=1) > 0.05).all()
+    assert oracle.contact_step(st).n_pairs >= 3
+
+
+@pytest.mark.gpu
+def test_library_moves_polytopes_like_the_oracle():
+    pytest.importorskip("torch")
+    from paper_2401_10878_gb300.contact import Contact
+    from tests.parity import compare, gpu_step
+    st = off_centre_polytopes()
+    m = Contact.from_state(st)
+    assert np.allclose(m.polytope_shift(), oracle.polytope_shift(st), rtol=0, atol=1e-11)
+    g = gpu_step(m, st)
+    r = oracle.contact_step(st)
+    print("off-centre polytopes", compare(st, g, r, fp64=False, smooth=False))
+    assert np.array_equal(m.particle_boxes().cpu().numpy(), oracle.aabb(st))
+    m.close()
