@@ -132,8 +132,11 @@ typedef struct {
                                it and each face moved inward to the nearest entry
                                of contact_resolution^2 axis-parallel lines into the
                                overlap, then contact_resolution^3 cell-centre
-                               samples; shared damping c only (no history, no
-                               friction), no contact_backward                     */
+                               samples; no contact_backward.  With the history, an
+                               ongoing contact's corrected box of the last step
+                               (kept relative to X_i), widened by sqrt(0.75) dx,
+                               cuts the widened rough box down per axis before
+                               the correction (the warm start of Sec. 4.3.3)      */
   int32_t contact_resolution; /* N_c of box_mode 1, 1..64 (the paper uses 8)      */
 } contact_config;
 
@@ -245,19 +248,25 @@ contact_status contact_narrow_time(contact_ctx* ctx, float* ms);
 contact_status contact_particle_boxes(contact_ctx* ctx, int32_t* lo_hi);
 
 /* Contact history (cfg.history = 1; Sec. 4.3.3): the contacts of the last
- * completed step (pairs (i, j), i < j, with V > 0) and the damping factor c
- * each keeps; the next step reads them.  All three return CONTACT_ESTATE
- * with the history off.
+ * completed step (pairs (i, j), i < j, with V > 0), the damping factor c
+ * each keeps and, with box_mode 1, its corrected box (lo[3], hi[3]) minus
+ * X_i, the warm start of the next correction; the next step reads them.
+ * All three return CONTACT_ESTATE with the history off.
  * contact_history_get synchronises, then writes the first min(*n, max_rows)
- * contacts, sorted by (i, j), to ij [max_rows,2] i32 host and c [max_rows]
- * f64 host; *n receives the number of contacts (which may exceed max_rows).
+ * contacts, sorted by (i, j), to ij [max_rows,2] i32 host, c [max_rows] f64
+ * host and box [max_rows,6] f64 host (nullable; zeros with box_mode 0); *n
+ * receives the number of contacts (which may exceed max_rows).
  * contact_history_set replaces them with the n_rows given (host arrays, as
- * a checkpoint to resume from): CONTACT_EINVAL for a row with i >= j, i
- * outside [0, N), j outside [0, N + n_walls) (j >= N: a wall), a repeated
- * (i, j), or more than max_neighbors rows of one i.  contact_history_reset forgets every contact (asynchronous, on
- * the context stream). */
-contact_status contact_history_get(contact_ctx* ctx, int64_t max_rows, int32_t* ij, double* c, int64_t* n);
-contact_status contact_history_set(contact_ctx* ctx, int64_t n_rows, const int32_t* ij, const double* c);
+ * a checkpoint to resume from; box is read with box_mode 1 only, where it is
+ * required): CONTACT_EINVAL for a row with i >= j, i outside [0, N), j
+ * outside [0, N + n_walls) (j >= N: a wall), a repeated (i, j), more than
+ * max_neighbors rows of one i, or a box with lo > hi or a non-finite bound.
+ * contact_history_reset forgets every contact (asynchronous, on the context
+ * stream). */
+contact_status contact_history_get(contact_ctx* ctx, int64_t max_rows, int32_t* ij, double* c, double* box,
+                                   int64_t* n);
+contact_status contact_history_set(contact_ctx* ctx, int64_t n_rows, const int32_t* ij, const double* c,
+                                   const double* box);
 contact_status contact_history_reset(contact_ctx* ctx);
 
 /* Volume centroid (host) of the polytope {y : n_f . y <= d_f} given by

@@ -64,16 +64,16 @@ def _load():
         P = ctypes.c_void_p
         lib.oracle_contact_step.restype = ctypes.c_int64
         lib.oracle_contact_step.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 9 + \
-            [ctypes.c_int64] + [P] * 7 + [ctypes.c_int32]
+            [ctypes.c_int64] + [P] * 7 + [ctypes.c_int64, P, P, ctypes.c_int32]
         lib.oracle_contact_step_ext.restype = ctypes.c_int64
         lib.oracle_contact_step_ext.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Law), ctypes.c_int32] + \
-            [P] * 9 + [ctypes.c_int64] + [P] * 5 + [ctypes.c_int64, P, P, ctypes.c_int64, P, P, P, ctypes.c_int32]
+            [P] * 9 + [ctypes.c_int64] + [P] * 5 + [ctypes.c_int64, P, P, P, ctypes.c_int64, P, P, P, P, ctypes.c_int32]
         lib.oracle_gradient_ext.restype = ctypes.c_int64
         lib.oracle_gradient_ext.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Law), ctypes.c_int32] + \
             [P] * 9 + [ctypes.c_int64] + [P] * 6 + [ctypes.c_int32]
         lib.oracle_box_pipeline.restype = ctypes.c_int64
         lib.oracle_box_pipeline.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 8 + \
-            [ctypes.c_int64] + [P] * 3
+            [ctypes.c_int64, P, P, ctypes.c_int64] + [P] * 3
         lib.oracle_polytope_centroid.restype = ctypes.c_int32
         lib.oracle_polytope_centroid.argtypes = [P, ctypes.c_int32, P]
         lib.oracle_gradient.restype = ctypes.c_int64
@@ -157,9 +157,14 @@ class Result:
         return int(self.pair_aux[:, 3].sum())
 
 
-def contact_step(st, pos=None, quat=None, vel=None, n_threads: int = 0, band_eps: float = BAND_EPS) -> Result:
-    """Evaluate every candidate pair of the state (see contact_oracle.cpp)."""
+def contact_step(st, pos=None, quat=None, vel=None, n_threads: int = 0, band_eps: float = BAND_EPS,
+                 hist=None) -> Result:
+    """Evaluate every candidate pair of the state (see contact_oracle.cpp);
+    with the box pipeline, hist = (hist_ij, hist_c, hist_box) of the previous
+    step gives the ongoing contacts' warm starts (the shared damping c stays)."""
     lib = _load()
+    hij = np.zeros((0, 2), np.int32) if hist is None else _c(hist[0], np.int32)
+    hb = None if hist is None or len(hist) < 3 or hist[2] is None else _c(hist[2], np.float64)
     pos = _c(st.pos if pos is None else pos, np.float64)
     quat = _c(st.quat if quat is None else quat, np.float64)
     vel = None if vel is None else _c(vel, np.float64)
@@ -179,7 +184,7 @@ def contact_step(st, pos=None, quat=None, vel=None, n_threads: int = 0, band_eps
         t0 = time.perf_counter()
         P = lib.oracle_contact_step(ctypes.byref(cfg), n, *[_ptr(a) for a in arrs], _ptr(pos), _ptr(quat),
                                     _ptr(vel), cap, _ptr(ij), _ptr(sh), _ptr(bx), _ptr(out), _ptr(aux),
-                                    _ptr(f), _ptr(t), threads)
+                                    _ptr(f), _ptr(t), len(hij), _ptr(hij), _ptr(hb), threads)
         dt = time.perf_counter() - t0
         if P < 0:
             raise OracleError(-P)
@@ -211,6 +216,7 @@ class ExtResult:
     torque: np.ndarray
     hist_ij: np.ndarray     # this step's contacts (V > 0), sorted by (i, j)
     hist_c: np.ndarray
+    hist_box: np.ndarray    # [H,6] their corrected boxes relative to X_i (box pipeline; zeros otherwise)
 
     @property
     def n_pairs(self):
@@ -219,7 +225,9 @@ class ExtResult:
 
 def contact_step_ext(st, law: ContactLaw, pos=None, quat=None, vel=None, hist=None, n_threads: int = 0) -> ExtResult:
     """The contact step with friction and the contact history; hist is the
-    previous step's (hist_ij, hist_c) or None (no ongoing contact)."""
+    previous step's (hist_ij, hist_c) or (hist_ij, hist_c, hist_box), or None
+    (no ongoing contact).  hist_box [H,6] (the box pipeline's warm start) is
+    each contact's corrected box relative to the lower-ID particle's position."""
     lib = _load()
     pos = _c(st.pos if pos is None else pos, np.float64)
     quat = _c(st.quat if quat is None else quat, np.float64)
@@ -229,6 +237,7 @@ def contact_step_ext(st, law: ContactLaw, pos=None, quat=None, vel=None, hist=No
     lw = _Law(law.restitution, law.mu_s, law.mu_k, law.u_k, int(law.history), int(law.friction))
     hij = np.zeros((0, 2), np.int32) if hist is None else _c(hist[0], np.int32)
     hc = np.zeros(0) if hist is None else _c(hist[1], np.float64)
+    hb = None if hist is None or len(hist) < 3 or hist[2] is None else _c(hist[2], np.float64)
     n = st.n
     cap = max(16, 16 * n)
     threads = n_threads if n_threads > 0 else lib.oracle_max_threads()
@@ -240,16 +249,17 @@ def contact_step_ext(st, law: ContactLaw, pos=None, quat=None, vel=None, hist=No
         t = np.zeros((n, 3))
         hij_o = np.zeros((cap, 2), np.int32)
         hc_o = np.zeros(cap)
+        hb_o = np.zeros((cap, 6))
         nh = ctypes.c_int64(0)
         P = lib.oracle_contact_step_ext(ctypes.byref(cfg), ctypes.byref(lw), n, *[_ptr(a) for a in arrs],
                                         _ptr(pos), _ptr(quat), _ptr(vel), cap, _ptr(ij), _ptr(out), _ptr(pc),
-                                        _ptr(f), _ptr(t), len(hc), _ptr(hij), _ptr(hc), cap, _ptr(hij_o),
-                                        _ptr(hc_o), ctypes.byref(nh), threads)
+                                        _ptr(f), _ptr(t), len(hc), _ptr(hij), _ptr(hc), _ptr(hb), cap, _ptr(hij_o),
+                                        _ptr(hc_o), _ptr(hb_o), ctypes.byref(nh), threads)
         if P < 0:
             raise OracleError(-P)
         if P <= cap:
             H = nh.value
-            return ExtResult(ij[:P], out[:P], pc[:P], f, t, hij_o[:H], hc_o[:H])
+            return ExtResult(ij[:P], out[:P], pc[:P], f, t, hij_o[:H], hc_o[:H], hb_o[:H])
         cap = int(P)
 
 
@@ -295,19 +305,24 @@ def gradient_ext(st, law: ContactLaw, grad_force, grad_torque, pos=None, quat=No
     return gp, gq
 
 
-def box_pipeline(st, pos=None, quat=None):
+def box_pipeline(st, pos=None, quat=None, hist=None):
     """The box pipeline's rough boxes [P,6] (node indices), corrected boxes
-    [P,6] (physical) and flags [P,2] per candidate pair (st.box_mode = 1)."""
+    [P,6] (physical) and flags [P,2] per candidate pair (st.box_mode = 1);
+    hist = (hist_ij, hist_c, hist_box) of the previous step gives the warm
+    starts of the ongoing contacts."""
     lib = _load()
     pos = _c(st.pos if pos is None else pos, np.float64)
     quat = _c(st.quat if quat is None else quat, np.float64)
+    hij = np.zeros((0, 2), np.int32) if hist is None else _c(hist[0], np.int32)
+    hb = None if hist is None or len(hist) < 3 or hist[2] is None else _c(hist[2], np.float64)
     cap = max(16, 16 * st.n)
     while True:
         rough = np.zeros((cap, 6), np.int32)
         box = np.zeros((cap, 6))
         flags = np.zeros((cap, 2))
         P = lib.oracle_box_pipeline(ctypes.byref(_cfg(st)), st.n, *[_ptr(a) for a in _shape_arrays(st)], _ptr(pos),
-                                    _ptr(quat), cap, _ptr(rough), _ptr(box), _ptr(flags))
+                                    _ptr(quat), len(hij), _ptr(hij), _ptr(hb), cap, _ptr(rough), _ptr(box),
+                                    _ptr(flags))
         if P < 0:
             raise OracleError(-P)
         if P <= cap:

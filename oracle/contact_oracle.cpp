@@ -384,6 +384,9 @@ struct ContactLaw {
   double restitution = 1.0;
   bool friction = false;
   double mu_s = 0.0, mu_k = 0.0, u_k = 1.0;
+  // box pipeline with the contact history (Sec. 4.3.3): the ongoing
+  // contact's corrected box of the previous step, relative to X_i (or null)
+  const double* warm_box = nullptr;
 };
 
 // Parameter interval [t0, t1] of the line p + t e inside a shape reduced by
@@ -461,7 +464,7 @@ void line_interval(const Shape& sh, const double X[3], const double R[9], const 
 template <class S>
 bool box_pipeline(const Config& cfg, const Shape& A, const Shape& B, const PairGeom& pg, const double XA[3],
                   const double RA[9], const double XB[3], const double RB[9], PairResult<S>& res, double lo[3],
-                  double step[3]) {
+                  double step[3], const double* warm = nullptr) {
   const double dx = cfg.dx;
   const int Nc = cfg.contact_resolution;
   const double srough = std::sqrt(0.75) * dx;
@@ -497,6 +500,18 @@ bool box_pipeline(const Config& cfg, const Shape& A, const Shape& B, const PairG
     b0lo[a] = mn[a] * dx - srough;
     b0hi[a] = mx[a] * dx + srough;
   }
+  // warm start (Sec. 4.3.3): an ongoing contact's corrected box of the last
+  // step, moved with particle i and widened by the same sqrt(0.75) dx, cuts
+  // B0 down (per axis, unless the cut leaves nothing)
+  if (warm != nullptr)
+    for (int a = 0; a < 3; ++a) {
+      const double wl = (XA[a] + warm[a]) - srough, wh = (XA[a] + warm[3 + a]) + srough;
+      const double l = std::max(b0lo[a], wl), h = std::min(b0hi[a], wh);
+      if (l < h) {
+        b0lo[a] = l;
+        b0hi[a] = h;
+      }
+    }
   // correction: face (axis k, lower / upper), lines along the inward normal
   double shift[3][2];
   double n_face_tie = 0;
@@ -575,7 +590,7 @@ PairResult<S> eval_pair(const Config& cfg, const Shape& A, const Shape& B, const
     double XAd[3], XBd[3], RAd[9], RBd[9];
     for (int k = 0; k < 3; ++k) { XAd[k] = val(XA[k]); XBd[k] = val(XB[k]); }
     for (int k = 0; k < 9; ++k) { RAd[k] = val(RA[k]); RBd[k] = val(RB[k]); }
-    if (box_pipeline(cfg, A, B, pg, XAd, RAd, XBd, RBd, res, s_lo, s_step)) {
+    if (box_pipeline(cfg, A, B, pg, XAd, RAd, XBd, RBd, res, s_lo, s_step, law.warm_box)) {
       for (int k = 0; k < 3; ++k) {
         cnt[k] = cfg.contact_resolution;
         s_lo[k] += 0.5 * s_step[k];   // cell centres
@@ -1082,6 +1097,17 @@ int32_t oracle_polytope_shift(const oracle_config* cfg, int32_t n, const int32_t
   return OR_OK;
 }
 
+// Row of contact (i, j) in a history table sorted by (i, j), or -1.
+static int64_t hist_find(int64_t n_hist, const int32_t* hist_ij, int i, int j) {
+  int64_t a = 0, b = n_hist;
+  while (a < b) {
+    const int64_t m = (a + b) / 2;
+    const bool less = hist_ij[2 * m] < i || (hist_ij[2 * m] == i && hist_ij[2 * m + 1] < j);
+    if (less) a = m + 1; else b = m;
+  }
+  return (a < n_hist && hist_ij[2 * a] == i && hist_ij[2 * a + 1] == j) ? a : -1;
+}
+
 // Full contact evaluation.  Returns the number of candidate pairs P (>= 0;
 // only the first max_pairs rows are written when P > max_pairs) or a negative
 // status code.  Per pair: pair_ij [P,2], pair_shift [P,3], pair_box [P,6]
@@ -1095,7 +1121,8 @@ int64_t oracle_contact_step(const oracle_config* cfg, int32_t n, const int32_t* 
                             const double* young, const double* poisson, const double* pos,
                             const double* quat, const double* vel, int64_t max_pairs, int32_t* pair_ij,
                             int32_t* pair_shift, int32_t* pair_box, double* pair_out, double* pair_aux,
-                            double* force, double* torque, int32_t n_threads) {
+                            double* force, double* torque, int64_t n_hist, const int32_t* hist_ij,
+                            const double* hist_box, int32_t n_threads) {
   Problem pb;
   const int st = build_problem(pb, reinterpret_cast<const Config*>(cfg), n, shape_type, shape_param,
                                face_offset, planes, young, poisson, pos, quat);
@@ -1111,6 +1138,10 @@ int64_t oracle_contact_step(const oracle_config* cfg, int32_t n, const int32_t* 
     const double es = effective_modulus(pb.young[g.i], pb.poisson[g.i], pb.young[g.j], pb.poisson[g.j]);
     ContactLaw law;
     law.c = pb.cfg.damping_c;
+    if (pb.cfg.box_mode == 1 && hist_box != nullptr) {   // warm starts of the ongoing contacts
+      const int64_t row = hist_find(n_hist, hist_ij, g.i, g.j);
+      if (row >= 0) law.warm_box = hist_box + 6 * row;
+    }
     res[p] = eval_pair<double>(pb.cfg, pb.shapes[g.i], pb.shapes[g.j], g, pos + 3 * g.i, quat + 4 * g.i, XB,
                                partner_quat(pb, g, quat), vel ? vel + 6 * g.i : nullptr, partner_vel(pb, g, vel), es, law);
   }
@@ -1158,17 +1189,6 @@ typedef struct {
   int32_t friction;     // 1: tangential force of Eq. (contact_force_tangential)
 } oracle_contact_law;
 
-// Row of contact (i, j) in a history table sorted by (i, j), or -1.
-static int64_t hist_find(int64_t n_hist, const int32_t* hist_ij, int i, int j) {
-  int64_t a = 0, b = n_hist;
-  while (a < b) {
-    const int64_t m = (a + b) / 2;
-    const bool less = hist_ij[2 * m] < i || (hist_ij[2 * m] == i && hist_ij[2 * m + 1] < j);
-    if (less) a = m + 1; else b = m;
-  }
-  return (a < n_hist && hist_ij[2 * a] == i && hist_ij[2 * a + 1] == j) ? a : -1;
-}
-
 // The contact step with the contact law's extensions: friction, and the
 // contact history of Sec. 4.3.3 (a contact keeps the damping factor computed
 // from its approach speed at the first step with V > 0; it ends with the
@@ -1176,15 +1196,19 @@ static int64_t hist_find(int64_t n_hist, const int32_t* hist_ij, int i, int j) {
 // contacts of the previous step sorted by (i, j); the contacts of this step
 // (pairs with V > 0, in pair order) go to hist_ij_out / hist_c_out (up to
 // max_hist rows; *n_hist_out receives their count).  pair_c [P] (nullable)
-// receives the damping factor each pair used.  Other arguments and the
-// return value as oracle_contact_step.
+// receives the damping factor each pair used.  With the box pipeline,
+// hist_box [n_hist,6] (nullable) holds each contact's corrected box of the
+// previous step relative to X_i (lo, hi), the warm start of its box
+// correction, and hist_box_out [max_hist,6] (nullable) receives this step's.
+// Other arguments and the return value as oracle_contact_step.
 int64_t oracle_contact_step_ext(const oracle_config* cfg, const oracle_contact_law* law_in, int32_t n,
                                 const int32_t* shape_type, const double* shape_param, const int32_t* face_offset,
                                 const double* planes, const double* young, const double* poisson,
                                 const double* pos, const double* quat, const double* vel, int64_t max_pairs,
                                 int32_t* pair_ij, double* pair_out, double* pair_c, double* force, double* torque,
-                                int64_t n_hist, const int32_t* hist_ij, const double* hist_c, int64_t max_hist,
-                                int32_t* hist_ij_out, double* hist_c_out, int64_t* n_hist_out, int32_t n_threads) {
+                                int64_t n_hist, const int32_t* hist_ij, const double* hist_c, const double* hist_box,
+                                int64_t max_hist, int32_t* hist_ij_out, double* hist_c_out, double* hist_box_out,
+                                int64_t* n_hist_out, int32_t n_threads) {
   Problem pb;
   const int st = build_problem(pb, reinterpret_cast<const Config*>(cfg), n, shape_type, shape_param,
                                face_offset, planes, young, poisson, pos, quat);
@@ -1211,6 +1235,7 @@ int64_t oracle_contact_step_ext(const oracle_config* cfg, const oracle_contact_l
       const int64_t row = hist_find(n_hist, hist_ij, g.i, g.j);
       if (row >= 0) {
         law.c = hist_c[row];
+        if (pb.cfg.box_mode == 1 && hist_box != nullptr) law.warm_box = hist_box + 6 * row;
       } else {
         law.new_contact = true;
       }
@@ -1238,6 +1263,9 @@ int64_t oracle_contact_step_ext(const oracle_config* cfg, const oracle_contact_l
         hist_ij_out[2 * nh] = g.i;
         hist_ij_out[2 * nh + 1] = g.j;
         hist_c_out[nh] = r.c_used;
+        if (hist_box_out != nullptr)
+          for (int k = 0; k < 6; ++k)
+            hist_box_out[6 * nh + k] = pb.cfg.box_mode == 1 ? r.box[k] - pos[3 * g.i + k % 3] : 0.0;
       }
       ++nh;
     }
@@ -1354,11 +1382,15 @@ int64_t oracle_gradient_ext(const oracle_config* cfg, const oracle_contact_law* 
 // rough [P,6] node-index bounds (0 when no node is rough-in), box [P,6] the
 // corrected box (physical), flags [P,2] = rough-detection nodes within
 // band_eps of the threshold, faces whose two smallest line distances lie
-// within 1e-4 dx.  Returns P or a negative status.
+// within 1e-4 dx.  hist_ij [n_hist,2] (sorted by (i, j)) and hist_box
+// [n_hist,6] (nullable) are the ongoing contacts and their warm-start boxes
+// relative to X_i, as for oracle_contact_step_ext.  Returns P or a negative
+// status.
 int64_t oracle_box_pipeline(const oracle_config* cfg, int32_t n, const int32_t* shape_type,
                             const double* shape_param, const int32_t* face_offset, const double* planes,
                             const double* young, const double* poisson, const double* pos, const double* quat,
-                            int64_t max_pairs, int32_t* rough, double* box, double* flags) {
+                            int64_t n_hist, const int32_t* hist_ij, const double* hist_box, int64_t max_pairs,
+                            int32_t* rough, double* box, double* flags) {
   Problem pb;
   const int st = build_problem(pb, reinterpret_cast<const Config*>(cfg), n, shape_type, shape_param,
                                face_offset, planes, young, poisson, pos, quat);
@@ -1375,7 +1407,9 @@ int64_t oracle_box_pipeline(const oracle_config* cfg, int32_t n, const int32_t* 
     for (int k = 0; k < 6; ++k) { r.rough[k] = 0; r.box[k] = 0.0; }
     double lo[3], step[3];
     r.n_face_tie = 0.0;
-    box_pipeline(pb.cfg, pb.shapes[g.i], pb.shapes[g.j], g, pos + 3 * g.i, RA, XB, RB, r, lo, step);
+    const int64_t row = hist_box != nullptr ? hist_find(n_hist, hist_ij, g.i, g.j) : -1;
+    box_pipeline(pb.cfg, pb.shapes[g.i], pb.shapes[g.j], g, pos + 3 * g.i, RA, XB, RB, r, lo, step,
+                 row >= 0 ? hist_box + 6 * row : nullptr);
     for (int k = 0; k < 6; ++k) {
       rough[6 * p + k] = r.rough[k];
       box[6 * p + k] = r.box[k];

@@ -111,9 +111,9 @@ def load_library(build_if_missing: bool = True):
     lib.contact_polytope_centroid.restype = I32
     lib.contact_polytope_shift.argtypes = [P, P]
     lib.contact_polytope_shift.restype = I32
-    lib.contact_history_get.argtypes = [P, ctypes.c_int64, P, P, P]
+    lib.contact_history_get.argtypes = [P, ctypes.c_int64, P, P, P, P]
     lib.contact_history_get.restype = I32
-    lib.contact_history_set.argtypes = [P, ctypes.c_int64, P, P]
+    lib.contact_history_set.argtypes = [P, ctypes.c_int64, P, P, P]
     lib.contact_history_set.restype = I32
     lib.contact_history_reset.argtypes = [P]
     lib.contact_history_reset.restype = I32
@@ -329,27 +329,38 @@ class Contact:
             self._raise(rc, "contact_polytope_shift")
         return out
 
-    def history(self):
+    def history(self, boxes: bool = False):
         """Contact history after the last step: (ij [H,2] int32, c [H] float64)
-        host arrays sorted by (i, j)."""
+        host arrays sorted by (i, j); with boxes=True also box [H,6] float64,
+        each contact's corrected box minus X_i (the box pipeline's warm start;
+        zeros in the default sample set)."""
         n = ctypes.c_int64()
-        rc = self.lib.contact_history_get(self.ctx, 0, None, None, ctypes.byref(n))
+        rc = self.lib.contact_history_get(self.ctx, 0, None, None, None, ctypes.byref(n))
         if rc != OK:
             self._raise(rc, "contact_history_get")
         ij = np.zeros((n.value, 2), dtype=np.int32)
         c = np.zeros(n.value, dtype=np.float64)
-        rc = self.lib.contact_history_get(self.ctx, n.value, ij.ctypes.data, c.ctypes.data, ctypes.byref(n))
+        box = np.zeros((n.value, 6), dtype=np.float64)
+        rc = self.lib.contact_history_get(self.ctx, n.value, ij.ctypes.data, c.ctypes.data, box.ctypes.data,
+                                          ctypes.byref(n))
         if rc != OK:
             self._raise(rc, "contact_history_get")
-        return ij, c
+        return (ij, c, box) if boxes else (ij, c)
 
-    def set_history(self, ij, c):
-        """Replace the contact history (e.g. from a checkpoint)."""
+    def set_history(self, ij, c, box=None):
+        """Replace the contact history (e.g. from a checkpoint); box [H,6] is
+        required with the box pipeline."""
         ij = np.ascontiguousarray(ij, dtype=np.int32).reshape(-1, 2)
         c = np.ascontiguousarray(c, dtype=np.float64).reshape(-1)
         if len(c) != len(ij):
             raise ContactError(EINVAL, "ij and c differ in length")
-        rc = self.lib.contact_history_set(self.ctx, len(c), ij.ctypes.data, c.ctypes.data)
+        bp = None
+        if box is not None:
+            box = np.ascontiguousarray(box, dtype=np.float64).reshape(-1, 6)
+            if len(box) != len(ij):
+                raise ContactError(EINVAL, "ij and box differ in length")
+            bp = box.ctypes.data
+        rc = self.lib.contact_history_set(self.ctx, len(c), ij.ctypes.data, c.ctypes.data, bp)
         if rc != OK:
             self._raise(rc, "contact_history_set")
 

@@ -191,6 +191,7 @@ struct Lists {
   int* hist_j;      // [2, N, max_nbr] contact history: partner j > i of each ongoing contact of i
   double* hist_c;   // [2, N, max_nbr] its damping factor
   int* hist_n;      // [2, N] contacts per particle; buffer (steps & 1) is read, the other written
+  double* hist_box; // [2, N, max_nbr, 6] box pipeline: each contact's corrected box relative to X_i (or null)
   PairRec* pairs;   // [max_pairs]
   OvlRec* olist;    // [max_pairs] the step's overlapping pairs (counters[5] of them): the force law's work list
   int* tile_pair;   // [max_tiles] pair of each tile

@@ -311,8 +311,7 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
                      !std::isfinite(C.mu_k) || !std::isfinite(C.u_k)))
     return CONTACT_EINVAL;
   if (C.box_mode != 0 && C.box_mode != 1) return CONTACT_EINVAL;
-  if (C.box_mode == 1 && (C.contact_resolution < 1 || C.contact_resolution > 64 || C.history || C.friction))
-    return CONTACT_EINVAL;
+  if (C.box_mode == 1 && (C.contact_resolution < 1 || C.contact_resolution > 64)) return CONTACT_EINVAL;
   const int nw = C.n_walls;
   if (nw < 0 || nw > CONTACT_MAX_WALLS) return CONTACT_EINVAL;
   if (nw > 0 && (C.walls == nullptr || C.wall_young == nullptr || C.wall_poisson == nullptr)) return CONTACT_EINVAL;
@@ -601,6 +600,8 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
     GBC_TRY(dev_alloc(c, &W.hist_j, 2 * static_cast<size_t>(n) * max_nbr));
     GBC_TRY(dev_alloc(c, &W.hist_c, 2 * static_cast<size_t>(n) * max_nbr));
     GBC_TRY(dev_alloc(c, &W.hist_n, 2 * static_cast<size_t>(n)));
+    // the box pipeline's warm start: each contact's corrected box relative to X_i
+    if (C.box_mode == 1) GBC_TRY(dev_alloc(c, &W.hist_box, 2 * static_cast<size_t>(n) * max_nbr * 6));
   }
   GBC_TRY(dev_alloc(c, &W.pairs, mp));
   GBC_TRY(dev_alloc(c, &W.olist, mp));
@@ -784,7 +785,8 @@ contact_status history_buffer(contact_ctx* c, int* buf) {
 }
 }  // namespace
 
-contact_status contact_history_get(contact_ctx* c, int64_t max_rows, int32_t* ij, double* cv, int64_t* n) {
+contact_status contact_history_get(contact_ctx* c, int64_t max_rows, int32_t* ij, double* cv, double* box,
+                                   int64_t* n) {
   if (c == nullptr || n == nullptr || max_rows < 0 || (max_rows > 0 && (ij == nullptr || cv == nullptr)))
     return CONTACT_EINVAL;
   int b = 0;
@@ -792,35 +794,42 @@ contact_status contact_history_get(contact_ctx* c, int64_t max_rows, int32_t* ij
   if (hs != CONTACT_OK) return hs;
   const size_t np = static_cast<size_t>(c->P.n), cap = static_cast<size_t>(c->P.max_nbr);
   std::vector<int> cnt(np), hj(np * cap);
-  std::vector<double> hc(np * cap);
+  std::vector<double> hc(np * cap), hb(c->W.hist_box != nullptr ? np * cap * 6 : 0);
   cudaError_t e = cudaMemcpy(cnt.data(), c->W.hist_n + b * np, sizeof(int) * np, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess)
     e = cudaMemcpy(hj.data(), c->W.hist_j + b * np * cap, sizeof(int) * np * cap, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess)
     e = cudaMemcpy(hc.data(), c->W.hist_c + b * np * cap, sizeof(double) * np * cap, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && !hb.empty())
+    e = cudaMemcpy(hb.data(), c->W.hist_box + b * np * cap * 6, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(c, e, "contact_history_get");
-  std::vector<std::pair<std::pair<int, int>, double>> rows;
+  std::vector<std::pair<std::pair<int, int>, size_t>> rows;   // (i, j), slot
   for (size_t i = 0; i < np; ++i)
     for (int m = 0; m < std::min(cnt[i], c->P.max_nbr); ++m)
-      rows.push_back({{static_cast<int>(i), hj[i * cap + m]}, hc[i * cap + m]});
+      rows.push_back({{static_cast<int>(i), hj[i * cap + m]}, i * cap + m});
   std::sort(rows.begin(), rows.end());
   *n = static_cast<int64_t>(rows.size());
   for (int64_t r = 0; r < std::min<int64_t>(max_rows, *n); ++r) {
     ij[2 * r] = rows[r].first.first;
     ij[2 * r + 1] = rows[r].first.second;
-    cv[r] = rows[r].second;
+    cv[r] = hc[rows[r].second];
+    if (box != nullptr)
+      for (int k = 0; k < 6; ++k) box[6 * r + k] = hb.empty() ? 0.0 : hb[6 * rows[r].second + k];
   }
   return CONTACT_OK;
 }
 
-contact_status contact_history_set(contact_ctx* c, int64_t n_rows, const int32_t* ij, const double* cv) {
+contact_status contact_history_set(contact_ctx* c, int64_t n_rows, const int32_t* ij, const double* cv,
+                                   const double* box) {
   if (c == nullptr || n_rows < 0 || (n_rows > 0 && (ij == nullptr || cv == nullptr))) return CONTACT_EINVAL;
   int b = 0;
   const contact_status hs = history_buffer(c, &b);
   if (hs != CONTACT_OK) return hs;
   const size_t np = static_cast<size_t>(c->P.n), cap = static_cast<size_t>(c->P.max_nbr);
   std::vector<int> cnt(np, 0), hj(np * cap, -1);
-  std::vector<double> hc(np * cap, 0.0);
+  std::vector<double> hc(np * cap, 0.0), hb(c->W.hist_box != nullptr ? np * cap * 6 : 0, 0.0);
+  if (!hb.empty() && n_rows > 0 && box == nullptr)
+    return fail(c, CONTACT_EINVAL, "contact_history_set: the box pipeline's history needs the boxes");
   for (int64_t r = 0; r < n_rows; ++r) {
     const int i = ij[2 * r], j = ij[2 * r + 1];
     if (i < 0 || i >= c->P.n || j <= i || j >= c->P.n + c->P.nwall)   // j >= N: a wall
@@ -830,6 +839,12 @@ contact_status contact_history_set(contact_ctx* c, int64_t n_rows, const int32_t
       if (hj[i * cap + m] == j) return fail(c, CONTACT_EINVAL, "contact_history_set: repeated (i, j)");
     hj[i * cap + cnt[i]] = j;
     hc[i * cap + cnt[i]] = cv[r];
+    if (!hb.empty()) {
+      for (int k = 0; k < 3; ++k)
+        if (!(box[6 * r + k] <= box[6 * r + 3 + k]) || !std::isfinite(box[6 * r + k]) || !std::isfinite(box[6 * r + 3 + k]))
+          return fail(c, CONTACT_EINVAL, "contact_history_set: bad box");
+      for (int k = 0; k < 6; ++k) hb[6 * (i * cap + cnt[i]) + k] = box[6 * r + k];
+    }
     ++cnt[i];
   }
   cudaError_t e = cudaMemcpy(c->W.hist_n + b * np, cnt.data(), sizeof(int) * np, cudaMemcpyHostToDevice);
@@ -837,6 +852,8 @@ contact_status contact_history_set(contact_ctx* c, int64_t n_rows, const int32_t
     e = cudaMemcpy(c->W.hist_j + b * np * cap, hj.data(), sizeof(int) * np * cap, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(c->W.hist_c + b * np * cap, hc.data(), sizeof(double) * np * cap, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !hb.empty())
+    e = cudaMemcpy(c->W.hist_box + b * np * cap * 6, hb.data(), sizeof(double) * hb.size(), cudaMemcpyHostToDevice);
   return e == cudaSuccess ? CONTACT_OK : cuda_fail(c, e, "contact_history_set");
 }
 

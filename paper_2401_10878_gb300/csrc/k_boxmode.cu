@@ -277,6 +277,34 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
       XA[k] = D.X[3 * i + k];
       XB[k] = D.X[3 * j + k] - r.shift[k] * P.L[k];
     }
+    // contact history (Sec. 4.3.3): is (i, j) an ongoing contact?  Its c, and
+    // its last corrected box (relative to X_i) as the warm start: moved with
+    // particle i and widened by sqrt(0.75) dx, it cuts B0 down per axis
+    // (unless the cut leaves nothing)
+    size_t hslot = 0;
+    int hit = -1;
+    double c_hist = 0.0;
+    if (P.history) {
+      const int rd = W.counters[kStepCounter] & 1;
+      const size_t base = (static_cast<size_t>(rd) * P.n + i) * P.max_nbr;
+      const int cnt = min(W.hist_n[static_cast<size_t>(rd) * P.n + i], P.max_nbr);
+      for (int m = lane; m < cnt; m += 32)
+        if (W.hist_j[base + m] == j) hit = m;
+      hit = __reduce_max_sync(kFull, hit);
+      if (hit >= 0) {
+        hslot = base + hit;
+        c_hist = W.hist_c[hslot];
+        const double* wb = W.hist_box + 6 * hslot;
+        for (int k = 0; k < 3; ++k) {
+          const double wl = __dsub_rn(__dadd_rn(XA[k], wb[k]), s64), wh = __dadd_rn(__dadd_rn(XA[k], wb[3 + k]), s64);
+          const double l = fmax(b0lo[k], wl), h = fmin(b0hi[k], wh);
+          if (l < h) {
+            b0lo[k] = l;
+            b0hi[k] = h;
+          }
+        }
+      }
+    }
     // per face: the FP32 nearest line (line starts as FP32 offsets from each
     // centre: the face corner formed in FP64, plus the line's position on the
     // face), then lane f re-clips face f's nearest line in FP64
@@ -351,7 +379,7 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
     double shift_face[6];
 #pragma unroll
     for (int f = 0; f < 6; ++f) shift_face[f] = __shfl_sync(kFull, my_shift, f);
-    double lo1[3], step[3];
+    double lo1[3], hi1[3], step[3];
     for (int k = 0; k < 3; ++k) {
       double l = b0lo[k] + shift_face[2 * k], h = b0hi[k] - shift_face[2 * k + 1];
       if (!(l <= h)) {
@@ -359,6 +387,7 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
         h = b0hi[k];
       }
       lo1[k] = l;
+      hi1[k] = h;
       step[k] = (h - l) * inv_nc;
     }
     // 3. the N_c^3 sample points: offsets from each centre (and the box origin) in FP64, rounded once
@@ -464,20 +493,41 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
         ra[k] = xc[k] - XA[k];
         rb[k] = xc[k] - XB[k];
       }
-      if (vel != nullptr && P.damping_c != 0.0) {
+      // u_AB = (v_A + w_A x r_A) - (v_B + w_B x r_B) at x_c, ddot_n = u_AB . n
+      double uab[3] = {0.0, 0.0, 0.0}, ddot = 0.0;
+      if (vel != nullptr && (P.damping_c != 0.0 || P.history || P.friction)) {
         const double* va = vel + 6 * i;
         const double* vb = j < P.n ? vel + 6 * j : D.rest6;
         const double ua[3] = {va[0] + (va[4] * ra[2] - va[5] * ra[1]), va[1] + (va[5] * ra[0] - va[3] * ra[2]),
                               va[2] + (va[3] * ra[1] - va[4] * ra[0])};
         const double ub[3] = {vb[0] + (vb[4] * rb[2] - vb[5] * rb[1]), vb[1] + (vb[5] * rb[0] - vb[3] * rb[2]),
                               vb[2] + (vb[3] * rb[1] - vb[4] * rb[0])};
-        const double ddot = (ua[0] - ub[0]) * nv[0] + (ua[1] - ub[1]) * nv[1] + (ua[2] - ub[2]) * nv[2];
-        damp = fmax(0.0, 1.0 + P.damping_c * ddot);
+        for (int k = 0; k < 3; ++k) uab[k] = ua[k] - ub[k];
+        ddot = uab[0] * nv[0] + uab[1] * nv[1] + uab[2] * nv[2];
       }
+      // c: the shared one, or with the history the contact's own (a new
+      // contact's from u0 = ddot_n, Eq. damping_factor; 0 for u0 <= 0)
+      double cdamp = P.damping_c;
+      if (P.history) cdamp = hit >= 0 ? c_hist : (ddot > 0.0 ? P.damp_K / ddot : 0.0);
+      if (vel != nullptr && cdamp != 0.0) damp = fmax(0.0, 1.0 + cdamp * ddot);
       const double vd = V * d;
       const double fmag = vd > 0.0 ? (4.0 / (3.0 * 3.14159265358979323846)) * estar * sqrt(vd) * damp : 0.0;
       double F[3], TA[3], TB[3];
       for (int k = 0; k < 3; ++k) F[k] = fmag * nv[k];
+      if (P.friction && vel != nullptr && fmag > 0.0) {
+        // Eq. (contact_force_tangential): B receives +f(a) |F_n| t, t = u_t / |u_t|
+        const double ut[3] = {uab[0] - ddot * nv[0], uab[1] - ddot * nv[1], uab[2] - ddot * nv[2]};
+        const double utn = sqrt(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
+        if (utn > 0.0) {
+          const double a = utn * P.inv_u_k, a2 = a * a;
+          double coef = P.mu_k;
+          if (a2 < 1e30) {
+            const double den1 = a2 * a2 + 1.0, den2 = a2 + 1.0;
+            coef = a2 * ((2.0 * P.mu_s_star - P.mu_k) * den2 + P.mu_k * den1) / (den1 * den2);
+          }
+          for (int k = 0; k < 3; ++k) F[k] += coef * fmag * ut[k] / utn;
+        }
+      }
       TA[0] = -(ra[1] * F[2] - ra[2] * F[1]);
       TA[1] = -(ra[2] * F[0] - ra[0] * F[2]);
       TA[2] = -(ra[0] * F[1] - ra[1] * F[0]);
@@ -495,6 +545,19 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
       double* tp = W.tape + static_cast<size_t>(q) * kTapeDoubles;
       for (int k = 0; k < kTapeDoubles; ++k) tp[k] = 0.0;
       atomicAdd(&W.counters[5], 1);
+      if (P.history) {   // this step's contact: j, c and the corrected box minus X_i
+        const int wr = (W.counters[kStepCounter] & 1) ^ 1;
+        const int slot = atomicAdd(W.hist_n + static_cast<size_t>(wr) * P.n + i, 1);
+        if (slot < P.max_nbr) {
+          const size_t e = (static_cast<size_t>(wr) * P.n + i) * P.max_nbr + slot;
+          W.hist_j[e] = j;
+          W.hist_c[e] = cdamp;
+          for (int k = 0; k < 3; ++k) {
+            W.hist_box[6 * e + k] = __dsub_rn(lo1[k], XA[k]);
+            W.hist_box[6 * e + 3 + k] = __dsub_rn(hi1[k], XA[k]);
+          }
+        }
+      }
     }
   }
 }
