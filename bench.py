@@ -434,6 +434,18 @@ def extras(args, dev, flush, peak):
                            "pairs": s_["pairs"], "pairs_with_overlap": s_["overlapping"],
                            "samples_per_step": s_["pairs"] * nc ** 3}
         m.close()
+    # N_c = 8 with the contact history (each contact's c and its corrected box,
+    # the next correction's warm start) and friction, velocities as above
+    st_b = dataclasses.replace(headline_state(0))
+    st_b.box_mode, st_b.contact_resolution = 1, 8
+    m = Contact.from_state(st_b, narrow_events=True, history=True, restitution=0.5, friction=True, mu_s=0.5,
+                           mu_k=0.3, u_k=0.02)
+    r = time_forward(m, pd, qd, steps, 3, flush, narrow=True, vel_d=vd)
+    s_ = m.stats()
+    boxm["nc8_history_friction"] = {"ms_per_step": r["ms"] / steps, "box_kernel_ms": r["narrow_ms"] / steps,
+                                    "pairs": s_["pairs"], "pairs_with_overlap": s_["overlapping"],
+                                    "contacts_in_history": int(len(m.history()[1]))}
+    m.close()
     out["cubes1934_box_pipeline"] = boxm
     # the headline workload between a floor and a ceiling (fixed walls, 2 of them)
     st_w = W.floor_and_ceiling(headline_state(0))

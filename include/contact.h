@@ -193,9 +193,13 @@ contact_status contact_step(contact_ctx* ctx, const double* pos, const double* q
  * memory (n_pairs, force, torque must not be NULL), and returns when the
  * copies are complete.  When pair_ij / pair_out are not NULL the first
  * min(P, max_pairs) rows of the pair outputs are copied to them as well (as
- * laid out by contact_step).  Page-locked host buffers are copied inside one
- * captured graph together with the step; pageable ones with ordinary copies
- * around it.  The device buffers are allocated at the first call and owned by
+ * laid out by contact_step).  When pos, quat, n_pairs, force and torque are
+ * all page-locked and mapped into the device's address space (as cudaHostAlloc
+ * and cudaHostRegister memory is with unified addressing), the step's kernels
+ * read the poses and write the pair count, forces and torques there directly
+ * (coherent over NVLink-C2C on Grace-Blackwell), with vel copied, all in one
+ * captured graph; other page-locked buffers are copied inside that graph,
+ * pageable ones with ordinary copies around the step.  The device buffers are allocated at the first call and owned by
  * the context.  Errors: those of contact_step, reported by this call (it
  * synchronises the context stream); CONTACT_ENOMEM if the buffers cannot be
  * allocated.  A later contact_backward differentiates this step. */

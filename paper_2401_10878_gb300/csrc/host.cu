@@ -925,7 +925,37 @@ contact_status contact_step_host(contact_ctx* c, const double* pos, const double
   const bool all_pinned = same || (pinned(pos) && pinned(quat) && pinned(vel) && pinned(n_pairs) && pinned(force) &&
                                    pinned(torque));
   double* dvel = vel != nullptr ? c->hs_vel : nullptr;
+  // Page-locked host memory is mapped into the device's address space (and on
+  // Grace-Blackwell reached coherently over NVLink-C2C): when every buffer
+  // has a device address, the pose kernels read the poses and the particle
+  // sums write the forces and torques there directly, with no copy nodes.
+  // The velocities, read per pair by the force law, are still copied.
+  auto mapped = [](const void* p) -> void* {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+  };
+  const double *zpos = nullptr, *zquat = nullptr;
+  double *zforce = nullptr, *ztorque = nullptr;
+  int32_t* znp = nullptr;
+  bool zero_copy = false;
+  if (!same && all_pinned) {
+    zpos = static_cast<const double*>(mapped(pos));
+    zquat = static_cast<const double*>(mapped(quat));
+    zforce = static_cast<double*>(mapped(force));
+    ztorque = static_cast<double*>(mapped(torque));
+    znp = static_cast<int32_t*>(mapped(n_pairs));
+    zero_copy = zpos && zquat && zforce && ztorque && znp;
+  }
   auto enqueue_all = [&](bool capturing) {
+    if (zero_copy) {
+      if (vel != nullptr) cudaMemcpyAsync(c->hs_vel, vel, 6 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+      enqueue_step(c, capturing, zpos, zquat, dvel, c->hs_pair_ij, c->hs_pair_out, znp, zforce, ztorque);
+      return;
+    }
     cudaMemcpyAsync(c->hs_pos, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     cudaMemcpyAsync(c->hs_quat, quat, 4 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (vel != nullptr) cudaMemcpyAsync(c->hs_vel, vel, 6 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
