@@ -173,6 +173,7 @@ class Contact:
         cfg.narrow_events = int(bool(narrow_events))
         self.cfg = cfg
         self.n = n
+        self.steps = 0   # contact_step calls so far (the adjoint differentiates the last)
         self.max_pairs = int(cfg.max_pairs)
         arrs = [np.ascontiguousarray(shape_type, np.int32), np.ascontiguousarray(shape_param, np.float64),
                 np.ascontiguousarray(face_offset, np.int32),
@@ -239,6 +240,7 @@ class Contact:
                                         ctypes.c_void_p(torque.data_ptr()),
                                         ctypes.c_void_p(pij.data_ptr() if pairs else 0),
                                         ctypes.c_void_p(pout.data_ptr() if pairs else 0))
+        self.steps += 1
         if rc != OK:
             self._raise(rc, "contact_step_host")
         out = dict(force=force, torque=torque, n_pairs=int(n_pairs.item()))
@@ -256,6 +258,7 @@ class Contact:
             raise ContactError(EINVAL, "pos must be [N,3] and quat [N,4]")
         rc = self.lib.contact_step(self.ctx, _ptr(pos), _ptr(quat), _ptr(vel), _ptr(self.pair_ij),
                                    _ptr(self.pair_out), _ptr(self.n_pairs), _ptr(self.force), _ptr(self.torque))
+        self.steps += 1
         if rc != OK:
             self._raise(rc, "contact_step")
 
@@ -401,20 +404,38 @@ def polytope_centroid(planes) -> np.ndarray:
 
 
 class ContactFunction(torch.autograd.Function):
-    """(pos, quat) -> (force, torque) with the library's adjoint as backward."""
+    """(pos, quat, vel) -> (force, torque, pair_ij, pair_out) with the
+    library's adjoint as backward.  vel (or None) enters the damping and the
+    friction and is not differentiated; the pair outputs carry no gradient."""
 
     @staticmethod
-    def forward(ctx, model, pos, quat):
-        out = model.step(pos, quat)
+    def forward(ctx, model, pos, quat, vel):
+        v = None if vel is None else vel.detach().to(torch.float64).contiguous()
+        out = model.step(pos.detach().to(torch.float64).contiguous(), quat.detach().to(torch.float64).contiguous(), v)
         ctx.model = model
-        return out["force"].clone(), out["torque"].clone()
+        ctx.step_id = model.steps
+        ctx.vel = v   # the adjoint reads the step's velocities: they stay alive until backward
+        pij, pout = out["pair_ij"].clone(), out["pair_out"].clone()
+        ctx.mark_non_differentiable(pij, pout)
+        return out["force"].clone(), out["torque"].clone(), pij, pout
 
     @staticmethod
-    def backward(ctx, gF, gT):
+    def backward(ctx, gF, gT, _g_ij, _g_out):
+        if ctx.model.steps != ctx.step_id:
+            raise RuntimeError("contact_forces: the model stepped again after this forward; the adjoint "
+                               "differentiates the model's last step only")
         gp, gq = ctx.model.backward(gF.to(torch.float64).contiguous(), gT.to(torch.float64).contiguous())
-        return None, gp, gq
+        return None, gp, gq, None
 
 
-def contact_forces(model: Contact, pos: torch.Tensor, quat: torch.Tensor):
-    """Per-particle contact force and torque, differentiable w.r.t. pos and quat."""
-    return ContactFunction.apply(model, pos, quat)
+def contact_forces(model: Contact, pos: torch.Tensor, quat: torch.Tensor, vel: torch.Tensor = None,
+                   pairs: bool = False):
+    """Per-particle contact force and torque [N,3], differentiable w.r.t. pos
+    and quat (smoothed indicator).  vel [N,6] (v, omega), if given, drives the
+    damping and friction (not differentiated).  With pairs=True also returns
+    dict(pair_ij [P,2], pair_out [P,11]) of the step.  A backward must come
+    before the model's next step."""
+    force, torque, pij, pout = ContactFunction.apply(model, pos, quat, vel)
+    if pairs:
+        return force, torque, dict(pair_ij=pij, pair_out=pout)
+    return force, torque

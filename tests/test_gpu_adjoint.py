@@ -116,3 +116,36 @@ def test_adjoint_matches_central_differences_on_subblock():
     assert np.mean(smooth) >= 0.8
     assert np.mean(err[smooth] <= 1e-4) >= 0.99
     assert np.median(err[smooth]) <= 1e-6
+
+
+def test_autograd_function_with_velocities_and_pairs():
+    """contact_forces (torch.autograd.Function): a loss of the forces and
+    torques back-propagates to pos.grad and quat.grad equal to the oracle's
+    gradient, with shared damping driven by velocities that are not
+    differentiated; the pair outputs come back without gradient; a backward
+    after another step of the model is refused."""
+    from paper_2401_10878_gb300.contact import Contact, contact_forces
+    st = W.mixed_grid_27()
+    st.indicator, st.smooth_width, st.damping_c = 1, 1.0, 0.3
+    rng = np.random.default_rng(12)
+    vel = np.concatenate([rng.normal(size=(st.n, 3)) * 0.05, rng.normal(size=(st.n, 3)) * 0.01], axis=1)
+    gf, gt = W.loss_weights(st.n)
+    m = Contact.from_state(st)
+    pos = torch.tensor(st.pos, device="cuda", requires_grad=True)
+    quat = torch.tensor(st.quat, device="cuda", requires_grad=True)
+    v = torch.tensor(vel, device="cuda")
+    force, torque, pairs = contact_forces(m, pos, quat, v, pairs=True)
+    assert not pairs["pair_out"].requires_grad and len(pairs["pair_ij"]) == oracle.contact_step(st).n_pairs
+    loss = (force * torch.tensor(gf, device="cuda")).sum() + (torque * torch.tensor(gt, device="cuda")).sum()
+    loss.backward()
+    rp, rq = oracle.gradient(st, gf, gt, vel=vel)
+    s = _scale(rp, rq)
+    err = max(np.abs(pos.grad.cpu().numpy() - rp).max(), np.abs(quat.grad.cpu().numpy() - rq).max()) / s
+    print("autograd with damping: max |diff| / max |grad| =", err)
+    assert err <= 1e-4
+    # a stale tape: the model stepped again before the backward
+    f2, t2 = contact_forces(m, pos, quat, v)
+    m.step(pos.detach(), quat.detach(), v)
+    with pytest.raises(RuntimeError):
+        (f2.sum() + t2.sum()).backward()
+    m.close()
