@@ -324,7 +324,8 @@ def run_ours(args, ws, rank, local):
 def end_to_end(model, pos, quat, steps, warmup, dev):
     """The same step through the C-ABI call with HOST buffers
     (contact_step_host): page-locked host poses in, host forces and torques
-    out, the copies inside the call; wall-clock time per call."""
+    out, the transfers inside the call (the step's kernels read and write the
+    mapped host buffers over the host link); wall-clock time per call."""
     import torch
     hp = torch.tensor(pos).pin_memory()
     hq = torch.tensor(quat).pin_memory()
@@ -349,7 +350,8 @@ def end_to_end(model, pos, quat, steps, warmup, dev):
     n = model.n
     return {"value": cells / tot, "unit": UNIT, "h2d_bytes_per_step": n * 7 * 8,
             "d2h_bytes_per_step": n * 6 * 8 + 4, "ms_per_step": 1e3 * tot / steps,
-            "timing": "wall clock around contact_step_host (pinned host buffers, copies inside the call)"}
+            "timing": "wall clock around contact_step_host (pinned host buffers read and written by the step's "
+                      "kernels inside the call)"}
 
 
 def box_volume_percentiles(m, st, pos):

@@ -417,8 +417,9 @@ class Contact:
 
 def polytope_centroid(planes) -> np.ndarray:
     """Volume centroid of the polytope n . y <= d (rows (n, d), unit n, d > 0).
-    Poses refer to the centre of mass: a polytope whose centroid is off its
-    body origin is refused by contact_init; subtract n . centroid from every d."""
+    Poses refer to the centre of mass: contact_init moves a polytope whose
+    centroid is off its body origin there (d -= n . centroid; see
+    Contact.polytope_shift), so positions name the centroid."""
     lib = load_library()
     pl = np.ascontiguousarray(planes, dtype=np.float64).reshape(-1, 4)
     c = np.zeros(3)
