@@ -125,6 +125,57 @@ def test_periodic_corner_pairs():
     print("periodic", run_parity(st, 0))
 
 
+def test_positions_on_the_periodic_boundary():
+    """Centres at x = 0, y = -0.0 and z = the largest double below L, each
+    touching a partner across the boundary: the pairs, their images and the
+    node ranges bit for bit, the outputs with the usual tolerances (both
+    forms); a centre at exactly L is refused on both sides."""
+    from paper_2401_10878_gb300.contact import ContactError, EINVAL
+    top = np.nextafter(64.0, 0.0)
+    pos = [[0.0, 20.0, 20.0], [59.0, 20.5, 20.0], [30.0, -0.0, 30.0], [31.0, 55.0, 30.5],
+           [40.0, 40.0, top], [41.0, 40.5, 6.0]]
+    types = [1, 0, 0, 1, 1, 0]
+    params = [[5, 5, 5], [5.5, 0, 0], [6, 0, 0], [4.5, 4.5, 4.5], [3, 4, 5], [5, 0, 0]]
+    st = state(types, params, pos, W.random_quaternions(np.random.default_rng(3), 6))
+    r = oracle.contact_step(st)
+    assert r.n_pairs == 3 and np.all(r.pair_out[:, 0] > 0) and np.abs(r.pair_shift).sum() == 3
+    print("boundary", run_parity(st, 0), run_parity(st, 1))
+    m = model_for(st)
+    gpu_step(m, st)
+    assert np.array_equal(m.particle_boxes().cpu().numpy(), oracle.aabb(st))
+    bad = st.pos.copy()
+    bad[4, 2] = 64.0
+    with pytest.raises(ContactError) as e:
+        gpu_step(m, st, pos=bad)
+    assert e.value.code == EINVAL
+    with pytest.raises(oracle.OracleError):
+        oracle.contact_step(st, pos=bad)
+    m.close()
+
+
+def test_concentric_shapes_degenerate_normal():
+    """Concentric shapes centred on a node: G vanishes by symmetry, so the
+    normal is undefined (the oracle's FP64 sums cancel below the fallback
+    threshold and its centre-line fallback is zero; the FP32 partial sums
+    leave rounding noise).  What the method does define is compared: V bit for
+    bit, d, and a finite normal of unit or zero length with F along it."""
+    cases = [state([0, 0], [[6, 0, 0], [4, 0, 0]], [[30.0, 30.0, 30.0]] * 2),
+             state([1, 1], [[4, 4, 4], [4, 4, 4]], [[30.0, 30.0, 30.0]] * 2)]
+    for st in cases:
+        r = oracle.contact_step(st)
+        m = model_for(st)
+        g = gpu_step(m, st)
+        o, ro = g["pair_out"][0], r.pair_out[0]
+        assert g["n_pairs"] == 1 and o[0] == ro[0] and abs(o[7] - ro[7]) <= 1e-6
+        nn = np.linalg.norm(o[4:7])
+        assert np.all(np.isfinite(o)) and (nn == 0.0 or abs(nn - 1.0) < 1e-12)
+        if nn > 0:
+            assert np.linalg.norm(np.cross(o[8:11], o[4:7])) <= 1e-9 * np.linalg.norm(o[8:11])
+        print("concentric", st.shape_type.tolist(), "V", o[0], "d", o[7], "|n|", nn, "oracle |n|",
+              np.linalg.norm(ro[4:7]))
+        m.close()
+
+
 def test_many_face_polytopes_and_inflation():
     rng = np.random.default_rng(3)
     polys = [W.random_polytope(rng, f, 9.0)[0] for f in (24, 32, 8, 20)]
