@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/contact.h"
 #include "contact_dev.cuh"
 
@@ -45,6 +47,16 @@ struct contact_ctx {
 };
 
 namespace {
+
+// NVTX range around a public call (host side: a profiler's timeline shows each
+// call with the kernels and copies it enqueued; without a tool attached it
+// costs a function-pointer call)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 contact_status fail(contact_ctx* c, contact_status s, const std::string& msg) {
   if (c) c->last_error = msg;
@@ -650,6 +662,7 @@ contact_status contact_set_stream(contact_ctx* c, void* stream) {
 contact_status contact_step(contact_ctx* c, const double* pos, const double* quat, const double* vel,
                             int32_t* pair_ij, double* pair_out, int32_t* n_pairs, double* force,
                             double* torque) {
+  const NvtxRange range("contact_step");
   if (c == nullptr) return CONTACT_EINVAL;
   if (pos == nullptr || quat == nullptr || pair_ij == nullptr || pair_out == nullptr || n_pairs == nullptr ||
       force == nullptr || torque == nullptr)
@@ -872,6 +885,7 @@ int32_t contact_kernels_per_backward(const contact_ctx*) { return 3; }
 
 contact_status contact_backward(contact_ctx* c, const double* grad_force, const double* grad_torque,
                                 double* grad_pos, double* grad_quat) {
+  const NvtxRange range("contact_backward");
   if (c == nullptr) return CONTACT_EINVAL;
   if (grad_force == nullptr || grad_torque == nullptr || grad_pos == nullptr || grad_quat == nullptr)
     return fail(c, CONTACT_EINVAL, "contact_backward: null buffer");
@@ -891,6 +905,7 @@ contact_status contact_backward(contact_ctx* c, const double* grad_force, const 
 contact_status contact_step_host(contact_ctx* c, const double* pos, const double* quat, const double* vel,
                                  int32_t* n_pairs, double* force, double* torque, int32_t* pair_ij,
                                  double* pair_out) {
+  const NvtxRange range("contact_step_host");
   if (c == nullptr) return CONTACT_EINVAL;
   if (pos == nullptr || quat == nullptr || n_pairs == nullptr || force == nullptr || torque == nullptr)
     return fail(c, CONTACT_EINVAL, "contact_step_host: null buffer");

@@ -228,6 +228,18 @@ def test_capacity_and_input_errors():
     assert e.value.code == EINVAL
     m.clear_error()
     gpu_step(m, st)   # the context is usable again
+    # NaN position, NaN and zero quaternions: the same sticky error, then recovery
+    for field, row, value in (("pos", 7, np.nan), ("quat", 3, np.nan), ("quat", 4, 0.0)):
+        p, q = st.pos.copy(), st.quat.copy()
+        if field == "pos":
+            p[row, 0] = value
+        else:
+            q[row, :] = value
+        with pytest.raises(ContactError) as e:
+            gpu_step(m, st, pos=p, quat=q)
+        assert e.value.code == EINVAL, field
+        m.clear_error()
+    gpu_step(m, st)
     m.close()
 
 
