@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU baseline budget")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline (profiling runs)")
+    ap.add_argument("--workload", default="cubes1934", choices=sorted(WORKLOADS),
+                    help="state of the main line (default: the headline, 1934 cubes)")
+    ap.add_argument("--seed", type=int, default=None, help="seed of the state (default: the workload's own)")
     return ap.parse_args()
 
 
@@ -89,9 +92,41 @@ def headline_state(rank: int):
     return st
 
 
-def workload_config(st, extra=None):
-    cfg = {"workload": "1934 cuboids (edge 12) at 30% volume fraction, periodic 223^3 lattice, dx = 1",
-           "particles": st.n, "lattice": list(st.n_cells), "indicator": "sharp",
+# --workload: (description, state(seed offset) -> State); the default is the headline
+WORKLOADS = {
+    "cubes1934": ("1934 cuboids (edge 12) at 30% volume fraction, periodic 223^3 lattice, dx = 1", None),
+    "cubes1934_smooth": ("1934 cuboids (edge 12) at 30% volume fraction, periodic 223^3 lattice, dx = 1, "
+                         "smoothed indicator (w = 1 cell)", "settling_cubes_dense"),
+    "mixed1934": ("1934 particles (1/3 spheres d = 14.9, 1/3 cubes edge 12, 1/3 polytopes 12-20 faces) at 30% "
+                  "volume fraction, periodic 223^3 lattice", "mixed_settling"),
+    "cubes400": ("400 cubes (edge 12) at 10% volume fraction, periodic 190^3 lattice", "settling_cubes"),
+    "mixed27": ("27 particles (14 spheres d = 15, 13 cubes edge 12) on a jittered 3x3x3 grid, periodic 64^3 "
+                "lattice", "mixed_grid_27"),
+}
+
+
+def workload_state(args, rank: int):
+    """The main line's state: the headline unless --workload names another."""
+    from paper_2401_10878_gb300 import workloads as W
+    name = getattr(args, "workload", "cubes1934")
+    seed = getattr(args, "seed", None)
+    if name == "cubes1934":
+        st = headline_state(rank) if seed is None else W.settling_cubes_dense(seed=seed + 1000 * rank)
+        st.indicator = 0
+        st.name = "cubes1934_223"
+        return st
+    fn = getattr(W, WORKLOADS[name][1])
+    st = fn() if seed is None and rank == 0 else fn(seed=(seed if seed is not None else 0) + 1000 * rank + 1)
+    st.indicator = 1 if name == "cubes1934_smooth" else 0
+    if name == "cubes1934_smooth":
+        st.smooth_width = 1.0
+    st.name = name
+    return st
+
+
+def workload_config(st, extra=None, name="cubes1934"):
+    cfg = {"workload": WORKLOADS[name][0],
+           "particles": st.n, "lattice": list(st.n_cells), "indicator": "smoothed" if st.indicator else "sharp",
            "precision": "fp32 node tests, fp32 tile partials, fp64 pair/particle reductions",
            "pose_steps": "seeded increments dX~N(0,0.05), rot~N(0,0.01 rad)",
            "l2": "flushed (1 GiB write, > 129 MB L2) before every timed step; the host enqueues the step while the flush runs", "parallelism": "weak (one box per GPU)"}
@@ -162,7 +197,7 @@ def run_reference(args, ws, rank):
     import oracle
     from paper_2401_10878_gb300 import workloads as W
     oracle.build()
-    st = headline_state(0)
+    st = workload_state(args, 0)
     pos, quat = W.pose_sequence(st, max(args.steps + args.warmup, 1))
     threads = oracle.max_threads()
     for s in range(args.warmup):
@@ -177,7 +212,7 @@ def run_reference(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(st),
+            "data": "synthetic", "config": workload_config(st, None, args.workload),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{args.steps} full contact steps of the workload (all pairs)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -250,7 +285,7 @@ def run_ours(args, ws, rank, local):
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    st = headline_state(rank)
+    st = workload_state(args, rank)
     nseq = min(100, args.steps + args.warmup)   # the seeded pose sequence is cycled
     pos, quat = W.pose_sequence(st, nseq, seed=11 + rank)
     pos_d = torch.tensor(pos, device=dev)
@@ -290,7 +325,8 @@ def run_ours(args, ws, rank, local):
     achieved = ops_per_launch / narrow_avg_s / 1e12
     med = clocks.get("sm_mhz")
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32 lane-ops/s",
-                "frac": achieved / peak, "traffic": traffic_from_profile(),
+                "frac": achieved / peak,
+                "traffic": traffic_from_profile() if args.workload == "cubes1934" and args.seed is None else None,
                 "kernel": "k_narrow32 (node sweep)", "ops_per_launch": ops_per_launch,
                 "launch_ms": narrow_avg_s * 1e3,
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz (max SM clock)",
@@ -307,7 +343,8 @@ def run_ours(args, ws, rank, local):
             "config": workload_config(st, {"pairs_per_step": stats["pairs"],
                                            "cells_per_step": res["cells"] / args.steps,
                                            "overlapping_pairs": stats["overlapping"],
-                                           "tiles_per_step": stats["tiles"], "narrow_grid": stats["narrow_grid"]}),
+                                           "tiles_per_step": stats["tiles"], "narrow_grid": stats["narrow_grid"]},
+                                      args.workload),
             "roofline": roofline, "e2e": e2e, "gpu_launches": model.kernels_per_step() * args.steps,
             "clocks": clocks,
             "ms_per_step_median": float(np.median(res["per"])),
