@@ -313,22 +313,33 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
     unsigned my_key = 0xffffffffu;
     int my_line = 0;
     auto sel = [](const double* a, int c) { return c == 0 ? a[0] : (c == 1 ? a[1] : a[2]); };
-    for (int f = 0; f < 6; ++f) {
-      const int k = f >> 1, side = f & 1;
+    // each face's line geometry in FP64 once, face f on lane f (the FP64 pipe
+    // takes a warp instruction's time however few lanes it has): the corner's
+    // offsets from both centres, the line spacings and the line length, as FP32
+    float fca[3] = {0.f, 0.f, 0.f}, fcb[3] = {0.f, 0.f, 0.f}, fdu = 0.f, fdv = 0.f, flen = 0.f;
+    if (lane < 6) {
+      const int k = lane >> 1, side = lane & 1;
       const int u = k == 0 ? 1 : 0, v = k == 2 ? 1 : 2;
-      const float sgn = side == 0 ? 1.f : -1.f;
       const double corner[3] = {k == 0 ? (side == 0 ? b0lo[0] : b0hi[0]) : b0lo[0],
                                 k == 1 ? (side == 0 ? b0lo[1] : b0hi[1]) : b0lo[1],
                                 k == 2 ? (side == 0 ? b0lo[2] : b0hi[2]) : b0lo[2]};
-      float ca[3], cb[3];
       for (int c = 0; c < 3; ++c) {
-        ca[c] = static_cast<float>((corner[c] - XA[c]) * P.inv_dx);
-        cb[c] = B.kind == KIND_WALL ? static_cast<float>(corner[c] * P.inv_dx - r.lo[c])
-                                    : static_cast<float>((corner[c] - XB[c]) * P.inv_dx);
+        fca[c] = static_cast<float>((corner[c] - XA[c]) * P.inv_dx);
+        fcb[c] = B.kind == KIND_WALL ? static_cast<float>(corner[c] * P.inv_dx - r.lo[c])
+                                     : static_cast<float>((corner[c] - XB[c]) * P.inv_dx);
       }
-      const float du = static_cast<float>((sel(b0hi, u) - sel(b0lo, u)) * (P.inv_dx * inv_nc));
-      const float dv = static_cast<float>((sel(b0hi, v) - sel(b0lo, v)) * (P.inv_dx * inv_nc));
-      const float lenl = static_cast<float>((sel(b0hi, k) - sel(b0lo, k)) * P.inv_dx);
+      fdu = static_cast<float>((sel(b0hi, u) - sel(b0lo, u)) * (P.inv_dx * inv_nc));
+      fdv = static_cast<float>((sel(b0hi, v) - sel(b0lo, v)) * (P.inv_dx * inv_nc));
+      flen = static_cast<float>((sel(b0hi, k) - sel(b0lo, k)) * P.inv_dx);
+    }
+    for (int f = 0; f < 6; ++f) {
+      const int k = f >> 1, side = f & 1;
+      const float sgn = side == 0 ? 1.f : -1.f;
+      const float ca[3] = {__shfl_sync(kFull, fca[0], f), __shfl_sync(kFull, fca[1], f), __shfl_sync(kFull, fca[2], f)};
+      const float cb[3] = {__shfl_sync(kFull, fcb[0], f), __shfl_sync(kFull, fcb[1], f), __shfl_sync(kFull, fcb[2], f)};
+      const float du = __shfl_sync(kFull, fdu, f), dv = __shfl_sync(kFull, fdv, f);
+      const float lenl = __shfl_sync(kFull, flen, f);
+      const int u = k == 0 ? 1 : 0, v = k == 2 ? 1 : 2;
       float best = FLT_MAX;
       int bestl = 0x7fffffff;
       for (int l0 = 0; l0 < nl; l0 += 32) {
@@ -391,13 +402,21 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
       step[k] = (h - l) * inv_nc;
     }
     // 3. the N_c^3 sample points: offsets from each centre (and the box origin) in FP64, rounded once
+    // (component k on lane k, then shared)
+    float loA = 0.f, loB = 0.f, lst = 0.f;
+    if (lane < 3) {
+      const double lk = sel(lo1, lane), sk = sel(step, lane), xa = sel(XA, lane), xb = sel(XB, lane);
+      const int rlo = lane == 0 ? r.lo[0] : (lane == 1 ? r.lo[1] : r.lo[2]);
+      const double c0 = lk + 0.5 * sk;
+      loA = static_cast<float>((c0 - xa) * P.inv_dx);
+      loB = B.kind == KIND_WALL ? static_cast<float>(c0 * P.inv_dx - rlo) : static_cast<float>((c0 - xb) * P.inv_dx);
+      lst = static_cast<float>(sk * P.inv_dx);
+    }
     float oA[3], oB[3], st[3];
     for (int k = 0; k < 3; ++k) {
-      const double c0 = lo1[k] + 0.5 * step[k];
-      oA[k] = static_cast<float>((c0 - XA[k]) * P.inv_dx);
-      oB[k] = B.kind == KIND_WALL ? static_cast<float>(c0 * P.inv_dx - r.lo[k])
-                                  : static_cast<float>((c0 - XB[k]) * P.inv_dx);
-      st[k] = static_cast<float>(step[k] * P.inv_dx);
+      oA[k] = __shfl_sync(kFull, loA, k);
+      oB[k] = __shfl_sync(kFull, loB, k);
+      st[k] = __shfl_sync(kFull, lst, k);
     }
     const float inv_w = P.inv_w, hw = 0.5f * P.wdx_l;
     float cnt = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, bestf = -FLT_MAX;
