@@ -71,20 +71,23 @@ __device__ __forceinline__ void load_shape(const PairRec& r, bool second, const 
 }
 
 // Signed distance (lattice units) at q = point - centre, and the world
-// gradient of the active branch (first maximal face).
+// gradient of the active branch (first maximal face).  SET is the context's
+// kind set (2: cubes only, 1: spheres, cuboids and walls, 0: every kind): the
+// kinds a set cannot hold are compiled out.
+template <int SET>
 __device__ __forceinline__ float phi_f(const ShapeF& s, const float q[3], float g[3]) {
-  if (s.kind == KIND_SPHERE) {
+  if (SET != 2 && s.kind == KIND_SPHERE) {
     const float n2 = fmaf(q[0], q[0], fmaf(q[1], q[1], q[2] * q[2]));
     const float nr = sqrtf(n2);
     const float inv = nr > 0.f ? 1.f / nr : 0.f;
     for (int k = 0; k < 3; ++k) g[k] = q[k] * inv;
     return nr - s.sz[0];
   }
-  if (s.kind == KIND_WALL) {   // q = box-relative point; sz[0] = value at the box origin
+  if (SET != 2 && s.kind == KIND_WALL) {   // q = box-relative point; sz[0] = value at the box origin
     for (int k = 0; k < 3; ++k) g[k] = s.rt[k];
     return fmaf(s.rt[0], q[0], fmaf(s.rt[1], q[1], fmaf(s.rt[2], q[2], s.sz[0])));
   }
-  if (s.kind == KIND_CUBOID || s.kind == KIND_CUBE) {
+  if (SET != 0 || s.kind == KIND_CUBOID || s.kind == KIND_CUBE) {
     float best = -FLT_MAX;
     int kk = 0;
     float sg = 1.f;
@@ -111,7 +114,8 @@ __device__ __forceinline__ float phi_f(const ShapeF& s, const float q[3], float 
 }
 
 // Interval [t0, t1] of the line q + t e (q = start - centre, e = +-axis k)
-// inside the shape, FP32 (empty: t0 > t1).
+// inside the shape, FP32 (empty: t0 > t1); SET as for phi_f.
+template <int SET>
 __device__ __forceinline__ void clip_f(const ShapeF& s, const float q[3], int k, float sgn, float* t0, float* t1) {
   *t0 = -FLT_MAX;
   *t1 = FLT_MAX;
@@ -122,7 +126,7 @@ __device__ __forceinline__ void clip_f(const ShapeF& s, const float q[3], int k,
     else if (b < 0.f) *t0 = fmaxf(*t0, -a / b);
     else if (a > 0.f) { *t0 = FLT_MAX; *t1 = -FLT_MAX; }
   };
-  if (s.kind == KIND_SPHERE) {
+  if (SET != 2 && s.kind == KIND_SPHERE) {
     const float b = sgn * (k == 0 ? q[0] : (k == 1 ? q[1] : q[2]));
     const float c = fmaf(q[0], q[0], fmaf(q[1], q[1], q[2] * q[2])) - s.sz[0] * s.sz[0];
     const float disc = b * b - c;
@@ -132,11 +136,11 @@ __device__ __forceinline__ void clip_f(const ShapeF& s, const float q[3], int k,
     *t1 = -b + sq;
     return;
   }
-  if (s.kind == KIND_WALL) {
+  if (SET != 2 && s.kind == KIND_WALL) {
     plane(s.rt[0], s.rt[1], s.rt[2], -s.sz[0]);
     return;
   }
-  if (s.kind == KIND_CUBOID || s.kind == KIND_CUBE) {
+  if (SET != 0 || s.kind == KIND_CUBOID || s.kind == KIND_CUBE) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       plane(s.rt[3 * a], s.rt[3 * a + 1], s.rt[3 * a + 2], s.sz[a]);
@@ -218,7 +222,8 @@ __device__ __forceinline__ void zero_pair(const Lists& W, double* pair_out, int 
   if (lane < kTapeDoubles) W.tape[static_cast<size_t>(q) * kTapeDoubles + lane] = 0.0;
 }
 
-__global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S, Parts D, Lists W,
+template <int SET>
+__global__ void __launch_bounds__(kBoxWarps * 32, 2) k_box_pairs(Params P, Shapes S, Parts D, Lists W,
                                                               const double* __restrict__ vel,
                                                               double* __restrict__ pair_out) {
   __shared__ float4 s_pl[kBoxWarps][2][kMaxFaces];
@@ -250,7 +255,7 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
           qa[k] = static_cast<float>(c[k] - r.ai[k]) - r.af[k];
           qb[k] = B.kind == KIND_WALL ? static_cast<float>(c[k]) : static_cast<float>(c[k] - r.bi[k]) - r.bf[k];
         }
-        if (phi_f(A, qa, g) < srough && phi_f(B, qb, g) < srough)
+        if (phi_f<SET>(A, qa, g) < srough && phi_f<SET>(B, qb, g) < srough)
           for (int k = 0; k < 3; ++k) {
             mn[k] = min(mn[k], c[k]);
             mx[k] = max(mx[k], c[k]);
@@ -352,8 +357,8 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
           const float o2 = u == 2 ? ou : (v == 2 ? ov : 0.f);
           const float qa[3] = {ca[0] + o0, ca[1] + o1, ca[2] + o2}, qb[3] = {cb[0] + o0, cb[1] + o1, cb[2] + o2};
           float a0, a1, c0, c1;
-          clip_f(A, qa, k, sgn, &a0, &a1);
-          clip_f(B, qb, k, sgn, &c0, &c1);
+          clip_f<SET>(A, qa, k, sgn, &a0, &a1);
+          clip_f<SET>(B, qb, k, sgn, &c0, &c1);
           const float tin = fmaxf(fmaxf(a0, c0), 0.f);
           const float tout = fminf(fminf(a1, c1), lenl);
           if (tin <= tout && tin < best) { best = tin; bestl = l; }
@@ -432,7 +437,7 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
         qa[k] = fmaf(t[k], st[k], oA[k]);
         qb[k] = fmaf(t[k], st[k], oB[k]);
       }
-      const float fa = phi_f(A, qa, ga), fb = phi_f(B, qb, gb);
+      const float fa = phi_f<SET>(A, qa, ga), fb = phi_f<SET>(B, qb, gb);
       if (fmaxf(fa, fb) >= hw) continue;   // no weight and no band term
       const float ta = __saturatef(fmaf(fa, -inv_w, 0.5f)), tb = __saturatef(fmaf(fb, -inv_w, 0.5f));
       float w, ma, mb;
@@ -585,7 +590,13 @@ __global__ void __launch_bounds__(kBoxWarps * 32) k_box_pairs(Params P, Shapes S
 
 void launch_box(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel, double* pair_out,
                 int grid, cudaStream_t st) {
-  launch_pdl(k_box_pairs, dim3(grid), dim3(kBoxWarps * 32), 0, st, P, S, D, W, vel, pair_out);
+  // the node sweep's kind set: 2 cubes only, 1 spheres / cuboids / walls, 0 every kind
+  if (P.kind_set == 2)
+    launch_pdl(k_box_pairs<2>, dim3(grid), dim3(kBoxWarps * 32), 0, st, P, S, D, W, vel, pair_out);
+  else if (P.kind_set == 1)
+    launch_pdl(k_box_pairs<1>, dim3(grid), dim3(kBoxWarps * 32), 0, st, P, S, D, W, vel, pair_out);
+  else
+    launch_pdl(k_box_pairs<0>, dim3(grid), dim3(kBoxWarps * 32), 0, st, P, S, D, W, vel, pair_out);
 }
 
 }  // namespace gbc
