@@ -259,9 +259,12 @@ __device__ __forceinline__ void adj_load(const Shapes& S, const Parts& D, int pi
   g.sp = sm;
 }
 
-// phi (lattice units, inflate included), unit world gradient, |r| (spheres)
+// phi (lattice units, inflate included), unit world gradient, |r| (spheres).
+// SET is the context's kind set (2: cubes only, 1: spheres, cuboids and
+// walls, 0: every kind): the types a set cannot hold are compiled out.
+template <int SET>
 __device__ __forceinline__ float adj_eval(const AdjGeom& g, const float r[3], float gr[3], float* rn) {
-  if (g.type == 0) {
+  if (SET != 2 && g.type == 0) {
     const float q = fmaf(r[0], r[0], fmaf(r[1], r[1], r[2] * r[2]));
     const float nr = sqrtf(q);
     const float inv = nr > 0.f ? 1.f / nr : 0.f;
@@ -270,11 +273,11 @@ __device__ __forceinline__ float adj_eval(const AdjGeom& g, const float r[3], fl
     return nr - g.size[0];
   }
   *rn = 0.f;
-  if (g.type == 3) {   // wall
+  if (SET != 2 && g.type == 3) {   // wall
     for (int k = 0; k < 3; ++k) gr[k] = g.rt[k];
     return fmaf(g.rt[0], r[0], fmaf(g.rt[1], r[1], fmaf(g.rt[2], r[2], g.size[0])));
   }
-  if (g.type == 1) {
+  if (SET != 0 || g.type == 1) {
     float y[3], a[3];
     for (int k = 0; k < 3; ++k) {
       y[k] = fmaf(g.rt[3 * k], r[0], fmaf(g.rt[3 * k + 1], r[1], g.rt[3 * k + 2] * r[2]));
@@ -300,10 +303,11 @@ __device__ __forceinline__ float adj_eval(const AdjGeom& g, const float r[3], fl
 }
 
 // phi alone (the same arithmetic as adj_eval, without the gradient): the band test
+template <int SET>
 __device__ __forceinline__ float adj_phi(const AdjGeom& g, const float r[3]) {
-  if (g.type == 0) return sqrtf(fmaf(r[0], r[0], fmaf(r[1], r[1], r[2] * r[2]))) - g.size[0];
-  if (g.type == 3) return fmaf(g.rt[0], r[0], fmaf(g.rt[1], r[1], fmaf(g.rt[2], r[2], g.size[0])));
-  if (g.type == 1) {
+  if (SET != 2 && g.type == 0) return sqrtf(fmaf(r[0], r[0], fmaf(r[1], r[1], r[2] * r[2]))) - g.size[0];
+  if (SET != 2 && g.type == 3) return fmaf(g.rt[0], r[0], fmaf(g.rt[1], r[1], fmaf(g.rt[2], r[2], g.size[0])));
+  if (SET != 0 || g.type == 1) {
     float best = -FLT_MAX;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -434,6 +438,7 @@ __device__ __forceinline__ void adj_post_pass(const Params& P, const Shapes& S, 
   }
 }
 
+template <int SET>
 __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, Parts D, Lists W, AdjBufs B) {
   __shared__ float4 s_pl[kWarps][2][kMaxFaces];
   __shared__ AdjStage s_st[kWarps][kAdjStage];
@@ -509,9 +514,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
             rb[k] = static_cast<float>(c[k] - bi[k]) - bf[k];
           }
           // every term below needs both phi inside the upper half of the band
-          if (fmaxf(adj_phi(A, ra), adj_phi(Bg, rb)) >= hw) continue;
-          const float fa = adj_eval(A, ra, ga, &na);
-          const float fb = adj_eval(Bg, rb, gb, &nb);
+          if (fmaxf(adj_phi<SET>(A, ra), adj_phi<SET>(Bg, rb)) >= hw) continue;
+          const float fa = adj_eval<SET>(A, ra, ga, &na);
+          const float fb = adj_eval<SET>(Bg, rb, gb, &nb);
           const float ta = fminf(fmaxf(fmaf(fa, -inv_w, 0.5f), 0.f), 1.f);
           const float tb = fminf(fmaxf(fmaf(fb, -inv_w, 0.5f), 0.f), 1.f);
           const bool ina = ta > 0.f && ta < 1.f, inb = tb > 0.f && tb < 1.f;
@@ -537,7 +542,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
             acc[9 + k] += kb * xb[k];
           }
           const float wa = ha * Hb, wb = Ha * hb;
-          if (A.type == 0) {
+          if (SET != 2 && A.type == 0) {
             if (na > 0.f)
               for (int k = 0; k < 3; ++k) acc[k] -= wa * (sg[k] - gma * ga[k]) / na;
           } else {
@@ -545,7 +550,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
             cross3f(ga, sg, cr);
             for (int k = 0; k < 3; ++k) acc[3 + k] += wa * cr[k];
           }
-          if (Bg.type == 0) {
+          if (SET != 2 && Bg.type == 0) {
             if (nb > 0.f)
               for (int k = 0; k < 3; ++k) acc[6 + k] += wb * (sg[k] - gmb * gb[k]) / nb;
           } else {
@@ -685,11 +690,13 @@ void launch_adjoint(const Params& P, const Shapes& S, const Parts& D, const List
   const int wneed0 = (P.max_pairs + 31) / 32;
   const int wgrid0 = wneed0 < 8 * sms ? (wneed0 > 0 ? wneed0 : 1) : 8 * sms;
   launch_pdl(k_adj_pre, dim3(wgrid0), dim3(32), 0, st, P, S, D, W, B, vel, gF, gT);
+  // compiled per kind set, as the node sweep (2 cubes only, 1 spheres / cuboids / walls, 0 every kind)
+  auto cells = P.kind_set == 2 ? k_adj_cells<2> : (P.kind_set == 1 ? k_adj_cells<1> : k_adj_cells<0>);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_cells, kWarps * 32, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cells, kWarps * 32, 0);
   const int cgrid = (per_sm > 0 ? per_sm : 1) * sms;   // persistent: every resident slot pulls tiles
   (void)grid;
-  launch_pdl(k_adj_cells, dim3(cgrid), dim3(kWarps * 32), 0, st, P, S, D, W, B);
+  launch_pdl(cells, dim3(cgrid), dim3(kWarps * 32), 0, st, P, S, D, W, B);
   launch_pdl(k_adj_scatter, dim3((8 * P.n + 31) / 32), dim3(32), 0, st, P, D, W, B, gpos, gquat);
 }
 
