@@ -86,14 +86,17 @@ __device__ __forceinline__ double int_to_double(int v) {
   return __longlong_as_double(static_cast<long long>(sgn | (static_cast<unsigned long long>(1054 - lz) << 52) | frac));
 }
 
+// SET 2 (cubes only) compiles out every type but the cuboid (walls are
+// one-plane polytopes, so the other kind sets keep every branch).
+template <int SET>
 __device__ __forceinline__ double shape_value(int type, double prm0, double prmk, const double* planes, int nf, int k,
                                               const double r[3], const double y[3], double yk) {
-  if (type == 0) {   // sphere: |r| - radius (the same on the pair's lanes)
+  if (SET != 2 && type == 0) {   // sphere: |r| - radius (the same on the pair's lanes)
     const double rr = fma(r[2], r[2], fma(r[1], r[1], r[0] * r[0]));
     const double nr = __double_as_longlong(rr) > 0 ? rr * nr_rsqrt(rr) : 0.0;
     return nr - prm0;
   }
-  if (type == 1) return fabs(yk) - prmk;       // cuboid: this lane's face pair
+  if (SET == 2 || type == 1) return fabs(yk) - prmk;   // cuboid: this lane's face pair
   double best = -1e300;                          // polytope: faces k, k + 3, ... (loads 4 faces at a time)
   const double2* pl = reinterpret_cast<const double2*>(planes);
   for (int f0 = k; f0 < nf; f0 += 12) {
@@ -117,6 +120,10 @@ __device__ __forceinline__ double shape_value(int type, double prm0, double prmk
 constexpr int kForcePairsPerPass = 8;   // pairs one call handles (four lanes each)
 
 // The whole warp calls this for the n <= 8 pairs e[0..n) (shared memory).
+// SET: the context's kind set (as shape_value).  LAW: false when the step has
+// no contact history, no friction and no velocity-driven damping (the
+// relative-velocity, history and friction code is then compiled out).
+template <int SET, bool LAW>
 __device__ __forceinline__ void pair_force_law(ForceArgs a, const OvlRec* e, int n) {
   using namespace fl;
   const int lane = threadIdx.x & 31;
@@ -168,8 +175,8 @@ __device__ __forceinline__ void pair_force_law(ForceArgs a, const OvlRec* e, int
       yA[c] = __shfl_sync(kFull, yAk, b0 + c);
       yB[c] = __shfl_sync(kFull, yBk, b0 + c);
     }
-    double vA = k < 3 ? shape_value(ta, pa0, pak, a.planes + 4 * fa0, fa1 - fa0, kc, rA, yA, yAk) : -1e300;
-    double vB = k < 3 ? shape_value(tb, pb0, pbk, a.planes + 4 * fb0, fb1 - fb0, kc, rB, yB, yBk) : -1e300;
+    double vA = k < 3 ? shape_value<SET>(ta, pa0, pak, a.planes + 4 * fa0, fa1 - fa0, kc, rA, yA, yAk) : -1e300;
+    double vB = k < 3 ? shape_value<SET>(tb, pb0, pbk, a.planes + 4 * fb0, fb1 - fb0, kc, rB, yB, yBk) : -1e300;
     vA = dmax(vA, __shfl_xor_sync(kFull, vA, 1));
     vA = dmax(vA, __shfl_xor_sync(kFull, vA, 2));
     vB = dmax(vB, __shfl_xor_sync(kFull, vB, 1));
@@ -208,7 +215,7 @@ __device__ __forceinline__ void pair_force_law(ForceArgs a, const OvlRec* e, int
     // velocity of A relative to B at x_c, u_AB = (v_A + w_A x r_A) - (v_B + w_B x r_B),
     // and its normal part ddot_n (> 0 when approaching)
     double uabk = 0.0, ddot = 0.0;
-    if (a.vel != nullptr && (a.damping_c != 0.0 || a.history || a.friction)) {
+    if (LAW && a.vel != nullptr && (a.damping_c != 0.0 || a.history || a.friction)) {
       const double* va = a.vel + 6 * i;
       const double* vb = j < a.n ? a.vel + 6 * j : a.rest6;
       const double wak = fma(va[3 + k1], ra2v, -va[3 + k2] * ra1v);
@@ -221,7 +228,7 @@ __device__ __forceinline__ void pair_force_law(ForceArgs a, const OvlRec* e, int
     }
     // tangential part u_t = u_AB - ddot_n n, for the friction law
     double utk = 0.0, utn2 = 0.0;
-    if (a.friction && a.vel != nullptr) {
+    if (LAW && a.friction && a.vel != nullptr) {
       utk = fma(-ddot, nk, uabk);
       const double t2 = utk * utk;
       const double t0 = __shfl_sync(kFull, t2, b0), t1 = __shfl_sync(kFull, t2, b0 + 1),
@@ -232,14 +239,14 @@ __device__ __forceinline__ void pair_force_law(ForceArgs a, const OvlRec* e, int
     // c = damp_K / ddot_n) and of |u_t|^2 (lane 1)
     double inv_ddot = 0.0, inv_utn = 0.0;
     const bool dpos = __double_as_longlong(ddot) > 0, upos = __double_as_longlong(utn2) > 0;
-    if (a.history || a.friction) {
+    if (LAW && (a.history || a.friction)) {
       const double y5 = nr_rsqrt(k == 0 ? (dpos ? ddot : 1.0) : (upos ? utn2 : 1.0));
       const double ya = __shfl_sync(kFull, y5, b0), yb = __shfl_sync(kFull, y5, b0 + 1);
       inv_ddot = dpos ? ya * ya : 0.0;
       inv_utn = upos ? yb : 0.0;
     }
     double cdamp = a.damping_c;   // c of Eq. (damping_factor) for this pair
-    if (a.history) {
+    if (LAW && a.history) {
       // an ongoing contact (i, j) keeps its c; a new one takes c from u0 = ddot_n
       // (0 without velocities or for u0 <= 0).  Lane k of the pair checks the
       // entries k, k + 4, ... of i's list; the first 8 are loaded before the count.
@@ -269,10 +276,10 @@ __device__ __forceinline__ void pair_force_law(ForceArgs a, const OvlRec* e, int
       cdamp = src >= 0 ? ch : a.damp_K * inv_ddot;
     }
     double damp = 1.0;
-    if (a.vel != nullptr && cdamp != 0.0) damp = dmax(0.0, fma(cdamp, ddot, 1.0));
+    if (LAW && a.vel != nullptr && cdamp != 0.0) damp = dmax(0.0, fma(cdamp, ddot, 1.0));
     const double fmag = vok ? (4.0 / (3.0 * 3.14159265358979323846)) * estar * (vd * y3) * damp : 0.0;
     double Fk = fmag * nk;
-    if (a.friction && __double_as_longlong(fmag) > 0 && upos) {
+    if (LAW && a.friction && __double_as_longlong(fmag) > 0 && upos) {
       // Eq. (contact_force_tangential): B receives +f(a) |F_n| t, a = |u_t| / u_k,
       // f = (2 mu_s* - mu_k) a^2 / (a^4 + 1) + mu_k a^2 / (a^2 + 1)
       const double sa = utn2 * inv_utn * a.inv_u_k;
@@ -304,7 +311,7 @@ __device__ __forceinline__ void pair_force_law(ForceArgs a, const OvlRec* e, int
         tp[10] = estar; tp[11] = damp; tp[12] = fmag; tp[13] = int_to_double(idx);
         tp[14] = cdamp; tp[15] = 0.0;
       }
-      if (a.history && k == 0) {   // this step's contact list of i
+      if (LAW && a.history && k == 0) {   // this step's contact list of i
         const int slot = atomicAdd(a.hn_wr + i, 1);
         if (slot < a.hist_cap) {
           a.hj_wr[static_cast<size_t>(i) * a.hist_cap + slot] = j;

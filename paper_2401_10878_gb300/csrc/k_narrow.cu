@@ -543,6 +543,7 @@ __device__ __forceinline__ float reduce_tile(const Partial& o) {
 }
 
 // The force law of the n <= 8 overlapping pairs staged in ov (whole warp).
+template <int SET, bool LAW>
 __device__ __forceinline__ void flush_overlaps(const Params& P, const Shapes& S, const Parts& D, const Lists& W,
                                                const double* vel, double* pair_out, OvlRec* ov, int nov) {
   if (nov == 0) return;
@@ -566,7 +567,7 @@ __device__ __forceinline__ void flush_overlaps(const Params& P, const Shapes& S,
   } else {
     a.hn_rd = a.hj_rd = nullptr; a.hc_rd = nullptr; a.hn_wr = a.hj_wr = nullptr; a.hc_wr = nullptr;
   }
-  pair_force_law(a, ov, nov);
+  pair_force_law<SET, LAW>(a, ov, nov);
   __syncwarp();
 }
 
@@ -795,6 +796,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_narrow32(Params P, Shapes S,
 // The force law of the step's overlapping pairs (the overlap list), eight per
 // warp pass (four lanes each).  Batch b goes to block b mod grid, so the FP64
 // passes spread over the SMs instead of meeting at the sweep's tail.
+template <int SET, bool LAW>
 __global__ void __launch_bounds__(kWarps * 32) k_force(Params P, Shapes S, Parts D, Lists W, const double* vel,
                                                        double* pair_out) {
   __shared__ __align__(16) OvlRec s_ovl[kWarps][kForcePairsPerPass];
@@ -814,7 +816,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_force(Params P, Shapes S, Parts
       if (e < n * kPieces) dst[e] = src[e];
     }
     __syncwarp();
-    flush_overlaps(P, S, D, W, vel, pair_out, s_ovl[wid], n);
+    flush_overlaps<SET, LAW>(P, S, D, W, vel, pair_out, s_ovl[wid], n);
   }
 }
 
@@ -928,7 +930,12 @@ void launch_force(const Params& P, const Shapes& S, const Parts& D, const Lists&
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  launch_pdl(k_force, dim3(sms > 0 ? 2 * sms : 2), dim3(kWarps * 32), 0, st, P, S, D, W, vel, pair_out);
+  // compiled per kind set (cubes only, or any) and with or without the
+  // velocity-dependent law (damping from velocities, contact history, friction)
+  const bool law = P.history || P.friction || (vel != nullptr && P.damping_c != 0.0);
+  auto kern = P.kind_set == 2 ? (law ? k_force<2, true> : k_force<2, false>)
+                              : (law ? k_force<0, true> : k_force<0, false>);
+  launch_pdl(kern, dim3(sms > 0 ? 2 * sms : 2), dim3(kWarps * 32), 0, st, P, S, D, W, vel, pair_out);
 }
 
 void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel,
