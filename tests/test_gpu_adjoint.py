@@ -34,9 +34,11 @@ def _scale(gp, gq):
     return max(np.abs(gp).max(), np.abs(gq).max())
 
 
-@pytest.mark.parametrize("name", ["mixed27", "cubes1934"])
+@pytest.mark.parametrize("name", ["mixed27", "cubes1934", "mixed1934"])
 def test_adjoint_matches_oracle_gradient(name):
-    st = W.mixed_grid_27() if name == "mixed27" else W.settling_cubes_dense()
+    """mixed27: spheres and cubes; cubes1934: cubes only; mixed1934: spheres,
+    cubes and polytopes (every kind set of the adjoint's cell sweep)."""
+    st = {"mixed27": W.mixed_grid_27, "cubes1934": W.settling_cubes_dense, "mixed1934": W.mixed_settling}[name]()
     st.indicator, st.smooth_width = 1, 1.0
     gf, gt = W.loss_weights(st.n)
     gp, gq = _grad_gpu(st, gf, gt)
