@@ -372,6 +372,7 @@ def end_to_end(model, pos, quat, steps, warmup, dev):
     xq = torch.empty_like(hq[0]).pin_memory()
     tot, cells = 0.0, 0
     per_pose = {}
+    per = []
     for k in range(warmup + steps):
         idx = k % hp.shape[0]
         xp.copy_(hp[idx])   # the caller fills its buffers (not timed)
@@ -384,9 +385,12 @@ def end_to_end(model, pos, quat, steps, warmup, dev):
         if k >= warmup:
             tot += t1 - t0
             cells += per_pose[idx]
+            per.append(t1 - t0)
     n = model.n
     return {"value": cells / tot, "unit": UNIT, "h2d_bytes_per_step": n * 7 * 8,
             "d2h_bytes_per_step": n * 6 * 8 + 4, "ms_per_step": 1e3 * tot / steps,
+            "ms_per_step_median": 1e3 * float(np.median(per)),
+            "ms_per_step_p10_p90": [1e3 * float(np.percentile(per, 10)), 1e3 * float(np.percentile(per, 90))],
             "timing": "wall clock around contact_step_host (pinned host buffers read and written by the step's "
                       "kernels inside the call)"}
 
