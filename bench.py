@@ -333,6 +333,15 @@ def run_ours(args, ws, rank, local):
                 "frac_at_median_clock": (achieved / (sms * FP32_LANES_PER_SM * med * 1e6 / 1e12)) if med else None,
                 "cell_evals_per_s_kernel": (tres["cells"] / nsteps) / narrow_avg_s,
                 "timing": f"CUDA events around the node-sweep launch, {nsteps} steps of the same workload"}
+    # the derived peak checked against this GPU's measured FFMA rate
+    try:
+        from paper_2401_10878_gb300.contact import fp32_ffma_rate
+        ffma = fp32_ffma_rate() / 1e12
+        roofline["peak_ffma_measured"] = ffma
+        roofline["frac_of_measured_ffma"] = achieved / ffma
+    except Exception as e:   # a measurement aid only: the line stands without it
+        roofline["peak_ffma_measured"] = None
+        roofline["peak_ffma_error"] = str(e)[:200]
 
     # end to end through the public API with host buffers
     e2e = end_to_end(model, pos, quat, args.steps, args.warmup, dev)

@@ -335,6 +335,18 @@ contact_status contact_step_noalloc(const contact_config* cfg, const int32_t* sh
                                     const double* quat, int32_t* pair_ij, double* pair_out, int32_t* n_pairs,
                                     double* force, double* torque, void* stream);
 
+/* Measurement utility (no counterpart in the paper): the FP32 FFMA rate of
+ * the current device, the measured counterpart of the node sweep's roofline
+ * peak (SMs x 128 FP32 lanes x clock).  One warm-up and one timed launch of
+ * eight independent FFMA chains per thread, iters x 128 FFMAs each, on eight
+ * 256-thread blocks per SM (~1 ms at iters = 2000); synchronous, on the
+ * default stream, with its own 1.2 MB scratch allocation.
+ *   iters        1 .. 2^20
+ *   ffma_per_s   host out: FFMA lane-operations per second
+ * CONTACT_EINVAL for a bad argument, CONTACT_ENOMEM / CONTACT_ECUDA on a CUDA
+ * failure. */
+contact_status contact_fp32_ffma_rate(int32_t iters, double* ffma_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcontact.so")
-SOURCES = ["host.cu", "k_broad.cu", "k_narrow.cu", "k_boxmode.cu", "k_post.cu", "k_adjoint.cu", "noalloc.cu"]
+SOURCES = ["host.cu", "k_broad.cu", "k_narrow.cu", "k_boxmode.cu", "k_post.cu", "k_adjoint.cu", "noalloc.cu",
+           "k_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -32,7 +32,7 @@ EXPORTS = ["contact_config_default", "contact_init", "contact_step", "contact_ba
            "contact_particle_boxes", "contact_narrow_time", "contact_damping_factor", "contact_kernels_per_step",
            "contact_kernels_per_backward", "contact_destroy", "contact_step_noalloc", "contact_step_host",
            "contact_history_get", "contact_history_set", "contact_history_reset", "contact_polytope_centroid",
-           "contact_polytope_shift"]
+           "contact_polytope_shift", "contact_fp32_ffma_rate"]
 
 
 class Config(ctypes.Structure):
@@ -111,6 +111,8 @@ def load_library(build_if_missing: bool = True):
     lib.contact_polytope_centroid.restype = I32
     lib.contact_polytope_shift.argtypes = [P, P]
     lib.contact_polytope_shift.restype = I32
+    lib.contact_fp32_ffma_rate.argtypes = [I32, P]
+    lib.contact_fp32_ffma_rate.restype = I32
     lib.contact_history_get.argtypes = [P, ctypes.c_int64, P, P, P, P]
     lib.contact_history_get.restype = I32
     lib.contact_history_set.argtypes = [P, ctypes.c_int64, P, P, P]
@@ -465,3 +467,14 @@ def contact_forces(model: Contact, pos: torch.Tensor, quat: torch.Tensor, vel: t
     if pairs:
         return force, torque, dict(pair_ij=pij, pair_out=pout)
     return force, torque
+
+
+def fp32_ffma_rate(iters: int = 2000) -> float:
+    """Measured FP32 FFMA lane-operations per second of the current device
+    (contact_fp32_ffma_rate): the counterpart of the roofline's derived peak."""
+    lib = load_library()
+    out = ctypes.c_double()
+    rc = lib.contact_fp32_ffma_rate(int(iters), ctypes.byref(out))
+    if rc != OK:
+        raise ContactError(rc, "contact_fp32_ffma_rate")
+    return out.value

@@ -15,7 +15,7 @@ HEADER = os.path.join(os.path.dirname(__file__), "..", "include", "contact.h")
 def declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(contact_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(contact_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declarations_match_binding():

@@ -338,6 +338,17 @@ def test_step_host_mapped_buffers_with_velocities():
     m.close()
 
 
+def test_fp32_ffma_rate_against_the_derived_peak():
+    """The measured FFMA rate lies between half and 105 % of SMs x 128 lanes x
+    the maximum SM clock (the node sweep's roofline peak)."""
+    from paper_2401_10878_gb300.contact import fp32_ffma_rate
+    props = torch.cuda.get_device_properties(0)
+    rate = fp32_ffma_rate()
+    derived = props.multi_processor_count * 128 * 2070e6
+    print("FFMA rate", rate / 1e12, "T/s; derived peak at 2070 MHz", derived / 1e12)
+    assert 0.5 * derived <= rate <= 1.05 * derived
+
+
 def test_user_stream_capture():
     st = W.mixed_grid_27()
     m = model_for(st, use_graph=False)
