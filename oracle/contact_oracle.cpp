@@ -27,7 +27,12 @@
 //   max over face planes; smoothed indicator H_w(phi) = S(clamp(1/2 - phi/(w dx),0,1)),
 //   S(t) = 3t^2 - 2t^3; contact normal from G = 1/2 (dV/dX_A - dV/dX_B) in its
 //   band form; indentation depth d = max over overlap nodes of (-phi_A - phi_B);
-//   prefactor 4/(3 pi) as printed; one damping factor c for all contacts.
+//   prefactor 4/(3 pi) as printed; one damping factor c for all contacts, or
+//   with the contact history each contact's own (from its first step's
+//   approach speed) and, in the box pipeline, its last corrected box (relative
+//   to X_i, widened by sqrt(0.75) dx) as the warm start that cuts the next
+//   correction's starting box down (Sec. 4.3.3); a polytope whose volume
+//   centroid is off its body origin is moved there (Sec. 2.2).
 //
 // The per-pair evaluation is a template over the scalar type so that the same
 // code, run with forward-mode dual numbers, yields the oracle's own FP64
