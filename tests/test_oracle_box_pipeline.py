@@ -211,15 +211,17 @@ def test_stored_box_bounds_the_correction():
     assert np.array_equal(rf.pair_out, r0.pair_out) and np.array_equal(rf.hist_box, r0.hist_box)
 
 
-def test_warm_start_follows_particle_i_across_the_periodic_boundary():
+@pytest.mark.parametrize("offset, t, who", [(0.6875, 33.0, 0), (0.1875, 24.0, 1)])
+def test_warm_start_follows_particle_i_across_the_periodic_boundary(offset, t, who):
     """Two steps (both spheres moved by 1/8 along x in between) of the lens and
-    of the same lens translated by 33 nodes, where particle i crosses the
-    boundary at the second step: the same outputs and stored boxes (to
-    rounding), and the second step differs from a cold one."""
+    of the same lens translated by t nodes, where particle i (who = 0) or its
+    partner j (who = 1, so the pair's image changes) crosses the boundary at
+    the second step: the same outputs and stored boxes (to rounding), and the
+    second step differs from a cold one."""
     runs = []
-    for t in (0.0, 33.0):
+    for shift in (0.0, t):
         st, XA = _lens_state()
-        pos1 = st.pos + [t + 0.6875, 0.0, 0.0]
+        pos1 = st.pos + [shift + offset, 0.0, 0.0]
         pos2 = pos1 + [0.125, 0.0, 0.0]
         L = st.n_cells[0] * st.dx
         pos1[:, 0] = np.mod(pos1[:, 0], L)
@@ -229,7 +231,8 @@ def test_warm_start_follows_particle_i_across_the_periodic_boundary():
         cold = oracle.contact_step_ext(st, LAW_H, pos=pos2)
         runs.append((pos1, pos2, r2, cold))
     (p1a, p2a, ra, ca), (p1b, p2b, rb, cb) = runs
-    assert p1b[0, 0] > 63.0 and p2b[0, 0] < 1.0   # particle i wrapped
+    assert p1b[who, 0] > 63.0 and p2b[who, 0] < 1.0   # the particle wrapped
+    assert p1a[:, 0].max() < 63.0 and p2a[:, 0].max() < 63.0
     for k in (0, 4, 5, 6, 7, 8, 9, 10):
         assert ra.pair_out[0, k] == pytest.approx(rb.pair_out[0, k], rel=1e-11, abs=1e-12)
     assert np.allclose(ra.hist_box, rb.hist_box, rtol=0, atol=1e-11)
