@@ -60,41 +60,46 @@ def _load():
     global _lib
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_LIB)
-        P = ctypes.c_void_p
-        lib.oracle_contact_step.restype = ctypes.c_int64
-        lib.oracle_contact_step.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 9 + \
-            [ctypes.c_int64] + [P] * 7 + [ctypes.c_int64, P, P, ctypes.c_int32]
-        lib.oracle_contact_step_ext.restype = ctypes.c_int64
-        lib.oracle_contact_step_ext.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Law), ctypes.c_int32] + \
-            [P] * 9 + [ctypes.c_int64] + [P] * 5 + [ctypes.c_int64, P, P, P, ctypes.c_int64, P, P, P, P, ctypes.c_int32]
-        lib.oracle_gradient_ext.restype = ctypes.c_int64
-        lib.oracle_gradient_ext.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Law), ctypes.c_int32] + \
-            [P] * 9 + [ctypes.c_int64] + [P] * 6 + [ctypes.c_int32]
-        lib.oracle_box_pipeline.restype = ctypes.c_int64
-        lib.oracle_box_pipeline.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 8 + \
-            [ctypes.c_int64, P, P, ctypes.c_int64] + [P] * 3
-        lib.oracle_polytope_centroid.restype = ctypes.c_int32
-        lib.oracle_polytope_centroid.argtypes = [P, ctypes.c_int32, P]
-        lib.oracle_gradient.restype = ctypes.c_int64
-        lib.oracle_gradient.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 13 + [ctypes.c_int32]
-        lib.oracle_polytope_shift.restype = ctypes.c_int32
-        lib.oracle_polytope_shift.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 9
-        lib.oracle_aabb.restype = ctypes.c_int32
-        lib.oracle_aabb.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 9
-        lib.oracle_rotation.restype = None
-        lib.oracle_rotation.argtypes = [P, P]
-        lib.oracle_effective_modulus.restype = ctypes.c_double
-        lib.oracle_effective_modulus.argtypes = [ctypes.c_double] * 4
-        lib.oracle_damping_factor.restype = ctypes.c_double
-        lib.oracle_damping_factor.argtypes = [ctypes.c_double] * 2
-        lib.oracle_normal_force.restype = ctypes.c_double
-        lib.oracle_normal_force.argtypes = [ctypes.c_double] * 5
-        lib.oracle_polytope_vertices.restype = ctypes.c_int32
-        lib.oracle_polytope_vertices.argtypes = [ctypes.c_int32, P, ctypes.c_double, ctypes.c_int32, P]
-        lib.oracle_max_threads.restype = ctypes.c_int32
-        _lib = lib
+        _lib = _configure(ctypes.CDLL(_LIB))
     return _lib
+
+
+def _configure(lib):
+    """Argument and return types of the oracle's C entry points on a loaded
+    library (the tests that plant mistakes configure their variants with it)."""
+    P = ctypes.c_void_p
+    lib.oracle_contact_step.restype = ctypes.c_int64
+    lib.oracle_contact_step.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 9 + \
+        [ctypes.c_int64] + [P] * 7 + [ctypes.c_int64, P, P, ctypes.c_int32]
+    lib.oracle_contact_step_ext.restype = ctypes.c_int64
+    lib.oracle_contact_step_ext.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Law), ctypes.c_int32] + \
+        [P] * 9 + [ctypes.c_int64] + [P] * 5 + [ctypes.c_int64, P, P, P, ctypes.c_int64, P, P, P, P, ctypes.c_int32]
+    lib.oracle_gradient_ext.restype = ctypes.c_int64
+    lib.oracle_gradient_ext.argtypes = [ctypes.POINTER(_Cfg), ctypes.POINTER(_Law), ctypes.c_int32] + \
+        [P] * 9 + [ctypes.c_int64] + [P] * 6 + [ctypes.c_int32]
+    lib.oracle_box_pipeline.restype = ctypes.c_int64
+    lib.oracle_box_pipeline.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 8 + \
+        [ctypes.c_int64, P, P, ctypes.c_int64] + [P] * 3
+    lib.oracle_polytope_centroid.restype = ctypes.c_int32
+    lib.oracle_polytope_centroid.argtypes = [P, ctypes.c_int32, P]
+    lib.oracle_gradient.restype = ctypes.c_int64
+    lib.oracle_gradient.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 13 + [ctypes.c_int32]
+    lib.oracle_polytope_shift.restype = ctypes.c_int32
+    lib.oracle_polytope_shift.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 9
+    lib.oracle_aabb.restype = ctypes.c_int32
+    lib.oracle_aabb.argtypes = [ctypes.POINTER(_Cfg), ctypes.c_int32] + [P] * 9
+    lib.oracle_rotation.restype = None
+    lib.oracle_rotation.argtypes = [P, P]
+    lib.oracle_effective_modulus.restype = ctypes.c_double
+    lib.oracle_effective_modulus.argtypes = [ctypes.c_double] * 4
+    lib.oracle_damping_factor.restype = ctypes.c_double
+    lib.oracle_damping_factor.argtypes = [ctypes.c_double] * 2
+    lib.oracle_normal_force.restype = ctypes.c_double
+    lib.oracle_normal_force.argtypes = [ctypes.c_double] * 5
+    lib.oracle_polytope_vertices.restype = ctypes.c_int32
+    lib.oracle_polytope_vertices.argtypes = [ctypes.c_int32, P, ctypes.c_double, ctypes.c_int32, P]
+    lib.oracle_max_threads.restype = ctypes.c_int32
+    return lib
 
 
 def _ptr(a):

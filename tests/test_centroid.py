@@ -43,9 +43,11 @@ def test_tetrahedron_centroid_is_the_vertex_mean():
 
 
 def test_pyramid_centroid_at_a_quarter_height():
-    """Square pyramid, base z = -1 (side 2), apex z = 3: centroid at z = 0."""
-    v = np.array([[-1, -1, -1], [1, -1, -1], [1, 1, -1], [-1, 1, -1], [0, 0, 3.0]])
-    assert np.allclose(oracle.polytope_centroid(planes_from_vertices(v)), 0.0, atol=1e-13)
+    """Square pyramid, base z = -0.6 (side 2), apex z = 3.4: the centroid a
+    quarter of the height above the base, z = 0.4 (off the origin, so a wrong
+    weight of the face pyramids shows)."""
+    v = np.array([[-1, -1, -0.6], [1, -1, -0.6], [1, 1, -0.6], [-1, 1, -0.6], [0, 0, 3.4]])
+    assert np.allclose(oracle.polytope_centroid(planes_from_vertices(v)), [0.0, 0.0, 0.4], atol=1e-13)
 
 
 def test_library_centroid_matches_oracle():

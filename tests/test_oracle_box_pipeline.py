@@ -204,6 +204,8 @@ def test_stored_box_bounds_the_correction():
     s = math.sqrt(0.75)
     b = r.hist_box[0] + np.tile(XA, 2)
     assert np.all(b[:3] >= c - 0.3 - s - 1e-12) and np.all(b[3:] <= c + 0.3 + s + 1e-12)
+    # across the lens (which reaches far past it) the stored box is widened by s
+    assert np.all(b[1:3] <= c[1:3] - 0.3 - 0.5 * s) and np.all(b[4:6] >= c[1:3] + 0.3 + 0.5 * s)
     cold = r0.hist_box[0] + np.tile(XA, 2)
     assert np.all(b[1:3] > cold[1:3]) and np.all(b[4:6] < cold[4:6])   # cut across the lens (y, z)
     far = rel + 40.0

@@ -45,6 +45,19 @@ def test_no_extension_matches_base_step():
     assert np.array_equal(a.pair_out, b.pair_out) and np.array_equal(a.force, b.force)
 
 
+def test_shared_damping_clamped_when_separating_fast():
+    """Eq. (contact_force_normal) with (1 + c ddot_n) below zero (A leaving B
+    faster than 1/c) gives no force at all, not an attraction; at half the
+    threshold speed the force is half the undamped one."""
+    st = pair()
+    st.damping_c = 0.5
+    r0 = oracle.contact_step(st)
+    fast = oracle.contact_step(st, vel=vel(uA=(-3.0, 0, 0)))   # 1 + 0.5 (-3) < 0
+    half = oracle.contact_step(st, vel=vel(uA=(-1.0, 0, 0)))   # 1 + 0.5 (-1) = 0.5
+    assert fast.pair_out[0, 0] > 0 and np.all(fast.pair_out[0, 8:11] == 0.0)
+    assert half.pair_out[0, 8] == pytest.approx(0.5 * r0.pair_out[0, 8], rel=1e-14)
+
+
 def test_friction_kinetic_limit():
     """|u_t| >> u_k: the friction coefficient tends to mu_k."""
     r = oracle.contact_step_ext(pair(), friction(u_k=1e-3), vel=vel(uA=(0, 1e3, 0)))   # a = 1e6

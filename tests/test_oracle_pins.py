@@ -152,6 +152,16 @@ def test_lens_worked_example_force_and_depth():
     assert np.allclose(r.pair_out[0, 4:7], [1, 0, 0], atol=1e-14)
 
 
+def test_depth_of_a_deep_sphere_pair():
+    """Spheres r1 = 6, r2 = 4 with centres 3 apart on a lattice line: on the
+    segment between the centres -phi_A - phi_B = r1 + r2 - D = 7, its maximum,
+    so d = 7 (one body's depth alone would give 6)."""
+    XA = np.array([30.0, 31.0, 29.0])
+    st = state([0, 0], [[6, 0, 0], [4, 0, 0]], [XA, XA + [3.0, 0.0, 0.0]])
+    r = oracle.contact_step(st)
+    assert r.n_pairs == 1 and r.pair_out[0, 7] == pytest.approx(7.0, abs=1e-12)
+
+
 def test_lens_centroid_and_normal():
     """Contact point -> volume-weighted mean of the two cap centroids on the centre line."""
     r1, r2, D = 7.5, 6.0, 10.0
@@ -390,6 +400,24 @@ def test_smoothed_indicator_limits():
         a = oracle.contact_step(_sphere_pair(7.5, 6.0, c, c + [10.0 + e, 0.3, 0.1], indicator=1))
         vs.append(a.pair_out[0, 0])
     assert abs(vs[1] - vs[0]) < 1e-5 and abs(vs[2] - vs[1]) < 1e-5 and vs[0] != vs[1]
+
+
+def test_smoothed_band_weights_of_mirrored_faces_sum_to_sharp():
+    """S(t) + S(1 - t) = 1: a box whose only face inside the band sits at
+    offset delta or 1 - delta from a node row (its other faces on half-integer
+    nodes, where w = 1 leaves no node in the band), inside a large box, has
+    smoothed volumes that add up to the two sharp volumes exactly."""
+    def vol(delta, indicator):
+        lo_x, hi_x = 20.5, 30.0 + delta
+        A = [(hi_x - lo_x) / 2, 4.0, 4.0]
+        XA = [(hi_x + lo_x) / 2, 30.5, 30.5]
+        st = state([1, 1], [A, [8.0, 8.0, 8.0]], [XA, [25.5, 30.5, 30.5]], indicator=indicator, w=1.0)
+        return oracle.contact_step(st).pair_out[0, 0]
+    for delta in (0.2, 0.35):
+        smooth = vol(delta, 1) + vol(1 - delta, 1)
+        sharp = vol(delta, 0) + vol(1 - delta, 0)
+        assert smooth == pytest.approx(sharp, rel=1e-13), (delta, smooth, sharp)
+        assert vol(delta, 1) != vol(delta, 0)   # the face's band node is weighted
 
 
 # ---------------------------------------------------------------- gradient

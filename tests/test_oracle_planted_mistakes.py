@@ -1,0 +1,99 @@
+"""The pins catch plausible mistakes: each case compiles the oracle with one
+mistake planted in its source (a dropped term, a wrong sign or factor, a
+transposed index, a wrong rounding rule), swaps it in for the oracle, and
+requires the pin that guards that step to fail.  CPU only; the mistakes live
+in temporary copies, never in the oracle itself."""
+import concurrent.futures
+import ctypes
+import os
+import shutil
+import subprocess
+
+import pytest
+
+import oracle
+from tests import test_centroid as TC
+from tests import test_oracle_box_pipeline as TB
+from tests import test_oracle_contact_law as TL
+from tests import test_oracle_pins as TP
+from tests import test_oracle_walls as TW
+
+# (name, text in the oracle, planted replacement, pin that must fail)
+CASES = [
+    ("centroid pyramid factor", "mom[k] += vf * 0.75 * (ac[k] / area);", "mom[k] += vf * 0.70 * (ac[k] / area);",
+     TC.test_pyramid_centroid_at_a_quarter_height),
+    ("force prefactor", "if (val(vd) > 0.0) fmag = (4.0 / (3.0 * M_PI)) * estar * sqrt_s(vd) * damp;",
+     "if (val(vd) > 0.0) fmag = (4.0 / (3.0 * std::sqrt(M_PI))) * estar * sqrt_s(vd) * damp;",
+     TP.test_lens_worked_example_force_and_depth),
+    ("normal: sign of A's band term", "SG[k] = SG[k] + (-(HpA * HB)) * gA[k] + (HA * HpB) * gB[k];",
+     "SG[k] = SG[k] + (HpA * HB) * gA[k] + (HA * HpB) * gB[k];", TP.test_swap_labels_flips_normal_and_force),
+    ("first moments: transposed index", "SM[k] = SM[k] + W * c[k];", "SM[k] = SM[k] + W * c[(k + 1) % 3];",
+     TP.test_lens_centroid_and_normal),
+    ("depth: dropped term", "S f = -phA - phB;", "S f = -phA;", TP.test_depth_of_a_deep_sphere_pair),
+    ("effective modulus: nu not squared", "return 1.0 / ((1.0 - nuA * nuA) / EA + (1.0 - nuB * nuB) / EB);",
+     "return 1.0 / ((1.0 - nuA) / EA + (1.0 - nuB) / EB);", TP.test_effective_modulus_special_cases),
+    ("periodic image: floor for round", "std::nearbyint((pos[3 * j + k] - pos[3 * i + k]) / L)",
+     "std::floor((pos[3 * j + k] - pos[3 * i + k]) / L)", TP.test_periodic_pairs_across_faces_edges_corners),
+    ("warm start: box not relative to X_i",
+     "const double wl = (XA[a] + warm[a]) - srough, wh = (XA[a] + warm[3 + a]) + srough;",
+     "const double wl = warm[a] - srough, wh = warm[3 + a] + srough;",
+     lambda: TB.test_warm_start_follows_particle_i_across_the_periodic_boundary(0.6875, 33.0, 0)),
+    ("warm start: no widening",
+     "const double wl = (XA[a] + warm[a]) - srough, wh = (XA[a] + warm[3 + a]) + srough;",
+     "const double wl = (XA[a] + warm[a]), wh = (XA[a] + warm[3 + a]);",
+     TB.test_stored_box_bounds_the_correction),
+    ("rotation: sign of w z in R[0][1]", "R[1] = s * (x * y - w * z);", "R[1] = s * (x * y + w * z);",
+     TP.test_rotation_known_quaternions),
+    ("smoothed indicator: wrong smoothstep", "if (smooth) *H = t * t * (3.0 - 2.0 * t);",
+     "if (smooth) *H = t * (3.0 - 2.0 * t);", TP.test_smoothed_band_weights_of_mirrored_faces_sum_to_sharp),
+    ("damping: no clamp at zero", "if (val(damp) < 0.0) damp = S(0.0);", "",
+     TL.test_shared_damping_clamped_when_separating_fast),
+    ("friction: wrong direction", "res.F[k] = res.F[k] + coef * fmag * ut[k] / utn;",
+     "res.F[k] = res.F[k] - coef * fmag * ut[k] / utn;", TL.test_friction_opposes_sliding_and_dissipates),
+    ("history: c of an ongoing contact dropped", "        law.c = hist_c[row];", "        law.c = 0.0;",
+     TL.test_history_keeps_c_until_the_contact_ends),
+    ("box correction skipped", "shift[k][side] = std::isfinite(best) ? best : 0.0;", "shift[k][side] = 0.0;",
+     TB.test_face_aligned_boxes_exact),
+    ("wall: half-space inverted", "return S(((e[0] * x[0] + e[1] * x[1]) + e[2] * x[2]) - e[3] - inflate);",
+     "return S(e[3] - ((e[0] * x[0] + e[1] * x[1]) + e[2] * x[2]) - inflate);",
+     lambda: TW.test_face_aligned_cube_on_floor_exact(17.5, 1)),
+]
+
+
+def _compile(i, old, new, tmp):
+    src = open(oracle._SRC).read()
+    assert src.count(old) == 1, f"planted text not unique or missing: {old}"
+    path = os.path.join(tmp, f"planted_{i}.cpp")
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    so = os.path.join(tmp, f"planted_{i}.so")
+    subprocess.run(["g++", "-O1", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", path, "-o", so],
+                   check=True, capture_output=True)
+    return so
+
+
+@pytest.fixture(scope="module")
+def planted_libs(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("no g++")
+    tmp = str(tmp_path_factory.mktemp("planted"))
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        futs = [ex.submit(_compile, i, old, new, tmp) for i, (_, old, new, _) in enumerate(CASES)]
+        return [f.result() for f in futs]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)), ids=[c[0] for c in CASES])
+def test_pin_catches_planted_mistake(case, planted_libs):
+    name, _, _, pin = CASES[case]
+    saved = oracle._lib
+    oracle._lib = oracle._configure(ctypes.CDLL(planted_libs[case]))
+    try:
+        with pytest.raises(Exception):   # an assertion, or an index or oracle error from missing pairs
+            pin()
+    finally:
+        oracle._lib = saved
+
+
+def test_unplanted_oracle_passes_the_same_pins():
+    for _, _, _, pin in CASES:
+        pin()
