@@ -57,6 +57,14 @@ CASES = [
     ("wall: half-space inverted", "return S(((e[0] * x[0] + e[1] * x[1]) + e[2] * x[2]) - e[3] - inflate);",
      "return S(e[3] - ((e[0] * x[0] + e[1] * x[1]) + e[2] * x[2]) - inflate);",
      lambda: TW.test_face_aligned_cube_on_floor_exact(17.5, 1)),
+    ("rough detection: half the cell for the half diagonal", "const double srough = std::sqrt(0.75) * dx;",
+     "const double srough = 0.5 * dx;", TB.test_rough_box_equals_brute_force_scan),
+    ("quaternion not normalised", "const S s = 2.0 / nn;", "const S s = 2.0;",
+     TP.test_rotation_orthonormal_and_scale_free),
+    ("dual numbers: derivative of the square root", "r.g[i] = (r.v > 0.0) ? a.g[i] / (2.0 * r.v) : 0.0;",
+     "r.g[i] = (r.v > 0.0) ? a.g[i] / r.v : 0.0;", TP.test_dual_gradient_matches_central_differences),
+    ("wall candidate test too strict", "if (!(((t[0] + t[1]) + t[2]) <= H)) return false;",
+     "if (!(((t[0] + t[1]) + t[2]) <= H - 1.0)) return false;", TW.test_brute_force_scan_near_oblique_walls),
 ]
 
 

@@ -123,6 +123,23 @@ def test_brute_force_scan_near_oblique_walls():
             hits += 1
             assert np.allclose(r.pair_out[rows[0], 1:4], k[inside].mean(axis=0), atol=1e-12)
     assert hits >= 6
+    # grazing: axis-aligned walls entering a sphere by 0.9 cells, where the
+    # candidate test decides near its threshold
+    grazing = 0
+    for trial in range(6):
+        X = np.array([30.0, 31.0, 32.0]) + rng.random(3)
+        m = np.zeros(3)
+        m[trial % 3] = 1.0 if trial < 3 else -1.0
+        h = float(m @ X) - 5.5 + 0.9
+        st = with_walls(state([0], [[5.5, 0, 0]], [X]), [[*m, h]])
+        r = oracle.contact_step(st)
+        rows = wall_rows(r, 1)
+        k = np.stack(np.meshgrid(*[np.arange(16, 48)] * 3, indexing="ij"), -1).reshape(-1, 3).astype(float)
+        inside = (np.linalg.norm(k - X, axis=1) - 5.5 <= 0) & (k @ m - h <= 0)
+        V = r.pair_out[rows[0], 0] if len(rows) else 0.0
+        assert V == inside.sum(), (trial, V, inside.sum())
+        grazing += inside.sum() > 0
+    assert grazing >= 4
 
 
 def test_integer_translation_of_particle_and_wall():
