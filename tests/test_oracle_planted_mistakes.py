@@ -65,6 +65,12 @@ CASES = [
      "r.g[i] = (r.v > 0.0) ? a.g[i] / r.v : 0.0;", TP.test_dual_gradient_matches_central_differences),
     ("wall candidate test too strict", "if (!(((t[0] + t[1]) + t[2]) <= H)) return false;",
      "if (!(((t[0] + t[1]) + t[2]) <= H - 1.0)) return false;", TW.test_brute_force_scan_near_oblique_walls),
+    ("box correction: sphere entry point", "*t0 = -b - sq;", "*t0 = -b;",
+     lambda: TB.test_sphere_lens_box_inside_and_volume(8)),
+    ("friction: mu_s* coefficient", "law.mu_s * (1.0 - 0.09 * ratio * ratio * ratio * ratio);",
+     "law.mu_s * (1.0 - 0.9 * ratio * ratio * ratio * ratio);", TL.test_friction_worked_values),
+    ("box pipeline: samples at cell corners", "s_lo[k] += 0.5 * s_step[k];   // cell centres",
+     "s_lo[k] += 0.0 * s_step[k];", TB.test_face_aligned_boxes_exact),
 ]
 
 
