@@ -71,6 +71,15 @@ CASES = [
      "law.mu_s * (1.0 - 0.9 * ratio * ratio * ratio * ratio);", TL.test_friction_worked_values),
     ("box pipeline: samples at cell corners", "s_lo[k] += 0.5 * s_step[k];   // cell centres",
      "s_lo[k] += 0.0 * s_step[k];", TB.test_face_aligned_boxes_exact),
+    ("contact point: box origin dropped", "res.xc[k] = o[k] + (dx3 * SM[k]) / V;", "res.xc[k] = (dx3 * SM[k]) / V;",
+     TP.test_contact_point_inside_both_shapes),
+    ("torque on A: one component's sign", "res.TA[2] = ra[0] * FA[1] - ra[1] * FA[0];",
+     "res.TA[2] = ra[1] * FA[0] - ra[0] * FA[1];", TP.test_momentum_balance),
+    ("torque on B: lever arm from A's centre",
+     "centre of mass (Sec. 2.2)\n  S ra[3] = {res.xc[0] - XA[0], res.xc[1] - XA[1], res.xc[2] - XA[2]};\n"
+     "  S rb[3] = {res.xc[0] - XB[0], res.xc[1] - XB[1], res.xc[2] - XB[2]};",
+     "centre of mass (Sec. 2.2)\n  S ra[3] = {res.xc[0] - XA[0], res.xc[1] - XA[1], res.xc[2] - XA[2]};\n"
+     "  S rb[3] = {res.xc[0] - XA[0], res.xc[1] - XA[1], res.xc[2] - XA[2]};", TP.test_momentum_balance),
 ]
 
 
