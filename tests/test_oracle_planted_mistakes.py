@@ -15,6 +15,7 @@ import oracle
 from tests import test_centroid as TC
 from tests import test_oracle_box_pipeline as TB
 from tests import test_oracle_contact_law as TL
+from tests import test_oracle_diagnostics as TD
 from tests import test_oracle_pins as TP
 from tests import test_oracle_walls as TW
 
@@ -80,6 +81,26 @@ CASES = [
      "  S rb[3] = {res.xc[0] - XB[0], res.xc[1] - XB[1], res.xc[2] - XB[2]};",
      "centre of mass (Sec. 2.2)\n  S ra[3] = {res.xc[0] - XA[0], res.xc[1] - XA[1], res.xc[2] - XA[2]};\n"
      "  S rb[3] = {res.xc[0] - XA[0], res.xc[1] - XA[1], res.xc[2] - XA[2]};", TP.test_momentum_balance),
+    # the parity checks' diagnostics
+    ("band count: eps band ten times too wide", "const bool loose = pa <= eps && pb <= eps;",
+     "const bool loose = pa <= 10.0 * eps && pb <= 10.0 * eps;", TD.test_band_count_nodes_just_outside_a_sphere),
+    ("face ties: gap threshold", "const bool tieA = gapA < eps || (!smooth && std::fabs(pb) <= eps);",
+     "const bool tieA = gapA < 0.5 || (!smooth && std::fabs(pb) <= eps);", TD.test_face_tie_count_on_a_cube_edge),
+    ("depth gap: sign", "(top1 - top2) / dx", "(top2 - top1) / dx", TD.test_depth_gap_closed_form_and_symmetric_tie),
+    ("volume sensitivity: B's term dropped", "const double dw = hpa * hb + ha * hpb;", "const double dw = hpa * hb;",
+     TD.test_sensitivities_of_a_smoothed_slab),
+    ("moment sensitivity: a lever-arm component dropped",
+     "m_sens += dw * eps * std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);",
+     "m_sens += dw * eps * std::sqrt(c[0] * c[0] + c[1] * c[1]);", TD.test_sensitivities_of_a_smoothed_slab),
+    ("normal sensitivity: the product term dropped", "g_sens += (dhpa * hb + 2.0 * hpa * hpb + ha * dhpb) * eps;",
+     "g_sens += (dhpa * hb + ha * dhpb) * eps;", TD.test_sensitivities_of_a_smoothed_slab),
+    ("normal sensitivity (sharp): B's term dropped", "g_sens += (dhpa * hb + ha * dhpb) * eps;",
+     "g_sens += (dhpa * hb) * eps;", TD.test_sensitivities_of_a_sharp_slab),
+    ("rough band: eps ten times too wide", "const bool loose = pa < srough + eps && pb < srough + eps;",
+     "const bool loose = pa < srough + 10.0 * eps && pb < srough + 10.0 * eps;",
+     TD.test_rough_band_nodes_around_a_sphere),
+    ("box face ties: exact ties counted", "second - best < 1e-4 * dx && second != best", "second - best < 1e-4 * dx",
+     TD.test_face_ties_of_face_aligned_boxes_are_exact),
 ]
 
 
