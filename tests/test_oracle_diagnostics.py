@@ -24,7 +24,7 @@ import numpy as np
 import pytest
 
 import oracle
-from tests.helpers import state
+from tests.helpers import quat_axis_angle, state
 
 EPS = oracle.BAND_EPS
 S075 = math.sqrt(0.75)
@@ -178,3 +178,18 @@ def test_face_ties_of_face_aligned_boxes_are_exact():
     st = boxed(state([1, 1], [[4, 4, 4], [4, 10, 10]], [XA, XA + [7.2, 0.0, 0.0]], n=80))
     _, _, flags = oracle.box_pipeline(st)
     assert flags[0, 1] == 0
+
+
+def test_face_ties_of_slightly_tilted_boxes():
+    """The same boxes, each turned by theta about a generic axis: every face
+    of B0 is now met by its lines at an affine function of the line's
+    position with slopes O(theta), so on each of the six faces the nearest
+    and the second nearest line differ by about theta times the line spacing
+    (0.5 to 1.3 cells here), never exactly.  theta = 1e-5: below 1e-4 dx on
+    every face, six near ties.  theta = 3e-3: above it on every face, none."""
+    XA = np.array([30.3, 31.7, 29.2])
+    for theta, ties in ((1e-5, 6), (3e-3, 0)):
+        q = [quat_axis_angle([1, 2, 3], theta), quat_axis_angle([-2, 1, 0.5], theta)]
+        st = boxed(state([1, 1], [[4, 4, 4], [4, 10, 10]], [XA, XA + [7.2, 0.0, 0.0]], quat=q, n=80))
+        _, _, flags = oracle.box_pipeline(st)
+        assert flags[0, 1] == ties, (theta, flags)

@@ -101,6 +101,8 @@ CASES = [
      TD.test_rough_band_nodes_around_a_sphere),
     ("box face ties: exact ties counted", "second - best < 1e-4 * dx && second != best", "second - best < 1e-4 * dx",
      TD.test_face_ties_of_face_aligned_boxes_are_exact),
+    ("box face ties: threshold", "second - best < 1e-4 * dx && second != best",
+     "second - best < 1e-2 * dx && second != best", TD.test_face_ties_of_slightly_tilted_boxes),
 ]
 
 
