@@ -84,6 +84,9 @@ def combine_ranks(ms: float, cells: float, device):
     return float(t.item()), float(c.item())
 
 
+NARROW_REPEAT = 10   # back-to-back node-sweep runs between the timing events
+
+
 def headline_state(rank: int):
     from paper_2401_10878_gb300 import workloads as W
     st = W.settling_cubes_dense(seed=4 + 1000 * rank)
@@ -303,10 +306,16 @@ def run_ours(args, ws, rank, local):
     with ClockSampler(local) as clk:
         res = time_forward(model, pos_d, quat_d, args.steps, args.warmup, flush)
         # the node sweep's own time, live, from events the library records
-        # around that launch (a second context, same workload and steps)
-        tmodel = Contact.from_state(st, narrow_events=True)
+        # around it (second contexts, same workload and steps): around
+        # NARROW_REPEAT back-to-back runs of the sweep (the per-run mean, the
+        # roofline's duration), and around a single run (which adds the
+        # events' own overhead, reported beside it)
         nsteps = min(args.steps, 1000)
+        tmodel = Contact.from_state(st, narrow_events=NARROW_REPEAT)
         tres = time_forward(tmodel, pos_d, quat_d, nsteps, args.warmup, flush, narrow=True)
+        tmodel.close()
+        tmodel = Contact.from_state(st, narrow_events=1)
+        tres1 = time_forward(tmodel, pos_d, quat_d, nsteps, args.warmup, flush, narrow=True)
         tmodel.close()
     torch.cuda.synchronize()
     if ws > 1:
@@ -329,10 +338,12 @@ def run_ours(args, ws, rank, local):
                 "traffic": traffic_from_profile() if args.workload == "cubes1934" and args.seed is None else None,
                 "kernel": "k_narrow32 (node sweep)", "ops_per_launch": ops_per_launch,
                 "launch_ms": narrow_avg_s * 1e3,
+                "launch_ms_single": tres1["narrow_ms"] / nsteps,
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz (max SM clock)",
                 "frac_at_median_clock": (achieved / (sms * FP32_LANES_PER_SM * med * 1e6 / 1e12)) if med else None,
                 "cell_evals_per_s_kernel": (tres["cells"] / nsteps) / narrow_avg_s,
-                "timing": f"CUDA events around the node-sweep launch, {nsteps} steps of the same workload"}
+                "timing": f"CUDA events around {NARROW_REPEAT} back-to-back node-sweep runs per step (their mean), "
+                          f"{nsteps} steps of the same workload; launch_ms_single: events around one run"}
     # the derived peak checked against this GPU's measured FFMA rate
     try:
         from paper_2401_10878_gb300.contact import fp32_ffma_rate

@@ -93,8 +93,13 @@ typedef struct {
                                on first use and replays it while the buffers are
                                the same (not while the stream is being captured)   */
   int32_t narrow_events;    /* 1: record CUDA events around the node-sweep launch
-                               (read with contact_narrow_time); 0: none, so that
-                               consecutive kernels overlap their launch           */
+                               (read with contact_narrow_time); K in 2..64: the
+                               node sweep runs K times back to back between the
+                               events (the later runs recompute the same outputs)
+                               and contact_narrow_time returns the time per run,
+                               without the events' own overhead (not with
+                               box_mode 1: EINVAL); 0: none, so that consecutive
+                               kernels overlap their launch                       */
   int32_t history;          /* 1: contact history (Sec. 4.3.3): a contact (a pair
                                with V > 0) keeps the damping factor of Eq.
                                (damping_factor) computed with `restitution` from
@@ -244,8 +249,10 @@ contact_status contact_stats(contact_ctx* ctx, int64_t* stats);
 /* Synchronises, then writes the device time in milliseconds of the last
  * step's narrow-phase kernel (the node sweep), measured with CUDA events that
  * contact_step records on the context stream around that launch (also when
- * the step replays a graph) when cfg.narrow_events is 1.  CONTACT_ESTATE
- * before the first step or with narrow_events off. */
+ * the step replays a graph) when cfg.narrow_events is on; with
+ * narrow_events = K > 1 the events enclose K back-to-back runs and the time
+ * is their mean.  CONTACT_ESTATE before the first step or with narrow_events
+ * off. */
 contact_status contact_narrow_time(contact_ctx* ctx, float* ms);
 
 /* Per-particle node ranges (lo[3], hi[3]) [N,6] i32 dev of the last step. */
@@ -303,10 +310,19 @@ int32_t contact_kernels_per_backward(const contact_ctx* ctx);
 void contact_destroy(contact_ctx* ctx);
 
 /* Fixed capacity of contact_step_noalloc: the size of its scratch array in
- * MiB, and the largest particle count and pair capacity it accepts. */
+ * MiB, the largest particle count and pair capacity it accepts, the node-tile
+ * budget per pair (max_tiles 0 means CONTACT_NOALLOC_TILES_PER_PAIR x
+ * max_pairs; a tile holds up to 128 node lines of one pair, so this covers
+ * pair boxes of up to 256 lines on average), and the cell list's limits (at
+ * most CONTACT_NOALLOC_MAX_BINS bins per axis, and bins x bin capacity at
+ * most CONTACT_NOALLOC_MAX_BIN_ENTRIES).  contact_init allows 8 tiles per
+ * pair, 256 bins per axis and 2^26 bin entries. */
 #define CONTACT_NOALLOC_SCRATCH_MIB 32
 #define CONTACT_NOALLOC_MAX_PARTICLES 2048
 #define CONTACT_NOALLOC_MAX_PAIRS 8192
+#define CONTACT_NOALLOC_TILES_PER_PAIR 2
+#define CONTACT_NOALLOC_MAX_BINS 32
+#define CONTACT_NOALLOC_MAX_BIN_ENTRIES (1 << 20)
 
 /* contact_step for callers that cannot allocate device memory (no
  * counterpart in the paper: it is an interface for such callers, e.g. a host
@@ -325,8 +341,12 @@ void contact_destroy(contact_ctx* ctx);
  * Larger sizes, polytopes or other settings return CONTACT_EINVAL before any
  * work is enqueued.  The call waits for its stream and returns the device's
  * error (CONTACT_EINVAL for a bad pose, CONTACT_ECAPACITY) directly; velocities
- * are not taken (ddot_n = 0).  The first call on a device looks up the
- * array's device address, so make that call before any stream capture.  All
+ * are not taken (ddot_n = 0).  More pairs than max_pairs, more tiles than the
+ * tile budget or a fuller bin than the cell list holds return
+ * CONTACT_ECAPACITY (n_pairs then holds the pair count needed).  The first
+ * call on a device, and the first after its primary context was recreated
+ * (cudaDeviceReset), looks up the array's device address, so make that call
+ * before any stream capture.  All
  * calls share the one array and the set-up clears what must start at zero:
  * calls whose work overlaps on the GPU (from other threads or streams) race
  * and must be serialised by the caller. */

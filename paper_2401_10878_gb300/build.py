@@ -44,6 +44,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     """Compile (if sources changed) and return the path of libcontact.so."""
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, "contact_dev.cuh"), os.path.join(CSRC, "force_law.cuh"),
+               os.path.join(CSRC, "line_clip.cuh"),
                os.path.join(HERE, "..", "include", "contact.h")]
     objs, jobs = [], []
     for src in SOURCES:

@@ -172,7 +172,7 @@ class Contact:
         if max_pairs is not None:
             cfg.max_pairs = int(max_pairs)
         cfg.max_neighbors, cfg.max_tiles, cfg.use_graph = int(max_neighbors), int(max_tiles), int(bool(use_graph))
-        cfg.narrow_events = int(bool(narrow_events))
+        cfg.narrow_events = int(narrow_events)   # False/True, or K > 1 back-to-back node sweeps
         self.cfg = cfg
         self.n = n
         self.steps = 0   # contact_step calls so far (the adjoint differentiates the last)

@@ -22,11 +22,9 @@ enum Kind : int { KIND_SPHERE = 0, KIND_CUBOID = 1, KIND_POLY = 2, KIND_POLYG = 
 constexpr int kRegFaces = 20;
 
 constexpr int kMaxFaces = 32;         // faces of one polytope
-constexpr int kTileItemsPerLane = 4;  // node lines (segments) per lane per tile
-constexpr int kSegMax = 16;           // longest line segment of one item
+constexpr int kTileItemsPerLane = 4;  // node lines per lane per tile
 constexpr int kPartialFloats = 12;    // FP32 partial sums per tile
 constexpr int kTapeDoubles = 16;      // FP64 per-pair values kept for the adjoint
-constexpr int kCostBuckets = 4;       // node-sweep queue: tiles grouped by estimated cost, dearest first
 constexpr int kStepCounter = 12;      // counters[] slot of the completed-step count
 constexpr int kFtDoubles = 9;         // per-pair F, T_A, T_B
 
@@ -110,9 +108,9 @@ struct __align__(16) PairRec {   // 16-byte aligned: records are copied with 16-
   int lo[3];       // lower node of the pair box (i's frame)
   int dim[3];      // nodes per axis
   int shift[3];    // image index s of j: X_j' = X_j - s L
-  int axis;        // sweep axis
-  int seglen;      // nodes per line segment
-  int nseg;        // segments per line
+  int axis;        // sweep axis (the box's longest)
+  int seglen;      // nodes per line segment (the whole line)
+  int nseg;        // segments per line (1)
   int nitems;      // lines * nseg
   int tile0;       // first tile of the pair
   int ntiles;
@@ -193,18 +191,20 @@ struct Lists {
   int* hist_n;      // [2, N] contacts per particle; buffer (steps & 1) is read, the other written
   double* hist_box; // [2, N, max_nbr, 6] box pipeline: each contact's corrected box relative to X_i (or null)
   PairRec* pairs;   // [max_pairs]
-  OvlRec* olist;    // [max_pairs] the step's overlapping pairs (counters[5] of them): the force law's work list
+  OvlRec* olist;    // [max_pairs] entry q: pair q's sums when it overlaps (oflag[q] = 1): the force law's work
+  int* oflag;       // [max_pairs] 1 when pair q overlaps (V > 0), else 0 (written by the node sweep or the
+                    // pair builder's separation test)
   int* tile_pair;   // [max_tiles] pair of each tile
-  PairRec* tiles;   // [kCostBuckets, max_tiles] one record per tile (the pair's record with tile and
-                    // pair set), in the node sweep's queue order: bucket 0 (dearest) first
+  PairRec* tiles;   // [max_tiles] one record per tile (the pair's record with tile and pair set), the
+                    // node sweep's list: a pair's tiles contiguous from its tile0
   float* partial;   // [max_tiles, kPartialFloats]
   int* pdone;       // [max_pairs] tiles of the pair swept so far (pairs of several tiles)
   double* tape;     // [max_pairs, kTapeDoubles]
   double* ft;       // [max_pairs, kFtDoubles]
   const int* kind;  // [N] sweep kind of each particle (Kind, polytopes by face bucket)
-  int* counters;    // [16]: 0 pairs, 1 tiles, 2 queue, 3 cells(lo), 4 cells(hi), 5 overlapping pairs,
-                    // 6 adjoint queue, 8.. 8 + kCostBuckets tiles per cost bucket,
-                    // kStepCounter steps completed (its parity selects the contact-history buffer)
+  int* counters;    // [16]: 0 pairs, 1 tiles, 2 box pipeline queue, 3 cells(lo), 4 cells(hi), 5 overlapping
+                    // pairs, 6 adjoint queue, kStepCounter steps completed (its parity selects the
+                    // contact-history buffer)
   unsigned long long* u64;  // [4]: 0 node evaluations, 1 nominal lane-ops of the node sweep
   int* err;         // [1] sticky device error
   int* err_host;    // mapped host word mirroring err
@@ -313,23 +313,6 @@ __device__ __forceinline__ double widen(float f) {
   return __hiloint2double(static_cast<int>(hi), static_cast<int>(m << 29));
 }
 
-// FP64 reciprocal and reciprocal square root from an FP32 seed and two Newton
-// steps (relative error ~1e-16, not correctly rounded): a few FP64 FMAs
-// instead of a division sequence, which costs ~10x more on this GPU's narrow
-// FP64 pipe.  For positive normal arguments within the FP32 range.
-__device__ __forceinline__ double fast_rcp(double a) {
-  double r = static_cast<double>(__frcp_rn(static_cast<float>(a)));
-  r = r * fma(-a, r, 2.0);
-  r = r * fma(-a, r, 2.0);
-  return r;
-}
-__device__ __forceinline__ double fast_rsqrt(double a) {
-  double y = static_cast<double>(rsqrtf(static_cast<float>(a)));
-  y = y * fma(-0.5 * a, y * y, 1.5);
-  y = y * fma(-0.5 * a, y * y, 1.5);
-  return y;
-}
-
 // Programmatic dependent launch: every kernel of a step lets the next one
 // launch at its start, and waits for the previous one (completion and memory
 // visibility) before it reads that kernel's results.
@@ -361,7 +344,7 @@ void launch_pose(const Params& P, const Shapes& S, const Parts& D, const Lists& 
                  const double* quat, cudaStream_t st);
 void launch_broad(const Params& P, const Parts& D, const Lists& W, cudaStream_t st);
 void launch_plan(const Params& P, const Shapes& S, const Parts& D, const Lists& W, int32_t* pair_ij, int32_t* n_pairs,
-                 cudaStream_t st);
+                 double* pair_out, cudaStream_t st);
 constexpr int kRowGroup = 256;   // particles per group sum of the pair-row offsets
 int bin_capacity(int n, const double binw[3], double rin_min, long long nbins, long long max_entries);
 void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel,

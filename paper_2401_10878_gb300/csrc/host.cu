@@ -235,9 +235,13 @@ void enqueue_step(contact_ctx* c, bool capturing, const double* pos, const doubl
   // bin counts are zero: contact_init clears them, every step's last kernel clears them again
   launch_pose(c->P, c->S, c->D, c->W, pos, quat, c->stream);
   launch_broad(c->P, c->D, c->W, c->stream);
-  launch_plan(c->P, c->S, c->D, c->W, pair_ij, n_pairs, c->stream);
+  launch_plan(c->P, c->S, c->D, c->W, pair_ij, n_pairs, pair_out, c->stream);
   if (c->cfg.narrow_events) cudaEventRecordWithFlags(c->ev_narrow[0], c->stream, ev_flags);
   launch_narrow(c->P, c->S, c->D, c->W, vel, pair_out, c->grid_narrow, c->stream);
+  // narrow_events = K > 1: K - 1 more launches of the node sweep, each
+  // recomputing the same outputs from the same tiles (the timing's average)
+  for (int k = 1; k < c->cfg.narrow_events; ++k)
+    launch_narrow(c->P, c->S, c->D, c->W, vel, pair_out, c->grid_narrow, c->stream);
   if (c->cfg.narrow_events) cudaEventRecordWithFlags(c->ev_narrow[1], c->stream, ev_flags);
   if (c->P.box_mode == 0) launch_force(c->P, c->S, c->D, c->W, vel, pair_out, c->stream);
   launch_particle_sum(c->P, c->D, c->W, force, torque, c->stream);
@@ -323,6 +327,9 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
                      !std::isfinite(C.mu_k) || !std::isfinite(C.u_k)))
     return CONTACT_EINVAL;
   if (C.box_mode != 0 && C.box_mode != 1) return CONTACT_EINVAL;
+  // repeated node sweeps (timing) recompute the same outputs only without the
+  // box pipeline, whose kernel keeps the contact history and a work queue
+  if (C.narrow_events < 0 || C.narrow_events > 64 || (C.narrow_events > 1 && C.box_mode != 0)) return CONTACT_EINVAL;
   if (C.box_mode == 1 && (C.contact_resolution < 1 || C.contact_resolution > 64)) return CONTACT_EINVAL;
   const int nw = C.n_walls;
   if (nw < 0 || nw > CONTACT_MAX_WALLS) return CONTACT_EINVAL;
@@ -617,8 +624,9 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   }
   GBC_TRY(dev_alloc(c, &W.pairs, mp));
   GBC_TRY(dev_alloc(c, &W.olist, mp));
+  GBC_TRY(dev_alloc(c, &W.oflag, mp));
   GBC_TRY(dev_alloc(c, &W.tile_pair, mt));
-  GBC_TRY(dev_alloc(c, &W.tiles, mt * kCostBuckets));
+  GBC_TRY(dev_alloc(c, &W.tiles, mt));
   GBC_TRY(dev_alloc(c, &W.partial, mt * kPartialFloats));
   GBC_TRY(dev_alloc(c, &W.pdone, mp));
   GBC_TRY(dev_alloc(c, &W.tape, mp * kTapeDoubles));
@@ -781,6 +789,7 @@ contact_status contact_narrow_time(contact_ctx* c, float* ms) {
   cudaError_t e = cudaEventSynchronize(c->ev_narrow[1]);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
   e = cudaEventElapsedTime(ms, c->ev_narrow[0], c->ev_narrow[1]);
+  if (e == cudaSuccess && c->cfg.narrow_events > 1) *ms /= static_cast<float>(c->cfg.narrow_events);
   return e == cudaSuccess ? CONTACT_OK : cuda_fail(c, e, "cudaEventElapsedTime");
 }
 

@@ -11,7 +11,9 @@
 //   T_A = (x_c - X_A) x (-F), T_B = (x_c - X_B') x F.
 // k_adj_pre: FP64 chain rule from (gF, gT) to seeds dL/dS0, dL/dS1, dL/dSg
 //   and the explicit pose terms (torque arms, damping, fallback normal).
-// k_adj_cells: persistent tile sweep (same tiles as the forward pass); per node
+// k_adj_cells: persistent tile sweep (same tiles as the forward pass); each
+//   line clipped to the nodes where both phi < w/2 (line_clip.cuh), every
+//   other node's terms being exact zeros; per node
 //   dL/dphi and dL/d(grad phi) pulled back to the 12 pose directions of the
 //   pair (translation and infinitesimal world rotation of each particle):
 //     dphi/dX = -grad phi,  dphi/domega = grad phi x r,
@@ -25,6 +27,7 @@
 
 #include "contact_dev.cuh"
 #include "force_law.cuh"
+#include "line_clip.cuh"
 
 namespace gbc {
 
@@ -228,9 +231,13 @@ struct AdjGeom {
 };
 
 // A wall (pid >= n) is type 3: phi = m . c + p0 at box-relative node c, with
-// m from Rt row 0 and p0 from the pair record's size slot (wall_p0).
+// m from Rt row 0 and p0 from the pair record's size slot (wall_p0).  A
+// polytope's planes go to sm[0 .. nf), their inverse slopes along the sweep
+// axis au (the line clip) to the floats after sm[kMaxFaces].
+__device__ __forceinline__ float sel3(float a, float b, float c, int k) { return k == 0 ? a : (k == 1 ? b : c); }
+
 __device__ __forceinline__ void adj_load(const Shapes& S, const Parts& D, int pid, const int* ci, const float* cf,
-                                         float4* sm, AdjGeom& g, int n, float wall_p0) {
+                                         float4* sm, AdjGeom& g, int n, float wall_p0, int au) {
   const int lane = threadIdx.x & 31;
   if (pid >= n) {
     g.type = 3;
@@ -253,7 +260,11 @@ __device__ __forceinline__ void adj_load(const Shapes& S, const Parts& D, int pi
   if (g.type == 2) {
     const int f0 = S.face_off[pid];
     g.nf = S.face_off[pid + 1] - f0;
-    if (lane < g.nf) sm[lane] = D.wplane[f0 + lane];
+    if (lane < g.nf) {
+      const float4 e = D.wplane[f0 + lane];
+      sm[lane] = e;
+      reinterpret_cast<float*>(sm + kMaxFaces)[lane] = clip_inv(sel3(e.x, e.y, e.z, au));
+    }
     __syncwarp();
   }
   g.sp = sm;
@@ -322,6 +333,48 @@ __device__ __forceinline__ float adj_phi(const AdjGeom& g, const float r[3]) {
     best = fmaxf(best, fmaf(e.x, r[0], fmaf(e.y, r[1], fmaf(e.z, r[2], -e.w))));
   }
   return best;
+}
+
+// [lo, hi] (box coordinates along au) cut to where phi < T on the node line
+// with box coordinates cv, cw along av, aw; ci, cf: the particle centre
+// relative to the box origin as nearest node + remainder (r = (c - ci) - cf).
+template <int SET>
+__device__ __forceinline__ void adj_clip(const AdjGeom& g, int au, int av, int aw, int cv, int cw, const int* ci,
+                                         const float* cf, float T, float& lo, float& hi) {
+  const int iu = ci[0] * (au == 0) + ci[1] * (au == 1) + ci[2] * (au == 2);
+  const int iv = ci[0] * (av == 0) + ci[1] * (av == 1) + ci[2] * (av == 2);
+  const int iw = ci[0] * (aw == 0) + ci[1] * (aw == 1) + ci[2] * (aw == 2);
+  const float fu = sel3(cf[0], cf[1], cf[2], au);
+  const float rv = static_cast<float>(cv - iv) - sel3(cf[0], cf[1], cf[2], av);
+  const float rw = static_cast<float>(cw - iw) - sel3(cf[0], cf[1], cf[2], aw);
+  const float o = static_cast<float>(iu);
+  float l = lo - o, h = hi - o;   // node counter c = cu - iu, r_u = c - fu
+  if (SET != 2 && g.type == 0) {
+    clip_ball(fu, fmaf(rv, rv, rw * rw), g.size[0], T, l, h);
+  } else if (SET != 2 && g.type == 3) {
+    const float mu = sel3(g.rt[0], g.rt[1], g.rt[2], au);
+    const float p = fmaf(sel3(g.rt[0], g.rt[1], g.rt[2], av), rv,
+                         fmaf(sel3(g.rt[0], g.rt[1], g.rt[2], aw), rw, fmaf(-mu, fu, g.size[0])));
+    clip_half(mu, clip_inv(mu), p, T, l, h);
+  } else if (SET != 0 || g.type == 1) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float* t = g.rt + 3 * k;
+      const float tu = sel3(t[0], t[1], t[2], au);
+      const float p = fmaf(sel3(t[0], t[1], t[2], av), rv, fmaf(sel3(t[0], t[1], t[2], aw), rw, -tu * fu));
+      clip_slab(tu, clip_inv(tu), p, g.size[k] + T, l, h);
+    }
+  } else {
+    const float* inv = reinterpret_cast<const float*>(g.sp + kMaxFaces);
+    for (int f = 0; f < g.nf; ++f) {
+      const float4 e = g.sp[f];
+      const float eu = sel3(e.x, e.y, e.z, au);
+      const float p = fmaf(sel3(e.x, e.y, e.z, av), rv, fmaf(sel3(e.x, e.y, e.z, aw), rw, fmaf(-eu, fu, -e.w)));
+      clip_half(eu, inv[f], p, T, l, h);
+    }
+  }
+  lo = l + o;
+  hi = h + o;
 }
 
 __device__ __forceinline__ void cross3f(const float a[3], const float b[3], float c[3]) {
@@ -440,35 +493,21 @@ __device__ __forceinline__ void adj_post_pass(const Params& P, const Shapes& S, 
 
 template <int SET>
 __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, Parts D, Lists W, AdjBufs B) {
-  __shared__ float4 s_pl[kWarps][2][kMaxFaces];
+  __shared__ float4 s_pl[kWarps][2][kMaxFaces + kMaxFaces / 4];   // planes, then their inverse slopes
   __shared__ AdjStage s_st[kWarps][kAdjStage];
   int nst = 0;   // pairs staged in s_st[wid]
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int ntiles = min(W.counters[1], P.max_tiles);
-  const float inv_w = P.inv_w, hw = 0.5f * P.wdx_l;
-  // queue position -> tile record of the forward pass: cost buckets, dearest first
-  int bend[kCostBuckets];
-  {
-    int acc0 = 0;
-#pragma unroll
-    for (int b = 0; b < kCostBuckets; ++b) {
-      acc0 += W.counters[8 + b];
-      bend[b] = acc0;
-    }
-  }
+  const float inv_w = P.inv_w, hw = 0.5f * P.wdx_l, T = hw + kClipMargin;
   int qpos = 0;
   if (lane == 0) qpos = atomicAdd(&W.counters[6], 1);
   qpos = __shfl_sync(kFull, qpos, 0);
   while (qpos < ntiles) {
     int qn = 0;
     if (lane == 0) qn = atomicAdd(&W.counters[6], 1);
-    int b = 0, start = 0;
-#pragma unroll
-    for (int k = 0; k < kCostBuckets - 1; ++k)
-      if (qpos >= bend[k]) { b = k + 1; start = bend[k]; }
     // the pair record's fields in registers (no runtime-indexed local copy)
-    const PairRec& prg = W.tiles[static_cast<size_t>(b) * P.max_tiles + (qpos - start)];
+    const PairRec& prg = W.tiles[qpos];
     const int p = prg.pair;
     const int t = prg.tile0 + prg.tile;   // the tile's index (its partial slot)
     const int rec_i = prg.i, rec_j = prg.j, axis = prg.axis, nseg = prg.nseg, seglen = prg.seglen;
@@ -490,9 +529,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
                         (sg[1] != 0.f) || (sg[2] != 0.f) || (B.pgrad[static_cast<size_t>(p) * kPairGrad + 12] != 0.0);
     if (active) {
       AdjGeom A, Bg;
-      adj_load(S, D, rec_i, ai, af, s_pl[wid][0], A, P.n, 0.f);
-      adj_load(S, D, rec_j, bi, bf, s_pl[wid][1], Bg, P.n, wall_p0);
-      const int ax0 = axis;
+      adj_load(S, D, rec_i, ai, af, s_pl[wid][0], A, P.n, 0.f, axis);
+      adj_load(S, D, rec_j, bi, bf, s_pl[wid][1], Bg, P.n, wall_p0, axis);
+      const int ax0 = axis, ax1 = ax0 == 2 ? 0 : ax0 + 1, ax2 = ax1 == 2 ? 0 : ax1 + 1;
       const int du = ax0 == 0 ? dm0 : (ax0 == 1 ? dm1 : dm2);
       const int dv = ax0 == 0 ? dm1 : (ax0 == 1 ? dm2 : dm0);   // side along (ax0 + 1) mod 3
       const int it0 = (t - tile0) * 32 * kTileItemsPerLane;
@@ -502,7 +541,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
         const int line = it / nseg, seg = it - line * nseg;
         const int l1 = line % dv, l2 = line / dv;   // coordinates along axes ax1, ax2
         const int u0 = seg * seglen, u1 = min(u0 + seglen, du);
-        for (int cu = u0; cu < u1; ++cu) {
+        float clo = static_cast<float>(u0), chi = static_cast<float>(u1 - 1);
+        adj_clip<SET>(A, ax0, ax1, ax2, l1, l2, ai, af, T, clo, chi);
+        adj_clip<SET>(Bg, ax0, ax1, ax2, l1, l2, bi, bf, T, clo, chi);
+        int ub;
+        const int nk = clip_nodes(clo, chi, u0, u1 - u0, &ub);
+        for (int cu = ub; cu < ub + nk; ++cu) {
           // node coordinates in box axes x, y, z (selects: no runtime-indexed array)
           int c[3];
           c[0] = ax0 == 0 ? cu : (ax0 == 1 ? l2 : l1);

@@ -7,6 +7,7 @@
 #include <cfloat>
 
 #include "contact_dev.cuh"
+#include "line_clip.cuh"
 
 namespace gbc {
 
@@ -205,9 +206,8 @@ __global__ void k_pose(Params P, Shapes S, Parts D, Lists W, const double* __res
   if (t == 0) {
     W.counters[0] = 0;   // pairs
     W.counters[1] = 0;   // tiles allocated
-    W.counters[2] = 0;   // node-sweep queue head
+    W.counters[2] = 0;   // box pipeline queue head
     W.counters[5] = 0;   // pairs with V > 0
-    for (int b = 0; b < kCostBuckets; ++b) W.counters[8 + b] = 0;
     W.u64[0] = 0;        // node evaluations
     W.u64[1] = 0;        // nominal lane-ops
   }
@@ -487,12 +487,95 @@ static_assert(offsetof(PairRec, rta) == 30 * 4 && offsetof(PairRec, szb) == 51 *
                   offsetof(PairRec, pair) == 55 * 4 && sizeof(PairRec) == 14 * 16,
               "store_pair_rec follows the PairRec layout");
 
+// True when the regions {phi_A < T} and {phi_B < T} of the pair are disjoint
+// (by more than kCullMargin cells), so that no node can add to any of the
+// node sweep's sums (each needs both distances below w/2 < T): the pair's
+// outputs are zero and it is not queued.  Spheres, cubes and cuboids only
+// (their T-regions are balls and boxes of half extents size + T): box-box by
+// the 15 separating axes (faces of either box, edge cross products), sphere-box
+// by the box's closest point, sphere-sphere by the centre distance.  FP32 in
+// lattice units: the centres differ by an exact integer plus the FP32
+// difference of two remainders, and every rounding is far below the margin.
+constexpr float kCullMargin = 1e-3f;
+
+__device__ __forceinline__ float dot3(const float* a, const float* b) { return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2])); }
+
+// distance^2 from point c (world, relative to the box centre) to the box
+// with body axes rt rows and half extents e
+__device__ __forceinline__ float box_point_dist2(const float* rt, const float e[3], const float c[3]) {
+  float d2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float y = dot3(rt + 3 * k, c);
+    const float o = fmaxf(fabsf(y) - e[k], 0.f);
+    d2 = fmaf(o, o, d2);
+  }
+  return d2;
+}
+
+__device__ bool pair_apart(const PairRec& r, float T) {
+  const int ka = r.kinds & 0xff, kb = r.kinds >> 8;
+  const bool sa = ka == KIND_SPHERE, sb = kb == KIND_SPHERE;
+  const bool ba = ka == KIND_CUBOID || ka == KIND_CUBE, bb = kb == KIND_CUBOID || kb == KIND_CUBE;
+  if (!((sa || ba) && (sb || bb))) return false;
+  float d[3];   // centre of B minus centre of A (lattice units)
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d[k] = static_cast<float>(r.bi[k] - r.ai[k]) + (r.bf[k] - r.af[k]);
+  if (sa && sb) {
+    const float reach = r.sza[0] + r.szb[0] + 2.f * T + kCullMargin;
+    return dot3(d, d) > reach * reach;
+  }
+  if (sa || sb) {
+    const float* rt = sa ? r.rtb : r.rta;
+    const float* sz = sa ? r.szb : r.sza;
+    const float e[3] = {sz[0] + T, sz[1] + T, sz[2] + T};
+    const float rs = (sa ? r.sza[0] : r.szb[0]) + T + kCullMargin;
+    const float c[3] = {sa ? -d[0] : d[0], sa ? -d[1] : d[1], sa ? -d[2] : d[2]};   // sphere centre - box centre
+    return box_point_dist2(rt, e, c) > rs * rs;
+  }
+  // two boxes: R[i][j] = a_i . b_j, t = d in A's frame
+  const float ea[3] = {r.sza[0] + T, r.sza[1] + T, r.sza[2] + T};
+  const float eb[3] = {r.szb[0] + T, r.szb[1] + T, r.szb[2] + T};
+  float R[3][3], AR[3][3], t[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    t[i] = dot3(r.rta + 3 * i, d);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      R[i][j] = dot3(r.rta + 3 * i, r.rtb + 3 * j);
+      AR[i][j] = fabsf(R[i][j]) + 1e-6f;
+    }
+  }
+  bool sep = false;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)   // A's faces
+    sep = sep || fabsf(t[i]) > ea[i] + fmaf(eb[0], AR[i][0], fmaf(eb[1], AR[i][1], eb[2] * AR[i][2])) + kCullMargin;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {   // B's faces
+    const float tb = fmaf(t[0], R[0][j], fmaf(t[1], R[1][j], t[2] * R[2][j]));
+    sep = sep || fabsf(tb) > eb[j] + fmaf(ea[0], AR[0][j], fmaf(ea[1], AR[1][j], ea[2] * AR[2][j])) + kCullMargin;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {   // edge pairs a_i x b_j
+    const int i1 = i == 2 ? 0 : i + 1, i2 = i1 == 2 ? 0 : i1 + 1;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int j1 = j == 2 ? 0 : j + 1, j2 = j1 == 2 ? 0 : j1 + 1;
+      const float ra = fmaf(ea[i1], AR[i2][j], ea[i2] * AR[i1][j]);
+      const float rb = fmaf(eb[j1], AR[i][j2], eb[j2] * AR[i][j1]);
+      sep = sep || fabsf(fmaf(t[i2], R[i1][j], -t[i1] * R[i2][j])) > ra + rb + kCullMargin;
+    }
+  }
+  return sep;
+}
+
 __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shapes S, Parts D, Lists W,
                                                                   int32_t* __restrict__ pair_ij,
-                                                                  int32_t* __restrict__ n_pairs_out) {
-  // per warp: tiles, then queue slots per cost bucket (exclusive prefixes after the block scan)
-  __shared__ int s_w[kBuildWarps][1 + kCostBuckets];
-  __shared__ int s_base[1 + kCostBuckets];
+                                                                  int32_t* __restrict__ n_pairs_out,
+                                                                  double* __restrict__ pair_out) {
+  // per warp: tiles (exclusive prefix after the block scan)
+  __shared__ int s_w[kBuildWarps];
+  __shared__ int s_base;
   __shared__ unsigned long long s_u64[kBuildWarps][2];
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -568,38 +651,19 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
         pr.lo[k] = lo[k];
         pr.dim[k] = hi[k] - lo[k] + 1;
       }
-      // sweep layout: lines along one axis, lines cut into nseg segments; the
-      // choice minimises warp slots x (segment length + 2 node-equivalents
-      // for the line set-up).  Loops unrolled: every division is by a constant.
+      // sweep layout: whole node lines along the box's longest axis (the
+      // fewest lines).  The node sweeps clip every line to the few nodes near
+      // both surfaces, so a line costs about the same whatever its length
+      // (selects, not a runtime index into pr.dim: that would put pr in local memory).
       const long long volp = static_cast<long long>(pr.dim[0]) * pr.dim[1] * pr.dim[2];
       const int lines_of[3] = {pr.dim[1] * pr.dim[2], pr.dim[0] * pr.dim[2], pr.dim[0] * pr.dim[1]};
-      int best = -1;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const int du = pr.dim[a];
-        const int lines = lines_of[a];
-#pragma unroll
-        for (int ns = 1; ns <= 8; ++ns) {
-          const int sl = (du + ns - 1) / ns;
-          const int slots = (lines * ns + 31) >> 5;
-          const int cost = slots * (sl + 2);
-          if (ns <= du && sl <= kSegMax && (best < 0 || cost < best)) {
-            best = cost;
-            pr.axis = a;
-            pr.nseg = ns;
-            pr.seglen = sl;
-          }
-        }
-      }
-      if (best < 0) {   // a box longer than 8 * kSegMax nodes: longest axis, more segments
-        // (selects, not a runtime index into pr.dim: that would put pr in local memory)
+      {
         const int a = pr.dim[1] > pr.dim[0] ? (pr.dim[2] > pr.dim[1] ? 2 : 1) : (pr.dim[2] > pr.dim[0] ? 2 : 0);
-        const int da = a == 0 ? pr.dim[0] : (a == 1 ? pr.dim[1] : pr.dim[2]);
         pr.axis = a;
-        pr.nseg = (da + kSegMax - 1) / kSegMax;
-        pr.seglen = (da + pr.nseg - 1) / pr.nseg;
+        pr.nseg = 1;
+        pr.seglen = a == 0 ? pr.dim[0] : (a == 1 ? pr.dim[1] : pr.dim[2]);
       }
-      pr.nitems = (pr.axis == 0 ? lines_of[0] : (pr.axis == 1 ? lines_of[1] : lines_of[2])) * pr.nseg;
+      pr.nitems = pr.axis == 0 ? lines_of[0] : (pr.axis == 1 ? lines_of[1] : lines_of[2]);
       ntiles = (pr.nitems + 32 * kTileItemsPerLane - 1) / (32 * kTileItemsPerLane);
       pr.ntiles = ntiles;
       pr.kinds = W.kind[i] | (W.kind[j] << 8);
@@ -632,6 +696,22 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
           pr.bf[k] = 0.f;
         }
       }
+      // the FP32 node sweep skips pairs whose distance regions are apart:
+      // their outputs are written here as the sweep would write them (zeros)
+      if (P.precision == 0 && P.box_mode == 0 && pair_apart(pr, 0.5f * P.wdx_l + kClipMargin)) {
+        ntiles = 0;
+        pr.ntiles = 0;
+        double* po = pair_out + static_cast<size_t>(pi) * 11;
+        double* pf = W.ft + static_cast<size_t>(pi) * kFtDoubles;
+        double* pt = W.tape + static_cast<size_t>(pi) * kTapeDoubles;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) po[k] = 0.0;
+#pragma unroll
+        for (int k = 0; k < kFtDoubles; ++k) pf[k] = 0.0;
+#pragma unroll
+        for (int k = 0; k < kTapeDoubles; ++k) pt[k] = 0.0;
+        W.oflag[pi] = 0;
+      }
       pr.tile = 0;
       pr.pair = pi;
       W.pdone[pi] = 0;
@@ -647,10 +727,8 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
       if (!wall) W.dn_pair[static_cast<size_t>(j) * cap + a0] = pi;
     }
     // allocations aggregated over the block (one atomic per counter and
-    // block, all in flight together): the pairs' tiles (partials,
-    // counters[1]) and their node-sweep queue slots in a cost bucket
-    // (estimated cost of a full tile: slots x (segment + 2), scaled by the
-    // pair's nominal ops per node; all tiles of a pair in one bucket)
+    // block, all in flight together): the pairs' tiles, contiguous per pair;
+    // tile k of a pair is entry tile0 + k of the node sweep's tile list
     int incl = ntiles;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -663,43 +741,22 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
       wv += __shfl_xor_sync(kFull, wv, d);
       wo += __shfl_xor_sync(kFull, wo, d);
     }
-    int bucket = kCostBuckets;   // none
-    if (active && ntiles > 0) {
-      const int slots = min(kTileItemsPerLane, (pr.nitems + 31) / 32);
-      const int cost = slots * (pr.seglen + 2) * (S.nomops[pr.i] + S.nomops[pr.j]);   // ~ warp instructions
-      bucket = cost >= 2400 ? 0 : (cost >= 1200 ? 1 : (cost >= 600 ? 2 : 3));
-    }
-    const int nq = bucket < kCostBuckets ? ntiles : 0;
-    const unsigned grp = __match_any_sync(kFull, bucket);
-    int before = 0;   // exclusive prefix of nq among the warp's lanes of this bucket
-    for (unsigned m = grp; m; m &= m - 1) {   // every lane of the group runs the same iterations
-      const int l = __ffs(m) - 1;
-      const int v = __shfl_sync(grp, nq, l);
-      if (l < lane) before += v;
-    }
-    int wtot[kCostBuckets];
-#pragma unroll
-    for (int b = 0; b < kCostBuckets; ++b) wtot[b] = __reduce_add_sync(kFull, bucket == b ? nq : 0);
     const int wtiles = __shfl_sync(kFull, incl, 31);
     if (lane == 0) {
-      s_w[wid][0] = wtiles;
-#pragma unroll
-      for (int b = 0; b < kCostBuckets; ++b) s_w[wid][1 + b] = wtot[b];
+      s_w[wid] = wtiles;
       s_u64[wid][0] = wv;
       s_u64[wid][1] = wo;
     }
     __syncthreads();
-    if (threadIdx.x <= kCostBuckets) {   // counter c: exclusive prefix over the warps, one atomic
-      const int c = threadIdx.x;
+    if (threadIdx.x == 0) {   // exclusive prefix over the warps, one atomic
       int run = 0;
       for (int w = 0; w < kBuildWarps; ++w) {
-        const int v = s_w[w][c];
-        s_w[w][c] = run;
+        const int v = s_w[w];
+        s_w[w] = run;
         run += v;
       }
-      int* ctr = c == 0 ? &W.counters[1] : &W.counters[8 + c - 1];
-      s_base[c] = run > 0 ? atomicAdd(ctr, run) : 0;
-    } else if (threadIdx.x == kCostBuckets + 1) {
+      s_base = run > 0 ? atomicAdd(&W.counters[1], run) : 0;
+    } else if (threadIdx.x == 32) {
       unsigned long long a = 0, b = 0;
       for (int w = 0; w < kBuildWarps; ++w) { a += s_u64[w][0]; b += s_u64[w][1]; }
       if (a > 0) {
@@ -708,19 +765,20 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
       }
     }
     __syncthreads();
-    const int tbase = s_base[0] + s_w[wid][0];
-    const int pos = bucket < kCostBuckets ? s_base[1 + bucket] + s_w[wid][1 + bucket] + before : 0;
+    const int tbase = s_base + s_w[wid];
     if (active) {
       pr.tile0 = tbase + incl - ntiles;
       store_pair_rec(W.pairs + pi, pr, 0);
-      for (int k = 0; k < ntiles; ++k) {
-        if (pr.tile0 + k < P.max_tiles) W.tile_pair[pr.tile0 + k] = pi;
-        else set_error(W.err, kErrCapacity);
-      }
-      // queue records (beyond the tile capacity the step fails with
+      // the tile records (beyond the tile capacity the step fails with
       // ECAPACITY and the node sweep does not run)
-      PairRec* dst = W.tiles + static_cast<size_t>(bucket) * P.max_tiles;
-      for (int k = 0; k < nq && pos + k < P.max_tiles; ++k) store_pair_rec(dst + pos + k, pr, k);
+      for (int k = 0; k < ntiles; ++k) {
+        if (pr.tile0 + k < P.max_tiles) {
+          W.tile_pair[pr.tile0 + k] = pi;
+          store_pair_rec(W.tiles + pr.tile0 + k, pr, k);
+        } else {
+          set_error(W.err, kErrCapacity);
+        }
+      }
     }
   }
 }
@@ -745,9 +803,10 @@ void launch_broad(const Params& P, const Parts& D, const Lists& W, cudaStream_t 
 }
 
 void launch_plan(const Params& P, const Shapes& S, const Parts& D, const Lists& W, int32_t* pair_ij, int32_t* n_pairs,
-                 cudaStream_t st) {
+                 double* pair_out, cudaStream_t st) {
   const int nb = (P.n + kBuildWarps - 1) / kBuildWarps;   // one particle row per warp
-  launch_pdl(k_build_pairs, dim3(nb > 0 ? nb : 1), dim3(kBuildWarps * 32), 0, st, P, S, D, W, pair_ij, n_pairs);
+  launch_pdl(k_build_pairs, dim3(nb > 0 ? nb : 1), dim3(kBuildWarps * 32), 0, st, P, S, D, W, pair_ij, n_pairs,
+             pair_out);
 }
 
 }  // namespace gbc

@@ -6,11 +6,17 @@
 // point, the contact normal, the indentation depth").
 //
 // k_narrow32 (FP32 node tests, FP32 tile partials):
-//   * persistent grid, one warp per tile; warps pull tiles from a device queue
-//     (atomic counter, next tile fetched while the current one runs), so pairs
-//     with very uneven boxes balance across the GPU;
-//   * a pair's box is cut into node lines along its longest axis, lines into
-//     segments of <= 16 nodes; a tile is 32 lanes x 4 segments of one pair;
+//   * persistent grid, one warp per tile; warp w takes tiles w, w + W, ...
+//     of the cost-ordered tile list (W warps; no queue atomics), the next
+//     tile's record fetched while the current one runs; pairs whose distance
+//     regions are apart never reach the list (the pair builder's test);
+//   * a pair's box is cut into node lines along its longest axis; a tile is
+//     32 lanes x 4 lines of one pair;
+//   * each lane clips its line to the interval where both signed distances
+//     lie below w/2 (line_clip.cuh: one bound per face plane, the sphere's
+//     quadratic) and evaluates only the nodes inside it: every node outside
+//     adds exact zeros to every sum, and ~99 % of a settling box's pair-box
+//     nodes lie outside;
 //   * along a line only the sweep coordinate changes, so the per-line part of
 //     each face value is computed once and a node costs one FMA per face;
 //   * node coordinates relative to each particle are exact integers minus an
@@ -19,13 +25,16 @@
 //     for the normal's gradient lookups in shared memory;
 //   * the volume/moment/depth update and the normal-band update run only when
 //     some lane of the warp needs them (warp-uniform branches);
-//   * warp-shuffle reduction per tile; partials go to HBM and are summed per
-//     pair in FP64 by the finalize kernel in tile order (deterministic).
+//   * warp-shuffle reduction per tile (skipped when no lane met a node to
+//     evaluate); a pair of one tile is finished from the warp's registers,
+//     otherwise the partials go to HBM and the warp that completes the pair's
+//     last tile sums them in FP64 in tile order (deterministic).
 // k_narrow64: all-FP64 comparison form, one thread block per pair.
 #include <cfloat>
 
 #include "contact_dev.cuh"
 #include "force_law.cuh"
+#include "line_clip.cuh"
 
 namespace gbc {
 
@@ -94,6 +103,16 @@ struct SphereEval {
     gl = 0.f;
     cnt_u = static_cast<float>(u0 - iu) - 1.f;
   }
+  // [lo, hi] (line coordinates) cut to where phi < T on the current line
+  __device__ __forceinline__ void clip(float T, float& lo, float& hi) const {
+    const float o = static_cast<float>(iu);
+    float l = lo - o, h = hi - o;
+    clip_ball(fu, rho2, rad, T, l, h);
+    lo = l + o;
+    hi = h + o;
+  }
+  // the next phi() evaluates node u
+  __device__ __forceinline__ void seek(int u) { cnt_u = static_cast<float>(u - iu) - 1.f; }
   // node offset cu - iu of the current node (exact integer in FP32)
   __device__ __forceinline__ float counter() const { return cnt_u; }
   __device__ __forceinline__ int origin() const { return iu; }
@@ -118,7 +137,7 @@ struct SphereEval {
 struct CuboidEval {
   int iu, iv, iw;
   float fu, fv, fw;
-  float tu[3], tv[3], tw[3], h[3];
+  float tu[3], tv[3], tw[3], h[3], itu[3];
   float cnt_u, p[3], y[3], a[3];
   float gb[3];
   __device__ void load(const PairRec& r, bool second, const Shapes&, const Parts&, const Local& L, float4*) {
@@ -134,6 +153,7 @@ struct CuboidEval {
       tv[k] = rt[3 * k + L.v];
       tw[k] = rt[3 * k + L.w];
       h[k] = sz[k];
+      itu[k] = clip_inv(tu[k]);
       gb[k] = 0.f;
     }
   }
@@ -146,6 +166,15 @@ struct CuboidEval {
     for (int k = 0; k < 3; ++k) p[k] = fmaf(-tu[k], fu, fmaf(tv[k], rv, tw[k] * rw));
     cnt_u = static_cast<float>(u0 - iu) - 1.f;
   }
+  __device__ __forceinline__ void clip(float T, float& lo, float& hi) const {
+    const float o = static_cast<float>(iu);
+    float l = lo - o, hh = hi - o;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) clip_slab(tu[k], itu[k], p[k], h[k] + T, l, hh);
+    lo = l + o;
+    hi = hh + o;
+  }
+  __device__ __forceinline__ void seek(int u) { cnt_u = static_cast<float>(u - iu) - 1.f; }
   __device__ __forceinline__ float counter() const { return cnt_u; }
   __device__ __forceinline__ int origin() const { return iu; }
   __device__ __forceinline__ float phi() {
@@ -178,7 +207,7 @@ struct CuboidEval {
 // shared-memory pair record at each line start.
 struct CubeEval {
   int iu;
-  float fu, tu0, tu1, tu2, h;
+  float fu, tu0, tu1, tu2, h, itu0, itu1, itu2;
   float cnt_u, p0, p1, p2, y0, y1, y2;
   float gb0, gb1, gb2;
   __device__ void load(const PairRec& r, bool second, const Shapes&, const Parts&, const Local& L, float4*) {
@@ -189,6 +218,7 @@ struct CubeEval {
     fu = cf[L.u];
     h = second ? r.szb[0] : r.sza[0];
     tu0 = rt[L.u]; tu1 = rt[3 + L.u]; tu2 = rt[6 + L.u];
+    itu0 = clip_inv(tu0); itu1 = clip_inv(tu1); itu2 = clip_inv(tu2);
     gb0 = gb1 = gb2 = 0.f;
   }
   __device__ __forceinline__ void begin_line_rec(const PairRec& r, bool second, const Local& L, int cv, int cw,
@@ -203,6 +233,16 @@ struct CubeEval {
     p2 = fmaf(-tu2, fu, fmaf(rt[6 + L.v], rv, rt[6 + L.w] * rw));
     cnt_u = static_cast<float>(u0 - iu) - 1.f;
   }
+  __device__ __forceinline__ void clip(float T, float& lo, float& hi) const {
+    const float o = static_cast<float>(iu), ht = h + T;
+    float l = lo - o, hh = hi - o;
+    clip_slab(tu0, itu0, p0, ht, l, hh);
+    clip_slab(tu1, itu1, p1, ht, l, hh);
+    clip_slab(tu2, itu2, p2, ht, l, hh);
+    lo = l + o;
+    hi = hh + o;
+  }
+  __device__ __forceinline__ void seek(int u) { cnt_u = static_cast<float>(u - iu) - 1.f; }
   __device__ __forceinline__ float counter() const { return cnt_u; }
   __device__ __forceinline__ int origin() const { return iu; }
   __device__ __forceinline__ float phi() {
@@ -228,7 +268,9 @@ struct CubeEval {
 };
 
 // Stage a polytope's world planes in local axes (u, v, w, offset) into shared
-// memory; faces beyond nf are padded so that they never win the maximum.
+// memory, and each face's inverse slope along u (the line clip) after them;
+// faces beyond nf are padded so that they never win the maximum (and are
+// constant along the line, below any threshold).
 __device__ __forceinline__ int stage_planes(const Shapes& S, const Parts& D, int pid, const Local& L,
                                             float4* sm, int npad) {
   const int lane = threadIdx.x & 31;
@@ -242,6 +284,7 @@ __device__ __forceinline__ int stage_planes(const Shapes& S, const Parts& D, int
                       L.w == 0 ? w.x : (L.w == 1 ? w.y : w.z), w.w);
     }
     sm[lane] = e;
+    reinterpret_cast<float*>(sm + kMaxFaces)[lane] = clip_inv(e.x);
   }
   __syncwarp();
   return nf;
@@ -277,6 +320,16 @@ struct PolyEval {
     }
     cnt_u = static_cast<float>(u0 - iu) - 1.f;
   }
+  __device__ __forceinline__ void clip(float T, float& lo, float& hi) const {
+    const float o = static_cast<float>(iu);
+    const float* inv = reinterpret_cast<const float*>(sp + kMaxFaces);
+    float l = lo - o, h = hi - o;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) clip_half(mu[f], inv[f], p[f], T, l, h);
+    lo = l + o;
+    hi = h + o;
+  }
+  __device__ __forceinline__ void seek(int u) { cnt_u = static_cast<float>(u - iu) - 1.f; }
   __device__ __forceinline__ float counter() const { return cnt_u; }
   __device__ __forceinline__ int origin() const { return iu; }
   __device__ __forceinline__ float phi() {
@@ -325,6 +378,18 @@ struct PolyGEval {
     rw = static_cast<float>(cw - iw) - fw;
     cnt_u = static_cast<float>(u0 - iu) - 1.f;
   }
+  __device__ __forceinline__ void clip(float T, float& lo, float& hi) const {
+    const float o = static_cast<float>(iu);
+    const float* inv = reinterpret_cast<const float*>(sp + kMaxFaces);
+    float l = lo - o, h = hi - o;
+    for (int f = 0; f < nf; ++f) {
+      const float4 e = sp[f];
+      clip_half(e.x, inv[f], fmaf(-e.x, fu, fmaf(e.y, rv, fmaf(e.z, rw, -e.w))), T, l, h);
+    }
+    lo = l + o;
+    hi = h + o;
+  }
+  __device__ __forceinline__ void seek(int u) { cnt_u = static_cast<float>(u - iu) - 1.f; }
   __device__ __forceinline__ float counter() const { return cnt_u; }
   __device__ __forceinline__ int origin() const { return iu; }
   __device__ __forceinline__ float value(int f) const {
@@ -360,11 +425,12 @@ struct PolyGEval {
 // centre of a wall is the box origin).  Box-relative values stay small, so
 // FP32 keeps them to ~1e-6.
 struct WallEval {
-  float mu_, mv_, mw_, p0;
+  float mu_, mv_, mw_, p0, imu_;
   float base, cnt_u, g;
   __device__ void load(const PairRec& r, bool second, const Shapes&, const Parts&, const Local& L, float4*) {
     const float* rt = second ? r.rtb : r.rta;   // row 0: the wall normal m (world)
     mu_ = rt[L.u]; mv_ = rt[L.v]; mw_ = rt[L.w];
+    imu_ = clip_inv(mu_);
     p0 = second ? r.szb[0] : r.sza[0];
     g = 0.f;
   }
@@ -372,6 +438,8 @@ struct WallEval {
     base = fmaf(mv_, static_cast<float>(cv), fmaf(mw_, static_cast<float>(cw), p0));
     cnt_u = static_cast<float>(u0) - 1.f;
   }
+  __device__ __forceinline__ void clip(float T, float& lo, float& hi) const { clip_half(mu_, imu_, base, T, lo, hi); }
+  __device__ __forceinline__ void seek(int u) { cnt_u = static_cast<float>(u) - 1.f; }
   __device__ __forceinline__ float counter() const { return cnt_u; }
   __device__ __forceinline__ int origin() const { return 0; }
   __device__ __forceinline__ float phi() {
@@ -403,6 +471,7 @@ __device__ __forceinline__ void begin_line_of(E& e, const PairRec&, bool, const 
 struct Partial {
   float cnt, mx, my, mz, gx, gy, gz, bestf;
   int bestidx;
+  bool touched;   // warp-uniform: some lane evaluated a node (else every sum is zero)
 };
 
 // Order-preserving map of FP32 values to signed ints (for integer max).
@@ -412,11 +481,16 @@ __device__ __forceinline__ int float_key(float f) {
 }
 __device__ __forceinline__ float key_float(int k) { return __int_as_float(k >= 0 ? k : (k ^ 0x7fffffff)); }
 
-// `prefetch` runs once, after the first slot of the tile (it fetches the next
-// tile's record while this one runs).
-template <bool SMOOTH, class EA, class EB, class Pre>
+// Two phases per slot of 32 lines.  (A) Each lane clips its line to the
+// nodes where both distances lie below w/2 (+ the clip margin).  (B) The
+// warp's clipped nodes, typically a dozen spread over a few lines, are
+// numbered across the lanes (a scan of the counts) and each lane evaluates
+// one of them: its line is found by a binary search over the scan, the
+// evaluators restart on that line, and the node gets exactly the
+// arithmetic of a node walk (the same FP32 distances, bit for bit).
+template <bool SMOOTH, class EA, class EB>
 __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, const Parts& D, const PairRec& r,
-                                              bool swap, int tl, float4* smA, float4* smB, Pre& prefetch) {
+                                              bool swap, int tl, float4* smA, float4* smB) {
   const int lane = threadIdx.x & 31;
   const Local L = make_local(r);
   EA A;
@@ -424,75 +498,84 @@ __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, 
   A.load(r, swap, S, D, L, smA);
   B.load(r, !swap, S, D, L, smB);
   const int du = r.dim[L.u], dv = r.dim[L.v];
-  const int nseg = r.nseg, seglen = r.seglen;
-  const float inv_dv = 1.f / static_cast<float>(dv), inv_nseg = 1.f / static_cast<float>(nseg);
-  const float inv_w = P.inv_w, hw = 0.5f * P.wdx_l;
+  const float inv_dv = __fdividef(1.f, static_cast<float>(dv));
+  const float inv_w = P.inv_w, hw = 0.5f * P.wdx_l, T = hw + kClipMargin;
   float cnt = 0.f, mu = 0.f, mv = 0.f, mw = 0.f, bestf = -FLT_MAX;
   int bestidx = 0x7fffffff;
+  bool touched = false;
   const int it0 = tl * 32 * kTileItemsPerLane;
   for (int s = 0; s < kTileItemsPerLane; ++s) {
     const int itb = it0 + s * 32;
     if (itb >= r.nitems) break;
-    if (s == 1) prefetch();
+    // (A) this lane's line it = cw * dv + cv, clipped to [ub, ub + nk)
     const int it = itb + lane;
-    const bool valid = it < r.nitems;
-    int seg, cv;
-    const int line = div_small(it, nseg, inv_nseg, &seg);
-    const int cw = div_small(line, dv, inv_dv, &cv);
-    const int u0 = seg * seglen;
-    const int len = valid ? min(seglen, du - u0) : 0;
-    begin_line_of(A, r, swap, L, cv, cw, u0, 0);
-    begin_line_of(B, r, !swap, L, cv, cw, u0, 0);
-    float cl = 0.f, ml = 0.f, bfl = -FLT_MAX;
-    int bul = 0;
-#pragma unroll 2
-    for (int k = 0; k < seglen; ++k) {
+    int cv;
+    const int cw = div_small(it, dv, inv_dv, &cv);
+    const int len = it < r.nitems ? du : 0;
+    begin_line_of(A, r, swap, L, cv, cw, 0, 0);
+    begin_line_of(B, r, !swap, L, cv, cw, 0, 0);
+    float clo = 0.f, chi = static_cast<float>(len - 1);
+    A.clip(T, clo, chi);
+    B.clip(T, clo, chi);
+    int ub;
+    const int nk = clip_nodes(clo, chi, 0, len, &ub);
+    int incl = nk;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(kFull, incl, d);
+      if (lane >= d) incl += v;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) continue;
+    touched = true;
+    const int excl = incl - nk;
+    // (B) node g of the warp's clipped nodes on lane g mod 32
+    for (int base = 0; base < total; base += 32) {
+      const int g = base + lane;
+      int o = 0;   // owner: the last lane whose first node is <= g
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int e = __shfl_sync(kFull, excl, o + step);
+        if (e <= g) o += step;
+      }
+      const int ocv = __shfl_sync(kFull, cv, o), ocw = __shfl_sync(kFull, cw, o);
+      const int u = __shfl_sync(kFull, ub, o) + (g - __shfl_sync(kFull, excl, o));
+      begin_line_of(A, r, swap, L, ocv, ocw, u, 0);
+      begin_line_of(B, r, !swap, L, ocv, ocw, u, 0);
       const float fa = A.phi();
       const float fb = B.phi();
-      const float hi = fmaxf(fa, fb);
       // W > 0, or a band term of the normal: max < w/2 and (sharp) min <= 0
-      const bool any = (k < len) && hi < hw && (SMOOTH || fminf(fa, fb) <= 0.f);
-      if (__any_sync(kFull, any)) {
-        const float ta = __saturatef(fmaf(fa, -inv_w, 0.5f));
-        const float tb = __saturatef(fmaf(fb, -inv_w, 0.5f));
-        float w, ma, mb;
-        if (SMOOTH) {
-          const float ha = ta * ta * fmaf(-2.f, ta, 3.f);
-          const float hb = tb * tb * fmaf(-2.f, tb, 3.f);
-          w = any ? ha * hb : 0.f;
-          ma = any ? fmaf(-ta, ta, ta) * hb : 0.f;
-          mb = any ? ha * fmaf(-tb, tb, tb) : 0.f;
-        } else {
-          w = (any && hi <= 0.f) ? 1.f : 0.f;
-          ma = (any && fb <= 0.f) ? fmaf(-ta, ta, ta) : 0.f;
-          mb = (any && fa <= 0.f) ? fmaf(-tb, tb, tb) : 0.f;
-        }
-        cl += w;
-        ml = fmaf(w, A.counter(), ml);   // sum of W (cu - iu_A)
-        const float f = -(fa + fb);
-        if (w > 0.f && f > bfl) {
-          bfl = f;
-          bul = u0 + k;
-        }
-        A.grad(ma);
-        B.grad(mb);
+      const bool any = g < total && fmaxf(fa, fb) < hw && (SMOOTH || fminf(fa, fb) <= 0.f);
+      const float ta = __saturatef(fmaf(fa, -inv_w, 0.5f));
+      const float tb = __saturatef(fmaf(fb, -inv_w, 0.5f));
+      float w, ma, mb;
+      if (SMOOTH) {
+        const float ha = ta * ta * fmaf(-2.f, ta, 3.f);
+        const float hb = tb * tb * fmaf(-2.f, tb, 3.f);
+        w = any ? ha * hb : 0.f;
+        ma = any ? fmaf(-ta, ta, ta) * hb : 0.f;
+        mb = any ? ha * fmaf(-tb, tb, tb) : 0.f;
+      } else {
+        w = (any && fmaxf(fa, fb) <= 0.f) ? 1.f : 0.f;
+        ma = (any && fb <= 0.f) ? fmaf(-ta, ta, ta) : 0.f;
+        mb = (any && fa <= 0.f) ? fmaf(-tb, tb, tb) : 0.f;
       }
-    }
-    A.end_line();
-    B.end_line();
-    cnt += cl;
-    mu = fmaf(cl, static_cast<float>(A.origin()), mu + ml);
-    mv = fmaf(cl, static_cast<float>(cv), mv);
-    mw = fmaf(cl, static_cast<float>(cw), mw);
-    if (bfl > -FLT_MAX) {
-      const int idx = bul * L.su + cv * L.sv + cw * L.sw;
-      if (bfl > bestf || (bfl == bestf && idx < bestidx)) {
-        bestf = bfl;
+      cnt += w;
+      mu = fmaf(w, static_cast<float>(u), mu);
+      mv = fmaf(w, static_cast<float>(ocv), mv);
+      mw = fmaf(w, static_cast<float>(ocw), mw);
+      const float f = -(fa + fb);
+      const int idx = u * L.su + ocv * L.sv + ocw * L.sw;
+      if (w > 0.f && (f > bestf || (f == bestf && idx < bestidx))) {
+        bestf = f;
         bestidx = idx;
       }
+      A.grad(ma);
+      B.grad(mb);
+      A.end_line();
+      B.end_line();
     }
   }
-  if (kTileItemsPerLane < 2 || it0 + 32 >= r.nitems) prefetch();   // tiles with a single slot
   Partial o;
   o.cnt = cnt;
   o.mx = world_comp(0, L, mu, mv, mw);
@@ -503,6 +586,7 @@ __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, 
   o.gz = A.world(2, L, r, swap) - B.world(2, L, r, !swap);
   o.bestf = bestf;
   o.bestidx = bestidx;
+  o.touched = touched;
   return o;
 }
 
@@ -542,6 +626,12 @@ __device__ __forceinline__ float reduce_tile(const Partial& o) {
   return v;   // lane c < 9: component c of the tile partial
 }
 
+// The partial of a tile in which no node was evaluated: zero sums, no deepest node.
+__device__ __forceinline__ float empty_partial() {
+  const int lane = threadIdx.x & 31;
+  return lane == 7 ? -FLT_MAX : (lane == 8 ? __int_as_float(0x7fffffff) : 0.f);
+}
+
 // The force law of the n <= 8 overlapping pairs staged in ov (whole warp).
 template <int SET, bool LAW>
 __device__ __forceinline__ void flush_overlaps(const Params& P, const Shapes& S, const Parts& D, const Lists& W,
@@ -573,25 +663,22 @@ __device__ __forceinline__ void flush_overlaps(const Params& P, const Shapes& S,
 
 // End of a pair (called by the whole warp once all its nodes are summed):
 // lanes c < 7 hold the FP64 sum of component c, every lane the deepest node.
-// A pair without overlap gets its zero outputs; an overlapping pair is
-// appended to the step's overlap list, whose force law the next kernel runs
-// eight pairs per warp pass.
+// A pair without overlap gets its zero outputs; an overlapping pair's sums go
+// to its entry of the overlap list, flagged for the force law (the next
+// kernel gathers the flagged entries, eight pairs per warp pass).
 __device__ __forceinline__ void pair_done(const Params& P, const Lists& W, const PairRec& r, double* pair_out,
                                           double sv, int idx) {
   const int lane = threadIdx.x & 31;
   const int q = r.pair;
   const double s0 = __shfl_sync(kFull, sv, 0);
-  if (__double_as_longlong(s0) > 0) {   // V > 0
-    int slot = 0;
-    if (lane == 0) slot = atomicAdd(&W.counters[5], 1);
-    slot = __shfl_sync(kFull, slot, 0);
-    if (slot < P.max_pairs) {
-      OvlRec* e = W.olist + slot;
-      if (lane < 7) e->s[lane] = sv;
-      if (lane == 7) e->q = q;
-      if (lane == 8) e->idx = idx;
-      if (lane >= 9 && lane < 20) (&e->i)[lane - 9] = reinterpret_cast<const int*>(&r)[lane - 9];   // i, j, lo, dim, shift
-    }
+  const bool hit = __double_as_longlong(s0) > 0;   // V > 0
+  if (lane == 31) W.oflag[q] = hit ? 1 : 0;
+  if (hit) {
+    OvlRec* e = W.olist + q;
+    if (lane < 7) e->s[lane] = sv;
+    if (lane == 7) e->q = q;
+    if (lane == 8) e->idx = idx;
+    if (lane >= 9 && lane < 20) (&e->i)[lane - 9] = reinterpret_cast<const int*>(&r)[lane - 9];   // i, j, lo, dim, shift
   } else {
     if (lane < 11) pair_out[static_cast<size_t>(q) * 11 + lane] = 0.0;
     if (lane < kFtDoubles) W.ft[static_cast<size_t>(q) * kFtDoubles + lane] = 0.0;
@@ -656,6 +743,7 @@ __device__ __forceinline__ void tile_done(const Params& P, const Lists& W, const
     const int oi = __shfl_xor_sync(kFull, bi, o);
     if (ob > bf || (ob == bf && oi < bi)) { bf = ob; bi = oi; }
   }
+  if (lane == 0) W.pdone[r.pair] = 0;   // ready for a repeated sweep of the same tiles
   pair_done(P, W, r, pair_out, acc, __shfl_sync(kFull, bi, 7));
 }
 
@@ -663,9 +751,9 @@ __device__ __forceinline__ void tile_done(const Params& P, const Lists& W, const
 // (chosen at init when no polytope is present; fewer registers, no spills).
 enum KindSet : int { SET_ALL = 0, SET_SC = 1, SET_CUBE = 2 };
 
-template <bool SMOOTH, int SET, class Pre>
+template <bool SMOOTH, int SET>
 __device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, const Parts& D, const PairRec& r,
-                                            int tl, float4* smA, float4* smB, Pre& pre) {
+                                            int tl, float4* smA, float4* smB) {
   // kind order for canonical pairs: wall < sphere < cube < cuboid < polytope < large polytope
   constexpr int rank[6] = {1, 3, 4, 5, 2, 0};
   int ka = r.kinds & 0xff, kb = r.kinds >> 8;
@@ -677,13 +765,13 @@ __device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, co
     ka = ka == KIND_CUBE ? KIND_CUBOID : ka;
     kb = kb == KIND_CUBE ? KIND_CUBOID : kb;
   }
-  Partial o{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -FLT_MAX, 0x7fffffff};
+  Partial o{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -FLT_MAX, 0x7fffffff, false};
 #define GBC_CASE(KA, KB, TA, TB)                                                  \
   case (KA) * 8 + (KB):                                                          \
-    o = sweep_tile<SMOOTH, TA, TB>(P, S, D, r, swap, tl, smA, smB, pre);         \
+    o = sweep_tile<SMOOTH, TA, TB>(P, S, D, r, swap, tl, smA, smB);              \
     break;
   if constexpr (SET == SET_CUBE) {
-    o = sweep_tile<SMOOTH, CubeEval, CubeEval>(P, S, D, r, swap, tl, smA, smB, pre);
+    o = sweep_tile<SMOOTH, CubeEval, CubeEval>(P, S, D, r, swap, tl, smA, smB);
   } else if constexpr (SET == SET_SC) {
     switch (ka * 8 + kb) {
       GBC_CASE(0, 0, SphereEval, SphereEval)
@@ -696,7 +784,6 @@ __device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, co
       GBC_CASE(5, 4, WallEval, CubeEval)
       GBC_CASE(5, 1, WallEval, CuboidEval)
       default:
-        pre();
         break;
     }
   } else {
@@ -716,7 +803,6 @@ __device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, co
       GBC_CASE(5, 2, WallEval, PolyEval<kRegFaces>)
       GBC_CASE(5, 3, WallEval, PolyGEval)
       default:
-        pre();
         break;
     }
   }
@@ -735,55 +821,33 @@ __device__ __forceinline__ void store_rec_part(PairRec* dst, int lane, int4 v) {
   if (lane < kPairRecWords / 4) reinterpret_cast<int4*>(dst)[lane] = v;
 }
 
+// Blocks per SM: 3 for the sphere/cuboid/cube variants (<= 85 registers, so
+// 24 warps per SM: about one tile per warp at a settling box's size), 2 for
+// the variant with polytopes (the registers of their face values).
 template <bool SMOOTH, int SET>
-__global__ void __launch_bounds__(kWarps * 32, 2) k_narrow32(Params P, Shapes S, Parts D,
+__global__ void __launch_bounds__(kWarps * 32, SET == 0 ? 2 : 3) k_narrow32(Params P, Shapes S, Parts D,
                                                                                   Lists W, const double* vel,
                                                                                   double* pair_out) {
   __shared__ __align__(16) PairRec s_rec[kWarps][2];
-  __shared__ float4 s_planes[kWarps][2][kMaxFaces];
+  __shared__ float4 s_planes[kWarps][2][kMaxFaces + kMaxFaces / 4];   // planes, then their inverse slopes
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int ntiles = W.counters[1];
-  if (ntiles > P.max_tiles) return;   // capacity exceeded: the step reports ECAPACITY
-  // queue position -> record: buckets of decreasing cost, one after the other
-  int bend[kCostBuckets];
-  {
-    int acc = 0;
-#pragma unroll
-    for (int b = 0; b < kCostBuckets; ++b) {
-      acc += W.counters[8 + b];
-      bend[b] = acc;
-    }
-  }
-  auto rec_at = [&](int q) -> const PairRec* {
-    int b = 0, start = 0;
-#pragma unroll
-    for (int k = 0; k < kCostBuckets - 1; ++k) {
-      if (q >= bend[k]) { b = k + 1; start = bend[k]; }
-    }
-    return W.tiles + static_cast<size_t>(b) * P.max_tiles + (q - start);
-  };
-  // first tile: the warp's global index; later tiles from the queue
+  // tiles w, w + W, ... of the list (W warps); the first record is fetched
+  // with the tile count, the next one while a tile runs
   const int nwarps = gridDim.x * kWarps;
   int t = blockIdx.x * kWarps + wid;
-  if (t < ntiles) store_rec_part(&s_rec[wid][0], lane, load_rec_part(rec_at(t), lane));
+  const int4 first = t < P.max_tiles ? load_rec_part(W.tiles + t, lane) : make_int4(0, 0, 0, 0);
+  if (ntiles > P.max_tiles) return;   // capacity exceeded: the step reports ECAPACITY
+  if (t < ntiles) store_rec_part(&s_rec[wid][0], lane, first);
   __syncwarp();
   int buf = 0;
   while (t < ntiles) {
-    int tn = 0;
-    if (lane == 0) tn = atomicAdd(&W.counters[2], 1) + nwarps;  // next tile, fetched ahead
-    int4 next = make_int4(0, 0, 0, 0);
-    bool fetched = false;
-    auto prefetch = [&]() {
-      if (fetched) return;
-      fetched = true;
-      tn = __shfl_sync(kFull, tn, 0);
-      if (tn < ntiles) next = load_rec_part(rec_at(tn), lane);
-    };
+    const int tn = t + nwarps;
+    const int4 next = tn < ntiles ? load_rec_part(W.tiles + tn, lane) : make_int4(0, 0, 0, 0);
     const PairRec& r = s_rec[wid][buf];
-    const Partial o = dispatch<SMOOTH, SET>(P, S, D, r, r.tile, s_planes[wid][0], s_planes[wid][1], prefetch);
-    prefetch();
-    tile_done(P, W, r, pair_out, reduce_tile<SMOOTH>(o));
+    const Partial o = dispatch<SMOOTH, SET>(P, S, D, r, r.tile, s_planes[wid][0], s_planes[wid][1]);
+    tile_done(P, W, r, pair_out, o.touched ? reduce_tile<SMOOTH>(o) : empty_partial());
     __syncwarp();
     if (tn < ntiles) store_rec_part(&s_rec[wid][buf ^ 1], lane, next);
     __syncwarp();
@@ -793,31 +857,44 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_narrow32(Params P, Shapes S,
   (void)vel;   // the velocities enter with the force law (next kernel)
 }
 
-// The force law of the step's overlapping pairs (the overlap list), eight per
-// warp pass (four lanes each).  Batch b goes to block b mod grid, so the FP64
-// passes spread over the SMs instead of meeting at the sweep's tail.
+// The force law of the step's overlapping pairs, eight per warp pass (four
+// lanes each).  Warp w takes the pairs 32 c .. 32 c + 31 of chunks c = w,
+// w + W, ...: one flag load per lane, a ballot, and the flagged entries of
+// the overlap list staged eight at a time; each warp adds its count of
+// overlapping pairs to counters[5] (reported by contact_stats).
 template <int SET, bool LAW>
 __global__ void __launch_bounds__(kWarps * 32) k_force(Params P, Shapes S, Parts D, Lists W, const double* vel,
                                                        double* pair_out) {
   __shared__ __align__(16) OvlRec s_ovl[kWarps][kForcePairsPerPass];
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nov = min(W.counters[5], P.max_pairs);
-  const int nb = (nov + kForcePairsPerPass - 1) / kForcePairsPerPass;
-  for (int b = wid * gridDim.x + blockIdx.x; b < nb; b += gridDim.x * kWarps) {
-    const int first = b * kForcePairsPerPass, n = min(kForcePairsPerPass, nov - first);
-    // stage the batch: 8 records x 128 bytes, two 16-byte pieces per lane
-    const int4* src = reinterpret_cast<const int4*>(W.olist + first);
-    int4* dst = reinterpret_cast<int4*>(s_ovl[wid]);
-    constexpr int kPieces = static_cast<int>(sizeof(OvlRec) / 16);
+  if (W.counters[1] > P.max_tiles) return;   // the node sweep did not run (ECAPACITY)
+  const int np = min(W.counters[0], P.max_pairs);
+  const int nchunk = (np + 31) / 32;
+  int nov = 0;
+  for (int c = wid * gridDim.x + blockIdx.x; c < nchunk; c += gridDim.x * kWarps) {
+    const int q = 32 * c + lane;
+    unsigned mask = __ballot_sync(kFull, q < np && W.oflag[q] != 0);
+    nov += __popc(mask);
+    while (mask != 0u) {
+      const int n = min(__popc(mask), kForcePairsPerPass);
+      // stage the batch: n records x 128 bytes, two 16-byte pieces per lane
+      int4* dst = reinterpret_cast<int4*>(s_ovl[wid]);
+      constexpr int kPieces = static_cast<int>(sizeof(OvlRec) / 16);
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int e = lane + 32 * u;
-      if (e < n * kPieces) dst[e] = src[e];
+      for (int u = 0; u < 2; ++u) {
+        const int e = lane + 32 * u, k = e / kPieces;
+        if (k < n) {
+          const int src = 32 * c + __fns(mask, 0, k + 1);   // the (k+1)-th flagged pair of the chunk
+          dst[e] = reinterpret_cast<const int4*>(W.olist + src)[e - k * kPieces];
+        }
+      }
+      for (int k = 0; k < n; ++k) mask &= mask - 1;
+      __syncwarp();
+      flush_overlaps<SET, LAW>(P, S, D, W, vel, pair_out, s_ovl[wid], n);
     }
-    __syncwarp();
-    flush_overlaps<SET, LAW>(P, S, D, W, vel, pair_out, s_ovl[wid], n);
   }
+  if (lane == 0 && nov > 0) atomicAdd(&W.counters[5], nov);
 }
 
 // ---------------------------------------------------------------- FP64 form

@@ -18,6 +18,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <cuda.h>   // CUcontext (types only; cuCtxGetCurrent is reached through the runtime)
+
 #include "../../include/contact.h"
 #include "contact_dev.cuh"
 
@@ -27,22 +29,46 @@ namespace {
 
 constexpr size_t kScratchBytes = static_cast<size_t>(CONTACT_NOALLOC_SCRATCH_MIB) << 20;
 constexpr int kMaxNbr = 64;
-constexpr int kMaxTilesPerPair = 2;
-constexpr int kMaxBinsPerAxis = 32;
+constexpr int kMaxTilesPerPair = CONTACT_NOALLOC_TILES_PER_PAIR;
+constexpr int kMaxBinsPerAxis = CONTACT_NOALLOC_MAX_BINS;
 
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Per-device address of g_scratch (host code may not use the symbol itself).
+// Per-device address of g_scratch (host code may not use the symbol itself),
+// with the context it belongs to: a device reset destroys the primary
+// context and the module with it, and the next call, in a new context,
+// looks the address up again.
 std::mutex g_mutex;
 unsigned char* g_addr[64] = {};
+CUcontext g_ctx[64] = {};
+
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+
+CUcontext current_context() {
+  static const CtxGetCurrent fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return static_cast<CtxGetCurrent>(nullptr);
+    return reinterpret_cast<CtxGetCurrent>(p);
+  }();
+  CUcontext c = nullptr;
+  if (fn == nullptr || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
 
 contact_status scratch_address(int dev, unsigned char** out) {
   if (dev < 0 || dev >= 64) return CONTACT_ECUDA;
+  // the device's primary context, current (cudaSetDevice initialises it)
+  if (cudaSetDevice(dev) != cudaSuccess) return CONTACT_ECUDA;
+  const CUcontext ctx = current_context();
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (g_addr[dev] == nullptr) {
+  if (g_addr[dev] == nullptr || ctx == nullptr || ctx != g_ctx[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess) return CONTACT_ECUDA;
     g_addr[dev] = static_cast<unsigned char*>(p);
+    g_ctx[dev] = ctx;
   }
   *out = g_addr[dev];
   return CONTACT_OK;
@@ -73,13 +99,14 @@ __global__ void k_noalloc_prep(Params P, int* type, int* kind, double* param, fl
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < P.n) {
     const int ty = type[t];
-    compl_[t] = (1.0 - poisson[t] * poisson[t]) / young[t];
+    // the same rounded operations as contact_init's host code (no contraction)
+    compl_[t] = __ddiv_rn(__dsub_rn(1.0, __dmul_rn(poisson[t], poisson[t])), young[t]);
     for (int k = 0; k < 3; ++k) ext[3 * t + k] = (ty == 0 && k > 0) ? 0.0 : __dadd_rn(param[3 * t + k], P.delta);
     const double* q = param + 3 * t;
     kind[t] = ty == 0 ? KIND_SPHERE : ((q[0] == q[1] && q[0] == q[2]) ? KIND_CUBE : KIND_CUBOID);
     nomops[t] = ty == 0 ? 7 : 15;
     for (int k = 0; k < 3; ++k)
-      size_l[3 * t + k] = static_cast<float>((param[3 * t + k] + P.inflate) * P.inv_dx);
+      size_l[3 * t + k] = static_cast<float>(__ddiv_rn(__dadd_rn(param[3 * t + k], P.inflate), P.dx));
   }
   if (t <= P.n) {
     face_off[t] = 0;
@@ -153,7 +180,8 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
     P.binw[k] = P.L[k] / P.nbin[k];
     P.inv_binw_f[k] = static_cast<float>(P.nbin[k] / P.L[k]);
   }
-  P.bin_cap = bin_capacity(n, P.binw, rin_min, static_cast<long long>(P.nbin[0]) * P.nbin[1] * P.nbin[2], 1LL << 20);
+  P.bin_cap = bin_capacity(n, P.binw, rin_min, static_cast<long long>(P.nbin[0]) * P.nbin[1] * P.nbin[2],
+                           CONTACT_NOALLOC_MAX_BIN_ENTRIES);
   P.dx = C.dx;
   P.inv_dx = 1.0 / C.dx;
   {
@@ -229,8 +257,9 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   W.grp_sum = cv.take<int>((N + kRowGroup - 1) / kRowGroup);
   W.pairs = cv.take<PairRec>(MP);
   W.olist = cv.take<OvlRec>(MP);
+  W.oflag = cv.take<int>(MP);
   W.tile_pair = cv.take<int>(MT);
-  W.tiles = cv.take<PairRec>(MT * kCostBuckets);
+  W.tiles = cv.take<PairRec>(MT);
   W.partial = cv.take<float>(MT * kPartialFloats);
   W.pdone = cv.take<int>(MP);
   W.tape = cv.take<double>(MP * kTapeDoubles);
@@ -255,7 +284,7 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   // the step's kernels, unchanged, on the scratch array
   launch_pose(P, S, D, W, pos, quat, s);
   launch_broad(P, D, W, s);
-  launch_plan(P, S, D, W, pair_ij, n_pairs, s);
+  launch_plan(P, S, D, W, pair_ij, n_pairs, pair_out, s);
   launch_narrow(P, S, D, W, nullptr, pair_out, narrow_grid(P), s);
   launch_force(P, S, D, W, nullptr, pair_out, s);
   launch_particle_sum(P, D, W, force, torque, s);

@@ -37,11 +37,83 @@ class Report:
     cells: int
     flagged: int
     flips: int
-    max_err: dict
+    max_err: dict            # worst err / tol ratio per check (<= 1 passes)
+    rel: dict = dataclasses.field(default_factory=dict)   # achieved error per output (output_errors)
 
     def __str__(self):
         r = ", ".join(f"{k}={v:.2e}" for k, v in self.max_err.items())
-        return f"pairs={self.pairs} cells={self.cells} flagged={self.flagged} flips={self.flips} {r}"
+        e = ", ".join(f"{k}={v:.2e}" for k, v in self.rel.items())
+        return f"pairs={self.pairs} cells={self.cells} flagged={self.flagged} flips={self.flips} ratios: {r} | errors: {e}"
+
+
+# The bounds the benchmark spec fixes for the FP32-tile form: volume and first
+# moments 1e-6 relative, force and torque 1e-5 relative.
+FLAT = {"V": 1e-6, "M": 1e-6, "F_pair": 1e-5, "F": 1e-5, "T": 1e-5}
+
+
+def output_errors(st, g, r, clean, ro=None, r_force=None, r_torque=None) -> dict:
+    """Achieved error of each output against the oracle, over the pairs in
+    `clean` (unflagged) and the particles that only such pairs touch:
+      V       max |dV| / V                          (pairs with V > 0)
+      M       max |dM| / |M|, M = V (x_c - o) the first moments about the
+              box origin o (|M| floored at V dx)
+      x_c     max |dx_c| / dx                       (absolute, cells)
+      n       max |dn|                              (unit vector)
+      d       max |dd| / d
+      F_pair  max |dF| / |F|                        (pairs with F != 0)
+      F, T    per particle max |dF_p| / sum |F_pair| and |dT_p| / sum |F_pair| |arm|
+              over its pairs (the scale of the sum, which may cancel)."""
+    ro = r.pair_out if ro is None else ro
+    r_force = r.force if r_force is None else r_force
+    r_torque = r.torque if r_torque is None else r_torque
+    go = g["pair_out"]
+    dx = st.dx
+    V = ro[:, 0]
+    hit = clean & (V > 0)
+    out = {}
+
+    def worst(x):
+        return float(np.max(x, initial=0.0))
+
+    out["V"] = worst(np.abs(go[hit, 0] - V[hit]) / V[hit])
+    o = r.pair_box[:, :3] * dx
+    Mr = V[:, None] * (ro[:, 1:4] - o)
+    Mg = go[:, 0:1] * (go[:, 1:4] - o)
+    den = np.maximum(np.linalg.norm(Mr, axis=1), V * dx)
+    out["M"] = worst(np.linalg.norm(Mg[hit] - Mr[hit], axis=1) / den[hit])
+    out["x_c"] = worst(np.linalg.norm(go[hit, 1:4] - ro[hit, 1:4], axis=1) / dx)
+    out["n"] = worst(np.linalg.norm(go[hit, 4:7] - ro[hit, 4:7], axis=1))
+    dpos = hit & (ro[:, 7] > 0)
+    out["d"] = worst(np.abs(go[dpos, 7] - ro[dpos, 7]) / ro[dpos, 7])
+    Fs = np.linalg.norm(ro[:, 8:11], axis=1)
+    fh = hit & (Fs > 0)
+    out["F_pair"] = worst(np.linalg.norm(go[fh, 8:11] - ro[fh, 8:11], axis=1) / Fs[fh])
+    nrow = st.n + len(getattr(st, "walls", ()))
+    pos_w = np.concatenate([st.pos, np.zeros((nrow - st.n, 3))])
+    XA = pos_w[r.pair_ij[:, 0]]
+    XB = pos_w[r.pair_ij[:, 1]] - r.pair_shift * st.box
+    armA = np.linalg.norm(ro[:, 1:4] - XA, axis=1)
+    armB = np.linalg.norm(ro[:, 1:4] - XB, axis=1)
+    sF = np.zeros(nrow)
+    sT = np.zeros(nrow)
+    dirty = np.zeros(nrow, bool)
+    dirty[r.pair_ij[~clean].ravel()] = True
+    for col, arm in ((0, armA), (1, armB)):
+        np.add.at(sF, r.pair_ij[:, col], Fs)
+        np.add.at(sT, r.pair_ij[:, col], Fs * arm)
+    sF, sT, dirty = sF[:st.n], sT[:st.n], dirty[:st.n]
+    okF = ~dirty & (sF > 0)
+    out["F"] = worst(np.linalg.norm(g["force"][okF] - r_force[okF], axis=1) / sF[okF])
+    okT = ~dirty & (sT > 0)
+    out["T"] = worst(np.linalg.norm(g["torque"][okT] - r_torque[okT], axis=1) / sT[okT])
+    return out
+
+
+def assert_flat(rep: Report, bounds=None):
+    """Assert the benchmark spec's flat relative bounds on the achieved errors."""
+    bounds = FLAT if bounds is None else bounds
+    for k, b in bounds.items():
+        assert rep.rel[k] <= b, f"{k}: achieved error {rep.rel[k]:.3e} above the bound {b:.0e} ({rep})"
 
 
 def gpu_step(model, st, pos=None, quat=None, vel=None):
@@ -168,4 +240,5 @@ def compare(st, g, r, fp64: bool, smooth: bool, forces=None, tol_force=None, box
     _check("T", np.abs(g["torque"][ok] - r_torque[ok]).max(axis=1, initial=0), tT[ok] + 1e-12 * sT[ok], out)
     none = ~ok & ~touched_flag
     assert np.all(g["force"][none] == 0.0) and np.all(g["torque"][none] == 0.0)
-    return Report(r.n_pairs, r.cells, int(flagged.sum()), int(flips.sum()), out)
+    rel = output_errors(st, g, r, clean & ~skipF, ro, r_force, r_torque)
+    return Report(r.n_pairs, r.cells, int(flagged.sum()), int(flips.sum()), out, rel)

@@ -34,6 +34,23 @@ def _scale(gp, gq):
     return max(np.abs(gp).max(), np.abs(gq).max())
 
 
+# Per-component bound: |g - g_ref| <= REL |g_ref| + FLOOR max|g_ref|.  REL is
+# the benchmark spec's 1e-4; the floor covers components that are sums of
+# cancelling pair terms, whose absolute FP32 error stays at the scale of the
+# terms rather than of the result.
+REL, FLOOR = 1e-4, 1e-6
+
+
+def _per_component(g, ref, s):
+    """Worst err / (REL |ref| + FLOOR s) and percentiles of the relative error."""
+    g, ref = np.ravel(g), np.ravel(ref)
+    d = np.abs(g - ref)
+    ratio = d / (REL * np.abs(ref) + FLOOR * s)
+    big = np.abs(ref) > 1e-3 * s
+    rel = d[big] / np.abs(ref[big])
+    return ratio.max(initial=0.0), (np.percentile(rel, [50, 99, 100]) if rel.size else [0, 0, 0])
+
+
 @pytest.mark.parametrize("name", ["mixed27", "cubes1934", "mixed1934"])
 def test_adjoint_matches_oracle_gradient(name):
     """mixed27: spheres and cubes; cubes1934: cubes only; mixed1934: spheres,
@@ -45,8 +62,13 @@ def test_adjoint_matches_oracle_gradient(name):
     rp, rq = oracle.gradient(st, gf, gt)
     s = _scale(rp, rq)
     err = max(np.abs(gp - rp).max(), np.abs(gq - rq).max()) / s
-    print(name, "adjoint vs oracle gradient: max |diff| / max |grad| =", err)
+    worst, pct = _per_component(np.concatenate([gp.ravel(), gq.ravel()]),
+                                np.concatenate([rp.ravel(), rq.ravel()]), s)
+    print(name, "adjoint vs oracle gradient: max |diff| / max |grad| =", err,
+          "| per component: worst err / (1e-4 |g| + 1e-6 max|g|) =", worst,
+          "| relative error of components above 1e-3 max|g| (median, 99 %, max):", pct)
     assert err <= 1e-4
+    assert worst <= 1.0
     # quaternion gradient orthogonal to the quaternion
     assert np.abs(np.einsum("ij,ij->i", gq, st.quat)).max() <= 1e-9 * s
 
@@ -112,11 +134,20 @@ def test_adjoint_matches_central_differences_on_subblock():
     # on a smooth stencil; stencils with |D+ - D-| > 1e-2 max|grad| are
     # excluded as well.
     smooth = (np.abs(fd - fd2) <= 5e-5 * s) & (np.abs(dpm) <= 1e-2 * s)
+    # per component on the smooth stencils: |ad - fd| <= 1e-4 |fd| + E + 1e-6 max|grad|,
+    # E the stencil's own uncertainty: a jump moves FD(h) by at most
+    # 2 |FD(h) - FD(h/2)| (above), a slope kink near the centre by at most
+    # |D+ - D-| / 2 (both central differences then carry half the slope jump)
+    E = np.maximum(2 * np.abs(fd - fd2), 0.5 * np.abs(dpm))
+    pc = np.abs(fd - ad) / (REL * np.abs(fd) + E + FLOOR * s)
+    w = np.argmax(np.where(smooth, pc, 0))
+    print("worst smooth stencil: fd", fd[w], "fd(h/2)", fd2[w], "D+ - D-", dpm[w], "adjoint", ad[w], "max|g|", s)
     print("adjoint vs central differences (h = 1e-4): smooth stencils", smooth.sum(), "of", len(fd),
-          "| on them: median", np.median(err[smooth]), "max", err[smooth].max(),
-          "| all: fraction within 1e-4", np.mean(err <= 1e-4))
+          "(excluded as non-smooth:", int((~smooth).sum()), ") | on them: median", np.median(err[smooth]),
+          "max", err[smooth].max(), "| per component worst |ad - fd| / (1e-4 |fd| + E + 1e-6 max|g|) =",
+          pc[smooth].max(), "| all: fraction within 1e-4", np.mean(err <= 1e-4))
     assert np.mean(smooth) >= 0.8
-    assert np.mean(err[smooth] <= 1e-4) >= 0.99
+    assert pc[smooth].max() <= 1.0
     assert np.median(err[smooth]) <= 1e-6
 
 

@@ -211,6 +211,33 @@ def test_graph_replay_and_repeat():
     m.close()
 
 
+def test_repeated_node_sweep_for_timing():
+    """narrow_events = K > 1 runs the node sweep K times between the timing
+    events; every run recomputes the same outputs from the same tiles (a pair
+    of several tiles resets its counter when it completes), so the step's
+    results are those of a plain step bit for bit, in both forms and both
+    indicators; box_mode 1 refuses it."""
+    from paper_2401_10878_gb300.contact import ContactError, EINVAL
+    for st in (W.mixed_settling(n=300, L=120), W.settling_cubes()):
+        for ind in (0, 1):
+            st.indicator = ind
+            for prec in (0, 1):
+                m = model_for(st, precision=prec)
+                a = gpu_step(m, st)
+                m.close()
+                m = model_for(st, precision=prec, narrow_events=3)
+                b = gpu_step(m, st)
+                assert m.narrow_time_ms() > 0.0
+                m.close()
+                for k in ("pair_ij", "pair_out", "force", "torque"):
+                    assert np.array_equal(a[k], b[k]), (st.name, ind, prec, k)
+    st = W.mixed_grid_27()
+    st.box_mode = 1
+    with pytest.raises(ContactError) as e:
+        model_for(st, narrow_events=2)
+    assert e.value.code == EINVAL
+
+
 def test_capacity_and_input_errors():
     from paper_2401_10878_gb300.contact import ContactError, ECAPACITY, EINVAL
     st = W.mixed_settling(n=300, L=120)
