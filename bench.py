@@ -130,7 +130,6 @@ def workload_state(args, rank: int):
 def workload_config(st, extra=None, name="cubes1934"):
     cfg = {"workload": WORKLOADS[name][0],
            "particles": st.n, "lattice": list(st.n_cells), "indicator": "smoothed" if st.indicator else "sharp",
-           "precision": "fp32 node tests, fp32 tile partials, fp64 pair/particle reductions",
            "pose_steps": "seeded increments dX~N(0,0.05), rot~N(0,0.01 rad)",
            "l2": "flushed (1 GiB write, > 129 MB L2) before every timed step; the host enqueues the step while the flush runs", "parallelism": "weak (one box per GPU)"}
     if extra:
@@ -216,6 +215,7 @@ def run_reference(args, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(st, None, args.workload),
+            "precision": "fp64 throughout (the oracle)",
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{args.steps} full contact steps of the workload (all pairs)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -223,14 +223,68 @@ def run_reference(args, ws, rank):
 
 
 # ---------------------------------------------------------------- our arm
-def cpu_baseline(st, pos, quat, budget_s):
+def output_errors(st, g, r):
+    """Achieved error of each output of the GPU step g against the oracle's
+    step r on the same pose, over the pairs the oracle does not flag (nodes
+    within 1e-5 cells of flipping, of switching the active face or the
+    deepest node) and the particles only such pairs touch: V, the first
+    moments about the box origin M = V (x_c - o), the normal n (absolute),
+    the depth d, the pair force and the particle sums F, T (relative to the
+    sum of the magnitudes they add up)."""
+    aux = r.pair_aux
+    gap = aux[:, 6]
+    clean = ~((aux[:, 4] > 0) | (aux[:, 5] > 0) | ((gap > 0) & (gap < 4e-5)))
+    go, ro = g["pair_out"], r.pair_out
+    if g["n_pairs"] != r.n_pairs or not np.array_equal(g["pair_ij"], r.pair_ij):
+        return {"pair_list": "differs"}
+    V = ro[:, 0]
+    hit = clean & (V > 0)
+
+    def worst(x):
+        return float(np.max(x, initial=0.0))
+
+    o = r.pair_box[:, :3] * st.dx
+    Mr = V[:, None] * (ro[:, 1:4] - o)
+    Mg = go[:, 0:1] * (go[:, 1:4] - o)
+    den = np.maximum(np.linalg.norm(Mr, axis=1), V * st.dx)
+    Fs = np.linalg.norm(ro[:, 8:11], axis=1)
+    fh = hit & (Fs > 0)
+    dpos = hit & (ro[:, 7] > 0)
+    XA = st.pos[r.pair_ij[:, 0]]
+    XB = st.pos[r.pair_ij[:, 1]] - r.pair_shift * st.box
+    arm = (np.linalg.norm(ro[:, 1:4] - XA, axis=1), np.linalg.norm(ro[:, 1:4] - XB, axis=1))
+    sF, sT = np.zeros(st.n), np.zeros(st.n)
+    dirty = np.zeros(st.n, bool)
+    dirty[r.pair_ij[~clean].ravel()] = True
+    for col in (0, 1):
+        np.add.at(sF, r.pair_ij[:, col], Fs)
+        np.add.at(sT, r.pair_ij[:, col], Fs * arm[col])
+    okF, okT = ~dirty & (sF > 0), ~dirty & (sT > 0)
+    return {"pair_list": "identical", "pairs_checked": int(hit.sum()), "pairs_flagged": int((~clean).sum()),
+            "V_rel": worst(np.abs(go[hit, 0] - V[hit]) / V[hit]),
+            "moments_rel": worst(np.linalg.norm(Mg[hit] - Mr[hit], axis=1) / den[hit]),
+            "x_c_abs_cells": worst(np.linalg.norm(go[hit, 1:4] - ro[hit, 1:4], axis=1) / st.dx),
+            "n_abs": worst(np.linalg.norm(go[hit, 4:7] - ro[hit, 4:7], axis=1)),
+            "d_rel": worst(np.abs(go[dpos, 7] - ro[dpos, 7]) / ro[dpos, 7]),
+            "F_pair_rel": worst(np.linalg.norm(go[fh, 8:11] - ro[fh, 8:11], axis=1) / Fs[fh]),
+            "F_rel": worst(np.linalg.norm(g["force"][okF] - r.force[okF], axis=1) / sF[okF]),
+            "T_rel": worst(np.linalg.norm(g["torque"][okT] - r.torque[okT], axis=1) / sT[okT]),
+            "bounds": {"V_rel": 1e-6, "moments_rel": 1e-6, "F_pair_rel": 1e-5, "F_rel": 1e-5, "T_rel": 1e-5}}
+
+
+def cpu_baseline(st, pos, quat, budget_s, gpu0=None):
+    """The oracle timed on the host cores; with gpu0 (the GPU step on pose 0)
+    also the achieved error of each output against the oracle's step on it."""
     import oracle
     oracle.build()
     threads = oracle.max_threads()
     cells, secs, steps = 0, 0.0, 0
+    errors = None
     t_end = time.perf_counter() + budget_s
     while steps < 3 or (time.perf_counter() < t_end and steps < len(pos)):
         r = oracle.contact_step(st, pos=pos[steps % len(pos)], quat=quat[steps % len(quat)])
+        if steps == 0 and gpu0 is not None:
+            errors = output_errors(st.with_poses(pos[0], quat[0]), gpu0, r)
         cells += r.cells
         secs += r.seconds
         steps += 1
@@ -242,10 +296,11 @@ def cpu_baseline(st, pos, quat, budget_s):
         c1 += r.cells
         s1 += r.seconds
         n1 += 1
-    return {"value": cells / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
+    base = {"value": cells / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{steps} full contact steps of the workload ({cells} node evaluations), "
                       f"OpenMP over pairs", "ms_per_step": 1e3 * secs / steps,
             "one_thread": {"value": c1 / s1, "ms_per_step": 1e3 * s1 / n1, "steps": n1}}
+    return (base, errors) if gpu0 is not None else base
 
 
 def time_forward(model, pos_d, quat_d, steps, warmup, flush, narrow=False, vel_d=None):
@@ -360,17 +415,21 @@ def run_ours(args, ws, rank, local):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(st, {"pairs_per_step": stats["pairs"],
-                                           "cells_per_step": res["cells"] / args.steps,
-                                           "overlapping_pairs": stats["overlapping"],
-                                           "tiles_per_step": stats["tiles"], "narrow_grid": stats["narrow_grid"]},
-                                      args.workload),
+            "config": workload_config(st, None, args.workload),
+            "precision": "fp32 node tests, fp32 tile partials, fp64 pair/particle reductions",
+            "step_stats": {"pairs_per_step": stats["pairs"], "cells_per_step": res["cells"] / args.steps,
+                           "overlapping_pairs": stats["overlapping"], "tiles_per_step": stats["tiles"],
+                           "narrow_grid": stats["narrow_grid"]},
             "roofline": roofline, "e2e": e2e, "gpu_launches": model.kernels_per_step() * args.steps,
             "clocks": clocks,
             "ms_per_step_median": float(np.median(res["per"])),
             "ms_per_step_p10_p90": [float(np.percentile(res["per"], 10)), float(np.percentile(res["per"], 90))]}
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(st, pos, quat, args.cpu_seconds)
+        # one checked step outside the timed region: the first pose, whose
+        # oracle step the CPU leg runs first
+        ref_out = model.step(pos_d[0], quat_d[0])
+        gpu0 = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in ref_out.items()}
+        line["cpu_baseline"], line["errors"] = cpu_baseline(st, pos, quat, args.cpu_seconds, gpu0)
     if rank == 0 and not args.no_extras:
         line["extras"] = extras(args, dev, flush, peak)
     model.close()
@@ -449,10 +508,18 @@ def extras(args, dev, flush, peak):
     m = Contact.from_state(st, narrow_events=True)
     r = time_forward(m, torch.tensor(pos, device=dev), torch.tensor(quat, device=dev), steps, 3, flush, narrow=True)
     s = m.stats()
+    m.close()
+    # the node sweep's roofline on this workload: the mean of back-to-back runs (as the headline's)
+    m = Contact.from_state(st, narrow_events=NARROW_REPEAT)
+    rr = time_forward(m, torch.tensor(pos, device=dev), torch.tensor(quat, device=dev), steps, 3, flush, narrow=True)
+    achieved = rr["ops"] / (rr["narrow_ms"] * 1e-3) / 1e12
     out["mixed1934_223"] = {"cell_evals_per_s": r["cells"] / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / steps,
-                            "narrow_ms": r["narrow_ms"] / steps, "pairs": s["pairs"],
-                            "cells_per_step": r["cells"] / steps,
-                            "nominal_Tops_per_s": r["ops"] / (r["narrow_ms"] * 1e-3) / 1e12}
+                            "narrow_ms_single": r["narrow_ms"] / steps, "pairs": s["pairs"],
+                            "tiles_per_step": s["tiles"], "cells_per_step": r["cells"] / steps,
+                            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32 lane-ops/s",
+                                         "frac": achieved / peak, "launch_ms": rr["narrow_ms"] / steps,
+                                         "ops_per_launch": rr["ops"] / steps,
+                                         "timing": f"CUDA events around {NARROW_REPEAT} back-to-back node-sweep runs"}}
     out["mixed1934_223"]["box_volume_percentiles_10_50_90_99"] = box_volume_percentiles(m, st, st.pos)
     m.close()
     # all-FP64 one-pair-per-block form on the headline workload
@@ -463,6 +530,17 @@ def extras(args, dev, flush, peak):
     out["cubes1934_fp64_form"] = {"cell_evals_per_s": r["cells"] / (r["ms"] * 1e-3),
                                   "ms_per_step": r["ms"] / steps, "narrow_ms": r["narrow_ms"] / steps}
     m.close()
+    # its node sweep against the FP64 pipe: the same nominal lane-ops, in FP64, over the
+    # measured DFMA rate of this GPU
+    try:
+        from paper_2401_10878_gb300.contact import fp64_dfma_rate
+        dfma = fp64_dfma_rate() / 1e12
+        a64 = r["ops"] / (r["narrow_ms"] * 1e-3) / 1e12
+        out["cubes1934_fp64_form"]["roofline"] = {"bound": "fp64", "achieved": a64, "peak": dfma,
+                                                  "unit": "T FP64 lane-ops/s", "frac": a64 / dfma,
+                                                  "peak_basis": "measured DFMA rate (contact_fp64_dfma_rate)"}
+    except Exception as e:   # a measurement aid only
+        out["cubes1934_fp64_form"]["roofline_error"] = str(e)[:200]
     # the headline workload with velocities: shared damping, then contact history + friction
     # (timed like the other extras, with the library's events around the node sweep; the
     # first entry, without velocities, is the same timing of the headline step)
@@ -542,13 +620,13 @@ def extras(args, dev, flush, peak):
     # smoothed indicator: forward + adjoint
     st = W.settling_cubes_dense()
     pos, quat = W.pose_sequence(st, steps + 3)
-    m = Contact.from_state(st)
+    m = Contact.from_state(st, narrow_events=True)
     gf, gt = W.loss_weights(st.n)
     gf, gt = torch.tensor(gf, device=dev), torch.tensor(gt, device=dev)
     gp = torch.empty((st.n, 3), dtype=torch.float64, device=dev)
     gq = torch.empty((st.n, 4), dtype=torch.float64, device=dev)
     pd, qd = torch.tensor(pos, device=dev), torch.tensor(quat, device=dev)
-    fwd, bwd, cells = 0.0, 0.0, 0
+    fwd, bwd, cells, adj_ms, ops = 0.0, 0.0, 0, 0.0, 0
     import ctypes
     for k in range(steps + 3):
         with torch.cuda.stream(m.stream):
@@ -565,11 +643,22 @@ def extras(args, dev, flush, peak):
         if k >= 3:
             fwd += e0.elapsed_time(e1)
             bwd += e1.elapsed_time(e2)
-            cells += m.stats()["cells"]
+            st_ = m.stats()
+            cells += st_["cells"]
+            ops += st_["nominal_ops"]
+            adj_ms += m.adjoint_time_ms()
     m.check()
+    # the adjoint's cell sweep against the FP32 peak: the forward's nominal lane-ops of the
+    # two distance tests per node of every pair box (it sweeps the same nodes), over its
+    # event-timed duration (one launch between the events)
+    aa = ops / (adj_ms * 1e-3) / 1e12
     out["cubes1934_smooth_fwd_bwd"] = {"fwd_ms": fwd / steps, "bwd_ms": bwd / steps,
                                        "cell_evals_per_s_fwd_bwd": cells / ((fwd + bwd) * 1e-3),
-                                       "cells_per_step": cells / steps}
+                                       "cells_per_step": cells / steps,
+                                       "adjoint_cell_sweep": {"bound": "alu", "achieved": aa, "peak": peak,
+                                                              "unit": "T FP32 lane-ops/s", "frac": aa / peak,
+                                                              "launch_ms": adj_ms / steps,
+                                                              "timing": "CUDA events around its launch"}}
     m.close()
     return out
 

@@ -255,6 +255,12 @@ contact_status contact_stats(contact_ctx* ctx, int64_t* stats);
  * off. */
 contact_status contact_narrow_time(contact_ctx* ctx, float* ms);
 
+/* Synchronises, then writes the device time in milliseconds of the last
+ * contact_backward's node-level kernel (the adjoint's cell sweep), measured
+ * with CUDA events recorded around that launch when cfg.narrow_events is on.
+ * CONTACT_ESTATE before the first backward or with narrow_events off. */
+contact_status contact_adjoint_time(contact_ctx* ctx, float* ms);
+
 /* Per-particle node ranges (lo[3], hi[3]) [N,6] i32 dev of the last step. */
 contact_status contact_particle_boxes(contact_ctx* ctx, int32_t* lo_hi);
 
@@ -366,6 +372,17 @@ contact_status contact_step_noalloc(const contact_config* cfg, const int32_t* sh
  * CONTACT_EINVAL for a bad argument, CONTACT_ENOMEM / CONTACT_ECUDA on a CUDA
  * failure. */
 contact_status contact_fp32_ffma_rate(int32_t iters, double* ffma_per_s);
+
+/* Measurement utility (no counterpart in the paper): the FP64 DFMA rate of
+ * the current device, the measured peak of the all-FP64 comparison form.
+ * The same launch shape as contact_fp32_ffma_rate with FP64 chains (GB300's
+ * FP64 pipe is narrow: iters = 50 takes ~2 ms); synchronous, default stream,
+ * its own 2.5 MB scratch allocation.
+ *   iters        1 .. 2^20
+ *   dfma_per_s   host out: DFMA lane-operations per second
+ * CONTACT_EINVAL for a bad argument, CONTACT_ENOMEM / CONTACT_ECUDA on a CUDA
+ * failure. */
+contact_status contact_fp64_dfma_rate(int32_t iters, double* dfma_per_s);
 
 #ifdef __cplusplus
 }

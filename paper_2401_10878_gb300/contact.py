@@ -32,7 +32,8 @@ EXPORTS = ["contact_config_default", "contact_init", "contact_step", "contact_ba
            "contact_particle_boxes", "contact_narrow_time", "contact_damping_factor", "contact_kernels_per_step",
            "contact_kernels_per_backward", "contact_destroy", "contact_step_noalloc", "contact_step_host",
            "contact_history_get", "contact_history_set", "contact_history_reset", "contact_polytope_centroid",
-           "contact_polytope_shift", "contact_fp32_ffma_rate"]
+           "contact_polytope_shift", "contact_fp32_ffma_rate", "contact_fp64_dfma_rate",
+           "contact_adjoint_time"]
 
 
 class Config(ctypes.Structure):
@@ -93,6 +94,8 @@ def load_library(build_if_missing: bool = True):
     lib.contact_stats.restype = I32
     lib.contact_narrow_time.argtypes = [P, P]
     lib.contact_narrow_time.restype = I32
+    lib.contact_adjoint_time.argtypes = [P, P]
+    lib.contact_adjoint_time.restype = I32
     lib.contact_particle_boxes.argtypes = [P, P]
     lib.contact_particle_boxes.restype = I32
     lib.contact_damping_factor.argtypes = [D, D]
@@ -113,6 +116,8 @@ def load_library(build_if_missing: bool = True):
     lib.contact_polytope_shift.restype = I32
     lib.contact_fp32_ffma_rate.argtypes = [I32, P]
     lib.contact_fp32_ffma_rate.restype = I32
+    lib.contact_fp64_dfma_rate.argtypes = [I32, P]
+    lib.contact_fp64_dfma_rate.restype = I32
     lib.contact_history_get.argtypes = [P, ctypes.c_int64, P, P, P, P]
     lib.contact_history_get.restype = I32
     lib.contact_history_set.argtypes = [P, ctypes.c_int64, P, P, P]
@@ -333,6 +338,14 @@ class Contact:
                 "nominal_ops", "max_tiles"]
         return dict(zip(keys, [int(v) for v in s]))
 
+    def adjoint_time_ms(self) -> float:
+        """Device time of the last backward's cell-sweep kernel (CUDA events)."""
+        ms = ctypes.c_float()
+        rc = self.lib.contact_adjoint_time(self.ctx, ctypes.byref(ms))
+        if rc != OK:
+            self._raise(rc, "contact_adjoint_time")
+        return float(ms.value)
+
     def narrow_time_ms(self) -> float:
         """Device time of the last step's node-sweep kernel (CUDA events)."""
         ms = ctypes.c_float()
@@ -477,4 +490,15 @@ def fp32_ffma_rate(iters: int = 2000) -> float:
     rc = lib.contact_fp32_ffma_rate(int(iters), ctypes.byref(out))
     if rc != OK:
         raise ContactError(rc, "contact_fp32_ffma_rate")
+    return out.value
+
+
+def fp64_dfma_rate(iters: int = 50) -> float:
+    """Measured FP64 DFMA lane-operations per second of the current device
+    (contact_fp64_dfma_rate): the peak of the all-FP64 comparison form."""
+    lib = load_library()
+    out = ctypes.c_double()
+    rc = lib.contact_fp64_dfma_rate(int(iters), ctypes.byref(out))
+    if rc != OK:
+        raise ContactError(rc, "contact_fp64_dfma_rate")
     return out.value

@@ -359,6 +359,6 @@ void launch_particle_sum(const Params& P, const Parts& D, const Lists& W, double
 size_t adjoint_scratch_doubles(int max_pairs, int max_tiles);
 void launch_adjoint(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel,
                     const double* gF, const double* gT, double* gpos, double* gquat, double* scratch,
-                    int grid, cudaStream_t st);
+                    int grid, cudaStream_t st, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 
 }  // namespace gbc

@@ -35,6 +35,8 @@ struct contact_ctx {
   std::vector<double> shift;   // [N,3]: polytope body origins moved to the centroid by this
   int last_replay = 0;   // 0 instantiated (or no graph), 1 replayed, 2 replayed after an in-place update
   cudaEvent_t ev_narrow[2] = {nullptr, nullptr};
+  cudaEvent_t ev_adj[2] = {nullptr, nullptr};
+  bool have_backward = false;
   // contact_step_host: device staging buffers and their own graph cache
   double *hs_pos = nullptr, *hs_quat = nullptr, *hs_vel = nullptr, *hs_force = nullptr, *hs_torque = nullptr;
   double* hs_pair_out = nullptr;
@@ -645,6 +647,8 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   if (C.history) GBC_TRY(cudaMemset(W.hist_n, 0, sizeof(int) * 2 * n));
   GBC_TRY(cudaEventCreate(&c->ev_narrow[0]));
   GBC_TRY(cudaEventCreate(&c->ev_narrow[1]));
+  GBC_TRY(cudaEventCreate(&c->ev_adj[0]));
+  GBC_TRY(cudaEventCreate(&c->ev_adj[1]));
   GBC_TRY(cudaHostAlloc(reinterpret_cast<void**>(&c->err_host), sizeof(int), cudaHostAllocMapped));
   *c->err_host = 0;
   int* err_dev_view = nullptr;
@@ -905,10 +909,22 @@ contact_status contact_backward(contact_ctx* c, const double* grad_force, const 
   const contact_status sticky = check_sticky(c);
   if (sticky != CONTACT_OK) return sticky;
   launch_adjoint(c->P, c->S, c->D, c->W, c->last_vel, grad_force, grad_torque, grad_pos, grad_quat,
-                 c->adj_scratch, c->grid_adjoint, c->stream);
+                 c->adj_scratch, c->grid_adjoint, c->stream, c->cfg.narrow_events ? c->ev_adj[0] : nullptr,
+                 c->cfg.narrow_events ? c->ev_adj[1] : nullptr);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+  c->have_backward = true;
   return CONTACT_OK;
+}
+
+contact_status contact_adjoint_time(contact_ctx* c, float* ms) {
+  if (c == nullptr || ms == nullptr) return CONTACT_EINVAL;
+  if (!c->have_backward) return fail(c, CONTACT_ESTATE, "contact_adjoint_time: no backward yet");
+  if (!c->cfg.narrow_events) return fail(c, CONTACT_ESTATE, "contact_adjoint_time: narrow_events is off");
+  cudaError_t e = cudaEventSynchronize(c->ev_adj[1]);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
+  e = cudaEventElapsedTime(ms, c->ev_adj[0], c->ev_adj[1]);
+  return e == cudaSuccess ? CONTACT_OK : cuda_fail(c, e, "cudaEventElapsedTime");
 }
 
 contact_status contact_step_host(contact_ctx* c, const double* pos, const double* quat, const double* vel,
@@ -1047,6 +1063,8 @@ void contact_destroy(contact_ctx* c) {
   cudaDeviceSynchronize();
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   for (cudaEvent_t ev : c->ev_narrow)
+    if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : c->ev_adj)
     if (ev) cudaEventDestroy(ev);
   for (void* p : c->dev_allocs) cudaFree(p);
   if (c->err_host) cudaFreeHost(c->err_host);

@@ -720,9 +720,10 @@ size_t adjoint_scratch_doubles(int max_pairs, int max_tiles) {
          static_cast<size_t>(max_pairs) * kPairGrad + static_cast<size_t>(max_pairs) / 2 + 16;
 }
 
+// ev0 / ev1 (nullable): events recorded around the cell sweep's launch.
 void launch_adjoint(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel,
                     const double* gF, const double* gT, double* gpos, double* gquat, double* scratch, int grid,
-                    cudaStream_t st) {
+                    cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
   AdjBufs B;
   B.partial = reinterpret_cast<float*>(scratch);
   B.seeds = B.partial + static_cast<size_t>(P.max_tiles) * kAdjPartial;
@@ -740,7 +741,9 @@ void launch_adjoint(const Params& P, const Shapes& S, const Parts& D, const List
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cells, kWarps * 32, 0);
   const int cgrid = (per_sm > 0 ? per_sm : 1) * sms;   // persistent: every resident slot pulls tiles
   (void)grid;
+  if (ev0 != nullptr) cudaEventRecord(ev0, st);
   launch_pdl(cells, dim3(cgrid), dim3(kWarps * 32), 0, st, P, S, D, W, B);
+  if (ev1 != nullptr) cudaEventRecord(ev1, st);
   launch_pdl(k_adj_scatter, dim3((8 * P.n + 31) / 32), dim3(32), 0, st, P, D, W, B, gpos, gquat);
 }
 

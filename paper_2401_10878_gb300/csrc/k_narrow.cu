@@ -857,39 +857,54 @@ __global__ void __launch_bounds__(kWarps * 32, SET == 0 ? 2 : 3) k_narrow32(Para
   (void)vel;   // the velocities enter with the force law (next kernel)
 }
 
-// The force law of the step's overlapping pairs, eight per warp pass (four
-// lanes each).  Warp w takes the pairs 32 c .. 32 c + 31 of chunks c = w,
-// w + W, ...: one flag load per lane, a ballot, and the flagged entries of
-// the overlap list staged eight at a time; each warp adds its count of
-// overlapping pairs to counters[5] (reported by contact_stats).
+// The force law of the step's overlapping pairs, up to eight per warp pass
+// (four lanes each).  Warp w of block b takes chunk c = b + grid * w (then
+// c + grid * 8, ...) of 16 consecutive pairs: their overlap flags and, in the
+// same round of loads, all 16 entries of the overlap list (the flagged ones
+// are kept, in pair order), so one memory round trip precedes the pass.  With
+// one block per SM the chunks of a step land on different sub-partitions, so
+// the FP64 passes (the pipe serialises one warp instruction per ~64 cycles)
+// run side by side.  Each warp adds its count of overlapping pairs to
+// counters[5] (reported by contact_stats).
+constexpr int kForceChunk = 16;
+
 template <int SET, bool LAW>
 __global__ void __launch_bounds__(kWarps * 32) k_force(Params P, Shapes S, Parts D, Lists W, const double* vel,
                                                        double* pair_out) {
-  __shared__ __align__(16) OvlRec s_ovl[kWarps][kForcePairsPerPass];
+  __shared__ __align__(16) OvlRec s_ovl[kWarps][kForceChunk];
   pdl_begin();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (W.counters[1] > P.max_tiles) return;   // the node sweep did not run (ECAPACITY)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int np = min(W.counters[0], P.max_pairs);
-  const int nchunk = (np + 31) / 32;
+  const int nchunk = (np + kForceChunk - 1) / kForceChunk;
+  constexpr int kPieces = static_cast<int>(sizeof(OvlRec) / 16);          // 16-byte pieces per entry
+  constexpr int kPerLane = kForceChunk * kPieces / 32;                    // pieces per lane
   int nov = 0;
-  for (int c = wid * gridDim.x + blockIdx.x; c < nchunk; c += gridDim.x * kWarps) {
-    const int q = 32 * c + lane;
-    unsigned mask = __ballot_sync(kFull, q < np && W.oflag[q] != 0);
+  for (int c = blockIdx.x + gridDim.x * wid; c < nchunk; c += gridDim.x * kWarps) {
+    const int q0 = kForceChunk * c;
+    const int q = q0 + lane;
+    const bool flag = lane < kForceChunk && q < np && W.oflag[q] != 0;
+    int4 piece[kPerLane];
+#pragma unroll
+    for (int u = 0; u < kPerLane; ++u) {   // entry e / kPieces, part e % kPieces of the chunk
+      const int e = lane + 32 * u;
+      const int qe = q0 + e / kPieces;
+      piece[u] = qe < np ? reinterpret_cast<const int4*>(W.olist + qe)[e % kPieces] : make_int4(0, 0, 0, 0);
+    }
+    unsigned mask = __ballot_sync(kFull, flag);
     nov += __popc(mask);
     while (mask != 0u) {
       const int n = min(__popc(mask), kForcePairsPerPass);
-      // stage the batch: n records x 128 bytes, two 16-byte pieces per lane
+      // keep the next n flagged entries, packed in pair order
+      unsigned take = mask;   // the lowest n flagged entries (all of them but in a rare 9th+)
+      if (n < __popc(mask)) take = mask & ((1u << __fns(mask, 0, n + 1)) - 1u);   // below the (n+1)-th
       int4* dst = reinterpret_cast<int4*>(s_ovl[wid]);
-      constexpr int kPieces = static_cast<int>(sizeof(OvlRec) / 16);
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int e = lane + 32 * u, k = e / kPieces;
-        if (k < n) {
-          const int src = 32 * c + __fns(mask, 0, k + 1);   // the (k+1)-th flagged pair of the chunk
-          dst[e] = reinterpret_cast<const int4*>(W.olist + src)[e - k * kPieces];
-        }
+      for (int u = 0; u < kPerLane; ++u) {
+        const int e = lane + 32 * u, r = e / kPieces;
+        if ((take >> r) & 1u) dst[__popc(take & ((1u << r) - 1u)) * kPieces + e % kPieces] = piece[u];
       }
-      for (int k = 0; k < n; ++k) mask &= mask - 1;
+      mask &= ~take;
       __syncwarp();
       flush_overlaps<SET, LAW>(P, S, D, W, vel, pair_out, s_ovl[wid], n);
     }
@@ -1012,7 +1027,7 @@ void launch_force(const Params& P, const Shapes& S, const Parts& D, const Lists&
   const bool law = P.history || P.friction || (vel != nullptr && P.damping_c != 0.0);
   auto kern = P.kind_set == 2 ? (law ? k_force<2, true> : k_force<2, false>)
                               : (law ? k_force<0, true> : k_force<0, false>);
-  launch_pdl(kern, dim3(sms > 0 ? 2 * sms : 2), dim3(kWarps * 32), 0, st, P, S, D, W, vel, pair_out);
+  launch_pdl(kern, dim3(sms > 0 ? sms : 1), dim3(kWarps * 32), 0, st, P, S, D, W, vel, pair_out);
 }
 
 void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel,

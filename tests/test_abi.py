@@ -40,6 +40,7 @@ def test_library_exports_every_declared_symbol():
 def test_config_struct_layout():
     from paper_2401_10878_gb300.contact import Config
     # int32 + int32[3] (16), double dx (24), int32 + pad (32), 3 doubles (56),
-    # 6 int32 (80): 80 bytes
+    # 8 int32 (88), 4 doubles (120), 2 int32 (128), 3 pointers (152),
+    # 2 int32 (160): 160 bytes
     assert ctypes.sizeof(Config) == 160
     assert Config.dx.offset == 16 and Config.smooth_width.offset == 32 and Config.precision.offset == 56

@@ -89,3 +89,52 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
                                   host.ctypes.data_as(ctypes.c_void_p), *[ctypes.c_void_p(dummy.data_ptr())] * 7,
                                   None)
     assert rc == EINVAL
+
+
+def test_noalloc_matches_contact_step_at_a_spacing_that_is_not_a_power_of_two():
+    """dx = 0.7: the per-particle tables (sizes in lattice units, compliance)
+    are formed with the same rounded operations on both paths, so the node
+    classification and the pair volumes agree exactly."""
+    from paper_2401_10878_gb300.contact import Contact
+    st = W.mixed_grid_27()
+    st.indicator = 0
+    st.dx = 0.7
+    st.pos = st.pos * 0.7
+    st.shape_param = st.shape_param * 0.7
+    model = Contact.from_state(st, max_pairs=8192)
+    pos = torch.tensor(st.pos, device="cuda")
+    quat = torch.tensor(st.quat, device="cuda")
+    ref = model.step(pos, quat)
+    rc, out = _noalloc(model.lib, model, st, pos, quat)
+    assert rc == 0, rc
+    P = int(out["n_pairs"].item())
+    assert P == ref["n_pairs"] > 0
+    assert torch.equal(out["pair_ij"][:P], ref["pair_ij"])
+    po, pr = out["pair_out"][:P].cpu().numpy(), ref["pair_out"].cpu().numpy()
+    assert np.array_equal(po[:, 0], pr[:, 0])
+    scale = np.abs(pr[:, 8:11]).max()
+    assert np.abs(po - pr).max() <= 1e-5 * max(scale, 1.0)
+    model.close()
+
+
+def test_noalloc_capacity_limits():
+    """Fewer pair slots than pairs, or a tile budget below the pairs' tiles,
+    return CONTACT_ECAPACITY with n_pairs holding the pairs needed; the next
+    call with room succeeds."""
+    from paper_2401_10878_gb300.contact import Contact, ECAPACITY
+    st = W.mixed_grid_27()
+    st.indicator = 0
+    model = Contact.from_state(st, max_pairs=8192)
+    pos = torch.tensor(st.pos, device="cuda")
+    quat = torch.tensor(st.quat, device="cuda")
+    need = model.step(pos, quat)["n_pairs"]
+    for field, value in (("max_pairs", 8), ("max_tiles", 4)):
+        saved = getattr(model.cfg, field)
+        setattr(model.cfg, field, value)
+        rc, out = _noalloc(model.lib, model, st, pos, quat)
+        setattr(model.cfg, field, saved)
+        assert rc == ECAPACITY, (field, rc)
+        assert int(out["n_pairs"].item()) == need
+    rc, out = _noalloc(model.lib, model, st, pos, quat)
+    assert rc == 0 and int(out["n_pairs"].item()) == need
+    model.close()
