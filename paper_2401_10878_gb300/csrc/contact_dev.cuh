@@ -15,11 +15,10 @@
 
 namespace gbc {
 
-// Sweep kinds: polytopes with up to 20 faces keep their face values in
-// registers (padded to 20); larger ones (up to 32) read planes from shared memory.
-// Cubes (equal half extents) have their own kind: max|y| - h needs no per-axis offset.
-enum Kind : int { KIND_SPHERE = 0, KIND_CUBOID = 1, KIND_POLY = 2, KIND_POLYG = 3, KIND_CUBE = 4, KIND_WALL = 5 };
-constexpr int kRegFaces = 20;
+// Sweep kinds: polytopes (up to 32 faces) read their planes from shared
+// memory; cubes (equal half extents) have their own kind: max|y| - h needs no
+// per-axis offset.  (Kind 2 is not used.)
+enum Kind : int { KIND_SPHERE = 0, KIND_CUBOID = 1, KIND_POLY = 3, KIND_CUBE = 4, KIND_WALL = 5 };
 
 constexpr int kMaxFaces = 32;         // faces of one polytope
 constexpr int kTileItemsPerLane = 4;  // node lines per lane per tile

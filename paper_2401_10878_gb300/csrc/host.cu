@@ -12,6 +12,7 @@
 
 #include "../../include/contact.h"
 #include "contact_dev.cuh"
+#include "line_clip.cuh"
 
 using namespace gbc;
 
@@ -420,8 +421,19 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
       if (v.size() < 12) return CONTACT_EINVAL;
       for (size_t t = 0; t < v.size(); t += 3)
         circ = std::max(circ, std::sqrt(v[t] * v[t] + v[t + 1] * v[t + 1] + v[t + 2] * v[t + 2]));
+      // the node sweep's pair test bounds a polytope by balls (lattice units,
+      // rounded up): its region {phi <= 0} (offset inflate) in size slot 0, its
+      // region {phi < w/2 + the clip margin} in slot 1
+      const double tcut = (0.5 * C.smooth_width + static_cast<double>(kClipMargin)) * C.dx;
+      for (int s = 0; s < 2; ++s) {
+        const std::vector<double> vs = offset_vertices(pl, F, C.inflate + (s == 0 ? 0.0 : tcut));
+        double r = 0.0;
+        for (size_t t = 0; t < vs.size(); t += 3)
+          r = std::max(r, std::sqrt(vs[t] * vs[t] + vs[t + 1] * vs[t + 1] + vs[t + 2] * vs[t + 2]));
+        size_l[3 * p + s] = std::nextafter(static_cast<float>(r / C.dx), 3.0e38f);
+      }
       verts.insert(verts.end(), v.begin(), v.end());
-      kind[p] = F <= kRegFaces ? KIND_POLY : KIND_POLYG;
+      kind[p] = KIND_POLY;
       nomops[p] = 4 * F;
     } else {
       return CONTACT_EINVAL;

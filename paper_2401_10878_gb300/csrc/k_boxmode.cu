@@ -62,7 +62,7 @@ __device__ __forceinline__ void load_shape(const PairRec& r, bool second, const 
   for (int k = 0; k < 9; ++k) s.rt[k] = rt[k];
   s.nf = 0;
   s.pl = sm;
-  if (s.kind == KIND_POLY || s.kind == KIND_POLYG) {
+  if (s.kind == KIND_POLY) {
     const int f0 = S.face_off[pid];
     s.nf = S.face_off[pid + 1] - f0;
     if (lane < s.nf) sm[lane] = D.wplane[f0 + lane];

@@ -204,7 +204,7 @@ __global__ void k_pose(Params P, Shapes S, Parts D, Lists W, const double* __res
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   // the step's counters start at zero (the previous step has completed)
   if (t == 0) {
-    W.counters[0] = 0;   // pairs
+    W.counters[0] = 0;   // pairs (written by the pair builder)
     W.counters[1] = 0;   // tiles allocated
     W.counters[2] = 0;   // box pipeline queue head
     W.counters[5] = 0;   // pairs with V > 0
@@ -315,10 +315,33 @@ __device__ __forceinline__ bool pair_box(const Params& P, const Parts& D, int p,
 // each list is then sorted by rank.
 __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
   extern __shared__ int s_buf[];
+  // the block's partner count (its particles share one row group), added
+  // to the group sum by the block's last warp to finish: one global atomic per block
+  __shared__ int s_gsum, s_gdone;
+  if (threadIdx.x == 0) {
+    s_gsum = 0;
+    s_gdone = 0;
+  }
+  __syncthreads();
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int p = blockIdx.x * (blockDim.x >> 5) + wid;
-  if (p >= P.n) return;
+  const int nw = static_cast<int>(blockDim.x >> 5);
+  auto group_sum = [&](int nup) {
+    if (lane == 0) {
+      if (nup > 0) atomicAdd_block(&s_gsum, nup);
+      __threadfence_block();
+      if (atomicAdd_block(&s_gdone, 1) == nw - 1) {   // every warp's count is in
+        __threadfence_block();
+        const int tot = atomicAdd_block(&s_gsum, 0);
+        if (tot > 0) atomicAdd(&W.grp_sum[(blockIdx.x * nw) / kRowGroup], tot);
+      }
+    }
+  };
+  if (p >= P.n) {
+    group_sum(0);
+    return;
+  }
   const int cap = P.max_nbr;
   int* up = s_buf + wid * 2 * cap;
   int* dn = up + cap;
@@ -447,11 +470,8 @@ __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
   if (lane == 0) {
     W.up_count[p] = nup;
     W.dn_count[p] = ndn;
-    if (nup > 0) {
-      atomicAdd(&W.grp_sum[p / kRowGroup], nup);
-      atomicAdd(&W.counters[0], nup);
-    }
   }
+  group_sum(nup);
 }
 
 
@@ -487,15 +507,19 @@ static_assert(offsetof(PairRec, rta) == 30 * 4 && offsetof(PairRec, szb) == 51 *
                   offsetof(PairRec, pair) == 55 * 4 && sizeof(PairRec) == 14 * 16,
               "store_pair_rec follows the PairRec layout");
 
-// True when the regions {phi_A < T} and {phi_B < T} of the pair are disjoint
-// (by more than kCullMargin cells), so that no node can add to any of the
-// node sweep's sums (each needs both distances below w/2 < T): the pair's
-// outputs are zero and it is not queued.  Spheres, cubes and cuboids only
-// (their T-regions are balls and boxes of half extents size + T): box-box by
-// the 15 separating axes (faces of either box, edge cross products), sphere-box
-// by the box's closest point, sphere-sphere by the centre distance.  FP32 in
-// lattice units: the centres differ by an exact integer plus the FP32
-// difference of two remainders, and every rounding is far below the margin.
+// Whether the regions {phi_A < Ta} and {phi_B < Tb} of the pair are
+// disjoint (by more than kCullMargin cells).  A node adds to the node sweep's
+// sums only when both distances lie below w/2 and, with the sharp indicator,
+// one of them is <= 0; so with T = w/2 (+ the clip margin) a pair apart for
+// (T, T) (smoothed), or for both (0, T) and (T, 0) (sharp), has zero
+// outputs and is not queued.  Spheres, cubes, cuboids and polytopes (their
+// regions are balls and boxes of half extents size + T; a polytope is bounded
+// by a ball, its circumradius at each threshold from the shape tables):
+// box-box by the 15 separating axes (faces of either box, edge cross
+// products), ball-box by the box's closest point, ball-ball by the centre
+// distance; walls are never skipped.  FP32 in lattice units: the centres
+// differ by an exact integer plus the FP32 difference of two remainders, and
+// every rounding is far below the margin.
 constexpr float kCullMargin = 1e-3f;
 
 __device__ __forceinline__ float dot3(const float* a, const float* b) { return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2])); }
@@ -513,29 +537,67 @@ __device__ __forceinline__ float box_point_dist2(const float* rt, const float e[
   return d2;
 }
 
-__device__ bool pair_apart(const PairRec& r, float T) {
+// The three threshold pairs of the test, from one set of projections: bit 0
+// (T, T), bit 1 (0, T), bit 2 (T, 0) set when the regions are apart.  On an
+// axis the reach of a box's region is R0 + T S (R0 its reach at 0, S the sum
+// of its axes' projections), of a ball r + T or its tabulated radius.
+struct Apart {
+  unsigned bits = 0;
+  __device__ __forceinline__ void axis(float proj, float ra0, float sa, float rb0, float sb, float T) {
+    const float base = proj - kCullMargin - ra0 - rb0;
+    bits |= (base > T * (sa + sb) ? 1u : 0u) | (base > T * sb ? 2u : 0u) | (base > T * sa ? 4u : 0u);
+  }
+};
+
+__device__ unsigned pair_apart(const PairRec& r, float T) {
   const int ka = r.kinds & 0xff, kb = r.kinds >> 8;
-  const bool sa = ka == KIND_SPHERE, sb = kb == KIND_SPHERE;
+  const bool pa = ka == KIND_POLY, pb = kb == KIND_POLY;
+  const bool sa = ka == KIND_SPHERE || pa, sb = kb == KIND_SPHERE || pb;   // balls
   const bool ba = ka == KIND_CUBOID || ka == KIND_CUBE, bb = kb == KIND_CUBOID || kb == KIND_CUBE;
-  if (!((sa || ba) && (sb || bb))) return false;
+  if (!((sa || ba) && (sb || bb))) return 0u;
   float d[3];   // centre of B minus centre of A (lattice units)
 #pragma unroll
   for (int k = 0; k < 3; ++k) d[k] = static_cast<float>(r.bi[k] - r.ai[k]) + (r.bf[k] - r.af[k]);
+  Apart ap;
   if (sa && sb) {
-    const float reach = r.sza[0] + r.szb[0] + 2.f * T + kCullMargin;
-    return dot3(d, d) > reach * reach;
+    // ball radii at 0 and at T: a sphere's r and r + T, a polytope's two tabulated radii
+    const float a0 = r.sza[0], aT = pa ? r.sza[1] : r.sza[0] + T;
+    const float b0 = r.szb[0], bT = pb ? r.szb[1] : r.szb[0] + T;
+    const float dist = sqrtf(dot3(d, d));
+    ap.axis(dist, a0, (aT - a0) / T, b0, (bT - b0) / T, T);
+    return ap.bits;
   }
-  if (sa || sb) {
-    const float* rt = sa ? r.rtb : r.rta;
-    const float* sz = sa ? r.szb : r.sza;
-    const float e[3] = {sz[0] + T, sz[1] + T, sz[2] + T};
-    const float rs = (sa ? r.sza[0] : r.szb[0]) + T + kCullMargin;
-    const float c[3] = {sa ? -d[0] : d[0], sa ? -d[1] : d[1], sa ? -d[2] : d[2]};   // sphere centre - box centre
-    return box_point_dist2(rt, e, c) > rs * rs;
+  if (sa || sb) {   // a ball and a box: the distance from the ball's centre to the box at each threshold
+    // (element-wise selects: a runtime-chosen pointer into the record would put it in local memory)
+    const bool pol = sa ? pa : pb;
+    const float r0 = sa ? r.sza[0] : r.szb[0];
+    const float rT = pol ? (sa ? r.sza[1] : r.szb[1]) : r0 + T;
+    float y[3], sz[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {   // |ball centre - box centre| in the box frame
+      const float t0 = sa ? r.rtb[3 * k] : r.rta[3 * k], t1 = sa ? r.rtb[3 * k + 1] : r.rta[3 * k + 1],
+                  t2 = sa ? r.rtb[3 * k + 2] : r.rta[3 * k + 2];
+      y[k] = fabsf(fmaf(t0, d[0], fmaf(t1, d[1], t2 * d[2])));
+      sz[k] = sa ? r.szb[k] : r.sza[k];
+    }
+    // the box at 0 and at T, the ball at 0 and at T: bits as (A, B) thresholds
+    float dist[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      float d2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float o = fmaxf(y[k] - (sz[k] + (t ? T : 0.f)), 0.f);
+        d2 = fmaf(o, o, d2);
+      }
+      dist[t] = sqrtf(d2) - kCullMargin;
+    }
+    // (T, T): box T, ball T; (0, T) and (T, 0) with the ball on side A or B
+    const bool tt = dist[1] > rT, box0_ballT = dist[0] > rT, boxT_ball0 = dist[1] > r0;
+    ap.bits = (tt ? 1u : 0u) | ((sa ? boxT_ball0 : box0_ballT) ? 2u : 0u) | ((sa ? box0_ballT : boxT_ball0) ? 4u : 0u);
+    return ap.bits;
   }
-  // two boxes: R[i][j] = a_i . b_j, t = d in A's frame
-  const float ea[3] = {r.sza[0] + T, r.sza[1] + T, r.sza[2] + T};
-  const float eb[3] = {r.szb[0] + T, r.szb[1] + T, r.szb[2] + T};
+  // two boxes: R[i][j] = a_i . b_j, t = d in A's frame; 15 axes
   float R[3][3], AR[3][3], t[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -546,14 +608,17 @@ __device__ bool pair_apart(const PairRec& r, float T) {
       AR[i][j] = fabsf(R[i][j]) + 1e-6f;
     }
   }
-  bool sep = false;
+  const float ea[3] = {r.sza[0], r.sza[1], r.sza[2]}, eb[3] = {r.szb[0], r.szb[1], r.szb[2]};
 #pragma unroll
-  for (int i = 0; i < 3; ++i)   // A's faces
-    sep = sep || fabsf(t[i]) > ea[i] + fmaf(eb[0], AR[i][0], fmaf(eb[1], AR[i][1], eb[2] * AR[i][2])) + kCullMargin;
+  for (int i = 0; i < 3; ++i) {   // A's faces
+    const float sbi = AR[i][0] + AR[i][1] + AR[i][2];
+    ap.axis(fabsf(t[i]), ea[i], 1.f, fmaf(eb[0], AR[i][0], fmaf(eb[1], AR[i][1], eb[2] * AR[i][2])), sbi, T);
+  }
 #pragma unroll
   for (int j = 0; j < 3; ++j) {   // B's faces
     const float tb = fmaf(t[0], R[0][j], fmaf(t[1], R[1][j], t[2] * R[2][j]));
-    sep = sep || fabsf(tb) > eb[j] + fmaf(ea[0], AR[0][j], fmaf(ea[1], AR[1][j], ea[2] * AR[2][j])) + kCullMargin;
+    const float saj = AR[0][j] + AR[1][j] + AR[2][j];
+    ap.axis(fabsf(tb), fmaf(ea[0], AR[0][j], fmaf(ea[1], AR[1][j], ea[2] * AR[2][j])), saj, eb[j], 1.f, T);
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {   // edge pairs a_i x b_j
@@ -561,12 +626,13 @@ __device__ bool pair_apart(const PairRec& r, float T) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const int j1 = j == 2 ? 0 : j + 1, j2 = j1 == 2 ? 0 : j1 + 1;
-      const float ra = fmaf(ea[i1], AR[i2][j], ea[i2] * AR[i1][j]);
-      const float rb = fmaf(eb[j1], AR[i][j2], eb[j2] * AR[i][j1]);
-      sep = sep || fabsf(fmaf(t[i2], R[i1][j], -t[i1] * R[i2][j])) > ra + rb + kCullMargin;
+      const float ra0 = fmaf(ea[i1], AR[i2][j], ea[i2] * AR[i1][j]);
+      const float rb0 = fmaf(eb[j1], AR[i][j2], eb[j2] * AR[i][j1]);
+      ap.axis(fabsf(fmaf(t[i2], R[i1][j], -t[i1] * R[i2][j])), ra0, AR[i2][j] + AR[i1][j], rb0,
+              AR[i][j2] + AR[i][j1], T);
     }
   }
-  return sep;
+  return ap.bits;
 }
 
 __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shapes S, Parts D, Lists W,
@@ -605,8 +671,9 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
   const int row = __reduce_add_sync(kFull, acc);
   if (lane == 0 && row_ok) {
     W.row_off[i] = row;
-    if (i == P.n - 1) {
-      const int total = W.counters[0];
+    if (i == P.n - 1) {   // the pair count: the last row's offset plus its partners
+      const int total = row + cnt;
+      W.counters[0] = total;
       W.row_off[P.n] = total;
       *n_pairs_out = total;
       if (total > P.max_pairs) set_error(W.err, kErrCapacity);
@@ -698,7 +765,8 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
       }
       // the FP32 node sweep skips pairs whose distance regions are apart:
       // their outputs are written here as the sweep would write them (zeros)
-      if (P.precision == 0 && P.box_mode == 0 && pair_apart(pr, 0.5f * P.wdx_l + kClipMargin)) {
+      const unsigned apart = (P.precision == 0 && P.box_mode == 0) ? pair_apart(pr, 0.5f * P.wdx_l + kClipMargin) : 0u;
+      if (P.smooth ? (apart & 1u) != 0u : (apart & 6u) == 6u) {
         ntiles = 0;
         pr.ntiles = 0;
         double* po = pair_out + static_cast<size_t>(pi) * 11;

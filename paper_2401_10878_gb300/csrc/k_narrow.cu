@@ -21,8 +21,8 @@
 //     each face value is computed once and a node costs one FMA per face;
 //   * node coordinates relative to each particle are exact integers minus an
 //     FP32 remainder in [-1/2, 1/2] (no large-offset cancellation);
-//   * polytope faces (<= 20, padded) live in registers, the face table used
-//     for the normal's gradient lookups in shared memory;
+//   * polytope faces (and their inverse slopes along the line) are staged
+//     in shared memory;
 //   * the volume/moment/depth update and the normal-band update run only when
 //     some lane of the warp needs them (warp-uniform branches);
 //   * warp-shuffle reduction per tile (skipped when no lane met a node to
@@ -290,74 +290,8 @@ __device__ __forceinline__ int stage_planes(const Shapes& S, const Parts& D, int
   return nf;
 }
 
-template <int NF>
+// Polytopes: planes (and their inverse slopes along u) read from shared memory.
 struct PolyEval {
-  int iu, iv, iw;
-  float fu, fv, fw;
-  const float4* sp;
-  float mu[NF], p[NF];
-  float cnt_u, ru;
-  float gu, gv, gw;
-  __device__ void load(const PairRec& r, bool second, const Shapes& S, const Parts& D, const Local& L,
-                       float4* sm) {
-    const int* ci = second ? r.bi : r.ai;
-    const float* cf = second ? r.bf : r.af;
-    iu = ci[L.u]; iv = ci[L.v]; iw = ci[L.w];
-    fu = cf[L.u]; fv = cf[L.v]; fw = cf[L.w];
-    stage_planes(S, D, second ? r.j : r.i, L, sm, NF);
-    sp = sm;
-#pragma unroll
-    for (int f = 0; f < NF; ++f) mu[f] = sm[f].x;
-    gu = gv = gw = 0.f;
-  }
-  __device__ __forceinline__ void begin_line(int cv, int cw, int u0) {
-    const float rv = static_cast<float>(cv - iv) - fv;
-    const float rw = static_cast<float>(cw - iw) - fw;
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const float4 e = sp[f];
-      p[f] = fmaf(-e.x, fu, fmaf(e.y, rv, fmaf(e.z, rw, -e.w)));
-    }
-    cnt_u = static_cast<float>(u0 - iu) - 1.f;
-  }
-  __device__ __forceinline__ void clip(float T, float& lo, float& hi) const {
-    const float o = static_cast<float>(iu);
-    const float* inv = reinterpret_cast<const float*>(sp + kMaxFaces);
-    float l = lo - o, h = hi - o;
-#pragma unroll
-    for (int f = 0; f < NF; ++f) clip_half(mu[f], inv[f], p[f], T, l, h);
-    lo = l + o;
-    hi = h + o;
-  }
-  __device__ __forceinline__ void seek(int u) { cnt_u = static_cast<float>(u - iu) - 1.f; }
-  __device__ __forceinline__ float counter() const { return cnt_u; }
-  __device__ __forceinline__ int origin() const { return iu; }
-  __device__ __forceinline__ float phi() {
-    cnt_u += 1.f;
-    float best = fmaf(mu[0], cnt_u, p[0]);
-#pragma unroll
-    for (int f = 1; f < NF; ++f) best = fmaxf(best, fmaf(mu[f], cnt_u, p[f]));
-    return best;
-  }
-  __device__ __forceinline__ void grad(float m) {
-    int k = 0;
-    float best = fmaf(mu[0], cnt_u, p[0]);
-#pragma unroll
-    for (int f = 1; f < NF; ++f) {
-      const float v = fmaf(mu[f], cnt_u, p[f]);
-      if (v > best) { best = v; k = f; }
-    }
-    const float4 e = sp[k];
-    gu = fmaf(m, e.x, gu);
-    gv = fmaf(m, e.y, gv);
-    gw = fmaf(m, e.z, gw);
-  }
-  __device__ __forceinline__ void end_line() {}
-  __device__ float world(int c, const Local& L, const PairRec&, bool) const { return world_comp(c, L, gu, gv, gw); }
-};
-
-// Polytopes with more than kRegFaces faces: planes read from shared memory.
-struct PolyGEval {
   int iu, iv, iw, nf;
   float fu, fv, fw;
   const float4* sp;
@@ -754,8 +688,8 @@ enum KindSet : int { SET_ALL = 0, SET_SC = 1, SET_CUBE = 2 };
 template <bool SMOOTH, int SET>
 __device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, const Parts& D, const PairRec& r,
                                             int tl, float4* smA, float4* smB) {
-  // kind order for canonical pairs: wall < sphere < cube < cuboid < polytope < large polytope
-  constexpr int rank[6] = {1, 3, 4, 5, 2, 0};
+  // kind order for canonical pairs: wall < sphere < cube < cuboid < polytope (kind 2 unused)
+  constexpr int rank[6] = {1, 3, 6, 5, 2, 0};
   int ka = r.kinds & 0xff, kb = r.kinds >> 8;
   const bool swap = rank[ka] > rank[kb];   // evaluate the cheaper kind as A; G's sign flips back below
   if (swap) {
@@ -790,18 +724,13 @@ __device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, co
     switch (ka * 8 + kb) {
       GBC_CASE(0, 0, SphereEval, SphereEval)
       GBC_CASE(0, 1, SphereEval, CuboidEval)
-      GBC_CASE(0, 2, SphereEval, PolyEval<kRegFaces>)
-      GBC_CASE(0, 3, SphereEval, PolyGEval)
+      GBC_CASE(0, 3, SphereEval, PolyEval)
       GBC_CASE(1, 1, CuboidEval, CuboidEval)
-      GBC_CASE(1, 2, CuboidEval, PolyEval<kRegFaces>)
-      GBC_CASE(1, 3, CuboidEval, PolyGEval)
-      GBC_CASE(2, 2, PolyEval<kRegFaces>, PolyEval<kRegFaces>)
-      GBC_CASE(2, 3, PolyEval<kRegFaces>, PolyGEval)
-      GBC_CASE(3, 3, PolyGEval, PolyGEval)
+      GBC_CASE(1, 3, CuboidEval, PolyEval)
+      GBC_CASE(3, 3, PolyEval, PolyEval)
       GBC_CASE(5, 0, WallEval, SphereEval)
       GBC_CASE(5, 1, WallEval, CuboidEval)
-      GBC_CASE(5, 2, WallEval, PolyEval<kRegFaces>)
-      GBC_CASE(5, 3, WallEval, PolyGEval)
+      GBC_CASE(5, 3, WallEval, PolyEval)
       default:
         break;
     }
@@ -823,7 +752,7 @@ __device__ __forceinline__ void store_rec_part(PairRec* dst, int lane, int4 v) {
 
 // Blocks per SM: 3 for the sphere/cuboid/cube variants (<= 85 registers, so
 // 24 warps per SM: about one tile per warp at a settling box's size), 2 for
-// the variant with polytopes (the registers of their face values).
+// the variant with every kind (measured faster than 3, which spills more).
 template <bool SMOOTH, int SET>
 __global__ void __launch_bounds__(kWarps * 32, SET == 0 ? 2 : 3) k_narrow32(Params P, Shapes S, Parts D,
                                                                                   Lists W, const double* vel,
