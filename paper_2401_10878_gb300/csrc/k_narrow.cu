@@ -87,6 +87,7 @@ struct SphereEval {
   int iu, iv, iw;
   float fu, fv, fw, rad;
   float cnt_u, rv, rw, rho2, ru, q;
+  float nv, nw, nrho2;   // the node's line (pull)
   float gu, gv, gw, gl;
   __device__ void load(const PairRec& r, bool second, const Shapes&, const Parts&, const Local& L, float4*) {
     const int* ci = second ? r.bi : r.ai;
@@ -111,15 +112,19 @@ struct SphereEval {
     lo = l + o;
     hi = h + o;
   }
-  // the next phi() evaluates node u
-  __device__ __forceinline__ void seek(int u) { cnt_u = static_cast<float>(u - iu) - 1.f; }
-  // node offset cu - iu of the current node (exact integer in FP32)
-  __device__ __forceinline__ float counter() const { return cnt_u; }
-  __device__ __forceinline__ int origin() const { return iu; }
+  // the next phi() evaluates node u of lane o's line (its terms by shuffle:
+  // the same values begin_line gives on that line)
+  __device__ __forceinline__ void pull(int o, int u) {
+    nv = __shfl_sync(kFull, rv, o);
+    nw = __shfl_sync(kFull, rw, o);
+    nrho2 = __shfl_sync(kFull, rho2, o);
+    gl = 0.f;
+    cnt_u = static_cast<float>(u - iu) - 1.f;
+  }
   __device__ __forceinline__ float phi() {
     cnt_u += 1.f;
     ru = cnt_u - fu;
-    q = fmaf(ru, ru, rho2);
+    q = fmaf(ru, ru, nrho2);
     return sqrtf(q) - rad;
   }
   __device__ __forceinline__ void grad(float m) {
@@ -128,8 +133,8 @@ struct SphereEval {
     gl += mi;
   }
   __device__ __forceinline__ void end_line() {
-    gv = fmaf(gl, rv, gv);
-    gw = fmaf(gl, rw, gw);
+    gv = fmaf(gl, nv, gv);
+    gw = fmaf(gl, nw, gw);
   }
   __device__ float world(int c, const Local& L, const PairRec&, bool) const { return world_comp(c, L, gu, gv, gw); }
 };
@@ -139,6 +144,7 @@ struct CuboidEval {
   float fu, fv, fw;
   float tu[3], tv[3], tw[3], h[3], itu[3];
   float cnt_u, p[3], y[3], a[3];
+  float np_[3];   // the node's line (pull)
   float gb[3];
   __device__ void load(const PairRec& r, bool second, const Shapes&, const Parts&, const Local& L, float4*) {
     const int* ci = second ? r.bi : r.ai;
@@ -174,14 +180,16 @@ struct CuboidEval {
     lo = l + o;
     hi = hh + o;
   }
-  __device__ __forceinline__ void seek(int u) { cnt_u = static_cast<float>(u - iu) - 1.f; }
-  __device__ __forceinline__ float counter() const { return cnt_u; }
-  __device__ __forceinline__ int origin() const { return iu; }
+  __device__ __forceinline__ void pull(int o, int u) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) np_[k] = __shfl_sync(kFull, p[k], o);
+    cnt_u = static_cast<float>(u - iu) - 1.f;
+  }
   __device__ __forceinline__ float phi() {
     cnt_u += 1.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      y[k] = fmaf(tu[k], cnt_u, p[k]);
+      y[k] = fmaf(tu[k], cnt_u, np_[k]);
       a[k] = fabsf(y[k]) - h[k];
     }
     return fmaxf(a[0], fmaxf(a[1], a[2]));
@@ -209,6 +217,7 @@ struct CubeEval {
   int iu;
   float fu, tu0, tu1, tu2, h, itu0, itu1, itu2;
   float cnt_u, p0, p1, p2, y0, y1, y2;
+  float n0, n1, n2;   // the node's line (pull)
   float gb0, gb1, gb2;
   __device__ void load(const PairRec& r, bool second, const Shapes&, const Parts&, const Local& L, float4*) {
     const int* ci = second ? r.bi : r.ai;
@@ -242,14 +251,17 @@ struct CubeEval {
     lo = l + o;
     hi = hh + o;
   }
-  __device__ __forceinline__ void seek(int u) { cnt_u = static_cast<float>(u - iu) - 1.f; }
-  __device__ __forceinline__ float counter() const { return cnt_u; }
-  __device__ __forceinline__ int origin() const { return iu; }
+  __device__ __forceinline__ void pull(int o, int u) {
+    n0 = __shfl_sync(kFull, p0, o);
+    n1 = __shfl_sync(kFull, p1, o);
+    n2 = __shfl_sync(kFull, p2, o);
+    cnt_u = static_cast<float>(u - iu) - 1.f;
+  }
   __device__ __forceinline__ float phi() {
     cnt_u += 1.f;
-    y0 = fmaf(tu0, cnt_u, p0);
-    y1 = fmaf(tu1, cnt_u, p1);
-    y2 = fmaf(tu2, cnt_u, p2);
+    y0 = fmaf(tu0, cnt_u, n0);
+    y1 = fmaf(tu1, cnt_u, n1);
+    y2 = fmaf(tu2, cnt_u, n2);
     return fmaxf(fabsf(y0), fmaxf(fabsf(y1), fabsf(y2))) - h;
   }
   __device__ __forceinline__ void grad(float m) {
@@ -296,6 +308,7 @@ struct PolyEval {
   float fu, fv, fw;
   const float4* sp;
   float cnt_u, ru, rv, rw;
+  float nv, nw;   // the node's line (pull)
   float gu, gv, gw;
   __device__ void load(const PairRec& r, bool second, const Shapes& S, const Parts& D, const Local& L,
                        float4* sm) {
@@ -323,12 +336,14 @@ struct PolyEval {
     lo = l + o;
     hi = h + o;
   }
-  __device__ __forceinline__ void seek(int u) { cnt_u = static_cast<float>(u - iu) - 1.f; }
-  __device__ __forceinline__ float counter() const { return cnt_u; }
-  __device__ __forceinline__ int origin() const { return iu; }
+  __device__ __forceinline__ void pull(int o, int u) {
+    nv = __shfl_sync(kFull, rv, o);
+    nw = __shfl_sync(kFull, rw, o);
+    cnt_u = static_cast<float>(u - iu) - 1.f;
+  }
   __device__ __forceinline__ float value(int f) const {
     const float4 e = sp[f];
-    return fmaf(e.x, ru, fmaf(e.y, rv, fmaf(e.z, rw, -e.w)));
+    return fmaf(e.x, ru, fmaf(e.y, nv, fmaf(e.z, nw, -e.w)));
   }
   __device__ __forceinline__ float phi() {
     cnt_u += 1.f;
@@ -360,7 +375,7 @@ struct PolyEval {
 // FP32 keeps them to ~1e-6.
 struct WallEval {
   float mu_, mv_, mw_, p0, imu_;
-  float base, cnt_u, g;
+  float base, nbase, cnt_u, g;   // nbase: the node's line (pull)
   __device__ void load(const PairRec& r, bool second, const Shapes&, const Parts&, const Local& L, float4*) {
     const float* rt = second ? r.rtb : r.rta;   // row 0: the wall normal m (world)
     mu_ = rt[L.u]; mv_ = rt[L.v]; mw_ = rt[L.w];
@@ -373,12 +388,13 @@ struct WallEval {
     cnt_u = static_cast<float>(u0) - 1.f;
   }
   __device__ __forceinline__ void clip(float T, float& lo, float& hi) const { clip_half(mu_, imu_, base, T, lo, hi); }
-  __device__ __forceinline__ void seek(int u) { cnt_u = static_cast<float>(u) - 1.f; }
-  __device__ __forceinline__ float counter() const { return cnt_u; }
-  __device__ __forceinline__ int origin() const { return 0; }
+  __device__ __forceinline__ void pull(int o, int u) {
+    nbase = __shfl_sync(kFull, base, o);
+    cnt_u = static_cast<float>(u) - 1.f;
+  }
   __device__ __forceinline__ float phi() {
     cnt_u += 1.f;
-    return fmaf(mu_, cnt_u, base);
+    return fmaf(mu_, cnt_u, nbase);
   }
   __device__ __forceinline__ void grad(float m) { g += m; }
   __device__ __forceinline__ void end_line() {}
@@ -474,8 +490,8 @@ __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, 
       }
       const int ocv = __shfl_sync(kFull, cv, o), ocw = __shfl_sync(kFull, cw, o);
       const int u = __shfl_sync(kFull, ub, o) + (g - __shfl_sync(kFull, excl, o));
-      begin_line_of(A, r, swap, L, ocv, ocw, u, 0);
-      begin_line_of(B, r, !swap, L, ocv, ocw, u, 0);
+      A.pull(o, u);
+      B.pull(o, u);
       const float fa = A.phi();
       const float fb = B.phi();
       // W > 0, or a band term of the normal: max < w/2 and (sharp) min <= 0
