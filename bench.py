@@ -667,7 +667,7 @@ def node_sweep_source_hash():
     """Hash of the sources the node-sweep kernel is compiled from."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("k_narrow.cu", "force_law.cuh", "contact_dev.cuh"):
+    for f in ("k_narrow.cu", "force_law.cuh", "contact_dev.cuh", "line_clip.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2401_10878_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -201,9 +201,8 @@ struct Lists {
   double* tape;     // [max_pairs, kTapeDoubles]
   double* ft;       // [max_pairs, kFtDoubles]
   const int* kind;  // [N] sweep kind of each particle (Kind, polytopes by face bucket)
-  int* counters;    // [16]: 0 pairs, 1 tiles, 2 box pipeline queue, 3 cells(lo), 4 cells(hi), 5 overlapping
-                    // pairs, 6 adjoint queue, kStepCounter steps completed (its parity selects the
-                    // contact-history buffer)
+  int* counters;    // [16]: 0 pairs, 1 tiles, 2 box pipeline queue, 5 overlapping pairs, kStepCounter
+                    // steps completed (its parity selects the contact-history buffer)
   unsigned long long* u64;  // [4]: 0 node evaluations, 1 nominal lane-ops of the node sweep
   int* err;         // [1] sticky device error
   int* err_host;    // mapped host word mirroring err

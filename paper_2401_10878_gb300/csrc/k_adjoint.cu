@@ -11,9 +11,10 @@
 //   T_A = (x_c - X_A) x (-F), T_B = (x_c - X_B') x F.
 // k_adj_pre: FP64 chain rule from (gF, gT) to seeds dL/dS0, dL/dS1, dL/dSg
 //   and the explicit pose terms (torque arms, damping, fallback normal).
-// k_adj_cells: persistent tile sweep (same tiles as the forward pass); each
-//   line clipped to the nodes where both phi < w/2 (line_clip.cuh), every
-//   other node's terms being exact zeros; per node
+// k_adj_cells: persistent tile sweep (the forward's tiles, warp w taking
+//   tiles w, w + W, ...); each line clipped to the nodes where both phi < w/2
+//   (line_clip.cuh), every other node's terms being exact zeros, the clipped
+//   nodes spread one per lane; per node
 //   dL/dphi and dL/d(grad phi) pulled back to the 12 pose directions of the
 //   pair (translation and infinitesimal world rotation of each particle):
 //     dphi/dX = -grad phi,  dphi/domega = grad phi x r,
@@ -66,7 +67,6 @@ __global__ void __launch_bounds__(32) k_adj_pre(Params P, Shapes S, Parts D, Lis
                                                  const double* __restrict__ gT) {
   pdl_begin();
   const int np = min(W.counters[0], P.max_pairs);
-  if (blockIdx.x == 0 && threadIdx.x == 0) W.counters[6] = 0;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
     const PairRec pr = W.pairs[p];
     const double* tp = W.tape + static_cast<size_t>(p) * kTapeDoubles;
@@ -500,12 +500,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int ntiles = min(W.counters[1], P.max_tiles);
   const float inv_w = P.inv_w, hw = 0.5f * P.wdx_l, T = hw + kClipMargin;
-  int qpos = 0;
-  if (lane == 0) qpos = atomicAdd(&W.counters[6], 1);
-  qpos = __shfl_sync(kFull, qpos, 0);
-  while (qpos < ntiles) {
-    int qn = 0;
-    if (lane == 0) qn = atomicAdd(&W.counters[6], 1);
+  // tiles w, w + W, ... of the forward's list (W warps)
+  const int nwarps = gridDim.x * kWarps;
+  for (int qpos = blockIdx.x * kWarps + wid; qpos < ntiles; qpos += nwarps) {
     // the pair record's fields in registers (no runtime-indexed local copy)
     const PairRec& prg = W.tiles[qpos];
     const int p = prg.pair;
@@ -534,74 +531,99 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
       const int ax0 = axis, ax1 = ax0 == 2 ? 0 : ax0 + 1, ax2 = ax1 == 2 ? 0 : ax1 + 1;
       const int du = ax0 == 0 ? dm0 : (ax0 == 1 ? dm1 : dm2);
       const int dv = ax0 == 0 ? dm1 : (ax0 == 1 ? dm2 : dm0);   // side along (ax0 + 1) mod 3
+      // (A) each lane clips its line; (B) the warp's clipped nodes, numbered
+      // across the lanes by a scan of the counts, one per lane (its line by a
+      // binary search over the scan): the same node set as a walk of every
+      // line, with the work spread over the warp
+      auto node = [&](int cu, int l1, int l2) {
+        // node coordinates in box axes x, y, z (selects: no runtime-indexed array)
+        int c[3];
+        c[0] = ax0 == 0 ? cu : (ax0 == 1 ? l2 : l1);
+        c[1] = ax0 == 1 ? cu : (ax0 == 2 ? l2 : l1);
+        c[2] = ax0 == 2 ? cu : (ax0 == 0 ? l2 : l1);
+        float ra[3], rb[3], ga[3], gb[3], na, nb;
+        for (int k = 0; k < 3; ++k) {
+          ra[k] = static_cast<float>(c[k] - ai[k]) - af[k];
+          rb[k] = static_cast<float>(c[k] - bi[k]) - bf[k];
+        }
+        // every term below needs both phi inside the upper half of the band
+        if (fmaxf(adj_phi<SET>(A, ra), adj_phi<SET>(Bg, rb)) >= hw) return;
+        const float fa = adj_eval<SET>(A, ra, ga, &na);
+        const float fb = adj_eval<SET>(Bg, rb, gb, &nb);
+        const float ta = fminf(fmaxf(fmaf(fa, -inv_w, 0.5f), 0.f), 1.f);
+        const float tb = fminf(fmaxf(fmaf(fb, -inv_w, 0.5f), 0.f), 1.f);
+        const bool ina = ta > 0.f && ta < 1.f, inb = tb > 0.f && tb < 1.f;
+        const float Ha = ta * ta * (3.f - 2.f * ta), Hb = tb * tb * (3.f - 2.f * tb);
+        const float ha = ta * (1.f - ta), hb = tb * (1.f - tb);
+        // derivatives with respect to phi (lattice units); zero outside the band
+        const float dHa = ina ? -6.f * ha * inv_w : 0.f, dHb = inb ? -6.f * hb * inv_w : 0.f;
+        const float dha = ina ? -(1.f - 2.f * ta) * inv_w : 0.f, dhb = inb ? -(1.f - 2.f * tb) * inv_w : 0.f;
+        if (Ha * Hb == 0.f && ha * Hb == 0.f && Ha * hb == 0.f && dHa * Hb == 0.f && Ha * dHb == 0.f) return;
+        const float sw = fmaf(s1[0], static_cast<float>(c[0]),
+                              fmaf(s1[1], static_cast<float>(c[1]), fmaf(s1[2], static_cast<float>(c[2]), s0)));
+        const float gma = sg[0] * ga[0] + sg[1] * ga[1] + sg[2] * ga[2];
+        const float gmb = sg[0] * gb[0] + sg[1] * gb[1] + sg[2] * gb[2];
+        const float ka = sw * dHa * Hb + dha * Hb * gma - dHa * hb * gmb;
+        const float kb = sw * Ha * dHb + ha * dHb * gma - Ha * dhb * gmb;
+        float xa[3], xb[3];
+        cross3f(ga, ra, xa);
+        cross3f(gb, rb, xb);
+        for (int k = 0; k < 3; ++k) {
+          acc[k] -= ka * ga[k];
+          acc[3 + k] += ka * xa[k];
+          acc[6 + k] -= kb * gb[k];
+          acc[9 + k] += kb * xb[k];
+        }
+        const float wa = ha * Hb, wb = Ha * hb;
+        if (SET != 2 && A.type == 0) {
+          if (na > 0.f)
+            for (int k = 0; k < 3; ++k) acc[k] -= wa * (sg[k] - gma * ga[k]) / na;
+        } else {
+          float cr[3];
+          cross3f(ga, sg, cr);
+          for (int k = 0; k < 3; ++k) acc[3 + k] += wa * cr[k];
+        }
+        if (SET != 2 && Bg.type == 0) {
+          if (nb > 0.f)
+            for (int k = 0; k < 3; ++k) acc[6 + k] += wb * (sg[k] - gmb * gb[k]) / nb;
+        } else {
+          float cr[3];
+          cross3f(gb, sg, cr);
+          for (int k = 0; k < 3; ++k) acc[9 + k] -= wb * cr[k];
+        }
+      };
       const int it0 = (t - tile0) * 32 * kTileItemsPerLane;
       for (int s = 0; s < kTileItemsPerLane; ++s) {
-        const int it = it0 + s * 32 + lane;
-        if (it >= nitems) continue;
+        const int itb = it0 + s * 32;
+        if (itb >= nitems) break;
+        const int it = itb + lane;
         const int line = it / nseg, seg = it - line * nseg;
         const int l1 = line % dv, l2 = line / dv;   // coordinates along axes ax1, ax2
-        const int u0 = seg * seglen, u1 = min(u0 + seglen, du);
+        const int u0 = seg * seglen, u1 = it < nitems ? min(u0 + seglen, du) : u0;
         float clo = static_cast<float>(u0), chi = static_cast<float>(u1 - 1);
         adj_clip<SET>(A, ax0, ax1, ax2, l1, l2, ai, af, T, clo, chi);
         adj_clip<SET>(Bg, ax0, ax1, ax2, l1, l2, bi, bf, T, clo, chi);
         int ub;
         const int nk = clip_nodes(clo, chi, u0, u1 - u0, &ub);
-        for (int cu = ub; cu < ub + nk; ++cu) {
-          // node coordinates in box axes x, y, z (selects: no runtime-indexed array)
-          int c[3];
-          c[0] = ax0 == 0 ? cu : (ax0 == 1 ? l2 : l1);
-          c[1] = ax0 == 1 ? cu : (ax0 == 2 ? l2 : l1);
-          c[2] = ax0 == 2 ? cu : (ax0 == 0 ? l2 : l1);
-          float ra[3], rb[3], ga[3], gb[3], na, nb;
-          for (int k = 0; k < 3; ++k) {
-            ra[k] = static_cast<float>(c[k] - ai[k]) - af[k];
-            rb[k] = static_cast<float>(c[k] - bi[k]) - bf[k];
+        int incl = nk;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int v = __shfl_up_sync(kFull, incl, d);
+          if (lane >= d) incl += v;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - nk;
+        for (int base = 0; base < total; base += 32) {
+          const int g = base + lane;
+          int o = 0;   // owner: the last lane whose first node is <= g
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            const int e = __shfl_sync(kFull, excl, o + step);
+            if (e <= g) o += step;
           }
-          // every term below needs both phi inside the upper half of the band
-          if (fmaxf(adj_phi<SET>(A, ra), adj_phi<SET>(Bg, rb)) >= hw) continue;
-          const float fa = adj_eval<SET>(A, ra, ga, &na);
-          const float fb = adj_eval<SET>(Bg, rb, gb, &nb);
-          const float ta = fminf(fmaxf(fmaf(fa, -inv_w, 0.5f), 0.f), 1.f);
-          const float tb = fminf(fmaxf(fmaf(fb, -inv_w, 0.5f), 0.f), 1.f);
-          const bool ina = ta > 0.f && ta < 1.f, inb = tb > 0.f && tb < 1.f;
-          const float Ha = ta * ta * (3.f - 2.f * ta), Hb = tb * tb * (3.f - 2.f * tb);
-          const float ha = ta * (1.f - ta), hb = tb * (1.f - tb);
-          // derivatives with respect to phi (lattice units); zero outside the band
-          const float dHa = ina ? -6.f * ha * inv_w : 0.f, dHb = inb ? -6.f * hb * inv_w : 0.f;
-          const float dha = ina ? -(1.f - 2.f * ta) * inv_w : 0.f, dhb = inb ? -(1.f - 2.f * tb) * inv_w : 0.f;
-          if (Ha * Hb == 0.f && ha * Hb == 0.f && Ha * hb == 0.f && dHa * Hb == 0.f && Ha * dHb == 0.f) continue;
-          const float sw = fmaf(s1[0], static_cast<float>(c[0]),
-                                fmaf(s1[1], static_cast<float>(c[1]), fmaf(s1[2], static_cast<float>(c[2]), s0)));
-          const float gma = sg[0] * ga[0] + sg[1] * ga[1] + sg[2] * ga[2];
-          const float gmb = sg[0] * gb[0] + sg[1] * gb[1] + sg[2] * gb[2];
-          const float ka = sw * dHa * Hb + dha * Hb * gma - dHa * hb * gmb;
-          const float kb = sw * Ha * dHb + ha * dHb * gma - Ha * dhb * gmb;
-          float xa[3], xb[3];
-          cross3f(ga, ra, xa);
-          cross3f(gb, rb, xb);
-          for (int k = 0; k < 3; ++k) {
-            acc[k] -= ka * ga[k];
-            acc[3 + k] += ka * xa[k];
-            acc[6 + k] -= kb * gb[k];
-            acc[9 + k] += kb * xb[k];
-          }
-          const float wa = ha * Hb, wb = Ha * hb;
-          if (SET != 2 && A.type == 0) {
-            if (na > 0.f)
-              for (int k = 0; k < 3; ++k) acc[k] -= wa * (sg[k] - gma * ga[k]) / na;
-          } else {
-            float cr[3];
-            cross3f(ga, sg, cr);
-            for (int k = 0; k < 3; ++k) acc[3 + k] += wa * cr[k];
-          }
-          if (SET != 2 && Bg.type == 0) {
-            if (nb > 0.f)
-              for (int k = 0; k < 3; ++k) acc[6 + k] += wb * (sg[k] - gmb * gb[k]) / nb;
-          } else {
-            float cr[3];
-            cross3f(gb, sg, cr);
-            for (int k = 0; k < 3; ++k) acc[9 + k] -= wb * cr[k];
-          }
+          const int ol1 = __shfl_sync(kFull, l1, o), ol2 = __shfl_sync(kFull, l2, o);
+          const int ocu = __shfl_sync(kFull, ub, o) + (g - __shfl_sync(kFull, excl, o));
+          if (g < total) node(ocu, ol1, ol2);
         }
       }
     }
@@ -654,7 +676,6 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
         }
       }
     }
-    qpos = __shfl_sync(kFull, qn, 0);
     __syncwarp();
   }
   if (nst > 0) {
