@@ -590,13 +590,15 @@ __global__ void __launch_bounds__(kBoxWarps * 32, 2) k_box_pairs(Params P, Shape
 
 void launch_box(const Params& P, const Shapes& S, const Parts& D, const Lists& W, const double* vel, double* pair_out,
                 int grid, cudaStream_t st) {
-  // the node sweep's kind set: 2 cubes only, 1 spheres / cuboids / walls, 0 every kind
-  if (P.kind_set == 2)
-    launch_pdl(k_box_pairs<2>, dim3(grid), dim3(kBoxWarps * 32), 0, st, P, S, D, W, vel, pair_out);
-  else if (P.kind_set == 1)
-    launch_pdl(k_box_pairs<1>, dim3(grid), dim3(kBoxWarps * 32), 0, st, P, S, D, W, vel, pair_out);
-  else
-    launch_pdl(k_box_pairs<0>, dim3(grid), dim3(kBoxWarps * 32), 0, st, P, S, D, W, vel, pair_out);
+  // the node sweep's kind set: 2 cubes only, 1 spheres / cuboids / walls, 0 every kind;
+  // persistent: as many blocks as are resident (the kernel's own occupancy)
+  auto kern = P.kind_set == 2 ? k_box_pairs<2> : (P.kind_set == 1 ? k_box_pairs<1> : k_box_pairs<0>);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBoxWarps * 32, 0);
+  const int g = sms > 0 && per_sm > 0 ? sms * per_sm : grid;
+  launch_pdl(kern, dim3(g), dim3(kBoxWarps * 32), 0, st, P, S, D, W, vel, pair_out);
 }
 
 }  // namespace gbc
