@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--workload", default="cubes1934", choices=sorted(WORKLOADS),
                     help="state of the main line (default: the headline, 1934 cubes)")
     ap.add_argument("--seed", type=int, default=None, help="seed of the state (default: the workload's own)")
+    ap.add_argument("--cpu-threads", type=int, default=0,
+                    help="threads of the oracle in --impl reference (default: all host cores)")
+    ap.add_argument("--backward", action="store_true",
+                    help="--impl reference: each step also takes the oracle's FP64 gradient of the smoothed "
+                         "workload's force/torque loss (the adjoint's CPU baseline)")
     return ap.parse_args()
 
 
@@ -106,6 +111,10 @@ WORKLOADS = {
     "mixed27": ("27 particles (14 spheres d = 15, 13 cubes edge 12) on a jittered 3x3x3 grid, periodic 64^3 "
                 "lattice", "mixed_grid_27"),
 }
+# the resolution sweep: 500 cubes of edge e cells at 20 % (L = round(e 2500^(1/3)))
+for _e, _L in ((8, 109), (12, 163), (16, 217), (24, 326)):
+    WORKLOADS[f"sweep_e{_e}"] = (f"500 cubes (edge {_e}) at 20% volume fraction, periodic {_L}^3 lattice, half of them "
+                                 "axis-aligned on half-integer faces", ("resolution_sweep", _e))
 
 
 def workload_state(args, rank: int):
@@ -118,8 +127,9 @@ def workload_state(args, rank: int):
         st.indicator = 0
         st.name = "cubes1934_223"
         return st
-    fn = getattr(W, WORKLOADS[name][1])
-    st = fn() if seed is None and rank == 0 else fn(seed=(seed if seed is not None else 0) + 1000 * rank + 1)
+    spec = WORKLOADS[name][1]
+    fn, pre = (getattr(W, spec), ()) if isinstance(spec, str) else (getattr(W, spec[0]), spec[1:])
+    st = fn(*pre) if seed is None and rank == 0 else fn(*pre, seed=(seed if seed is not None else 0) + 1000 * rank + 1)
     st.indicator = 1 if name == "cubes1934_smooth" else 0
     if name == "cubes1934_smooth":
         st.smooth_width = 1.0
@@ -201,15 +211,21 @@ def run_reference(args, ws, rank):
     oracle.build()
     st = workload_state(args, 0)
     pos, quat = W.pose_sequence(st, max(args.steps + args.warmup, 1))
-    threads = oracle.max_threads()
+    threads = args.cpu_threads if args.cpu_threads > 0 else oracle.max_threads()
+    gf, gt = W.loss_weights(st.n)
     for s in range(args.warmup):
-        oracle.contact_step(st, pos=pos[s], quat=quat[s])
-    cells, secs = 0, 0.0
+        oracle.contact_step(st, pos=pos[s], quat=quat[s], n_threads=threads)
+    cells, secs, gsecs = 0, 0.0, 0.0
     for s in range(args.steps):
         k = args.warmup + s
-        r = oracle.contact_step(st, pos=pos[k], quat=quat[k])
+        r = oracle.contact_step(st, pos=pos[k], quat=quat[k], n_threads=threads)
         cells += r.cells
         secs += r.seconds
+        if args.backward:
+            t0 = time.perf_counter()
+            oracle.gradient(st, gf, gt, pos=pos[k], quat=quat[k], n_threads=threads)
+            gsecs += time.perf_counter() - t0
+    secs += gsecs
     v = cells / secs
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
@@ -217,8 +233,12 @@ def run_reference(args, ws, rank):
             "data": "synthetic", "config": workload_config(st, None, args.workload),
             "precision": "fp64 throughout (the oracle)",
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{args.steps} full contact steps of the workload (all pairs)"},
+                             "sample": f"{args.steps} full contact steps of the workload (all pairs)"
+                                       + (", each with the FP64 gradient of the force/torque loss" if args.backward
+                                          else "")},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if args.backward:
+        line["gradient_ms_per_step"] = 1e3 * gsecs / args.steps
     print(json.dumps(line), flush=True)
 
 
@@ -522,6 +542,11 @@ def extras(args, dev, flush, peak):
                                          "timing": f"CUDA events around {NARROW_REPEAT} back-to-back node-sweep runs"}}
     out["mixed1934_223"]["box_volume_percentiles_10_50_90_99"] = box_volume_percentiles(m, st, st.pos)
     m.close()
+    m = Contact.from_state(st, precision=FP64_PAIR, narrow_events=True)
+    r = time_forward(m, torch.tensor(pos, device=dev), torch.tensor(quat, device=dev), steps, 3, flush, narrow=True)
+    out["mixed1934_223"]["fp64_form"] = {"cell_evals_per_s": r["cells"] / (r["ms"] * 1e-3),
+                                         "ms_per_step": r["ms"] / steps, "narrow_ms": r["narrow_ms"] / steps}
+    m.close()
     # all-FP64 one-pair-per-block form on the headline workload
     st = headline_state(0)
     pos, quat = W.pose_sequence(st, steps + 3)
@@ -616,6 +641,7 @@ def extras(args, dev, flush, peak):
             m.close()
         return res
     out["cubes400_190"] = both_forms(W.settling_cubes(), steps)
+    out["mixed27_64"] = both_forms(W.mixed_grid_27(), steps)
     out["resolution_sweep"] = {f"edge{e}": both_forms(W.resolution_sweep(e), min(steps, 20)) for e in (8, 12, 16, 24)}
     # smoothed indicator: forward + adjoint
     st = W.settling_cubes_dense()

@@ -58,7 +58,11 @@ typedef enum {
                             smallest inscribed ball, plus 8)                   */
   CONTACT_EDOMAIN = 5,   /* periodic box too small for the largest particle   */
   CONTACT_ETIMEOUT = 6,  /* a bounded device wait ran out                     */
-  CONTACT_ESTATE = 7     /* call out of order (e.g. backward before a step)   */
+  CONTACT_ESTATE = 7,    /* call out of order (e.g. backward before a step)   */
+  CONTACT_EBOUNDS = 8    /* a device index check failed: only the checked
+                            build (compiled with -DCONTACT_CHECKS) tests the
+                            indices it reads from device lists; the access is
+                            skipped and the step's outputs are invalid       */
 } contact_status;
 
 enum { CONTACT_SHAPE_SPHERE = 0, CONTACT_SHAPE_CUBOID = 1, CONTACT_SHAPE_POLYTOPE = 2 };
@@ -165,7 +169,9 @@ void contact_config_default(contact_config* cfg, int32_t n_particles, const int3
  * Returns CONTACT_EINVAL for an invalid shape or configuration,
  * CONTACT_EDOMAIN when L <= 4 R_max + 2 dx on some axis (R_max = the largest
  * circumradius after inflation), so that at most one periodic image of a
- * partner can overlap a particle.  *out is NULL on failure. */
+ * partner can overlap a particle, or when 2 R_max / dx + 4 >= 65535 (a pair's
+ * node box spans fewer than 2^16 nodes along every axis).  *out is NULL on
+ * failure. */
 contact_status contact_init(const contact_config* cfg, const int32_t* shape_type, const double* shape_param,
                             const int32_t* face_offset, const double* planes, const double* young,
                             const double* poisson, void* stream, contact_ctx** out);
@@ -383,6 +389,16 @@ contact_status contact_fp32_ffma_rate(int32_t iters, double* ffma_per_s);
  * CONTACT_EINVAL for a bad argument, CONTACT_ENOMEM / CONTACT_ECUDA on a CUDA
  * failure. */
 contact_status contact_fp64_dfma_rate(int32_t iters, double* dfma_per_s);
+
+/* Self-test of the device index checks (no counterpart in the paper).
+ * Enqueues on the context stream one kernel that passes the index n to the
+ * check for an array of n entries (one past its end; nothing is accessed),
+ * then synchronises and reads the sticky error word like contact_check.  The
+ * checked build (libcontact_checks.so, compiled with -DCONTACT_CHECKS)
+ * returns CONTACT_EBOUNDS and keeps it sticky until contact_clear_error; the
+ * normal build compiles the check away and returns CONTACT_OK.
+ * CONTACT_EINVAL for a null context. */
+contact_status contact_bounds_selftest(contact_ctx* ctx);
 
 #ifdef __cplusplus
 }

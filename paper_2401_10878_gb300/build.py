@@ -16,6 +16,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcontact.so")
+# the checked build: every index read from a device list is tested
+# (-DCONTACT_CHECKS; a failed test sets CONTACT_EBOUNDS and skips the access)
+BUILD_CHECKS = os.path.join(HERE, "_build_checks")
+LIB_CHECKS = os.path.join(BUILD_CHECKS, "libcontact_checks.so")
 SOURCES = ["host.cu", "k_broad.cu", "k_narrow.cu", "k_boxmode.cu", "k_post.cu", "k_adjoint.cu", "noalloc.cu",
            "k_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -40,16 +44,20 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile (if sources changed) and return the path of libcontact.so."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checks: bool = False) -> str:
+    """Compile (if sources changed) and return the path of libcontact.so, or
+    with checks=True of the checked build libcontact_checks.so."""
+    out_dir, lib = (BUILD_CHECKS, LIB_CHECKS) if checks else (BUILD, LIB)
+    if checks:
+        extra_flags = tuple(extra_flags) + ("-DCONTACT_CHECKS",)
+    os.makedirs(out_dir, exist_ok=True)
     headers = [os.path.join(CSRC, "contact_dev.cuh"), os.path.join(CSRC, "force_law.cuh"),
                os.path.join(CSRC, "line_clip.cuh"),
                os.path.join(HERE, "..", "include", "contact.h")]
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(out_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
             jobs.append((s, o))
@@ -68,14 +76,14 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             for log in ex.map(compile_one, jobs):
                 if verbose and log:
                     print(log)
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-cudart", "static"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -19,9 +19,9 @@ import torch
 
 from . import build as _build
 
-OK, EINVAL, ENOMEM, ECUDA, ECAPACITY, EDOMAIN, ETIMEOUT, ESTATE = range(8)
+OK, EINVAL, ENOMEM, ECUDA, ECAPACITY, EDOMAIN, ETIMEOUT, ESTATE, EBOUNDS = range(9)
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECAPACITY", 5: "EDOMAIN", 6: "ETIMEOUT",
-          7: "ESTATE"}
+          7: "ESTATE", 8: "EBOUNDS"}
 SHARP, SMOOTH = 0, 1
 FP32_TILE, FP64_PAIR = 0, 1
 PAIR_OUT_COLS = 11
@@ -33,7 +33,7 @@ EXPORTS = ["contact_config_default", "contact_init", "contact_step", "contact_ba
            "contact_kernels_per_backward", "contact_destroy", "contact_step_noalloc", "contact_step_host",
            "contact_history_get", "contact_history_set", "contact_history_reset", "contact_polytope_centroid",
            "contact_polytope_shift", "contact_fp32_ffma_rate", "contact_fp64_dfma_rate",
-           "contact_adjoint_time"]
+           "contact_adjoint_time", "contact_bounds_selftest"]
 
 
 class Config(ctypes.Structure):
@@ -55,23 +55,23 @@ class ContactError(RuntimeError):
         self.code = code
 
 
-_lib = None
+_libs = {}
 
 
-def library_path() -> str:
-    return _build.LIB
+def library_path(checks: bool = False) -> str:
+    return _build.LIB_CHECKS if checks else _build.LIB
 
 
-def load_library(build_if_missing: bool = True):
-    """Load libcontact.so (compiling it first when missing and nvcc exists)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    path = _build.LIB
+def load_library(build_if_missing: bool = True, checks: bool = False):
+    """Load libcontact.so, or with checks=True the checked build
+    libcontact_checks.so (compiling it first when missing and nvcc exists)."""
+    if checks in _libs:
+        return _libs[checks]
+    path = library_path(checks)
     if not os.path.exists(path):
         if not build_if_missing:
             raise ContactError(ECUDA, f"{path} not built (run __graft_entry__.build())")
-        _build.build()
+        _build.build(checks=checks)
     lib = ctypes.CDLL(path)
     P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
     lib.contact_config_default.argtypes = [ctypes.POINTER(Config), I32, P, D]
@@ -96,6 +96,8 @@ def load_library(build_if_missing: bool = True):
     lib.contact_narrow_time.restype = I32
     lib.contact_adjoint_time.argtypes = [P, P]
     lib.contact_adjoint_time.restype = I32
+    lib.contact_bounds_selftest.argtypes = [P]
+    lib.contact_bounds_selftest.restype = I32
     lib.contact_particle_boxes.argtypes = [P, P]
     lib.contact_particle_boxes.restype = I32
     lib.contact_damping_factor.argtypes = [D, D]
@@ -124,7 +126,7 @@ def load_library(build_if_missing: bool = True):
     lib.contact_history_set.restype = I32
     lib.contact_history_reset.argtypes = [P]
     lib.contact_history_reset.restype = I32
-    _lib = lib
+    _libs[checks] = lib
     return lib
 
 
@@ -149,10 +151,10 @@ class Contact:
                  max_pairs=None, max_neighbors=64, max_tiles=0, use_graph=True, narrow_events=False,
                  history=False, restitution=1.0, friction=False, mu_s=0.0, mu_k=0.0, u_k=1.0,
                  walls=None, wall_young=None, wall_poisson=None, box_mode=0, contact_resolution=8,
-                 device=None, stream=None):
+                 device=None, stream=None, checks=False):
         if not torch.cuda.is_available():
             raise ContactError(ECUDA, "no CUDA device: the contact path has no CPU fallback")
-        self.lib = load_library()
+        self.lib = load_library(checks=checks)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         n = int(len(shape_type))
         cfg = Config()

@@ -30,6 +30,27 @@ constexpr int kFtDoubles = 9;         // per-pair F, T_A, T_B
 // Error codes written by kernels (same numbering as contact_status).
 constexpr int kErrInval = 1;
 constexpr int kErrCapacity = 4;
+constexpr int kErrBounds = 8;
+
+__device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0, code); }
+
+// Index checks of the checked build (-DCONTACT_CHECKS): an index read from a
+// device list (a partner, a pair, a tile, a bin) that lies outside [0, n)
+// sets the sticky error word to kErrBounds and is replaced by `safe` (an
+// index that is in range, or a value the caller already treats as "none"),
+// so the access it feeds stays inside its array and no lane leaves its warp.
+// In the normal build the index passes through unchanged and the check
+// compiles away.
+__device__ __forceinline__ int checked_index(int* err, int i, long long n, int safe) {
+#ifdef CONTACT_CHECKS
+  if (i >= 0 && static_cast<long long>(i) < n) return i;
+  set_error(err, kErrBounds);
+  return safe;
+#else
+  (void)err; (void)n; (void)safe;
+  return i;
+#endif
+}
 
 // --------------------------------------------------------------------------
 // Constant per-context parameters, passed to every kernel by value.
@@ -157,6 +178,24 @@ __device__ __forceinline__ bool wall_box(const double* e, double delta, double d
     }
   }
   return lo[0] <= hi[0] && lo[1] <= hi[1] && lo[2] <= hi[2];
+}
+
+// Checked build: a pair or tile record read from a device list names a pair,
+// two particles (j may be a wall) and tiles inside their arrays; otherwise the
+// sticky error word gets kErrBounds and the caller skips the record (its
+// value is warp-uniform, so the whole warp skips it).  Always true, and
+// compiled away, in the normal build.
+__device__ __forceinline__ bool record_in_bounds(const Params& P, int* err, const PairRec& r, bool tile_rec) {
+#ifdef CONTACT_CHECKS
+  bool ok = r.i >= 0 && r.i < P.n && r.j >= 0 && r.j < P.n + P.nwall && r.ntiles >= 0 && r.tile0 >= 0 &&
+            static_cast<long long>(r.tile0) + r.ntiles <= P.max_tiles;
+  if (tile_rec) ok = ok && r.pair >= 0 && r.pair < P.max_pairs && r.tile >= 0 && r.tile < r.ntiles;
+  if (!ok) set_error(err, kErrBounds);
+  return ok;
+#else
+  (void)P; (void)err; (void)r; (void)tile_rec;
+  return true;
+#endif
 }
 
 // Work lists shared by the step's kernels.
@@ -290,7 +329,6 @@ __device__ inline double sdf64(int type, const double* prm, const double* planes
   return best - inflate;
 }
 
-__device__ __forceinline__ void set_error(int* err, int code) { atomicCAS(err, 0, code); }
 
 // Exact FP32 -> FP64 conversion with integer operations (IEEE 754: sign kept,
 // exponent rebiased by 1023 - 127, fraction widened by 29 bits; subnormals

@@ -85,6 +85,9 @@ int bin_capacity(int n, const double binw[3], double rin_min, long long nbins, l
   cap = std::min<long long>(cap, std::max<long long>(1, max_entries / std::max<long long>(1, nbins)));
   return static_cast<int>(cap);
 }
+
+// contact_bounds_selftest: the index n checked against an array of n entries
+__global__ void k_bounds_selftest(int* err, int n) { (void)checked_index(err, n, n, 0); }
 }  // namespace gbc
 
 namespace {
@@ -225,6 +228,7 @@ contact_status check_sticky(contact_ctx* c) {
   if (e != 0) {
     return fail(c, static_cast<contact_status>(e),
                 e == CONTACT_ECAPACITY ? "device: capacity exceeded (pairs, neighbours or tiles)"
+                : e == CONTACT_EBOUNDS ? "device: an index read from a device list is out of range (checked build)"
                                        : "device: invalid pose (position outside [0, L), zero or non-finite quaternion)");
   }
   return CONTACT_OK;
@@ -458,6 +462,8 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
     L[k] = C.n_cells[k] * C.dx;
     if (!(L[k] > 4.0 * rmax + 2.0 * C.dx)) return CONTACT_EDOMAIN;
   }
+  // a pair box spans below 2^16 nodes along every axis (the node sweep packs node offsets in 16 bits)
+  if (!(2.0 * rmax / C.dx + 4.0 < 65535.0)) return CONTACT_EDOMAIN;
 
   contact_ctx* c = new contact_ctx();
   c->cfg = C;
@@ -756,6 +762,14 @@ contact_status contact_check(contact_ctx* c) {
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy");
   *c->err_host = err;
   return check_sticky(c);
+}
+
+contact_status contact_bounds_selftest(contact_ctx* c) {
+  if (c == nullptr) return CONTACT_EINVAL;
+  k_bounds_selftest<<<1, 1, 0, c->stream>>>(c->W.err, 1);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "bounds self-test launch");
+  return contact_check(c);
 }
 
 void contact_clear_error(contact_ctx* c) {

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(32) k_adj_pre(Params P, Shapes S, Parts D, Lis
     B.done[p] = 0;
     const double S0 = tp[0];
     const double fmag = tp[12];
-    if (!(S0 > 0.0)) continue;
+    if (!(S0 > 0.0) || !record_in_bounds(P, W.err, pr, false)) continue;
     const int i = pr.i, j = pr.j;
     const double dx = P.dx;
     double XA[3], XB[3], xc[3], n[3], F[3], rA[3], rB[3], gFi[3], gFj[3], gTi[3], gTj[3];
@@ -505,6 +505,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
   for (int qpos = blockIdx.x * kWarps + wid; qpos < ntiles; qpos += nwarps) {
     // the pair record's fields in registers (no runtime-indexed local copy)
     const PairRec& prg = W.tiles[qpos];
+    if (!record_in_bounds(P, W.err, prg, true)) continue;   // warp-uniform (checked build only)
     const int p = prg.pair;
     const int t = prg.tile0 + prg.tile;   // the tile's index (its partial slot)
     const int rec_i = prg.i, rec_j = prg.j, axis = prg.axis, nseg = prg.nseg, seglen = prg.seglen;
@@ -709,7 +710,8 @@ __global__ void __launch_bounds__(32) k_adj_scatter(Params P, Parts D, Lists W, 
       for (int u = 0; u < 8; ++u) {
         const int e = base + u;
         const bool isj = e < nd;   // p is the pair's j: columns 6..11; else its i: columns 0..5
-        const int q = isj ? dp[e] : (e < total ? r0 + (e - nd) : np);
+        int q = isj ? dp[e] : (e < total ? r0 + (e - nd) : np);
+        if (e < total) q = checked_index(W.err, q, np, -1);
         v[u] = (q >= 0 && q < np) ? B.pgrad[static_cast<size_t>(q) * kPairGrad + (isj ? 6 + c : c)] : 0.0;
       }
 #pragma unroll

@@ -238,6 +238,7 @@ __global__ void __launch_bounds__(kBoxWarps * 32, 2) k_box_pairs(Params P, Shape
     q = __shfl_sync(kFull, q, 0);
     if (q >= np) break;
     const PairRec& r = W.pairs[q];
+    if (!record_in_bounds(P, W.err, r, false)) continue;   // warp-uniform (checked build only)
     const int i = r.i, j = r.j;
     const int d0 = r.dim[0], d1 = r.dim[1], d2 = r.dim[2];
     ShapeF A, B;

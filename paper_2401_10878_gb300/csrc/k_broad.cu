@@ -279,7 +279,8 @@ __global__ void k_pose(Params P, Shapes S, Parts D, Lists W, const double* __res
   if (k == 0) {
     int b[3];
     for (int cc = 0; cc < 3; ++cc) b[cc] = min(max(static_cast<int>(xs[cc] * P.inv_binw_f[cc]), 0), P.nbin[cc] - 1);
-    const int bin = b[0] + P.nbin[0] * (b[1] + P.nbin[1] * b[2]);
+    const int bin = checked_index(W.err, b[0] + P.nbin[0] * (b[1] + P.nbin[1] * b[2]),
+                                  static_cast<long long>(P.nbin[0]) * P.nbin[1] * P.nbin[2], 0);
     D.bin[p] = bin;
     const int slot = atomicAdd(&W.bin_count[bin], 1);
     if (slot < P.bin_cap) W.bin_items[static_cast<size_t>(bin) * P.bin_cap + slot] = p;
@@ -368,7 +369,8 @@ __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
       const int c = P.nbin[k] >= 3 ? b[k] + o[k] - 1 : o[k];
       o[k] = (c + P.nbin[k]) % P.nbin[k];
     }
-    const int q = o[0] + P.nbin[0] * (o[1] + P.nbin[1] * o[2]);
+    const int q = checked_index(W.err, o[0] + P.nbin[0] * (o[1] + P.nbin[1] * o[2]),
+                                static_cast<long long>(P.nbin[0]) * P.nbin[1] * P.nbin[2], bin);
     num = min(W.bin_count[q], P.bin_cap);
     items += static_cast<size_t>(q) * P.bin_cap;
   }
@@ -378,7 +380,7 @@ __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
   for (int t0 = 0; t0 < maxn; t0 += 4) {
     int jj[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) jj[u] = t0 + u < num ? items[t0 + u] : -1;
+    for (int u = 0; u < 4; ++u) jj[u] = t0 + u < num ? checked_index(W.err, items[t0 + u], P.n, -1) : -1;
     float xj[4][3];
     int jlo[4][3], jhi[4][3];
 #pragma unroll
@@ -687,12 +689,13 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
     unsigned long long vol = 0, ops = 0;
     if (active) {
       pi = row + r;
-      const int j = base == 0 ? jpre : W.up_list[static_cast<size_t>(i) * cap + r];
+      const int j = checked_index(W.err, base == 0 ? jpre : W.up_list[static_cast<size_t>(i) * cap + r],
+                                  P.n + P.nwall, i);
       // j's lower-partner list, fetched with j's particle data (slot of this pair below);
       // a wall (j >= n) has none
       const bool wall = j >= P.n;
       const int* dl = W.dn_list + static_cast<size_t>(wall ? 0 : j) * cap;
-      const int dc = wall ? 0 : W.dn_count[j];
+      const int dc = wall ? 0 : checked_index(W.err, W.dn_count[j], cap + 1, 0);
       int dpre[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) dpre[u] = u < cap ? dl[u] : 0;
@@ -792,7 +795,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
 #pragma unroll
       for (int u = 0; u < 8; ++u) a0 += (u < dc && dpre[u] < i) ? 1 : 0;
       for (int b = 8; b < dc; ++b) a0 += dl[b] < i ? 1 : 0;
-      if (!wall) W.dn_pair[static_cast<size_t>(j) * cap + a0] = pi;
+      if (!wall) W.dn_pair[static_cast<size_t>(j) * cap + checked_index(W.err, a0, cap, 0)] = pi;
     }
     // allocations aggregated over the block (one atomic per counter and
     // block, all in flight together): the pairs' tiles, contiguous per pair;

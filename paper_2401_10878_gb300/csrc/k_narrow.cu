@@ -87,7 +87,6 @@ struct SphereEval {
   int iu, iv, iw;
   float fu, fv, fw, rad;
   float cnt_u, rv, rw, rho2, ru, q;
-  float nv, nw, nrho2;   // the node's line (pull)
   float gu, gv, gw, gl;
   __device__ void load(const PairRec& r, bool second, const Shapes&, const Parts&, const Local& L, float4*) {
     const int* ci = second ? r.bi : r.ai;
@@ -112,19 +111,10 @@ struct SphereEval {
     lo = l + o;
     hi = h + o;
   }
-  // the next phi() evaluates node u of lane o's line (its terms by shuffle:
-  // the same values begin_line gives on that line)
-  __device__ __forceinline__ void pull(int o, int u) {
-    nv = __shfl_sync(kFull, rv, o);
-    nw = __shfl_sync(kFull, rw, o);
-    nrho2 = __shfl_sync(kFull, rho2, o);
-    gl = 0.f;
-    cnt_u = static_cast<float>(u - iu) - 1.f;
-  }
   __device__ __forceinline__ float phi() {
     cnt_u += 1.f;
     ru = cnt_u - fu;
-    q = fmaf(ru, ru, nrho2);
+    q = fmaf(ru, ru, rho2);
     return sqrtf(q) - rad;
   }
   __device__ __forceinline__ void grad(float m) {
@@ -133,8 +123,8 @@ struct SphereEval {
     gl += mi;
   }
   __device__ __forceinline__ void end_line() {
-    gv = fmaf(gl, nv, gv);
-    gw = fmaf(gl, nw, gw);
+    gv = fmaf(gl, rv, gv);
+    gw = fmaf(gl, rw, gw);
   }
   __device__ float world(int c, const Local& L, const PairRec&, bool) const { return world_comp(c, L, gu, gv, gw); }
 };
@@ -144,7 +134,6 @@ struct CuboidEval {
   float fu, fv, fw;
   float tu[3], tv[3], tw[3], h[3], itu[3];
   float cnt_u, p[3], y[3], a[3];
-  float np_[3];   // the node's line (pull)
   float gb[3];
   __device__ void load(const PairRec& r, bool second, const Shapes&, const Parts&, const Local& L, float4*) {
     const int* ci = second ? r.bi : r.ai;
@@ -180,16 +169,11 @@ struct CuboidEval {
     lo = l + o;
     hi = hh + o;
   }
-  __device__ __forceinline__ void pull(int o, int u) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) np_[k] = __shfl_sync(kFull, p[k], o);
-    cnt_u = static_cast<float>(u - iu) - 1.f;
-  }
   __device__ __forceinline__ float phi() {
     cnt_u += 1.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      y[k] = fmaf(tu[k], cnt_u, np_[k]);
+      y[k] = fmaf(tu[k], cnt_u, p[k]);
       a[k] = fabsf(y[k]) - h[k];
     }
     return fmaxf(a[0], fmaxf(a[1], a[2]));
@@ -217,7 +201,6 @@ struct CubeEval {
   int iu;
   float fu, tu0, tu1, tu2, h, itu0, itu1, itu2;
   float cnt_u, p0, p1, p2, y0, y1, y2;
-  float n0, n1, n2;   // the node's line (pull)
   float gb0, gb1, gb2;
   __device__ void load(const PairRec& r, bool second, const Shapes&, const Parts&, const Local& L, float4*) {
     const int* ci = second ? r.bi : r.ai;
@@ -251,17 +234,11 @@ struct CubeEval {
     lo = l + o;
     hi = hh + o;
   }
-  __device__ __forceinline__ void pull(int o, int u) {
-    n0 = __shfl_sync(kFull, p0, o);
-    n1 = __shfl_sync(kFull, p1, o);
-    n2 = __shfl_sync(kFull, p2, o);
-    cnt_u = static_cast<float>(u - iu) - 1.f;
-  }
   __device__ __forceinline__ float phi() {
     cnt_u += 1.f;
-    y0 = fmaf(tu0, cnt_u, n0);
-    y1 = fmaf(tu1, cnt_u, n1);
-    y2 = fmaf(tu2, cnt_u, n2);
+    y0 = fmaf(tu0, cnt_u, p0);
+    y1 = fmaf(tu1, cnt_u, p1);
+    y2 = fmaf(tu2, cnt_u, p2);
     return fmaxf(fabsf(y0), fmaxf(fabsf(y1), fabsf(y2))) - h;
   }
   __device__ __forceinline__ void grad(float m) {
@@ -308,7 +285,6 @@ struct PolyEval {
   float fu, fv, fw;
   const float4* sp;
   float cnt_u, ru, rv, rw;
-  float nv, nw;   // the node's line (pull)
   float gu, gv, gw;
   __device__ void load(const PairRec& r, bool second, const Shapes& S, const Parts& D, const Local& L,
                        float4* sm) {
@@ -336,14 +312,9 @@ struct PolyEval {
     lo = l + o;
     hi = h + o;
   }
-  __device__ __forceinline__ void pull(int o, int u) {
-    nv = __shfl_sync(kFull, rv, o);
-    nw = __shfl_sync(kFull, rw, o);
-    cnt_u = static_cast<float>(u - iu) - 1.f;
-  }
   __device__ __forceinline__ float value(int f) const {
     const float4 e = sp[f];
-    return fmaf(e.x, ru, fmaf(e.y, nv, fmaf(e.z, nw, -e.w)));
+    return fmaf(e.x, ru, fmaf(e.y, rv, fmaf(e.z, rw, -e.w)));
   }
   __device__ __forceinline__ float phi() {
     cnt_u += 1.f;
@@ -375,7 +346,7 @@ struct PolyEval {
 // FP32 keeps them to ~1e-6.
 struct WallEval {
   float mu_, mv_, mw_, p0, imu_;
-  float base, nbase, cnt_u, g;   // nbase: the node's line (pull)
+  float base, cnt_u, g;
   __device__ void load(const PairRec& r, bool second, const Shapes&, const Parts&, const Local& L, float4*) {
     const float* rt = second ? r.rtb : r.rta;   // row 0: the wall normal m (world)
     mu_ = rt[L.u]; mv_ = rt[L.v]; mw_ = rt[L.w];
@@ -388,13 +359,9 @@ struct WallEval {
     cnt_u = static_cast<float>(u0) - 1.f;
   }
   __device__ __forceinline__ void clip(float T, float& lo, float& hi) const { clip_half(mu_, imu_, base, T, lo, hi); }
-  __device__ __forceinline__ void pull(int o, int u) {
-    nbase = __shfl_sync(kFull, base, o);
-    cnt_u = static_cast<float>(u) - 1.f;
-  }
   __device__ __forceinline__ float phi() {
     cnt_u += 1.f;
-    return fmaf(mu_, cnt_u, nbase);
+    return fmaf(mu_, cnt_u, base);
   }
   __device__ __forceinline__ void grad(float m) { g += m; }
   __device__ __forceinline__ void end_line() {}
@@ -431,16 +398,21 @@ __device__ __forceinline__ int float_key(float f) {
 }
 __device__ __forceinline__ float key_float(int k) { return __int_as_float(k >= 0 ? k : (k ^ 0x7fffffff)); }
 
-// Two phases per slot of 32 lines.  (A) Each lane clips its line to the
-// nodes where both distances lie below w/2 (+ the clip margin).  (B) The
-// warp's clipped nodes, typically a dozen spread over a few lines, are
-// numbered across the lanes (a scan of the counts) and each lane evaluates
-// one of them: its line is found by a binary search over the scan, the
-// evaluators restart on that line, and the node gets exactly the
+// Two phases per tile.  (A) Lane l clips its lines it0 + 32 s + l (s <
+// kTileItemsPerLane) to the nodes where both distances lie below w/2 (+ the
+// clip margin) and keeps each clipped range's first node and count.  (B) The
+// tile's clipped nodes, typically a few dozen spread over a few lines, are
+// numbered lane by lane (a scan of the lanes' counts), each lane's in slot
+// order, and each lane evaluates one of them: the owning lane by a binary
+// search over the scan, the slot by the owner's counts, and the evaluators
+// start that node's line at the node itself, so the node gets exactly the
 // arithmetic of a node walk (the same FP32 distances, bit for bit).
-template <bool SMOOTH, class EA, class EB>
+// ROLL (the kernel with every kind, nine kind pairs): the slot loops stay
+// rolled, with the slots' clipped ranges in shared memory, to keep the
+// kernel's code small; otherwise they are unrolled over registers.
+template <bool SMOOTH, bool ROLL, class EA, class EB>
 __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, const Parts& D, const PairRec& r,
-                                              bool swap, int tl, float4* smA, float4* smB) {
+                                              bool swap, int tl, float4* smA, float4* smB, unsigned* spk) {
   const int lane = threadIdx.x & 31;
   const Local L = make_local(r);
   EA A;
@@ -452,79 +424,103 @@ __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, 
   const float inv_w = P.inv_w, hw = 0.5f * P.wdx_l, T = hw + kClipMargin;
   float cnt = 0.f, mu = 0.f, mv = 0.f, mw = 0.f, bestf = -FLT_MAX;
   int bestidx = 0x7fffffff;
-  bool touched = false;
   const int it0 = tl * 32 * kTileItemsPerLane;
+  const int ns = min(kTileItemsPerLane, (r.nitems - it0 + 31) >> 5);   // slots of this tile (warp-uniform)
+  // (A) per slot: first clipped node (low 16 bits) and count (high 16 bits);
+  // a pair box is below 2^16 nodes along an axis
+  unsigned pk[kTileItemsPerLane];
+  int nl = 0;
+#pragma unroll(ROLL ? 1 : kTileItemsPerLane)
   for (int s = 0; s < kTileItemsPerLane; ++s) {
-    const int itb = it0 + s * 32;
-    if (itb >= r.nitems) break;
-    // (A) this lane's line it = cw * dv + cv, clipped to [ub, ub + nk)
-    const int it = itb + lane;
-    int cv;
-    const int cw = div_small(it, dv, inv_dv, &cv);
-    const int len = it < r.nitems ? du : 0;
-    begin_line_of(A, r, swap, L, cv, cw, 0, 0);
-    begin_line_of(B, r, !swap, L, cv, cw, 0, 0);
-    float clo = 0.f, chi = static_cast<float>(len - 1);
-    A.clip(T, clo, chi);
-    B.clip(T, clo, chi);
-    int ub;
-    const int nk = clip_nodes(clo, chi, 0, len, &ub);
-    int incl = nk;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int v = __shfl_up_sync(kFull, incl, d);
-      if (lane >= d) incl += v;
+    if (!ROLL) pk[s] = 0u;
+    if (s < ns) {
+      const int it = it0 + s * 32 + lane;
+      int cv;
+      const int cw = div_small(it, dv, inv_dv, &cv);
+      const int len = it < r.nitems ? du : 0;
+      begin_line_of(A, r, swap, L, cv, cw, 0, 0);
+      begin_line_of(B, r, !swap, L, cv, cw, 0, 0);
+      float clo = 0.f, chi = static_cast<float>(len - 1);
+      A.clip(T, clo, chi);
+      B.clip(T, clo, chi);
+      int ub;
+      const int nk = clip_nodes(clo, chi, 0, len, &ub);
+      const unsigned v = static_cast<unsigned>(ub) | (static_cast<unsigned>(nk) << 16);
+      if constexpr (ROLL) spk[s * 32 + lane] = v;
+      else pk[s] = v;
+      nl += nk;
     }
-    const int total = __shfl_sync(kFull, incl, 31);
-    if (total == 0) continue;
-    touched = true;
-    const int excl = incl - nk;
-    // (B) node g of the warp's clipped nodes on lane g mod 32
-    for (int base = 0; base < total; base += 32) {
-      const int g = base + lane;
-      int o = 0;   // owner: the last lane whose first node is <= g
+  }
+  if (ROLL) __syncwarp();
+  int incl = nl;
 #pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int e = __shfl_sync(kFull, excl, o + step);
-        if (e <= g) o += step;
-      }
-      const int ocv = __shfl_sync(kFull, cv, o), ocw = __shfl_sync(kFull, cw, o);
-      const int u = __shfl_sync(kFull, ub, o) + (g - __shfl_sync(kFull, excl, o));
-      A.pull(o, u);
-      B.pull(o, u);
-      const float fa = A.phi();
-      const float fb = B.phi();
-      // W > 0, or a band term of the normal: max < w/2 and (sharp) min <= 0
-      const bool any = g < total && fmaxf(fa, fb) < hw && (SMOOTH || fminf(fa, fb) <= 0.f);
-      const float ta = __saturatef(fmaf(fa, -inv_w, 0.5f));
-      const float tb = __saturatef(fmaf(fb, -inv_w, 0.5f));
-      float w, ma, mb;
-      if (SMOOTH) {
-        const float ha = ta * ta * fmaf(-2.f, ta, 3.f);
-        const float hb = tb * tb * fmaf(-2.f, tb, 3.f);
-        w = any ? ha * hb : 0.f;
-        ma = any ? fmaf(-ta, ta, ta) * hb : 0.f;
-        mb = any ? ha * fmaf(-tb, tb, tb) : 0.f;
-      } else {
-        w = (any && fmaxf(fa, fb) <= 0.f) ? 1.f : 0.f;
-        ma = (any && fb <= 0.f) ? fmaf(-ta, ta, ta) : 0.f;
-        mb = (any && fa <= 0.f) ? fmaf(-tb, tb, tb) : 0.f;
-      }
-      cnt += w;
-      mu = fmaf(w, static_cast<float>(u), mu);
-      mv = fmaf(w, static_cast<float>(ocv), mv);
-      mw = fmaf(w, static_cast<float>(ocw), mw);
-      const float f = -(fa + fb);
-      const int idx = u * L.su + ocv * L.sv + ocw * L.sw;
-      if (w > 0.f && (f > bestf || (f == bestf && idx < bestidx))) {
-        bestf = f;
-        bestidx = idx;
-      }
-      A.grad(ma);
-      B.grad(mb);
-      A.end_line();
-      B.end_line();
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += v;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  const int excl = incl - nl;
+  // (B) node g of the tile's clipped nodes on lane g mod 32
+  for (int base = 0; base < total; base += 32) {
+    const int g = base + lane;
+    int o = 0;   // owner: the last lane whose first node is <= g
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int e = __shfl_sync(kFull, excl, o + step);
+      if (e <= g) o += step;
     }
+    int k = g - __shfl_sync(kFull, excl, o);   // the node's rank among the owner's
+    int os = 0, u = 0;
+#pragma unroll(ROLL ? 1 : kTileItemsPerLane)
+    for (int s = 0; s < kTileItemsPerLane; ++s) {
+      if (s < ns) {
+        unsigned q;
+        if constexpr (ROLL) q = spk[s * 32 + o];
+        else q = __shfl_sync(kFull, pk[s], o);
+        const int n = static_cast<int>(q >> 16);
+        if (k >= 0 && k < n) {
+          os = s;
+          u = static_cast<int>(q & 0xffffu) + k;
+        }
+        k -= n;
+      }
+    }
+    int ocv;
+    const int ocw = div_small(it0 + os * 32 + o, dv, inv_dv, &ocv);
+    begin_line_of(A, r, swap, L, ocv, ocw, u, 0);
+    begin_line_of(B, r, !swap, L, ocv, ocw, u, 0);
+    const float fa = A.phi();
+    const float fb = B.phi();
+    // W > 0, or a band term of the normal: max < w/2 and (sharp) min <= 0
+    const bool any = g < total && fmaxf(fa, fb) < hw && (SMOOTH || fminf(fa, fb) <= 0.f);
+    const float ta = __saturatef(fmaf(fa, -inv_w, 0.5f));
+    const float tb = __saturatef(fmaf(fb, -inv_w, 0.5f));
+    float w, ma, mb;
+    if (SMOOTH) {
+      const float ha = ta * ta * fmaf(-2.f, ta, 3.f);
+      const float hb = tb * tb * fmaf(-2.f, tb, 3.f);
+      w = any ? ha * hb : 0.f;
+      ma = any ? fmaf(-ta, ta, ta) * hb : 0.f;
+      mb = any ? ha * fmaf(-tb, tb, tb) : 0.f;
+    } else {
+      w = (any && fmaxf(fa, fb) <= 0.f) ? 1.f : 0.f;
+      ma = (any && fb <= 0.f) ? fmaf(-ta, ta, ta) : 0.f;
+      mb = (any && fa <= 0.f) ? fmaf(-tb, tb, tb) : 0.f;
+    }
+    cnt += w;
+    mu = fmaf(w, static_cast<float>(u), mu);
+    mv = fmaf(w, static_cast<float>(ocv), mv);
+    mw = fmaf(w, static_cast<float>(ocw), mw);
+    const float f = -(fa + fb);
+    const int idx = u * L.su + ocv * L.sv + ocw * L.sw;
+    if (w > 0.f && (f > bestf || (f == bestf && idx < bestidx))) {
+      bestf = f;
+      bestidx = idx;
+    }
+    A.grad(ma);
+    B.grad(mb);
+    A.end_line();
+    B.end_line();
   }
   Partial o;
   o.cnt = cnt;
@@ -536,7 +532,7 @@ __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, 
   o.gz = A.world(2, L, r, swap) - B.world(2, L, r, !swap);
   o.bestf = bestf;
   o.bestidx = bestidx;
-  o.touched = touched;
+  o.touched = total > 0;
   return o;
 }
 
@@ -703,7 +699,7 @@ enum KindSet : int { SET_ALL = 0, SET_SC = 1, SET_CUBE = 2 };
 
 template <bool SMOOTH, int SET>
 __device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, const Parts& D, const PairRec& r,
-                                            int tl, float4* smA, float4* smB) {
+                                            int tl, float4* smA, float4* smB, unsigned* spk) {
   // kind order for canonical pairs: wall < sphere < cube < cuboid < polytope (kind 2 unused)
   constexpr int rank[6] = {1, 3, 6, 5, 2, 0};
   int ka = r.kinds & 0xff, kb = r.kinds >> 8;
@@ -718,10 +714,10 @@ __device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, co
   Partial o{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -FLT_MAX, 0x7fffffff, false};
 #define GBC_CASE(KA, KB, TA, TB)                                                  \
   case (KA) * 8 + (KB):                                                          \
-    o = sweep_tile<SMOOTH, TA, TB>(P, S, D, r, swap, tl, smA, smB);              \
+    o = sweep_tile<SMOOTH, SET == SET_ALL, TA, TB>(P, S, D, r, swap, tl, smA, smB, spk); \
     break;
   if constexpr (SET == SET_CUBE) {
-    o = sweep_tile<SMOOTH, CubeEval, CubeEval>(P, S, D, r, swap, tl, smA, smB);
+    o = sweep_tile<SMOOTH, false, CubeEval, CubeEval>(P, S, D, r, swap, tl, smA, smB, spk);
   } else if constexpr (SET == SET_SC) {
     switch (ka * 8 + kb) {
       GBC_CASE(0, 0, SphereEval, SphereEval)
@@ -775,6 +771,7 @@ __global__ void __launch_bounds__(kWarps * 32, SET == 0 ? 2 : 3) k_narrow32(Para
                                                                                   double* pair_out) {
   __shared__ __align__(16) PairRec s_rec[kWarps][2];
   __shared__ float4 s_planes[kWarps][2][kMaxFaces + kMaxFaces / 4];   // planes, then their inverse slopes
+  __shared__ unsigned s_pk[SET == SET_ALL ? kWarps : 1][kTileItemsPerLane * 32];   // clipped ranges (rolled sweep)
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int ntiles = W.counters[1];
@@ -791,8 +788,11 @@ __global__ void __launch_bounds__(kWarps * 32, SET == 0 ? 2 : 3) k_narrow32(Para
     const int tn = t + nwarps;
     const int4 next = tn < ntiles ? load_rec_part(W.tiles + tn, lane) : make_int4(0, 0, 0, 0);
     const PairRec& r = s_rec[wid][buf];
-    const Partial o = dispatch<SMOOTH, SET>(P, S, D, r, r.tile, s_planes[wid][0], s_planes[wid][1]);
-    tile_done(P, W, r, pair_out, o.touched ? reduce_tile<SMOOTH>(o) : empty_partial());
+    if (record_in_bounds(P, W.err, r, true)) {
+      const Partial o = dispatch<SMOOTH, SET>(P, S, D, r, r.tile, s_planes[wid][0], s_planes[wid][1],
+                                              s_pk[SET == SET_ALL ? wid : 0]);
+      tile_done(P, W, r, pair_out, o.touched ? reduce_tile<SMOOTH>(o) : empty_partial());
+    }
     __syncwarp();
     if (tn < ntiles) store_rec_part(&s_rec[wid][buf ^ 1], lane, next);
     __syncwarp();
@@ -851,6 +851,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_force(Params P, Shapes S, Parts
       }
       mask &= ~take;
       __syncwarp();
+#ifdef CONTACT_CHECKS
+      if (lane < n) {   // the staged entries' pair and particles
+        OvlRec& e = s_ovl[wid][lane];
+        e.q = checked_index(W.err, e.q, P.max_pairs, 0);
+        e.i = checked_index(W.err, e.i, P.n, 0);
+        e.j = checked_index(W.err, e.j, P.n + P.nwall, 0);
+      }
+      __syncwarp();
+#endif
       flush_overlaps<SET, LAW>(P, S, D, W, vel, pair_out, s_ovl[wid], n);
     }
   }
@@ -869,6 +878,7 @@ __global__ void __launch_bounds__(256) k_narrow64(Params P, Shapes S, Parts D, L
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int p = blockIdx.x; p < np; p += gridDim.x) {
     const PairRec pr = W.pairs[p];
+    if (!record_in_bounds(P, W.err, pr, false)) continue;   // block-uniform (checked build only)
     const int i = pr.i, j = pr.j;
     double XA[3], XB[3], RA[9], RB[9];
     for (int k = 0; k < 3; ++k) {

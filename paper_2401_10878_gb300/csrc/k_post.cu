@@ -47,7 +47,8 @@ __global__ void __launch_bounds__(32) k_particle_sum(Params P, Parts D, Lists W,
     for (int u = 0; u < 8; ++u) {
       const int e = base + u;
       const bool isj = e < nd;
-      const int q = isj ? (base == 0 ? pre[u] : dp[e]) : (e < total ? r0 + (e - nd) : np);
+      int q = isj ? (base == 0 ? pre[u] : dp[e]) : (e < total ? r0 + (e - nd) : np);
+      if (e < total) q = checked_index(W.err, q, np, -1);
       const bool ok = q >= 0 && q < np;
       const long long b = ok ? __double_as_longlong(W.ft[static_cast<size_t>(q) * kFtDoubles + (isj ? offj : offi)]) : 0LL;
       v[u] = __longlong_as_double(isj ? b : b ^ flip_i);

@@ -174,6 +174,7 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
     P.ncell[k] = C.n_cells[k];
     P.L[k] = C.n_cells[k] * C.dx;
     if (!(P.L[k] > 4.0 * rmax + 2.0 * C.dx)) return CONTACT_EDOMAIN;
+    if (!(2.0 * rmax / C.dx + 4.0 < 65535.0)) return CONTACT_EDOMAIN;
     int nb = static_cast<int>(std::floor(P.L[k] / (2.0 * rmax + 2.0 * C.dx)));
     if (nb < 3) nb = 1;
     P.nbin[k] = std::min(nb, kMaxBinsPerAxis);
