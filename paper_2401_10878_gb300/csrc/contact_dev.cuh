@@ -52,6 +52,17 @@ __device__ __forceinline__ int checked_index(int* err, int i, long long n, int s
 #endif
 }
 
+// floor(a / b) and the remainder for small non-negative ints via an FP32
+// reciprocal, corrected by one step (exact for a < 2^22)
+__device__ __forceinline__ int div_small(int a, int b, float inv_b, int* rem) {
+  int q = static_cast<int>((static_cast<float>(a) + 0.5f) * inv_b);
+  int r = a - q * b;
+  if (r < 0) { --q; r += b; }
+  if (r >= b) { ++q; r -= b; }
+  *rem = r;
+  return q;
+}
+
 // --------------------------------------------------------------------------
 // Constant per-context parameters, passed to every kernel by value.
 struct Params {

@@ -25,6 +25,7 @@
 // k_adj_scatter: per particle in the forward order; the rotation gradient tau
 //   becomes dL/dq = (2/|q|) (-v.tau, w tau + tau x v) for q/|q| = (w, v).
 #include <cfloat>
+#include <cstddef>
 
 #include "contact_dev.cuh"
 #include "force_law.cuh"
@@ -491,51 +492,167 @@ __device__ __forceinline__ void adj_post_pass(const Params& P, const Shapes& S, 
   }
 }
 
+// The geometry of particle i (second = false) or j of a staged pair record:
+// centre, R^T rows and sizes as the forward's sweep reads them, the type from
+// the record's kinds; a polytope's planes and their inverse slopes along the
+// sweep axis au go to sm (planes at sm[0 .. nf), slopes after sm[kMaxFaces]).
+__device__ __forceinline__ void adj_load_rec(const PairRec& r, bool second, const Shapes& S, const Parts& D,
+                                             float4* sm, AdjGeom& g, int au) {
+  const int lane = threadIdx.x & 31;
+  const int kind = second ? (r.kinds >> 8) : (r.kinds & 0xff);
+  const int* ci = second ? r.bi : r.ai;
+  const float* cf = second ? r.bf : r.af;
+  const float* rt = second ? r.rtb : r.rta;
+  const float* sz = second ? r.szb : r.sza;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) g.rt[k] = rt[k];
+  g.nf = 0;
+  g.sp = sm;
+  if (kind == KIND_WALL) {   // phi = m . c + p0 at box-relative node c (p0 in the size slot)
+    g.type = 3;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      g.c[k] = 0.f;
+      g.size[k] = sz[0];
+    }
+    return;
+  }
+  g.type = kind == KIND_SPHERE ? 0 : (kind == KIND_POLY ? 2 : 1);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    g.c[k] = static_cast<float>(ci[k]) + cf[k];
+    g.size[k] = sz[k];
+  }
+  if (g.type == 2) {
+    const int pid = second ? r.j : r.i;
+    const int f0 = S.face_off[pid];
+    g.nf = S.face_off[pid + 1] - f0;
+    if (lane < g.nf) {
+      const float4 e = D.wplane[f0 + lane];
+      sm[lane] = e;
+      reinterpret_cast<float*>(sm + kMaxFaces)[lane] = clip_inv(sel3(e.x, e.y, e.z, au));
+    }
+    __syncwarp();
+  }
+}
+
+// The warp copies a 224-byte pair record with 14 lanes x 16 bytes.
+__device__ __forceinline__ int4 adj_rec_part(const PairRec* src, int lane) {
+  return lane < kPairRecWords / 4 ? reinterpret_cast<const int4*>(src)[lane] : make_int4(0, 0, 0, 0);
+}
+// The pair index of a record held as adj_rec_part pieces (every lane gets it).
+constexpr int kPairWord = static_cast<int>(offsetof(PairRec, pair) / 4);
+__device__ __forceinline__ int adj_rec_pair(const int4& v) {
+  constexpr int c = kPairWord & 3;
+  const int w = c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+  return __shfl_sync(kFull, w, kPairWord >> 2);
+}
+// The seeds of pair p: lanes 0..6 hold s0, s1 and sg, lane 7 a flag for a
+// non-zero depth seed.
+__device__ __forceinline__ float adj_seed(const AdjBufs& B, int p, int lane) {
+  if (lane < 7) return B.seeds[static_cast<size_t>(p) * kSeedFloats + lane];
+  if (lane == 7) return B.pgrad[static_cast<size_t>(p) * kPairGrad + 12] != 0.0 ? 1.f : 0.f;
+  return 0.f;
+}
+
+// Sum of acc[0 .. 12) over the warp by halving exchanges (14 shuffles): lane
+// c < 12 returns the sum of component c.
+__device__ __forceinline__ float adj_warp_sum12(const float acc[12]) {
+  const int lane = threadIdx.x & 31;
+  const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1, b1 = (lane >> 1) & 1;
+  float h6[6];   // components 6 b4 + (0 .. 6)
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float send = b4 ? acc[k] : acc[6 + k];
+    h6[k] = (b4 ? acc[6 + k] : acc[k]) + __shfl_xor_sync(kFull, send, 16);
+  }
+  float h4[4];   // components 6 b4 + 3 b3 + (0 .. 3), the fourth a zero pad
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float send = b3 ? h6[k] : h6[3 + k];
+    h4[k] = (b3 ? h6[3 + k] : h6[k]) + __shfl_xor_sync(kFull, send, 8);
+  }
+  h4[3] = 0.f;
+  float h2[2];   // ... + 2 b2 + (0 .. 2)
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = b2 ? h4[k] : h4[2 + k];
+    h2[k] = (b2 ? h4[2 + k] : h4[k]) + __shfl_xor_sync(kFull, send, 4);
+  }
+  float h1 = (b1 ? h2[1] : h2[0]) + __shfl_xor_sync(kFull, b1 ? h2[0] : h2[1], 2);   // ... + b1
+  h1 += __shfl_xor_sync(kFull, h1, 1);
+  // lane c < 12 reads the lane holding component c = 6 b4 + 3 b3 + 2 b2 + b1
+  const int c = lane < 12 ? lane : 0;
+  const int c4 = c >= 6, r4 = c - 6 * c4, c3 = r4 >= 3, r3 = r4 - 3 * c3;
+  return __shfl_sync(kFull, h1, (c4 << 4) | (c3 << 3) | ((r3 >> 1) << 2) | ((r3 & 1) << 1));
+}
+
 template <int SET>
 __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, Parts D, Lists W, AdjBufs B) {
   __shared__ float4 s_pl[kWarps][2][kMaxFaces + kMaxFaces / 4];   // planes, then their inverse slopes
   __shared__ AdjStage s_st[kWarps][kAdjStage];
+  __shared__ __align__(16) PairRec s_rec[kWarps][2];
+  __shared__ unsigned s_pk[SET == 0 ? kWarps : 1][kTileItemsPerLane * 32];   // clipped ranges (rolled sweep)
+  constexpr bool ROLL = SET == 0;   // every kind: rolled slot loops (code size)
   int nst = 0;   // pairs staged in s_st[wid]
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int ntiles = min(W.counters[1], P.max_tiles);
   const float inv_w = P.inv_w, hw = 0.5f * P.wdx_l, T = hw + kClipMargin;
-  // tiles w, w + W, ... of the forward's list (W warps)
+  unsigned* spk = s_pk[ROLL ? wid : 0];
+  // tiles w, w + W, ... of the forward's list (W warps): each record is staged
+  // in shared memory, the next record and its pair's seeds are fetched while
+  // a tile runs
   const int nwarps = gridDim.x * kWarps;
-  for (int qpos = blockIdx.x * kWarps + wid; qpos < ntiles; qpos += nwarps) {
-    // the pair record's fields in registers (no runtime-indexed local copy)
-    const PairRec& prg = W.tiles[qpos];
-    if (!record_in_bounds(P, W.err, prg, true)) continue;   // warp-uniform (checked build only)
-    const int p = prg.pair;
-    const int t = prg.tile0 + prg.tile;   // the tile's index (its partial slot)
-    const int rec_i = prg.i, rec_j = prg.j, axis = prg.axis, nseg = prg.nseg, seglen = prg.seglen;
-    const int nitems = prg.nitems, tile0 = prg.tile0;
-    const float wall_p0 = prg.szb[0];   // used when j is a wall
-    const int dm0 = prg.dim[0], dm1 = prg.dim[1], dm2 = prg.dim[2];
-    int ai[3], bi[3];
-    float af[3], bf[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      ai[k] = prg.ai[k]; bi[k] = prg.bi[k];
-      af[k] = prg.af[k]; bf[k] = prg.bf[k];
+  int qpos = blockIdx.x * kWarps + wid;
+  float seed = 0.f;
+  if (qpos < ntiles) {
+    const int4 v = adj_rec_part(W.tiles + qpos, lane);
+    if (lane < kPairRecWords / 4) reinterpret_cast<int4*>(&s_rec[wid][0])[lane] = v;
+    seed = adj_seed(B, checked_index(W.err, adj_rec_pair(v), P.max_pairs, 0), lane);
+  }
+  __syncwarp();
+  int buf = 0;
+  while (qpos < ntiles) {
+    const int qn = qpos + nwarps;
+    int4 next = make_int4(0, 0, 0, 0);
+    float seed_n = 0.f;
+    if (qn < ntiles) {
+      next = adj_rec_part(W.tiles + qn, lane);
+      seed_n = adj_seed(B, checked_index(W.err, adj_rec_pair(next), P.max_pairs, 0), lane);
     }
-    const float* sd = B.seeds + static_cast<size_t>(p) * kSeedFloats;
-    const float s0 = sd[0], s1[3] = {sd[1], sd[2], sd[3]}, sg[3] = {sd[4], sd[5], sd[6]};
+    const PairRec& r = s_rec[wid][buf];
+    const bool valid = record_in_bounds(P, W.err, r, true);
+    const bool active = valid && __any_sync(kFull, lane < 8 && seed != 0.f);
+    const int p = r.pair;
+    const int t = r.tile0 + r.tile;   // the tile's index (its partial slot)
     float acc[12];
+#pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = 0.f;
-    const bool active = (s0 != 0.f) || (s1[0] != 0.f) || (s1[1] != 0.f) || (s1[2] != 0.f) || (sg[0] != 0.f) ||
-                        (sg[1] != 0.f) || (sg[2] != 0.f) || (B.pgrad[static_cast<size_t>(p) * kPairGrad + 12] != 0.0);
     if (active) {
+      const float s0 = __shfl_sync(kFull, seed, 0);
+      const float s1[3] = {__shfl_sync(kFull, seed, 1), __shfl_sync(kFull, seed, 2), __shfl_sync(kFull, seed, 3)};
+      const float sg[3] = {__shfl_sync(kFull, seed, 4), __shfl_sync(kFull, seed, 5), __shfl_sync(kFull, seed, 6)};
+      int ai[3], bi[3];
+      float af[3], bf[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        ai[k] = r.ai[k]; bi[k] = r.bi[k];
+        af[k] = r.af[k]; bf[k] = r.bf[k];
+      }
+      const int ax0 = r.axis, ax1 = ax0 == 2 ? 0 : ax0 + 1, ax2 = ax1 == 2 ? 0 : ax1 + 1;
       AdjGeom A, Bg;
-      adj_load(S, D, rec_i, ai, af, s_pl[wid][0], A, P.n, 0.f, axis);
-      adj_load(S, D, rec_j, bi, bf, s_pl[wid][1], Bg, P.n, wall_p0, axis);
-      const int ax0 = axis, ax1 = ax0 == 2 ? 0 : ax0 + 1, ax2 = ax1 == 2 ? 0 : ax1 + 1;
+      adj_load_rec(r, false, S, D, s_pl[wid][0], A, ax0);
+      adj_load_rec(r, true, S, D, s_pl[wid][1], Bg, ax0);
+      const int dm0 = r.dim[0], dm1 = r.dim[1], dm2 = r.dim[2];
       const int du = ax0 == 0 ? dm0 : (ax0 == 1 ? dm1 : dm2);
       const int dv = ax0 == 0 ? dm1 : (ax0 == 1 ? dm2 : dm0);   // side along (ax0 + 1) mod 3
-      // (A) each lane clips its line; (B) the warp's clipped nodes, numbered
-      // across the lanes by a scan of the counts, one per lane (its line by a
-      // binary search over the scan): the same node set as a walk of every
-      // line, with the work spread over the warp
+      const float inv_dv = __fdividef(1.f, static_cast<float>(dv));
+      const int nitems = r.nitems;
+      // (A) lane l clips its lines it0 + 32 s + l; (B) the tile's clipped
+      // nodes, numbered lane by lane by a scan of the counts, one per lane
+      // (owner lane by a binary search over the scan, slot by the owner's
+      // counts): the same node set as a walk of every line
       auto node = [&](int cu, int l1, int l2) {
         // node coordinates in box axes x, y, z (selects: no runtime-indexed array)
         int c[3];
@@ -593,54 +710,75 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
           for (int k = 0; k < 3; ++k) acc[9 + k] -= wb * cr[k];
         }
       };
-      const int it0 = (t - tile0) * 32 * kTileItemsPerLane;
+      const int it0 = r.tile * 32 * kTileItemsPerLane;
+      const int ns = min(kTileItemsPerLane, (nitems - it0 + 31) >> 5);
+      unsigned pk[kTileItemsPerLane];
+      int nl = 0;
+#pragma unroll(ROLL ? 1 : kTileItemsPerLane)
       for (int s = 0; s < kTileItemsPerLane; ++s) {
-        const int itb = it0 + s * 32;
-        if (itb >= nitems) break;
-        const int it = itb + lane;
-        const int line = it / nseg, seg = it - line * nseg;
-        const int l1 = line % dv, l2 = line / dv;   // coordinates along axes ax1, ax2
-        const int u0 = seg * seglen, u1 = it < nitems ? min(u0 + seglen, du) : u0;
-        float clo = static_cast<float>(u0), chi = static_cast<float>(u1 - 1);
-        adj_clip<SET>(A, ax0, ax1, ax2, l1, l2, ai, af, T, clo, chi);
-        adj_clip<SET>(Bg, ax0, ax1, ax2, l1, l2, bi, bf, T, clo, chi);
-        int ub;
-        const int nk = clip_nodes(clo, chi, u0, u1 - u0, &ub);
-        int incl = nk;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const int v = __shfl_up_sync(kFull, incl, d);
-          if (lane >= d) incl += v;
-        }
-        const int total = __shfl_sync(kFull, incl, 31);
-        const int excl = incl - nk;
-        for (int base = 0; base < total; base += 32) {
-          const int g = base + lane;
-          int o = 0;   // owner: the last lane whose first node is <= g
-#pragma unroll
-          for (int step = 16; step > 0; step >>= 1) {
-            const int e = __shfl_sync(kFull, excl, o + step);
-            if (e <= g) o += step;
-          }
-          const int ol1 = __shfl_sync(kFull, l1, o), ol2 = __shfl_sync(kFull, l2, o);
-          const int ocu = __shfl_sync(kFull, ub, o) + (g - __shfl_sync(kFull, excl, o));
-          if (g < total) node(ocu, ol1, ol2);
+        if (!ROLL) pk[s] = 0u;
+        if (s < ns) {
+          const int it = it0 + s * 32 + lane;
+          int l1;
+          const int l2 = div_small(it, dv, inv_dv, &l1);   // coordinates along axes ax1, ax2
+          const int u1 = it < nitems ? du : 0;
+          float clo = 0.f, chi = static_cast<float>(u1 - 1);
+          adj_clip<SET>(A, ax0, ax1, ax2, l1, l2, ai, af, T, clo, chi);
+          adj_clip<SET>(Bg, ax0, ax1, ax2, l1, l2, bi, bf, T, clo, chi);
+          int ub;
+          const int nk = clip_nodes(clo, chi, 0, u1, &ub);
+          const unsigned v = static_cast<unsigned>(ub) | (static_cast<unsigned>(nk) << 16);
+          if constexpr (ROLL) spk[s * 32 + lane] = v;
+          else pk[s] = v;
+          nl += nk;
         }
       }
+      if (ROLL) __syncwarp();
+      int incl = nl;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += v;
+      }
+      const int total = __shfl_sync(kFull, incl, 31);
+      const int excl = incl - nl;
+      for (int base = 0; base < total; base += 32) {
+        const int g = base + lane;
+        int o = 0;   // owner: the last lane whose first node is <= g
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int e = __shfl_sync(kFull, excl, o + step);
+          if (e <= g) o += step;
+        }
+        int k = g - __shfl_sync(kFull, excl, o);   // the node's rank among the owner's
+        int os = 0, cu = 0;
+#pragma unroll(ROLL ? 1 : kTileItemsPerLane)
+        for (int s = 0; s < kTileItemsPerLane; ++s) {
+          if (s < ns) {
+            unsigned q;
+            if constexpr (ROLL) q = spk[s * 32 + o];
+            else q = __shfl_sync(kFull, pk[s], o);
+            const int n = static_cast<int>(q >> 16);
+            if (k >= 0 && k < n) {
+              os = s;
+              cu = static_cast<int>(q & 0xffffu) + k;
+            }
+            k -= n;
+          }
+        }
+        int ol1;
+        const int ol2 = div_small(it0 + os * 32 + o, dv, inv_dv, &ol1);
+        if (g < total) node(cu, ol1, ol2);
+      }
+      if (ROLL) __syncwarp();   // spk is rewritten by the next tile
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-      for (int k = 0; k < 12; ++k) acc[k] += __shfl_xor_sync(kFull, acc[k], off);
+    const float x = adj_warp_sum12(acc);   // lane c < 12: component c
     if (active) {
       // end of the pair: one tile -> its sums directly; several -> the warp
       // completing the last tile sums all partials in FP64 (fixed order)
       bool complete = true;
       double sum = 0.0;   // lane c < 12: component c
-      float x = acc[0];
-#pragma unroll
-      for (int k = 1; k < 12; ++k) x = (lane == k) ? acc[k] : x;
-      const int ntp = prg.ntiles;
+      const int ntp = r.ntiles, tile0 = r.tile0;
       if (ntp == 1) {
         sum = widen(x);
       } else {
@@ -678,6 +816,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
       }
     }
     __syncwarp();
+    if (qn < ntiles && lane < kPairRecWords / 4) reinterpret_cast<int4*>(&s_rec[wid][buf ^ 1])[lane] = next;
+    __syncwarp();
+    buf ^= 1;
+    qpos = qn;
+    seed = seed_n;
   }
   if (nst > 0) {
     __syncwarp();

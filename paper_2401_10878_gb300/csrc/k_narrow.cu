@@ -67,16 +67,6 @@ __device__ __forceinline__ float world_comp(int c, const Local& L, float au, flo
   return c == L.u ? au : (c == L.v ? av : aw);
 }
 
-// floor(a / b) and the remainder for small non-negative ints via an FP32
-// reciprocal, corrected by one step (exact for a < 2^22)
-__device__ __forceinline__ int div_small(int a, int b, float inv_b, int* rem) {
-  int q = static_cast<int>((static_cast<float>(a) + 0.5f) * inv_b);
-  int r = a - q * b;
-  if (r < 0) { --q; r += b; }
-  if (r >= b) { ++q; r -= b; }
-  *rem = r;
-  return q;
-}
 
 // ---------------------------------------------------------------- evaluators
 // Each evaluator holds one particle's geometry for the current tile, in
