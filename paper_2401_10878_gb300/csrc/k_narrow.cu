@@ -186,7 +186,10 @@ struct CuboidEval {
 
 // Cube (equal half extents h): phi = max_k |y_k| - h.  Only what the node
 // loop needs stays in registers; the cross-axis terms are re-read from the
-// shared-memory pair record at each line start.
+// shared-memory pair record at each line start.  The line clip reads per-tile
+// constants from shared memory (prep_clip): along the line, slab k of
+// |y_k| < h + T is the node-counter interval centred at
+// c_k = fu - (tv_k rv + tw_k rw) / tu_k with half-width (h + T) / |tu_k|.
 struct CubeEval {
   int iu;
   float fu, tu0, tu1, tu2, h, itu0, itu1, itu2;
@@ -223,6 +226,60 @@ struct CubeEval {
     clip_slab(tu2, itu2, p2, ht, l, hh);
     lo = l + o;
     hi = hh + o;
+  }
+  // per-tile constants in cs[0 .. 6): (sv_k, hd_0), (sw_k, hd_1),
+  // (hd_2, fu, fv, fw), (iv, iw, iu, flat), (tv_k, 0), (tw_k, 0) with
+  // sv_k = tv_k / tu_k, sw_k = tw_k / tu_k, hd_k = (h + T) / |tu_k|; flat:
+  // a slab parallel to the line (|tu_k| <= kClipFlat), which takes the
+  // general clip
+  __device__ __forceinline__ void prep_clip(const PairRec& r, bool second, const Local& L, float T, float4* cs) {
+    const int* ci = second ? r.bi : r.ai;
+    const float* cf = second ? r.bf : r.af;
+    const float* rt = second ? r.rtb : r.rta;
+    const float ht = h + T;
+    const float4 a = make_float4(rt[L.v] * itu0, rt[3 + L.v] * itu1, rt[6 + L.v] * itu2, ht * fabsf(itu0));
+    const float4 b = make_float4(rt[L.w] * itu0, rt[3 + L.w] * itu1, rt[6 + L.w] * itu2, ht * fabsf(itu1));
+    const float4 c = make_float4(ht * fabsf(itu2), fu, cf[L.v], cf[L.w]);
+    const bool flat = !(fabsf(tu0) > kClipFlat && fabsf(tu1) > kClipFlat && fabsf(tu2) > kClipFlat);
+    const float4 d = make_float4(__int_as_float(ci[L.v]), __int_as_float(ci[L.w]), __int_as_float(iu),
+                                 __int_as_float(flat ? 1 : 0));
+    if ((threadIdx.x & 31) == 0) {
+      cs[0] = a;
+      cs[1] = b;
+      cs[2] = c;
+      cs[3] = d;
+      cs[4] = make_float4(rt[L.v], rt[3 + L.v], rt[6 + L.v], 0.f);
+      cs[5] = make_float4(rt[L.w], rt[3 + L.w], rt[6 + L.w], 0.f);
+    }
+    __syncwarp();
+  }
+  // begin_line_rec from the staged constants (the same operands, the same arithmetic)
+  __device__ __forceinline__ void begin_node(const float4* cs, int cv, int cw, int u0) {
+    const float4 c = cs[2], d = cs[3], tv = cs[4], tw = cs[5];
+    const float rv = static_cast<float>(cv - __float_as_int(d.x)) - c.z;
+    const float rw = static_cast<float>(cw - __float_as_int(d.y)) - c.w;
+    p0 = fmaf(-tu0, fu, fmaf(tv.x, rv, tw.x * rw));
+    p1 = fmaf(-tu1, fu, fmaf(tv.y, rv, tw.y * rw));
+    p2 = fmaf(-tu2, fu, fmaf(tv.z, rv, tw.z * rw));
+    cnt_u = static_cast<float>(u0 - iu) - 1.f;
+  }
+  // [lo, hi] cut to the nodes of line (cv, cw) inside all three slabs
+  __device__ __forceinline__ void clip_line(const PairRec& r, bool second, const Local& L, const float4* cs, int cv,
+                                            int cw, float T, float& lo, float& hi) {
+    const float4 a = cs[0], b = cs[1], c = cs[2], d = cs[3];
+    if (__float_as_int(d.w) != 0) {
+      begin_line_rec(r, second, L, cv, cw, 0);
+      clip(T, lo, hi);
+      return;
+    }
+    const float rv = static_cast<float>(cv - __float_as_int(d.x)) - c.z;
+    const float rw = static_cast<float>(cw - __float_as_int(d.y)) - c.w;
+    const float o = static_cast<float>(__float_as_int(d.z));
+    const float x0 = fmaf(-a.x, rv, fmaf(-b.x, rw, c.y));
+    const float x1 = fmaf(-a.y, rv, fmaf(-b.y, rw, c.y));
+    const float x2 = fmaf(-a.z, rv, fmaf(-b.z, rw, c.y));
+    lo = fmaxf(lo, fmaxf(fmaxf(x0 - a.w, x1 - b.w), x2 - c.x) + o);
+    hi = fminf(hi, fminf(fminf(x0 + a.w, x1 + b.w), x2 + c.x) + o);
   }
   __device__ __forceinline__ float phi() {
     cnt_u += 1.f;
@@ -372,6 +429,39 @@ __device__ __forceinline__ void begin_line_of(E& e, const PairRec&, bool, const 
   e.begin_line(cv, cw, u0);
 }
 
+// Line clip of an evaluator: its own clip_line (per-tile constants staged by
+// prep_clip) where it has one, else the line start and the general clip.
+template <class E>
+__device__ __forceinline__ auto prep_clip_of(E& e, const PairRec& r, bool second, const Local& L, float T, float4* cs,
+                                             int) -> decltype(e.prep_clip(r, second, L, T, cs)) {
+  e.prep_clip(r, second, L, T, cs);
+}
+template <class E>
+__device__ __forceinline__ void prep_clip_of(E&, const PairRec&, bool, const Local&, float, float4*, long) {}
+template <class E>
+__device__ __forceinline__ auto clip_line_of(E& e, const PairRec& r, bool second, const Local& L, const float4* cs,
+                                             int cv, int cw, float T, float& lo, float& hi, int)
+    -> decltype(e.clip_line(r, second, L, cs, cv, cw, T, lo, hi)) {
+  e.clip_line(r, second, L, cs, cv, cw, T, lo, hi);
+}
+template <class E>
+__device__ __forceinline__ void clip_line_of(E& e, const PairRec& r, bool second, const Local& L, const float4*, int cv,
+                                             int cw, float T, float& lo, float& hi, long) {
+  begin_line_of(e, r, second, L, cv, cw, 0, 0);
+  e.clip(T, lo, hi);
+}
+
+template <class E>
+__device__ __forceinline__ auto node_line_of(E& e, const PairRec&, bool, const Local&, const float4* cs, int cv, int cw,
+                                             int u0, int) -> decltype(e.begin_node(cs, cv, cw, u0)) {
+  e.begin_node(cs, cv, cw, u0);
+}
+template <class E>
+__device__ __forceinline__ void node_line_of(E& e, const PairRec& r, bool second, const Local& L, const float4*,
+                                             int cv, int cw, int u0, long) {
+  begin_line_of(e, r, second, L, cv, cw, u0, 0);
+}
+
 // ---------------------------------------------------------------- tile sweep
 // Per-lane partials of a tile: node count and first moments (exact integers
 // in sharp mode), the band sum of the normal, and the deepest node.
@@ -412,6 +502,12 @@ __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, 
   const int du = r.dim[L.u], dv = r.dim[L.v];
   const float inv_dv = __fdividef(1.f, static_cast<float>(dv));
   const float inv_w = P.inv_w, hw = 0.5f * P.wdx_l, T = hw + kClipMargin;
+  // evaluators with a staged line clip keep its constants in their (otherwise
+  // unused) plane buffer
+  prep_clip_of(A, r, swap, L, T, smA, 0);
+  prep_clip_of(B, r, !swap, L, T, smB, 0);
+  const float4* csA = smA;
+  const float4* csB = smB;
   float cnt = 0.f, mu = 0.f, mv = 0.f, mw = 0.f, bestf = -FLT_MAX;
   int bestidx = 0x7fffffff;
   const int it0 = tl * 32 * kTileItemsPerLane;
@@ -428,11 +524,9 @@ __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, 
       int cv;
       const int cw = div_small(it, dv, inv_dv, &cv);
       const int len = it < r.nitems ? du : 0;
-      begin_line_of(A, r, swap, L, cv, cw, 0, 0);
-      begin_line_of(B, r, !swap, L, cv, cw, 0, 0);
       float clo = 0.f, chi = static_cast<float>(len - 1);
-      A.clip(T, clo, chi);
-      B.clip(T, clo, chi);
+      clip_line_of(A, r, swap, L, csA, cv, cw, T, clo, chi, 0);
+      clip_line_of(B, r, !swap, L, csB, cv, cw, T, clo, chi, 0);
       int ub;
       const int nk = clip_nodes(clo, chi, 0, len, &ub);
       const unsigned v = static_cast<unsigned>(ub) | (static_cast<unsigned>(nk) << 16);
@@ -477,8 +571,8 @@ __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, 
     }
     int ocv;
     const int ocw = div_small(it0 + os * 32 + o, dv, inv_dv, &ocv);
-    begin_line_of(A, r, swap, L, ocv, ocw, u, 0);
-    begin_line_of(B, r, !swap, L, ocv, ocw, u, 0);
+    node_line_of(A, r, swap, L, csA, ocv, ocw, u, 0);
+    node_line_of(B, r, !swap, L, csB, ocv, ocw, u, 0);
     const float fa = A.phi();
     const float fb = B.phi();
     // W > 0, or a band term of the normal: max < w/2 and (sharp) min <= 0
