@@ -492,7 +492,8 @@ __device__ __forceinline__ float key_float(int k) { return __int_as_float(k >= 0
 // kernel's code small; otherwise they are unrolled over registers.
 template <bool SMOOTH, bool ROLL, class EA, class EB>
 __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, const Parts& D, const PairRec& r,
-                                              bool swap, int tl, float4* smA, float4* smB, unsigned* spk) {
+                                              bool swap, int tl, float4* smA, float4* smB, unsigned* spk,
+                                              int4* own) {
   const int lane = threadIdx.x & 31;
   const Local L = make_local(r);
   EA A;
@@ -544,23 +545,45 @@ __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, 
   }
   const int total = __shfl_sync(kFull, incl, 31);
   const int excl = incl - nl;
-  // (B) node g of the tile's clipped nodes on lane g mod 32
+  // the lanes with nodes, in lane order (their first nodes strictly
+  // increase): entry k of own holds the k-th one's lane, first node and
+  // clipped ranges
+  const bool has = nl > 0;
+  if (total > 0) {
+    const int rank = __popc(__ballot_sync(kFull, has) & ((1u << lane) - 1u));
+    if (has) {
+      if constexpr (ROLL) {
+        own[rank] = make_int4(lane, excl, 0, 0);
+      } else {
+        static_assert(kTileItemsPerLane == 4, "own holds four clipped ranges per lane");
+        own[rank] = make_int4(lane, excl, static_cast<int>(pk[0]), static_cast<int>(pk[1]));
+        own[32 + rank] = make_int4(static_cast<int>(pk[2]), static_cast<int>(pk[3]), 0, 0);
+      }
+    }
+    __syncwarp();
+  }
+  // (B) node g of the tile's clipped nodes on lane g mod 32; its owner is the
+  // last lane with nodes whose first node is <= g, i.e. entry (number of such
+  // lanes) - 1 of own, counted from the lanes that start before the pass and
+  // a mask of the first nodes inside it
   for (int base = 0; base < total; base += 32) {
     const int g = base + lane;
-    int o = 0;   // owner: the last lane whose first node is <= g
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      const int e = __shfl_sync(kFull, excl, o + step);
-      if (e <= g) o += step;
-    }
-    int k = g - __shfl_sync(kFull, excl, o);   // the node's rank among the owner's
+    const unsigned before = __ballot_sync(kFull, has && excl < base);
+    const unsigned inside =
+        __reduce_or_sync(kFull, (has && excl >= base && excl - base < 32) ? 1u << (excl - base) : 0u);
+    const int cnt_le = __popc(before) + __popc(inside & (lane == 31 ? 0xffffffffu : (2u << lane) - 1u));
+    const int4 e = own[min(max(cnt_le - 1, 0), 31)];
+    const int o = e.x;
+    int k = g - e.y;   // the node's rank among the owner's
+    int4 e2 = make_int4(0, 0, 0, 0);
+    if (!ROLL) e2 = own[32 + min(max(cnt_le - 1, 0), 31)];
     int os = 0, u = 0;
 #pragma unroll(ROLL ? 1 : kTileItemsPerLane)
     for (int s = 0; s < kTileItemsPerLane; ++s) {
       if (s < ns) {
         unsigned q;
         if constexpr (ROLL) q = spk[s * 32 + o];
-        else q = __shfl_sync(kFull, pk[s], o);
+        else q = static_cast<unsigned>(s == 0 ? e.z : (s == 1 ? e.w : (s == 2 ? e2.x : e2.y)));
         const int n = static_cast<int>(q >> 16);
         if (k >= 0 && k < n) {
           os = s;
@@ -783,7 +806,7 @@ enum KindSet : int { SET_ALL = 0, SET_SC = 1, SET_CUBE = 2 };
 
 template <bool SMOOTH, int SET>
 __device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, const Parts& D, const PairRec& r,
-                                            int tl, float4* smA, float4* smB, unsigned* spk) {
+                                            int tl, float4* smA, float4* smB, unsigned* spk, int4* own) {
   // kind order for canonical pairs: wall < sphere < cube < cuboid < polytope (kind 2 unused)
   constexpr int rank[6] = {1, 3, 6, 5, 2, 0};
   int ka = r.kinds & 0xff, kb = r.kinds >> 8;
@@ -798,10 +821,10 @@ __device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, co
   Partial o{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -FLT_MAX, 0x7fffffff, false};
 #define GBC_CASE(KA, KB, TA, TB)                                                  \
   case (KA) * 8 + (KB):                                                          \
-    o = sweep_tile<SMOOTH, SET == SET_ALL, TA, TB>(P, S, D, r, swap, tl, smA, smB, spk); \
+    o = sweep_tile<SMOOTH, SET == SET_ALL, TA, TB>(P, S, D, r, swap, tl, smA, smB, spk, own); \
     break;
   if constexpr (SET == SET_CUBE) {
-    o = sweep_tile<SMOOTH, false, CubeEval, CubeEval>(P, S, D, r, swap, tl, smA, smB, spk);
+    o = sweep_tile<SMOOTH, false, CubeEval, CubeEval>(P, S, D, r, swap, tl, smA, smB, spk, own);
   } else if constexpr (SET == SET_SC) {
     switch (ka * 8 + kb) {
       GBC_CASE(0, 0, SphereEval, SphereEval)
@@ -856,6 +879,7 @@ __global__ void __launch_bounds__(kWarps * 32, SET == 0 ? 2 : 3) k_narrow32(Para
   __shared__ __align__(16) PairRec s_rec[kWarps][2];
   __shared__ float4 s_planes[kWarps][2][kMaxFaces + kMaxFaces / 4];   // planes, then their inverse slopes
   __shared__ unsigned s_pk[SET == SET_ALL ? kWarps : 1][kTileItemsPerLane * 32];   // clipped ranges (rolled sweep)
+  __shared__ int4 s_own[kWarps][64];   // the lanes with clipped nodes (sweep_tile)
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int ntiles = W.counters[1];
@@ -874,7 +898,7 @@ __global__ void __launch_bounds__(kWarps * 32, SET == 0 ? 2 : 3) k_narrow32(Para
     const PairRec& r = s_rec[wid][buf];
     if (record_in_bounds(P, W.err, r, true)) {
       const Partial o = dispatch<SMOOTH, SET>(P, S, D, r, r.tile, s_planes[wid][0], s_planes[wid][1],
-                                              s_pk[SET == SET_ALL ? wid : 0]);
+                                              s_pk[SET == SET_ALL ? wid : 0], s_own[wid]);
       tile_done(P, W, r, pair_out, o.touched ? reduce_tile<SMOOTH>(o) : empty_partial());
     }
     __syncwarp();
