@@ -358,12 +358,23 @@ __device__ __forceinline__ void adj_clip(const AdjGeom& g, int au, int av, int a
                          fmaf(sel3(g.rt[0], g.rt[1], g.rt[2], aw), rw, fmaf(-mu, fu, g.size[0])));
     clip_half(mu, clip_inv(mu), p, T, l, h);
   } else if (SET != 0 || g.type == 1) {
+    // constants staged by adj_prep_clip: slab k is the node-counter interval
+    // centred at fu - sv_k rv - sw_k rw with half-width hd_k
+    const float4 a = g.sp[0], b = g.sp[1], c = g.sp[2];
+    if (__float_as_int(c.y) == 0) {
+      const float x0 = fmaf(-a.x, rv, fmaf(-b.x, rw, fu));
+      const float x1 = fmaf(-a.y, rv, fmaf(-b.y, rw, fu));
+      const float x2 = fmaf(-a.z, rv, fmaf(-b.z, rw, fu));
+      l = fmaxf(l, fmaxf(fmaxf(x0 - a.w, x1 - b.w), x2 - c.x));
+      h = fminf(h, fminf(fminf(x0 + a.w, x1 + b.w), x2 + c.x));
+    } else {   // a slab parallel to the line
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float* t = g.rt + 3 * k;
-      const float tu = sel3(t[0], t[1], t[2], au);
-      const float p = fmaf(sel3(t[0], t[1], t[2], av), rv, fmaf(sel3(t[0], t[1], t[2], aw), rw, -tu * fu));
-      clip_slab(tu, clip_inv(tu), p, g.size[k] + T, l, h);
+      for (int k = 0; k < 3; ++k) {
+        const float* t = g.rt + 3 * k;
+        const float tu = sel3(t[0], t[1], t[2], au);
+        const float p = fmaf(sel3(t[0], t[1], t[2], av), rv, fmaf(sel3(t[0], t[1], t[2], aw), rw, -tu * fu));
+        clip_slab(tu, clip_inv(tu), p, g.size[k] + T, l, h);
+      }
     }
   } else {
     const float* inv = reinterpret_cast<const float*>(g.sp + kMaxFaces);
@@ -376,6 +387,38 @@ __device__ __forceinline__ void adj_clip(const AdjGeom& g, int au, int av, int a
   }
   lo = l + o;
   hi = h + o;
+}
+
+// Per-tile constants of a cuboid's line clip along au (sweep axis) in
+// g.sp[0 .. 3): (sv_k, hd_0), (sw_k, hd_1), (hd_2, flat) with sv_k = tv_k / tu_k,
+// sw_k = tw_k / tu_k, hd_k = (size_k + T) / |tu_k| (tu, tv, tw: body axis k's
+// components along au, av, aw); flat: a slab parallel to the lines.
+__device__ __forceinline__ void adj_prep_clip(AdjGeom& g, int au, int av, int aw, float T) {
+  float4 a, b, c;
+  float* pa = &a.x;
+  float* pb = &b.x;
+  bool flat = false;
+  float hd[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float* t = g.rt + 3 * k;
+    const float tu = sel3(t[0], t[1], t[2], au);
+    flat = flat || !(fabsf(tu) > kClipFlat);
+    const float it = clip_inv(tu);
+    pa[k] = sel3(t[0], t[1], t[2], av) * it;
+    pb[k] = sel3(t[0], t[1], t[2], aw) * it;
+    hd[k] = (g.size[k] + T) * fabsf(it);
+  }
+  a.w = hd[0];
+  b.w = hd[1];
+  c = make_float4(hd[2], __int_as_float(flat ? 1 : 0), 0.f, 0.f);
+  float4* sm = const_cast<float4*>(g.sp);
+  if ((threadIdx.x & 31) == 0) {
+    sm[0] = a;
+    sm[1] = b;
+    sm[2] = c;
+  }
+  __syncwarp();
 }
 
 __device__ __forceinline__ void cross3f(const float a[3], const float b[3], float c[3]) {
@@ -593,6 +636,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
   __shared__ AdjStage s_st[kWarps][kAdjStage];
   __shared__ __align__(16) PairRec s_rec[kWarps][2];
   __shared__ unsigned s_pk[SET == 0 ? kWarps : 1][kTileItemsPerLane * 32];   // clipped ranges (rolled sweep)
+  __shared__ int4 s_own[kWarps][64];   // the lanes with clipped nodes of the current tile
   constexpr bool ROLL = SET == 0;   // every kind: rolled slot loops (code size)
   int nst = 0;   // pairs staged in s_st[wid]
   pdl_begin();
@@ -644,6 +688,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
       AdjGeom A, Bg;
       adj_load_rec(r, false, S, D, s_pl[wid][0], A, ax0);
       adj_load_rec(r, true, S, D, s_pl[wid][1], Bg, ax0);
+      const float Tc = hw + kClipMargin;
+      if (SET == 2 || A.type == 1) adj_prep_clip(A, ax0, ax1, ax2, Tc);
+      if (SET == 2 || Bg.type == 1) adj_prep_clip(Bg, ax0, ax1, ax2, Tc);
       const int dm0 = r.dim[0], dm1 = r.dim[1], dm2 = r.dim[2];
       const int du = ax0 == 0 ? dm0 : (ax0 == 1 ? dm1 : dm2);
       const int dv = ax0 == 0 ? dm1 : (ax0 == 1 ? dm2 : dm0);   // side along (ax0 + 1) mod 3
@@ -742,22 +789,43 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
       }
       const int total = __shfl_sync(kFull, incl, 31);
       const int excl = incl - nl;
+      // the lanes with nodes in lane order: entry k of own holds the k-th
+      // one's lane, first node and clipped ranges
+      const bool has = nl > 0;
+      int4* own = s_own[wid];
+      if (total > 0) {
+        const int rank = __popc(__ballot_sync(kFull, has) & ((1u << lane) - 1u));
+        if (has) {
+          if constexpr (ROLL) {
+            own[rank] = make_int4(lane, excl, 0, 0);
+          } else {
+            static_assert(kTileItemsPerLane == 4, "own holds four clipped ranges per lane");
+            own[rank] = make_int4(lane, excl, static_cast<int>(pk[0]), static_cast<int>(pk[1]));
+            own[32 + rank] = make_int4(static_cast<int>(pk[2]), static_cast<int>(pk[3]), 0, 0);
+          }
+        }
+        __syncwarp();
+      }
       for (int base = 0; base < total; base += 32) {
         const int g = base + lane;
-        int o = 0;   // owner: the last lane whose first node is <= g
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const int e = __shfl_sync(kFull, excl, o + step);
-          if (e <= g) o += step;
-        }
-        int k = g - __shfl_sync(kFull, excl, o);   // the node's rank among the owner's
+        // owner: the last lane with nodes whose first node is <= g
+        const unsigned before = __ballot_sync(kFull, has && excl < base);
+        const unsigned inside =
+            __reduce_or_sync(kFull, (has && excl >= base && excl - base < 32) ? 1u << (excl - base) : 0u);
+        const int cnt_le = __popc(before) + __popc(inside & (lane == 31 ? 0xffffffffu : (2u << lane) - 1u));
+        const int ie = min(max(cnt_le - 1, 0), 31);
+        const int4 e = own[ie];
+        const int o = e.x;
+        int k = g - e.y;   // the node's rank among the owner's
+        int4 e2 = make_int4(0, 0, 0, 0);
+        if (!ROLL) e2 = own[32 + ie];
         int os = 0, cu = 0;
 #pragma unroll(ROLL ? 1 : kTileItemsPerLane)
         for (int s = 0; s < kTileItemsPerLane; ++s) {
           if (s < ns) {
             unsigned q;
             if constexpr (ROLL) q = spk[s * 32 + o];
-            else q = __shfl_sync(kFull, pk[s], o);
+            else q = static_cast<unsigned>(s == 0 ? e.z : (s == 1 ? e.w : (s == 2 ? e2.x : e2.y)));
             const int n = static_cast<int>(q >> 16);
             if (k >= 0 && k < n) {
               os = s;
