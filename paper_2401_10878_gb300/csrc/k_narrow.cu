@@ -320,15 +320,20 @@ __device__ __forceinline__ int stage_planes(const Shapes& S, const Parts& D, int
                       L.w == 0 ? w.x : (L.w == 1 ? w.y : w.z), w.w);
     }
     sm[lane] = e;
-    reinterpret_cast<float*>(sm + kMaxFaces)[lane] = clip_inv(e.x);
   }
   __syncwarp();
   return nf;
 }
 
-// Polytopes: planes (and their inverse slopes along u) read from shared memory.
+// Polytopes: planes read from shared memory (sp[0 .. nf)); phi keeps the index
+// of the first maximal face for the gradient.  The line clip reads per-tile
+// half-line bounds (prep_clip) from sp[kMaxFaces ..): along the line, face f
+// of slope m = e.x bounds the node counter c - iu by
+// C_f - sy_f rv - sz_f rw (above for m > 0, below for m < 0) with
+// sy_f = e.y / m, sz_f = e.z / m, C_f = (T + e.w) / m + fu; a face parallel
+// to the line (|m| <= kClipFlat) keeps or empties the whole line.
 struct PolyEval {
-  int iu, iv, iw, nf;
+  int iu, iv, iw, nf, nup, ndn, kbest;
   float fu, fv, fw;
   const float4* sp;
   float cnt_u, ru, rv, rw;
@@ -348,13 +353,46 @@ struct PolyEval {
     rw = static_cast<float>(cw - iw) - fw;
     cnt_u = static_cast<float>(u0 - iu) - 1.f;
   }
-  __device__ __forceinline__ void clip(float T, float& lo, float& hi) const {
+  // the half-line bounds of the tile's faces in sp[kMaxFaces ..): faces
+  // bounding from above, then from below, then parallel ones (their planes)
+  __device__ __forceinline__ void prep_clip(const PairRec&, bool, const Local&, float T, float4* cs) {
+    const int lane = threadIdx.x & 31;
+    const bool act = lane < nf;
+    const float4 e = sp[act ? lane : 0];
+    const bool up = act && e.x > kClipFlat, dn = act && e.x < -kClipFlat, par = act && !up && !dn;
+    const unsigned bu = __ballot_sync(kFull, up), bd = __ballot_sync(kFull, dn), bp = __ballot_sync(kFull, par);
+    nup = __popc(bu);
+    ndn = __popc(bd);
+    const unsigned lt = (1u << lane) - 1u;
+    const int pos = up ? __popc(bu & lt) : (dn ? nup + __popc(bd & lt) : nup + ndn + __popc(bp & lt));
+    if (act) {
+      float4 c = e;
+      if (!par) {
+        const float im = __fdividef(1.f, e.x);
+        c = make_float4(e.y * im, e.z * im, fmaf(T + e.w, im, fu), 0.f);
+      }
+      cs[kMaxFaces + pos] = c;
+    }
+    __syncwarp();
+  }
+  __device__ __forceinline__ void clip_line(const PairRec&, bool, const Local&, const float4*, int cv, int cw,
+                                            float T, float& lo, float& hi) const {
+    const float lrv = static_cast<float>(cv - iv) - fv, lrw = static_cast<float>(cw - iw) - fw;
     const float o = static_cast<float>(iu);
-    const float* inv = reinterpret_cast<const float*>(sp + kMaxFaces);
+    const float4* cl = sp + kMaxFaces;
     float l = lo - o, h = hi - o;
-    for (int f = 0; f < nf; ++f) {
-      const float4 e = sp[f];
-      clip_half(e.x, inv[f], fmaf(-e.x, fu, fmaf(e.y, rv, fmaf(e.z, rw, -e.w))), T, l, h);
+    int f = 0;
+    for (; f < nup; ++f) {
+      const float4 c = cl[f];
+      h = fminf(h, fmaf(-c.x, lrv, fmaf(-c.y, lrw, c.z)));
+    }
+    for (; f < nup + ndn; ++f) {
+      const float4 c = cl[f];
+      l = fmaxf(l, fmaf(-c.x, lrv, fmaf(-c.y, lrw, c.z)));
+    }
+    for (; f < nf; ++f) {
+      const float4 e = cl[f];
+      if (!(fmaf(-e.x, fu, fmaf(e.y, lrv, fmaf(e.z, lrw, -e.w))) < T)) l = kClipEmpty;
     }
     lo = l + o;
     hi = h + o;
@@ -366,18 +404,17 @@ struct PolyEval {
   __device__ __forceinline__ float phi() {
     cnt_u += 1.f;
     ru = cnt_u - fu;
-    float best = value(0);
-    for (int f = 1; f < nf; ++f) best = fmaxf(best, value(f));
-    return best;
-  }
-  __device__ __forceinline__ void grad(float m) {
     int k = 0;
     float best = value(0);
     for (int f = 1; f < nf; ++f) {
       const float v = value(f);
       if (v > best) { best = v; k = f; }
     }
-    const float4 e = sp[k];
+    kbest = k;
+    return best;
+  }
+  __device__ __forceinline__ void grad(float m) {
+    const float4 e = sp[kbest];
     gu = fmaf(m, e.x, gu);
     gv = fmaf(m, e.y, gv);
     gw = fmaf(m, e.z, gw);
@@ -877,7 +914,8 @@ __global__ void __launch_bounds__(kWarps * 32, SET == 0 ? 2 : 3) k_narrow32(Para
                                                                                   Lists W, const double* vel,
                                                                                   double* pair_out) {
   __shared__ __align__(16) PairRec s_rec[kWarps][2];
-  __shared__ float4 s_planes[kWarps][2][kMaxFaces + kMaxFaces / 4];   // planes, then their inverse slopes
+  // per evaluator: a polytope's planes, then its line clip's constants (a cube: the clip constants)
+  __shared__ float4 s_planes[kWarps][2][SET == SET_CUBE ? 8 : 2 * kMaxFaces];
   __shared__ unsigned s_pk[SET == SET_ALL ? kWarps : 1][kTileItemsPerLane * 32];   // clipped ranges (rolled sweep)
   __shared__ int4 s_own[kWarps][64];   // the lanes with clipped nodes (sweep_tile)
   pdl_begin();
