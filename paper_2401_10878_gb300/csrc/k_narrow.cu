@@ -960,7 +960,7 @@ __global__ void __launch_bounds__(kWarps * 32, SET == 0 ? 2 : 3) k_narrow32(Para
 constexpr int kForceChunk = 16;
 
 template <int SET, bool LAW>
-__global__ void __launch_bounds__(kWarps * 32) k_force(Params P, Shapes S, Parts D, Lists W, const double* vel,
+__global__ void __launch_bounds__(kWarps * 32, 1) k_force(Params P, Shapes S, Parts D, Lists W, const double* vel,
                                                        double* pair_out) {
   __shared__ __align__(16) OvlRec s_ovl[kWarps][kForceChunk];
   pdl_begin();
