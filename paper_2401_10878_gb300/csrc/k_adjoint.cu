@@ -63,63 +63,77 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
 }
 
 // ---------------------------------------------------------------- pair level
+// The pair-level chain rule, four lanes per pair and eight pairs per warp pass:
+// component k = 0..2 of every 3-vector on lanes 0..2 of the pair (cross and dot
+// products by shuffles), lane 3 for the third reciprocal square root and the
+// scalar stores.  Every FP64 warp instruction holds a sub-partition's FP64 pipe
+// ~40 ns however many lanes are active, so splitting each pair's vectors over
+// lanes shortens the chain about threefold.  Per-pair conditions are taken by
+// selects (or branches without shuffles); a branch with shuffles is entered
+// by the whole warp when any of its pairs needs it.
 __global__ void __launch_bounds__(32) k_adj_pre(Params P, Shapes S, Parts D, Lists W, AdjBufs B,
                                                  const double* __restrict__ vel, const double* __restrict__ gF,
                                                  const double* __restrict__ gT) {
   pdl_begin();
+  const int lane = threadIdx.x & 31;
+  const int slot = lane >> 2, k = lane & 3, kc = k < 3 ? k : 0, b0 = lane & ~3;
+  const int k1 = kc == 2 ? 0 : kc + 1, k2 = kc == 0 ? 2 : kc - 1;
   const int np = min(W.counters[0], P.max_pairs);
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
-    const PairRec pr = W.pairs[p];
-    const double* tp = W.tape + static_cast<size_t>(p) * kTapeDoubles;
-    float* sd = B.seeds + static_cast<size_t>(p) * kSeedFloats;
-    double* pg = B.pgrad + static_cast<size_t>(p) * kPairGrad;
-    for (int k = 0; k < kSeedFloats; ++k) sd[k] = 0.f;
-    for (int k = 0; k < kPairGrad; ++k) pg[k] = 0.0;
-    B.done[p] = 0;
+  const int nw = gridDim.x * static_cast<int>(blockDim.x >> 5);
+  const int gw = static_cast<int>((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  // component c of the pair's vector held as v (component k on lane b0 + k)
+  auto at = [&](double v, int c) { return __shfl_sync(kFull, v, b0 + c); };
+  auto sum3 = [&](double v) { return (at(v, 0) + at(v, 1)) + at(v, 2); };
+  // component kc of a x b
+  auto cross = [&](double a, double b) { return at(a, k1) * at(b, k2) - at(a, k2) * at(b, k1); };
+  for (int q0 = 8 * gw; q0 < np; q0 += 8 * nw) {
+    const int p = q0 + slot;
+    const bool inr = p < np;
+    const int pc = inr ? p : q0;
+    const double* tp = W.tape + static_cast<size_t>(pc) * kTapeDoubles;
+    const PairRec& pr = W.pairs[pc];
     const double S0 = tp[0];
     const double fmag = tp[12];
-    if (!(S0 > 0.0) || !record_in_bounds(P, W.err, pr, false)) continue;
-    const int i = pr.i, j = pr.j;
+    const bool act = inr && S0 > 0.0 && record_in_bounds(P, W.err, pr, false);
+    const int i = act ? pr.i : 0, j = act ? pr.j : 0;
+    const bool wallj = j >= P.n;   // a wall has no output and no velocity
     const double dx = P.dx;
-    double XA[3], XB[3], xc[3], n[3], F[3], rA[3], rB[3], gFi[3], gFj[3], gTi[3], gTj[3];
-    for (int k = 0; k < 3; ++k) {
-      XA[k] = D.X[3 * i + k];
-      XB[k] = D.X[3 * j + k] - pr.shift[k] * P.L[k];
-      xc[k] = tp[1 + k];
-      n[k] = tp[4 + k];
-      F[k] = fmag * n[k];
-      rA[k] = xc[k] - XA[k];
-      rB[k] = xc[k] - XB[k];
-      gFi[k] = gF[3 * i + k]; gFj[k] = j < P.n ? gF[3 * j + k] : 0.0;   // a wall has no output
-      gTi[k] = gT[3 * i + k]; gTj[k] = j < P.n ? gT[3 * j + k] : 0.0;
-    }
-    const double d = tp[7], gnorm = tp[8], estar = tp[10], damp = tp[11];
+    const double Lk = kc == 0 ? P.L[0] : (kc == 1 ? P.L[1] : P.L[2]);
+    const double XA = D.X[3 * i + kc];
+    const double XB = D.X[3 * j + kc] - pr.shift[kc] * Lk;
+    const double xc = tp[1 + kc], nk = tp[4 + kc];
+    double Fk = fmag * nk;
+    const double rA = xc - XA, rB = xc - XB;
+    const double gFi = gF[3 * i + kc], gFj = wallj ? 0.0 : gF[3 * j + kc];
+    const double gTi = gT[3 * i + kc], gTj = wallj ? 0.0 : gT[3 * j + kc];
+    const double d = tp[7], gnorm = tp[8], damp = tp[11], fb = tp[9];
     // c of Eq. (damping_factor) as the forward used it (the shared one, or the
     // contact's own with contact history, held fixed like every per-contact constant)
     const double cdamp = tp[14];
     // relative velocity u_AB = (v_A + w_A x r_A) - (v_B + w_B x r_B) at x_c, ddot_n = u_AB . n
-    double uab[3] = {0.0, 0.0, 0.0}, ddot = 0.0;
+    double uab = 0.0, ddot = 0.0;
     const double* va = vel != nullptr ? vel + 6 * i : nullptr;
-    const double* vb = vel != nullptr ? (j < P.n ? vel + 6 * j : D.rest6) : nullptr;
-    if (vel != nullptr && fmag > 0.0 && (cdamp != 0.0 || P.friction)) {
-      double wa[3], wb[3];
-      cross3(va + 3, rA, wa);
-      cross3(vb + 3, rB, wb);
-      for (int k = 0; k < 3; ++k) uab[k] = (va[k] + wa[k]) - (vb[k] + wb[k]);
-      ddot = uab[0] * n[0] + uab[1] * n[1] + uab[2] * n[2];
+    const double* vb = vel != nullptr ? (wallj ? D.rest6 : vel + 6 * j) : nullptr;
+    if (vel != nullptr) {
+      const double wa = va[3 + k1] * at(rA, k2) - va[3 + k2] * at(rA, k1);
+      const double wb = vb[3 + k1] * at(rB, k2) - vb[3 + k2] * at(rB, k1);
+      const double u = (va[kc] + wa) - (vb[kc] + wb);
+      const double dd = sum3(u * nk);
+      const bool vlaw = fmag > 0.0 && (cdamp != 0.0 || P.friction);
+      uab = vlaw ? u : 0.0;
+      ddot = vlaw ? dd : 0.0;
     }
     // friction, Eq. (contact_force_tangential): F = fmag (n + f(a) t), t = u_t / |u_t|,
     // u_t = u_AB - ddot_n n, a = |u_t| / u_k
     bool fric = false;
-    double tdir[3] = {0.0, 0.0, 0.0}, coef = 0.0, dcoef = 0.0, utn = 0.0;
-    if (P.friction && vel != nullptr && fmag > 0.0) {
-      double ut[3];
-      for (int k = 0; k < 3; ++k) ut[k] = uab[k] - ddot * n[k];
-      const double utn2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
-      if (utn2 > 0.0) {
-        fric = true;
+    double tdir = 0.0, coef = 0.0, dcoef = 0.0, utn = 0.0;
+    if (P.friction && vel != nullptr) {
+      const double ut = uab - ddot * nk;
+      const double utn2 = sum3(ut * ut);
+      fric = fmag > 0.0 && utn2 > 0.0;
+      if (fric) {
         utn = sqrt(utn2);
-        for (int k = 0; k < 3; ++k) tdir[k] = ut[k] / utn;
+        tdir = ut / utn;
         const double a = utn * P.inv_u_k, a2 = a * a;
         const double A = 2.0 * P.mu_s_star - P.mu_k;
         coef = P.mu_k;
@@ -129,96 +143,96 @@ __global__ void __launch_bounds__(32) k_adj_pre(Params P, Shapes S, Parts D, Lis
           // f'(a) = 2a [A (1 - a^4) / (a^4 + 1)^2 + mu_k / (a^2 + 1)^2]
           dcoef = 2.0 * a * (A * (1.0 - a2 * a2) / (den1 * den1) + P.mu_k / (den2 * den2));
         }
-        for (int k = 0; k < 3; ++k) F[k] += fmag * coef * tdir[k];
+        Fk += fmag * coef * tdir;
       }
     }
     // dL/dF = Lambda, dL/dx_c, explicit dL/dX_A, dL/dX_B'
-    double c1[3], c2[3], Lam[3], gxc[3], gXA[3], gXB[3], t1[3], t2[3];
-    cross3(gTi, rA, c1);
-    cross3(gTj, rB, c2);
-    for (int k = 0; k < 3; ++k) Lam[k] = gFj[k] - gFi[k] - c1[k] + c2[k];
-    double dT[3] = {gTj[0] - gTi[0], gTj[1] - gTi[1], gTj[2] - gTi[2]};
-    cross3(F, dT, gxc);
-    cross3(F, gTi, t1);
-    cross3(gTj, F, t2);
-    for (int k = 0; k < 3; ++k) { gXA[k] = t1[k]; gXB[k] = t2[k]; }
-    const double Ln = Lam[0] * n[0] + Lam[1] * n[1] + Lam[2] * n[2];
-    const double Lt = Lam[0] * tdir[0] + Lam[1] * tdir[1] + Lam[2] * tdir[2];
+    const double c1 = cross(gTi, rA), c2 = cross(gTj, rB);
+    const double Lam = gFj - gFi - c1 + c2;
+    const double dT = gTj - gTi;
+    double gxc = cross(Fk, dT);
+    double gXA = cross(Fk, gTi);
+    double gXB = cross(gTj, Fk);
+    const double Ln = sum3(Lam * nk);
+    const double Lt = sum3(Lam * tdir);
     const double Lm = Ln + coef * Lt;   // dL/dfmag
-    double gn[3] = {fmag * Lam[0], fmag * Lam[1], fmag * Lam[2]};
-    double guab[3] = {0.0, 0.0, 0.0};   // dL/du_AB
-    if (fric) {
+    double gn = fmag * Lam;
+    double guab = 0.0;   // dL/du_AB
+    if (__any_sync(kFull, fric)) {
       // through t (projected on its normal plane) and through f(a)
-      double gut[3];
-      const double s_dir = fmag * coef / utn, s_mag = fmag * Lt * dcoef * P.inv_u_k;
-      for (int k = 0; k < 3; ++k) gut[k] = s_dir * (Lam[k] - Lt * tdir[k]) + s_mag * tdir[k];
-      const double gun = gut[0] * n[0] + gut[1] * n[1] + gut[2] * n[2];
-      for (int k = 0; k < 3; ++k) {
-        guab[k] += gut[k] - gun * n[k];
-        gn[k] -= uab[k] * gun + ddot * gut[k];
+      const double s_dir = fric ? fmag * coef / utn : 0.0, s_mag = fmag * Lt * dcoef * P.inv_u_k;
+      const double gut = s_dir * (Lam - Lt * tdir) + s_mag * tdir;
+      const double gun = sum3(gut * nk);
+      if (fric) {
+        guab += gut - gun * nk;
+        gn -= uab * gun + ddot * gut;
       }
     }
+    // reciprocal square roots by Newton-Raphson from an FP32 seed (no FP64
+    // division sequence): lane 0 of S0, lane 1 of d, lane 2 of |G|^2
+    const double rarg = k == 0 ? S0 : (k == 1 ? d : (k == 2 ? gnorm : 1.0));
+    const double rr = fl::nr_rsqrt(rarg > 0.0 ? rarg : 1.0);
+    const double yS = at(rr, 0), yd = at(rr, 1), yg = at(rr, 2);
+    const double inv_S0 = yS * yS;
     double gV = 0.0, gd = 0.0;
-    // reciprocals by Newton-Raphson from an FP32 seed (no FP64 division sequence)
-    const double inv_S0 = fl::nr_rsqrt(S0) * fl::nr_rsqrt(S0);
     if (fmag > 0.0) {
       const double half_lf = 0.5 * Lm * fmag;
       gV = half_lf * inv_S0 * (P.inv_dx * P.inv_dx * P.inv_dx);
-      const double yd = fl::nr_rsqrt(d);
       gd = half_lf * (yd * yd);
       if (vel != nullptr && cdamp != 0.0 && damp > 0.0) {
         const double gdd = Lm * fmag * cdamp / damp;   // dL/d(ddot_n)
-        for (int k = 0; k < 3; ++k) {
-          gn[k] += gdd * uab[k];
-          guab[k] += gdd * n[k];
-        }
+        gn += gdd * uab;
+        guab += gdd * nk;
       }
     }
-    if (vel != nullptr && (fric || cdamp != 0.0)) {
+    if (vel != nullptr) {
       // u_AB depends on x_c, X_A and X_B' through the angular velocities
-      double ga[3], gb[3];
-      cross3(guab, va + 3, ga);
-      cross3(guab, vb + 3, gb);
-      for (int k = 0; k < 3; ++k) {
-        gxc[k] += ga[k] - gb[k];
-        gXA[k] -= ga[k];
-        gXB[k] += gb[k];
+      const double ga = at(guab, k1) * va[3 + k2] - at(guab, k2) * va[3 + k1];
+      const double gb = at(guab, k1) * vb[3 + k2] - at(guab, k2) * vb[3 + k1];
+      if (fric || cdamp != 0.0) {
+        gxc += ga - gb;
+        gXA -= ga;
+        gXB += gb;
       }
     }
     // normal: n = G / |G| with G = kappa Sg, or the centre-line fallback
     const double kappa = P.gscale;
-    const double gnn = gn[0] * n[0] + gn[1] * n[1] + gn[2] * n[2];
-    double sg[3] = {0.0, 0.0, 0.0};
-    if (tp[9] == 0.0) {
-      const double yg = fl::nr_rsqrt(gnorm);
-      const double kinv = kappa * (yg * yg);
-      for (int k = 0; k < 3; ++k) sg[k] = kinv * (gn[k] - gnn * n[k]);
-    } else {
-      double dl = 0.0;
-      for (int k = 0; k < 3; ++k) dl += (XB[k] - XA[k]) * (XB[k] - XA[k]);
-      dl = sqrt(dl);
-      if (dl > 0.0)
-        for (int k = 0; k < 3; ++k) {
-          const double g = (gn[k] - gnn * n[k]) / dl;
-          gXB[k] += g;
-          gXA[k] -= g;
-        }
+    const double gnn = sum3(gn * nk);
+    double sg = 0.0;
+    if (fb == 0.0) sg = (kappa * (yg * yg)) * (gn - gnn * nk);
+    if (__any_sync(kFull, act && fb != 0.0)) {
+      const double e = XB - XA;
+      const double dl = sqrt(sum3(e * e));
+      if (fb != 0.0 && dl > 0.0) {
+        const double g = (gn - gnn * nk) / dl;
+        gXB += g;
+        gXA -= g;
+      }
     }
     // x_c = (lo + S1/S0) dx ; V = dx^3 S0
-    double s0 = gV * dx * dx * dx;
-    double s1[3];
-    for (int k = 0; k < 3; ++k) {
-      s1[k] = gxc[k] * dx * inv_S0;
-      s0 -= gxc[k] * (xc[k] - pr.lo[k] * dx) * inv_S0;
+    const double s1 = gxc * dx * inv_S0;
+    const double s0t = gxc * (xc - pr.lo[kc] * dx) * inv_S0;
+    const double s0 = ((gV * dx * dx * dx - at(s0t, 0)) - at(s0t, 1)) - at(s0t, 2);
+    if (inr) {
+      float* sd = B.seeds + static_cast<size_t>(p) * kSeedFloats;
+      double* pg = B.pgrad + static_cast<size_t>(p) * kPairGrad;
+      if (k < 3) {
+        sd[1 + k] = act ? static_cast<float>(s1) : 0.f;
+        sd[4 + k] = act ? static_cast<float>(sg) : 0.f;
+        pg[k] = act ? gXA : 0.0;
+        pg[3 + k] = 0.0;
+        pg[6 + k] = act ? gXB : 0.0;
+        pg[9 + k] = 0.0;
+      } else {
+        sd[0] = act ? static_cast<float>(s0) : 0.f;
+        sd[7] = 0.f;
+        pg[12] = act ? gd : 0.0;
+        pg[13] = 0.0;
+        pg[14] = 0.0;
+        pg[15] = 0.0;
+        B.done[p] = 0;
+      }
     }
-    sd[0] = static_cast<float>(s0);
-    for (int k = 0; k < 3; ++k) {
-      sd[1 + k] = static_cast<float>(s1[k]);
-      sd[4 + k] = static_cast<float>(sg[k]);
-    }
-    for (int k = 0; k < 3; ++k) { pg[k] = gXA[k]; pg[6 + k] = gXB[k]; }
-    pg[12] = gd;
-    (void)estar;
   }
 }
 
@@ -231,45 +245,9 @@ struct AdjGeom {
   const float4* sp;  // world planes (x, y, z, offset) in shared memory
 };
 
-// A wall (pid >= n) is type 3: phi = m . c + p0 at box-relative node c, with
-// m from Rt row 0 and p0 from the pair record's size slot (wall_p0).  A
-// polytope's planes go to sm[0 .. nf), their inverse slopes along the sweep
-// axis au (the line clip) to the floats after sm[kMaxFaces].
+// Component k of (a, b, c) by selects (no runtime-indexed array).
 __device__ __forceinline__ float sel3(float a, float b, float c, int k) { return k == 0 ? a : (k == 1 ? b : c); }
 
-__device__ __forceinline__ void adj_load(const Shapes& S, const Parts& D, int pid, const int* ci, const float* cf,
-                                         float4* sm, AdjGeom& g, int n, float wall_p0, int au) {
-  const int lane = threadIdx.x & 31;
-  if (pid >= n) {
-    g.type = 3;
-    for (int k = 0; k < 3; ++k) {
-      g.c[k] = 0.f;
-      g.size[k] = wall_p0;
-    }
-    for (int k = 0; k < 9; ++k) g.rt[k] = D.Rt[9 * pid + k];
-    g.nf = 0;
-    g.sp = sm;
-    return;
-  }
-  g.type = S.type[pid];
-  for (int k = 0; k < 3; ++k) {
-    g.c[k] = static_cast<float>(ci[k]) + cf[k];
-    g.size[k] = S.size_l[3 * pid + k];
-  }
-  for (int k = 0; k < 9; ++k) g.rt[k] = D.Rt[9 * pid + k];
-  g.nf = 0;
-  if (g.type == 2) {
-    const int f0 = S.face_off[pid];
-    g.nf = S.face_off[pid + 1] - f0;
-    if (lane < g.nf) {
-      const float4 e = D.wplane[f0 + lane];
-      sm[lane] = e;
-      reinterpret_cast<float*>(sm + kMaxFaces)[lane] = clip_inv(sel3(e.x, e.y, e.z, au));
-    }
-    __syncwarp();
-  }
-  g.sp = sm;
-}
 
 // phi (lattice units, inflate included), unit world gradient, |r| (spheres).
 // SET is the context's kind set (2: cubes only, 1: spheres, cuboids and
@@ -966,7 +944,7 @@ void launch_adjoint(const Params& P, const Shapes& S, const Parts& D, const List
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int wneed0 = (P.max_pairs + 31) / 32;
+  const int wneed0 = (P.max_pairs + 7) / 8;   // pre: eight pairs per warp pass
   const int wgrid0 = wneed0 < 8 * sms ? (wneed0 > 0 ? wneed0 : 1) : 8 * sms;
   launch_pdl(k_adj_pre, dim3(wgrid0), dim3(32), 0, st, P, S, D, W, B, vel, gF, gT);
   // compiled per kind set, as the node sweep (2 cubes only, 1 spheres / cuboids / walls, 0 every kind)
