@@ -44,3 +44,35 @@ def test_config_struct_layout():
     # 2 int32 (160): 160 bytes
     assert ctypes.sizeof(Config) == 160
     assert Config.dx.offset == 16 and Config.smooth_width.offset == 32 and Config.precision.offset == 56
+
+
+def test_init_refuses_domains_before_touching_the_device():
+    """contact_init's domain checks run on the host before any CUDA call: a
+    periodic box not above 4 R_max + 2 dx, and a particle whose node range could
+    reach 2^16 nodes along an axis (the node sweep packs node offsets in 16
+    bits), both return CONTACT_EDOMAIN with no context."""
+    try:
+        path = build.build()
+    except RuntimeError as e:
+        pytest.skip(f"nvcc unavailable: {e}")
+    from paper_2401_10878_gb300.contact import EDOMAIN, Config
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    lib.contact_config_default.argtypes = [ctypes.POINTER(Config), ctypes.c_int32, P, ctypes.c_double]
+    lib.contact_config_default.restype = None
+    lib.contact_init.argtypes = [ctypes.POINTER(Config), P, P, P, P, P, P, P, ctypes.POINTER(P)]
+    lib.contact_init.restype = ctypes.c_int32
+    import numpy as np
+
+    def init(radius, cells):
+        cfg = Config()
+        nc = (ctypes.c_int32 * 3)(cells, cells, cells)
+        lib.contact_config_default(ctypes.byref(cfg), 1, nc, 1.0)
+        arrs = [np.zeros(1, np.int32), np.array([radius, 0.0, 0.0]), np.zeros(2, np.int32),
+                np.zeros(4), np.full(1, 5e3), np.full(1, 0.3)]
+        out = P(1)
+        rc = lib.contact_init(ctypes.byref(cfg), *[a.ctypes.data_as(P) for a in arrs], None, ctypes.byref(out))
+        return rc, out.value
+
+    assert init(10.0, 41) == (EDOMAIN, None)          # L = 41 <= 4 * 10 + 2
+    assert init(40000.0, 200000) == (EDOMAIN, None)   # 2 R / dx + 4 >= 65535
