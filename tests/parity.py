@@ -189,7 +189,9 @@ def compare(st, g, r, fp64: bool, smooth: bool, forces=None, tol_force=None, box
     # contact point x_c = o + M / V
     o = r.pair_box[:, :3] * dx
     arm_o = np.linalg.norm(ro[:, 1:4] - o, axis=1)
-    tolx = np.where(V > 0, (msens + arm_o * vsens) / np.maximum(V, 1e-300), 0) + rel * L
+    # FP32 moments are summed in box coordinates: their rounding scales with the pair box, not the lattice
+    ext = (r.pair_box[:, 3:6] - r.pair_box[:, :3] + 1).max(axis=1) * dx
+    tolx = np.where(V > 0, (msens + arm_o * vsens) / np.maximum(V, 1e-300), 0) + rel * ext
     if not smooth and not fp64:
         tolx = np.full(len(V), 1e-12 * L)
     _check("x_c", np.abs(go[hit, 1:4] - ro[hit, 1:4]).max(axis=1, initial=0), tolx[hit], out)
