@@ -686,6 +686,24 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Warp sums of (a, b, c) by halving exchanges (7 shuffles): lanes 4, 5, 6
+// return the sums of a, b, c (other lanes: partial values).
+__device__ __forceinline__ float warp_sum3_to_456(float a, float b, float c) {
+  const int lane = threadIdx.x & 31;
+  const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1;
+  // (a, b) on lanes with bit 4 clear, (c, 0) on the others
+  const float h0 = (b4 ? c : a) + __shfl_xor_sync(kFull, b4 ? a : c, 16);
+  const float h1 = (b4 ? 0.f : b) + __shfl_xor_sync(kFull, b4 ? b : 0.f, 16);
+  // component 2 b4 + b3
+  float h = (b3 ? h1 : h0) + __shfl_xor_sync(kFull, b3 ? h0 : h1, 8);
+  h += __shfl_xor_sync(kFull, h, 4);
+  h += __shfl_xor_sync(kFull, h, 2);
+  h += __shfl_xor_sync(kFull, h, 1);
+  // lane 4 + c reads the lane holding component c (c = 0: lane 0, 1: lane 8, 2: lane 16)
+  const int c3 = lane - 4;
+  return __shfl_sync(kFull, h, (c3 >= 0 && c3 < 3) ? 8 * c3 : 0);
+}
+
 // Tile reduction.  Sharp mode: counts and moments are exact integers, summed
 // with integer warp reductions; the deepest node via an integer max of an
 // order-preserving key and an integer min of the node index among the ties.
@@ -701,16 +719,14 @@ __device__ __forceinline__ float reduce_tile(const Partial& o) {
     y = static_cast<float>(__reduce_add_sync(kFull, __float2int_rn(o.my)));
     z = static_cast<float>(__reduce_add_sync(kFull, __float2int_rn(o.mz)));
   }
-  const float gx = warp_sum(o.gx), gy = warp_sum(o.gy), gz = warp_sum(o.gz);
+  const float g = warp_sum3_to_456(o.gx, o.gy, o.gz);   // lanes 4, 5, 6
   const int key = __reduce_max_sync(kFull, float_key(o.bestf));
   const int idx = __reduce_min_sync(kFull, float_key(o.bestf) == key ? o.bestidx : 0x7fffffff);
   float v = c;
   v = lane == 1 ? x : v;
   v = lane == 2 ? y : v;
   v = lane == 3 ? z : v;
-  v = lane == 4 ? gx : v;
-  v = lane == 5 ? gy : v;
-  v = lane == 6 ? gz : v;
+  v = (lane >= 4 && lane < 7) ? g : v;
   v = lane == 7 ? key_float(key) : v;
   v = lane == 8 ? __int_as_float(idx) : v;
   return v;   // lane c < 9: component c of the tile partial
