@@ -211,9 +211,15 @@ contact_status contact_step(contact_ctx* ctx, const double* pos, const double* q
  * (coherent over NVLink-C2C on Grace-Blackwell), with vel copied, all in one
  * captured graph; other page-locked buffers are copied inside that graph,
  * pageable ones with ordinary copies around the step.  The device buffers are allocated at the first call and owned by
- * the context.  Errors: those of contact_step, reported by this call (it
- * synchronises the context stream); CONTACT_ENOMEM if the buffers cannot be
- * allocated.  A later contact_backward differentiates this step. */
+ * the context.  Completion: with the results written in place and no step of
+ * contact_step still unwaited on this context, the call waits (spinning on a
+ * mapped host word, bounded, then falling back to a synchronisation) for a
+ * token its step publishes after the forces and torques are stored, so it may
+ * return while the step's last kernel is still retiring; otherwise it
+ * synchronises the context stream.  Either way the outputs are complete on
+ * return.  Errors: those of contact_step, reported by this call;
+ * CONTACT_ENOMEM if the buffers cannot be allocated.  A later
+ * contact_backward differentiates this step. */
 contact_status contact_step_host(contact_ctx* ctx, const double* pos, const double* quat, const double* vel,
                                  int32_t* n_pairs, double* force, double* torque, int32_t* pair_ij,
                                  double* pair_out);

@@ -25,6 +25,8 @@ constexpr int kTileItemsPerLane = 4;  // node lines per lane per tile
 constexpr int kPartialFloats = 12;    // FP32 partial sums per tile
 constexpr int kTapeDoubles = 16;      // FP64 per-pair values kept for the adjoint
 constexpr int kStepCounter = 12;      // counters[] slot of the completed-step count
+constexpr int kDoneCounter = 13;      // counters[] slot: particle-sum blocks finished (the last resets it)
+constexpr int kTokenCounter = 14;     // counters[] slot: the host's token of this step
 constexpr int kFtDoubles = 9;         // per-pair F, T_A, T_B
 
 // Error codes written by kernels (same numbering as contact_status).
@@ -255,7 +257,9 @@ struct Lists {
                     // steps completed (its parity selects the contact-history buffer)
   unsigned long long* u64;  // [4]: 0 node evaluations, 1 nominal lane-ops of the node sweep
   int* err;         // [1] sticky device error
-  int* err_host;    // mapped host word mirroring err
+  int* err_host;    // [3] mapped host words: 0 mirrors err; 1 the token of the last completed step
+                    // (written by the step's last block); 2 the token the host gave the step being
+                    // launched (read by k_pose into counters[kTokenCounter])
 };
 
 // --------------------------------------------------------------------------

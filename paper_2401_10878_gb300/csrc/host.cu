@@ -27,7 +27,10 @@ struct contact_ctx {
   int grid_narrow = 0;
   int grid_adjoint = 0;
   std::vector<void*> dev_allocs;
-  int* err_host = nullptr;        // mapped pinned word written by the last kernel of a step
+  int* err_host = nullptr;        // mapped pinned words: the error mirror and the step tokens (Lists::err_host)
+  int host_token = 0;             // the last token contact_step_host gave a step
+  bool hzero = false;             // the captured host-buffer graph writes the results in place (no copies)
+  bool step_unwaited = false;     // contact_step enqueued a step nobody has waited for through this context
   double* adj_scratch = nullptr;  // adjoint tile partials, pair seeds and pair gradients
   std::string last_error = "no error";
   // graph cache
@@ -667,8 +670,8 @@ contact_status contact_init(const contact_config* cfg, const int32_t* shape_type
   GBC_TRY(cudaEventCreate(&c->ev_narrow[1]));
   GBC_TRY(cudaEventCreate(&c->ev_adj[0]));
   GBC_TRY(cudaEventCreate(&c->ev_adj[1]));
-  GBC_TRY(cudaHostAlloc(reinterpret_cast<void**>(&c->err_host), sizeof(int), cudaHostAllocMapped));
-  *c->err_host = 0;
+  GBC_TRY(cudaHostAlloc(reinterpret_cast<void**>(&c->err_host), 3 * sizeof(int), cudaHostAllocMapped));
+  c->err_host[0] = c->err_host[1] = c->err_host[2] = 0;
   int* err_dev_view = nullptr;
   GBC_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&err_dev_view), c->err_host, 0));
   W.err_host = err_dev_view;
@@ -748,6 +751,7 @@ contact_status contact_step(contact_ctx* c, const double* pos, const double* qua
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
   }
+  c->step_unwaited = true;
   c->have_step = true;
   c->last_vel = vel;
   return CONTACT_OK;
@@ -1031,6 +1035,20 @@ contact_status contact_step_host(contact_ctx* c, const double* pos, const double
     cudaMemcpyAsync(torque, c->hs_torque, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     cudaMemcpyAsync(n_pairs, c->hs_npairs, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
   };
+  // When the kernels write the results in place (no copies after the last
+  // kernel) and no step of contact_step may still be queued, the step gets a
+  // fresh token (read by its first kernel, published by its last block once
+  // the results are stored) and the call waits for that token instead of
+  // synchronising the stream; a queued step could carry the token, so after
+  // contact_step, as with copies, it synchronises (and later calls use tokens
+  // again).
+  const bool in_place = same ? c->hzero : zero_copy;
+  const bool idle = in_place && !c->step_unwaited;
+  int token = 0;
+  if (idle) {
+    token = c->host_token = c->host_token == 0x7fffffff ? 1 : c->host_token + 1;
+    reinterpret_cast<volatile int*>(c->err_host)[2] = token;
+  }
   if (all_pinned && c->cfg.use_graph && c->stream != nullptr) {
     if (!same) {
       cudaGraph_t g = nullptr;
@@ -1057,6 +1075,7 @@ contact_status contact_step_host(contact_ctx* c, const double* pos, const double
       }
       cudaGraphDestroy(g);
       std::memcpy(c->hkey, key, sizeof(key));
+      c->hzero = zero_copy;
     }
     e = cudaGraphLaunch(c->hexec, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
@@ -1067,8 +1086,16 @@ contact_status contact_step_host(contact_ctx* c, const double* pos, const double
   }
   c->have_step = true;
   c->last_vel = dvel;
-  e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  bool done = false;
+  if (idle) {   // bounded wait for the token (a step that fails to finish is reported by the synchronisation)
+    const volatile int* published = c->err_host + 1;
+    for (long it = 0; it < (1L << 26) && !done; ++it) done = *published == token;
+  }
+  if (!done) {
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  }
+  c->step_unwaited = false;
   const contact_status st = check_sticky(c);
   if (st != CONTACT_OK) return st;
   if (pair_ij != nullptr || pair_out != nullptr) {

@@ -13,24 +13,9 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// K6: per particle and component (eight lanes per particle, six used), FP64
-// adds in a fixed order: the pairs where the particle is j (by i), then the
-// pairs where it is i (by j).  j receives +F and T_B, i receives -F and T_A.
-// The first eight lower-partner pair indices are fetched together with the
-// counts.
-__global__ void __launch_bounds__(32) k_particle_sum(Params P, Parts D, Lists W, double* __restrict__ force,
-                                                      double* __restrict__ torque) {
-  pdl_begin();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t == 0) {
-    *W.err_host = *W.err;
-    ++W.counters[kStepCounter];   // the contact history written this step is read by the next
-  }
-  // the cell list's bin counts start the next step at zero
-  const int nbins = P.nbin[0] * P.nbin[1] * P.nbin[2];
-  for (int b = t; b < nbins; b += gridDim.x * blockDim.x) W.bin_count[b] = 0;
-  const int p = t >> 3, c = t & 7;
-  if (p >= P.n || c >= 6) return;
+// The sum of particle p's component c (one lane).
+__device__ __forceinline__ void particle_sum(const Params& P, const Lists& W, int p, int c, double* __restrict__ force,
+                                             double* __restrict__ torque) {
   const int* dp = W.dn_pair + static_cast<size_t>(p) * P.max_nbr;
   int pre[8];
 #pragma unroll
@@ -59,6 +44,38 @@ __global__ void __launch_bounds__(32) k_particle_sum(Params P, Parts D, Lists W,
   }
   if (c < 3) force[3 * p + c] = acc;
   else torque[3 * p + c - 3] = acc;
+}
+
+// K6: per particle and component (eight lanes per particle, six used), FP64
+// adds in a fixed order: the pairs where the particle is j (by i), then the
+// pairs where it is i (by j).  j receives +F and T_B, i receives -F and T_A.
+// The first eight lower-partner pair indices are fetched together with the
+// counts.
+__global__ void __launch_bounds__(32) k_particle_sum(Params P, Parts D, Lists W, double* __restrict__ force,
+                                                      double* __restrict__ torque) {
+  pdl_begin();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) ++W.counters[kStepCounter];   // the contact history written this step is read by the next
+  // the cell list's bin counts start the next step at zero
+  const int nbins = P.nbin[0] * P.nbin[1] * P.nbin[2];
+  for (int b = t; b < nbins; b += gridDim.x * blockDim.x) W.bin_count[b] = 0;
+  const int p = t >> 3, c = t & 7;
+  if (p < P.n && c < 6) particle_sum(P, W, p, c, force, torque);
+  // the step is complete when every block's sums are stored: the last block
+  // to finish mirrors the error word and then publishes the host's token of
+  // this step (mapped host memory), so a host waiting for the results can
+  // return without a stream synchronisation
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) {
+    __threadfence_system();
+    const unsigned prev = atomicAdd(reinterpret_cast<unsigned*>(W.counters + kDoneCounter), 1u);
+    if (prev == gridDim.x - 1) {
+      W.counters[kDoneCounter] = 0;
+      *reinterpret_cast<volatile int*>(W.err_host) = __ldcg(W.err);
+      __threadfence_system();
+      *reinterpret_cast<volatile int*>(W.err_host + 1) = __ldcg(W.counters + kTokenCounter);
+    }
+  }
 }
 
 }  // namespace

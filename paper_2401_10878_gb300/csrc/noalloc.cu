@@ -115,10 +115,8 @@ __global__ void k_noalloc_prep(Params P, int* type, int* kind, double* param, fl
   for (int b = t; b < nbins; b += gridDim.x * blockDim.x) W.bin_count[b] = 0;
   if (t < 16) W.counters[t] = 0;
   if (t < 4) W.u64[t] = 0;
-  if (t == 0) {
-    *W.err = 0;
-    *W.err_host = 0;
-  }
+  if (t == 0) *W.err = 0;
+  if (t < 4) W.err_host[t] = 0;
 }
 
 }  // namespace
@@ -269,7 +267,7 @@ extern "C" contact_status contact_step_noalloc(const contact_config* cfg, const 
   W.counters = cv.take<int>(16);
   W.u64 = cv.take<unsigned long long>(4);
   W.err = cv.take<int>(1);
-  W.err_host = cv.take<int>(1);
+  W.err_host = cv.take<int>(4);   // the mapped-host words of the context path, here on the device
   if (cv.overflow) return CONTACT_EINVAL;
 
   // inputs into the scratch array (copies, no allocation)

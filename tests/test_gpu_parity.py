@@ -370,6 +370,39 @@ def test_step_host_mapped_buffers_with_velocities():
     m.close()
 
 
+def test_step_host_waits_for_its_own_step():
+    """contact_step_host returns once its own step's results are in host
+    memory: with in-place host buffers and an idle stream it waits for the
+    token its step publishes at the end.  A loop of calls with changing poses
+    gives the device-pointer steps' forces and torques bit for bit, and a call
+    right after an asynchronous step (work still queued on the stream)
+    synchronises instead and is exact too."""
+    st = W.settling_cubes()
+    m = model_for(st)
+    pos, quat = W.pose_sequence(st, 6, seed=5, sigma_x=0.3, sigma_rot=0.02)
+    refs = []
+    for k in range(6):
+        dev = m.step(torch.tensor(pos[k], device="cuda"), torch.tensor(quat[k], device="cuda"))
+        refs.append((dev["force"].cpu(), dev["torque"].cpu()))
+    hp = torch.empty((st.n, 3), dtype=torch.float64).pin_memory()
+    hq = torch.empty((st.n, 4), dtype=torch.float64).pin_memory()
+    hf = torch.empty((st.n, 3), dtype=torch.float64).pin_memory()
+    ht = torch.empty((st.n, 3), dtype=torch.float64).pin_memory()
+    for rnd in range(2):
+        for k in range(6):
+            hp.copy_(torch.from_numpy(pos[k]))
+            hq.copy_(torch.from_numpy(quat[k]))
+            m.step_host(hp, hq, force=hf, torque=ht)
+            assert torch.equal(hf, refs[k][0]) and torch.equal(ht, refs[k][1]), (rnd, k)
+    tp, tq = torch.tensor(pos[0], device="cuda"), torch.tensor(quat[0], device="cuda")
+    m.step_async(tp, tq)   # queued, not waited for
+    hp.copy_(torch.from_numpy(pos[3]))
+    hq.copy_(torch.from_numpy(quat[3]))
+    m.step_host(hp, hq, force=hf, torque=ht)
+    assert torch.equal(hf, refs[3][0]) and torch.equal(ht, refs[3][1])
+    m.close()
+
+
 def test_fp32_ffma_rate_against_the_derived_peak():
     """The measured FFMA rate lies between half and 105 % of SMs x 128 lanes x
     the maximum SM clock (the node sweep's roofline peak)."""
