@@ -20,8 +20,8 @@
 //     dphi/dX = -grad phi,  dphi/domega = grad phi x r,
 //     sphere: d(grad phi)/dX = -(I - g g^T)/|r|; faces: d(grad phi) = omega x grad phi.
 //   The warp completing a pair's last tile sums the tile partials in FP64
-//   and stages the pair; eight staged pairs at a time get the post step:
-//   lattice -> physical and the depth term at x* (four lanes per pair).
+//   and adds them, in physical units, to the pair's pose gradient (which
+//   k_adj_pre starts with the explicit and the depth terms).
 // k_adj_scatter: per particle in the forward order; the rotation gradient tau
 //   becomes dL/dq = (2/|q|) (-v.tau, w tau + tau x v) for q/|q| = (w, v).
 #include <cfloat>
@@ -48,13 +48,6 @@ struct AdjBufs {
   int* done;       // [max_pairs] tiles of the pair swept so far (pairs of several tiles)
 };
 
-// A pair whose cell sums are complete, staged in shared memory for the post step.
-struct AdjStage {
-  double s[12];    // FP64 sums of the 12 pose directions (lattice units)
-  int q;           // pair index
-  int pad;
-};
-constexpr int kAdjStage = 8;   // pairs per post pass (four lanes each)
 
 __device__ __forceinline__ void cross3(const double a[3], const double b[3], double c[3]) {
   c[0] = a[1] * b[2] - a[2] * b[1];
@@ -63,6 +56,137 @@ __device__ __forceinline__ void cross3(const double a[3], const double b[3], dou
 }
 
 // ---------------------------------------------------------------- pair level
+// The depth term of d = -phiA(x*) - phiB(x*) at the pair's deepest node x*
+// (the tape's node index), seeded with gd = dL/dd: d(-phi)/dX = grad phi and
+// d(-phi)/domega = r x grad phi (world frame; the face of the maximum, first
+// index on ties), component kc on lanes 0..2 of the pair's four (the layout
+// of k_adj_pre).  Called by the whole warp; `want` selects the pairs that
+// need it (the others get zeros).
+__device__ __forceinline__ void adj_depth_term(const Params& P, const Shapes& S, const Parts& D, const PairRec& pr,
+                                               const double* tp, double gd, bool want, double& dA, double& dcA,
+                                               double& dB, double& dcB) {
+  const int lane = threadIdx.x & 31;
+  const int k = lane & 3, kc = k < 3 ? k : 0, b0 = lane & ~3;
+  const int k1 = kc == 2 ? 0 : kc + 1, k2 = kc == 0 ? 2 : kc - 1;
+  dA = dcA = dB = dcB = 0.0;
+  if (__any_sync(kFull, want)) {
+    const int i = pr.i, j = pr.j;
+    const int d0 = pr.dim[0], d1 = pr.dim[1], d2 = pr.dim[2];
+    const int idx = min(max(static_cast<int>(tp[13]), 0), d0 * d1 * d2 - 1);
+    const int ck = kc == 0 ? idx % d0 : (kc == 1 ? (idx / d0) % d1 : idx / (d0 * d1));
+    const int lok = kc == 0 ? pr.lo[0] : (kc == 1 ? pr.lo[1] : pr.lo[2]);
+    const int sh = kc == 0 ? pr.shift[0] : (kc == 1 ? pr.shift[1] : pr.shift[2]);
+    const double Lk = kc == 0 ? P.L[0] : (kc == 1 ? P.L[1] : P.L[2]);
+    const double xk = static_cast<double>(lok + ck) * P.dx;
+    const double XA = D.X[3 * i + kc];
+    const double XB = D.X[3 * j + kc] - (sh == 0 ? 0.0 : (sh > 0 ? Lk : -Lk));
+    const double rAk = xk - XA, rBk = xk - XB;
+    double rA[3], rB[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      rA[c] = __shfl_sync(kFull, rAk, b0 + c);
+      rB[c] = __shfl_sync(kFull, rBk, b0 + c);
+    }
+    // world gradient component kc of one particle's phi at x* (r = x* - X, scalars;
+    // shp: the image shift of this lane's component, 0 for particle i)
+    auto grad_k = [&](int pid, double r0, double r1, double r2, int shp) -> double {
+      const double* R = D.R + 9 * pid;
+      const int type = S.type[pid];
+      const double yk = R[kc] * r0 + R[3 + kc] * r1 + R[6 + kc] * r2;   // y = R^T r
+      const double y0 = __shfl_sync(kFull, yk, b0), y1 = __shfl_sync(kFull, yk, b0 + 1),
+                   y2 = __shfl_sync(kFull, yk, b0 + 2);
+      // this lane's candidate: value and index of its faces (cuboid: face pair kc; polytope: kc, kc + 3, ...)
+      double best = -1e300;
+      int bidx = 0x7fffffff;
+      // polytopes: an FP32 prefilter over the world planes (lattice units,
+      // inflate included: the FP64 values up to a constant shift and scale,
+      // so the same order of faces).  Each lane keeps its best face and the
+      // value of its second; the FP64 value of a lane's best face is formed
+      // when it lies within the margin of the pair's FP32 maximum, and every
+      // face is formed in FP64 when a second face of a lane lies within it
+      // too.  The margin is far above the FP32 rounding (~1e-6 of the terms),
+      // so the faces left out lie below the FP64 maximum.  The shuffles run on
+      // every lane (other types carry no faces).
+      const bool poly = type == 2;
+      const int f0 = poly ? S.face_off[pid] : 0, nf = poly ? S.face_off[pid + 1] - f0 : 0;
+      float rl = 0.f;
+      if (poly) {
+        const float ncell = static_cast<float>(kc == 0 ? P.ncell[0] : (kc == 1 ? P.ncell[1] : P.ncell[2]));
+        rl = (static_cast<float>((lok + ck) - D.kX[3 * pid + kc]) + static_cast<float>(shp) * ncell) -
+             D.fX[3 * pid + kc];
+      }
+      const float rl0 = __shfl_sync(kFull, rl, b0), rl1 = __shfl_sync(kFull, rl, b0 + 1),
+                  rl2 = __shfl_sync(kFull, rl, b0 + 2);
+      float v1 = -FLT_MAX, v2 = -FLT_MAX, wmax = 0.f;
+      int i1 = kc;
+      for (int f = kc; f < nf && k < 3; f += 3) {
+        const float4 e = D.wplane[f0 + f];
+        const float v = fmaf(e.x, rl0, fmaf(e.y, rl1, fmaf(e.z, rl2, -e.w)));
+        wmax = fmaxf(wmax, fabsf(e.w));
+        if (v > v1) {
+          v2 = v1;
+          v1 = v;
+          i1 = f;
+        } else {
+          v2 = fmaxf(v2, v);
+        }
+      }
+      float m32 = fmaxf(v1, __shfl_xor_sync(kFull, v1, 1));
+      m32 = fmaxf(m32, __shfl_xor_sync(kFull, m32, 2));
+      wmax = fmaxf(wmax, __shfl_xor_sync(kFull, wmax, 1));
+      wmax = fmaxf(wmax, __shfl_xor_sync(kFull, wmax, 2));
+      const float margin = 1e-5f * (1.f + fabsf(rl0) + fabsf(rl1) + fabsf(rl2) + wmax);
+      const bool all_faces = __any_sync(kFull, poly && k < 3 && v2 >= m32 - margin);
+      if (type == 1) {
+        best = fabs(yk) - S.param[3 * pid + kc];
+        bidx = kc;
+      } else if (poly && all_faces) {
+        for (int f = kc; f < nf; f += 3) {
+          const double* pl = S.planes + 4 * (f0 + f);
+          const double a = (pl[0] * y0 + pl[1] * y1 + pl[2] * y2) - pl[3];
+          if (a > best) { best = a; bidx = f; }
+        }
+      } else if (poly && k < 3 && i1 < nf && v1 >= m32 - margin) {
+        const double* pl = S.planes + 4 * (f0 + i1);
+        best = (pl[0] * y0 + pl[1] * y1 + pl[2] * y2) - pl[3];
+        bidx = i1;
+      }
+      if (k == 3) { best = -1e300; bidx = 0x7fffffff; }
+      // first maximal face over the pair's three lanes
+#pragma unroll
+      for (int o = 1; o <= 2; o <<= 1) {
+        const double ob = __shfl_xor_sync(kFull, best, o);
+        const int oi = __shfl_xor_sync(kFull, bidx, o);
+        if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+      }
+      // sphere r / |r|; cuboid R e_kk sign(y_kk); polytope R n_f
+      if (type == 0) {   // r / |r| by a Newton-Raphson reciprocal square root
+        const double rr = r0 * r0 + r1 * r1 + r2 * r2;
+        return rr > 0.0 ? (kc == 0 ? r0 : (kc == 1 ? r1 : r2)) * fl::nr_rsqrt(rr) : 0.0;
+      }
+      if (type == 1) {
+        const int bb = min(max(bidx, 0), 2);
+        const double ykk = bb == 0 ? y0 : (bb == 1 ? y1 : y2);
+        return R[3 * kc + bb] * (ykk < 0.0 ? -1.0 : 1.0);
+      }
+      const double* pl = S.planes + 4 * (f0 + min(max(bidx, 0), nf - 1));   // (a face always: nf >= 1 here)
+      return R[3 * kc] * pl[0] + R[3 * kc + 1] * pl[1] + R[3 * kc + 2] * pl[2];
+    };
+    const double g[2] = {grad_k(i, rA[0], rA[1], rA[2], 0), grad_k(j, rB[0], rB[1], rB[2], sh)};
+    // r x grad phi, component kc
+    const double gA1 = __shfl_sync(kFull, g[0], b0 + k1), gA2 = __shfl_sync(kFull, g[0], b0 + k2);
+    const double gB1 = __shfl_sync(kFull, g[1], b0 + k1), gB2 = __shfl_sync(kFull, g[1], b0 + k2);
+    const double rA1 = kc == 0 ? rA[1] : (kc == 1 ? rA[2] : rA[0]), rA2 = kc == 0 ? rA[2] : (kc == 1 ? rA[0] : rA[1]);
+    const double rB1 = kc == 0 ? rB[1] : (kc == 1 ? rB[2] : rB[0]), rB2 = kc == 0 ? rB[2] : (kc == 1 ? rB[0] : rB[1]);
+    if (want) {
+      dA = gd * g[0];
+      dcA = gd * (rA1 * gA2 - rA2 * gA1);
+      dB = gd * g[1];
+      dcB = gd * (rB1 * gB2 - rB2 * gB1);
+    }
+  }
+}
+
 // The pair-level chain rule, four lanes per pair and eight pairs per warp pass:
 // component k = 0..2 of every 3-vector on lanes 0..2 of the pair (cross and dot
 // products by shuffles), lane 3 for the third reciprocal square root and the
@@ -209,6 +333,11 @@ __global__ void __launch_bounds__(32) k_adj_pre(Params P, Shapes S, Parts D, Lis
         gXA -= g;
       }
     }
+    // the depth term at the deepest node (independent of the cell sums, so formed here)
+    double dA, dcA, dB, dcB;
+    adj_depth_term(P, S, D, pr, tp, gd, act && gd != 0.0 && d > 0.0, dA, dcA, dB, dcB);
+    gXA += dA;
+    gXB += dB;
     // x_c = (lo + S1/S0) dx ; V = dx^3 S0
     const double s1 = gxc * dx * inv_S0;
     const double s0t = gxc * (xc - pr.lo[kc] * dx) * inv_S0;
@@ -220,9 +349,9 @@ __global__ void __launch_bounds__(32) k_adj_pre(Params P, Shapes S, Parts D, Lis
         sd[1 + k] = act ? static_cast<float>(s1) : 0.f;
         sd[4 + k] = act ? static_cast<float>(sg) : 0.f;
         pg[k] = act ? gXA : 0.0;
-        pg[3 + k] = 0.0;
+        pg[3 + k] = act ? dcA : 0.0;
         pg[6 + k] = act ? gXB : 0.0;
-        pg[9 + k] = 0.0;
+        pg[9 + k] = act ? dcB : 0.0;
       } else {
         sd[0] = act ? static_cast<float>(s0) : 0.f;
         sd[7] = 0.f;
@@ -406,113 +535,6 @@ __device__ __forceinline__ void cross3f(const float a[3], const float b[3], floa
 }
 
 
-// ---------------------------------------------------------------- pair post
-// FP64 post step of up to kAdjStage staged pairs, four lanes per pair
-// (component k = 0..2 on lanes 0..2, lane 3 idle): the cell sums scaled to
-// physical units are added to the pair's pose gradient, then the depth term of
-// d = -phiA(x*) - phiB(x*) at the deepest node: d(-phi)/dX = grad phi and
-// d(-phi)/domega = r x grad phi (world frame; the face of the maximum, first
-// index on ties).
-__device__ __forceinline__ void adj_post_pass(const Params& P, const Shapes& S, const Parts& D, const Lists& W,
-                                              const AdjBufs& B, const AdjStage* e, int n) {
-  const int lane = threadIdx.x & 31;
-  const int slot = lane >> 2, k = lane & 3, kc = k < 3 ? k : 0, b0 = lane & ~3;
-  const int k1 = kc == 2 ? 0 : kc + 1, k2 = kc == 0 ? 2 : kc - 1;
-  const bool act = slot < n;
-  const AdjStage& st = e[act ? slot : 0];
-  const int q = st.q;
-  double* pg = B.pgrad + static_cast<size_t>(q) * kPairGrad;
-  const double* tp = W.tape + static_cast<size_t>(q) * kTapeDoubles;
-  const PairRec& pr = W.pairs[q];
-  const double gd = pg[12];
-  const bool depth = gd != 0.0 && tp[7] > 0.0;
-  const double inv_dx = P.inv_dx;
-  double dA = 0.0, dcA = 0.0, dB = 0.0, dcB = 0.0;   // depth-term increments of component kc
-  if (__any_sync(kFull, act && depth)) {
-    const int i = pr.i, j = pr.j;
-    const int d0 = pr.dim[0], d1 = pr.dim[1], d2 = pr.dim[2];
-    const int idx = min(max(static_cast<int>(tp[13]), 0), d0 * d1 * d2 - 1);
-    const int ck = kc == 0 ? idx % d0 : (kc == 1 ? (idx / d0) % d1 : idx / (d0 * d1));
-    const int lok = kc == 0 ? pr.lo[0] : (kc == 1 ? pr.lo[1] : pr.lo[2]);
-    const int sh = kc == 0 ? pr.shift[0] : (kc == 1 ? pr.shift[1] : pr.shift[2]);
-    const double Lk = kc == 0 ? P.L[0] : (kc == 1 ? P.L[1] : P.L[2]);
-    const double xk = static_cast<double>(lok + ck) * P.dx;
-    const double XA = D.X[3 * i + kc];
-    const double XB = D.X[3 * j + kc] - (sh == 0 ? 0.0 : (sh > 0 ? Lk : -Lk));
-    const double rAk = xk - XA, rBk = xk - XB;
-    double rA[3], rB[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      rA[c] = __shfl_sync(kFull, rAk, b0 + c);
-      rB[c] = __shfl_sync(kFull, rBk, b0 + c);
-    }
-    // world gradient component kc of one particle's phi at x* (r = x* - X, scalars)
-    auto grad_k = [&](int pid, double r0, double r1, double r2) -> double {
-      const double* R = D.R + 9 * pid;
-      const int type = S.type[pid];
-      const double yk = R[kc] * r0 + R[3 + kc] * r1 + R[6 + kc] * r2;   // y = R^T r
-      const double y0 = __shfl_sync(kFull, yk, b0), y1 = __shfl_sync(kFull, yk, b0 + 1),
-                   y2 = __shfl_sync(kFull, yk, b0 + 2);
-      // this lane's candidate: value and index of its faces (cuboid: face pair kc; polytope: kc, kc + 3, ...)
-      double best = -1e300;
-      int bidx = 0x7fffffff;
-      if (type == 1) {
-        best = fabs(yk) - S.param[3 * pid + kc];
-        bidx = kc;
-      } else if (type == 2) {
-        const int f0 = S.face_off[pid], nf = S.face_off[pid + 1] - f0;
-        for (int f = kc; f < nf; f += 3) {
-          const double* pl = S.planes + 4 * (f0 + f);
-          const double a = (pl[0] * y0 + pl[1] * y1 + pl[2] * y2) - pl[3];
-          if (a > best) { best = a; bidx = f; }
-        }
-      }
-      if (k == 3) { best = -1e300; bidx = 0x7fffffff; }
-      // first maximal face over the pair's three lanes
-#pragma unroll
-      for (int o = 1; o <= 2; o <<= 1) {
-        const double ob = __shfl_xor_sync(kFull, best, o);
-        const int oi = __shfl_xor_sync(kFull, bidx, o);
-        if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
-      }
-      // sphere r / |r|; cuboid R e_kk sign(y_kk); polytope R n_f
-      if (type == 0) {
-        const double nr = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
-        return nr > 0.0 ? (kc == 0 ? r0 : (kc == 1 ? r1 : r2)) / nr : 0.0;
-      }
-      if (type == 1) {
-        const double ykk = bidx == 0 ? y0 : (bidx == 1 ? y1 : y2);
-        return R[3 * kc + bidx] * (ykk < 0.0 ? -1.0 : 1.0);
-      }
-      const double* pl = S.planes + 4 * (S.face_off[pid] + bidx);
-      return R[3 * kc] * pl[0] + R[3 * kc + 1] * pl[1] + R[3 * kc + 2] * pl[2];
-    };
-    const double g[2] = {grad_k(i, rA[0], rA[1], rA[2]), grad_k(j, rB[0], rB[1], rB[2])};
-    // r x grad phi, component kc
-    const double gA1 = __shfl_sync(kFull, g[0], b0 + k1), gA2 = __shfl_sync(kFull, g[0], b0 + k2);
-    const double gB1 = __shfl_sync(kFull, g[1], b0 + k1), gB2 = __shfl_sync(kFull, g[1], b0 + k2);
-    const double rA1 = kc == 0 ? rA[1] : (kc == 1 ? rA[2] : rA[0]), rA2 = kc == 0 ? rA[2] : (kc == 1 ? rA[0] : rA[1]);
-    const double rB1 = kc == 0 ? rB[1] : (kc == 1 ? rB[2] : rB[0]), rB2 = kc == 0 ? rB[2] : (kc == 1 ? rB[0] : rB[1]);
-    dA = gd * g[0];
-    dcA = gd * (rA1 * gA2 - rA2 * gA1);
-    dB = gd * g[1];
-    dcB = gd * (rB1 * gB2 - rB2 * gB1);
-  }
-  if (act && k < 3) {
-    // lattice position -> physical position, then the depth term
-    pg[k] += st.s[k] * inv_dx;
-    pg[3 + k] += st.s[3 + k];
-    pg[6 + k] += st.s[6 + k] * inv_dx;
-    pg[9 + k] += st.s[9 + k];
-    if (depth) {
-      pg[k] += dA;
-      pg[3 + k] += dcA;
-      pg[6 + k] += dB;
-      pg[9 + k] += dcB;
-    }
-  }
-}
-
 // The geometry of particle i (second = false) or j of a staged pair record:
 // centre, R^T rows and sizes as the forward's sweep reads them, the type from
 // the record's kinds; a polytope's planes and their inverse slopes along the
@@ -568,12 +590,10 @@ __device__ __forceinline__ int adj_rec_pair(const int4& v) {
   const int w = c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
   return __shfl_sync(kFull, w, kPairWord >> 2);
 }
-// The seeds of pair p: lanes 0..6 hold s0, s1 and sg, lane 7 a flag for a
-// non-zero depth seed.
+// The seeds of pair p: lanes 0..6 hold s0, s1 and sg (all zero: the pair's
+// cells add nothing, its explicit and depth terms came from k_adj_pre).
 __device__ __forceinline__ float adj_seed(const AdjBufs& B, int p, int lane) {
-  if (lane < 7) return B.seeds[static_cast<size_t>(p) * kSeedFloats + lane];
-  if (lane == 7) return B.pgrad[static_cast<size_t>(p) * kPairGrad + 12] != 0.0 ? 1.f : 0.f;
-  return 0.f;
+  return lane < 7 ? B.seeds[static_cast<size_t>(p) * kSeedFloats + lane] : 0.f;
 }
 
 // Sum of acc[0 .. 12) over the warp by halving exchanges (14 shuffles): lane
@@ -611,12 +631,10 @@ __device__ __forceinline__ float adj_warp_sum12(const float acc[12]) {
 template <int SET>
 __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, Parts D, Lists W, AdjBufs B) {
   __shared__ float4 s_pl[kWarps][2][kMaxFaces + kMaxFaces / 4];   // planes, then their inverse slopes
-  __shared__ AdjStage s_st[kWarps][kAdjStage];
   __shared__ __align__(16) PairRec s_rec[kWarps][2];
   __shared__ unsigned s_pk[SET == 0 ? kWarps : 1][kTileItemsPerLane * 32];   // clipped ranges (rolled sweep)
   __shared__ int4 s_own[kWarps][64];   // the lanes with clipped nodes of the current tile
   constexpr bool ROLL = SET == 0;   // every kind: rolled slot loops (code size)
-  int nst = 0;   // pairs staged in s_st[wid]
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int ntiles = min(W.counters[1], P.max_tiles);
@@ -645,9 +663,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
     }
     const PairRec& r = s_rec[wid][buf];
     const bool valid = record_in_bounds(P, W.err, r, true);
-    const bool active = valid && __any_sync(kFull, lane < 8 && seed != 0.f);
+    const bool active = valid && __any_sync(kFull, lane < 7 && seed != 0.f);
     const int p = r.pair;
     const int t = r.tile0 + r.tile;   // the tile's index (its partial slot)
+    // the pair's pose gradient so far (explicit and depth terms), lane c < 12:
+    // component c, read now for the sum added at the pair's end
+    const double pgv = (active && lane < 12) ? B.pgrad[static_cast<size_t>(p) * kPairGrad + lane] : 0.0;
     float acc[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = 0.f;
@@ -850,15 +871,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
           sum += __shfl_xor_sync(kFull, sum, 16);
         }
       }
-      if (complete) {
-        if (lane < 12) s_st[wid][nst].s[lane] = sum;
-        if (lane == 0) s_st[wid][nst].q = p;
-        if (++nst == kAdjStage) {
-          __syncwarp();
-          adj_post_pass(P, S, D, W, B, s_st[wid], nst);
-          __syncwarp();
-          nst = 0;
-        }
+      if (complete && lane < 12) {   // cell sums in lattice units -> physical (positions / dx)
+        const bool pos_part = lane < 3 || (lane >= 6 && lane < 9);
+        B.pgrad[static_cast<size_t>(p) * kPairGrad + lane] = pgv + (pos_part ? sum * P.inv_dx : sum);
       }
     }
     __syncwarp();
@@ -867,10 +882,6 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
     buf ^= 1;
     qpos = qn;
     seed = seed_n;
-  }
-  if (nst > 0) {
-    __syncwarp();
-    adj_post_pass(P, S, D, W, B, s_st[wid], nst);
   }
 }
 
