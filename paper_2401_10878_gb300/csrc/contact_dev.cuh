@@ -260,6 +260,9 @@ struct Lists {
   int* err_host;    // [3] mapped host words: 0 mirrors err; 1 the token of the last completed step
                     // (written by the step's last block); 2 the token the host gave the step being
                     // launched (read by k_pose into counters[kTokenCounter])
+  int publish;      // 1 in a host-buffer step that returns on its token: k_pose reads the token, the
+                    // particle sums' last block mirrors err and publishes it (0: err mirrored at the
+                    // start of the particle sums, no token)
 };
 
 // --------------------------------------------------------------------------

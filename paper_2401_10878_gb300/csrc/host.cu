@@ -239,22 +239,27 @@ contact_status check_sticky(contact_ctx* c) {
 
 // `capturing`: the stream is being captured (ours or the caller's), so the
 // timing events must become event-record nodes of the graph.
+// publish: the step reads the host's token and publishes it when done (a
+// host-buffer step whose results are written in place)
 void enqueue_step(contact_ctx* c, bool capturing, const double* pos, const double* quat, const double* vel,
-                  int32_t* pair_ij, double* pair_out, int32_t* n_pairs, double* force, double* torque) {
+                  int32_t* pair_ij, double* pair_out, int32_t* n_pairs, double* force, double* torque,
+                  bool publish = false) {
   const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  Lists W = c->W;
+  W.publish = publish ? 1 : 0;
   // bin counts are zero: contact_init clears them, every step's last kernel clears them again
-  launch_pose(c->P, c->S, c->D, c->W, pos, quat, c->stream);
-  launch_broad(c->P, c->D, c->W, c->stream);
-  launch_plan(c->P, c->S, c->D, c->W, pair_ij, n_pairs, pair_out, c->stream);
+  launch_pose(c->P, c->S, c->D, W, pos, quat, c->stream);
+  launch_broad(c->P, c->D, W, c->stream);
+  launch_plan(c->P, c->S, c->D, W, pair_ij, n_pairs, pair_out, c->stream);
   if (c->cfg.narrow_events) cudaEventRecordWithFlags(c->ev_narrow[0], c->stream, ev_flags);
-  launch_narrow(c->P, c->S, c->D, c->W, vel, pair_out, c->grid_narrow, c->stream);
+  launch_narrow(c->P, c->S, c->D, W, vel, pair_out, c->grid_narrow, c->stream);
   // narrow_events = K > 1: K - 1 more launches of the node sweep, each
   // recomputing the same outputs from the same tiles (the timing's average)
   for (int k = 1; k < c->cfg.narrow_events; ++k)
-    launch_narrow(c->P, c->S, c->D, c->W, vel, pair_out, c->grid_narrow, c->stream);
+    launch_narrow(c->P, c->S, c->D, W, vel, pair_out, c->grid_narrow, c->stream);
   if (c->cfg.narrow_events) cudaEventRecordWithFlags(c->ev_narrow[1], c->stream, ev_flags);
-  if (c->P.box_mode == 0) launch_force(c->P, c->S, c->D, c->W, vel, pair_out, c->stream);
-  launch_particle_sum(c->P, c->D, c->W, force, torque, c->stream);
+  if (c->P.box_mode == 0) launch_force(c->P, c->S, c->D, W, vel, pair_out, c->stream);
+  launch_particle_sum(c->P, c->D, W, force, torque, c->stream);
 }
 
 }  // namespace
@@ -1023,7 +1028,7 @@ contact_status contact_step_host(contact_ctx* c, const double* pos, const double
   auto enqueue_all = [&](bool capturing) {
     if (zero_copy) {
       if (vel != nullptr) cudaMemcpyAsync(c->hs_vel, vel, 6 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
-      enqueue_step(c, capturing, zpos, zquat, dvel, c->hs_pair_ij, c->hs_pair_out, znp, zforce, ztorque);
+      enqueue_step(c, capturing, zpos, zquat, dvel, c->hs_pair_ij, c->hs_pair_out, znp, zforce, ztorque, true);
       return;
     }
     cudaMemcpyAsync(c->hs_pos, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream);

@@ -203,7 +203,7 @@ __global__ void k_pose(Params P, Shapes S, Parts D, Lists W, const double* __res
   pdl_begin();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   // the host's token of this step (mapped host memory: read here, stored at the end)
-  const int token = t == 0 ? *reinterpret_cast<const volatile int*>(W.err_host + 2) : 0;
+  const int token = (t == 0 && W.publish) ? *reinterpret_cast<const volatile int*>(W.err_host + 2) : 0;
   // the step's counters start at zero (the previous step has completed)
   if (t == 0) {
     W.counters[0] = 0;   // pairs (written by the pair builder)
@@ -288,7 +288,7 @@ __global__ void k_pose(Params P, Shapes S, Parts D, Lists W, const double* __res
     if (slot < P.bin_cap) W.bin_items[static_cast<size_t>(bin) * P.bin_cap + slot] = p;
     else set_error(W.err, kErrCapacity);
   }
-  if (t == 0) W.counters[kTokenCounter] = token;
+  if (t == 0 && W.publish) W.counters[kTokenCounter] = token;
 }
 
 // Node box of pair (p, q) with q's image nearest p; returns false if empty.

@@ -55,16 +55,20 @@ __global__ void __launch_bounds__(32) k_particle_sum(Params P, Parts D, Lists W,
                                                       double* __restrict__ torque) {
   pdl_begin();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t == 0) ++W.counters[kStepCounter];   // the contact history written this step is read by the next
+  if (t == 0) {
+    if (!W.publish) *W.err_host = *W.err;
+    ++W.counters[kStepCounter];   // the contact history written this step is read by the next
+  }
   // the cell list's bin counts start the next step at zero
   const int nbins = P.nbin[0] * P.nbin[1] * P.nbin[2];
   for (int b = t; b < nbins; b += gridDim.x * blockDim.x) W.bin_count[b] = 0;
   const int p = t >> 3, c = t & 7;
   if (p < P.n && c < 6) particle_sum(P, W, p, c, force, torque);
-  // the step is complete when every block's sums are stored: the last block
-  // to finish mirrors the error word and then publishes the host's token of
-  // this step (mapped host memory), so a host waiting for the results can
-  // return without a stream synchronisation
+  // a host-buffer step that returns on its token: the step is complete when
+  // every block's sums are stored, and the last block to finish mirrors the
+  // error word and then publishes the host's token of this step (mapped host
+  // memory), so the host can return without a stream synchronisation
+  if (!W.publish) return;
   __syncwarp();
   if ((threadIdx.x & 31) == 0) {
     __threadfence_system();
