@@ -20,6 +20,10 @@ namespace gbc {
 // per-axis offset.  (Kind 2 is not used.)
 enum Kind : int { KIND_SPHERE = 0, KIND_CUBOID = 1, KIND_POLY = 3, KIND_CUBE = 4, KIND_WALL = 5 };
 
+// Half the cell diagonal, sqrt(0.75), in lattice units: the box pipeline's
+// rough-detection threshold (Sec. 3.3.1).
+constexpr float kRoughT = 0.8660254037844386f;
+
 constexpr int kMaxFaces = 32;         // faces of one polytope
 constexpr int kTileItemsPerLane = 4;  // node lines per lane per tile
 constexpr int kPartialFloats = 12;    // FP32 partial sums per tile

@@ -18,7 +18,11 @@
 //      path's estimators, each sample weighing its cell's volume), then the
 //      force law of Eq. (contact_force_normal).
 //
-// One warp per pair, pairs pulled from a queue.  The node tests, the line
+// One warp per pair, pulled from a queue over the pairs the pair builder
+// keeps: pairs whose regions at the rough threshold are apart (separating
+// axes of two boxes, the distance tests of balls) have no rough-contact node
+// and get their zero outputs there, and two boxes' node box is cut to the
+// bounding box of their regions' intersection.  The node tests, the line
 // clipping and the sample sweep run in FP32 relative to the particle centres
 // (offsets formed in FP64); each face's nearest line is re-clipped in FP64,
 // so the corrected box carries no FP32 error; the pair sums, the depth at the
@@ -229,16 +233,20 @@ __global__ void __launch_bounds__(kBoxWarps * 32, 2) k_box_pairs(Params P, Shape
   __shared__ float4 s_pl[kBoxWarps][2][kMaxFaces];
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int np = min(W.counters[0], P.max_pairs);
+  // the pairs the pair builder kept (one entry of the tile list each; the
+  // others are apart at the rough threshold and have their zero outputs)
+  const int ntl = W.counters[1];
+  if (ntl > P.max_tiles) return;   // capacity exceeded: the step reports ECAPACITY
   const int Nc = P.box_res;
-  const float srough = 0.8660254037844386f;   // sqrt(0.75): half the cell diagonal, lattice units
+  const float srough = kRoughT;
   for (;;) {
-    int q = 0;
-    if (lane == 0) q = atomicAdd(&W.counters[2], 1);
-    q = __shfl_sync(kFull, q, 0);
-    if (q >= np) break;
-    const PairRec& r = W.pairs[q];
-    if (!record_in_bounds(P, W.err, r, false)) continue;   // warp-uniform (checked build only)
+    int t = 0;
+    if (lane == 0) t = atomicAdd(&W.counters[2], 1);
+    t = __shfl_sync(kFull, t, 0);
+    if (t >= ntl) break;
+    const PairRec& r = W.tiles[t];
+    if (!record_in_bounds(P, W.err, r, true)) continue;   // warp-uniform (checked build only)
+    const int q = r.pair;
     const int i = r.i, j = r.j;
     const int d0 = r.dim[0], d1 = r.dim[1], d2 = r.dim[2];
     ShapeF A, B;

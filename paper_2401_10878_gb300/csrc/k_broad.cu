@@ -529,19 +529,6 @@ constexpr float kCullMargin = 1e-3f;
 
 __device__ __forceinline__ float dot3(const float* a, const float* b) { return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2])); }
 
-// distance^2 from point c (world, relative to the box centre) to the box
-// with body axes rt rows and half extents e
-__device__ __forceinline__ float box_point_dist2(const float* rt, const float e[3], const float c[3]) {
-  float d2 = 0.f;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const float y = dot3(rt + 3 * k, c);
-    const float o = fmaxf(fabsf(y) - e[k], 0.f);
-    d2 = fmaf(o, o, d2);
-  }
-  return d2;
-}
-
 // The three threshold pairs of the test, from one set of projections: bit 0
 // (T, T), bit 1 (0, T), bit 2 (T, 0) set when the regions are apart.  On an
 // axis the reach of a box's region is R0 + T S (R0 its reach at 0, S the sum
@@ -640,6 +627,75 @@ __device__ unsigned pair_apart(const PairRec& r, float T) {
   return ap.bits;
 }
 
+// The node range of a pair of boxes (cubes, cuboids) where both distances lie
+// below T (the box pipeline's rough-detection threshold).  A node outside
+// {phi_A < T} or {phi_B < T} is no rough-contact node, so the pair's node box
+// shrinks to the bounding box of the intersection of the two boxes grown by T
+// (half extents size + T).  The vertices of that intersection are end points
+// of the edges of either box clipped to the other one, so lane e < 24 clips
+// edge e (A's twelve, then B's) to the other box, grown by kCutSlack more, and
+// the bounds of the end points, widened by kCutSlack, are reduced over the
+// warp.  FP32 in box-relative lattice units: the rounding (~1e-5 cells) stays
+// far inside the slack, so every node with both distances below T is kept.
+// The whole warp calls this with the record in shared memory; false: the
+// intersection is empty.
+constexpr float kCutSlack = 1e-2f;
+
+__device__ __forceinline__ bool cut_box(const PairRec& sr, float T, int nlo[3], int nhi[3]) {
+  const int lane = threadIdx.x & 31;
+  const bool onb = lane >= 12;
+  const int q = onb ? lane - 12 : lane;
+  const int m = min(q >> 2, 2), m1 = m == 2 ? 0 : m + 1, m2 = m1 == 2 ? 0 : m1 + 1;
+  const float s1 = (q & 1) ? 1.f : -1.f, s2 = (q & 2) ? 1.f : -1.f;
+  const float* ro = onb ? sr.rtb : sr.rta;   // the edge's box: body axis k = row k
+  const float* rx = onb ? sr.rta : sr.rtb;   // the other box
+  const float* eo = onb ? sr.szb : sr.sza;
+  const float* ex = onb ? sr.sza : sr.szb;
+  const int* io = onb ? sr.bi : sr.ai;
+  const int* ix = onb ? sr.ai : sr.bi;
+  const float* fo = onb ? sr.bf : sr.af;
+  const float* fx = onb ? sr.af : sr.bf;
+  const float e0 = eo[m] + T, e1 = eo[m1] + T, e2 = eo[m2] + T;
+  // edge p0 + t dv, t in [-1, 1]; rel = p0 minus the other box's centre
+  float p0[3], dv[3], rel[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float co = static_cast<float>(io[c]) + fo[c], cx = static_cast<float>(ix[c]) + fx[c];
+    p0[c] = fmaf(s2 * e2, ro[3 * m2 + c], fmaf(s1 * e1, ro[3 * m1 + c], co));
+    dv[c] = e0 * ro[3 * m + c];
+    rel[c] = p0[c] - cx;
+  }
+  float t0 = -1.f, t1 = 1.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float base = dot3(rx + 3 * k, rel), sl = dot3(rx + 3 * k, dv);
+    const float E = ex[k] + T + kCutSlack;
+    if (fabsf(sl) > 1e-6f) {
+      const float is = __fdividef(1.f, sl);
+      const float a = (-E - base) * is, b = (E - base) * is;
+      t0 = fmaxf(t0, fminf(a, b));
+      t1 = fminf(t1, fmaxf(a, b));
+    } else if (!(fabsf(base) <= E)) {
+      t1 = -2.f;
+    }
+  }
+  const bool ok = lane < 24 && t0 <= t1;
+  bool any = true;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float a = t0 * dv[c], b = t1 * dv[c];
+    const int lo = ok ? static_cast<int>(ceilf(p0[c] + fminf(a, b) - kCutSlack)) : 0x7fffffff;
+    const int hi = ok ? static_cast<int>(floorf(p0[c] + fmaxf(a, b) + kCutSlack)) : -0x7fffffff;
+    nlo[c] = __reduce_min_sync(kFull, lo);
+    nhi[c] = __reduce_max_sync(kFull, hi);
+    any = any && nlo[c] <= nhi[c];
+  }
+  return any;
+}
+
+// BOXM: the box pipeline's variant (its separation test at the rough threshold,
+// the cut node boxes of two boxes, one list entry per kept pair).
+template <bool BOXM>
 __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shapes S, Parts D, Lists W,
                                                                   int32_t* __restrict__ pair_ij,
                                                                   int32_t* __restrict__ n_pairs_out,
@@ -648,6 +704,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
   __shared__ int s_w[kBuildWarps];
   __shared__ int s_base;
   __shared__ unsigned long long s_u64[kBuildWarps][2];
+  __shared__ __align__(16) PairRec s_pr[BOXM ? kBuildWarps : 1];   // a record being cut (cut_box)
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int i0 = blockIdx.x * kBuildWarps + wid;
@@ -689,6 +746,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
     const bool active = r < cnt && (row + r) < P.max_pairs;
     PairRec pr;
     int pi = 0, ntiles = 0;
+    bool skip = false, cut = false;
     unsigned long long vol = 0, ops = 0;
     if (active) {
       pi = row + r;
@@ -724,21 +782,9 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
         pr.lo[k] = lo[k];
         pr.dim[k] = hi[k] - lo[k] + 1;
       }
-      // sweep layout: whole node lines along the box's longest axis (the
-      // fewest lines).  The node sweeps clip every line to the few nodes near
-      // both surfaces, so a line costs about the same whatever its length
-      // (selects, not a runtime index into pr.dim: that would put pr in local memory).
+      // the candidate box's nodes (the cell evaluations and nominal lane-ops
+      // of the step), whatever the node sweep later skips
       const long long volp = static_cast<long long>(pr.dim[0]) * pr.dim[1] * pr.dim[2];
-      const int lines_of[3] = {pr.dim[1] * pr.dim[2], pr.dim[0] * pr.dim[2], pr.dim[0] * pr.dim[1]};
-      {
-        const int a = pr.dim[1] > pr.dim[0] ? (pr.dim[2] > pr.dim[1] ? 2 : 1) : (pr.dim[2] > pr.dim[0] ? 2 : 0);
-        pr.axis = a;
-        pr.nseg = 1;
-        pr.seglen = a == 0 ? pr.dim[0] : (a == 1 ? pr.dim[1] : pr.dim[2]);
-      }
-      pr.nitems = pr.axis == 0 ? lines_of[0] : (pr.axis == 1 ? lines_of[1] : lines_of[2]);
-      ntiles = (pr.nitems + 32 * kTileItemsPerLane - 1) / (32 * kTileItemsPerLane);
-      pr.ntiles = ntiles;
       pr.kinds = W.kind[i] | (W.kind[j] << 8);
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
@@ -769,23 +815,18 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
           pr.bf[k] = 0.f;
         }
       }
-      // the FP32 node sweep skips pairs whose distance regions are apart:
-      // their outputs are written here as the sweep would write them (zeros)
-      const unsigned apart = (P.precision == 0 && P.box_mode == 0) ? pair_apart(pr, 0.5f * P.wdx_l + kClipMargin) : 0u;
-      if (P.smooth ? (apart & 1u) != 0u : (apart & 6u) == 6u) {
-        ntiles = 0;
-        pr.ntiles = 0;
-        double* po = pair_out + static_cast<size_t>(pi) * 11;
-        double* pf = W.ft + static_cast<size_t>(pi) * kFtDoubles;
-        double* pt = W.tape + static_cast<size_t>(pi) * kTapeDoubles;
-#pragma unroll
-        for (int k = 0; k < 11; ++k) po[k] = 0.0;
-#pragma unroll
-        for (int k = 0; k < kFtDoubles; ++k) pf[k] = 0.0;
-#pragma unroll
-        for (int k = 0; k < kTapeDoubles; ++k) pt[k] = 0.0;
-        W.oflag[pi] = 0;
-      }
+      // the FP32 node sweep skips pairs whose distance regions are apart, and
+      // so does the box pipeline (regions at its rough-detection threshold;
+      // a polytope's tabulated radii belong to the node sweep's threshold, so
+      // pairs with one are kept there); the skipped pairs' zero outputs are
+      // written below.  In the box pipeline two boxes' node box is also cut to
+      // their regions' intersection (after the record is complete).
+      const int ka = pr.kinds & 0xff, kb = pr.kinds >> 8;
+      constexpr bool boxm = BOXM;
+      const bool test = (P.precision == 0 && !boxm) || (boxm && ka != KIND_POLY && kb != KIND_POLY);
+      const unsigned apart = test ? pair_apart(pr, boxm ? kRoughT : 0.5f * P.wdx_l + kClipMargin) : 0u;
+      skip = (P.smooth || boxm) ? (apart & 1u) != 0u : (apart & 6u) == 6u;
+      cut = boxm && !skip && (ka == KIND_CUBE || ka == KIND_CUBOID) && (kb == KIND_CUBE || kb == KIND_CUBOID);
       pr.tile = 0;
       pr.pair = pi;
       W.pdone[pi] = 0;
@@ -799,6 +840,69 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build_pairs(Params P, Shap
       for (int u = 0; u < 8; ++u) a0 += (u < dc && dpre[u] < i) ? 1 : 0;
       for (int b = 8; b < dc; ++b) a0 += dl[b] < i ? 1 : 0;
       if (!wall) W.dn_pair[static_cast<size_t>(j) * cap + checked_index(W.err, a0, cap, 0)] = pi;
+    }
+    // the box pipeline's cut node boxes, one pair at a time for the whole
+    // warp (the record passes through shared memory); the box, the centres'
+    // integer parts and nothing else change, so every node keeps its FP32
+    // distances
+    for (unsigned todo = BOXM ? __ballot_sync(kFull, cut) : 0u; todo != 0u; todo &= todo - 1u) {
+      const int src = __ffs(todo) - 1;
+      if (lane == src) store_pair_rec(&s_pr[wid], pr, 0);
+      __syncwarp();
+      int nlo[3], nhi[3];
+      const bool any = cut_box(s_pr[wid], kRoughT, nlo, nhi);
+      if (lane == src) {
+        int a[3], b[3];
+        bool keep = any;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          a[k] = max(nlo[k], 0);
+          b[k] = min(nhi[k], pr.dim[k] - 1);
+          keep = keep && a[k] <= b[k];
+        }
+        if (keep) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            pr.lo[k] += a[k];
+            pr.dim[k] = b[k] - a[k] + 1;
+            pr.ai[k] -= a[k];
+            pr.bi[k] -= a[k];
+          }
+        } else {
+          skip = true;   // no rough-contact node: zero outputs
+        }
+      }
+      __syncwarp();
+    }
+    if (active) {
+      // sweep layout: whole node lines along the box's longest axis (the
+      // fewest lines).  The node sweeps clip every line to the few nodes near
+      // both surfaces, so a line costs about the same whatever its length
+      // (selects, not a runtime index into pr.dim: that would put pr in local memory).
+      const int lines_of[3] = {pr.dim[1] * pr.dim[2], pr.dim[0] * pr.dim[2], pr.dim[0] * pr.dim[1]};
+      {
+        const int a = pr.dim[1] > pr.dim[0] ? (pr.dim[2] > pr.dim[1] ? 2 : 1) : (pr.dim[2] > pr.dim[0] ? 2 : 0);
+        pr.axis = a;
+        pr.nseg = 1;
+        pr.seglen = a == 0 ? pr.dim[0] : (a == 1 ? pr.dim[1] : pr.dim[2]);
+      }
+      pr.nitems = pr.axis == 0 ? lines_of[0] : (pr.axis == 1 ? lines_of[1] : lines_of[2]);
+      // the box pipeline takes each kept pair as one entry of the tile list
+      ntiles = skip ? 0 : (BOXM ? 1 : (pr.nitems + 32 * kTileItemsPerLane - 1) / (32 * kTileItemsPerLane));
+      pr.ntiles = ntiles;
+      // a skipped pair's outputs, as the node sweep or the box pipeline would write them (zeros)
+      if (skip) {
+        double* po = pair_out + static_cast<size_t>(pi) * 11;
+        double* pf = W.ft + static_cast<size_t>(pi) * kFtDoubles;
+        double* pt = W.tape + static_cast<size_t>(pi) * kTapeDoubles;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) po[k] = 0.0;
+#pragma unroll
+        for (int k = 0; k < kFtDoubles; ++k) pf[k] = 0.0;
+#pragma unroll
+        for (int k = 0; k < kTapeDoubles; ++k) pt[k] = 0.0;
+        W.oflag[pi] = 0;
+      }
     }
     // allocations aggregated over the block (one atomic per counter and
     // block, all in flight together): the pairs' tiles, contiguous per pair;
@@ -879,8 +983,8 @@ void launch_broad(const Params& P, const Parts& D, const Lists& W, cudaStream_t 
 void launch_plan(const Params& P, const Shapes& S, const Parts& D, const Lists& W, int32_t* pair_ij, int32_t* n_pairs,
                  double* pair_out, cudaStream_t st) {
   const int nb = (P.n + kBuildWarps - 1) / kBuildWarps;   // one particle row per warp
-  launch_pdl(k_build_pairs, dim3(nb > 0 ? nb : 1), dim3(kBuildWarps * 32), 0, st, P, S, D, W, pair_ij, n_pairs,
-             pair_out);
+  launch_pdl(P.box_mode == 1 ? k_build_pairs<true> : k_build_pairs<false>, dim3(nb > 0 ? nb : 1),
+             dim3(kBuildWarps * 32), 0, st, P, S, D, W, pair_ij, n_pairs, pair_out);
 }
 
 }  // namespace gbc

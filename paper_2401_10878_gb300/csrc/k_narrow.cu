@@ -193,17 +193,11 @@ struct CuboidEval {
 struct CubeEval {
   int iu;
   float fu, tu0, tu1, tu2, h, itu0, itu1, itu2;
+  bool flat;   // a slab parallel to the lines (|tu_k| <= kClipFlat): the general clip
   float cnt_u, p0, p1, p2, y0, y1, y2;
   float gb0, gb1, gb2;
-  __device__ void load(const PairRec& r, bool second, const Shapes&, const Parts&, const Local& L, float4*) {
-    const int* ci = second ? r.bi : r.ai;
-    const float* cf = second ? r.bf : r.af;
-    const float* rt = second ? r.rtb : r.rta;
-    iu = ci[L.u];
-    fu = cf[L.u];
-    h = second ? r.szb[0] : r.sza[0];
-    tu0 = rt[L.u]; tu1 = rt[3 + L.u]; tu2 = rt[6 + L.u];
-    itu0 = clip_inv(tu0); itu1 = clip_inv(tu1); itu2 = clip_inv(tu2);
+  // the geometry comes with the staged constants (prep_clip, then fetch)
+  __device__ void load(const PairRec&, bool, const Shapes&, const Parts&, const Local&, float4*) {
     gb0 = gb1 = gb2 = 0.f;
   }
   __device__ __forceinline__ void begin_line_rec(const PairRec& r, bool second, const Local& L, int cv, int cw,
@@ -227,31 +221,45 @@ struct CubeEval {
     lo = l + o;
     hi = hh + o;
   }
-  // per-tile constants in cs[0 .. 6): (sv_k, hd_0), (sw_k, hd_1),
-  // (hd_2, fu, fv, fw), (iv, iw, iu, flat), (tv_k, 0), (tw_k, 0) with
-  // sv_k = tv_k / tu_k, sw_k = tw_k / tu_k, hd_k = (h + T) / |tu_k|; flat:
-  // a slab parallel to the line (|tu_k| <= kClipFlat), which takes the
-  // general clip
+  // per-tile constants in cs[0 .. 8): (sv_k, hd_0), (sw_k, hd_1),
+  // (hd_2, fu, fv, fw), (iv, iw, iu, -), (tv_k, -), (tw_k, -), (tu_k, h),
+  // (1 / tu_k, -) with sv_k = tv_k / tu_k, sw_k = tw_k / tu_k,
+  // hd_k = (h + T) / |tu_k|.  Lane k < 3 forms axis k's entries, lane 3 the
+  // centre and size; the caller syncs the warp once for both evaluators and
+  // every lane then fetches its registers.
   __device__ __forceinline__ void prep_clip(const PairRec& r, bool second, const Local& L, float T, float4* cs) {
+    const int lane = threadIdx.x & 31;
     const int* ci = second ? r.bi : r.ai;
     const float* cf = second ? r.bf : r.af;
     const float* rt = second ? r.rtb : r.rta;
-    const float ht = h + T;
-    const float4 a = make_float4(rt[L.v] * itu0, rt[3 + L.v] * itu1, rt[6 + L.v] * itu2, ht * fabsf(itu0));
-    const float4 b = make_float4(rt[L.w] * itu0, rt[3 + L.w] * itu1, rt[6 + L.w] * itu2, ht * fabsf(itu1));
-    const float4 c = make_float4(ht * fabsf(itu2), fu, cf[L.v], cf[L.w]);
-    const bool flat = !(fabsf(tu0) > kClipFlat && fabsf(tu1) > kClipFlat && fabsf(tu2) > kClipFlat);
-    const float4 d = make_float4(__int_as_float(ci[L.v]), __int_as_float(ci[L.w]), __int_as_float(iu),
-                                 __int_as_float(flat ? 1 : 0));
-    if ((threadIdx.x & 31) == 0) {
-      cs[0] = a;
-      cs[1] = b;
-      cs[2] = c;
-      cs[3] = d;
-      cs[4] = make_float4(rt[L.v], rt[3 + L.v], rt[6 + L.v], 0.f);
-      cs[5] = make_float4(rt[L.w], rt[3 + L.w], rt[6 + L.w], 0.f);
+    const float hh = second ? r.szb[0] : r.sza[0];
+    const int k = lane < 3 ? lane : 0;
+    const float tu = rt[3 * k + L.u], tv = rt[3 * k + L.v], tw = rt[3 * k + L.w];
+    const float itu = clip_inv(tu);
+    float* f = reinterpret_cast<float*>(cs);
+    if (lane < 3) {
+      f[k] = tv * itu;
+      f[4 + k] = tw * itu;
+      f[k == 0 ? 3 : (k == 1 ? 7 : 8)] = (hh + T) * fabsf(itu);
+      f[16 + k] = tv;
+      f[20 + k] = tw;
+      f[24 + k] = tu;
+      f[28 + k] = itu;
+    } else if (lane == 3) {
+      f[9] = cf[L.u];
+      f[10] = cf[L.v];
+      f[11] = cf[L.w];
+      cs[3] = make_float4(__int_as_float(ci[L.v]), __int_as_float(ci[L.w]), __int_as_float(ci[L.u]), 0.f);
+      f[27] = hh;
     }
-    __syncwarp();
+  }
+  __device__ __forceinline__ void fetch(const float4* cs) {
+    const float4 a = cs[6], b = cs[7], c = cs[2], d = cs[3];
+    tu0 = a.x; tu1 = a.y; tu2 = a.z; h = a.w;
+    itu0 = b.x; itu1 = b.y; itu2 = b.z;
+    fu = c.y;
+    iu = __float_as_int(d.z);
+    flat = !(fabsf(tu0) > kClipFlat && fabsf(tu1) > kClipFlat && fabsf(tu2) > kClipFlat);
   }
   // begin_line_rec from the staged constants (the same operands, the same arithmetic)
   __device__ __forceinline__ void begin_node(const float4* cs, int cv, int cw, int u0) {
@@ -267,7 +275,7 @@ struct CubeEval {
   __device__ __forceinline__ void clip_line(const PairRec& r, bool second, const Local& L, const float4* cs, int cv,
                                             int cw, float T, float& lo, float& hi) {
     const float4 a = cs[0], b = cs[1], c = cs[2], d = cs[3];
-    if (__float_as_int(d.w) != 0) {
+    if (flat) {
       begin_line_rec(r, second, L, cv, cw, 0);
       clip(T, lo, hi);
       return;
@@ -278,8 +286,8 @@ struct CubeEval {
     const float x0 = fmaf(-a.x, rv, fmaf(-b.x, rw, c.y));
     const float x1 = fmaf(-a.y, rv, fmaf(-b.y, rw, c.y));
     const float x2 = fmaf(-a.z, rv, fmaf(-b.z, rw, c.y));
-    lo = fmaxf(lo, fmaxf(fmaxf(x0 - a.w, x1 - b.w), x2 - c.x) + o);
-    hi = fminf(hi, fminf(fminf(x0 + a.w, x1 + b.w), x2 + c.x) + o);
+    lo = fmaxf(lo, max3f(x0 - a.w, x1 - b.w, x2 - c.x) + o);
+    hi = fminf(hi, min3f(x0 + a.w, x1 + b.w, x2 + c.x) + o);
   }
   __device__ __forceinline__ float phi() {
     cnt_u += 1.f;
@@ -475,6 +483,13 @@ __device__ __forceinline__ auto prep_clip_of(E& e, const PairRec& r, bool second
 }
 template <class E>
 __device__ __forceinline__ void prep_clip_of(E&, const PairRec&, bool, const Local&, float, float4*, long) {}
+// Registers from the staged constants (after the warp's sync), where the evaluator keeps them there.
+template <class E>
+__device__ __forceinline__ auto fetch_of(E& e, const float4* cs, int) -> decltype(e.fetch(cs)) {
+  e.fetch(cs);
+}
+template <class E>
+__device__ __forceinline__ void fetch_of(E&, const float4*, long) {}
 template <class E>
 __device__ __forceinline__ auto clip_line_of(E& e, const PairRec& r, bool second, const Local& L, const float4* cs,
                                              int cv, int cw, float T, float& lo, float& hi, int)
@@ -544,6 +559,9 @@ __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, 
   // unused) plane buffer
   prep_clip_of(A, r, swap, L, T, smA, 0);
   prep_clip_of(B, r, !swap, L, T, smB, 0);
+  __syncwarp();
+  fetch_of(A, smA, 0);
+  fetch_of(B, smB, 0);
   const float4* csA = smA;
   const float4* csB = smB;
   float cnt = 0.f, mu = 0.f, mv = 0.f, mw = 0.f, bestf = -FLT_MAX;
@@ -925,22 +943,31 @@ __device__ __forceinline__ void store_rec_part(PairRec* dst, int lane, int4 v) {
 // Blocks per SM: 3 for the sphere/cuboid/cube variants (<= 85 registers, so
 // 24 warps per SM: about one tile per warp at a settling box's size), 2 for
 // the variant with every kind (measured faster than 3, which spills more).
+// Warps per block and blocks per SM of the node sweep (compiled per kind set).
+constexpr int kNarrowWarps = 8, kNarrowBlocks = 3;
+template <int SET>
+__host__ __device__ constexpr int narrow_warps() { return SET == SET_ALL ? 8 : kNarrowWarps; }
+template <int SET>
+__host__ __device__ constexpr int narrow_blocks() { return SET == SET_ALL ? 2 : kNarrowBlocks; }
+
 template <bool SMOOTH, int SET>
-__global__ void __launch_bounds__(kWarps * 32, SET == 0 ? 2 : 3) k_narrow32(Params P, Shapes S, Parts D,
-                                                                                  Lists W, const double* vel,
-                                                                                  double* pair_out) {
-  __shared__ __align__(16) PairRec s_rec[kWarps][2];
+__global__ void __launch_bounds__(narrow_warps<SET>() * 32, narrow_blocks<SET>()) k_narrow32(Params P, Shapes S,
+                                                                                             Parts D, Lists W,
+                                                                                             const double* vel,
+                                                                                             double* pair_out) {
+  constexpr int NW = narrow_warps<SET>();
+  __shared__ __align__(16) PairRec s_rec[NW][2];
   // per evaluator: a polytope's planes, then its line clip's constants (a cube: the clip constants)
-  __shared__ float4 s_planes[kWarps][2][SET == SET_CUBE ? 8 : 2 * kMaxFaces];
-  __shared__ unsigned s_pk[SET == SET_ALL ? kWarps : 1][kTileItemsPerLane * 32];   // clipped ranges (rolled sweep)
-  __shared__ int4 s_own[kWarps][64];   // the lanes with clipped nodes (sweep_tile)
+  __shared__ float4 s_planes[NW][2][SET == SET_CUBE ? 8 : 2 * kMaxFaces];
+  __shared__ unsigned s_pk[SET == SET_ALL ? NW : 1][kTileItemsPerLane * 32];   // clipped ranges (rolled sweep)
+  __shared__ int4 s_own[NW][64];   // the lanes with clipped nodes (sweep_tile)
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int ntiles = W.counters[1];
   // tiles w, w + W, ... of the list (W warps); the first record is fetched
   // with the tile count, the next one while a tile runs
-  const int nwarps = gridDim.x * kWarps;
-  int t = blockIdx.x * kWarps + wid;
+  const int nwarps = gridDim.x * NW;
+  int t = blockIdx.x * NW + wid;
   const int4 first = t < P.max_tiles ? load_rec_part(W.tiles + t, lane) : make_int4(0, 0, 0, 0);
   if (ntiles > P.max_tiles) return;   // capacity exceeded: the step reports ECAPACITY
   if (t < ntiles) store_rec_part(&s_rec[wid][0], lane, first);
@@ -1114,7 +1141,7 @@ __global__ void __launch_bounds__(256) k_narrow64(Params P, Shapes S, Parts D, L
 template <bool SMOOTH, int SET>
 int blocks_per_sm() {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_narrow32<SMOOTH, SET>, kWarps * 32, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_narrow32<SMOOTH, SET>, narrow_warps<SET>() * 32, 0);
   return per_sm > 0 ? per_sm : 1;
 }
 
@@ -1160,15 +1187,15 @@ void launch_narrow(const Params& P, const Shapes& S, const Parts& D, const Lists
       launch_pdl(k_narrow64<false>, dim3(grid), dim3(256), 0, st, P, S, D, W, vel, pair_out);
     return;
   }
-  const int b = kWarps * 32;
+  const dim3 bc(narrow_warps<SET_CUBE>() * 32), bs(narrow_warps<SET_SC>() * 32), ba(narrow_warps<SET_ALL>() * 32);
   if (P.smooth) {
-    if (P.kind_set == SET_CUBE) launch_pdl(k_narrow32<true, SET_CUBE>, dim3(grid), dim3(b), 0, st, P, S, D, W, vel, pair_out);
-    else if (P.kind_set == SET_SC) launch_pdl(k_narrow32<true, SET_SC>, dim3(grid), dim3(b), 0, st, P, S, D, W, vel, pair_out);
-    else launch_pdl(k_narrow32<true, SET_ALL>, dim3(grid), dim3(b), 0, st, P, S, D, W, vel, pair_out);
+    if (P.kind_set == SET_CUBE) launch_pdl(k_narrow32<true, SET_CUBE>, dim3(grid), bc, 0, st, P, S, D, W, vel, pair_out);
+    else if (P.kind_set == SET_SC) launch_pdl(k_narrow32<true, SET_SC>, dim3(grid), bs, 0, st, P, S, D, W, vel, pair_out);
+    else launch_pdl(k_narrow32<true, SET_ALL>, dim3(grid), ba, 0, st, P, S, D, W, vel, pair_out);
   } else {
-    if (P.kind_set == SET_CUBE) launch_pdl(k_narrow32<false, SET_CUBE>, dim3(grid), dim3(b), 0, st, P, S, D, W, vel, pair_out);
-    else if (P.kind_set == SET_SC) launch_pdl(k_narrow32<false, SET_SC>, dim3(grid), dim3(b), 0, st, P, S, D, W, vel, pair_out);
-    else launch_pdl(k_narrow32<false, SET_ALL>, dim3(grid), dim3(b), 0, st, P, S, D, W, vel, pair_out);
+    if (P.kind_set == SET_CUBE) launch_pdl(k_narrow32<false, SET_CUBE>, dim3(grid), bc, 0, st, P, S, D, W, vel, pair_out);
+    else if (P.kind_set == SET_SC) launch_pdl(k_narrow32<false, SET_SC>, dim3(grid), bs, 0, st, P, S, D, W, vel, pair_out);
+    else launch_pdl(k_narrow32<false, SET_ALL>, dim3(grid), ba, 0, st, P, S, D, W, vel, pair_out);
   }
 }
 

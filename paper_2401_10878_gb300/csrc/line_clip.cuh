@@ -33,6 +33,19 @@ constexpr float kClipEmpty = 3.0e38f;    // a lower bound that empties the inter
 // 1 / a for the clip (0 for faces parallel to the line: they take the constant
 // branch); the approximate reciprocal's relative error (~2^-22) moves a bound
 // by far less than the margin.
+// Three-operand maximum and minimum (one instruction each on this GPU; like
+// fmaxf / fminf, a NaN operand gives way to the others).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 __device__ __forceinline__ float clip_inv(float a) { return fabsf(a) > kClipFlat ? __fdividef(1.f, a) : 0.f; }
 
 // |t c + p| < T: c in ((-T - p) / t, (T - p) / t), ordered by the sign of t.
