@@ -483,60 +483,68 @@ __global__ void __launch_bounds__(kBoxWarps * 32, 2) k_box_pairs(Params P, Shape
       zero_pair(W, pair_out, q);
       continue;
     }
-    // 4. FP64 pair results and the force law (lane 0)
-    if (lane == 0) {
+    // 4. FP64 pair results and the force law: component k of every vector on
+    // lane k < 3 (cross and dot products by shuffles; every FP64 warp
+    // instruction costs the same however few lanes it has), the distances of
+    // A and B at the deepest sample on lanes 0 and 1; the scalars on every lane
+    {
+      const int kc = lane < 3 ? lane : 0;
+      const int k1 = kc == 2 ? 0 : kc + 1, k2 = k1 == 2 ? 0 : k1 + 1;
+      auto at = [&](double v, int c) { return __shfl_sync(kFull, v, c); };
       const double dV = step[0] * step[1] * step[2];
       const double V = dV * cnt;
-      double xc[3], G[3], nv[3];
-      const double Mx[3] = {m0, m1, m2}, Gs[3] = {g0, g1, g2};
       const double gscale = 0.5 * dV * 6.0 / P.wdx;
       const double inv_cnt = 1.0 / static_cast<double>(cnt);
-      for (int k = 0; k < 3; ++k) {
-        xc[k] = lo1[k] + (Mx[k] * inv_cnt + 0.5) * step[k];
-        G[k] = gscale * Gs[k];
-      }
-      const double gn = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
+      const double stk = sel(step, kc), lok = sel(lo1, kc), xak = sel(XA, kc), xbk = sel(XB, kc);
+      const double Mk = kc == 0 ? m0 : (kc == 1 ? m1 : m2);
+      const double Gsk = kc == 0 ? g0 : (kc == 1 ? g1 : g2);
+      const double xck = lok + (Mk * inv_cnt + 0.5) * stk;
+      const double Gk = gscale * Gsk;
+      const double G0 = at(Gk, 0), G1 = at(Gk, 1), G2 = at(Gk, 2);
+      const double gn = sqrt(G0 * G0 + G1 * G1 + G2 * G2);
+      const double ddk = xbk - xak;
+      const double dd0 = at(ddk, 0), dd1 = at(ddk, 1), dd2 = at(ddk, 2);
+      double nk;
       if (gn > 1e-12 * P.dx * P.dx) {
         const double ig = 1.0 / gn;
-        for (int k = 0; k < 3; ++k) nv[k] = G[k] * ig;
+        nk = Gk * ig;
       } else if (j >= P.n) {
-        const double* e = S.planes + 4 * S.face_off[j];
-        for (int k = 0; k < 3; ++k) nv[k] = -e[k];
+        nk = -S.planes[4 * S.face_off[j] + kc];
       } else {
-        const double dd[3] = {XB[0] - XA[0], XB[1] - XA[1], XB[2] - XA[2]};
-        const double dn = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-        for (int k = 0; k < 3; ++k) nv[k] = dn > 0.0 ? dd[k] / dn : 0.0;
+        const double dn = sqrt(dd0 * dd0 + dd1 * dd1 + dd2 * dd2);
+        nk = dn > 0.0 ? ddk / dn : 0.0;
       }
-      // depth at the deepest sample, FP64
+      // depth at the deepest sample, FP64: A's distance on lane 0, B's on lane 1
       const int bi = min(max(bestidx, 0), ns - 1);
       const int bx = bi % Nc, by = (bi / Nc) % Nc, bz = bi / (Nc * Nc);
       const double xs[3] = {lo1[0] + (bx + 0.5) * step[0], lo1[1] + (by + 0.5) * step[1],
                             lo1[2] + (bz + 0.5) * step[2]};
-      double gA[3], gB[3];
-      const int fa0 = S.face_off[i], fb0 = S.face_off[j];
-      const double pa = sdf64(S.type[i], S.param + 3 * i, S.planes + 4 * fa0, S.face_off[i + 1] - fa0, XA,
-                              D.R + 9 * i, xs, P.inflate, gA);
-      const double pb = sdf64(S.type[j], S.param + 3 * j, S.planes + 4 * fb0, S.face_off[j + 1] - fb0, XB,
-                              D.R + 9 * j, xs, P.inflate, gB);
+      double pv = 0.0;
+      if (lane < 2) {
+        const bool sb = lane == 1;
+        const int pid = sb ? j : i;
+        const double Xp[3] = {sb ? XB[0] : XA[0], sb ? XB[1] : XA[1], sb ? XB[2] : XA[2]};
+        const int f0 = S.face_off[pid];
+        double gdummy[3];
+        pv = sdf64(S.type[pid], S.param + 3 * pid, S.planes + 4 * f0, S.face_off[pid + 1] - f0, Xp, D.R + 9 * pid,
+                   xs, P.inflate, gdummy);
+      }
+      const double pa = at(pv, 0), pb = at(pv, 1);
       const double d = fmax(0.0, -(pa + pb));
       const double estar = 1.0 / (S.compl_[i] + S.compl_[j]);
       double damp = 1.0;
-      double ra[3], rb[3];
-      for (int k = 0; k < 3; ++k) {
-        ra[k] = xc[k] - XA[k];
-        rb[k] = xc[k] - XB[k];
-      }
+      const double rak = xck - xak, rbk = xck - xbk;
+      const double n0 = at(nk, 0), n1 = at(nk, 1), n2 = at(nk, 2);
       // u_AB = (v_A + w_A x r_A) - (v_B + w_B x r_B) at x_c, ddot_n = u_AB . n
-      double uab[3] = {0.0, 0.0, 0.0}, ddot = 0.0;
+      double uabk = 0.0, ddot = 0.0;
       if (vel != nullptr && (P.damping_c != 0.0 || P.history || P.friction)) {
         const double* va = vel + 6 * i;
         const double* vb = j < P.n ? vel + 6 * j : D.rest6;
-        const double ua[3] = {va[0] + (va[4] * ra[2] - va[5] * ra[1]), va[1] + (va[5] * ra[0] - va[3] * ra[2]),
-                              va[2] + (va[3] * ra[1] - va[4] * ra[0])};
-        const double ub[3] = {vb[0] + (vb[4] * rb[2] - vb[5] * rb[1]), vb[1] + (vb[5] * rb[0] - vb[3] * rb[2]),
-                              vb[2] + (vb[3] * rb[1] - vb[4] * rb[0])};
-        for (int k = 0; k < 3; ++k) uab[k] = ua[k] - ub[k];
-        ddot = uab[0] * nv[0] + uab[1] * nv[1] + uab[2] * nv[2];
+        const double ra1 = at(rak, k1), ra2 = at(rak, k2), rb1 = at(rbk, k1), rb2 = at(rbk, k2);
+        const double uak = va[kc] + (va[3 + k1] * ra2 - va[3 + k2] * ra1);
+        const double ubk = vb[kc] + (vb[3 + k1] * rb2 - vb[3 + k2] * rb1);
+        uabk = uak - ubk;
+        ddot = at(uabk, 0) * n0 + at(uabk, 1) * n1 + at(uabk, 2) * n2;
       }
       // c: the shared one, or with the history the contact's own (a new
       // contact's from u0 = ddot_n, Eq. damping_factor; 0 for u0 <= 0)
@@ -545,12 +553,12 @@ __global__ void __launch_bounds__(kBoxWarps * 32, 2) k_box_pairs(Params P, Shape
       if (vel != nullptr && cdamp != 0.0) damp = fmax(0.0, 1.0 + cdamp * ddot);
       const double vd = V * d;
       const double fmag = vd > 0.0 ? (4.0 / (3.0 * 3.14159265358979323846)) * estar * sqrt(vd) * damp : 0.0;
-      double F[3], TA[3], TB[3];
-      for (int k = 0; k < 3; ++k) F[k] = fmag * nv[k];
+      double Fk = fmag * nk;
       if (P.friction && vel != nullptr && fmag > 0.0) {
         // Eq. (contact_force_tangential): B receives +f(a) |F_n| t, t = u_t / |u_t|
-        const double ut[3] = {uab[0] - ddot * nv[0], uab[1] - ddot * nv[1], uab[2] - ddot * nv[2]};
-        const double utn = sqrt(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
+        const double utk = uabk - ddot * nk;
+        const double u0 = at(utk, 0), u1 = at(utk, 1), u2 = at(utk, 2);
+        const double utn = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
         if (utn > 0.0) {
           const double a = utn * P.inv_u_k, a2 = a * a;
           double coef = P.mu_k;
@@ -558,36 +566,38 @@ __global__ void __launch_bounds__(kBoxWarps * 32, 2) k_box_pairs(Params P, Shape
             const double den1 = a2 * a2 + 1.0, den2 = a2 + 1.0;
             coef = a2 * ((2.0 * P.mu_s_star - P.mu_k) * den2 + P.mu_k * den1) / (den1 * den2);
           }
-          for (int k = 0; k < 3; ++k) F[k] += coef * fmag * ut[k] / utn;
+          Fk += coef * fmag * utk / utn;
         }
       }
-      TA[0] = -(ra[1] * F[2] - ra[2] * F[1]);
-      TA[1] = -(ra[2] * F[0] - ra[0] * F[2]);
-      TA[2] = -(ra[0] * F[1] - ra[1] * F[0]);
-      TB[0] = rb[1] * F[2] - rb[2] * F[1];
-      TB[1] = rb[2] * F[0] - rb[0] * F[2];
-      TB[2] = rb[0] * F[1] - rb[1] * F[0];
+      const double F1 = at(Fk, k1), F2 = at(Fk, k2);
+      const double TAk = -(at(rak, k1) * F2 - at(rak, k2) * F1);
+      const double TBk = at(rbk, k1) * F2 - at(rbk, k2) * F1;
       double* o = pair_out + static_cast<size_t>(q) * 11;
       double* ft = W.ft + static_cast<size_t>(q) * kFtDoubles;
-      o[0] = V;
-      for (int k = 0; k < 3; ++k) {
-        o[1 + k] = xc[k]; o[4 + k] = nv[k]; o[8 + k] = F[k];
-        ft[k] = F[k]; ft[3 + k] = TA[k]; ft[6 + k] = TB[k];
+      if (lane < 3) {
+        o[1 + lane] = xck; o[4 + lane] = nk; o[8 + lane] = Fk;
+        ft[lane] = Fk; ft[3 + lane] = TAk; ft[6 + lane] = TBk;
       }
-      o[7] = d;
-      double* tp = W.tape + static_cast<size_t>(q) * kTapeDoubles;
-      for (int k = 0; k < kTapeDoubles; ++k) tp[k] = 0.0;
-      atomicAdd(&W.counters[5], 1);
+      if (lane == 0) {
+        o[0] = V;
+        o[7] = d;
+        atomicAdd(&W.counters[5], 1);
+      }
+      if (lane < kTapeDoubles) W.tape[static_cast<size_t>(q) * kTapeDoubles + lane] = 0.0;
       if (P.history) {   // this step's contact: j, c and the corrected box minus X_i
         const int wr = (W.counters[kStepCounter] & 1) ^ 1;
-        const int slot = atomicAdd(W.hist_n + static_cast<size_t>(wr) * P.n + i, 1);
+        int slot = 0;
+        if (lane == 0) slot = atomicAdd(W.hist_n + static_cast<size_t>(wr) * P.n + i, 1);
+        slot = __shfl_sync(kFull, slot, 0);
         if (slot < P.max_nbr) {
           const size_t e = (static_cast<size_t>(wr) * P.n + i) * P.max_nbr + slot;
-          W.hist_j[e] = j;
-          W.hist_c[e] = cdamp;
-          for (int k = 0; k < 3; ++k) {
-            W.hist_box[6 * e + k] = __dsub_rn(lo1[k], XA[k]);
-            W.hist_box[6 * e + 3 + k] = __dsub_rn(hi1[k], XA[k]);
+          if (lane == 0) {
+            W.hist_j[e] = j;
+            W.hist_c[e] = cdamp;
+          }
+          if (lane < 3) {
+            W.hist_box[6 * e + lane] = __dsub_rn(lok, xak);
+            W.hist_box[6 * e + 3 + lane] = __dsub_rn(sel(hi1, kc), xak);
           }
         }
       }
