@@ -36,7 +36,14 @@ namespace gbc {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kWarps = 8;
+// Warps per block and blocks per SM of the cell sweep, per kind set: the
+// cubes-only and sphere/cuboid variants at three blocks (a warp per tile at a
+// settling box's size, a few spilled registers: 16.0 -> 15.0 us on the 1934
+// cubes), the variant with every kind at two (three spill too much there:
+// 23.5 -> 28.5 us on the mixed box).
+constexpr int kAdjWarps = 8;
+template <int SET>
+__host__ __device__ constexpr int adj_blocks() { return SET == 0 ? 2 : 3; }
 constexpr int kAdjPartial = 12;
 constexpr int kSeedFloats = 8;
 constexpr int kPairGrad = 16;
@@ -629,11 +636,12 @@ __device__ __forceinline__ float adj_warp_sum12(const float acc[12]) {
 }
 
 template <int SET>
-__global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, Parts D, Lists W, AdjBufs B) {
-  __shared__ float4 s_pl[kWarps][2][kMaxFaces + kMaxFaces / 4];   // planes, then their inverse slopes
-  __shared__ __align__(16) PairRec s_rec[kWarps][2];
-  __shared__ unsigned s_pk[SET == 0 ? kWarps : 1][kTileItemsPerLane * 32];   // clipped ranges (rolled sweep)
-  __shared__ int4 s_own[kWarps][64];   // the lanes with clipped nodes of the current tile
+__global__ void __launch_bounds__(kAdjWarps * 32, adj_blocks<SET>()) k_adj_cells(Params P, Shapes S, Parts D,
+                                                                               Lists W, AdjBufs B) {
+  __shared__ float4 s_pl[kAdjWarps][2][kMaxFaces + kMaxFaces / 4];   // planes, then their inverse slopes
+  __shared__ __align__(16) PairRec s_rec[kAdjWarps][2];
+  __shared__ unsigned s_pk[SET == 0 ? kAdjWarps : 1][kTileItemsPerLane * 32];   // clipped ranges (rolled sweep)
+  __shared__ int4 s_own[kAdjWarps][64];   // the lanes with clipped nodes of the current tile
   constexpr bool ROLL = SET == 0;   // every kind: rolled slot loops (code size)
   pdl_begin();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -643,8 +651,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_adj_cells(Params P, Shapes S, P
   // tiles w, w + W, ... of the forward's list (W warps): each record is staged
   // in shared memory, the next record and its pair's seeds are fetched while
   // a tile runs
-  const int nwarps = gridDim.x * kWarps;
-  int qpos = blockIdx.x * kWarps + wid;
+  const int nwarps = gridDim.x * kAdjWarps;
+  int qpos = blockIdx.x * kAdjWarps + wid;
   float seed = 0.f;
   if (qpos < ntiles) {
     const int4 v = adj_rec_part(W.tiles + qpos, lane);
@@ -961,11 +969,11 @@ void launch_adjoint(const Params& P, const Shapes& S, const Parts& D, const List
   // compiled per kind set, as the node sweep (2 cubes only, 1 spheres / cuboids / walls, 0 every kind)
   auto cells = P.kind_set == 2 ? k_adj_cells<2> : (P.kind_set == 1 ? k_adj_cells<1> : k_adj_cells<0>);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cells, kWarps * 32, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cells, kAdjWarps * 32, 0);
   const int cgrid = (per_sm > 0 ? per_sm : 1) * sms;   // persistent: every resident slot pulls tiles
   (void)grid;
   if (ev0 != nullptr) cudaEventRecord(ev0, st);
-  launch_pdl(cells, dim3(cgrid), dim3(kWarps * 32), 0, st, P, S, D, W, B);
+  launch_pdl(cells, dim3(cgrid), dim3(kAdjWarps * 32), 0, st, P, S, D, W, B);
   if (ev1 != nullptr) cudaEventRecord(ev1, st);
   launch_pdl(k_adj_scatter, dim3((8 * P.n + 31) / 32), dim3(32), 0, st, P, D, W, B, gpos, gquat);
 }
