@@ -20,6 +20,15 @@ namespace gbc {
 // per-axis offset.  (Kind 2 is not used.)
 enum Kind : int { KIND_SPHERE = 0, KIND_CUBOID = 1, KIND_POLY = 3, KIND_CUBE = 4, KIND_WALL = 5 };
 
+// Evaluator order of a pair in the node sweep: the cheaper kind is A (wall <
+// sphere < cube < cuboid < polytope; kind 2 is unused); true when the
+// record's particle j is A.
+__device__ __forceinline__ bool sweep_swap(int ka, int kb) {
+  // ranks 1, 3, 6, 5, 2, 0 of kinds 0 .. 5 in nibbles (an indexed array would live in local memory)
+  constexpr unsigned kRank = 0x025631u;
+  return ((kRank >> (4 * ka)) & 15u) > ((kRank >> (4 * kb)) & 15u);
+}
+
 // Half the cell diagonal, sqrt(0.75), in lattice units: the box pipeline's
 // rough-detection threshold (Sec. 3.3.1).
 constexpr float kRoughT = 0.8660254037844386f;

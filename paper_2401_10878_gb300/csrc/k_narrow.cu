@@ -878,10 +878,8 @@ enum KindSet : int { SET_ALL = 0, SET_SC = 1, SET_CUBE = 2 };
 template <bool SMOOTH, int SET>
 __device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, const Parts& D, const PairRec& r,
                                             int tl, float4* smA, float4* smB, unsigned* spk, int4* own) {
-  // kind order for canonical pairs: wall < sphere < cube < cuboid < polytope (kind 2 unused)
-  constexpr int rank[6] = {1, 3, 6, 5, 2, 0};
   int ka = r.kinds & 0xff, kb = r.kinds >> 8;
-  const bool swap = rank[ka] > rank[kb];   // evaluate the cheaper kind as A; G's sign flips back below
+  const bool swap = sweep_swap(ka, kb);   // evaluate the cheaper kind as A; G's sign flips back below
   if (swap) {
     const int t = ka; ka = kb; kb = t;
   }
