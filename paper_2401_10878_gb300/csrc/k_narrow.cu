@@ -31,6 +31,7 @@
 //     last tile sums them in FP64 in tile order (deterministic).
 // k_narrow64: all-FP64 comparison form, one thread block per pair.
 #include <cfloat>
+#include <type_traits>
 
 #include "contact_dev.cuh"
 #include "force_law.cuh"
@@ -222,22 +223,29 @@ struct CubeEval {
     hi = hh + o;
   }
   // per-tile constants in cs[0 .. 8): (sv_k, hd_0), (sw_k, hd_1),
-  // (hd_2, fu, fv, fw), (iv, iw, iu, -), (tv_k, -), (tw_k, -), (tu_k, h),
-  // (1 / tu_k, -) with sv_k = tv_k / tu_k, sw_k = tw_k / tu_k,
-  // hd_k = (h + T) / |tu_k|.  Lane k < 3 forms axis k's entries, lane 3 the
-  // centre and size; the caller syncs the warp once for both evaluators and
-  // every lane then fetches its registers.
+  // (hd_2, iv + fv, iw + fw, fu + iu), (iv, iw, iu, fu), (tv_k, fv),
+  // (tw_k, fw), (tu_k, h), (1 / tu_k, -) with sv_k = tv_k / tu_k,
+  // sw_k = tw_k / tu_k, hd_k = (h + T) / |tu_k| (the line clip reads the
+  // first three, the node start the next three).  Lane k < 3 forms axis k's entries, lane 3 the
+  // centre and size (two cubes: lanes 4 .. 7 form B's in the same pass); the
+  // caller syncs the warp once for both evaluators and every lane then
+  // fetches its registers.
   __device__ __forceinline__ void prep_clip(const PairRec& r, bool second, const Local& L, float T, float4* cs) {
-    const int lane = threadIdx.x & 31;
+    prep_lanes(r, second, L, T, cs, threadIdx.x & 31);
+  }
+  // the stores of lane q of the group that forms the constants (q < 3: axis
+  // q's entries, q = 3: the centre and size, q > 3: none)
+  static __device__ __forceinline__ void prep_lanes(const PairRec& r, bool second, const Local& L, float T,
+                                                    float4* cs, int q) {
     const int* ci = second ? r.bi : r.ai;
     const float* cf = second ? r.bf : r.af;
     const float* rt = second ? r.rtb : r.rta;
     const float hh = second ? r.szb[0] : r.sza[0];
-    const int k = lane < 3 ? lane : 0;
+    const int k = q < 3 ? q : 0;
     const float tu = rt[3 * k + L.u], tv = rt[3 * k + L.v], tw = rt[3 * k + L.w];
     const float itu = clip_inv(tu);
     float* f = reinterpret_cast<float*>(cs);
-    if (lane < 3) {
+    if (q < 3) {
       f[k] = tv * itu;
       f[4 + k] = tw * itu;
       f[k == 0 ? 3 : (k == 1 ? 7 : 8)] = (hh + T) * fabsf(itu);
@@ -245,27 +253,31 @@ struct CubeEval {
       f[20 + k] = tw;
       f[24 + k] = tu;
       f[28 + k] = itu;
-    } else if (lane == 3) {
-      f[9] = cf[L.u];
-      f[10] = cf[L.v];
-      f[11] = cf[L.w];
-      cs[3] = make_float4(__int_as_float(ci[L.v]), __int_as_float(ci[L.w]), __int_as_float(ci[L.u]), 0.f);
+    } else if (q == 3) {
+      const int iu = ci[L.u], iv = ci[L.v], iw = ci[L.w];
+      const float fu = cf[L.u], fv = cf[L.v], fw = cf[L.w];
+      f[9] = static_cast<float>(iv) + fv;
+      f[10] = static_cast<float>(iw) + fw;
+      f[11] = fu + static_cast<float>(iu);
+      cs[3] = make_float4(__int_as_float(iv), __int_as_float(iw), __int_as_float(iu), fu);
+      f[19] = fv;
+      f[23] = fw;
       f[27] = hh;
     }
   }
   __device__ __forceinline__ void fetch(const float4* cs) {
-    const float4 a = cs[6], b = cs[7], c = cs[2], d = cs[3];
+    const float4 a = cs[6], b = cs[7], d = cs[3];
     tu0 = a.x; tu1 = a.y; tu2 = a.z; h = a.w;
     itu0 = b.x; itu1 = b.y; itu2 = b.z;
-    fu = c.y;
+    fu = d.w;
     iu = __float_as_int(d.z);
     flat = !(fabsf(tu0) > kClipFlat && fabsf(tu1) > kClipFlat && fabsf(tu2) > kClipFlat);
   }
   // begin_line_rec from the staged constants (the same operands, the same arithmetic)
   __device__ __forceinline__ void begin_node(const float4* cs, int cv, int cw, int u0) {
-    const float4 c = cs[2], d = cs[3], tv = cs[4], tw = cs[5];
-    const float rv = static_cast<float>(cv - __float_as_int(d.x)) - c.z;
-    const float rw = static_cast<float>(cw - __float_as_int(d.y)) - c.w;
+    const float4 d = cs[3], tv = cs[4], tw = cs[5];
+    const float rv = static_cast<float>(cv - __float_as_int(d.x)) - tv.w;
+    const float rw = static_cast<float>(cw - __float_as_int(d.y)) - tw.w;
     p0 = fmaf(-tu0, fu, fmaf(tv.x, rv, tw.x * rw));
     p1 = fmaf(-tu1, fu, fmaf(tv.y, rv, tw.y * rw));
     p2 = fmaf(-tu2, fu, fmaf(tv.z, rv, tw.z * rw));
@@ -274,20 +286,21 @@ struct CubeEval {
   // [lo, hi] cut to the nodes of line (cv, cw) inside all three slabs
   __device__ __forceinline__ void clip_line(const PairRec& r, bool second, const Local& L, const float4* cs, int cv,
                                             int cw, float T, float& lo, float& hi) {
-    const float4 a = cs[0], b = cs[1], c = cs[2], d = cs[3];
+    const float4 a = cs[0], b = cs[1], c = cs[2];
     if (flat) {
       begin_line_rec(r, second, L, cv, cw, 0);
       clip(T, lo, hi);
       return;
     }
-    const float rv = static_cast<float>(cv - __float_as_int(d.x)) - c.z;
-    const float rw = static_cast<float>(cw - __float_as_int(d.y)) - c.w;
-    const float o = static_cast<float>(__float_as_int(d.z));
-    const float x0 = fmaf(-a.x, rv, fmaf(-b.x, rw, c.y));
-    const float x1 = fmaf(-a.y, rv, fmaf(-b.y, rw, c.y));
-    const float x2 = fmaf(-a.z, rv, fmaf(-b.z, rw, c.y));
-    lo = fmaxf(lo, max3f(x0 - a.w, x1 - b.w, x2 - c.x) + o);
-    hi = fminf(hi, min3f(x0 + a.w, x1 + b.w, x2 + c.x) + o);
+    // in box nodes: the centre's offsets (iv + fv, iw + fw) and fu + iu formed
+    // once per tile (their rounding, ~1e-5 cells, stays far inside the margin)
+    const float rv = static_cast<float>(cv) - c.y;
+    const float rw = static_cast<float>(cw) - c.z;
+    const float x0 = fmaf(-a.x, rv, fmaf(-b.x, rw, c.w));
+    const float x1 = fmaf(-a.y, rv, fmaf(-b.y, rw, c.w));
+    const float x2 = fmaf(-a.z, rv, fmaf(-b.z, rw, c.w));
+    lo = fmaxf(lo, max3f(x0 - a.w, x1 - b.w, x2 - c.x));
+    hi = fminf(hi, min3f(x0 + a.w, x1 + b.w, x2 + c.x));
   }
   __device__ __forceinline__ float phi() {
     cnt_u += 1.f;
@@ -535,8 +548,8 @@ __device__ __forceinline__ float key_float(int k) { return __int_as_float(k >= 0
 // clip margin) and keeps each clipped range's first node and count.  (B) The
 // tile's clipped nodes, typically a few dozen spread over a few lines, are
 // numbered lane by lane (a scan of the lanes' counts), each lane's in slot
-// order, and each lane evaluates one of them: the owning lane by a binary
-// search over the scan, the slot by the owner's counts, and the evaluators
+// order, and each lane evaluates one of them: the owning lane from a table
+// of the lanes with nodes, the slot by the owner's counts, and the evaluators
 // start that node's line at the node itself, so the node gets exactly the
 // arithmetic of a node walk (the same FP32 distances, bit for bit).
 // ROLL (the kernel with every kind, nine kind pairs): the slot loops stay
@@ -557,8 +570,14 @@ __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, 
   const float inv_w = P.inv_w, hw = 0.5f * P.wdx_l, T = hw + kClipMargin;
   // evaluators with a staged line clip keep its constants in their (otherwise
   // unused) plane buffer
-  prep_clip_of(A, r, swap, L, T, smA, 0);
-  prep_clip_of(B, r, !swap, L, T, smB, 0);
+  if constexpr (std::is_same<EA, CubeEval>::value && std::is_same<EB, CubeEval>::value) {
+    // two cubes in one pass: lanes 0 .. 3 form A's constants, lanes 4 .. 7 B's
+    const bool isb = (lane & 4) != 0;
+    CubeEval::prep_lanes(r, isb ? !swap : swap, L, T, isb ? smB : smA, lane < 8 ? (lane & 3) : 4);
+  } else {
+    prep_clip_of(A, r, swap, L, T, smA, 0);
+    prep_clip_of(B, r, !swap, L, T, smB, 0);
+  }
   __syncwarp();
   fetch_of(A, smA, 0);
   fetch_of(B, smB, 0);
@@ -572,13 +591,21 @@ __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, 
   // a pair box is below 2^16 nodes along an axis
   unsigned pk[kTileItemsPerLane];
   int nl = 0;
+  // line it0 + 32 s + lane as (cv, cw) = its remainder and quotient by dv:
+  // unrolled, one division for slot 0, then steps of 32 = q32 dv + r32; the
+  // rolled loop divides per slot (fewer live registers)
+  int cv = 0, r32 = 0, q32 = 0;
+  int cw = 0;
+  if constexpr (!ROLL) {
+    cw = div_small(it0 + lane, dv, inv_dv, &cv);
+    q32 = div_small(32, dv, inv_dv, &r32);
+  }
 #pragma unroll(ROLL ? 1 : kTileItemsPerLane)
   for (int s = 0; s < kTileItemsPerLane; ++s) {
     if (!ROLL) pk[s] = 0u;
     if (s < ns) {
       const int it = it0 + s * 32 + lane;
-      int cv;
-      const int cw = div_small(it, dv, inv_dv, &cv);
+      if constexpr (ROLL) cw = div_small(it, dv, inv_dv, &cv);
       const int len = it < r.nitems ? du : 0;
       float clo = 0.f, chi = static_cast<float>(len - 1);
       clip_line_of(A, r, swap, L, csA, cv, cw, T, clo, chi, 0);
@@ -589,6 +616,14 @@ __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, 
       if constexpr (ROLL) spk[s * 32 + lane] = v;
       else pk[s] = v;
       nl += nk;
+    }
+    if constexpr (!ROLL) {
+      cv += r32;
+      cw += q32;
+      if (cv >= dv) {
+        cv -= dv;
+        ++cw;
+      }
     }
   }
   if (ROLL) __syncwarp();
@@ -611,8 +646,11 @@ __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, 
         own[rank] = make_int4(lane, excl, 0, 0);
       } else {
         static_assert(kTileItemsPerLane == 4, "own holds four clipped ranges per lane");
+        // and the lane's node counts before slots 2 and 3
+        const int c2 = static_cast<int>(pk[0] >> 16) + static_cast<int>(pk[1] >> 16);
         own[rank] = make_int4(lane, excl, static_cast<int>(pk[0]), static_cast<int>(pk[1]));
-        own[32 + rank] = make_int4(static_cast<int>(pk[2]), static_cast<int>(pk[3]), 0, 0);
+        own[32 + rank] = make_int4(static_cast<int>(pk[2]), static_cast<int>(pk[3]), c2,
+                                   c2 + static_cast<int>(pk[2] >> 16));
       }
     }
     __syncwarp();
@@ -633,19 +671,26 @@ __device__ __forceinline__ Partial sweep_tile(const Params& P, const Shapes& S, 
     int4 e2 = make_int4(0, 0, 0, 0);
     if (!ROLL) e2 = own[32 + min(max(cnt_le - 1, 0), 31)];
     int os = 0, u = 0;
-#pragma unroll(ROLL ? 1 : kTileItemsPerLane)
-    for (int s = 0; s < kTileItemsPerLane; ++s) {
-      if (s < ns) {
-        unsigned q;
-        if constexpr (ROLL) q = spk[s * 32 + o];
-        else q = static_cast<unsigned>(s == 0 ? e.z : (s == 1 ? e.w : (s == 2 ? e2.x : e2.y)));
-        const int n = static_cast<int>(q >> 16);
-        if (k >= 0 && k < n) {
-          os = s;
-          u = static_cast<int>(q & 0xffffu) + k;
+    if constexpr (ROLL) {
+#pragma unroll 1
+      for (int s = 0; s < kTileItemsPerLane; ++s) {
+        if (s < ns) {
+          const unsigned q = spk[s * 32 + o];
+          const int n = static_cast<int>(q >> 16);
+          if (k >= 0 && k < n) {
+            os = s;
+            u = static_cast<int>(q & 0xffffu) + k;
+          }
+          k -= n;
         }
-        k -= n;
       }
+    } else {
+      // the slot: how many of the owner's slot boundaries (node counts before
+      // slots 1, 2, 3; empty slots repeat a boundary) lie at or below k
+      const int c1 = static_cast<int>(static_cast<unsigned>(e.z) >> 16), c2 = e2.z, c3 = e2.w;
+      os = (k >= c1 ? 1 : 0) + (k >= c2 ? 1 : 0) + (k >= c3 ? 1 : 0);
+      const unsigned q = static_cast<unsigned>(os == 0 ? e.z : (os == 1 ? e.w : (os == 2 ? e2.x : e2.y)));
+      u = static_cast<int>(q & 0xffffu) + k - (os == 0 ? 0 : (os == 1 ? c1 : (os == 2 ? c2 : c3)));
     }
     int ocv;
     const int ocw = div_small(it0 + os * 32 + o, dv, inv_dv, &ocv);
@@ -879,7 +924,8 @@ template <bool SMOOTH, int SET>
 __device__ __forceinline__ Partial dispatch(const Params& P, const Shapes& S, const Parts& D, const PairRec& r,
                                             int tl, float4* smA, float4* smB, unsigned* spk, int4* own) {
   int ka = r.kinds & 0xff, kb = r.kinds >> 8;
-  const bool swap = sweep_swap(ka, kb);   // evaluate the cheaper kind as A; G's sign flips back below
+  // evaluate the cheaper kind as A (G's sign flips back below); two cubes keep the record's order
+  const bool swap = SET == SET_CUBE ? false : sweep_swap(ka, kb);
   if (swap) {
     const int t = ka; ka = kb; kb = t;
   }

@@ -30,9 +30,6 @@ constexpr float kClipMargin = 1e-3f;     // cells, added to the threshold of the
 constexpr float kClipFlat = 1e-20f;      // a face this parallel to the line is constant along it
 constexpr float kClipEmpty = 3.0e38f;    // a lower bound that empties the interval
 
-// 1 / a for the clip (0 for faces parallel to the line: they take the constant
-// branch); the approximate reciprocal's relative error (~2^-22) moves a bound
-// by far less than the margin.
 // Three-operand maximum and minimum (one instruction each on this GPU; like
 // fmaxf / fminf, a NaN operand gives way to the others).
 __device__ __forceinline__ float max3f(float a, float b, float c) {
@@ -46,6 +43,9 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
   return d;
 }
 
+// 1 / a for the clip (0 for faces parallel to the line: they take the constant
+// branch); the approximate reciprocal's relative error (~2^-22) moves a bound
+// by far less than the margin.
 __device__ __forceinline__ float clip_inv(float a) { return fabsf(a) > kClipFlat ? __fdividef(1.f, a) : 0.f; }
 
 // |t c + p| < T: c in ((-T - p) / t, (T - p) / t), ordered by the sign of t.
