@@ -608,9 +608,19 @@ def extras(args, dev, flush, peak):
         m = Contact.from_state(st_b, narrow_events=True)
         r = time_forward(m, pd, qd, steps, 3, flush, narrow=True)
         s_ = m.stats()
+        # roofline of the box kernel: the nominal FP32 lane-ops of its sample
+        # tests (the overlapping pairs' N_c^3 samples, the same ops per test as
+        # the node sweep's) against the FP32 peak; its FP64 pipe is the busier
+        # unit (ncu: 55 % of active cycles at N_c = 8)
+        kern_s = r["narrow_ms"] / steps * 1e-3
+        ops_per_test = s_["nominal_ops"] / max(s_["cells"], 1)
+        sample_ops = s_["overlapping"] * nc ** 3 * ops_per_test
         boxm[f"nc{nc}"] = {"ms_per_step": r["ms"] / steps, "box_kernel_ms": r["narrow_ms"] / steps,
                            "pairs": s_["pairs"], "pairs_with_overlap": s_["overlapping"],
-                           "samples_per_step": s_["pairs"] * nc ** 3}
+                           "samples_per_step": s_["overlapping"] * nc ** 3,
+                           "roofline": {"bound": "fp64 pipe", "achieved": sample_ops / kern_s / 1e12,
+                                        "peak": peak, "unit": "T FP32 lane-ops/s (sample tests)",
+                                        "frac": sample_ops / kern_s / (peak * 1e12)}}
         m.close()
     # N_c = 8 with the contact history (each contact's c and its corrected box,
     # the next correction's warm start) and friction, velocities as above
