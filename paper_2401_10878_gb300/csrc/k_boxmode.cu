@@ -181,9 +181,8 @@ __device__ void clip_d(const Params& P, const Shapes& S, const Parts& D, int pid
   // lower bound -a0/b0 (b0 < 0), upper bound -a1/b1 (b1 > 0); none yet: b = 0
   double a0 = 0.0, b0 = 0.0, a1 = 0.0, b1 = 0.0;
   bool empty = false;
-  auto plane = [&](double n0, double n1, double n2, double off) {
-    const double a = ((n0 * p[0] + n1 * p[1]) + n2 * p[2]) - off;
-    const double b = sgn * (k == 0 ? n0 : (k == 1 ? n1 : n2));
+  // the half-line a + b t <= 0 of one face along the line
+  auto bound = [&](double a, double b) {
     if (b > 0.0) {   // t <= -a/b: keep the smaller, -a/b < -a1/b1  <=>  a b1 > a1 b
       if (b1 == 0.0 || a * b1 > a1 * b) { a1 = a; b1 = b; }
     } else if (b < 0.0) {   // t >= -a/b: keep the larger, -a/b > -a0/b0  <=>  a b0 < a0 b (b b0 > 0)
@@ -192,12 +191,19 @@ __device__ void clip_d(const Params& P, const Shapes& S, const Parts& D, int pid
       empty = true;
     }
   };
-  if (type == 1) {   // cuboid
-    for (int a = 0; a < 3; ++a)
-      for (int sg = -1; sg <= 1; sg += 2) {
-        const double n0 = sg * R[a], n1 = sg * R[3 + a], n2 = sg * R[6 + a];   // +-R e_a
-        plane(n0, n1, n2, ((n0 * X[0] + n1 * X[1]) + n2 * X[2]) + S.param[3 * pid + a] + P.inflate);
-      }
+  auto plane = [&](double n0, double n1, double n2, double off) {
+    bound(((n0 * p[0] + n1 * p[1]) + n2 * p[2]) - off, sgn * (k == 0 ? n0 : (k == 1 ? n1 : n2)));
+  };
+  if (type == 1) {   // cuboid: faces +-R e_a share n = R e_a and d = n . (p - X)
+    const double q0 = p[0] - X[0], q1 = p[1] - X[1], q2 = p[2] - X[2];
+    for (int a = 0; a < 3; ++a) {
+      const double n0 = R[a], n1 = R[3 + a], n2 = R[6 + a];
+      const double d = (n0 * q0 + n1 * q1) + n2 * q2;
+      const double h = S.param[3 * pid + a] + P.inflate;
+      const double b = sgn * (k == 0 ? n0 : (k == 1 ? n1 : n2));
+      bound(d - h, b);     // n . (x - X) <= h
+      bound(-d - h, -b);   // -n . (x - X) <= h
+    }
   } else {   // polytope, or a wall's single plane
     const int f0 = S.face_off[pid], nf = S.face_off[pid + 1] - f0;
     for (int f = 0; f < nf; ++f) {
