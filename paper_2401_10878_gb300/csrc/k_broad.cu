@@ -365,6 +365,7 @@ __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
   const int nnb = cnt[0] * cnt[1] * cnt[2];
   int num = 0;
   const int* items = W.bin_items;
+  int pre[4] = {-1, -1, -1, -1};   // the bin's next four entries (the first ones fetched with its count)
   if (lane < nnb) {
     int o[3] = {lane % cnt[0], (lane / cnt[0]) % cnt[1], lane / (cnt[0] * cnt[1])};
 #pragma unroll
@@ -374,8 +375,11 @@ __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
     }
     const int q = checked_index(W.err, o[0] + P.nbin[0] * (o[1] + P.nbin[1] * o[2]),
                                 static_cast<long long>(P.nbin[0]) * P.nbin[1] * P.nbin[2], bin);
-    num = min(W.bin_count[q], P.bin_cap);
     items += static_cast<size_t>(q) * P.bin_cap;
+    // (entries past the count are stale and unused)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) pre[u] = u < P.bin_cap ? items[u] : -1;
+    num = min(W.bin_count[q], P.bin_cap);
   }
   const int maxn = __reduce_max_sync(kFull, num);
   int nup = 0, ndn = 0;
@@ -383,7 +387,10 @@ __global__ void __launch_bounds__(256) k_broad(Params P, Parts D, Lists W) {
   for (int t0 = 0; t0 < maxn; t0 += 4) {
     int jj[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) jj[u] = t0 + u < num ? checked_index(W.err, items[t0 + u], P.n, -1) : -1;
+    for (int u = 0; u < 4; ++u) jj[u] = t0 + u < num ? checked_index(W.err, pre[u], P.n, -1) : -1;
+    // the next four entries, fetched with this round's candidate data
+#pragma unroll
+    for (int u = 0; u < 4; ++u) pre[u] = t0 + 4 + u < num ? items[t0 + 4 + u] : -1;
     float xj[4][3];
     int jlo[4][3], jhi[4][3];
 #pragma unroll
