@@ -243,16 +243,17 @@ def _touch_offset(st_i, st_j, ci, base, direction, lo, hi):
     return lo
 
 
-def mixed_grid_27(seed: int = 1) -> State:
-    """27 particles (14 spheres of diameter 15, 13 cubes of edge 12) on a
-    jittered 3x3x3 grid in a periodic 64^3 lattice.  Along every periodic grid
-    line two of the three neighbour gaps are closed (the same open gap for all
-    lines of one axis): the partner moves along the axis to first touch and then
-    on by a penetration drawn from U(0, 1.5)."""
+def mixed_grid_27(seed: int = 1, cuboid_half=(6.0, 6.0, 6.0)) -> State:
+    """27 particles (14 spheres of diameter 15, 13 cubes of edge 12, or
+    cuboids of the given half extents) on a jittered 3x3x3 grid in a periodic
+    64^3 lattice.  Along every periodic grid line two of the three neighbour
+    gaps are closed (the same open gap for all lines of one axis): the partner
+    moves along the axis to first touch and then on by a penetration drawn
+    from U(0, 1.5)."""
     rng = np.random.default_rng(seed)
     n, L = 27, 64.0
     types = np.array([SPHERE] * 14 + [CUBOID] * 13)[rng.permutation(27)]
-    params = np.where(types[:, None] == SPHERE, [[7.5, 7.5, 7.5]], [[6.0, 6.0, 6.0]]).astype(np.float64)
+    params = np.where(types[:, None] == SPHERE, [[7.5, 7.5, 7.5]], [list(cuboid_half)]).astype(np.float64)
     a = L / 3
     g = np.stack(np.meshgrid(np.arange(3), np.arange(3), np.arange(3), indexing="ij"), -1).reshape(-1, 3)
     pos = (g + 0.5) * a + rng.uniform(-1, 1, size=(n, 3))

@@ -48,6 +48,15 @@ def test_mixed27_box_pipeline(nc):
     assert np.count_nonzero(r.pair_out[:, 0]) > 20
 
 
+def test_elongated_cuboids_box_pipeline():
+    """Cuboids of unequal half extents (7, 5, 4) with spheres: the pair
+    builder's cut of two boxes' node box and the FP64 re-clip with per-axis
+    extents."""
+    rep, r = run(boxed(W.mixed_grid_27(cuboid_half=(7.0, 5.0, 4.0))))
+    print("mixed27 cuboids box", rep)
+    assert rep.pairs > 40
+
+
 def test_cubes400_box_pipeline():
     rep, _ = run(boxed(W.settling_cubes()))
     print("cubes400 box", rep)

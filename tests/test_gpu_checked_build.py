@@ -62,6 +62,9 @@ def _cases():
     st = W.mixed_grid_27()
     st.indicator = 0
     c["mixed27_fp64_form"] = (st, dict(precision=1))
+    st = W.mixed_grid_27(cuboid_half=(7.0, 5.0, 4.0))
+    st.indicator = 0
+    c["mixed27_elongated_cuboids"] = (st, {})
     st = W.settling_cubes()
     st.indicator = 0
     st.box_mode, st.contact_resolution = 1, 8

@@ -52,6 +52,20 @@ def test_mixed27_grid(states, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("smooth", [False, True])
+def test_mixed27_elongated_cuboids(precision, smooth):
+    """Spheres and cuboids of unequal half extents (7, 5, 4): the sphere /
+    cuboid kernel variant with per-axis slabs (every other workload's cuboids
+    are cubes)."""
+    st = W.mixed_grid_27(cuboid_half=(7.0, 5.0, 4.0))
+    if smooth:
+        st.indicator, st.smooth_width = 1, 1.0
+    rep = run_parity(st, precision)
+    print("mixed27 cuboids", precision, smooth, rep)
+    assert rep.pairs > 40
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 def test_cubes400_settling(states, precision):
     print("cubes400", precision, run_parity(states["c2"], precision))
 
