@@ -64,6 +64,15 @@ def test_spheres_and_cuboids_walls():
     assert walls >= 6
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_elongated_cuboids_walls(precision):
+    """Cuboids of unequal half extents (7, 5, 4) and spheres against a floor,
+    a ceiling and an oblique wall: the wall-cuboid evaluator pair."""
+    rep, walls = run(oblique(W.mixed_grid_27(cuboid_half=(7.0, 5.0, 4.0)), gap=1.0), precision)
+    print("mixed27 cuboids + walls", precision, rep, "wall pairs", walls)
+    assert walls >= 6
+
+
 def test_face_aligned_cube_on_floor_exact():
     X = np.array([30.5, 31.5, 20.5])
     st = W.with_walls(state([1], [[4, 4, 4]], [X]), [[0, 0, 1, 19.5]])
