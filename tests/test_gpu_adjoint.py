@@ -51,11 +51,13 @@ def _per_component(g, ref, s):
     return ratio.max(initial=0.0), (np.percentile(rel, [50, 99, 100]) if rel.size else [0, 0, 0])
 
 
-@pytest.mark.parametrize("name", ["mixed27", "cubes1934", "mixed1934"])
+@pytest.mark.parametrize("name", ["mixed27", "mixed27_cuboids", "cubes1934", "mixed1934"])
 def test_adjoint_matches_oracle_gradient(name):
-    """mixed27: spheres and cubes; cubes1934: cubes only; mixed1934: spheres,
+    """mixed27: spheres and cubes; mixed27_cuboids: spheres and cuboids of
+    unequal half extents (7, 5, 4); cubes1934: cubes only; mixed1934: spheres,
     cubes and polytopes (every kind set of the adjoint's cell sweep)."""
-    st = {"mixed27": W.mixed_grid_27, "cubes1934": W.settling_cubes_dense, "mixed1934": W.mixed_settling}[name]()
+    st = {"mixed27": W.mixed_grid_27, "mixed27_cuboids": lambda: W.mixed_grid_27(cuboid_half=(7.0, 5.0, 4.0)),
+          "cubes1934": W.settling_cubes_dense, "mixed1934": W.mixed_settling}[name]()
     st.indicator, st.smooth_width = 1, 1.0
     gf, gt = W.loss_weights(st.n)
     gp, gq = _grad_gpu(st, gf, gt)
